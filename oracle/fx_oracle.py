@@ -1,0 +1,286 @@
+"""FP64 oracle of the FX correlator hot path -- TEST INFRASTRUCTURE ONLY.
+
+Every function is the plain definition of one step, written in numpy float64 /
+complex128, with no blocking, fusion or reordering beyond what the definition
+states.  Library primitives used as single steps: ``numpy.fft.rfft`` (the
+channeliser at full size; pinned against :func:`dft_brute`), ``numpy.einsum``
+(the correlation sum) and ``numpy.sort`` (order statistics).
+
+Paper passages followed (arXiv 2604.20640):
+
+* Eq. 1 (Sec. 4.1): cross-power spectrum S_ij(nu) = < V_i V_j^* e^{j 2 pi nu tau_g,ij} >,
+  the geometric delay compensated by a linear phase, <.> a time integration.
+* Sec. 4.2, "F-engine (PFB and FFT)": raw samples unpacked to voltages, a
+  polyphase-filter-bank weighting, then an FFT (Fig. 4 shows the PFB's lower
+  sidelobes against a rectangular-window FFT).
+* Sec. 4.2, "X-engine and integration" and Algorithm 1: V_i V_j^* for all
+  baselines accumulated over the integration interval.
+* Eq. 2 (Sec. 7): MAD sigma clipping, T = median(A) + sigma * MAD(A) * 1.4826,
+  sigma = 5, on visibility amplitude A.
+
+Readings where the paper is silent (each also recorded in the design notes):
+
+1. Prototype filter: symmetric Hann window (denominator L-1) times a sinc with
+   cutoff 1/M centred at (L-1)/2, L = P*M, unnormalised.
+2. Zero history before the first sample: spectrum s (s = 0 .. S//M - 1) uses
+   frames s-P+1 .. s, frames before the stream are zero.
+3. Real samples, M = 2*n_chan point real transform, DC kept, Nyquist dropped.
+4. Forward transform sign e^{-j...}, unscaled.
+5. Delay correction per input: coarse advance by d = floor(tau + 1/2) samples
+   (x'[n] = x[n+d], zero outside the stream), then the fine phase
+   exp(+j 2 pi k r / M) with r = tau - d, then the instrument phase exp(-j phi).
+   Eq. 1's per-baseline factor exp(j 2 pi nu (tau_i - tau_j)) factorises into
+   these per-input terms.
+6. <.> is the mean over n_int consecutive spectra; a partial last integration
+   is emitted only at end of stream, divided by its actual count.
+7. Visibility R[k][a][b] = <V_a[k] conj(V_b[k])>, full Hermitian matrix.
+8. MAD flagging per integration, per baseline (a, b) (autos included), on
+   windows of ``window`` channels aligned at channel 0; A = |R_ab|; even-count
+   median = mean of the two middle order statistics; MAD = 0 not special-cased;
+   flag = A > T (strict, upper one-sided).
+"""
+
+from __future__ import annotations
+
+import math
+from typing import Optional, Sequence
+
+import numpy as np
+
+MAD_TO_SIGMA = 1.4826   # Eq. 2
+
+
+# --------------------------------------------------------------------------
+# F-engine
+# --------------------------------------------------------------------------
+
+def pfb_coefficients(M: int, P: int) -> np.ndarray:
+    """Prototype FIR h[n], n = 0 .. P*M-1 (Sec. 4.2 PFB weighting; reading 1)."""
+    L = P * M
+    if L < 2:
+        raise ValueError("P*M must be at least 2")
+    n = np.arange(L, dtype=np.float64)
+    w = 0.5 - 0.5 * np.cos(2.0 * np.pi * n / (L - 1))
+    x = (n - (L - 1) / 2.0) / M
+    sinc = np.ones(L)
+    nz = x != 0.0
+    sinc[nz] = np.sin(np.pi * x[nz]) / (np.pi * x[nz])
+    return w * sinc
+
+
+def split_delay(tau) -> tuple:
+    """Coarse integer advance d = floor(tau + 1/2) and fine remainder r = tau - d."""
+    tau = np.asarray(tau, dtype=np.float64)
+    d = np.floor(tau + 0.5)
+    return d.astype(np.int64), tau - d
+
+
+def coarse_shift(x: np.ndarray, d: int) -> np.ndarray:
+    """x'[n] = x[n + d] for 0 <= n + d < S, else 0 (reading 5)."""
+    x = np.asarray(x, dtype=np.float64)
+    S = x.shape[-1]
+    out = np.zeros(S)
+    lo, hi = max(0, -d), min(S, S - d)
+    if hi > lo:
+        out[lo:hi] = x[lo + d: hi + d]
+    return out
+
+
+def pfb_fir(xp: np.ndarray, h: np.ndarray, M: int, P: int) -> np.ndarray:
+    """y[s][m] = sum_p h[pM + m] x'[(s - P + 1 + p) M + m], zero frames before 0."""
+    n_spec = xp.shape[-1] // M
+    frames = xp[: n_spec * M].reshape(n_spec, M)
+    y = np.zeros((n_spec, M))
+    for p in range(P):
+        shift = P - 1 - p               # frame index s - shift
+        if shift >= n_spec:
+            continue
+        y[shift:] += h[p * M:(p + 1) * M][None, :] * frames[: n_spec - shift]
+    return y
+
+
+def dft_brute(y: np.ndarray) -> np.ndarray:
+    """Y[k] = sum_m y[m] e^{-j 2 pi k m / M}, k = 0 .. M/2-1, by direct summation."""
+    M = y.shape[-1]
+    k = np.arange(M // 2)[:, None]
+    m = np.arange(M)[None, :]
+    W = np.exp(-2j * np.pi * ((k * m) % M) / M)
+    return y @ W.T
+
+
+def channelise(y: np.ndarray) -> np.ndarray:
+    """Same sum as :func:`dft_brute`, through numpy's FFT (library step)."""
+    M = y.shape[-1]
+    return np.fft.rfft(y, axis=-1)[..., : M // 2]
+
+
+def fine_correct(Y: np.ndarray, r: float, phi: float, M: int) -> np.ndarray:
+    """V[k] = Y[k] exp(j (2 pi k r / M - phi))  (Eq. 1 phase term; reading 5)."""
+    k = np.arange(Y.shape[-1])
+    return Y * np.exp(1j * (2.0 * np.pi * k * r / M - phi))
+
+
+def f_engine(x: np.ndarray, n_chan: int, taps: int, tau=None, phi=None,
+             h: Optional[np.ndarray] = None, brute: bool = False) -> np.ndarray:
+    """Channelised, delay-corrected voltages V[a][s][k] (complex128).
+
+    ``x`` is ``[n_in][S]``; ``tau`` total delays in samples, ``phi`` instrument
+    phases in radians (both per input, default 0).
+    """
+    x = np.asarray(x)
+    n_in = x.shape[0]
+    M = 2 * n_chan
+    if h is None:
+        h = pfb_coefficients(M, taps)
+    tau = np.zeros(n_in) if tau is None else np.asarray(tau, np.float64)
+    phi = np.zeros(n_in) if phi is None else np.asarray(phi, np.float64)
+    d, r = split_delay(tau)
+    n_spec = x.shape[1] // M
+    V = np.empty((n_in, n_spec, n_chan), dtype=np.complex128)
+    for a in range(n_in):
+        xp = coarse_shift(x[a], int(d[a]))
+        y = pfb_fir(xp, h, M, taps)
+        Y = dft_brute(y) if brute else channelise(y)
+        V[a] = fine_correct(Y, float(r[a]), float(phi[a]), M)
+    return V
+
+
+def f_engine_sampled(x: np.ndarray, n_chan: int, taps: int, tau, phi, spectra: Sequence[int],
+                     chans: Sequence[int]) -> np.ndarray:
+    """V[a][i][j] for spectrum ``spectra[i]`` and channel ``chans[j]`` only.
+
+    Each value is the direct sum of the definition (filter then one DFT row),
+    so it scales to streams of any length.
+    """
+    x = np.asarray(x)
+    n_in = x.shape[0]
+    M = 2 * n_chan
+    h = pfb_coefficients(M, taps)
+    d, r = split_delay(np.asarray(tau, np.float64))
+    phi = np.asarray(phi, np.float64)
+    chans = np.asarray(chans)
+    m = np.arange(M)
+    rows = np.exp(-2j * np.pi * ((chans[:, None] * m[None, :]) % M) / M)
+    S = x.shape[1]
+    out = np.empty((n_in, len(spectra), len(chans)), dtype=np.complex128)
+    for a in range(n_in):
+        rot = np.exp(1j * (2.0 * np.pi * chans * r[a] / M - phi[a]))
+        for i, s in enumerate(spectra):
+            y = np.zeros(M)
+            for p in range(taps):
+                f = s - taps + 1 + p
+                if f < 0:
+                    continue
+                idx = f * M + m + d[a]
+                ok = (idx >= 0) & (idx < S)
+                xs = np.zeros(M)
+                xs[ok] = x[a, idx[ok]]
+                y += h[p * M:(p + 1) * M] * xs
+            out[a, i] = (rows @ y) * rot
+    return out
+
+
+# --------------------------------------------------------------------------
+# X-engine and integration
+# --------------------------------------------------------------------------
+
+def x_engine(V: np.ndarray, n_int: int, partial: bool = False) -> np.ndarray:
+    """R[i][k][a][b] = (1/count) sum_{s in integration i} V_a,s[k] conj(V_b,s[k])."""
+    n_in, n_spec, n_chan = V.shape
+    n_full = n_spec // n_int
+    starts = [i * n_int for i in range(n_full)]
+    if partial and n_spec % n_int:
+        starts.append(n_full * n_int)
+    R = np.empty((len(starts), n_chan, n_in, n_in), dtype=np.complex128)
+    for i, s0 in enumerate(starts):
+        s1 = min(s0 + n_int, n_spec)
+        blk = V[:, s0:s1, :]
+        R[i] = np.einsum('ask,bsk->kab', blk, blk.conj()) / (s1 - s0)
+    return R
+
+
+# --------------------------------------------------------------------------
+# MAD flagging (Eq. 2)
+# --------------------------------------------------------------------------
+
+def median_exact(v: np.ndarray) -> float:
+    """Median by sorting; even count -> mean of the two middle order statistics."""
+    s = np.sort(np.asarray(v, dtype=np.float64).ravel())
+    n = s.size
+    if n == 0:
+        raise ValueError("median of empty set")
+    if n % 2:
+        return float(s[n // 2])
+    return 0.5 * (float(s[n // 2 - 1]) + float(s[n // 2]))
+
+
+def mad_threshold(A: np.ndarray, sigma: float = 5.0) -> float:
+    """T = median(A) + sigma * MAD(A) * 1.4826 with MAD = median(|A - median(A)|)."""
+    med = median_exact(A)
+    mad = median_exact(np.abs(np.asarray(A, np.float64) - med))
+    return med + sigma * mad * MAD_TO_SIGMA
+
+
+def mad_flags(R: np.ndarray, sigma: float = 5.0, window: int = 64):
+    """Flags[i][k][a][b] (uint8) and the thresholds T[i][k][a][b] for R[i][k][a][b]."""
+    n_i, n_chan, n_in, _ = R.shape
+    w = min(window, n_chan)
+    if n_chan % w:
+        raise ValueError("n_chan must be a multiple of the flag window")
+    A = np.abs(R)
+    T = np.empty(A.shape)
+    for i in range(n_i):
+        for a in range(n_in):
+            for b in range(n_in):
+                for k0 in range(0, n_chan, w):
+                    T[i, k0:k0 + w, a, b] = mad_threshold(A[i, k0:k0 + w, a, b], sigma)
+    flags = (A > T).astype(np.uint8)
+    return flags, A, T
+
+
+# --------------------------------------------------------------------------
+# Whole hot path
+# --------------------------------------------------------------------------
+
+def correlate(x: np.ndarray, n_chan: int, taps: int, n_int: int, tau=None, phi=None,
+              sigma: float = 5.0, window: int = 64, partial: bool = False,
+              schedule: Optional[Sequence[tuple]] = None):
+    """Visibilities R[i][k][a][b] and MAD flags for a whole stream (Algorithm 1).
+
+    ``schedule`` optionally gives one ``(tau, phi)`` per integration (a delay
+    change takes effect at an integration boundary); otherwise ``tau``/``phi``
+    hold throughout.
+    """
+    if schedule is None:
+        V = f_engine(x, n_chan, taps, tau, phi)
+    else:
+        M = 2 * n_chan
+        n_spec = np.asarray(x).shape[1] // M
+        V = None
+        cache = {}
+        for i, (t, p) in enumerate(schedule):
+            s0, s1 = i * n_int, min((i + 1) * n_int, n_spec)
+            if s0 >= n_spec:
+                break
+            key = (tuple(np.asarray(t, np.float64)), tuple(np.asarray(p, np.float64)))
+            if key not in cache:
+                cache[key] = f_engine(x, n_chan, taps, t, p)
+            if V is None:
+                V = np.empty_like(cache[key])
+            V[:, s0:s1] = cache[key][:, s0:s1]
+    R = x_engine(V, n_int, partial=partial)
+    flags, A, T = mad_flags(R, sigma, window)
+    return R, flags, T
+
+
+def rel_frobenius_per_channel(R_test: np.ndarray, R_ref: np.ndarray) -> np.ndarray:
+    """||R_test[.., k] - R_ref[.., k]||_F / ||R_ref[.., k]||_F per (integration, channel)."""
+    num = np.sqrt(np.sum(np.abs(R_test - R_ref) ** 2, axis=(-2, -1)))
+    den = np.sqrt(np.sum(np.abs(R_ref) ** 2, axis=(-2, -1)))
+    return num / np.maximum(den, 1e-300)
+
+
+def normalised_coefficients(R: np.ndarray) -> np.ndarray:
+    """rho_ab = R_ab / sqrt(R_aa R_bb) per channel."""
+    d = np.sqrt(np.abs(np.einsum('...aa->...a', R)))
+    return R / np.maximum(d[..., :, None] * d[..., None, :], 1e-300)
