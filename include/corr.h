@@ -1,0 +1,191 @@
+/*
+ * corr.h -- C ABI of the GB300 FX correlator (libcorr.so).
+ *
+ * The library computes, on one GPU, the hot path of an FX software correlator
+ * (arXiv 2604.20640):
+ *
+ *   F-engine  (Sec. 4.2, "F-engine (PFB and FFT)"): int8 samples -> P-tap
+ *             windowed-sinc polyphase FIR over M = 2*n_chan branches -> M-point
+ *             real FFT (channels 0 .. n_chan-1, DC kept, Nyquist dropped),
+ *             with the geometric delay of Eq. 1 (Sec. 4.1) removed per input
+ *             as a coarse integer advance d = floor(tau + 1/2) plus a fine
+ *             phase exp(+j 2 pi k (tau - d) / M), and the instrument phase
+ *             removed as exp(-j phi).
+ *   X-engine  (Sec. 4.2, "X-engine and integration"; Algorithm 1):
+ *             R[k][a][b] = (1/n_int) sum_s V_a,s[k] conj(V_b,s[k]) over each
+ *             integration of n_int consecutive spectra, full Hermitian matrix.
+ *   Flagging  (Eq. 2, Sec. 7): per integration, baseline (a,b) and aligned
+ *             window of `flag_window` channels, A = |R_ab|,
+ *             T = median(A) + sigma * 1.4826 * MAD(A), flag = A > T.
+ *
+ * Conventions
+ *   - Every call returns a status (CORR_OK = 0 or a negative CORR_E* code)
+ *     and never aborts; corr_last_error() gives a message for the last
+ *     failure on that handle (or on handle creation when h is NULL).
+ *   - Inputs are n_in = n_ant * n_pol planes of int8 samples, input index
+ *     a = ant * n_pol + pol; plane a starts at samples + a * input_stride.
+ *   - Visibilities are complex64 stored as interleaved float pairs
+ *     (re, im), layout [integration][n_chan][n_in][n_in]; flags are uint8
+ *     in the same layout (symmetric in a, b).
+ *   - Host pointers are owned by the caller and may be reused as soon as a
+ *     call returns.  Device pointers (the *_dev calls) are owned by the
+ *     caller and must stay valid until the work queued on `stream` finishes.
+ *   - The library owns all of its own device memory and streams.  A handle
+ *     is not thread-safe: use one host thread per handle.
+ *   - `stream` arguments are cudaStream_t values passed as void*; NULL
+ *     means the legacy default stream.
+ */
+#ifndef CORR_H
+#define CORR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct corr_s* corr_t;
+
+enum {
+    CORR_OK = 0,
+    CORR_EINVAL = -1,     /* bad argument or shape */
+    CORR_ENOMEM = -2,     /* device or pinned allocation failed */
+    CORR_ECUDA = -3,      /* a CUDA runtime call failed */
+    CORR_EAGAIN = -4,     /* nothing ready yet (results) */
+    CORR_ETIMEDOUT = -5,  /* a bounded device wait expired */
+    CORR_ESTATE = -6      /* call not valid in the handle's current state */
+};
+
+/* Precision of the X-engine (option "precision"). */
+enum { CORR_FP32 = 0, CORR_INT8 = 1, CORR_FP8 = 2 };
+
+/*
+ * corr_create -- allocate a correlator.
+ *   n_ant, n_pol >= 1; n_in = n_ant*n_pol <= 256.
+ *   n_chan: power of two, 8 <= n_chan <= 8192 (M = 2*n_chan point real FFT;
+ *           the "FFT length" runtime parameter of Sec. 4.3).
+ *   taps:   PFB taps P, 1 <= P <= 16 (Sec. 4.3 "number of PFB taps").
+ *   n_int:  spectra per integration >= 1 (Sec. 4.3 "integration interval").
+ * Delays and phases start at zero.  Returns CORR_EINVAL on bad shapes and
+ * CORR_ENOMEM / CORR_ECUDA if device set-up fails (*out is then NULL).
+ */
+int corr_create(corr_t* out, int n_ant, int n_pol, int n_chan, int taps, int n_int);
+
+/* corr_destroy -- wait for queued work, free everything.  NULL is a no-op. */
+int corr_destroy(corr_t h);
+
+/* corr_last_error -- message of the last failed call on h (never NULL). */
+const char* corr_last_error(corr_t h);
+
+/*
+ * corr_set_option -- set a tunable before the first push (CORR_ESTATE after).
+ *   "flag_sigma"  (double > 0, default 5)     sigma of Eq. 2
+ *   "flag_window" (power of two, default 64)  channels per MAD window
+ *                 (min(window, n_chan) is used)
+ *   "max_delay"   (samples, default 4096)     bound on |coarse delay|
+ *   "chunk"       (samples/input, default 1<<23) largest device batch
+ *   "precision"   (CORR_FP32 / CORR_INT8 / CORR_FP8, default FP32)
+ *   "result_slots" (default 8)               pinned result FIFO depth (grows)
+ */
+int corr_set_option(corr_t h, const char* key, double value);
+
+/*
+ * corr_set_delays -- total delay per input in samples (FP64) and instrument
+ * phase per input in radians (NULL => zeros), Eq. 1.  The library splits
+ * tau into d = floor(tau + 1/2) and r = tau - d.  |d| must be <= max_delay.
+ * Before the first push the values apply from spectrum 0; afterwards they
+ * take effect at the next integration boundary, never mid-integration.
+ */
+int corr_set_delays(corr_t h, const double* delay_samples, const double* phase_rad);
+
+/*
+ * corr_push -- append n_per_input samples to every input from a host buffer
+ * (planar, plane a at samples + a*input_stride, input_stride >= n_per_input).
+ * The samples are copied to the device before the call returns, so the
+ * buffer may be reused at once; page-locked buffers are copied directly by
+ * DMA, others through the library's pinned staging.  Every spectrum whose
+ * samples are now all present is channelised and correlated; completed
+ * integrations are finalised, flagged and queued for corr_get_vis /
+ * corr_get_flags.  Any chunking of a stream gives bit-identical results.
+ */
+int corr_push(corr_t h, const int8_t* samples, size_t n_per_input, size_t input_stride);
+
+/*
+ * corr_push_dev -- as corr_push, from device memory d_samples (caller-owned,
+ * planar with input_stride), work queued on `stream`.  No host sync.
+ */
+int corr_push_dev(corr_t h, const int8_t* d_samples, size_t n_per_input,
+                  size_t input_stride, void* stream);
+
+/*
+ * corr_flush -- end of stream: samples past the end read as zero, the last
+ * spectra are processed, and a partial last integration (if any) is
+ * finalised with its actual spectrum count.  The handle then accepts no
+ * more pushes (CORR_ESTATE) until corr_reset.
+ */
+int corr_flush(corr_t h);
+
+/* corr_reset -- forget the stream (history, counters, queued results). */
+int corr_reset(corr_t h);
+
+/*
+ * corr_get_vis / corr_get_flags -- pop up to max_int completed integrations
+ * (oldest first) into the caller's host buffer out
+ * [max_int][n_chan][n_in][n_in] (vis: complex64 as float pairs; flags: uint8).
+ * Visibilities and flags are popped independently, in the same order.
+ * Blocks only until the oldest queued integration's copy has landed.
+ * *n_got receives the count (0 and CORR_EAGAIN when none is queued).
+ */
+int corr_get_vis(corr_t h, float* out, int max_int, int* n_got);
+int corr_get_flags(corr_t h, uint8_t* out, int max_int, int* n_got);
+
+/* corr_pending -- number of completed integrations not yet popped (vis). */
+int corr_pending(corr_t h, int* n);
+
+/*
+ * corr_run_dev -- whole-stream, device-resident form of the hot path:
+ * d_samples holds an entire stream of n_samples per input (zero history
+ * before sample 0, zero after the end), planar with input_stride.  Computes
+ * floor(n_samples / M) spectra with the handle's current delays, every
+ * complete integration (plus the partial last one if include_partial != 0),
+ * into caller-owned device buffers d_vis [n][n_chan][n_in][n_in] complex64
+ * and d_flags (same layout, uint8; may be NULL to skip flagging), with
+ * n <= max_int (CORR_EINVAL if too small).  *n_out = integrations written.
+ * Work is queued on `stream`; the handle's streaming state is untouched.
+ */
+int corr_run_dev(corr_t h, const int8_t* d_samples, size_t n_samples, size_t input_stride,
+                 float* d_vis, uint8_t* d_flags, int max_int, int include_partial,
+                 int* n_out, void* stream);
+
+/*
+ * Stateless stage entry points (device pointers, queued on `stream`), used
+ * to test and time the stages one by one.  They use the handle's shapes,
+ * filter, delays, phases and options only.
+ *
+ * corr_fengine_dev -- channelise spectra s0 .. s0+n_spec-1 of the
+ *   device-resident stream (same conventions as corr_run_dev) into
+ *   d_V [n_spec][n_chan][n_in_pad] complex64, n_in_pad = n_in rounded up to
+ *   a multiple of 4 (padding inputs are written as zeros).  Sec. 4.2 F-engine
+ *   with Eq. 1's delay and phase terms.
+ * corr_xengine_dev -- R[k][a][b] = (1/n_spec) sum_s V V^* over all n_spec
+ *   spectra of d_V (layout as above) into d_vis [n_chan][n_in][n_in]
+ *   complex64.  Sec. 4.2 X-engine.
+ * corr_flag_dev -- MAD flags (Eq. 2) of n_vis integrations d_vis into d_flags.
+ */
+int corr_fengine_dev(corr_t h, const int8_t* d_samples, size_t n_samples, size_t input_stride,
+                     long long s0, int n_spec, float* d_V, void* stream);
+int corr_xengine_dev(corr_t h, const float* d_V, int n_spec, float* d_vis, void* stream);
+int corr_flag_dev(corr_t h, const float* d_vis, int n_vis, uint8_t* d_flags, void* stream);
+
+/* Shapes of a handle: n_in, n_chan, taps, n_int, n_in_pad (any may be NULL). */
+int corr_shape(corr_t h, int* n_in, int* n_chan, int* taps, int* n_int, int* n_in_pad);
+
+/* Number of CUDA kernels this handle has launched (instrumentation). */
+long long corr_kernel_launches(corr_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CORR_H */

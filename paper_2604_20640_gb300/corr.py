@@ -1,0 +1,269 @@
+"""ctypes binding of libcorr.so (the C ABI declared in include/corr.h).
+
+Argument marshalling only: every step of the correlator runs in the CUDA
+library.  Device buffers are torch CUDA tensors (PyTorch supplies device
+memory and streams); host buffers are numpy arrays.  If the library has not
+been built, every call raises :class:`CorrError` -- there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcorr.so")
+
+CORR_OK = 0
+CORR_EINVAL = -1
+CORR_ENOMEM = -2
+CORR_ECUDA = -3
+CORR_EAGAIN = -4
+CORR_ETIMEDOUT = -5
+CORR_ESTATE = -6
+
+CORR_FP32, CORR_INT8, CORR_FP8 = 0, 1, 2
+
+# Every symbol the header declares (checked by the CPU test-suite).
+EXPORTED = [
+    "corr_create", "corr_destroy", "corr_last_error", "corr_set_option", "corr_set_delays",
+    "corr_push", "corr_push_dev", "corr_flush", "corr_reset", "corr_get_vis", "corr_get_flags",
+    "corr_pending", "corr_run_dev", "corr_fengine_dev", "corr_xengine_dev", "corr_flag_dev",
+    "corr_shape", "corr_kernel_launches",
+]
+
+
+class CorrError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("libcorr error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_ll = ctypes.c_longlong
+_sz = ctypes.c_size_t
+_d = ctypes.c_double
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libcorr.so and declare its signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise CorrError(CORR_ESTATE, "libcorr.so not built at %s (run __graft_entry__.build())" % path)
+    L = ctypes.CDLL(path)
+    sig = {
+        "corr_create": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _i, _i]),
+        "corr_destroy": (_i, [_vp]),
+        "corr_last_error": (ctypes.c_char_p, [_vp]),
+        "corr_set_option": (_i, [_vp, ctypes.c_char_p, _d]),
+        "corr_set_delays": (_i, [_vp, _vp, _vp]),
+        "corr_push": (_i, [_vp, _vp, _sz, _sz]),
+        "corr_push_dev": (_i, [_vp, _vp, _sz, _sz, _vp]),
+        "corr_flush": (_i, [_vp]),
+        "corr_reset": (_i, [_vp]),
+        "corr_get_vis": (_i, [_vp, _vp, _i, ctypes.POINTER(_i)]),
+        "corr_get_flags": (_i, [_vp, _vp, _i, ctypes.POINTER(_i)]),
+        "corr_pending": (_i, [_vp, ctypes.POINTER(_i)]),
+        "corr_run_dev": (_i, [_vp, _vp, _sz, _sz, _vp, _vp, _i, _i, ctypes.POINTER(_i), _vp]),
+        "corr_fengine_dev": (_i, [_vp, _vp, _sz, _sz, _ll, _i, _vp, _vp]),
+        "corr_xengine_dev": (_i, [_vp, _vp, _i, _vp, _vp]),
+        "corr_flag_dev": (_i, [_vp, _vp, _i, _vp, _vp]),
+        "corr_shape": (_i, [_vp] + [ctypes.POINTER(_i)] * 5),
+        "corr_kernel_launches": (_ll, [_vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dev_ptr(t, dtype_name: str):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise CorrError(CORR_EINVAL, "expected a CUDA tensor for a device buffer")
+    if not t.is_contiguous() and dtype_name != "samples":
+        raise CorrError(CORR_EINVAL, "device buffer must be contiguous")
+    return t.data_ptr()
+
+
+class Correlator:
+    """One correlator handle: ``corr_create(n_ant, n_pol, n_chan, taps, n_int)``."""
+
+    def __init__(self, n_ant: int, n_pol: int, n_chan: int, taps: int, n_int: int, **options):
+        self._L = load_library()
+        h = _vp()
+        rc = self._L.corr_create(ctypes.byref(h), n_ant, n_pol, n_chan, taps, n_int)
+        if rc != CORR_OK:
+            raise CorrError(rc, self._L.corr_last_error(None).decode())
+        self._h = h
+        self.n_ant, self.n_pol, self.n_chan, self.taps, self.n_int = n_ant, n_pol, n_chan, taps, n_int
+        self.n_in = n_ant * n_pol
+        self.n_in_pad = (self.n_in + 3) // 4 * 4
+        self.M = 2 * n_chan
+        for k, v in options.items():
+            self.set_option(k, v)
+
+    # -- helpers ----------------------------------------------------------
+    def _check(self, rc: int, allow=(CORR_OK,)):
+        if rc not in allow:
+            raise CorrError(rc, self._L.corr_last_error(self._h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.corr_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- configuration ----------------------------------------------------
+    def set_option(self, key: str, value: float):
+        self._check(self._L.corr_set_option(self._h, key.encode(), float(value)))
+
+    def set_delays(self, tau, phi=None):
+        tau = np.ascontiguousarray(tau, dtype=np.float64)
+        if tau.shape != (self.n_in,):
+            raise CorrError(CORR_EINVAL, "tau must have n_in entries")
+        pp = None
+        if phi is not None:
+            phi = np.ascontiguousarray(phi, dtype=np.float64)
+            if phi.shape != (self.n_in,):
+                raise CorrError(CORR_EINVAL, "phi must have n_in entries")
+            pp = phi.ctypes.data
+        self._check(self._L.corr_set_delays(self._h, tau.ctypes.data, pp))
+
+    # -- streaming --------------------------------------------------------
+    def push(self, samples):
+        """Append host samples ``[n_in][n]`` (int8 numpy array or CPU tensor)."""
+        try:
+            import torch
+            if isinstance(samples, torch.Tensor):
+                if samples.is_cuda:
+                    return self.push_dev(samples)
+                if samples.dtype != torch.int8 or samples.dim() != 2 or samples.shape[0] != self.n_in:
+                    raise CorrError(CORR_EINVAL, "samples must be int8 [n_in][n]")
+                if samples.stride(1) != 1:
+                    raise CorrError(CORR_EINVAL, "samples rows must be contiguous")
+                self._check(self._L.corr_push(self._h, samples.data_ptr(), samples.shape[1],
+                                              samples.stride(0)))
+                return
+        except ImportError:
+            pass
+        a = np.asarray(samples)
+        if a.dtype != np.int8 or a.ndim != 2 or a.shape[0] != self.n_in:
+            raise CorrError(CORR_EINVAL, "samples must be int8 [n_in][n]")
+        if a.strides[1] != 1:
+            a = np.ascontiguousarray(a)
+        self._check(self._L.corr_push(self._h, a.ctypes.data, a.shape[1], a.strides[0]))
+
+    def push_dev(self, samples, stream=None):
+        """Append device samples (CUDA int8 tensor ``[n_in][n]``, rows contiguous)."""
+        if samples.dim() != 2 or samples.shape[0] != self.n_in or samples.stride(1) != 1:
+            raise CorrError(CORR_EINVAL, "samples must be int8 [n_in][n] with contiguous rows")
+        self._check(self._L.corr_push_dev(self._h, _dev_ptr(samples, "samples"), samples.shape[1],
+                                          samples.stride(0), _stream_ptr(stream)))
+
+    def flush(self):
+        self._check(self._L.corr_flush(self._h))
+
+    def reset(self):
+        self._check(self._L.corr_reset(self._h))
+
+    def pending(self) -> int:
+        n = _i()
+        self._check(self._L.corr_pending(self._h, ctypes.byref(n)))
+        return n.value
+
+    def get_vis(self, max_int: Optional[int] = None) -> np.ndarray:
+        if max_int is None:
+            max_int = self.pending()
+        out = np.empty((max_int, self.n_chan, self.n_in, self.n_in), dtype=np.complex64)
+        got = _i()
+        self._check(self._L.corr_get_vis(self._h, out.ctypes.data, max_int, ctypes.byref(got)),
+                    allow=(CORR_OK, CORR_EAGAIN))
+        return out[: got.value]
+
+    def get_flags(self, max_int: Optional[int] = None) -> np.ndarray:
+        if max_int is None:
+            max_int = 1 << 20
+            # flags FIFO may be longer than the vis FIFO; pop what is there
+        out_list = []
+        got = _i()
+        while max_int > 0:
+            n = min(max_int, 64)
+            out = np.empty((n, self.n_chan, self.n_in, self.n_in), dtype=np.uint8)
+            rc = self._check(self._L.corr_get_flags(self._h, out.ctypes.data, n, ctypes.byref(got)),
+                             allow=(CORR_OK, CORR_EAGAIN))
+            out_list.append(out[: got.value])
+            max_int -= got.value
+            if rc == CORR_EAGAIN or got.value < n:
+                break
+        if not out_list:
+            return np.empty((0, self.n_chan, self.n_in, self.n_in), dtype=np.uint8)
+        return np.concatenate(out_list, axis=0)
+
+    # -- device-resident entry points ----------------------------------------
+    def n_integrations(self, n_samples: int, include_partial: bool = False) -> int:
+        n_spec = n_samples // self.M
+        return n_spec // self.n_int + (1 if include_partial and n_spec % self.n_int else 0)
+
+    def run_dev(self, samples, vis_out, flags_out=None, include_partial=False, stream=None) -> int:
+        """Whole stream on device: samples [n_in][S] int8 CUDA -> vis / flags."""
+        if samples.dim() != 2 or samples.shape[0] != self.n_in or samples.stride(1) != 1:
+            raise CorrError(CORR_EINVAL, "samples must be int8 [n_in][S] with contiguous rows")
+        n_out = _i()
+        max_int = vis_out.numel() * vis_out.element_size() // (8 * self.n_chan * self.n_in * self.n_in)
+        fp = _dev_ptr(flags_out, "flags") if flags_out is not None else None
+        self._check(self._L.corr_run_dev(self._h, _dev_ptr(samples, "samples"), samples.shape[1],
+                                         samples.stride(0), _dev_ptr(vis_out, "vis"), fp, int(max_int),
+                                         1 if include_partial else 0, ctypes.byref(n_out),
+                                         _stream_ptr(stream)))
+        return n_out.value
+
+    def fengine_dev(self, samples, s0: int, n_spec: int, V_out, stream=None):
+        if samples.dim() != 2 or samples.shape[0] != self.n_in or samples.stride(1) != 1:
+            raise CorrError(CORR_EINVAL, "samples must be int8 [n_in][S] with contiguous rows")
+        self._check(self._L.corr_fengine_dev(self._h, _dev_ptr(samples, "samples"), samples.shape[1],
+                                             samples.stride(0), int(s0), int(n_spec), _dev_ptr(V_out, "V"),
+                                             _stream_ptr(stream)))
+
+    def xengine_dev(self, V, n_spec: int, vis_out, stream=None):
+        self._check(self._L.corr_xengine_dev(self._h, _dev_ptr(V, "V"), int(n_spec), _dev_ptr(vis_out, "vis"),
+                                             _stream_ptr(stream)))
+
+    def flag_dev(self, vis, n_vis: int, flags_out, stream=None):
+        self._check(self._L.corr_flag_dev(self._h, _dev_ptr(vis, "vis"), int(n_vis),
+                                          _dev_ptr(flags_out, "flags"), _stream_ptr(stream)))
+
+    @property
+    def launches(self) -> int:
+        return int(self._L.corr_kernel_launches(self._h))

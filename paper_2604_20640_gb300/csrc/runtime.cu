@@ -1,0 +1,860 @@
+// Runtime and C ABI of libcorr: handles, device tables, the streaming state
+// (history carry-over between pushes, integration bookkeeping), the pinned
+// result FIFO and the whole-stream / per-stage device entry points.
+//
+// Streaming follows Algorithm 1 of the paper: samples arrive in pushes, are
+// copied host -> device on a copy stream, every spectrum whose samples are
+// all present is channelised (F-engine) and summed (X-engine) on a compute
+// stream, and each completed integration is finalised, flagged (Eq. 2) and
+// copied device -> host asynchronously.
+#include "corr.h"
+#include "corr_internal.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <string>
+#include <vector>
+
+using namespace corr;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Pipe {
+    long long s_next = 0;     // next spectrum to channelise
+    long long s_xdone = 0;    // first spectrum not yet summed into a partial slot
+    float2* V = nullptr;      // ring of channelised spectra
+    int v_cap = 0;
+    float* part = nullptr;    // [gpi][nt][32][n_chan]
+};
+
+struct Slot {
+    float2* d_R = nullptr;
+    uint8_t* d_F = nullptr;
+    float2* h_R = nullptr;
+    uint8_t* h_F = nullptr;
+    cudaEvent_t ev = nullptr;
+    bool in_vis = false, in_flag = false;
+};
+
+struct Tables {
+    float2* phasor = nullptr;   // [n_in_pad][n_chan]
+    int* coarse = nullptr;      // [n_in_pad]
+    int d_max = 0;              // largest coarse advance
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct corr_s {
+    int n_ant = 0, n_pol = 0, n_in = 0, n_in_pad = 0, n_chan = 0, M = 0, taps = 0, n_int = 0;
+    int nt = 0;        // 4x4 block-pairs of the Hermitian matrix
+    int G = 0;         // spectra per partial slot
+    int gpi = 0;       // partial slots per integration
+    int dev = 0;
+    // options
+    double flag_sigma = 5.0;
+    int flag_window = 64;
+    long long max_delay = 4096;
+    long long chunk = 1LL << 23;
+    int precision = CORR_FP32;
+    int result_slots = 8;
+    // constant tables
+    float* d_h = nullptr;
+    float2* d_tw = nullptr;
+    Tables tab_stream, tab_direct;
+    std::vector<double> tau, phi;            // latest values set
+    std::vector<double> tau_pend, phi_pend;  // waiting for an integration boundary
+    bool pending = false;
+    // streaming state
+    cudaStream_t s_comp = nullptr, s_copy = nullptr;
+    cudaEvent_t ev_h2d = nullptr, ev_comp = nullptr;
+    bool started = false, flushed = false, stream_alloc = false;
+    int8_t* d_stage = nullptr;
+    int8_t* d_tmp = nullptr;
+    long long stage_cap = 0, stage_base = 0, stage_len = 0, tmp_cap = 0;
+    int8_t* h_pin = nullptr;
+    long long pin_cap = 0;
+    long long n_pushed = 0;
+    Pipe ps;                 // stream pipe
+    Pipe pd;                 // whole-stream device pipe
+    float* d_part_x = nullptr;   // scratch of corr_xengine_dev
+    long long part_x_slots = 0;
+    std::vector<Slot> slots;
+    std::deque<int> q_vis, q_flag;
+    std::string err;
+    long long launches = 0;
+};
+
+namespace {
+
+int fail(corr_t h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+#define CK(call)                                                                      \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess)                                                        \
+            return fail(h, CORR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define CKRET(expr)              \
+    do {                         \
+        int r_ = (expr);         \
+        if (r_ != CORR_OK) return r_; \
+    } while (0)
+
+bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+
+size_t vis_elems(const corr_s* h) { return (size_t)h->n_chan * h->n_in * h->n_in; }
+
+// Polyphase prototype (Sec. 4.2 PFB weighting): symmetric Hann window times
+// a sinc with cutoff 1/M centred on the filter, evaluated in FP64.
+std::vector<float> make_filter(int M, int P) {
+    const int L = M * P;
+    std::vector<float> h(L);
+    const double pi = 3.14159265358979323846;
+    for (int n = 0; n < L; ++n) {
+        const double w = (L > 1) ? 0.5 - 0.5 * std::cos(2.0 * pi * n / (double)(L - 1)) : 1.0;
+        const double x = (n - 0.5 * (L - 1)) / (double)M;
+        const double sn = (x == 0.0) ? 1.0 : std::sin(pi * x) / (pi * x);
+        h[n] = (float)(w * sn);
+    }
+    return h;
+}
+
+int upload_tables(corr_t h, Tables& t, const std::vector<double>& tau, const std::vector<double>& phi,
+                  cudaStream_t st) {
+    const double pi = 3.14159265358979323846;
+    std::vector<float2> ph((size_t)h->n_in_pad * h->n_chan, make_float2(0.f, 0.f));
+    std::vector<int> co(h->n_in_pad, 0);
+    int dmax = -(1 << 30);
+    for (int a = 0; a < h->n_in; ++a) {
+        const double d = std::floor(tau[a] + 0.5);
+        const double r = tau[a] - d;
+        co[a] = (int)d;
+        if (co[a] > dmax) dmax = co[a];
+        // Pair packing: even inputs carry 1/2, odd inputs 1/(2j) = -j/2.
+        const bool odd = (a & 1) != 0;
+        for (int k = 0; k < h->n_chan; ++k) {
+            const double ang = 2.0 * pi * k * r / (double)h->M - phi[a];
+            double re = 0.5 * std::cos(ang), im = 0.5 * std::sin(ang);
+            if (odd) {
+                const double t2 = re;
+                re = im;
+                im = -t2;
+            }
+            ph[(size_t)a * h->n_chan + k] = make_float2((float)re, (float)im);
+        }
+    }
+    t.d_max = dmax;
+    CK(cudaMemcpyAsync(t.phasor, ph.data(), ph.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(t.coarse, co.data(), co.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    return CORR_OK;
+}
+
+int alloc_tables(corr_t h, Tables& t) {
+    CK(cudaMalloc(&t.phasor, sizeof(float2) * (size_t)h->n_in_pad * h->n_chan));
+    CK(cudaMalloc(&t.coarse, sizeof(int) * (size_t)h->n_in_pad));
+    return CORR_OK;
+}
+
+int choose_spt(long long n_spec, int n_pairs) {
+    const long long target = 152LL * 4;
+    long long spt = (n_spec * n_pairs) / target;
+    if (spt < 1) spt = 1;
+    if (spt > 8) spt = 8;
+    return (int)spt;
+}
+
+int alloc_pipe(corr_t h, Pipe& p) {
+    if (p.V) return CORR_OK;
+    const size_t per_spec = (size_t)h->n_chan * h->n_in_pad * sizeof(float2);
+    long long cap = (long long)((32ull << 20) / per_spec);
+    if (cap > 4096) cap = 4096;
+    if (cap < h->G) cap = h->G;
+    cap = (cap / h->G) * h->G;
+    p.v_cap = (int)cap;
+    CK(cudaMalloc(&p.V, per_spec * (size_t)p.v_cap));
+    CK(cudaMalloc(&p.part, sizeof(float) * (size_t)h->gpi * h->nt * 32 * h->n_chan));
+    return CORR_OK;
+}
+
+int launch_f(corr_t h, const StreamView& sv, const Tables& t, Pipe& p, long long s_begin, long long s_end,
+             cudaStream_t st) {
+    FArgs a{};
+    a.src = sv;
+    a.h = h->d_h;
+    a.tw = h->d_tw;
+    a.phasor = t.phasor;
+    a.coarse = t.coarse;
+    a.V = p.V;
+    a.s_begin = s_begin;
+    a.s_end = s_end;
+    a.v_origin = 0;
+    a.v_cap = p.v_cap;
+    a.n_in = h->n_in;
+    a.n_in_pad = h->n_in_pad;
+    a.M = h->M;
+    a.taps = h->taps;
+    a.spt = choose_spt(s_end - s_begin, h->n_in_pad / 2);
+    launch_fengine(a, st);
+    ++h->launches;
+    CK(cudaGetLastError());
+    return CORR_OK;
+}
+
+long long ready_spectra(corr_t h, bool final) {
+    if (final) return h->n_pushed / h->M;
+    const long long r = h->n_pushed - h->tab_stream.d_max;
+    if (r < h->M) return 0;
+    return r / h->M;
+}
+
+using Sink = int (*)(corr_t, void*, long long /*integration*/, int /*count*/, int /*slots*/, cudaStream_t);
+
+// Drive F -> X -> finalise over every spectrum below ready_end.  When
+// `final` is set, the stream has ended: a last partial group / integration
+// is closed at ready_end.
+int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_end, bool final, bool is_stream,
+          Sink sink, void* ctx, cudaStream_t st) {
+    const long long n_int = h->n_int;
+    for (;;) {
+        const long long i = p.s_next / n_int;
+        const long long istart = i * n_int, iend = istart + n_int;
+        if (is_stream && h->pending && p.s_next == istart && p.s_xdone == istart) {
+            CKRET(upload_tables(h, t, h->tau_pend, h->phi_pend, st));
+            h->pending = false;
+            ready_end = ready_spectra(h, final);
+        }
+        bool progress = false;
+        long long s_end = ready_end;
+        if (s_end > iend) s_end = iend;
+        if (s_end > p.s_xdone + p.v_cap) s_end = p.s_xdone + p.v_cap;
+        if (s_end > p.s_next) {
+            CKRET(launch_f(h, sv, t, p, p.s_next, s_end, st));
+            p.s_next = s_end;
+            progress = true;
+        }
+        // Partial slots: group j covers [istart + jG, min(istart + (j+1)G, iend)).
+        const bool closing = final && p.s_next == ready_end && p.s_next < iend;
+        const long long s_limit = closing ? p.s_next : iend;
+        const int j_begin = (int)((p.s_xdone - istart) / h->G);
+        int j_end;
+        if (p.s_next >= iend) j_end = h->gpi;
+        else if (closing) j_end = (int)((p.s_next - istart + h->G - 1) / h->G);
+        else j_end = (int)((p.s_next - istart) / h->G);
+        if (j_end > j_begin) {
+            XArgs x{};
+            x.V = p.V;
+            x.v_origin = 0;
+            x.v_cap = p.v_cap;
+            x.n_chan = h->n_chan;
+            x.n_in_pad = h->n_in_pad;
+            x.nt = h->nt;
+            x.int_start = istart;
+            x.int_end = iend;
+            x.s_limit = s_limit;
+            x.G = h->G;
+            x.j0 = j_begin;
+            x.n_groups = j_end - j_begin;
+            x.part = p.part;
+            launch_xengine(x, st);
+            ++h->launches;
+            CK(cudaGetLastError());
+            long long nx = istart + (long long)j_end * h->G;
+            if (nx > s_limit) nx = s_limit;
+            p.s_xdone = nx;
+            progress = true;
+        }
+        if (p.s_next == iend && p.s_xdone == iend) {
+            CKRET(sink(h, ctx, i, (int)n_int, h->gpi, st));
+            progress = true;
+            continue;
+        }
+        if (closing && p.s_xdone == p.s_next && p.s_next > istart) {
+            CKRET(sink(h, ctx, i, (int)(p.s_next - istart), j_end, st));
+            // The partial integration is closed; nothing further can follow.
+            p.s_xdone = p.s_next = iend;
+            return CORR_OK;
+        }
+        if (!progress) return CORR_OK;
+    }
+}
+
+int finalize_into(corr_t h, const Pipe& p, float2* R, uint8_t* F, int count, int slots, cudaStream_t st) {
+    FinArgs f{};
+    f.part = p.part;
+    f.n_slots = slots;
+    f.nt = h->nt;
+    f.n_chan = h->n_chan;
+    f.n_in = h->n_in;
+    f.scale = 1.0f / (float)count;
+    f.R = R;
+    launch_finalize(f, st);
+    ++h->launches;
+    CK(cudaGetLastError());
+    if (F) {
+        const int w = h->flag_window < h->n_chan ? h->flag_window : h->n_chan;
+        launch_mad_flags(R, F, 1, h->n_chan, h->n_in, w, (float)h->flag_sigma, st);
+        ++h->launches;
+        CK(cudaGetLastError());
+    }
+    return CORR_OK;
+}
+
+int add_slot(corr_t h) {
+    Slot s;
+    const size_t ne = vis_elems(h);
+    CK(cudaMalloc(&s.d_R, ne * sizeof(float2)));
+    CK(cudaMalloc(&s.d_F, ne));
+    CK(cudaHostAlloc(&s.h_R, ne * sizeof(float2), cudaHostAllocDefault));
+    CK(cudaHostAlloc(&s.h_F, ne, cudaHostAllocDefault));
+    CK(cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
+    h->slots.push_back(s);
+    return CORR_OK;
+}
+
+int new_slot(corr_t h, int* idx) {
+    for (size_t i = 0; i < h->slots.size(); ++i) {
+        if (!h->slots[i].in_vis && !h->slots[i].in_flag) {
+            *idx = (int)i;
+            return CORR_OK;
+        }
+    }
+    CKRET(add_slot(h));
+    *idx = (int)h->slots.size() - 1;
+    return CORR_OK;
+}
+
+int sink_stream(corr_t h, void*, long long, int count, int slots, cudaStream_t st) {
+    int idx;
+    CKRET(new_slot(h, &idx));
+    Slot& s = h->slots[idx];
+    CKRET(finalize_into(h, h->ps, s.d_R, s.d_F, count, slots, st));
+    const size_t ne = vis_elems(h);
+    CK(cudaMemcpyAsync(s.h_R, s.d_R, ne * sizeof(float2), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(s.h_F, s.d_F, ne, cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(s.ev, st));
+    s.in_vis = s.in_flag = true;
+    h->q_vis.push_back(idx);
+    h->q_flag.push_back(idx);
+    return CORR_OK;
+}
+
+struct DirectCtx {
+    float2* vis;
+    uint8_t* flags;
+    int max_int;
+    int n_out;
+};
+
+int sink_direct(corr_t h, void* vctx, long long i, int count, int slots, cudaStream_t st) {
+    DirectCtx* c = static_cast<DirectCtx*>(vctx);
+    if (i >= c->max_int) return fail(h, CORR_EINVAL, "max_int too small for the stream");
+    const size_t ne = vis_elems(h);
+    CKRET(finalize_into(h, h->pd, c->vis + (size_t)i * ne, c->flags ? c->flags + (size_t)i * ne : nullptr,
+                        count, slots, st));
+    c->n_out = (int)i + 1;
+    return CORR_OK;
+}
+
+int ensure_stream_alloc(corr_t h) {
+    if (h->stream_alloc) return CORR_OK;
+    const long long keep = (long long)(h->taps + 1) * h->M + 2 * h->max_delay + 64;
+    h->stage_cap = ((h->chunk + keep + 15) / 16) * 16;
+    h->tmp_cap = ((keep + 15) / 16) * 16;
+    CK(cudaMalloc(&h->d_stage, (size_t)h->stage_cap * h->n_in));
+    CK(cudaMalloc(&h->d_tmp, (size_t)h->tmp_cap * h->n_in));
+    CK(cudaMemset(h->d_stage, 0, (size_t)h->stage_cap * h->n_in));
+    CKRET(alloc_pipe(h, h->ps));
+    while ((int)h->slots.size() < h->result_slots) CKRET(add_slot(h));
+    h->stream_alloc = true;
+    return CORR_OK;
+}
+
+// Keep the samples still needed by unprocessed spectra at the front of the
+// staging buffer so that `need` more samples fit behind them.
+int make_room(corr_t h, long long need) {
+    if (h->stage_len + need <= h->stage_cap) return CORR_OK;
+    long long keep_lo = (h->ps.s_next - h->taps + 1) * (long long)h->M - h->max_delay;
+    if (keep_lo < h->stage_base) keep_lo = h->stage_base;
+    const long long off = keep_lo - h->stage_base;
+    const long long keep = h->stage_len - off;
+    if (keep + need > h->stage_cap || keep > h->tmp_cap)
+        return fail(h, CORR_EINVAL, "internal: staging buffer too small");
+    if (keep > 0 && off > 0) {
+        if (off >= keep) {
+            CK(cudaMemcpy2DAsync(h->d_stage, h->stage_cap, h->d_stage + off, h->stage_cap, keep, h->n_in,
+                                 cudaMemcpyDeviceToDevice, h->s_comp));
+        } else {
+            CK(cudaMemcpy2DAsync(h->d_tmp, h->tmp_cap, h->d_stage + off, h->stage_cap, keep, h->n_in,
+                                 cudaMemcpyDeviceToDevice, h->s_comp));
+            CK(cudaMemcpy2DAsync(h->d_stage, h->stage_cap, h->d_tmp, h->tmp_cap, keep, h->n_in,
+                                 cudaMemcpyDeviceToDevice, h->s_comp));
+        }
+    }
+    h->stage_base = keep_lo;
+    h->stage_len = keep;
+    // Later host->device copies overwrite regions the queued kernels read.
+    CK(cudaEventRecord(h->ev_comp, h->s_comp));
+    CK(cudaStreamWaitEvent(h->s_copy, h->ev_comp, 0));
+    return CORR_OK;
+}
+
+int process_stream(corr_t h, bool final) {
+    StreamView sv;
+    sv.x = h->d_stage;
+    sv.stride = h->stage_cap;
+    sv.base = h->stage_base;
+    sv.vhi = h->n_pushed;
+    return drive(h, h->ps, sv, h->tab_stream, ready_spectra(h, final), final, true, sink_stream, nullptr,
+                 h->s_comp);
+}
+
+int push_common(corr_t h, const int8_t* src, size_t n, size_t stride, bool on_device, cudaStream_t ust) {
+    if (h->flushed) return fail(h, CORR_ESTATE, "stream already flushed; call corr_reset");
+    if (n == 0) return CORR_OK;
+    if (!src) return fail(h, CORR_EINVAL, "samples is NULL");
+    if (stride < n) return fail(h, CORR_EINVAL, "input_stride < n_per_input");
+    CKRET(ensure_stream_alloc(h));
+    bool pinned = false;
+    if (!on_device) {
+        cudaPointerAttributes attr;
+        if (cudaPointerGetAttributes(&attr, src) == cudaSuccess && attr.type == cudaMemoryTypeHost)
+            pinned = true;
+        cudaGetLastError();
+    } else {
+        CK(cudaEventRecord(h->ev_comp, ust));
+        CK(cudaStreamWaitEvent(h->s_copy, h->ev_comp, 0));
+    }
+    h->started = true;
+    size_t done = 0;
+    while (done < n) {
+        const long long piece = (long long)std::min<size_t>(n - done, (size_t)h->chunk);
+        CKRET(make_room(h, piece));
+        const int8_t* s = src + done;
+        size_t spitch = stride;
+        cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        if (!on_device && !pinned) {
+            if (h->pin_cap < piece * h->n_in) {
+                if (h->h_pin) cudaFreeHost(h->h_pin);
+                h->h_pin = nullptr;
+                CK(cudaHostAlloc(&h->h_pin, (size_t)piece * h->n_in, cudaHostAllocDefault));
+                h->pin_cap = piece * h->n_in;
+            }
+            for (int a = 0; a < h->n_in; ++a)
+                std::memcpy(h->h_pin + (size_t)a * piece, src + (size_t)a * stride + done, (size_t)piece);
+            s = h->h_pin;
+            spitch = (size_t)piece;
+        }
+        CK(cudaMemcpy2DAsync(h->d_stage + h->stage_len, h->stage_cap, s, spitch, (size_t)piece, h->n_in, kind,
+                             h->s_copy));
+        CK(cudaEventRecord(h->ev_h2d, h->s_copy));
+        CK(cudaStreamWaitEvent(h->s_comp, h->ev_h2d, 0));
+        h->stage_len += piece;
+        h->n_pushed += piece;
+        CKRET(process_stream(h, false));
+        if (!on_device) CK(cudaEventSynchronize(h->ev_h2d));
+        done += (size_t)piece;
+    }
+    if (on_device) {
+        // The caller's buffer may be reused once its stream passes this point.
+        CK(cudaEventRecord(h->ev_h2d, h->s_copy));
+        CK(cudaStreamWaitEvent(ust, h->ev_h2d, 0));
+    }
+    return CORR_OK;
+}
+
+int pop_results(corr_t h, std::deque<int>& q, bool vis, void* out, int max_int, int* n_got) {
+    if (n_got) *n_got = 0;
+    if (max_int < 0) return fail(h, CORR_EINVAL, "max_int < 0");
+    if (max_int > 0 && !out) return fail(h, CORR_EINVAL, "out is NULL");
+    int got = 0;
+    const size_t ne = vis_elems(h);
+    while (got < max_int && !q.empty()) {
+        const int idx = q.front();
+        Slot& s = h->slots[idx];
+        CK(cudaEventSynchronize(s.ev));
+        if (vis) {
+            std::memcpy(static_cast<float2*>(out) + (size_t)got * ne, s.h_R, ne * sizeof(float2));
+            s.in_vis = false;
+        } else {
+            std::memcpy(static_cast<uint8_t*>(out) + (size_t)got * ne, s.h_F, ne);
+            s.in_flag = false;
+        }
+        q.pop_front();
+        ++got;
+    }
+    if (n_got) *n_got = got;
+    return got == 0 && max_int > 0 ? CORR_EAGAIN : CORR_OK;
+}
+
+void free_pipe(Pipe& p) {
+    if (p.V) cudaFree(p.V);
+    if (p.part) cudaFree(p.part);
+    p = Pipe{};
+}
+
+}  // namespace
+
+extern "C" {
+
+int corr_create(corr_t* out, int n_ant, int n_pol, int n_chan, int taps, int n_int) {
+    if (!out) return fail(nullptr, CORR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_ant < 1 || n_pol < 1 || n_ant * n_pol > 256)
+        return fail(nullptr, CORR_EINVAL, "need n_ant, n_pol >= 1 and n_ant*n_pol <= 256");
+    if (!is_pow2(n_chan) || n_chan < 8 || n_chan > 8192)
+        return fail(nullptr, CORR_EINVAL, "n_chan must be a power of two in [8, 8192]");
+    if (taps < 1 || taps > 16) return fail(nullptr, CORR_EINVAL, "taps must be in [1, 16]");
+    if (n_int < 1) return fail(nullptr, CORR_EINVAL, "n_int must be >= 1");
+    corr_t h = new corr_s();
+    h->n_ant = n_ant;
+    h->n_pol = n_pol;
+    h->n_in = n_ant * n_pol;
+    h->n_in_pad = (h->n_in + 3) & ~3;
+    h->n_chan = n_chan;
+    h->M = 2 * n_chan;
+    h->taps = taps;
+    h->n_int = n_int;
+    const int nb = h->n_in_pad / 4;
+    h->nt = nb * (nb + 1) / 2;
+    int G = n_int < 64 ? n_int : 64;
+    if (n_int / G > 16) G = (int)(((n_int + 15) / 16 + 63) / 64 * 64);
+    h->G = G;
+    h->gpi = (n_int + G - 1) / G;
+    h->tau.assign(h->n_in, 0.0);
+    h->phi.assign(h->n_in, 0.0);
+    cudaError_t e = cudaGetDevice(&h->dev);
+    auto bail = [&](int code, const std::string& m) {
+        corr_destroy(h);
+        return fail(nullptr, code, m);
+    };
+    if (e != cudaSuccess) return bail(CORR_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    const std::vector<float> hf = make_filter(h->M, taps);
+    std::vector<float2> tw(h->M);
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k < h->M; ++k)
+        tw[k] = make_float2((float)std::cos(-2.0 * pi * k / h->M), (float)std::sin(-2.0 * pi * k / h->M));
+    if (cudaStreamCreateWithFlags(&h->s_comp, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->s_copy, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_h2d, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_comp, cudaEventDisableTiming) != cudaSuccess)
+        return bail(CORR_ECUDA, "stream/event creation failed");
+    if (cudaMalloc(&h->d_h, hf.size() * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&h->d_tw, tw.size() * sizeof(float2)) != cudaSuccess)
+        return bail(CORR_ENOMEM, "cudaMalloc of filter tables failed");
+    if (cudaMemcpy(h->d_h, hf.data(), hf.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(CORR_ECUDA, "upload of filter tables failed");
+    if (alloc_tables(h, h->tab_stream) != CORR_OK || alloc_tables(h, h->tab_direct) != CORR_OK)
+        return bail(CORR_ENOMEM, "cudaMalloc of delay tables failed");
+    if (upload_tables(h, h->tab_stream, h->tau, h->phi, h->s_comp) != CORR_OK ||
+        upload_tables(h, h->tab_direct, h->tau, h->phi, h->s_comp) != CORR_OK)
+        return bail(CORR_ECUDA, "upload of delay tables failed");
+    *out = h;
+    return CORR_OK;
+}
+
+int corr_destroy(corr_t h) {
+    if (!h) return CORR_OK;
+    DeviceGuard g(h->dev);
+    if (h->s_comp) cudaStreamSynchronize(h->s_comp);
+    if (h->s_copy) cudaStreamSynchronize(h->s_copy);
+    for (Slot& s : h->slots) {
+        cudaFree(s.d_R);
+        cudaFree(s.d_F);
+        cudaFreeHost(s.h_R);
+        cudaFreeHost(s.h_F);
+        if (s.ev) cudaEventDestroy(s.ev);
+    }
+    free_pipe(h->ps);
+    free_pipe(h->pd);
+    cudaFree(h->d_part_x);
+    cudaFree(h->d_h);
+    cudaFree(h->d_tw);
+    cudaFree(h->tab_stream.phasor);
+    cudaFree(h->tab_stream.coarse);
+    cudaFree(h->tab_direct.phasor);
+    cudaFree(h->tab_direct.coarse);
+    cudaFree(h->d_stage);
+    cudaFree(h->d_tmp);
+    if (h->h_pin) cudaFreeHost(h->h_pin);
+    if (h->ev_h2d) cudaEventDestroy(h->ev_h2d);
+    if (h->ev_comp) cudaEventDestroy(h->ev_comp);
+    if (h->s_comp) cudaStreamDestroy(h->s_comp);
+    if (h->s_copy) cudaStreamDestroy(h->s_copy);
+    cudaGetLastError();
+    delete h;
+    return CORR_OK;
+}
+
+const char* corr_last_error(corr_t h) {
+    if (!h) return g_create_error.c_str();
+    return h->err.c_str();
+}
+
+int corr_set_option(corr_t h, const char* key, double v) {
+    if (!h || !key) return fail(h, CORR_EINVAL, "NULL argument");
+    if (h->started) return fail(h, CORR_ESTATE, "options must be set before the first push");
+    const std::string k(key);
+    if (k == "flag_sigma") {
+        if (!(v > 0)) return fail(h, CORR_EINVAL, "flag_sigma must be > 0");
+        h->flag_sigma = v;
+    } else if (k == "flag_window") {
+        if (!is_pow2((long long)v) || v > 256 || v < 2) return fail(h, CORR_EINVAL, "flag_window: power of two in [2, 256]");
+        h->flag_window = (int)v;
+    } else if (k == "max_delay") {
+        if (v < 0 || v > (1 << 24)) return fail(h, CORR_EINVAL, "max_delay out of range");
+        if (h->stream_alloc) return fail(h, CORR_ESTATE, "max_delay must be set before buffers exist");
+        h->max_delay = (long long)v;
+    } else if (k == "chunk") {
+        if (v < 1 || v > (double)(1LL << 32)) return fail(h, CORR_EINVAL, "chunk out of range");
+        if (h->stream_alloc) return fail(h, CORR_ESTATE, "chunk must be set before buffers exist");
+        h->chunk = (long long)v;
+    } else if (k == "precision") {
+        if (v != CORR_FP32) return fail(h, CORR_EINVAL, "precision: only CORR_FP32 in this build");
+        h->precision = (int)v;
+    } else if (k == "result_slots") {
+        if (v < 1 || v > 4096) return fail(h, CORR_EINVAL, "result_slots out of range");
+        h->result_slots = (int)v;
+    } else {
+        return fail(h, CORR_EINVAL, "unknown option " + k);
+    }
+    return CORR_OK;
+}
+
+int corr_set_delays(corr_t h, const double* tau, const double* phi) {
+    if (!h || !tau) return fail(h, CORR_EINVAL, "NULL argument");
+    DeviceGuard g(h->dev);
+    std::vector<double> t(tau, tau + h->n_in), p(h->n_in, 0.0);
+    if (phi) p.assign(phi, phi + h->n_in);
+    for (int a = 0; a < h->n_in; ++a) {
+        if (!std::isfinite(t[a]) || !std::isfinite(p[a])) return fail(h, CORR_EINVAL, "non-finite delay/phase");
+        if (std::fabs(std::floor(t[a] + 0.5)) > (double)h->max_delay)
+            return fail(h, CORR_EINVAL, "coarse delay exceeds max_delay");
+    }
+    h->tau = t;
+    h->phi = p;
+    CKRET(upload_tables(h, h->tab_direct, t, p, h->s_comp));
+    if (!h->started) {
+        CKRET(upload_tables(h, h->tab_stream, t, p, h->s_comp));
+        h->pending = false;
+    } else {
+        h->tau_pend = t;
+        h->phi_pend = p;
+        h->pending = true;
+    }
+    return CORR_OK;
+}
+
+int corr_push(corr_t h, const int8_t* samples, size_t n, size_t stride) {
+    if (!h) return fail(h, CORR_EINVAL, "NULL handle");
+    DeviceGuard g(h->dev);
+    return push_common(h, samples, n, stride, false, nullptr);
+}
+
+int corr_push_dev(corr_t h, const int8_t* d_samples, size_t n, size_t stride, void* stream) {
+    if (!h) return fail(h, CORR_EINVAL, "NULL handle");
+    DeviceGuard g(h->dev);
+    return push_common(h, d_samples, n, stride, true, static_cast<cudaStream_t>(stream));
+}
+
+int corr_flush(corr_t h) {
+    if (!h) return fail(h, CORR_EINVAL, "NULL handle");
+    DeviceGuard g(h->dev);
+    if (h->flushed) return fail(h, CORR_ESTATE, "already flushed");
+    if (!h->started) {
+        h->flushed = true;
+        return CORR_OK;
+    }
+    CKRET(process_stream(h, true));
+    h->flushed = true;
+    return CORR_OK;
+}
+
+int corr_reset(corr_t h) {
+    if (!h) return fail(h, CORR_EINVAL, "NULL handle");
+    DeviceGuard g(h->dev);
+    if (h->s_comp) CK(cudaStreamSynchronize(h->s_comp));
+    if (h->s_copy) CK(cudaStreamSynchronize(h->s_copy));
+    h->started = h->flushed = false;
+    h->stage_base = h->stage_len = 0;
+    h->n_pushed = 0;
+    h->ps.s_next = h->ps.s_xdone = 0;
+    h->q_vis.clear();
+    h->q_flag.clear();
+    for (Slot& s : h->slots) s.in_vis = s.in_flag = false;
+    if (h->pending) {
+        CKRET(upload_tables(h, h->tab_stream, h->tau_pend, h->phi_pend, h->s_comp));
+        h->pending = false;
+    } else {
+        CKRET(upload_tables(h, h->tab_stream, h->tau, h->phi, h->s_comp));
+    }
+    return CORR_OK;
+}
+
+int corr_get_vis(corr_t h, float* out, int max_int, int* n_got) {
+    if (!h) return fail(h, CORR_EINVAL, "NULL handle");
+    DeviceGuard g(h->dev);
+    return pop_results(h, h->q_vis, true, out, max_int, n_got);
+}
+
+int corr_get_flags(corr_t h, uint8_t* out, int max_int, int* n_got) {
+    if (!h) return fail(h, CORR_EINVAL, "NULL handle");
+    DeviceGuard g(h->dev);
+    return pop_results(h, h->q_flag, false, out, max_int, n_got);
+}
+
+int corr_pending(corr_t h, int* n) {
+    if (!h || !n) return fail(h, CORR_EINVAL, "NULL argument");
+    *n = (int)h->q_vis.size();
+    return CORR_OK;
+}
+
+int corr_run_dev(corr_t h, const int8_t* d_samples, size_t n_samples, size_t stride, float* d_vis,
+                 uint8_t* d_flags, int max_int, int include_partial, int* n_out, void* stream) {
+    if (!h) return fail(h, CORR_EINVAL, "NULL handle");
+    DeviceGuard g(h->dev);
+    if (n_out) *n_out = 0;
+    if (!d_samples || !d_vis) return fail(h, CORR_EINVAL, "NULL buffer");
+    if (stride < n_samples) return fail(h, CORR_EINVAL, "input_stride < n_samples");
+    const long long n_spec = (long long)(n_samples / (size_t)h->M);
+    long long need = n_spec / h->n_int + ((include_partial && n_spec % h->n_int) ? 1 : 0);
+    if (need > max_int) return fail(h, CORR_EINVAL, "max_int too small for the stream");
+    CKRET(alloc_pipe(h, h->pd));
+    h->pd.s_next = h->pd.s_xdone = 0;
+    StreamView sv;
+    sv.x = d_samples;
+    sv.stride = (long long)stride;
+    sv.base = 0;
+    sv.vhi = (long long)n_samples;
+    DirectCtx c{reinterpret_cast<float2*>(d_vis), d_flags, max_int, 0};
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CKRET(drive(h, h->pd, sv, h->tab_direct, n_spec, include_partial != 0, false, sink_direct, &c, st));
+    if (n_out) *n_out = c.n_out;
+    return CORR_OK;
+}
+
+int corr_fengine_dev(corr_t h, const int8_t* d_samples, size_t n_samples, size_t stride, long long s0,
+                     int n_spec, float* d_V, void* stream) {
+    if (!h) return fail(h, CORR_EINVAL, "NULL handle");
+    DeviceGuard g(h->dev);
+    if (!d_samples || !d_V || n_spec < 0 || s0 < 0) return fail(h, CORR_EINVAL, "bad argument");
+    if (stride < n_samples) return fail(h, CORR_EINVAL, "input_stride < n_samples");
+    if (n_spec == 0) return CORR_OK;
+    Pipe p;
+    p.V = reinterpret_cast<float2*>(d_V);
+    p.v_cap = n_spec;
+    StreamView sv{d_samples, (long long)stride, 0, (long long)n_samples};
+    FArgs a{};
+    a.src = sv;
+    a.h = h->d_h;
+    a.tw = h->d_tw;
+    a.phasor = h->tab_direct.phasor;
+    a.coarse = h->tab_direct.coarse;
+    a.V = p.V;
+    a.s_begin = s0;
+    a.s_end = s0 + n_spec;
+    a.v_origin = s0;
+    a.v_cap = n_spec;
+    a.n_in = h->n_in;
+    a.n_in_pad = h->n_in_pad;
+    a.M = h->M;
+    a.taps = h->taps;
+    a.spt = choose_spt(n_spec, h->n_in_pad / 2);
+    launch_fengine(a, static_cast<cudaStream_t>(stream));
+    ++h->launches;
+    CK(cudaGetLastError());
+    return CORR_OK;
+}
+
+int corr_xengine_dev(corr_t h, const float* d_V, int n_spec, float* d_vis, void* stream) {
+    if (!h) return fail(h, CORR_EINVAL, "NULL handle");
+    DeviceGuard g(h->dev);
+    if (!d_V || !d_vis || n_spec < 1) return fail(h, CORR_EINVAL, "bad argument");
+    const int G = 64;
+    const long long slots = (n_spec + G - 1) / G;
+    if (slots > h->part_x_slots) {
+        cudaFree(h->d_part_x);
+        h->d_part_x = nullptr;
+        CK(cudaMalloc(&h->d_part_x, sizeof(float) * (size_t)slots * h->nt * 32 * h->n_chan));
+        h->part_x_slots = slots;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    XArgs x{};
+    x.V = reinterpret_cast<const float2*>(d_V);
+    x.v_origin = 0;
+    x.v_cap = n_spec;
+    x.n_chan = h->n_chan;
+    x.n_in_pad = h->n_in_pad;
+    x.nt = h->nt;
+    x.int_start = 0;
+    x.int_end = n_spec;
+    x.s_limit = n_spec;
+    x.G = G;
+    x.j0 = 0;
+    x.n_groups = (int)slots;
+    x.part = h->d_part_x;
+    launch_xengine(x, st);
+    ++h->launches;
+    CK(cudaGetLastError());
+    FinArgs f{};
+    f.part = h->d_part_x;
+    f.n_slots = (int)slots;
+    f.nt = h->nt;
+    f.n_chan = h->n_chan;
+    f.n_in = h->n_in;
+    f.scale = 1.0f / (float)n_spec;
+    f.R = reinterpret_cast<float2*>(d_vis);
+    launch_finalize(f, st);
+    ++h->launches;
+    CK(cudaGetLastError());
+    return CORR_OK;
+}
+
+int corr_flag_dev(corr_t h, const float* d_vis, int n_vis, uint8_t* d_flags, void* stream) {
+    if (!h) return fail(h, CORR_EINVAL, "NULL handle");
+    DeviceGuard g(h->dev);
+    if (!d_vis || !d_flags || n_vis < 0) return fail(h, CORR_EINVAL, "bad argument");
+    const int w = h->flag_window < h->n_chan ? h->flag_window : h->n_chan;
+    launch_mad_flags(reinterpret_cast<const float2*>(d_vis), d_flags, n_vis, h->n_chan, h->n_in, w,
+                     (float)h->flag_sigma, static_cast<cudaStream_t>(stream));
+    ++h->launches;
+    CK(cudaGetLastError());
+    return CORR_OK;
+}
+
+int corr_shape(corr_t h, int* n_in, int* n_chan, int* taps, int* n_int, int* n_in_pad) {
+    if (!h) return fail(h, CORR_EINVAL, "NULL handle");
+    if (n_in) *n_in = h->n_in;
+    if (n_chan) *n_chan = h->n_chan;
+    if (taps) *taps = h->taps;
+    if (n_int) *n_int = h->n_int;
+    if (n_in_pad) *n_in_pad = h->n_in_pad;
+    return CORR_OK;
+}
+
+long long corr_kernel_launches(corr_t h) { return h ? h->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,184 @@
+// X-engine and integration (Sec. 4.2 "X-engine and integration",
+// Algorithm 1): R[k][a][b] = (1/count) sum_s V_a,s[k] conj(V_b,s[k]).
+//
+// CUDA-core form.  Inputs are taken in blocks of four; one thread owns one
+// channel and one 4x4 block-pair (A <= B) of the Hermitian matrix and keeps
+// its 16 complex sums in registers over a group of spectra.  Each group's
+// sums go to their own partial slot; the finaliser adds the slots of an
+// integration in a fixed order, so the result does not depend on how a
+// stream was split into pushes (no atomics anywhere).
+#include "corr_internal.h"
+
+namespace corr {
+
+namespace {
+
+__device__ __forceinline__ void tile_decode(int t, int nb, int& A, int& B) {
+    // t enumerates (A, B), A <= B < nb, row by row.
+    int r = 0, rem = t;
+    while (rem >= nb - r) { rem -= nb - r; ++r; }
+    A = r;
+    B = r + rem;
+}
+
+__global__ void __launch_bounds__(128) xengine_kernel(const XArgs X) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.y;
+    const int g = blockIdx.z;
+    if (k >= X.n_chan) return;
+    int A, B;
+    tile_decode(t, X.n_in_pad >> 2, A, B);
+    long long s0 = X.int_start + (long long)(X.j0 + g) * X.G;
+    long long s1 = s0 + X.G;
+    if (s1 > X.int_end) s1 = X.int_end;
+    if (s1 > X.s_limit) s1 = X.s_limit;
+
+    float acc[32];
+#pragma unroll
+    for (int e = 0; e < 32; ++e) acc[e] = 0.f;
+    const int q4 = X.n_in_pad >> 1;   // float4 per (slot, channel)
+    for (long long s = s0; s < s1; ++s) {
+        long long slot = (s - X.v_origin) % X.v_cap;
+        if (slot < 0) slot += X.v_cap;
+        const float4* vp = reinterpret_cast<const float4*>(X.V) + ((size_t)slot * X.n_chan + k) * q4;
+        const float4 a01 = __ldg(vp + 2 * A), a23 = __ldg(vp + 2 * A + 1);
+        const float4 b01 = __ldg(vp + 2 * B), b23 = __ldg(vp + 2 * B + 1);
+        const float ar[4] = {a01.x, a01.z, a23.x, a23.z}, ai[4] = {a01.y, a01.w, a23.y, a23.w};
+        const float br[4] = {b01.x, b01.z, b23.x, b23.z}, bi[4] = {b01.y, b01.w, b23.y, b23.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float& re = acc[(i * 4 + j) * 2];
+                float& im = acc[(i * 4 + j) * 2 + 1];
+                re = fmaf(ar[i], br[j], re);
+                re = fmaf(ai[i], bi[j], re);
+                im = fmaf(ai[i], br[j], im);
+                im = fmaf(-ar[i], bi[j], im);
+            }
+        }
+    }
+    float* out = X.part + (((size_t)(X.j0 + g) * X.nt + t) * 32) * X.n_chan + k;
+#pragma unroll
+    for (int e = 0; e < 32; ++e) out[(size_t)e * X.n_chan] = acc[e];
+}
+
+__global__ void __launch_bounds__(128) finalize_kernel(const FinArgs F) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.y;
+    if (k >= F.n_chan) return;
+    const int n_in_pad = (F.n_in + 3) & ~3;
+    int A, B;
+    tile_decode(t, n_in_pad >> 2, A, B);
+    float acc[32];
+#pragma unroll
+    for (int e = 0; e < 32; ++e) acc[e] = 0.f;
+    for (int j = 0; j < F.n_slots; ++j) {
+        const float* p = F.part + (((size_t)j * F.nt + t) * 32) * F.n_chan + k;
+#pragma unroll
+        for (int e = 0; e < 32; ++e) acc[e] += p[(size_t)e * F.n_chan];
+    }
+    float2* R = F.R + (size_t)k * F.n_in * F.n_in;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int a = 4 * A + i, b = 4 * B + j;
+            if (a >= F.n_in || b >= F.n_in) continue;
+            if (A == B && i > j) continue;
+            const float re = acc[(i * 4 + j) * 2] * F.scale;
+            const float im = acc[(i * 4 + j) * 2 + 1] * F.scale;
+            if (a == b) {
+                R[a * F.n_in + a] = make_float2(re, 0.f);
+            } else {
+                R[a * F.n_in + b] = make_float2(re, im);
+                R[b * F.n_in + a] = make_float2(re, -im);
+            }
+        }
+    }
+}
+
+// ---- MAD flagging, Eq. 2 ------------------------------------------------
+// One warp per (integration, window, baseline a <= b).  Order statistics are
+// exact: every value's rank (ties broken by position) is counted against the
+// whole window, the value is stored at its rank, and the median is read from
+// the sorted array (even count: mean of the two middle values).
+constexpr int kMaxWindow = 256;
+constexpr int kFlagWarps = 4;
+
+__device__ float warp_median(const float* v, float* sorted, int W, int lane) {
+    for (int c = lane; c < W; c += 32) {
+        const float x = v[c];
+        int rank = 0;
+        for (int d = 0; d < W; ++d) {
+            const float y = v[d];
+            rank += (y < x) || (y == x && d < c);
+        }
+        sorted[rank] = x;
+    }
+    __syncwarp();
+    const float med = (W & 1) ? sorted[W >> 1] : 0.5f * (sorted[(W >> 1) - 1] + sorted[W >> 1]);
+    __syncwarp();
+    return med;
+}
+
+__global__ void __launch_bounds__(32 * kFlagWarps) mad_flag_kernel(const float2* R, uint8_t* F, int n_vis,
+                                                                   int n_chan, int n_in, int W,
+                                                                   float sigma) {
+    __shared__ float sm[kFlagWarps][3][kMaxWindow];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_bl = n_in * (n_in + 1) / 2;
+    const int n_win = n_chan / W;
+    const long long item = (long long)blockIdx.x * kFlagWarps + warp;
+    if (item >= (long long)n_vis * n_win * n_bl) return;
+    const int bl = (int)(item % n_bl);
+    const int w = (int)((item / n_bl) % n_win);
+    const int i = (int)(item / ((long long)n_bl * n_win));
+    int a = 0, rem = bl;
+    while (rem >= n_in - a) { rem -= n_in - a; ++a; }
+    const int b = a + rem;
+    float* vA = sm[warp][0];
+    float* vS = sm[warp][1];
+    float* vD = sm[warp][2];
+    const size_t base = (size_t)i * n_chan * n_in * n_in;
+    for (int c = lane; c < W; c += 32) {
+        const int k = w * W + c;
+        const float2 r = R[base + ((size_t)k * n_in + a) * n_in + b];
+        vA[c] = sqrtf(r.x * r.x + r.y * r.y);
+    }
+    __syncwarp();
+    const float med = warp_median(vA, vS, W, lane);
+    for (int c = lane; c < W; c += 32) vD[c] = fabsf(vA[c] - med);
+    __syncwarp();
+    const float mad = warp_median(vD, vS, W, lane);
+    const float T = med + sigma * mad * 1.4826f;
+    for (int c = lane; c < W; c += 32) {
+        const int k = w * W + c;
+        const uint8_t f = vA[c] > T ? 1 : 0;
+        F[base + ((size_t)k * n_in + a) * n_in + b] = f;
+        F[base + ((size_t)k * n_in + b) * n_in + a] = f;
+    }
+}
+
+}  // namespace
+
+void launch_xengine(const XArgs& a, cudaStream_t st) {
+    if (a.n_groups <= 0) return;
+    dim3 grid((a.n_chan + 127) / 128, a.nt, a.n_groups);
+    xengine_kernel<<<grid, 128, 0, st>>>(a);
+}
+
+void launch_finalize(const FinArgs& a, cudaStream_t st) {
+    dim3 grid((a.n_chan + 127) / 128, a.nt);
+    finalize_kernel<<<grid, 128, 0, st>>>(a);
+}
+
+void launch_mad_flags(const float2* R, uint8_t* F, int n_vis, int n_chan, int n_in, int window,
+                      float sigma, cudaStream_t st) {
+    const long long items = (long long)n_vis * (n_chan / window) * (n_in * (n_in + 1) / 2);
+    if (items <= 0) return;
+    const unsigned blocks = (unsigned)((items + kFlagWarps - 1) / kFlagWarps);
+    mad_flag_kernel<<<blocks, 32 * kFlagWarps, 0, st>>>(R, F, n_vis, n_chan, n_in, window, sigma);
+}
+
+}  // namespace corr

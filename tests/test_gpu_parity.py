@@ -1,0 +1,318 @@
+"""GPU parity of the CUDA hot path against the FP64 oracle (through the C ABI).
+
+Tolerances (FP32 path):
+  * channelised voltages: relative L2 error per (input, spectrum) < 1e-5;
+  * visibilities: relative Frobenius error per channel < 1e-5;
+  * flags: identical except where |A - T| < 1e-4 T (A, T in FP64);
+  * any two chunkings of one stream: bit-identical.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from fxsynth import StreamSpec, make_stream, config_c1  # noqa: E402
+from oracle import fx_oracle as fx  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_20640_gb300.build import build_library
+    build_library()
+
+
+def _corr(*a, **k):
+    from paper_2604_20640_gb300 import Correlator
+    return Correlator(*a, **k)
+
+
+def _stream(n_in, S, seed, tau=None, phi=None, **kw):
+    return make_stream(StreamSpec(n_ant=n_in, n_pol=1, n_samples=S, seed=seed, tau=tau, phi=phi, **kw))
+
+
+def _vis_err(Rg, Ro):
+    return fx.rel_frobenius_per_channel(np.asarray(Rg).astype(np.complex128), Ro)
+
+
+def _flags_ok(Fg, Ro, Fo, To):
+    A = np.abs(Ro)
+    return (Fg == Fo) | (np.abs(A - To) < 1e-4 * To)
+
+
+def _fengine(c, x, s0, n_spec):
+    xd = torch.from_numpy(x).to(DEV)
+    V = torch.full((n_spec, c.n_chan, c.n_in_pad), complex(np.nan, np.nan), dtype=torch.complex64, device=DEV)
+    c.fengine_dev(xd, s0, n_spec, V)
+    torch.cuda.synchronize()
+    return V.cpu().numpy()
+
+
+# ---------------------------------------------------------------------------
+# F-engine alone
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n_chan", [8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 8192])
+def test_fengine_matches_oracle_all_lengths(n_chan):
+    M, P, n_in = 2 * n_chan, 4, 3
+    n_spec = 11
+    S = M * n_spec + 37                    # ragged tail
+    tau = np.array([0.0, 13.4, -6.6])
+    phi = np.array([0.3, -2.0, 1.1])
+    x = _stream(n_in, S, seed=n_chan, tau=tau, phi=phi)
+    c = _corr(n_in, 1, n_chan, P, 4)
+    c.set_delays(tau, phi)
+    Vg = _fengine(c, x, 0, n_spec)
+    Vo = fx.f_engine(x, n_chan, P, tau, phi)
+    assert Vo.shape[1] == n_spec
+    for a in range(n_in):
+        num = np.linalg.norm(Vg[:, :, a] - Vo[a], axis=1)
+        den = np.linalg.norm(Vo[a], axis=1)
+        assert np.all(num <= 1e-5 * den + 1e-6), (a, (num / np.maximum(den, 1e-30)).max())
+    assert np.all(Vg[:, :, n_in:] == 0)     # padding inputs are zero
+
+
+@pytest.mark.parametrize("taps", [1, 2, 3, 8, 16])
+def test_fengine_taps_and_subrange(taps):
+    n_chan, n_in = 64, 4
+    M = 2 * n_chan
+    S = M * 40
+    tau = np.array([0.0, 3.0, 40.0, 17.5])
+    x = _stream(n_in, S, seed=taps, tau=tau)
+    c = _corr(n_in, 1, n_chan, taps, 8)
+    c.set_delays(tau)
+    Vo = fx.f_engine(x, n_chan, taps, tau)
+    for s0, n in [(0, 40), (7, 9), (39, 1)]:
+        Vg = _fengine(c, x, s0, n)
+        for a in range(n_in):
+            num = np.linalg.norm(Vg[:, :, a] - Vo[a, s0:s0 + n], axis=1)
+            den = np.linalg.norm(Vo[a, s0:s0 + n], axis=1)
+            assert np.all(num <= 1e-5 * den + 1e-6)
+
+
+def test_fengine_delays_beyond_stream_read_zero():
+    n_chan, n_in = 32, 2
+    M = 2 * n_chan
+    S = M * 6
+    x = _stream(n_in, S, seed=5)
+    tau = np.array([float(S + 10), -float(S + 10)])
+    c = _corr(n_in, 1, n_chan, 4, 2, max_delay=S + 100)
+    c.set_delays(tau)
+    Vg = _fengine(c, x, 0, 6)
+    assert np.all(Vg[:, :, :2] == 0)
+
+
+def test_fengine_tone_lands_in_its_channel():
+    n_chan, P = 512, 4
+    M = 2 * n_chan
+    k0 = 77
+    n = np.arange(M * 12)
+    x = np.clip(np.rint(60 * np.cos(2 * np.pi * k0 * n / M + 0.4)), -128, 127).astype(np.int8)[None, :]
+    x = np.repeat(x, 2, axis=0)
+    c = _corr(2, 1, n_chan, P, 4)
+    Vg = _fengine(c, x, 0, 12)
+    for s in range(P - 1, 12):
+        assert np.argmax(np.abs(Vg[s, :, 0])) == k0
+
+
+# ---------------------------------------------------------------------------
+# X-engine and flagging alone
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n_in,n_chan,n_spec", [(1, 64, 7), (2, 32, 100), (4, 256, 130), (5, 64, 64),
+                                                (8, 512, 257), (12, 64, 33), (16, 128, 65), (64, 32, 70)])
+def test_xengine_matches_oracle(n_in, n_chan, n_spec):
+    rng = np.random.default_rng(n_in * 1000 + n_chan)
+    n_pad = (n_in + 3) // 4 * 4
+    V = np.zeros((n_spec, n_chan, n_pad), dtype=np.complex64)
+    V[:, :, :n_in] = (rng.standard_normal((n_spec, n_chan, n_in)) +
+                      1j * rng.standard_normal((n_spec, n_chan, n_in))).astype(np.complex64)
+    c = _corr(n_in, 1, n_chan, 4, 16)
+    Vd = torch.from_numpy(V).to(DEV)
+    R = torch.empty((n_chan, n_in, n_in), dtype=torch.complex64, device=DEV)
+    c.xengine_dev(Vd, n_spec, R)
+    torch.cuda.synchronize()
+    Ro = fx.x_engine(np.transpose(V[:, :, :n_in].astype(np.complex128), (2, 0, 1)), n_spec)[0]
+    Rg = R.cpu().numpy()
+    assert _vis_err(Rg[None], Ro[None]).max() < 1e-5
+    assert np.all(Rg == np.conj(np.swapaxes(Rg, -1, -2)))          # exactly Hermitian
+    assert np.all(np.einsum('kaa->ka', Rg).imag == 0)
+
+
+@pytest.mark.parametrize("window,n_chan,n_in", [(64, 256, 3), (64, 64, 1), (32, 128, 4), (8, 8, 2), (256, 512, 2)])
+def test_mad_flags_match_oracle(window, n_chan, n_in):
+    rng = np.random.default_rng(window + n_chan)
+    n_vis = 3
+    R = (rng.rayleigh(1.0, (n_vis, n_chan, n_in, n_in)) *
+         np.exp(1j * rng.uniform(0, 6.3, (n_vis, n_chan, n_in, n_in))))
+    hit = rng.random(R.shape) < 0.05
+    R[hit] *= 20.0                                           # outliers
+    R[1, :window, 0, 0] = 2.0                                # MAD = 0 window
+    R[1, 3, 0, 0] = 3.0
+    R = (R + np.conj(np.swapaxes(R, -1, -2))) / 2            # Hermitian
+    R = R.astype(np.complex64)
+    c = _corr(n_in, 1, n_chan, 4, 16, flag_window=window)
+    Rd = torch.from_numpy(R).to(DEV)
+    F = torch.full(R.shape, 7, dtype=torch.uint8, device=DEV)
+    c.flag_dev(Rd, n_vis, F)
+    torch.cuda.synchronize()
+    Fo, Ao, To = fx.mad_flags(R.astype(np.complex128), 5.0, window)
+    ok = _flags_ok(F.cpu().numpy(), R.astype(np.complex128), Fo, To)
+    assert ok.all(), np.argwhere(~ok)[:5]
+    assert F.cpu().numpy()[1, 3, 0, 0] == 1
+
+
+# ---------------------------------------------------------------------------
+# Whole path
+# ---------------------------------------------------------------------------
+
+def _run_dev(c, x, partial=False):
+    xd = torch.from_numpy(x).to(DEV)
+    n = c.n_integrations(x.shape[1], partial)
+    vis = torch.empty((max(n, 1), c.n_chan, c.n_in, c.n_in), dtype=torch.complex64, device=DEV)
+    flags = torch.empty((max(n, 1), c.n_chan, c.n_in, c.n_in), dtype=torch.uint8, device=DEV)
+    got = c.run_dev(xd, vis, flags, include_partial=partial)
+    torch.cuda.synchronize()
+    assert got == n
+    return vis.cpu().numpy()[:n], flags.cpu().numpy()[:n]
+
+
+@pytest.mark.parametrize("n_chan,n_int,n_in,partial", [(1024, 512, 4, False), (256, 100, 5, True),
+                                                       (64, 3, 8, True), (4096, 64, 8, False),
+                                                       (8192, 16, 2, True)])
+def test_run_dev_matches_oracle(n_chan, n_int, n_in, partial):
+    M = 2 * n_chan
+    S = M * (n_int * 3 + (n_int // 2 if partial else 0)) + 333
+    rng = np.random.default_rng(n_chan)
+    tau = np.concatenate([[0.0], rng.uniform(0, 40, n_in - 1)])
+    phi = rng.uniform(0, 2 * np.pi, n_in)
+    x = _stream(n_in, S, seed=n_chan + n_in, tau=tau, phi=phi)
+    c = _corr(n_in, 1, n_chan, 4, n_int)
+    c.set_delays(tau, phi)
+    Rg, Fg = _run_dev(c, x, partial)
+    Ro, Fo, To = fx.correlate(x, n_chan, 4, n_int, tau, phi, partial=partial)
+    assert Rg.shape == Ro.shape
+    assert _vis_err(Rg, Ro).max() < 1e-5
+    assert _flags_ok(Fg, Ro, Fo, To).all()
+
+
+def test_c1_full_size_matches_oracle():
+    spec = config_c1()                                  # 4 x 2^22 samples
+    x = make_stream(spec)
+    tau, phi = np.asarray(spec.tau), np.asarray(spec.phi)
+    c = _corr(4, 1, 1024, 4, 512)
+    c.set_delays(tau, phi)
+    Rg, Fg = _run_dev(c, x)
+    Ro, Fo, To = fx.correlate(x, 1024, 4, 512, tau, phi)
+    assert Rg.shape == (4, 1024, 4, 4)
+    assert _vis_err(Rg, Ro).max() < 1e-5
+    assert _flags_ok(Fg, Ro, Fo, To).all()
+    # the same stream through the host streaming API
+    c2 = _corr(4, 1, 1024, 4, 512)
+    c2.set_delays(tau, phi)
+    c2.push(x)
+    c2.flush()
+    assert np.array_equal(c2.get_vis(), Rg)
+    assert np.array_equal(c2.get_flags(), Fg)
+
+
+# ---------------------------------------------------------------------------
+# Streaming: chunking invariance, flush, delay changes
+# ---------------------------------------------------------------------------
+
+def _push_all(c, x, sizes):
+    pos = 0
+    for n in sizes:
+        c.push(x[:, pos:pos + n])
+        pos += n
+    assert pos == x.shape[1]
+
+
+def test_streaming_chunking_is_bit_identical_and_matches_oracle():
+    n_chan, n_int, n_in = 128, 24, 4
+    M = 2 * n_chan
+    S = M * (n_int * 4 + 7) + 51
+    tau = np.array([0.0, 9.7, 33.2, 2.0])
+    phi = np.array([0.0, 1.0, 2.0, 3.0])
+    x = _stream(n_in, S, seed=77, tau=tau, phi=phi)
+    outs = []
+    rng = np.random.default_rng(3)
+    plans = [[S], [1] * 300 + [S - 300], [257, 13, 4099, 1, 3] + [S - 4373]]
+    sizes = []
+    left = S
+    while left > 0:
+        n = int(min(left, rng.integers(1, 3 * M)))
+        sizes.append(n)
+        left -= n
+    plans.append(sizes)
+    for plan in plans:
+        c = _corr(n_in, 1, n_chan, 4, n_int, chunk=1000)
+        c.set_delays(tau, phi)
+        _push_all(c, x, plan)
+        c.flush()
+        outs.append((c.get_vis(), c.get_flags()))
+    for v, f in outs[1:]:
+        assert np.array_equal(v, outs[0][0])
+        assert np.array_equal(f, outs[0][1])
+    Ro, Fo, To = fx.correlate(x, n_chan, 4, n_int, tau, phi, partial=True)
+    assert outs[0][0].shape == Ro.shape
+    assert _vis_err(outs[0][0], Ro).max() < 1e-5
+    assert _flags_ok(outs[0][1], Ro, Fo, To).all()
+
+
+def test_delay_change_applies_at_integration_boundary():
+    n_chan, n_int, n_in = 64, 10, 3
+    M = 2 * n_chan
+    S = M * n_int * 3
+    t0, p0 = np.array([0.0, 5.0, 20.0]), np.array([0.0, 0.5, 1.0])
+    t1, p1 = np.array([0.0, -3.2, 11.6]), np.array([0.2, -0.5, 2.0])
+    x = _stream(n_in, S, seed=11)
+    c = _corr(n_in, 1, n_chan, 4, n_int)
+    c.set_delays(t0, p0)
+    first = M * n_int + 20                       # integration 0 done, 1 not started
+    c.push(x[:, :first])
+    assert c.pending() == 1
+    c.set_delays(t1, p1)
+    c.push(x[:, first:])
+    c.flush()
+    Rg, Fg = c.get_vis(), c.get_flags()
+    Ro, Fo, To = fx.correlate(x, n_chan, 4, n_int, schedule=[(t0, p0), (t1, p1), (t1, p1)])
+    assert _vis_err(Rg, Ro).max() < 1e-5
+    assert _flags_ok(Fg, Ro, Fo, To).all()
+
+
+def test_empty_and_tiny_streams():
+    c = _corr(2, 1, 32, 4, 4)
+    c.push(np.zeros((2, 0), np.int8))
+    c.flush()
+    assert c.get_vis().shape[0] == 0
+    c.reset()
+    x = _stream(2, 63, seed=1)                   # shorter than one frame
+    c.push(x)
+    c.flush()
+    assert c.get_vis().shape[0] == 0
+    from paper_2604_20640_gb300 import CorrError, CORR_ESTATE
+    with pytest.raises(CorrError) as e:
+        c.push(x)
+    assert e.value.code == CORR_ESTATE
+
+
+def test_push_dev_matches_push():
+    n_chan, n_int, n_in = 256, 16, 4
+    M = 2 * n_chan
+    S = M * n_int * 3 + 100
+    x = _stream(n_in, S, seed=21)
+    c1 = _corr(n_in, 1, n_chan, 4, n_int)
+    c1.push(x)
+    c1.flush()
+    c2 = _corr(n_in, 1, n_chan, 4, n_int)
+    xd = torch.from_numpy(x).to(DEV)
+    c2.push_dev(xd[:, :5000])
+    c2.push_dev(xd[:, 5000:])
+    c2.flush()
+    assert np.array_equal(c1.get_vis(), c2.get_vis())
