@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 FX correlator hot path.
+
+One step = the whole hot path (F-engine: PFB + real FFT + coarse/fine delay
+and phase; X-engine with integration; MAD flagging) over one synthetic
+stream shaped like the four-antenna dual-pol L-band streaming workload:
+8 inputs x 2^28 int8 samples, 4096 channels, 4-tap PFB, 1024-spectrum
+integrations (32 per stream), sigma = 5 over 64-channel windows.
+
+  value : input GB/s with the stream resident in HBM (corr_run_dev), timed
+          with CUDA events on the launching stream; inputs (2 GiB) exceed L2.
+  e2e   : the same metric through corr_push from pinned host memory in
+          64 MiB chunks, plus corr_get_vis / corr_get_flags, per step.
+
+Multi-GPU: replicas only -- each rank correlates its own stream, no
+collective on the data path; value = all ranks' bytes / max rank time.
+``--impl reference`` times the FP64 CPU oracle on host cores instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sustained input GB/s (PFB+X+flag, 1 GB300) vs plain FP32 path at stated vis error"
+
+WORKLOADS = {
+    "c2": dict(n_ant=4, n_pol=2, n_chan=4096, taps=4, n_int=1024, samples=1 << 28, chunk=1 << 23,
+               desc="4 ant x 2 pol int8 real, 2^28 samples/input (2 GiB), 4-tap Hann-sinc PFB, "
+                    "4096 ch, n_int 1024, 3 tones +20 dB, 1% bursts +10 dB, delays 0-40 smp, "
+                    "MAD sigma 5 / 64 ch"),
+    "c1": dict(n_ant=4, n_pol=1, n_chan=1024, taps=4, n_int=512, samples=1 << 22, chunk=1 << 22,
+               desc="4 ant x 1 pol int8 real, 2^22 samples/input, 4-tap PFB, 1024 ch, n_int 512"),
+}
+
+# Algorithmic bytes per input sample of each kernel (see the design notes):
+# F-engine reads 1 B of int8 and writes one complex64 per channel per input,
+# i.e. 8 B per 2 samples.
+F_BYTES_PER_SAMPLE = 1.0 + 4.0
+
+
+def _spec(wl, rank, samples):
+    from fxsynth import config_c1, config_c2
+    if wl == "c2":
+        return config_c2(seed=2000 + rank, n_samples=samples, M=2 * WORKLOADS[wl]["n_chan"])
+    return config_c1(seed=1000 + rank, n_samples=samples)
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        self.gpu = gpu_index
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                pass
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_baseline(wl, n_integrations=4):
+    """Time the FP64 oracle, as it stands, on a bounded sample of the workload:
+    the first ``n_integrations`` integrations of one stream, one thread."""
+    W = WORKLOADS[wl]
+    M = 2 * W["n_chan"]
+    samples = M * W["n_int"] * n_integrations
+    code = (
+        "import sys, time, json, numpy as np\n"
+        "sys.path.insert(0, %r)\n"
+        "from fxsynth import config_c1, config_c2, make_stream\n"
+        "from oracle import fx_oracle as fx\n"
+        "spec = (config_c2(seed=2000, n_samples=%d, M=%d) if %r == 'c2' else config_c1(seed=1000, n_samples=%d))\n"
+        "x = make_stream(spec)\n"
+        "t0 = time.perf_counter()\n"
+        "R, F, T = fx.correlate(x, %d, %d, %d, spec.tau, spec.phi)\n"
+        "dt = time.perf_counter() - t0\n"
+        "print(json.dumps({'seconds': dt, 'bytes': int(x.size), 'n_int': int(R.shape[0])}))\n"
+    ) % (ROOT, samples, M, wl, samples, W["n_chan"], W["taps"], W["n_int"])
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else "failed"}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["bytes"] / d["seconds"] / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d integrations of one stream (%d MiB int8), FP64 numpy oracle, 1 thread, %.1f s"
+                      % (d["n_int"], d["bytes"] >> 20, d["seconds"])}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    W = WORKLOADS[args.workload]
+    M = 2 * W["n_chan"]
+    samples = M * W["n_int"]
+    code = (
+        "import sys, time, json, numpy as np\n"
+        "sys.path.insert(0, %r)\n"
+        "from fxsynth import config_c1, config_c2, make_stream\n"
+        "from oracle import fx_oracle as fx\n"
+        "spec = (config_c2(seed=2000, n_samples=%d, M=%d) if %r == 'c2' else config_c1(seed=1000, n_samples=%d))\n"
+        "x = make_stream(spec)\n"
+        "ts = []\n"
+        "for i in range(%d):\n"
+        "    t0 = time.perf_counter()\n"
+        "    fx.correlate(x, %d, %d, %d, spec.tau, spec.phi)\n"
+        "    ts.append(time.perf_counter() - t0)\n"
+        "print(json.dumps({'times': ts[%d:], 'bytes': int(x.size)}))\n"
+    ) % (ROOT, samples, M, args.workload, samples, args.warmup + args.steps, W["n_chan"], W["taps"],
+         W["n_int"], args.warmup)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle run failed: " +
+                          (r.stderr.strip().splitlines() or ["?"])[-1]}))
+        return
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    ms = 1e3 * sum(d["times"]) / len(d["times"])
+    val = d["bytes"] / (ms * 1e-3) / 1e9
+    out = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload + ": " + W["desc"], "sample": "one integration per step",
+                   "l2": "host CPU path"},
+        "cpu_baseline": {"value": val, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": "one integration (%d MiB int8) per step, FP64 numpy oracle, 1 thread"
+                                   % (d["bytes"] >> 20)},
+        "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--samples", type=int, default=0, help="override samples per input")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2604_20640_gb300 import Correlator
+    from fxsynth.streams_torch import make_stream_torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    W = WORKLOADS[args.workload]
+    S = args.samples or W["samples"]
+    n_in = W["n_ant"] * W["n_pol"]
+    spec = _spec(args.workload, rank, S)
+    x = make_stream_torch(spec, device=dev)
+    c = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"])
+    c.set_delays(spec.tau, spec.phi)
+    n_intg = c.n_integrations(S)
+    vis = torch.empty((n_intg, W["n_chan"], n_in, n_in), dtype=torch.complex64, device=dev)
+    flags = torch.empty((n_intg, W["n_chan"], n_in, n_in), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        c.run_dev(x, vis, flags)
+    torch.cuda.synchronize(dev)
+    c.set_option("stage_timing", 1)
+    c.stage_times()
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    l0 = c.launches
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        c.run_dev(x, vis, flags)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clk = clocks.stop()
+    launches = c.launches - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    stage_ms, stage_n = c.stage_times()
+    c.set_option("stage_timing", 0)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    bytes_step = n_in * S
+    value = world * bytes_step / (ms * 1e-3) / 1e9
+
+    # ---- end to end through the public host API ----
+    e2e = None
+    if not args.no_e2e:
+        ce = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"], chunk=W["chunk"])
+        ce.set_delays(spec.tau, spec.phi)
+        host = torch.empty((n_in, S), dtype=torch.int8, pin_memory=True)
+        host.copy_(x)
+        chunk = W["chunk"]
+
+        def e2e_step():
+            for p in range(0, S, chunk):
+                ce.push(host[:, p:p + chunk])
+            ce.flush()
+            v = ce.get_vis()
+            f = ce.get_flags()
+            ce.reset()
+            return v, f
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            v, f = e2e_step()
+        t1 = time.perf_counter()
+        barrier()
+        ems = (t1 - t0) * 1e3 / args.steps
+        if world > 1:
+            t = torch.tensor([ems], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * bytes_step / (ems * 1e-3) / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": int(v.nbytes + f.nbytes),
+               "ms_per_step": ems}
+        ce.close()
+        del host
+
+    # ---- roofline of the dominant kernel (F-engine), from the live events ----
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    f_launches = stage_n[0]
+    f_ms = stage_ms[0]
+    n_spec = S // (2 * W["n_chan"])
+    f_samples = args.steps * n_spec * 2 * W["n_chan"] * n_in
+    f_bytes_per_launch = F_BYTES_PER_SAMPLE * f_samples / max(1, f_launches)
+    f_avg_ms = f_ms / max(1, f_launches)
+    achieved = f_bytes_per_launch / (f_avg_ms * 1e-3) / 1e9
+    total_stage = sum(stage_ms) or 1.0
+    roofline = {"kernel": "fengine_kernel<8192>", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                "peak_source": peak_src,
+                "bytes_per_launch": f_bytes_per_launch, "avg_launch_ms": f_avg_ms,
+                "stage_share": {k: stage_ms[i] / total_stage for i, k in
+                                enumerate(["fengine", "xengine", "finalize", "flag"])}}
+
+    if rank == 0:
+        cpu = None if args.no_cpu else cpu_baseline(args.workload)
+        out = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload + ": " + W["desc"], "path": "plain FP32 (CUDA-core X)",
+                       "samples_per_input": S, "l2": "inputs (%d MiB/step) larger than L2" % (bytes_step >> 20),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "gpu_launches": launches, "clocks": clk, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
+        }
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

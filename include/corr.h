@@ -87,6 +87,7 @@ const char* corr_last_error(corr_t h);
  *   "chunk"       (samples/input, default 1<<23) largest device batch
  *   "precision"   (CORR_FP32 / CORR_INT8 / CORR_FP8, default FP32)
  *   "result_slots" (default 8)               pinned result FIFO depth (grows)
+ *   "stage_timing" (0/1, default 0; may change at any time)  per-stage events
  */
 int corr_set_option(corr_t h, const char* key, double value);
 
@@ -183,6 +184,17 @@ int corr_shape(corr_t h, int* n_in, int* n_chan, int* taps, int* n_int, int* n_i
 
 /* Number of CUDA kernels this handle has launched (instrumentation). */
 long long corr_kernel_launches(corr_t h);
+
+/*
+ * corr_stage_times -- per-stage GPU time, the correlator's counterpart of
+ * the per-stage timings the paper tracks in Sec. 6 (GPU compute, H2D).
+ * With option "stage_timing" = 1 every kernel launch is bracketed by CUDA
+ * events on its own stream.  This call waits for those events and returns,
+ * for stages 0 F-engine, 1 X-engine, 2 finalise, 3 flagging (first
+ * n_stages entries), the milliseconds and launch counts accumulated since
+ * the previous call, then clears them.  ms / counts may be NULL.
+ */
+int corr_stage_times(corr_t h, double* ms, long long* counts, int n_stages);
 
 #ifdef __cplusplus
 }

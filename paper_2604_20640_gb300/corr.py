@@ -32,7 +32,7 @@ EXPORTED = [
     "corr_create", "corr_destroy", "corr_last_error", "corr_set_option", "corr_set_delays",
     "corr_push", "corr_push_dev", "corr_flush", "corr_reset", "corr_get_vis", "corr_get_flags",
     "corr_pending", "corr_run_dev", "corr_fengine_dev", "corr_xengine_dev", "corr_flag_dev",
-    "corr_shape", "corr_kernel_launches",
+    "corr_shape", "corr_kernel_launches", "corr_stage_times",
 ]
 
 
@@ -78,6 +78,7 @@ def load_library(path: str = LIB_PATH):
         "corr_flag_dev": (_i, [_vp, _vp, _i, _vp, _vp]),
         "corr_shape": (_i, [_vp] + [ctypes.POINTER(_i)] * 5),
         "corr_kernel_launches": (_ll, [_vp]),
+        "corr_stage_times": (_i, [_vp, _vp, _vp, _i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -263,6 +264,13 @@ class Correlator:
     def flag_dev(self, vis, n_vis: int, flags_out, stream=None):
         self._check(self._L.corr_flag_dev(self._h, _dev_ptr(vis, "vis"), int(n_vis),
                                           _dev_ptr(flags_out, "flags"), _stream_ptr(stream)))
+
+    def stage_times(self):
+        """(ms, counts) per stage (F, X, finalise, flag) since the last call."""
+        ms = (ctypes.c_double * 4)()
+        n = (ctypes.c_longlong * 4)()
+        self._check(self._L.corr_stage_times(self._h, ms, n, 4))
+        return list(ms), list(n)
 
     @property
     def launches(self) -> int:

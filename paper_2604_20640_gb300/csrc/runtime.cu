@@ -46,6 +46,27 @@ struct Tables {
     int d_max = 0;              // largest coarse advance
 };
 
+// Optional CUDA-event brackets around every kernel launch, per stage
+// (0 F-engine, 1 X-engine, 2 finalise, 3 flag).
+constexpr int kStages = 4;
+struct StageTimer {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> open[kStages];
+    double ms[kStages] = {0, 0, 0, 0};
+    long long n[kStages] = {0, 0, 0, 0};
+    cudaEvent_t take() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+};
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {
@@ -99,6 +120,7 @@ struct corr_s {
     std::deque<int> q_vis, q_flag;
     std::string err;
     long long launches = 0;
+    StageTimer timer;
 };
 
 namespace {
@@ -121,6 +143,28 @@ int fail(corr_t h, int code, const std::string& msg) {
         int r_ = (expr);         \
         if (r_ != CORR_OK) return r_; \
     } while (0)
+
+// Bracket one launch of `stage` on stream st with events (when enabled).
+struct Timed {
+    corr_t h;
+    int stage;
+    cudaStream_t st;
+    cudaEvent_t e0 = nullptr;
+    Timed(corr_t h_, int stage_, cudaStream_t st_) : h(h_), stage(stage_), st(st_) {
+        if (h->timer.on) {
+            e0 = h->timer.take();
+            cudaEventRecord(e0, st);
+        }
+    }
+    ~Timed() {
+        ++h->launches;
+        if (e0) {
+            cudaEvent_t e1 = h->timer.take();
+            cudaEventRecord(e1, st);
+            h->timer.open[stage].push_back({e0, e1});
+        }
+    }
+};
 
 bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
 
@@ -217,8 +261,10 @@ int launch_f(corr_t h, const StreamView& sv, const Tables& t, Pipe& p, long long
     a.M = h->M;
     a.taps = h->taps;
     a.spt = choose_spt(s_end - s_begin, h->n_in_pad / 2);
-    launch_fengine(a, st);
-    ++h->launches;
+    {
+        Timed t_(h, 0, st);
+        launch_fengine(a, st);
+    }
     CK(cudaGetLastError());
     return CORR_OK;
 }
@@ -278,8 +324,10 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
             x.j0 = j_begin;
             x.n_groups = j_end - j_begin;
             x.part = p.part;
-            launch_xengine(x, st);
-            ++h->launches;
+            {
+                Timed t_(h, 1, st);
+                launch_xengine(x, st);
+            }
             CK(cudaGetLastError());
             long long nx = istart + (long long)j_end * h->G;
             if (nx > s_limit) nx = s_limit;
@@ -310,13 +358,17 @@ int finalize_into(corr_t h, const Pipe& p, float2* R, uint8_t* F, int count, int
     f.n_in = h->n_in;
     f.scale = 1.0f / (float)count;
     f.R = R;
-    launch_finalize(f, st);
-    ++h->launches;
+    {
+        Timed t_(h, 2, st);
+        launch_finalize(f, st);
+    }
     CK(cudaGetLastError());
     if (F) {
         const int w = h->flag_window < h->n_chan ? h->flag_window : h->n_chan;
-        launch_mad_flags(R, F, 1, h->n_chan, h->n_in, w, (float)h->flag_sigma, st);
-        ++h->launches;
+        {
+            Timed t_(h, 3, st);
+            launch_mad_flags(R, F, 1, h->n_chan, h->n_in, w, (float)h->flag_sigma, st);
+        }
         CK(cudaGetLastError());
     }
     return CORR_OK;
@@ -588,6 +640,12 @@ int corr_destroy(corr_t h) {
         cudaFreeHost(s.h_F);
         if (s.ev) cudaEventDestroy(s.ev);
     }
+    for (cudaEvent_t e : h->timer.pool) cudaEventDestroy(e);
+    for (int i = 0; i < kStages; ++i)
+        for (auto& pr : h->timer.open[i]) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
     free_pipe(h->ps);
     free_pipe(h->pd);
     cudaFree(h->d_part_x);
@@ -616,8 +674,9 @@ const char* corr_last_error(corr_t h) {
 
 int corr_set_option(corr_t h, const char* key, double v) {
     if (!h || !key) return fail(h, CORR_EINVAL, "NULL argument");
-    if (h->started) return fail(h, CORR_ESTATE, "options must be set before the first push");
     const std::string k(key);
+    if (h->started && k != "stage_timing")
+        return fail(h, CORR_ESTATE, "options must be set before the first push");
     if (k == "flag_sigma") {
         if (!(v > 0)) return fail(h, CORR_EINVAL, "flag_sigma must be > 0");
         h->flag_sigma = v;
@@ -635,6 +694,9 @@ int corr_set_option(corr_t h, const char* key, double v) {
     } else if (k == "precision") {
         if (v != CORR_FP32) return fail(h, CORR_EINVAL, "precision: only CORR_FP32 in this build");
         h->precision = (int)v;
+    } else if (k == "stage_timing") {
+        h->timer.on = v != 0;
+        return CORR_OK;
     } else if (k == "result_slots") {
         if (v < 1 || v > 4096) return fail(h, CORR_EINVAL, "result_slots out of range");
         h->result_slots = (int)v;
@@ -783,8 +845,10 @@ int corr_fengine_dev(corr_t h, const int8_t* d_samples, size_t n_samples, size_t
     a.M = h->M;
     a.taps = h->taps;
     a.spt = choose_spt(n_spec, h->n_in_pad / 2);
-    launch_fengine(a, static_cast<cudaStream_t>(stream));
-    ++h->launches;
+    {
+        Timed t_(h, 0, static_cast<cudaStream_t>(stream));
+        launch_fengine(a, static_cast<cudaStream_t>(stream));
+    }
     CK(cudaGetLastError());
     return CORR_OK;
 }
@@ -816,8 +880,10 @@ int corr_xengine_dev(corr_t h, const float* d_V, int n_spec, float* d_vis, void*
     x.j0 = 0;
     x.n_groups = (int)slots;
     x.part = h->d_part_x;
-    launch_xengine(x, st);
-    ++h->launches;
+    {
+        Timed t_(h, 1, st);
+        launch_xengine(x, st);
+    }
     CK(cudaGetLastError());
     FinArgs f{};
     f.part = h->d_part_x;
@@ -827,8 +893,10 @@ int corr_xengine_dev(corr_t h, const float* d_V, int n_spec, float* d_vis, void*
     f.n_in = h->n_in;
     f.scale = 1.0f / (float)n_spec;
     f.R = reinterpret_cast<float2*>(d_vis);
-    launch_finalize(f, st);
-    ++h->launches;
+    {
+        Timed t_(h, 2, st);
+        launch_finalize(f, st);
+    }
     CK(cudaGetLastError());
     return CORR_OK;
 }
@@ -838,9 +906,11 @@ int corr_flag_dev(corr_t h, const float* d_vis, int n_vis, uint8_t* d_flags, voi
     DeviceGuard g(h->dev);
     if (!d_vis || !d_flags || n_vis < 0) return fail(h, CORR_EINVAL, "bad argument");
     const int w = h->flag_window < h->n_chan ? h->flag_window : h->n_chan;
-    launch_mad_flags(reinterpret_cast<const float2*>(d_vis), d_flags, n_vis, h->n_chan, h->n_in, w,
-                     (float)h->flag_sigma, static_cast<cudaStream_t>(stream));
-    ++h->launches;
+    {
+        Timed t_(h, 3, static_cast<cudaStream_t>(stream));
+        launch_mad_flags(reinterpret_cast<const float2*>(d_vis), d_flags, n_vis, h->n_chan, h->n_in, w,
+                         (float)h->flag_sigma, static_cast<cudaStream_t>(stream));
+    }
     CK(cudaGetLastError());
     return CORR_OK;
 }
@@ -856,5 +926,31 @@ int corr_shape(corr_t h, int* n_in, int* n_chan, int* taps, int* n_int, int* n_i
 }
 
 long long corr_kernel_launches(corr_t h) { return h ? h->launches : 0; }
+
+int corr_stage_times(corr_t h, double* ms, long long* counts, int n_stages) {
+    if (!h) return fail(h, CORR_EINVAL, "NULL handle");
+    DeviceGuard g(h->dev);
+    for (int i = 0; i < kStages; ++i) {
+        for (auto& pr : h->timer.open[i]) {
+            CK(cudaEventSynchronize(pr.second));
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, pr.first, pr.second));
+            h->timer.ms[i] += t;
+            ++h->timer.n[i];
+            h->timer.pool.push_back(pr.first);
+            h->timer.pool.push_back(pr.second);
+        }
+        h->timer.open[i].clear();
+    }
+    for (int i = 0; i < n_stages && i < kStages; ++i) {
+        if (ms) ms[i] = h->timer.ms[i];
+        if (counts) counts[i] = h->timer.n[i];
+    }
+    for (int i = 0; i < kStages; ++i) {
+        h->timer.ms[i] = 0;
+        h->timer.n[i] = 0;
+    }
+    return CORR_OK;
+}
 
 }  // extern "C"
