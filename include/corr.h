@@ -196,6 +196,30 @@ long long corr_kernel_launches(corr_t h);
  */
 int corr_stage_times(corr_t h, double* ms, long long* counts, int n_stages);
 
+/*
+ * corr_xengine_noalloc -- the X-engine of corr_xengine_dev for callers that
+ * cannot allocate device memory (code recording a CUDA graph that must stay
+ * replayable, real-time loops where an allocator call could stall the
+ * device, hosts that manage the GPU's memory themselves).  The paper has no
+ * counterpart; it is a library facility.
+ *   d_V:    device [n_spec][n_chan][n_in_pad] complex64, n_in_pad = n_in
+ *           rounded up to a multiple of 4 (padding entries are ignored).
+ *   d_vis:  device [n_chan][n_in][n_in] complex64 output,
+ *           R[k][a][b] = (1/n_spec) sum_s V_a V_b^*.
+ *   stream: cudaStream_t as void*.
+ * Needs no handle and allocates nothing: its partial sums live in one 8 MiB
+ * file-scope device array that every GPU loading the library keeps until
+ * exit.  Shapes whose per-group scratch ((blocks of 4 inputs, A <= B) * 32 *
+ * n_chan floats) exceeds 2^21 floats are rejected with CORR_EINVAL; long
+ * streams are summed in fewer, longer groups.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  All calls share the array and it keeps the
+ * last call's contents (every part a call reads it first writes itself), so
+ * calls that overlap on the GPU race: serialise them on one stream.  On
+ * failure corr_last_error(NULL) describes the error.
+ */
+int corr_xengine_noalloc(const float* d_V, int n_spec, int n_in, int n_chan, float* d_vis, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,7 +32,7 @@ EXPORTED = [
     "corr_create", "corr_destroy", "corr_last_error", "corr_set_option", "corr_set_delays",
     "corr_push", "corr_push_dev", "corr_flush", "corr_reset", "corr_get_vis", "corr_get_flags",
     "corr_pending", "corr_run_dev", "corr_fengine_dev", "corr_xengine_dev", "corr_flag_dev",
-    "corr_shape", "corr_kernel_launches", "corr_stage_times",
+    "corr_shape", "corr_kernel_launches", "corr_stage_times", "corr_xengine_noalloc",
 ]
 
 
@@ -79,6 +79,7 @@ def load_library(path: str = LIB_PATH):
         "corr_shape": (_i, [_vp] + [ctypes.POINTER(_i)] * 5),
         "corr_kernel_launches": (_ll, [_vp]),
         "corr_stage_times": (_i, [_vp, _vp, _vp, _i]),
+        "corr_xengine_noalloc": (_i, [_vp, _i, _i, _i, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -104,6 +105,17 @@ def _dev_ptr(t, dtype_name: str):
     if not t.is_contiguous() and dtype_name != "samples":
         raise CorrError(CORR_EINVAL, "device buffer must be contiguous")
     return t.data_ptr()
+
+
+def xengine_noalloc(V, n_spec: int, n_in: int, n_chan: int, vis_out, stream=None):
+    """X-engine without any device allocation (corr_xengine_noalloc): for
+    callers that may not allocate, e.g. while capturing a CUDA graph.  Same
+    layouts as :meth:`Correlator.xengine_dev`; no handle needed."""
+    L = load_library()
+    rc = L.corr_xengine_noalloc(_dev_ptr(V, "V"), int(n_spec), int(n_in), int(n_chan),
+                                _dev_ptr(vis_out, "vis"), _stream_ptr(stream))
+    if rc != CORR_OK:
+        raise CorrError(rc, L.corr_last_error(None).decode())
 
 
 class Correlator:

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace corr {
 
 // Device-resident view of a sample stream for the F-engine.  Input a's
@@ -61,6 +63,9 @@ void launch_mad_flags(const float2* R, uint8_t* F, int n_vis, int n_chan, int n_
                       float sigma, cudaStream_t st);
 
 int fengine_threads(int M);
+
+// Error text reported by corr_last_error(NULL) (calls without a handle).
+void set_global_error(const std::string& msg);
 size_t fengine_smem_bytes(int M);
 
 }  // namespace corr

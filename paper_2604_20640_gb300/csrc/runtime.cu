@@ -569,6 +569,8 @@ void free_pipe(Pipe& p) {
 
 }  // namespace
 
+void corr::set_global_error(const std::string& msg) { g_create_error = msg; }
+
 extern "C" {
 
 int corr_create(corr_t* out, int n_ant, int n_pol, int n_chan, int taps, int n_int) {
