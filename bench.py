@@ -42,10 +42,15 @@ WORKLOADS = {
                desc="4 ant x 1 pol int8 real, 2^22 samples/input, 4-tap PFB, 1024 ch, n_int 512"),
 }
 
-# Algorithmic bytes per input sample of each kernel (see the design notes):
-# F-engine reads 1 B of int8 and writes one complex64 per channel per input,
-# i.e. 8 B per 2 samples.
-F_BYTES_PER_SAMPLE = 1.0 + 4.0
+# Stages reported by corr_stage_times, their kernels, and the algorithmic bytes
+# each moves per input sample (see the design notes):
+#   FIR  reads 1 B int8, writes z = (y_a, y_b) as FP32: 4 B;
+#   FFT  reads z (4 B) and writes one complex64 per channel per input (4 B);
+#   X    reads the channelised spectra (4 B); finalise / flag: per integration.
+STAGES = ["fir", "fft", "xengine", "finalize", "flag"]
+KERNELS = {"fir": "fir_kernel<4>", "fft": "fft_kernel<8192,false>", "xengine": "xengine_small_kernel<2>",
+           "finalize": "finalize_kernel", "flag": "mad_flag_kernel"}
+BYTES_PER_SAMPLE = {"fir": 5.0, "fft": 8.0, "xengine": 4.0, "finalize": 0.0, "flag": 0.0}
 
 
 def _spec(wl, rank, samples):
@@ -290,25 +295,24 @@ def main():
         ce.close()
         del host
 
-    # ---- roofline of the dominant kernel (F-engine), from the live events ----
+    # ---- roofline of the dominant kernel, from the live per-stage events ----
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs")
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
-    f_launches = stage_n[0]
-    f_ms = stage_ms[0]
-    n_spec = S // (2 * W["n_chan"])
-    f_samples = args.steps * n_spec * 2 * W["n_chan"] * n_in
-    f_bytes_per_launch = F_BYTES_PER_SAMPLE * f_samples / max(1, f_launches)
-    f_avg_ms = f_ms / max(1, f_launches)
-    achieved = f_bytes_per_launch / (f_avg_ms * 1e-3) / 1e9
     total_stage = sum(stage_ms) or 1.0
-    roofline = {"kernel": "fengine_kernel<8192>", "bound": "hbm", "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                "peak_source": peak_src,
-                "bytes_per_launch": f_bytes_per_launch, "avg_launch_ms": f_avg_ms,
-                "stage_share": {k: stage_ms[i] / total_stage for i, k in
-                                enumerate(["fengine", "xengine", "finalize", "flag"])}}
+    share = {k: stage_ms[i] / total_stage for i, k in enumerate(STAGES)}
+    dom = max((k for k in STAGES if BYTES_PER_SAMPLE[k] > 0), key=lambda k: share[k])
+    di = STAGES.index(dom)
+    n_spec = S // (2 * W["n_chan"])
+    samples_timed = args.steps * n_spec * 2 * W["n_chan"] * n_in
+    bytes_per_launch = BYTES_PER_SAMPLE[dom] * samples_timed / max(1, stage_n[di])
+    avg_ms = stage_ms[di] / max(1, stage_n[di])
+    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+    roofline = {"kernel": KERNELS[dom], "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "peak_source": peak_src,
+                "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms, "launches": stage_n[di],
+                "stage_share": share}
 
     if rank == 0:
         cpu = None if args.no_cpu else cpu_baseline(args.workload)

@@ -190,9 +190,10 @@ long long corr_kernel_launches(corr_t h);
  * the per-stage timings the paper tracks in Sec. 6 (GPU compute, H2D).
  * With option "stage_timing" = 1 every kernel launch is bracketed by CUDA
  * events on its own stream.  This call waits for those events and returns,
- * for stages 0 F-engine, 1 X-engine, 2 finalise, 3 flagging (first
- * n_stages entries), the milliseconds and launch counts accumulated since
- * the previous call, then clears them.  ms / counts may be NULL.
+ * for stages 0 FIR, 1 FFT (the two F-engine kernels), 2 X-engine,
+ * 3 finalise, 4 flagging (first n_stages entries), the milliseconds and
+ * launch counts accumulated since the previous call, then clears them.
+ * ms / counts may be NULL.
  */
 int corr_stage_times(corr_t h, double* ms, long long* counts, int n_stages);
 

@@ -278,10 +278,10 @@ class Correlator:
                                           _dev_ptr(flags_out, "flags"), _stream_ptr(stream)))
 
     def stage_times(self):
-        """(ms, counts) per stage (F, X, finalise, flag) since the last call."""
-        ms = (ctypes.c_double * 4)()
-        n = (ctypes.c_longlong * 4)()
-        self._check(self._L.corr_stage_times(self._h, ms, n, 4))
+        """(ms, counts) per stage (FIR, FFT, X, finalise, flag) since the last call."""
+        ms = (ctypes.c_double * 5)()
+        n = (ctypes.c_longlong * 5)()
+        self._check(self._L.corr_stage_times(self._h, ms, n, 5))
         return list(ms), list(n)
 
     @property

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 namespace corr {
 
@@ -18,20 +19,42 @@ struct StreamView {
     long long vhi;
 };
 
-// F-engine launch: spectra s in [s_begin, s_end), one CTA per (input pair,
-// block of spt spectra).  Spectrum s is written to ring slot
-// (s - v_origin) mod v_cap of V [slot][n_chan][n_in_pad] (float2).
-struct FArgs {
+// Ring slots: spectrum s lives in slot (s - origin) & mask.  Rings that wrap
+// have a power-of-two capacity (mask = capacity - 1); a buffer that holds
+// exactly the spectra of one call uses origin = first spectrum and an
+// all-ones mask.
+//
+// F-engine, stage 1 (polyphase FIR).  Spectra s in [s_begin, s_end) of
+// every input pair (a, a+1) are filtered into the ring Z
+// [zslot][n_pairs][M] float2, z[m] = (y_a[m], y_b[m]).  Each thread owns 4
+// branches of one pair over `spt` consecutive spectra.
+struct FirArgs {
     StreamView src;
     const float* h;          // [taps][M] polyphase prototype, FP32
-    const float2* tw;        // [M] W_M^k = exp(-2 pi j k / M)
-    const float2* phasor;    // [n_in_pad][n_chan] delay/phase rotation (pair factors folded in)
     const int* coarse;       // [n_in_pad] coarse advance d_a
-    float2* V;
+    float2* Z;
+    long long z_origin;
+    long long z_mask;
     long long s_begin, s_end;
+    int n_in, n_pairs, M, lgM, taps, spt;
+};
+
+// F-engine, stage 2 (M-point complex FFT of z, then the two real spectra of
+// the pair).  Writes ring V [slot][n_chan][n_in_pad] (float2) with
+// U_a = Z[k] + Z*[M-k] (= 2 Y_a) and U_b = -j (Z[k] - Z*[M-k]) (= 2 Y_b),
+// or, when `phasor` is set, the rotated V_a = Y_a P_a (fine delay and
+// instrument phase folded into P, Eq. 1).
+struct FftArgs {
+    const float2* Z;
+    long long z_origin;
+    long long z_mask;
+    const float2* tw;        // per-pass twiddles, see fft_twiddle_table()
+    const float2* phasor;    // [n_in_pad][n_chan] or nullptr
+    float2* V;
     long long v_origin;
-    int v_cap;
-    int n_in, n_in_pad, M, taps, spt;
+    long long v_mask;
+    long long s_begin, s_end;
+    int n_in_pad, M, spt;
 };
 
 // X-engine launch: groups of spectra, each group summed into one partial
@@ -41,31 +64,37 @@ struct FArgs {
 struct XArgs {
     const float2* V;
     long long v_origin;
-    int v_cap;
+    long long v_mask;
     int n_chan, n_in_pad, nt;
     long long int_start, int_end, s_limit;
     int G, j0, n_groups;
     float* part;             // [gpi][nt][32][n_chan]
 };
 
-// Finalise: R[k][a][b] = (sum over partial slots 0..n_slots-1) * scale.
+// Finalise: R[k][a][b] = scale * Q_a[k] conj(Q_b[k]) * (sum over partial
+// slots 0..n_slots-1), Q = rot (or 1 when rot is null).
 struct FinArgs {
     const float* part;
+    const float2* rot;       // [n_in_pad][n_chan] or nullptr
     int n_slots, nt, n_chan, n_in;
     float scale;
     float2* R;               // [n_chan][n_in][n_in]
 };
 
-void launch_fengine(const FArgs& a, cudaStream_t st);
+void launch_fir(const FirArgs& a, cudaStream_t st);
+void launch_fft(const FftArgs& a, cudaStream_t st);
 void launch_xengine(const XArgs& a, cudaStream_t st);
 void launch_finalize(const FinArgs& a, cudaStream_t st);
 void launch_mad_flags(const float2* R, uint8_t* F, int n_vis, int n_chan, int n_in, int window,
                       float sigma, cudaStream_t st);
 
-int fengine_threads(int M);
+// Twiddles of every radix-16 pass of the M-point Stockham FFT, laid out
+// [pass][r][k] (k contiguous) with entry W_{16 Ns}^{r k}, r < 16, k < Ns,
+// passes in execution order (Ns = first radix, then x16 ...).  Returns the
+// table, computed in FP64 and rounded to FP32.
+std::vector<float2> fft_twiddle_table(int M);
 
 // Error text reported by corr_last_error(NULL) (calls without a handle).
 void set_global_error(const std::string& msg);
-size_t fengine_smem_bytes(int M);
 
 }  // namespace corr

@@ -1,18 +1,25 @@
-// F-engine: int8 load with coarse delay -> P-tap polyphase FIR -> M-point
-// FFT -> fine-delay / instrument-phase rotation (Sec. 4.2 "F-engine (PFB and
-// FFT)", with the delay compensation of Eq. 1 applied per input).
+// F-engine (Sec. 4.2 "F-engine (PFB and FFT)"): int8 load with the coarse
+// delay of Eq. 1 -> P-tap polyphase FIR -> M-point FFT.
 //
-// One CTA channelises one pair of inputs (a, a+1) for a block of consecutive
-// spectra.  The two real FIR outputs of the pair are packed as one complex
-// sequence z[m] = y_a[m] + j y_b[m]; a single M-point complex FFT then gives
-// both spectra: Y_a[k] = (Z[k] + Z*[M-k]) / 2 and Y_b[k] = (Z[k] - Z*[M-k]) / 2j.
-// The 1/2 and 1/2j factors are folded into the per-input phasor table.
+// Two kernels.  fir_kernel streams the samples: a thread owns four branches
+// m of one input pair over a run of consecutive spectra, converts every int8
+// sample once, keeps the last P frames and its P x 4 filter taps in
+// registers, and writes z[m] = y_a[m] + j y_b[m] (the pair's two real FIR
+// outputs packed as one complex sequence).  fft_kernel transforms z with one
+// M-point complex FFT and separates the two real spectra,
+// Y_a[k] = (Z[k] + Z*[M-k]) / 2 and Y_b[k] = (Z[k] - Z*[M-k]) / 2j.
 //
-// The FFT is a Stockham autosort transform held in shared memory (padded by
-// one float2 every 16 to keep the strided passes free of bank conflicts),
-// radix-16 passes while they fit and one smaller pass for the remainder; each
-// thread keeps 16 points in registers per pass.
+// The FFT is a Stockham autosort transform: the first pass reads z straight
+// from global memory, later passes go through shared memory padded by one
+// float2 every 16 (conflict-free strided passes); radix-16 passes plus one
+// smaller first pass, 16 points per thread.  The fine-delay and phase
+// rotation of Eq. 1 is constant within an integration, so the streaming
+// pipeline applies it to the integrated visibilities (finalize_kernel) and
+// fft_kernel stores U = 2Y; the stage entry point can still rotate here.
 #include "corr_internal.h"
+
+#include <cmath>
+#include <vector>
 
 
 namespace corr {
@@ -98,241 +105,466 @@ struct StoreBitrev {
     }
 };
 
-// One Stockham pass of radix R over the padded shared buffer z (M points):
-// butterfly j reads z[j + r M/R], multiplies by W_{Ns R}^{r (j mod Ns)},
-// transforms, and writes z[(j - j mod Ns) R + j mod Ns + r Ns].  Each of the
-// M/16 active threads owns 16/R butterflies (16 points).
-template <int M, int R, int NS>
-__device__ __forceinline__ void stockham_pass(float2* z, const float2* __restrict__ tw, int tid) {
-    constexpr int B = 16 / R;
-    constexpr int NACT = M / 16;
-    constexpr int NR = M / R;
-    constexpr int TSTEP = M / (NS * R);
-    float2 v[16];
-    const bool act = tid < NACT;
-    if (act) {
-        if constexpr (M >= 256) {
-            // tid + b NACT + r NR with both strides multiples of 16.
-            const int pb = pidx(tid);
-#pragma unroll
-            for (int b = 0; b < B; ++b)
-#pragma unroll
-                for (int r = 0; r < R; ++r) v[b * R + r] = z[pb + (b * NACT + r * NR) / 16 * 17];
-        } else {
-#pragma unroll
-            for (int b = 0; b < B; ++b)
-#pragma unroll
-                for (int r = 0; r < R; ++r) v[b * R + r] = z[pidx(tid + b * NACT + r * NR)];
-        }
-    }
-    __syncthreads();
-    if (act) {
-#pragma unroll
-        for (int b = 0; b < B; ++b) {
-            const int j = tid + b * NACT;
-            const int k = j & (NS - 1);
-            float2 u[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) u[r] = v[b * R + r];
-            if constexpr (NS > 1) {
-#pragma unroll
-                for (int r = 1; r < R; ++r) u[r] = cmul(u[r], __ldg(tw + r * k * TSTEP));
-            }
-            dft_dif<R>(u);
-            const int o = (j - k) * R + k;
-            StoreBitrev<R, NS, 0>::run(z, u, o, pidx(o));
-        }
-    }
-    __syncthreads();
-}
-
+// One Stockham pass of radix R over M points: butterfly j reads
+// x[j + r M/R], multiplies by W_{Ns R}^{r (j mod Ns)}, transforms, and
+// writes z[(j - j mod Ns) R + j mod Ns + r Ns] (padded shared buffer).  Each
+// of the M/16 active threads owns 16 / R butterflies (16 points).  With
+// GLOBAL_IN the inputs come from the unpadded global array `gin`.
 __host__ __device__ constexpr int first_radix(int M) {
     int l = 0;
     while ((1 << l) < M) ++l;
     return (l % 4) == 0 ? 16 : (1 << (l % 4));
 }
 
-// Passes: one small-radix pass (radix M / 16^n) at Ns = 1 if needed, then
-// radix-16 passes.
-template <int M, int NS>
-__device__ __forceinline__ void fft_passes(float2* z, const float2* __restrict__ tw, int tid) {
-    if constexpr (NS < M) {
-        constexpr int R = NS == 1 ? first_radix(M) : 16;
-        stockham_pass<M, R, NS>(z, tw, tid);
-        fft_passes<M, NS * R>(z, tw, tid);
+// Offset of the radix-16 pass with stride NS in the twiddle table: the sum
+// of 16 * Ns' over the earlier radix-16 passes.
+__host__ __device__ constexpr int tw_offset(int M, int NS) {
+    int off = 0;
+    int ns = first_radix(M) == 16 ? 1 : first_radix(M);
+    if (first_radix(M) == 16 && NS == 1) return 0;
+    if (first_radix(M) == 16) {
+        off += 16 * 1;
+        ns = 16;
+    }
+    while (ns < NS) {
+        off += 16 * ns;
+        ns *= 16;
+    }
+    return off;
+}
+
+// Twiddle sources of a Stockham pass.
+enum { TW_NONE = 0, TW_SMEM = 1, TW_REG = 2, TW_GLOBAL = 3 };
+
+// Butterflies of one Stockham pass of radix R on the 16 points v a thread
+// holds: butterfly j = tid + b NACT multiplies input r by W_{16 Ns}^{r k}
+// (k = j mod Ns), transforms, and writes z[(j - k) R + k + q Ns] (padded).
+// Twiddles come from the shared table `tws` ([r][k], offset TWO) or, for
+// the last pass, from the thread's registers `twr` (k = tid there).
+template <int M, int R, int NS, int TWM>
+__device__ __forceinline__ void pass_compute_store(float2* z, const float2 (&v)[16], const float2* tws,
+                                                   const float2 (&twr)[15], int tid,
+                                                   const float2* __restrict__ gtw = nullptr) {
+    constexpr int B = 16 / R;
+    constexpr int NACT = M / 16;
+    constexpr int TWO = tw_offset(M, NS);
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int j = tid + b * NACT;
+        const int k = j & (NS - 1);
+        float2 u[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) u[r] = v[b * R + r];
+        if constexpr (TWM == TW_SMEM) {
+            static_assert(R == 16, "twiddled passes are radix 16");
+#pragma unroll
+            for (int r = 1; r < R; ++r) u[r] = cmul(u[r], tws[TWO + r * NS + k]);
+        } else if constexpr (TWM == TW_REG) {
+            static_assert(R == 16 && B == 1, "register twiddles: last radix-16 pass");
+#pragma unroll
+            for (int r = 1; r < R; ++r) u[r] = cmul(u[r], twr[r - 1]);
+        } else if constexpr (TWM == TW_GLOBAL) {
+            static_assert(R == 16, "twiddled passes are radix 16");
+#pragma unroll
+            for (int r = 1; r < R; ++r) u[r] = cmul(u[r], __ldg(gtw + TWO + r * NS + k));
+        }
+        dft_dif<R>(u);
+        const int o = (j - k) * R + k;
+        StoreBitrev<R, NS, 0>::run(z, u, o, pidx(o));
     }
 }
 
-// Sixteen consecutive int8 samples of one input starting at stream index n0,
-// returned as four little-endian words; zero outside the valid window.
-__device__ __forceinline__ void load16(const StreamView& sv, int a, long long n0, uint32_t w[4]) {
+// First-pass inputs of a thread: x[tid + b NACT + r M/R0] from global memory.
+template <int M>
+__device__ __forceinline__ void load_first(float2 (&v)[16], const float2* __restrict__ gin, int tid) {
+    constexpr int R = first_radix(M);
+    constexpr int B = 16 / R;
+    constexpr int NACT = M / 16;
+    constexpr int NR = M / R;
+    if (tid < NACT) {
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[b * R + r] = __ldg(gin + tid + b * NACT + r * NR);
+    }
+}
+
+// Inputs of a later (radix-16) pass from the padded shared buffer.
+template <int M>
+__device__ __forceinline__ void load_smem(float2 (&v)[16], const float2* z, int tid) {
+    constexpr int NR = M / 16;
+    if constexpr (M >= 256) {
+        // tid + r NR with NR a multiple of 16.
+        const int pb = pidx(tid);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = z[pb + r * NR / 16 * 17];
+    } else {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = z[pidx(tid + r * NR)];
+    }
+}
+
+// Radix-16 passes from shared memory, Ns = NS .. M/16.  The last one takes
+// its twiddles from registers (REGTW) or from the global table, the others
+// from the shared copy of the table.
+template <int M, int NS, bool REGTW>
+__device__ __forceinline__ void later_passes(float2* z, const float2* tws, const float2 (&twr)[15], int tid,
+                                             const float2* __restrict__ gtw) {
+    if constexpr (NS < M) {
+        constexpr bool last = (NS * 16 == M);
+        float2 v[16];
+        if (tid < M / 16) load_smem<M>(v, z, tid);
+        __syncthreads();
+        if (tid < M / 16) {
+            if constexpr (last && REGTW) pass_compute_store<M, 16, NS, TW_REG>(z, v, tws, twr, tid);
+            else if constexpr (last) pass_compute_store<M, 16, NS, TW_GLOBAL>(z, v, tws, twr, tid, gtw);
+            else pass_compute_store<M, 16, NS, TW_SMEM>(z, v, tws, twr, tid);
+        }
+        __syncthreads();
+        later_passes<M, NS * 16, REGTW>(z, tws, twr, tid, gtw);
+    }
+}
+
+// Entries of the twiddle table kept in shared memory: every pass but the
+// last (whose twiddles are in registers or read from global memory).
+template <int M>
+__host__ __device__ constexpr int tw_smem_entries() {
+    return M <= 16 ? 16 : tw_offset(M, M / 16);
+}
+
+// Four consecutive int8 samples of one input from stream index n0 as one
+// little-endian word; zero outside the valid window.
+__device__ __forceinline__ uint32_t load4(const StreamView& sv, int a, long long n0) {
     const long long lo = sv.base > 0 ? sv.base : 0;
     const int8_t* row = sv.x + (long long)a * sv.stride - sv.base;  // stream index 0
     const uintptr_t addr = reinterpret_cast<uintptr_t>(row + n0);
-    const int c = (int)(addr & 15);
-    // Fast path: both aligned 16-byte blocks lie inside the valid window.
-    if (n0 - c >= lo && n0 - c + 32 <= sv.vhi) {
-        const uint4* q = reinterpret_cast<const uint4*>(addr - c);
-        const uint4 A = __ldg(q);
-        uint4 Bv = make_uint4(0, 0, 0, 0);
-        if (c) Bv = __ldg(q + 1);
-        const uint32_t W8[8] = {A.x, A.y, A.z, A.w, Bv.x, Bv.y, Bv.z, Bv.w};
-        const int qw = c >> 2, sh = (c & 3) * 8;
-        // qw is uniform across the CTA (it depends on the input and the
-        // buffer alignment only), so this switch does not diverge.
-        switch (qw) {
-#define CORR_SEL(Q)                                                        \
-    case Q:                                                                \
-        w[0] = __funnelshift_r(W8[Q + 0], W8[Q + 1], sh);                 \
-        w[1] = __funnelshift_r(W8[Q + 1], W8[Q + 2], sh);                 \
-        w[2] = __funnelshift_r(W8[Q + 2], W8[Q + 3], sh);                 \
-        w[3] = __funnelshift_r(W8[Q + 3], W8[Q + 4], sh);                 \
-        break;
-            CORR_SEL(0)
-            CORR_SEL(1)
-            CORR_SEL(2)
-            CORR_SEL(3)
-#undef CORR_SEL
-        }
-        return;
+    const int c = (int)(addr & 3);
+    if (n0 - c >= lo && n0 - c + 8 <= sv.vhi) {
+        const uint32_t* q = reinterpret_cast<const uint32_t*>(addr - c);
+        const uint32_t w0 = __ldg(q);
+        const uint32_t w1 = c ? __ldg(q + 1) : 0u;
+        return __funnelshift_r(w0, w1, 8 * c);
     }
-    // Edge path: byte loads with bounds checks.
+    uint32_t v = 0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        uint32_t v = 0;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const long long n = n0 + i * 4 + b;
-            uint32_t byte = 0;
-            if (n >= lo && n < sv.vhi) byte = (uint8_t)row[n];
-            v |= byte << (8 * b);
-        }
-        w[i] = v;
+    for (int b = 0; b < 4; ++b) {
+        const long long n = n0 + b;
+        if (n >= lo && n < sv.vhi) v |= (uint32_t)(uint8_t)row[n] << (8 * b);
     }
+    return v;
 }
 
 // Exact int8 -> float: flip the sign bit, place the byte in the mantissa of
 // 2^23, subtract 2^23 + 128.
-__device__ __forceinline__ float b2f(uint32_t wflip, int sel) {
-    return __int_as_float((int)__byte_perm(wflip, 0x4B000000u, sel)) - 8388736.0f;
+__device__ __forceinline__ void unpack4(uint32_t w, float (&x)[4]) {
+    const uint32_t f = w ^ 0x80808080u;
+    x[0] = __int_as_float((int)__byte_perm(f, 0x4B000000u, 0x7440)) - 8388736.0f;
+    x[1] = __int_as_float((int)__byte_perm(f, 0x4B000000u, 0x7441)) - 8388736.0f;
+    x[2] = __int_as_float((int)__byte_perm(f, 0x4B000000u, 0x7442)) - 8388736.0f;
+    x[3] = __int_as_float((int)__byte_perm(f, 0x4B000000u, 0x7443)) - 8388736.0f;
 }
 
-__device__ __forceinline__ void fir_accum(float* y, const uint32_t w[4], const float* hv) {
+constexpr int kFirThreads = 256;
+
+// Per-input state of one FIR thread: an aligned word pointer at frame 0 for
+// branches m0..m0+3 shifted by the coarse delay, the byte offset inside the
+// word, and the frames [f_lo, f_hi] whose two words lie inside the valid
+// window (no bounds checks needed there).
+struct FirInput {
+    const uint32_t* q;
+    int sh;
+    long long f_lo, f_hi;
+    long long n0;             // stream index of branch m0 at frame 0 (with delay)
+    int in;
+    bool has;
+};
+
+__device__ __forceinline__ FirInput fir_input(const FirArgs& A, int in, bool has, int m0, int d) {
+    FirInput r;
+    r.in = in;
+    r.has = has;
+    r.n0 = (long long)m0 + d;
+    const long long lo = A.src.base > 0 ? A.src.base : 0;
+    const int8_t* p0 = A.src.x + (long long)in * A.src.stride - A.src.base + r.n0;   // frame 0
+    const int c = (int)(reinterpret_cast<uintptr_t>(p0) & 3);
+    r.q = reinterpret_cast<const uint32_t*>(p0 - c);
+    r.sh = 8 * c;
+    // frame f is safe when n0 + f M - c >= lo and n0 + f M - c + 8 <= vhi;
+    // M = 2^lgM, so ceil / floor division are arithmetic shifts.
+    const long long a_lo = lo - r.n0 + c;
+    const long long a_hi = A.src.vhi - 8 - r.n0 + c;
+    r.f_lo = (a_lo + A.M - 1) >> A.lgM;
+    r.f_hi = a_hi >> A.lgM;
+    if (!has) {
+        r.f_lo = -(1LL << 62);
+        r.f_hi = 1LL << 62;
+    }
+    return r;
+}
+
+// Raw int8 word (4 branches) of frame f of one input; zero before the stream.
+__device__ __forceinline__ uint32_t fir_word(const FirArgs& A, const FirInput& I, long long f) {
+    uint32_t w = 0u;
+    if (I.has && f >= 0) {
+        if (f >= I.f_lo && f <= I.f_hi) {
+            const uint32_t* q = I.q + (f << (A.lgM - 2));
+            w = __funnelshift_r(__ldg(q), __ldg(q + 1), I.sh);
+        } else {
+            w = load4(A.src, I.in, f * A.M + I.n0);
+        }
+    }
+    return w;
+}
+
+__device__ __forceinline__ void fir_frame(const FirArgs& A, const FirInput& I, long long f, float (&x)[4]) {
+    unpack4(fir_word(A, I, f), x);
+}
+
+// y_s[m] = sum_p h[pM + m] x'[(s - P + 1 + p) M + m] for 4 branches of both
+// inputs of a pair, over spectra [s_lo, s_hi).  The window holds frames
+// s-P+1 .. s in a circular register array indexed at compile time: spectra
+// are processed in steps of P so frame f always sits in slot (f - base) mod P.
+template <int P>
+__global__ void __launch_bounds__(kFirThreads, P <= 4 ? 3 : 1) fir_kernel(const FirArgs A) {
+    const int M = A.M;
+    const int g = blockIdx.x * kFirThreads + threadIdx.x;
+    if (g >= (M >> 2)) return;
+    const int m0 = 4 * g;
+    const int pair = blockIdx.y;
+    const int a = 2 * pair, b = a + 1;
+    const long long s_lo = A.s_begin + (long long)blockIdx.z * A.spt;
+    long long s_hi = s_lo + A.spt;
+    if (s_hi > A.s_end) s_hi = A.s_end;
+    if (s_lo >= s_hi) return;
+    const FirInput Ia = fir_input(A, a, a < A.n_in, m0, A.coarse[a]);
+    const FirInput Ib = fir_input(A, b, b < A.n_in, m0, A.coarse[b]);
+
+    float hr[P][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const uint32_t f = w[i] ^ 0x80808080u;
-        y[4 * i + 0] = fmaf(hv[4 * i + 0], b2f(f, 0x7440), y[4 * i + 0]);
-        y[4 * i + 1] = fmaf(hv[4 * i + 1], b2f(f, 0x7441), y[4 * i + 1]);
-        y[4 * i + 2] = fmaf(hv[4 * i + 2], b2f(f, 0x7442), y[4 * i + 2]);
-        y[4 * i + 3] = fmaf(hv[4 * i + 3], b2f(f, 0x7443), y[4 * i + 3]);
+    for (int p = 0; p < P; ++p) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(A.h + (size_t)p * M + m0));
+        hr[p][0] = t.x; hr[p][1] = t.y; hr[p][2] = t.z; hr[p][3] = t.w;
+    }
+    float wa[P][4], wb[P][4];
+    const long long base_f = s_lo - (P - 1);
+#pragma unroll
+    for (int q = 0; q < P - 1; ++q) {
+        fir_frame(A, Ia, base_f + q, wa[q]);
+        fir_frame(A, Ib, base_f + q, wb[q]);
+    }
+    float2* zp = A.Z + (size_t)pair * M + m0;
+    const size_t zstride = (size_t)A.n_pairs * M;
+    long long f_safe_lo = Ia.f_lo > Ib.f_lo ? Ia.f_lo : Ib.f_lo;
+    long long f_safe_hi = Ia.f_hi < Ib.f_hi ? Ia.f_hi : Ib.f_hi;
+    if (f_safe_lo < 0) f_safe_lo = 0;
+    for (long long s0 = s_lo; s0 < s_hi; s0 += P) {
+        // Issue the loads of the block's P new frames first (independent of
+        // the arithmetic below), then consume them.  Inside the safe frame
+        // range of both inputs no bounds checks are needed.
+        uint32_t ra[P], rb[P];
+        if (s0 >= f_safe_lo && s0 + P - 1 <= f_safe_hi && s0 + P <= s_hi) {
+            const uint32_t* qa = Ia.q + (s0 << (A.lgM - 2));
+            const uint32_t* qb = Ib.q + (s0 << (A.lgM - 2));
+            const int step = M >> 2;
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                ra[q] = Ia.has ? __funnelshift_r(__ldg(qa + q * step), __ldg(qa + q * step + 1), Ia.sh) : 0u;
+                rb[q] = Ib.has ? __funnelshift_r(__ldg(qb + q * step), __ldg(qb + q * step + 1), Ib.sh) : 0u;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const long long s = s0 + q;
+                ra[q] = s < s_hi ? fir_word(A, Ia, s) : 0u;
+                rb[q] = s < s_hi ? fir_word(A, Ib, s) : 0u;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const long long s = s0 + q;
+            if (s < s_hi) {
+                const int slot_new = (q + P - 1) % P;      // frame s
+                unpack4(ra[q], wa[slot_new]);
+                unpack4(rb[q], wb[slot_new]);
+                float ya[4] = {0.f, 0.f, 0.f, 0.f}, yb[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    const int sl = (q + p) % P;            // frame s - P + 1 + p
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        ya[i] = fmaf(hr[p][i], wa[sl][i], ya[i]);
+                        yb[i] = fmaf(hr[p][i], wb[sl][i], yb[i]);
+                    }
+                }
+                const long long zs = (s - A.z_origin) & A.z_mask;
+                float4* o = reinterpret_cast<float4*>(zp + (size_t)zs * zstride);
+                o[0] = make_float4(ya[0], yb[0], ya[1], yb[1]);
+                o[1] = make_float4(ya[2], yb[2], ya[3], yb[3]);
+            }
+        }
     }
 }
 
 template <int M>
-__global__ void __launch_bounds__(M / 16 < 32 ? 32 : M / 16) fengine_kernel(const FArgs A) {
-    extern __shared__ float2 zbuf[];
+struct FftCfg {
+    static constexpr int NACT = M / 16;
+    static constexpr int THREADS = NACT < 32 ? 32 : NACT;
+    // With at most 512 threads the last pass's 15 twiddles (fixed per thread)
+    // stay in registers and the next spectrum's first-pass input is
+    // prefetched; one CTA per SM then has up to 128 registers per thread.
+    static constexpr bool REGTW = (M >= 32) && NACT <= 512;
+    static constexpr int TWS = tw_smem_entries<M>();
+    static constexpr size_t SMEM = sizeof(float2) * (size_t)(M + M / 16 + 1 + TWS);
+};
+
+template <int M>
+__device__ __forceinline__ const float2* fft_input(const FftArgs& A, long long s, int pair, int n_pairs) {
+    const long long zs = (s - A.z_origin) & A.z_mask;
+    return A.Z + ((size_t)zs * n_pairs + pair) * M;
+}
+
+template <int M, bool ROT>
+__global__ void __launch_bounds__(FftCfg<M>::THREADS, 1) fft_kernel(const FftArgs A) {
+    using C = FftCfg<M>;
+    extern __shared__ float2 smem[];
+    float2* zbuf = smem;
+    float2* tws = smem + (M + M / 16 + 1);
     const int tid = threadIdx.x;
     constexpr int n_chan = M >> 1;
-    constexpr int nact = M >> 4;
-    const int a = 2 * blockIdx.y, b = a + 1;
-    const bool has_a = a < A.n_in, has_b = b < A.n_in;
-    const int da = A.coarse[a], db = A.coarse[b];
+    constexpr int R0 = first_radix(M);
+    const int pair = blockIdx.y;
+    const int n_pairs = gridDim.y;
+    const int a = 2 * pair;
     const long long s_lo = A.s_begin + (long long)blockIdx.x * A.spt;
     long long s_hi = s_lo + A.spt;
     if (s_hi > A.s_end) s_hi = A.s_end;
+    if (s_lo >= s_hi) return;
 
-    for (long long s = s_lo; s < s_hi; ++s) {
-        // ---- polyphase FIR, 16 consecutive branches per thread, one input
-        //      of the pair at a time (re part: input a, im part: input b) ----
-        if (tid < nact) {
-            const int m0 = tid * 16;
-            float* zf = reinterpret_cast<float*>(zbuf);
-#pragma unroll 1
-            for (int half = 0; half < 2; ++half) {
-                const int in = half ? b : a;
-                const bool has = half ? has_b : has_a;
-                const int d = half ? db : da;
-                float y[16];
+    for (int i = tid; i < C::TWS; i += blockDim.x) tws[i] = __ldg(A.tw + i);
+    float2 twr[15];
+    if constexpr (C::REGTW) {
+        constexpr int NSL = M / 16;
+        constexpr int TWL = tw_offset(M, NSL);
+        if (tid < C::NACT) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) y[i] = 0.f;
-                if (has) {
-                    for (int p = 0; p < A.taps; ++p) {
-                        const long long f = s - A.taps + 1 + p;
-                        if (f < 0) continue;
-                        uint32_t w[4];
-                        load16(A.src, in, f * M + m0 + d, w);
-                        float hv[16];
-                        const float4* hp = reinterpret_cast<const float4*>(A.h + (size_t)p * M + m0);
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const float4 t = __ldg(hp + i);
-                            hv[4 * i] = t.x; hv[4 * i + 1] = t.y; hv[4 * i + 2] = t.z; hv[4 * i + 3] = t.w;
-                        }
-                        fir_accum(y, w, hv);
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < 16; ++i) zf[2 * pidx(m0 + i) + half] = y[i];
-            }
+            for (int r = 1; r < 16; ++r) twr[r - 1] = __ldg(A.tw + TWL + r * NSL + tid);
         }
+    }
+    __syncthreads();
+
+    float2 cur[16];
+    load_first<M>(cur, fft_input<M>(A, s_lo, pair, n_pairs), tid);
+    for (long long s = s_lo; s < s_hi; ++s) {
+        float2 nxt[16];
+        if constexpr (C::REGTW) {
+            if (s + 1 < s_hi) load_first<M>(nxt, fft_input<M>(A, s + 1, pair, n_pairs), tid);
+        }
+        // first pass (Ns = 1, no twiddles) straight from the global input
+        if (tid < C::NACT) pass_compute_store<M, R0, 1, TW_NONE>(zbuf, cur, tws, twr, tid);
         __syncthreads();
-        fft_passes<M, 1>(zbuf, A.tw, tid);
-        // ---- unpack the two real spectra, rotate, store V[slot][k][a..a+1] ----
-        long long slot = (s - A.v_origin) % A.v_cap;
-        if (slot < 0) slot += A.v_cap;
+        later_passes<M, R0, C::REGTW>(zbuf, tws, twr, tid, A.tw);
+        const long long slot = (s - A.v_origin) & A.v_mask;
         float4* Vout = reinterpret_cast<float4*>(A.V + (size_t)slot * n_chan * A.n_in_pad + a);
-        const float2* pa = A.phasor + (size_t)a * n_chan;
-        const float2* pb = A.phasor + (size_t)b * n_chan;
         for (int k = tid; k < n_chan; k += blockDim.x) {
             const float2 zk = zbuf[pidx(k)];
             const float2 zm = zbuf[pidx((M - k) & (M - 1))];
             const float2 S = make_float2(zk.x + zm.x, zk.y - zm.y);
             const float2 D = make_float2(zk.x - zm.x, zk.y + zm.y);
-            const float2 va = cmul(S, __ldg(pa + k));
-            const float2 vb = cmul(D, __ldg(pb + k));
-            Vout[(size_t)k * (A.n_in_pad >> 1)] = make_float4(va.x, va.y, vb.x, vb.y);
+            float4 out;
+            if constexpr (ROT) {
+                const float2 va = cmul(S, __ldg(A.phasor + (size_t)a * n_chan + k));
+                const float2 vb = cmul(D, __ldg(A.phasor + (size_t)(a + 1) * n_chan + k));
+                out = make_float4(va.x, va.y, vb.x, vb.y);
+            } else {
+                out = make_float4(S.x, S.y, D.y, -D.x);
+            }
+            Vout[(size_t)k * (A.n_in_pad >> 1)] = out;
         }
         __syncthreads();
+        if constexpr (C::REGTW) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) cur[i] = nxt[i];
+        } else {
+            if (s + 1 < s_hi) load_first<M>(cur, fft_input<M>(A, s + 1, pair, n_pairs), tid);
+        }
     }
 }
 
 }  // namespace
 
-int fengine_threads(int M) {
-    int nt = M / 16;
-    if (nt < 32) nt = 32;
-    return nt;
+std::vector<float2> fft_twiddle_table(int M) {
+    const double pi = 3.14159265358979323846;
+    std::vector<float2> t;
+    int ns = first_radix(M) == 16 ? 1 : first_radix(M);
+    if (first_radix(M) == 16) {
+        t.resize(16, make_float2(1.f, 0.f));   // first pass at Ns = 1 (unused)
+        ns = 16;
+    }
+    while (ns < M) {
+        for (int r = 0; r < 16; ++r)
+            for (int k = 0; k < ns; ++k) {
+                const double ang = -2.0 * pi * (double)r * k / (16.0 * ns);
+                t.push_back(make_float2((float)std::cos(ang), (float)std::sin(ang)));
+            }
+        ns *= 16;
+    }
+    return t;
 }
 
-size_t fengine_smem_bytes(int M) { return sizeof(float2) * (size_t)(M + M / 16 + 1); }
-
-template <int M>
-static void launch_m(const FArgs& a, dim3 grid, cudaStream_t st) {
+template <int M, bool ROT>
+static void launch_fft_m(const FftArgs& a, cudaStream_t st) {
     static bool attr_set = false;
-    const size_t smem = fengine_smem_bytes(M);
+    const size_t smem = FftCfg<M>::SMEM;
     if (!attr_set) {
-        cudaFuncSetAttribute(fengine_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(fft_kernel<M, ROT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_set = true;
     }
-    fengine_kernel<M><<<grid, fengine_threads(M), smem, st>>>(a);
+    // One CTA per SM, each looping over a run of spectra of one pair.
+    const long long n = a.s_end - a.s_begin;
+    const int n_pairs = a.n_in_pad / 2;
+    long long runs = (152LL + n_pairs - 1) / n_pairs;
+    if (runs > n) runs = n;
+    if (runs < 1) runs = 1;
+    FftArgs b = a;
+    b.spt = (int)((n + runs - 1) / runs);
+    dim3 grid((unsigned)((n + b.spt - 1) / b.spt), (unsigned)n_pairs);
+    fft_kernel<M, ROT><<<grid, FftCfg<M>::THREADS, smem, st>>>(b);
 }
 
-void launch_fengine(const FArgs& a, cudaStream_t st) {
+template <bool ROT>
+static void launch_fft_rot(const FftArgs& a, cudaStream_t st) {
+    switch (a.M) {
+        case 16: launch_fft_m<16, ROT>(a, st); break;
+        case 32: launch_fft_m<32, ROT>(a, st); break;
+        case 64: launch_fft_m<64, ROT>(a, st); break;
+        case 128: launch_fft_m<128, ROT>(a, st); break;
+        case 256: launch_fft_m<256, ROT>(a, st); break;
+        case 512: launch_fft_m<512, ROT>(a, st); break;
+        case 1024: launch_fft_m<1024, ROT>(a, st); break;
+        case 2048: launch_fft_m<2048, ROT>(a, st); break;
+        case 4096: launch_fft_m<4096, ROT>(a, st); break;
+        case 8192: launch_fft_m<8192, ROT>(a, st); break;
+        case 16384: launch_fft_m<16384, ROT>(a, st); break;
+        default: break;
+    }
+}
+
+void launch_fft(const FftArgs& a, cudaStream_t st) {
+    if (a.s_end <= a.s_begin) return;
+    if (a.phasor) launch_fft_rot<true>(a, st);
+    else launch_fft_rot<false>(a, st);
+}
+
+void launch_fir(const FirArgs& a, cudaStream_t st) {
     const long long n = a.s_end - a.s_begin;
     if (n <= 0) return;
-    dim3 grid((unsigned)((n + a.spt - 1) / a.spt), (unsigned)(a.n_in_pad / 2));
-    switch (a.M) {
-        case 16: launch_m<16>(a, grid, st); break;
-        case 32: launch_m<32>(a, grid, st); break;
-        case 64: launch_m<64>(a, grid, st); break;
-        case 128: launch_m<128>(a, grid, st); break;
-        case 256: launch_m<256>(a, grid, st); break;
-        case 512: launch_m<512>(a, grid, st); break;
-        case 1024: launch_m<1024>(a, grid, st); break;
-        case 2048: launch_m<2048>(a, grid, st); break;
-        case 4096: launch_m<4096>(a, grid, st); break;
-        case 8192: launch_m<8192>(a, grid, st); break;
-        case 16384: launch_m<16384>(a, grid, st); break;
+    dim3 grid((unsigned)((a.M / 4 + kFirThreads - 1) / kFirThreads), (unsigned)a.n_pairs,
+              (unsigned)((n + a.spt - 1) / a.spt));
+    switch (a.taps) {
+#define CORR_FIR(P) case P: fir_kernel<P><<<grid, kFirThreads, 0, st>>>(a); break;
+        CORR_FIR(1) CORR_FIR(2) CORR_FIR(3) CORR_FIR(4) CORR_FIR(5) CORR_FIR(6) CORR_FIR(7) CORR_FIR(8)
+        CORR_FIR(9) CORR_FIR(10) CORR_FIR(11) CORR_FIR(12) CORR_FIR(13) CORR_FIR(14) CORR_FIR(15) CORR_FIR(16)
+#undef CORR_FIR
         default: break;
     }
 }

@@ -82,7 +82,7 @@ extern "C" int corr_xengine_noalloc(const float* d_V, int n_spec, int n_in, int 
     corr::XArgs x{};
     x.V = reinterpret_cast<const float2*>(d_V);
     x.v_origin = 0;
-    x.v_cap = n_spec;
+    x.v_mask = -1LL;
     x.n_chan = n_chan;
     x.n_in_pad = n_in_pad;
     x.nt = nt;

@@ -27,6 +27,7 @@ struct Pipe {
     long long s_next = 0;     // next spectrum to channelise
     long long s_xdone = 0;    // first spectrum not yet summed into a partial slot
     float2* V = nullptr;      // ring of channelised spectra
+    float2* Z = nullptr;      // ring of FIR outputs (same capacity)
     int v_cap = 0;
     float* part = nullptr;    // [gpi][nt][32][n_chan]
 };
@@ -41,20 +42,21 @@ struct Slot {
 };
 
 struct Tables {
-    float2* phasor = nullptr;   // [n_in_pad][n_chan]
+    float2* phasor = nullptr;   // [n_in_pad][n_chan] with the pair factors 1/2, 1/2j
+    float2* rot = nullptr;      // [n_in_pad][n_chan] exp(j(2 pi k r/M - phi))
     int* coarse = nullptr;      // [n_in_pad]
     int d_max = 0;              // largest coarse advance
 };
 
 // Optional CUDA-event brackets around every kernel launch, per stage
-// (0 F-engine, 1 X-engine, 2 finalise, 3 flag).
-constexpr int kStages = 4;
+// (0 FIR, 1 FFT, 2 X-engine, 3 finalise, 4 flag).
+constexpr int kStages = 5;
 struct StageTimer {
     bool on = false;
     std::vector<cudaEvent_t> pool;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> open[kStages];
-    double ms[kStages] = {0, 0, 0, 0};
-    long long n[kStages] = {0, 0, 0, 0};
+    double ms[kStages] = {};
+    long long n[kStages] = {};
     cudaEvent_t take() {
         if (!pool.empty()) {
             cudaEvent_t e = pool.back();
@@ -116,6 +118,8 @@ struct corr_s {
     Pipe pd;                 // whole-stream device pipe
     float* d_part_x = nullptr;   // scratch of corr_xengine_dev
     long long part_x_slots = 0;
+    float2* d_z_f = nullptr;     // scratch of corr_fengine_dev
+    long long z_f_spectra = 0;
     std::vector<Slot> slots;
     std::deque<int> q_vis, q_flag;
     std::string err;
@@ -189,6 +193,7 @@ int upload_tables(corr_t h, Tables& t, const std::vector<double>& tau, const std
                   cudaStream_t st) {
     const double pi = 3.14159265358979323846;
     std::vector<float2> ph((size_t)h->n_in_pad * h->n_chan, make_float2(0.f, 0.f));
+    std::vector<float2> rt((size_t)h->n_in_pad * h->n_chan, make_float2(0.f, 0.f));
     std::vector<int> co(h->n_in_pad, 0);
     int dmax = -(1 << 30);
     for (int a = 0; a < h->n_in; ++a) {
@@ -200,6 +205,7 @@ int upload_tables(corr_t h, Tables& t, const std::vector<double>& tau, const std
         const bool odd = (a & 1) != 0;
         for (int k = 0; k < h->n_chan; ++k) {
             const double ang = 2.0 * pi * k * r / (double)h->M - phi[a];
+            rt[(size_t)a * h->n_chan + k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
             double re = 0.5 * std::cos(ang), im = 0.5 * std::sin(ang);
             if (odd) {
                 const double t2 = re;
@@ -211,6 +217,7 @@ int upload_tables(corr_t h, Tables& t, const std::vector<double>& tau, const std
     }
     t.d_max = dmax;
     CK(cudaMemcpyAsync(t.phasor, ph.data(), ph.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(t.rot, rt.data(), rt.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(t.coarse, co.data(), co.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
     return CORR_OK;
@@ -218,6 +225,7 @@ int upload_tables(corr_t h, Tables& t, const std::vector<double>& tau, const std
 
 int alloc_tables(corr_t h, Tables& t) {
     CK(cudaMalloc(&t.phasor, sizeof(float2) * (size_t)h->n_in_pad * h->n_chan));
+    CK(cudaMalloc(&t.rot, sizeof(float2) * (size_t)h->n_in_pad * h->n_chan));
     CK(cudaMalloc(&t.coarse, sizeof(int) * (size_t)h->n_in_pad));
     return CORR_OK;
 }
@@ -230,40 +238,75 @@ int choose_spt(long long n_spec, int n_pairs) {
     return (int)spt;
 }
 
+// Spectra per FIR thread: long runs amortise the P-1 frames of warm-up,
+// but keep at least ~2 waves of CTAs on 152 SMs.
+int choose_fir_spt(long long n_spec, int n_pairs, int M, int taps) {
+    const long long ctas_per_run = (long long)((M / 4 + 255) / 256) * n_pairs;
+    long long spt = 16;
+    while (spt > 1 && ((n_spec + spt - 1) / spt) * ctas_per_run < 3 * 152) spt /= 2;
+    if (spt < 1) spt = 1;
+    (void)taps;
+    return (int)spt;
+}
+
 int alloc_pipe(corr_t h, Pipe& p) {
     if (p.V) return CORR_OK;
+    // Power-of-two rings of about 32 MiB each, so that the FIR output and the
+    // channelised spectra both stay in L2 between the kernels.
     const size_t per_spec = (size_t)h->n_chan * h->n_in_pad * sizeof(float2);
-    long long cap = (long long)((32ull << 20) / per_spec);
-    if (cap > 4096) cap = 4096;
-    if (cap < h->G) cap = h->G;
-    cap = (cap / h->G) * h->G;
+    long long cap = 1;
+    while (cap * 2 * per_spec <= (32ull << 20) && cap < 4096) cap *= 2;
+    while (cap < h->G) cap *= 2;
     p.v_cap = (int)cap;
     CK(cudaMalloc(&p.V, per_spec * (size_t)p.v_cap));
+    CK(cudaMalloc(&p.Z, per_spec * (size_t)p.v_cap));
     CK(cudaMalloc(&p.part, sizeof(float) * (size_t)h->gpi * h->nt * 32 * h->n_chan));
     return CORR_OK;
 }
 
-int launch_f(corr_t h, const StreamView& sv, const Tables& t, Pipe& p, long long s_begin, long long s_end,
-             cudaStream_t st) {
-    FArgs a{};
+// F-engine over spectra [s_begin, s_end): FIR into the Z ring, FFT into the
+// V ring.  `phasor` set -> rotated V (stage call); else U = 2Y (pipeline).
+int launch_f(corr_t h, const StreamView& sv, const Tables& t, float2* Z, long long z_origin, long long z_mask,
+             float2* V, long long v_origin, long long v_mask, const float2* phasor, long long s_begin,
+             long long s_end, cudaStream_t st) {
+    FirArgs a{};
     a.src = sv;
     a.h = h->d_h;
-    a.tw = h->d_tw;
-    a.phasor = t.phasor;
     a.coarse = t.coarse;
-    a.V = p.V;
+    a.Z = Z;
+    a.z_origin = z_origin;
+    a.z_mask = z_mask;
     a.s_begin = s_begin;
     a.s_end = s_end;
-    a.v_origin = 0;
-    a.v_cap = p.v_cap;
     a.n_in = h->n_in;
-    a.n_in_pad = h->n_in_pad;
+    a.n_pairs = h->n_in_pad / 2;
     a.M = h->M;
+    a.lgM = 0;
+    while ((1 << a.lgM) < h->M) ++a.lgM;
     a.taps = h->taps;
-    a.spt = choose_spt(s_end - s_begin, h->n_in_pad / 2);
+    a.spt = choose_fir_spt(s_end - s_begin, a.n_pairs, h->M, h->taps);
     {
         Timed t_(h, 0, st);
-        launch_fengine(a, st);
+        launch_fir(a, st);
+    }
+    CK(cudaGetLastError());
+    FftArgs f{};
+    f.Z = Z;
+    f.z_origin = z_origin;
+    f.z_mask = z_mask;
+    f.tw = h->d_tw;
+    f.phasor = phasor;
+    f.V = V;
+    f.v_origin = v_origin;
+    f.v_mask = v_mask;
+    f.s_begin = s_begin;
+    f.s_end = s_end;
+    f.n_in_pad = h->n_in_pad;
+    f.M = h->M;
+    f.spt = choose_spt(s_end - s_begin, h->n_in_pad / 2);
+    {
+        Timed t_(h, 1, st);
+        launch_fft(f, st);
     }
     CK(cudaGetLastError());
     return CORR_OK;
@@ -276,7 +319,8 @@ long long ready_spectra(corr_t h, bool final) {
     return r / h->M;
 }
 
-using Sink = int (*)(corr_t, void*, long long /*integration*/, int /*count*/, int /*slots*/, cudaStream_t);
+using Sink = int (*)(corr_t, void*, const Tables&, long long /*integration*/, int /*count*/, int /*slots*/,
+                     cudaStream_t);
 
 // Drive F -> X -> finalise over every spectrum below ready_end.  When
 // `final` is set, the stream has ended: a last partial group / integration
@@ -297,7 +341,7 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
         if (s_end > iend) s_end = iend;
         if (s_end > p.s_xdone + p.v_cap) s_end = p.s_xdone + p.v_cap;
         if (s_end > p.s_next) {
-            CKRET(launch_f(h, sv, t, p, p.s_next, s_end, st));
+            CKRET(launch_f(h, sv, t, p.Z, 0, p.v_cap - 1, p.V, 0, p.v_cap - 1, nullptr, p.s_next, s_end, st));
             p.s_next = s_end;
             progress = true;
         }
@@ -313,7 +357,7 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
             XArgs x{};
             x.V = p.V;
             x.v_origin = 0;
-            x.v_cap = p.v_cap;
+            x.v_mask = p.v_cap - 1;
             x.n_chan = h->n_chan;
             x.n_in_pad = h->n_in_pad;
             x.nt = h->nt;
@@ -325,7 +369,7 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
             x.n_groups = j_end - j_begin;
             x.part = p.part;
             {
-                Timed t_(h, 1, st);
+                Timed t_(h, 2, st);
                 launch_xengine(x, st);
             }
             CK(cudaGetLastError());
@@ -335,12 +379,12 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
             progress = true;
         }
         if (p.s_next == iend && p.s_xdone == iend) {
-            CKRET(sink(h, ctx, i, (int)n_int, h->gpi, st));
+            CKRET(sink(h, ctx, t, i, (int)n_int, h->gpi, st));
             progress = true;
             continue;
         }
         if (closing && p.s_xdone == p.s_next && p.s_next > istart) {
-            CKRET(sink(h, ctx, i, (int)(p.s_next - istart), j_end, st));
+            CKRET(sink(h, ctx, t, i, (int)(p.s_next - istart), j_end, st));
             // The partial integration is closed; nothing further can follow.
             p.s_xdone = p.s_next = iend;
             return CORR_OK;
@@ -349,24 +393,28 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
     }
 }
 
-int finalize_into(corr_t h, const Pipe& p, float2* R, uint8_t* F, int count, int slots, cudaStream_t st) {
+// The pipeline's spectra are U = 2Y without the fine-delay/phase rotation,
+// so R = Q_a conj(Q_b) sum U_a U_b^* / (4 count).
+int finalize_into(corr_t h, const Pipe& p, const Tables& t, float2* R, uint8_t* F, int count, int slots,
+                  cudaStream_t st) {
     FinArgs f{};
     f.part = p.part;
+    f.rot = t.rot;
     f.n_slots = slots;
     f.nt = h->nt;
     f.n_chan = h->n_chan;
     f.n_in = h->n_in;
-    f.scale = 1.0f / (float)count;
+    f.scale = 0.25f / (float)count;
     f.R = R;
     {
-        Timed t_(h, 2, st);
+        Timed t_(h, 3, st);
         launch_finalize(f, st);
     }
     CK(cudaGetLastError());
     if (F) {
         const int w = h->flag_window < h->n_chan ? h->flag_window : h->n_chan;
         {
-            Timed t_(h, 3, st);
+            Timed t_(h, 4, st);
             launch_mad_flags(R, F, 1, h->n_chan, h->n_in, w, (float)h->flag_sigma, st);
         }
         CK(cudaGetLastError());
@@ -398,11 +446,11 @@ int new_slot(corr_t h, int* idx) {
     return CORR_OK;
 }
 
-int sink_stream(corr_t h, void*, long long, int count, int slots, cudaStream_t st) {
+int sink_stream(corr_t h, void*, const Tables& t, long long, int count, int slots, cudaStream_t st) {
     int idx;
     CKRET(new_slot(h, &idx));
     Slot& s = h->slots[idx];
-    CKRET(finalize_into(h, h->ps, s.d_R, s.d_F, count, slots, st));
+    CKRET(finalize_into(h, h->ps, t, s.d_R, s.d_F, count, slots, st));
     const size_t ne = vis_elems(h);
     CK(cudaMemcpyAsync(s.h_R, s.d_R, ne * sizeof(float2), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(s.h_F, s.d_F, ne, cudaMemcpyDeviceToHost, st));
@@ -420,11 +468,11 @@ struct DirectCtx {
     int n_out;
 };
 
-int sink_direct(corr_t h, void* vctx, long long i, int count, int slots, cudaStream_t st) {
+int sink_direct(corr_t h, void* vctx, const Tables& t, long long i, int count, int slots, cudaStream_t st) {
     DirectCtx* c = static_cast<DirectCtx*>(vctx);
     if (i >= c->max_int) return fail(h, CORR_EINVAL, "max_int too small for the stream");
     const size_t ne = vis_elems(h);
-    CKRET(finalize_into(h, h->pd, c->vis + (size_t)i * ne, c->flags ? c->flags + (size_t)i * ne : nullptr,
+    CKRET(finalize_into(h, h->pd, t, c->vis + (size_t)i * ne, c->flags ? c->flags + (size_t)i * ne : nullptr,
                         count, slots, st));
     c->n_out = (int)i + 1;
     return CORR_OK;
@@ -563,6 +611,7 @@ int pop_results(corr_t h, std::deque<int>& q, bool vis, void* out, int max_int, 
 
 void free_pipe(Pipe& p) {
     if (p.V) cudaFree(p.V);
+    if (p.Z) cudaFree(p.Z);
     if (p.part) cudaFree(p.part);
     p = Pipe{};
 }
@@ -606,10 +655,7 @@ int corr_create(corr_t* out, int n_ant, int n_pol, int n_chan, int taps, int n_i
     };
     if (e != cudaSuccess) return bail(CORR_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     const std::vector<float> hf = make_filter(h->M, taps);
-    std::vector<float2> tw(h->M);
-    const double pi = 3.14159265358979323846;
-    for (int k = 0; k < h->M; ++k)
-        tw[k] = make_float2((float)std::cos(-2.0 * pi * k / h->M), (float)std::sin(-2.0 * pi * k / h->M));
+    const std::vector<float2> tw = corr::fft_twiddle_table(h->M);
     if (cudaStreamCreateWithFlags(&h->s_comp, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&h->s_copy, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_h2d, cudaEventDisableTiming) != cudaSuccess ||
@@ -654,9 +700,12 @@ int corr_destroy(corr_t h) {
     cudaFree(h->d_h);
     cudaFree(h->d_tw);
     cudaFree(h->tab_stream.phasor);
+    cudaFree(h->tab_stream.rot);
     cudaFree(h->tab_stream.coarse);
     cudaFree(h->tab_direct.phasor);
+    cudaFree(h->tab_direct.rot);
     cudaFree(h->tab_direct.coarse);
+    cudaFree(h->d_z_f);
     cudaFree(h->d_stage);
     cudaFree(h->d_tmp);
     if (h->h_pin) cudaFreeHost(h->h_pin);
@@ -827,31 +876,15 @@ int corr_fengine_dev(corr_t h, const int8_t* d_samples, size_t n_samples, size_t
     if (!d_samples || !d_V || n_spec < 0 || s0 < 0) return fail(h, CORR_EINVAL, "bad argument");
     if (stride < n_samples) return fail(h, CORR_EINVAL, "input_stride < n_samples");
     if (n_spec == 0) return CORR_OK;
-    Pipe p;
-    p.V = reinterpret_cast<float2*>(d_V);
-    p.v_cap = n_spec;
-    StreamView sv{d_samples, (long long)stride, 0, (long long)n_samples};
-    FArgs a{};
-    a.src = sv;
-    a.h = h->d_h;
-    a.tw = h->d_tw;
-    a.phasor = h->tab_direct.phasor;
-    a.coarse = h->tab_direct.coarse;
-    a.V = p.V;
-    a.s_begin = s0;
-    a.s_end = s0 + n_spec;
-    a.v_origin = s0;
-    a.v_cap = n_spec;
-    a.n_in = h->n_in;
-    a.n_in_pad = h->n_in_pad;
-    a.M = h->M;
-    a.taps = h->taps;
-    a.spt = choose_spt(n_spec, h->n_in_pad / 2);
-    {
-        Timed t_(h, 0, static_cast<cudaStream_t>(stream));
-        launch_fengine(a, static_cast<cudaStream_t>(stream));
+    if (n_spec > h->z_f_spectra) {
+        cudaFree(h->d_z_f);
+        h->d_z_f = nullptr;
+        CK(cudaMalloc(&h->d_z_f, sizeof(float2) * (size_t)n_spec * h->n_in_pad * h->n_chan));
+        h->z_f_spectra = n_spec;
     }
-    CK(cudaGetLastError());
+    StreamView sv{d_samples, (long long)stride, 0, (long long)n_samples};
+    CKRET(launch_f(h, sv, h->tab_direct, h->d_z_f, s0, -1LL, reinterpret_cast<float2*>(d_V), s0, -1LL,
+                   h->tab_direct.phasor, s0, s0 + n_spec, static_cast<cudaStream_t>(stream)));
     return CORR_OK;
 }
 
@@ -871,7 +904,7 @@ int corr_xengine_dev(corr_t h, const float* d_V, int n_spec, float* d_vis, void*
     XArgs x{};
     x.V = reinterpret_cast<const float2*>(d_V);
     x.v_origin = 0;
-    x.v_cap = n_spec;
+    x.v_mask = -1LL;
     x.n_chan = h->n_chan;
     x.n_in_pad = h->n_in_pad;
     x.nt = h->nt;
@@ -883,7 +916,7 @@ int corr_xengine_dev(corr_t h, const float* d_V, int n_spec, float* d_vis, void*
     x.n_groups = (int)slots;
     x.part = h->d_part_x;
     {
-        Timed t_(h, 1, st);
+        Timed t_(h, 2, st);
         launch_xengine(x, st);
     }
     CK(cudaGetLastError());
@@ -896,7 +929,7 @@ int corr_xengine_dev(corr_t h, const float* d_V, int n_spec, float* d_vis, void*
     f.scale = 1.0f / (float)n_spec;
     f.R = reinterpret_cast<float2*>(d_vis);
     {
-        Timed t_(h, 2, st);
+        Timed t_(h, 3, st);
         launch_finalize(f, st);
     }
     CK(cudaGetLastError());
@@ -909,7 +942,7 @@ int corr_flag_dev(corr_t h, const float* d_vis, int n_vis, uint8_t* d_flags, voi
     if (!d_vis || !d_flags || n_vis < 0) return fail(h, CORR_EINVAL, "bad argument");
     const int w = h->flag_window < h->n_chan ? h->flag_window : h->n_chan;
     {
-        Timed t_(h, 3, static_cast<cudaStream_t>(stream));
+        Timed t_(h, 4, static_cast<cudaStream_t>(stream));
         launch_mad_flags(reinterpret_cast<const float2*>(d_vis), d_flags, n_vis, h->n_chan, h->n_in, w,
                          (float)h->flag_sigma, static_cast<cudaStream_t>(stream));
     }

@@ -38,8 +38,7 @@ __global__ void __launch_bounds__(128) xengine_kernel(const XArgs X) {
     for (int e = 0; e < 32; ++e) acc[e] = 0.f;
     const int q4 = X.n_in_pad >> 1;   // float4 per (slot, channel)
     for (long long s = s0; s < s1; ++s) {
-        long long slot = (s - X.v_origin) % X.v_cap;
-        if (slot < 0) slot += X.v_cap;
+        const long long slot = (s - X.v_origin) & X.v_mask;
         const float4* vp = reinterpret_cast<const float4*>(X.V) + ((size_t)slot * X.n_chan + k) * q4;
         const float4 a01 = __ldg(vp + 2 * A), a23 = __ldg(vp + 2 * A + 1);
         const float4 b01 = __ldg(vp + 2 * B), b23 = __ldg(vp + 2 * B + 1);
@@ -63,39 +62,127 @@ __global__ void __launch_bounds__(128) xengine_kernel(const XArgs X) {
     for (int e = 0; e < 32; ++e) out[(size_t)e * X.n_chan] = acc[e];
 }
 
+// n_in_pad <= 8: one thread keeps the whole Hermitian triangle (a <= b) of
+// one channel.  A warp covers 4 channels x 8 sub-groups; sub-group q sums
+// spectra q, q+8, q+16, ... of the group and the eight partial sums are
+// added with a fixed xor-shuffle tree, then written in the 4x4 block layout.
+template <int NB>
+__global__ void __launch_bounds__(128) xengine_small_kernel(const XArgs X) {
+    constexpr int NI = 4 * NB;
+    constexpr int NC = NI * (NI - 1) / 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int q = lane >> 2;
+    const int k = (blockIdx.x * (blockDim.x >> 5) + warp) * 4 + (lane & 3);
+    const int g = blockIdx.y;
+    const bool valid = k < X.n_chan;
+    const int kk = valid ? k : X.n_chan - 1;
+    long long s0 = X.int_start + (long long)(X.j0 + g) * X.G;
+    long long s1 = s0 + X.G;
+    if (s1 > X.int_end) s1 = X.int_end;
+    if (s1 > X.s_limit) s1 = X.s_limit;
+    float au[NI], cr[NC], ci[NC];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) au[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < NC; ++i) { cr[i] = 0.f; ci[i] = 0.f; }
+    for (long long s = s0 + q; s < s1; s += 8) {
+        const long long slot = (s - X.v_origin) & X.v_mask;
+        const float4* vp = reinterpret_cast<const float4*>(X.V) + ((size_t)slot * X.n_chan + kk) * (NI / 2);
+        float xr[NI], xi[NI];
+#pragma unroll
+        for (int i = 0; i < NI / 2; ++i) {
+            const float4 t = __ldg(vp + i);
+            xr[2 * i] = t.x; xi[2 * i] = t.y; xr[2 * i + 1] = t.z; xi[2 * i + 1] = t.w;
+        }
+#pragma unroll
+        for (int a = 0; a < NI; ++a) au[a] = fmaf(xr[a], xr[a], fmaf(xi[a], xi[a], au[a]));
+        int c = 0;
+#pragma unroll
+        for (int a = 0; a < NI; ++a) {
+#pragma unroll
+            for (int b = a + 1; b < NI; ++b, ++c) {
+                cr[c] = fmaf(xr[a], xr[b], fmaf(xi[a], xi[b], cr[c]));
+                ci[c] = fmaf(xi[a], xr[b], fmaf(-xr[a], xi[b], ci[c]));
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 4; m <= 16; m <<= 1) {
+#pragma unroll
+        for (int i = 0; i < NI; ++i) au[i] += __shfl_xor_sync(0xffffffffu, au[i], m);
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            cr[i] += __shfl_xor_sync(0xffffffffu, cr[i], m);
+            ci[i] += __shfl_xor_sync(0xffffffffu, ci[i], m);
+        }
+    }
+    if (q != 0 || !valid) return;
+#pragma unroll
+    for (int A = 0; A < NB; ++A) {
+#pragma unroll
+        for (int B = A; B < NB; ++B) {
+            const int t = A * NB - A * (A - 1) / 2 + (B - A);
+            float* out = X.part + (((size_t)(X.j0 + g) * X.nt + t) * 32) * X.n_chan + k;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int a = 4 * A + i, b = 4 * B + j;
+                    float re = 0.f, im = 0.f;
+                    if (a == b) {
+                        re = au[a];
+                    } else if (a < b) {
+                        const int c = a * NI - a * (a + 1) / 2 + (b - a - 1);
+                        re = cr[c];
+                        im = ci[c];
+                    }
+                    out[(size_t)((i * 4 + j) * 2) * X.n_chan] = re;
+                    out[(size_t)((i * 4 + j) * 2 + 1) * X.n_chan] = im;
+                }
+            }
+        }
+    }
+}
+
+// One thread per (channel, 4x4 block, entry): sums the entry's partial
+// slots in slot order, scales, rotates and writes R_ab and its mirror.
 __global__ void __launch_bounds__(128) finalize_kernel(const FinArgs F) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int t = blockIdx.y;
+    const int i = blockIdx.z >> 2, j = blockIdx.z & 3;
     if (k >= F.n_chan) return;
     const int n_in_pad = (F.n_in + 3) & ~3;
     int A, B;
     tile_decode(t, n_in_pad >> 2, A, B);
-    float acc[32];
-#pragma unroll
-    for (int e = 0; e < 32; ++e) acc[e] = 0.f;
-    for (int j = 0; j < F.n_slots; ++j) {
-        const float* p = F.part + (((size_t)j * F.nt + t) * 32) * F.n_chan + k;
-#pragma unroll
-        for (int e = 0; e < 32; ++e) acc[e] += p[(size_t)e * F.n_chan];
+    const int a = 4 * A + i, b = 4 * B + j;
+    if (a >= F.n_in || b >= F.n_in) return;
+    if (A == B && i > j) return;
+    const int e = (i * 4 + j) * 2;
+    float re = 0.f, im = 0.f;
+    for (int s = 0; s < F.n_slots; ++s) {
+        const float* p = F.part + (((size_t)s * F.nt + t) * 32 + e) * F.n_chan + k;
+        re += p[0];
+        im += p[F.n_chan];
     }
+    re *= F.scale;
+    im *= F.scale;
     float2* R = F.R + (size_t)k * F.n_in * F.n_in;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int a = 4 * A + i, b = 4 * B + j;
-            if (a >= F.n_in || b >= F.n_in) continue;
-            if (A == B && i > j) continue;
-            const float re = acc[(i * 4 + j) * 2] * F.scale;
-            const float im = acc[(i * 4 + j) * 2 + 1] * F.scale;
-            if (a == b) {
-                R[a * F.n_in + a] = make_float2(re, 0.f);
-            } else {
-                R[a * F.n_in + b] = make_float2(re, im);
-                R[b * F.n_in + a] = make_float2(re, -im);
-            }
-        }
+    if (a == b) {
+        R[a * F.n_in + a] = make_float2(re, 0.f);
+        return;
     }
+    if (F.rot) {
+        // R_ab = Q_a conj(Q_b) * sum U_a U_b^*
+        const float2 qa = F.rot[(size_t)a * F.n_chan + k];
+        const float2 qb = F.rot[(size_t)b * F.n_chan + k];
+        const float pr = qa.x * qb.x + qa.y * qb.y;
+        const float pi = qa.y * qb.x - qa.x * qb.y;
+        const float r2 = re * pr - im * pi;
+        im = re * pi + im * pr;
+        re = r2;
+    }
+    R[a * F.n_in + b] = make_float2(re, im);
+    R[b * F.n_in + a] = make_float2(re, -im);
 }
 
 // ---- MAD flagging, Eq. 2 ------------------------------------------------
@@ -164,12 +251,18 @@ __global__ void __launch_bounds__(32 * kFlagWarps) mad_flag_kernel(const float2*
 
 void launch_xengine(const XArgs& a, cudaStream_t st) {
     if (a.n_groups <= 0) return;
+    if (a.n_in_pad <= 8) {
+        dim3 grid((a.n_chan + 15) / 16, a.n_groups);
+        if (a.n_in_pad == 4) xengine_small_kernel<1><<<grid, 128, 0, st>>>(a);
+        else xengine_small_kernel<2><<<grid, 128, 0, st>>>(a);
+        return;
+    }
     dim3 grid((a.n_chan + 127) / 128, a.nt, a.n_groups);
     xengine_kernel<<<grid, 128, 0, st>>>(a);
 }
 
 void launch_finalize(const FinArgs& a, cudaStream_t st) {
-    dim3 grid((a.n_chan + 127) / 128, a.nt);
+    dim3 grid((a.n_chan + 127) / 128, a.nt, 16);
     finalize_kernel<<<grid, 128, 0, st>>>(a);
 }
 
