@@ -1,0 +1,113 @@
+"""FP64 oracle of the reduced-precision correlator -- TEST INFRASTRUCTURE ONLY.
+
+The channelised voltages are requantised to int8 or FP8 (e4m3) with one
+scale per (input, channel) held fixed over an integration, correlated as an
+exact Gram matrix G = Q Q^T of the stacked real/imaginary rows
+Q = [Q_re; Q_im] (K = time), and rescaled:
+
+    sum_s q_a conj(q_b) = (G_rr + G_ii)[a, b] + j (G_ir - G_ri)[a, b]
+    R_ab = sigma_a sigma_b / n * sum_s q_a conj(q_b)
+
+Readings (the paper correlates in full precision; this reduced-precision form
+is the build's own; each reading is also listed in the design notes):
+
+* int8: round half to even, saturate to [-127, 127]; e4m3: round half to
+  even onto the e4m3 grid (3 mantissa bits, exponent bias 7, subnormals
+  down to 2^-9), saturate to +-448.
+* Scales: sigma_a[k] = sqrt(P_a[k] / 2) / g with P the mean power |V|^2 of
+  the input/channel, g = 32 (int8) or 64 (e4m3).  The first integration
+  takes P from its first min(n_int, 64) spectra; each later integration
+  from the previous integration's autocorrelation R_aa[k].
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+from . import fx_oracle as fx
+
+GAIN = {"int8": 32.0, "e4m3": 64.0}
+PREPASS_SPECTRA = 64
+
+
+def quantize_int8(x: np.ndarray) -> np.ndarray:
+    """Round half to even and saturate to [-127, 127] (FP64 in, FP64 codes out)."""
+    return np.clip(np.rint(np.asarray(x, np.float64)), -127.0, 127.0)
+
+
+def e4m3_round(x: np.ndarray) -> np.ndarray:
+    """Nearest e4m3 value (ties to even), saturating to +-448."""
+    x = np.asarray(x, np.float64)
+    a = np.abs(x)
+    out = np.zeros_like(a)
+    nz = a > 0
+    m, e = np.frexp(a[nz])                 # a = m 2^e, m in [0.5, 1)
+    exp = np.maximum(e - 1, -6)            # unbiased exponent, subnormals at 2^-6
+    step = np.ldexp(1.0, exp - 3)          # 3 mantissa bits
+    q = np.rint(a[nz] / step) * step       # exact division by a power of two
+    out[nz] = np.minimum(q, 448.0)
+    return np.sign(x) * out
+
+
+def quantize(x: np.ndarray, dtype: str) -> np.ndarray:
+    return quantize_int8(x) if dtype == "int8" else e4m3_round(x)
+
+
+def gram(Q: np.ndarray) -> np.ndarray:
+    """G[k] = Q[k] Q[k]^T for Q [n_chan][rows][K]; exact (int64 or FP64 of FP8 values)."""
+    if np.issubdtype(Q.dtype, np.integer):
+        Q = Q.astype(np.int64)
+        return np.einsum('crk,csk->crs', Q, Q)
+    return np.einsum('crk,csk->crs', Q.astype(np.float64), Q.astype(np.float64))
+
+
+def stacked_rows(q_re: np.ndarray, q_im: np.ndarray) -> np.ndarray:
+    """Q [n_chan][2N][K] from codes [N][K][n_chan] (rows: real parts, then imaginary)."""
+    return np.concatenate([np.transpose(q_re, (2, 0, 1)), np.transpose(q_im, (2, 0, 1))], axis=1)
+
+
+def visibilities_from_gram(G: np.ndarray, N: int) -> np.ndarray:
+    """sum_s q_a conj(q_b) per channel from the Gram matrix of the stacked rows."""
+    G = np.asarray(G, np.float64)
+    rr, ii = G[:, :N, :N], G[:, N:2 * N, N:2 * N]
+    ir, ri = G[:, N:2 * N, :N], G[:, :N, N:2 * N]
+    return (rr + ii) + 1j * (ir - ri)
+
+
+def scales_from_power(P: np.ndarray, dtype: str) -> np.ndarray:
+    P = np.asarray(P, np.float64)
+    s = np.sqrt(np.maximum(P, 0.0) / 2.0) / GAIN[dtype]
+    return np.where(s > 0, s, 1.0)
+
+
+def correlate_quantized(x: np.ndarray, n_chan: int, taps: int, n_int: int, tau=None, phi=None,
+                        dtype: str = "int8", partial: bool = False):
+    """Visibilities of the reduced-precision path, emulated exactly in FP64.
+
+    Returns (R [n_out][n_chan][N][N], scales [n_out][N][n_chan]).
+    """
+    V = fx.f_engine(x, n_chan, taps, tau, phi)            # [N][S][n_chan]
+    N, n_spec, _ = V.shape
+    starts = list(range(0, n_spec - n_int + 1, n_int))
+    if partial and n_spec % n_int:
+        starts.append((n_spec // n_int) * n_int)
+    R = np.empty((len(starts), n_chan, N, N), np.complex128)
+    S = np.empty((len(starts), N, n_chan))
+    prev = None
+    for i, s0 in enumerate(starts):
+        s1 = min(s0 + n_int, n_spec)
+        blk = V[:, s0:s1, :]
+        if prev is None:
+            P = np.mean(np.abs(blk[:, :min(PREPASS_SPECTRA, s1 - s0), :]) ** 2, axis=1)
+        else:
+            P = np.real(np.einsum('kaa->ak', prev))
+        sc = scales_from_power(P, dtype)                    # [N][n_chan]
+        q_re = quantize(blk.real / sc[:, None, :], dtype)
+        q_im = quantize(blk.imag / sc[:, None, :], dtype)
+        G = gram(stacked_rows(q_re, q_im) if dtype == "e4m3" else
+                 stacked_rows(q_re.astype(np.int64), q_im.astype(np.int64)))
+        C = visibilities_from_gram(G, N)                    # [n_chan][N][N]
+        R[i] = C * (sc.T[:, :, None] * sc.T[:, None, :]) / (s1 - s0)
+        S[i] = sc
+        prev = R[i]
+    return R, S
