@@ -179,6 +179,31 @@ int corr_fengine_dev(corr_t h, const int8_t* d_samples, size_t n_samples, size_t
 int corr_xengine_dev(corr_t h, const float* d_V, int n_spec, float* d_vis, void* stream);
 int corr_flag_dev(corr_t h, const float* d_vis, int n_vis, uint8_t* d_flags, void* stream);
 
+/*
+ * corr_gram_dev -- tensor-core Gram matrices, the dense form of the X-engine
+ * (Sec. 4.2, Algorithm 1) on requantised voltages: for every channel c,
+ * G[c] = Q[c] Q[c]^T with Q [n_chan][128 rows][k_pitch bytes] in device
+ * memory, K valid elements per row (later elements read as zero).  Rows hold
+ * the real parts of the inputs' codes, then the imaginary parts, then zeros,
+ * so sum_s q_a conj(q_b) = (G_rr + G_ii) + j (G_ir - G_ri).
+ *   dtype CORR_INT8: int8 codes stored as BF16 values (2 bytes each); the
+ *                    products are exact, the sums FP32 (exact while every
+ *                    partial sum stays below 2^24).
+ *   dtype CORR_FP8:  e4m3 bytes; FP32 sums.
+ * d_G: [n_chan][128][128] FP32.  k_pitch must be a multiple of 128 and d_Q
+ * 16-byte aligned (else CORR_EINVAL).  Runs on tcgen05 tensor cores with
+ * TMA-staged operands; a stalled pipeline sets the status word read by
+ * corr_device_status to CORR_ETIMEDOUT instead of hanging.
+ */
+int corr_gram_dev(corr_t h, const void* d_Q, int n_chan, int k_pitch, int K, int dtype, float* d_G,
+                  void* stream);
+
+/*
+ * corr_device_status -- wait for the device, return the handle's device
+ * status word (CORR_OK or CORR_ETIMEDOUT from a bounded wait) and clear it.
+ */
+int corr_device_status(corr_t h, int* status);
+
 /* Shapes of a handle: n_in, n_chan, taps, n_int, n_in_pad (any may be NULL). */
 int corr_shape(corr_t h, int* n_in, int* n_chan, int* taps, int* n_int, int* n_in_pad);
 

@@ -49,6 +49,18 @@ def e4m3_round(x: np.ndarray) -> np.ndarray:
     return np.sign(x) * out
 
 
+def e4m3_decode(b: np.ndarray) -> np.ndarray:
+    """FP64 value of e4m3 bytes: sign, 4-bit exponent (bias 7), 3-bit mantissa,
+    exponent field 0 subnormal (m / 8 * 2^-6); 0x7F / 0xFF are NaN."""
+    b = np.asarray(b, np.uint8).astype(np.int64)
+    sign = np.where(b & 0x80, -1.0, 1.0)
+    e = (b >> 3) & 0xF
+    m = b & 0x7
+    val = np.where(e == 0, m / 8.0 * 2.0 ** -6, (1.0 + m / 8.0) * np.ldexp(1.0, e - 7))
+    val = np.where((e == 15) & (m == 7), np.nan, val)
+    return sign * val
+
+
 def quantize(x: np.ndarray, dtype: str) -> np.ndarray:
     return quantize_int8(x) if dtype == "int8" else e4m3_round(x)
 

@@ -33,6 +33,7 @@ EXPORTED = [
     "corr_push", "corr_push_dev", "corr_flush", "corr_reset", "corr_get_vis", "corr_get_flags",
     "corr_pending", "corr_run_dev", "corr_fengine_dev", "corr_xengine_dev", "corr_flag_dev",
     "corr_shape", "corr_kernel_launches", "corr_stage_times", "corr_xengine_noalloc",
+    "corr_gram_dev", "corr_device_status",
 ]
 
 
@@ -80,6 +81,8 @@ def load_library(path: str = LIB_PATH):
         "corr_kernel_launches": (_ll, [_vp]),
         "corr_stage_times": (_i, [_vp, _vp, _vp, _i]),
         "corr_xengine_noalloc": (_i, [_vp, _i, _i, _i, _vp, _vp]),
+        "corr_gram_dev": (_i, [_vp, _vp, _i, _i, _i, _i, _vp, _vp]),
+        "corr_device_status": (_i, [_vp, ctypes.POINTER(_i)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -276,6 +279,16 @@ class Correlator:
     def flag_dev(self, vis, n_vis: int, flags_out, stream=None):
         self._check(self._L.corr_flag_dev(self._h, _dev_ptr(vis, "vis"), int(n_vis),
                                           _dev_ptr(flags_out, "flags"), _stream_ptr(stream)))
+
+    def gram_dev(self, Q, n_chan: int, k_pitch: int, K: int, dtype: int, G_out, stream=None):
+        """Tensor-core Gram matrices of Q (see corr_gram_dev in include/corr.h)."""
+        self._check(self._L.corr_gram_dev(self._h, _dev_ptr(Q, "Q"), int(n_chan), int(k_pitch), int(K),
+                                          int(dtype), _dev_ptr(G_out, "G"), _stream_ptr(stream)))
+
+    def device_status(self) -> int:
+        st = _i()
+        self._check(self._L.corr_device_status(self._h, ctypes.byref(st)))
+        return st.value
 
     def stage_times(self):
         """(ms, counts) per stage (FIR, FFT, X, finalise, flag) since the last call."""

@@ -81,6 +81,56 @@ struct FinArgs {
     float2* R;               // [n_chan][n_in][n_in]
 };
 
+// Tensor-core Gram matrix G[c] = Q[c] Q[c]^T, Q [n_chan][128 rows][k_pitch
+// bytes] of BF16 (int8 codes) or e4m3, K valid elements per row (later ones
+// read as zero); G [n_chan][128][128] FP32.  status: device word set to
+// CORR_ETIMEDOUT if a bounded wait expires (may be null).
+struct GramArgs {
+    const void* Q;
+    int n_chan, K, k_pitch;
+    bool fp8;
+    void* G;
+    int* status;
+};
+
+// Requantise spectra [s_begin, s_end) of the ring V (U = 2Y, unrotated) into
+// Q columns s - int_start: Q[k][a][.] = q(Re U / sigma), Q[k][N+a][.] =
+// q(Im U / sigma), sigma = scale[a][k]; int8 codes (round to nearest even,
+// saturate +-127) stored as BF16, or e4m3 (satfinite) bytes.
+struct RequantArgs {
+    const float2* V;
+    long long v_origin, v_mask;
+    const float* scale;      // [n_in_pad][n_chan]
+    uint8_t* Q;
+    int k_pitch;
+    long long s_begin, s_end, int_start;
+    int n_in, n_in_pad, n_chan;
+    bool fp8;
+};
+
+// R[k][a][b] = scale_a scale_b / (4 count) rot_a conj(rot_b) sum q_a conj(q_b),
+// from the Gram matrix.
+struct FinQArgs {
+    const void* G;
+    const float* scale;      // [n_in_pad][n_chan]
+    const float2* rot;       // [n_in_pad][n_chan] or nullptr
+    int n_chan, n_in, count;
+    bool fp8;
+    float2* R;
+};
+
+int launch_gram(const GramArgs& a, cudaStream_t st);
+size_t gram_smem_bytes();
+void launch_requant(const RequantArgs& a, cudaStream_t st);
+void launch_finalize_q(const FinQArgs& a, cudaStream_t st);
+// scale[a][k] = sqrt(P / 2) / gain with P the mean |U|^2 over spectra
+// [s0, s0 + n) of the ring (first integration of a stream).
+void launch_scale_from_ring(const float2* V, long long v_origin, long long v_mask, long long s0, int n, int n_in,
+                            int n_in_pad, int n_chan, float gain, float* scale, cudaStream_t st);
+// scale[a][k] = 2 sqrt(R_aa[k] / 2) / gain (U = 2V) from an integration's R.
+void launch_scale_from_vis(const float2* R, int n_in, int n_in_pad, int n_chan, float gain, float* scale,
+                           cudaStream_t st);
+
 void launch_fir(const FirArgs& a, cudaStream_t st);
 void launch_fft(const FftArgs& a, cudaStream_t st);
 void launch_xengine(const XArgs& a, cudaStream_t st);

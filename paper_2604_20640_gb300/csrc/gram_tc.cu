@@ -1,0 +1,298 @@
+// Tensor-core X-engine: per channel, the Gram matrix G = Q Q^T of the
+// requantised voltages stacked as Q = [Q_re; Q_im] (2N <= 128 rows, K = time),
+// so that
+//   sum_s q_a conj(q_b) = (G_rr + G_ii)[a][b] + j (G_ir - G_ri)[a][b]
+// (the X-engine of Sec. 4.2 / Algorithm 1 as a dense contraction).
+//
+// sm_103a has no integer tcgen05 MMA, so int8 codes travel as BF16 (exact
+// for |q| <= 127; every product is exact) through tcgen05.mma.kind::f16, and
+// e4m3 codes through kind::f8f6f4; both accumulate in FP32.  Either way one
+// MMA consumes 32 bytes of K per row.
+//
+// One CTA per channel, 128 threads.  Warp 0 lane 0 streams 128-row x 128-byte
+// K-tiles of Q through a ring of shared-memory stages with TMA (128-byte
+// swizzle); warp 1 lane 0 issues tcgen05.mma (M = N = 128, the same shared
+// tile as A and B operand) into a 128-column FP32 TMEM accumulator; all four
+// warps then read their 32 TMEM lanes with tcgen05.ld and store G.  Every
+// mbarrier wait is bounded by %globaltimer; on expiry the CTA records
+// CORR_ETIMEDOUT in the status word, frees its TMEM and returns.
+#include "corr.h"
+#include "corr_internal.h"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+
+namespace corr {
+
+namespace {
+
+constexpr int kRows = 128;
+constexpr int kKTile = 128;                      // bytes of K per stage
+constexpr int kStages = 6;
+constexpr int kStageBytes = kRows * kKTile;      // 16 KiB
+constexpr uint32_t kTmemCols = 128;
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
+
+struct __align__(8) GramShared {
+    uint64_t full[kStages];
+    uint64_t empty[kStages];
+    uint64_t accum;
+    uint32_t tmem_addr;
+    int abort;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of `bar` with the given parity; false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    while (!mbar_try(bar, parity)) {
+        if (globaltimer() - t0 > kWaitNs) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row groups 1024 bytes apart (the layout TMA writes).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);        // start address
+    d |= (uint64_t)(16 >> 4) << 16;                  // leading byte offset (unused here)
+    d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
+    d |= (uint64_t)1 << 46;                          // descriptor version
+    d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: dense, K-major A and B, M = N = 128, FP32
+// accumulator; A/B format BF16 (kind::f16) or E4M3 (kind::f8f6f4).
+__host__ __device__ constexpr uint32_t idesc(bool fp8) {
+    return (1u << 4)                                 // FP32 accumulator
+           | (fp8 ? 0u : (1u << 7))                  // A: E4M3 (0) / BF16 (1)
+           | (fp8 ? 0u : (1u << 10))                 // B: E4M3 (0) / BF16 (1)
+           | ((uint32_t)(kRows >> 3) << 17)          // N >> 3
+           | ((uint32_t)(kRows >> 4) << 24);         // M >> 4
+}
+
+template <bool FP8>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+    if constexpr (FP8) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc(true)), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc(false)), "r"(acc)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+#define CORR_R8(i) "=r"(r[i + 0]), "=r"(r[i + 1]), "=r"(r[i + 2]), "=r"(r[i + 3]), \
+                   "=r"(r[i + 4]), "=r"(r[i + 5]), "=r"(r[i + 6]), "=r"(r[i + 7])
+
+// 32 consecutive 32-bit TMEM columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : CORR_R8(0), CORR_R8(8), CORR_R8(16), CORR_R8(24)
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+#undef CORR_R8
+
+template <bool FP8>
+__global__ void __launch_bounds__(128, 1) gram_kernel(const __grid_constant__ CUtensorMap tmap, GramArgs A) {
+    extern __shared__ __align__(1024) uint8_t gsm_raw[];
+    // stage buffers first (1024-byte aligned), then the barriers
+    uint8_t* stages = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
+    GramShared* sh = reinterpret_cast<GramShared*>(stages + kStages * kStageBytes);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ch = blockIdx.x;
+    const int kt_elems = FP8 ? kKTile : kKTile / 2;
+    const int num_k = (A.K + kt_elems - 1) / kt_elems;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&sh->full[s], 1);
+            mbar_init(&sh->empty[s], 1);
+        }
+        mbar_init(&sh->accum, 1);
+        sh->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&sh->tmem_addr)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = sh->tmem_addr;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        for (int it = 0; it < num_k; ++it) {
+            const int s = it % kStages;
+            const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+            if (!mbar_wait(&sh->empty[s], ph ^ 1u)) {
+                sh->abort = 1;
+                break;
+            }
+            mbar_expect_tx(&sh->full[s], kStageBytes);
+            // inner coordinate in elements: 128 bytes = 128 e4m3 or 64 BF16
+            tma_load_2d(stages + s * kStageBytes, &tmap, &sh->full[s], it * (FP8 ? kKTile : kKTile / 2),
+                        ch * kRows);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        bool ok = true;
+        for (int it = 0; it < num_k && ok; ++it) {
+            const int s = it % kStages;
+            const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+            if (!mbar_wait(&sh->full[s], ph)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint64_t d0 = sdesc(smem_u32(stages + s * kStageBytes));
+#pragma unroll
+            for (int kk = 0; kk < kKTile / 32; ++kk) {
+                const uint64_t d = d0 + (uint64_t)((kk * 32) >> 4);
+                mma<FP8>(tmem, d, d, (it | kk) != 0 ? 1u : 0u);
+            }
+            mma_commit(&sh->empty[s]);
+        }
+        if (!ok) sh->abort = 1;
+        mma_commit(&sh->accum);
+    }
+    __syncwarp();
+    // Epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31.
+    if (!mbar_wait(&sh->accum, 0)) sh->abort = 1;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (sh->abort) {
+        if (threadIdx.x == 0 && A.status) atomicExch(A.status, CORR_ETIMEDOUT);
+    } else {
+        const int row = warp * 32 + lane;
+        uint32_t* G = reinterpret_cast<uint32_t*>(A.G) + ((size_t)ch * kRows + row) * kRows;
+#pragma unroll
+        for (int c0 = 0; c0 < kRows; c0 += 32) {
+            uint32_t r[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+            uint4* o = reinterpret_cast<uint4*>(G + c0);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) o[i] = make_uint4(r[4 * i], r[4 * i + 1], r[4 * i + 2], r[4 * i + 3]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                     : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+}  // namespace
+
+size_t gram_smem_bytes() { return (size_t)kStages * kStageBytes + sizeof(GramShared) + 1024; }
+
+int launch_gram(const GramArgs& a, cudaStream_t st) {
+    if (a.n_chan <= 0 || a.K <= 0) return CORR_OK;
+    const int eb = a.fp8 ? 1 : 2;
+    if (a.k_pitch % 128 != 0 || (long long)a.K * eb > a.k_pitch) return CORR_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(a.Q) & 15) != 0) return CORR_EINVAL;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return CORR_ECUDA;
+    CUtensorMap map;
+    // dim 0: K columns (elements, only the valid ones: later columns read as
+    // 0); dim 1: n_chan * 128 rows, k_pitch bytes apart.
+    cuuint64_t dims[2] = {(cuuint64_t)a.K, (cuuint64_t)a.n_chan * kRows};
+    cuuint64_t strides[1] = {(cuuint64_t)a.k_pitch};
+    cuuint32_t box[2] = {(cuuint32_t)(kKTile / eb), (cuuint32_t)kRows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&map, a.fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                     const_cast<void*>(a.Q), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return CORR_EINVAL;
+    const size_t smem = gram_smem_bytes();
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(gram_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(gram_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    if (a.fp8) gram_kernel<true><<<a.n_chan, 128, smem, st>>>(map, a);
+    else gram_kernel<false><<<a.n_chan, 128, smem, st>>>(map, a);
+    return CORR_OK;
+}
+
+}  // namespace corr

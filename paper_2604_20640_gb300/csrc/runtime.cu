@@ -125,6 +125,7 @@ struct corr_s {
     std::string err;
     long long launches = 0;
     StageTimer timer;
+    int* d_status = nullptr;     // device error word of bounded waits
 };
 
 namespace {
@@ -669,6 +670,8 @@ int corr_create(corr_t* out, int n_ant, int n_pol, int n_chan, int taps, int n_i
         return bail(CORR_ECUDA, "upload of filter tables failed");
     if (alloc_tables(h, h->tab_stream) != CORR_OK || alloc_tables(h, h->tab_direct) != CORR_OK)
         return bail(CORR_ENOMEM, "cudaMalloc of delay tables failed");
+    if (cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess || cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess)
+        return bail(CORR_ENOMEM, "cudaMalloc of the status word failed");
     if (upload_tables(h, h->tab_stream, h->tau, h->phi, h->s_comp) != CORR_OK ||
         upload_tables(h, h->tab_direct, h->tau, h->phi, h->s_comp) != CORR_OK)
         return bail(CORR_ECUDA, "upload of delay tables failed");
@@ -706,6 +709,7 @@ int corr_destroy(corr_t h) {
     cudaFree(h->tab_direct.rot);
     cudaFree(h->tab_direct.coarse);
     cudaFree(h->d_z_f);
+    cudaFree(h->d_status);
     cudaFree(h->d_stage);
     cudaFree(h->d_tmp);
     if (h->h_pin) cudaFreeHost(h->h_pin);
@@ -878,6 +882,7 @@ int corr_fengine_dev(corr_t h, const int8_t* d_samples, size_t n_samples, size_t
     if (n_spec == 0) return CORR_OK;
     if (n_spec > h->z_f_spectra) {
         cudaFree(h->d_z_f);
+    cudaFree(h->d_status);
         h->d_z_f = nullptr;
         CK(cudaMalloc(&h->d_z_f, sizeof(float2) * (size_t)n_spec * h->n_in_pad * h->n_chan));
         h->z_f_spectra = n_spec;
@@ -961,6 +966,38 @@ int corr_shape(corr_t h, int* n_in, int* n_chan, int* taps, int* n_int, int* n_i
 }
 
 long long corr_kernel_launches(corr_t h) { return h ? h->launches : 0; }
+
+int corr_gram_dev(corr_t h, const void* d_Q, int n_chan, int k_pitch, int K, int dtype, float* d_G, void* stream) {
+    if (!h) return fail(h, CORR_EINVAL, "NULL handle");
+    DeviceGuard g(h->dev);
+    if (!d_Q || !d_G || n_chan < 1 || K < 1 || (dtype != CORR_INT8 && dtype != CORR_FP8))
+        return fail(h, CORR_EINVAL, "bad argument");
+    GramArgs a{};
+    a.Q = d_Q;
+    a.n_chan = n_chan;
+    a.K = K;
+    a.k_pitch = k_pitch;
+    a.fp8 = dtype == CORR_FP8;
+    a.G = d_G;
+    a.status = h->d_status;
+    int rc;
+    {
+        Timed t_(h, 2, static_cast<cudaStream_t>(stream));
+        rc = launch_gram(a, static_cast<cudaStream_t>(stream));
+    }
+    if (rc != CORR_OK) return fail(h, rc, "gram: bad layout (k_pitch multiple of 128 bytes, 16-byte aligned Q)");
+    CK(cudaGetLastError());
+    return CORR_OK;
+}
+
+int corr_device_status(corr_t h, int* status) {
+    if (!h || !status) return fail(h, CORR_EINVAL, "NULL argument");
+    DeviceGuard g(h->dev);
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemset(h->d_status, 0, sizeof(int)));
+    return CORR_OK;
+}
 
 int corr_stage_times(corr_t h, double* ms, long long* counts, int n_stages) {
     if (!h) return fail(h, CORR_EINVAL, "NULL handle");

@@ -1,0 +1,98 @@
+"""Tensor-core X-engine (tcgen05 Gram matrices) against the exact oracle Gram.
+
+Inputs are seeded codes drawn on the host (never produced by the CUDA path):
+int8 codes carried as BF16 and e4m3 bytes.  With int8 codes every product is
+exact and FP32 sums are exact while partial sums stay below 2^24, which
+holds for K <= 1024 (1024 * 127^2 < 2^24): there the result must be
+bit-exact.  Longer sums and e4m3 are checked against the FP32 accumulation
+bound |G - G_exact| <= K * 2^-24 * sum_k |q_r q_s|.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import requant_oracle as rq  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_20640_gb300.build import build_library
+    build_library()
+
+
+def _corr():
+    from paper_2604_20640_gb300 import Correlator
+    return Correlator(4, 1, 64, 4, 16)
+
+
+def _bf16_bits(v):
+    return (np.asarray(v, np.float32).view(np.uint32) >> 16).astype(np.uint16)
+
+
+def _run_gram(c, Qbytes, n_chan, k_pitch, K, dtype):
+    Qd = torch.from_numpy(Qbytes).to(DEV)
+    G = torch.full((n_chan, 128, 128), float("nan"), dtype=torch.float32, device=DEV)
+    c.gram_dev(Qd, n_chan, k_pitch, K, dtype, G)
+    torch.cuda.synchronize()
+    assert c.device_status() == 0
+    return G.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("rows,K,k_pitch", [(128, 1024, 2048), (16, 1000, 2048), (100, 256, 512), (128, 64, 256)])
+def test_int8_gram_bit_exact(rows, K, k_pitch):
+    from paper_2604_20640_gb300 import CORR_INT8
+    rng = np.random.default_rng(rows + K)
+    n_chan = 6
+    codes = np.zeros((n_chan, 128, k_pitch // 2), np.int64)
+    codes[:, :rows, :K] = rng.integers(-127, 128, size=(n_chan, rows, K))
+    codes[:, :rows, K:] = rng.integers(-127, 128, size=(n_chan, rows, k_pitch // 2 - K))  # beyond K: ignored
+    Q = _bf16_bits(codes).view(np.uint8).reshape(n_chan, 128, k_pitch)
+    G = _run_gram(_corr(), Q, n_chan, k_pitch, K, CORR_INT8)
+    ref = rq.gram(codes[:, :, :K])
+    np.testing.assert_array_equal(G, ref.astype(np.float64))
+
+
+def test_int8_gram_long_sums_within_fp32_bound():
+    from paper_2604_20640_gb300 import CORR_INT8
+    rng = np.random.default_rng(7)
+    n_chan, K = 4, 4096
+    codes = rng.integers(-127, 128, size=(n_chan, 128, K))
+    codes[:, :, ::3] = 127                               # large positive sums
+    Q = _bf16_bits(codes).view(np.uint8).reshape(n_chan, 128, 2 * K)
+    G = _run_gram(_corr(), Q, n_chan, 2 * K, K, CORR_INT8)
+    ref = rq.gram(codes).astype(np.float64)
+    bound = K * 2.0 ** -24 * rq.gram(np.abs(codes)).astype(np.float64)
+    assert np.all(np.abs(G - ref) <= bound + 1e-9)
+
+
+def test_e4m3_gram_within_fp32_bound():
+    from paper_2604_20640_gb300 import CORR_FP8
+    rng = np.random.default_rng(9)
+    n_chan, K = 5, 2048
+    vals = rq.e4m3_round(rng.standard_normal((n_chan, 128, K)) * 40.0)
+    # encode grid values as bytes through the decode table
+    table = rq.e4m3_decode(np.arange(256, dtype=np.uint8))
+    lut = {float(v): i for i, v in enumerate(table) if not np.isnan(v)}
+    lut[0.0] = 0
+    Qb = np.vectorize(lambda v: lut[float(v)])(vals).astype(np.uint8)
+    G = _run_gram(_corr(), Qb, n_chan, K, K, CORR_FP8)
+    dec = rq.e4m3_decode(Qb)
+    ref = rq.gram(dec)
+    bound = K * 2.0 ** -24 * rq.gram(np.abs(dec))
+    assert np.all(np.abs(G - ref) <= bound + 1e-9)
+
+
+def test_gram_rejects_bad_layout():
+    from paper_2604_20640_gb300 import CorrError, CORR_INT8
+    c = _corr()
+    Q = torch.zeros((2, 128, 200), dtype=torch.uint8, device=DEV)
+    G = torch.zeros((2, 128, 128), dtype=torch.float32, device=DEV)
+    with pytest.raises(CorrError):
+        c.gram_dev(Q, 2, 200, 64, CORR_INT8, G)

@@ -33,6 +33,22 @@ def test_e4m3_matches_library_conversion():
     np.testing.assert_array_equal(rq.e4m3_round(x), ref)
 
 
+def test_e4m3_decode_matches_library_and_hand_values():
+    b = np.arange(256, dtype=np.uint8)
+    v = rq.e4m3_decode(b)
+    assert v[0x00] == 0.0 and v[0x38] == 1.0 and v[0x7E] == 448.0 and v[0x01] == 2.0 ** -9
+    assert v[0xB8] == -1.0 and np.isnan(v[0x7F]) and np.isnan(v[0xFF])
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("torch without float8")
+    ref = torch.from_numpy(b.copy()).view(torch.float8_e4m3fn).to(torch.float64).numpy()
+    ok = ~np.isnan(ref)
+    np.testing.assert_array_equal(v[ok], ref[ok])
+    assert np.all(np.isnan(v[~ok]))
+    # decode(round(x)) is idempotent on the grid
+    np.testing.assert_array_equal(rq.e4m3_round(v[ok]), v[ok])
+
+
 def test_gram_brute_force():
     rng = np.random.default_rng(1)
     Q = rng.integers(-127, 128, size=(2, 6, 9)).astype(np.int8)
