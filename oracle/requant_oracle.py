@@ -18,6 +18,13 @@ is the build's own; each reading is also listed in the design notes):
   the input/channel, g = 32 (int8) or 64 (e4m3).  The first integration
   takes P from its first min(n_int, 64) spectra; each later integration
   from the previous integration's autocorrelation R_aa[k].
+* The codes quantise the channelised voltages after the coarse delay but
+  before the fine-delay / instrument-phase factor of Eq. 1; that factor is
+  constant within an integration, so it multiplies the integrated sum,
+  R_ab = Q_a conj(Q_b) sigma_a sigma_b / n sum_s q_a conj(q_b) with
+  Q_a[k] = exp(j (2 pi k r_a / M - phi_a)).  In full precision the two
+  orders are the same; with requantisation only the noise realisation
+  differs.
 """
 
 from __future__ import annotations
@@ -98,8 +105,16 @@ def correlate_quantized(x: np.ndarray, n_chan: int, taps: int, n_int: int, tau=N
 
     Returns (R [n_out][n_chan][N][N], scales [n_out][N][n_chan]).
     """
-    V = fx.f_engine(x, n_chan, taps, tau, phi)            # [N][S][n_chan]
-    N, n_spec, _ = V.shape
+    x = np.asarray(x)
+    N = x.shape[0]
+    tau = np.zeros(N) if tau is None else np.asarray(tau, np.float64)
+    phi = np.zeros(N) if phi is None else np.asarray(phi, np.float64)
+    d, r = fx.split_delay(tau)
+    V = fx.f_engine(x, n_chan, taps, d.astype(np.float64), None)   # coarse delay only
+    M = 2 * n_chan
+    k = np.arange(n_chan)
+    rot = np.exp(1j * (2 * np.pi * k[None, :] * r[:, None] / M - phi[:, None]))   # [N][n_chan]
+    n_spec = V.shape[1]
     starts = list(range(0, n_spec - n_int + 1, n_int))
     if partial and n_spec % n_int:
         starts.append((n_spec // n_int) * n_int)
@@ -119,7 +134,8 @@ def correlate_quantized(x: np.ndarray, n_chan: int, taps: int, n_int: int, tau=N
         G = gram(stacked_rows(q_re, q_im) if dtype == "e4m3" else
                  stacked_rows(q_re.astype(np.int64), q_im.astype(np.int64)))
         C = visibilities_from_gram(G, N)                    # [n_chan][N][N]
-        R[i] = C * (sc.T[:, :, None] * sc.T[:, None, :]) / (s1 - s0)
+        ph = rot.T[:, :, None] * np.conj(rot.T[:, None, :])
+        R[i] = C * ph * (sc.T[:, :, None] * sc.T[:, None, :]) / (s1 - s0)
         S[i] = sc
         prev = R[i]
     return R, S

@@ -25,11 +25,17 @@ thread_local std::string g_create_error;
 
 struct Pipe {
     long long s_next = 0;     // next spectrum to channelise
-    long long s_xdone = 0;    // first spectrum not yet summed into a partial slot
+    long long s_xdone = 0;    // first spectrum not yet summed (or requantised)
     float2* V = nullptr;      // ring of channelised spectra
     float2* Z = nullptr;      // ring of FIR outputs (same capacity)
     int v_cap = 0;
     float* part = nullptr;    // [gpi][nt][32][n_chan]
+    // reduced-precision path (tensor-core X-engine)
+    uint8_t* Q = nullptr;     // [n_chan][128][q_pitch] codes of one integration
+    int q_pitch = 0;          // bytes per row (multiple of 128)
+    float* G = nullptr;       // [n_chan][128][128]
+    float* scale = nullptr;   // [n_in_pad][n_chan], fixed per integration
+    bool have_scale = false;  // false until the first integration's pre-pass
 };
 
 struct Slot {
@@ -49,8 +55,9 @@ struct Tables {
 };
 
 // Optional CUDA-event brackets around every kernel launch, per stage
-// (0 FIR, 1 FFT, 2 X-engine, 3 finalise, 4 flag).
-constexpr int kStages = 5;
+// (0 FIR, 1 FFT, 2 X-engine, 3 finalise, 4 flag, 5 requantise, 6 tensor-core
+// Gram).
+constexpr int kStages = 7;
 struct StageTimer {
     bool on = false;
     std::vector<cudaEvent_t> pool;
@@ -258,9 +265,21 @@ int alloc_pipe(corr_t h, Pipe& p) {
     long long cap = 1;
     while (cap * 2 * per_spec <= (32ull << 20) && cap < 4096) cap *= 2;
     while (cap < h->G) cap *= 2;
+    // the reduced-precision scale pre-pass reads the first 64 spectra from the ring
+    while (h->precision != CORR_FP32 && cap < 64) cap *= 2;
     p.v_cap = (int)cap;
     CK(cudaMalloc(&p.V, per_spec * (size_t)p.v_cap));
     CK(cudaMalloc(&p.Z, per_spec * (size_t)p.v_cap));
+    if (h->precision != CORR_FP32) {
+        const int eb = h->precision == CORR_FP8 ? 1 : 2;
+        p.q_pitch = (int)((((long long)h->n_int * eb) + 127) / 128 * 128);
+        const size_t qbytes = (size_t)h->n_chan * 128 * p.q_pitch;
+        CK(cudaMalloc(&p.Q, qbytes));
+        CK(cudaMemset(p.Q, 0, qbytes));
+        CK(cudaMalloc(&p.G, sizeof(float) * (size_t)h->n_chan * 128 * 128));
+        CK(cudaMalloc(&p.scale, sizeof(float) * (size_t)h->n_in_pad * h->n_chan));
+        p.have_scale = false;
+    }
     CK(cudaMalloc(&p.part, sizeof(float) * (size_t)h->gpi * h->nt * 32 * h->n_chan));
     return CORR_OK;
 }
@@ -346,38 +365,79 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
             p.s_next = s_end;
             progress = true;
         }
-        // Partial slots: group j covers [istart + jG, min(istart + (j+1)G, iend)).
         const bool closing = final && p.s_next == ready_end && p.s_next < iend;
         const long long s_limit = closing ? p.s_next : iend;
-        const int j_begin = (int)((p.s_xdone - istart) / h->G);
-        int j_end;
-        if (p.s_next >= iend) j_end = h->gpi;
-        else if (closing) j_end = (int)((p.s_next - istart + h->G - 1) / h->G);
-        else j_end = (int)((p.s_next - istart) / h->G);
-        if (j_end > j_begin) {
-            XArgs x{};
-            x.V = p.V;
-            x.v_origin = 0;
-            x.v_mask = p.v_cap - 1;
-            x.n_chan = h->n_chan;
-            x.n_in_pad = h->n_in_pad;
-            x.nt = h->nt;
-            x.int_start = istart;
-            x.int_end = iend;
-            x.s_limit = s_limit;
-            x.G = h->G;
-            x.j0 = j_begin;
-            x.n_groups = j_end - j_begin;
-            x.part = p.part;
-            {
-                Timed t_(h, 2, st);
-                launch_xengine(x, st);
+        int j_end = 0;
+        if (h->precision != CORR_FP32) {
+            // Requantise every channelised spectrum into the integration's Q.
+            // The first integration of a stream first fixes its scales from
+            // the mean power of its first min(n_int, 64) spectra.
+            if (!p.have_scale) {
+                const long long want = n_int < 64 ? n_int : 64;
+                const long long have = p.s_next - istart;
+                if (have >= want || (closing && have > 0)) {
+                    const int n = (int)(have < want ? have : want);
+                    launch_scale_from_ring(p.V, 0, p.v_cap - 1, istart, n, h->n_in, h->n_in_pad, h->n_chan,
+                                           h->precision == CORR_FP8 ? 64.f : 32.f, p.scale, st);
+                    ++h->launches;
+                    CK(cudaGetLastError());
+                    p.have_scale = true;
+                }
             }
-            CK(cudaGetLastError());
-            long long nx = istart + (long long)j_end * h->G;
-            if (nx > s_limit) nx = s_limit;
-            p.s_xdone = nx;
-            progress = true;
+            if (p.have_scale && p.s_next > p.s_xdone) {
+                RequantArgs r{};
+                r.V = p.V;
+                r.v_origin = 0;
+                r.v_mask = p.v_cap - 1;
+                r.scale = p.scale;
+                r.Q = p.Q;
+                r.k_pitch = p.q_pitch;
+                r.s_begin = p.s_xdone;
+                r.s_end = p.s_next;
+                r.int_start = istart;
+                r.n_in = h->n_in;
+                r.n_in_pad = h->n_in_pad;
+                r.n_chan = h->n_chan;
+                r.fp8 = h->precision == CORR_FP8;
+                {
+                    Timed t_(h, 5, st);
+                    launch_requant(r, st);
+                }
+                CK(cudaGetLastError());
+                p.s_xdone = p.s_next;
+                progress = true;
+            }
+        } else {
+            // Partial slots: group j covers [istart + jG, min(istart + (j+1)G, iend)).
+            const int j_begin = (int)((p.s_xdone - istart) / h->G);
+            if (p.s_next >= iend) j_end = h->gpi;
+            else if (closing) j_end = (int)((p.s_next - istart + h->G - 1) / h->G);
+            else j_end = (int)((p.s_next - istart) / h->G);
+            if (j_end > j_begin) {
+                XArgs x{};
+                x.V = p.V;
+                x.v_origin = 0;
+                x.v_mask = p.v_cap - 1;
+                x.n_chan = h->n_chan;
+                x.n_in_pad = h->n_in_pad;
+                x.nt = h->nt;
+                x.int_start = istart;
+                x.int_end = iend;
+                x.s_limit = s_limit;
+                x.G = h->G;
+                x.j0 = j_begin;
+                x.n_groups = j_end - j_begin;
+                x.part = p.part;
+                {
+                    Timed t_(h, 2, st);
+                    launch_xengine(x, st);
+                }
+                CK(cudaGetLastError());
+                long long nx = istart + (long long)j_end * h->G;
+                if (nx > s_limit) nx = s_limit;
+                p.s_xdone = nx;
+                progress = true;
+            }
         }
         if (p.s_next == iend && p.s_xdone == iend) {
             CKRET(sink(h, ctx, t, i, (int)n_int, h->gpi, st));
@@ -396,8 +456,53 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
 
 // The pipeline's spectra are U = 2Y without the fine-delay/phase rotation,
 // so R = Q_a conj(Q_b) sum U_a U_b^* / (4 count).
-int finalize_into(corr_t h, const Pipe& p, const Tables& t, float2* R, uint8_t* F, int count, int slots,
+int finalize_into(corr_t h, Pipe& p, const Tables& t, float2* R, uint8_t* F, int count, int slots,
                   cudaStream_t st) {
+    if (h->precision != CORR_FP32) {
+        // Tensor-core Gram of the integration's codes, then rescale and
+        // rotate; the autocorrelations fix the next integration's scales.
+        GramArgs g{};
+        g.Q = p.Q;
+        g.n_chan = h->n_chan;
+        g.K = count;
+        g.k_pitch = p.q_pitch;
+        g.fp8 = h->precision == CORR_FP8;
+        g.G = p.G;
+        g.status = h->d_status;
+        int rc;
+        {
+            Timed t_(h, 6, st);
+            rc = launch_gram(g, st);
+        }
+        if (rc != CORR_OK) return fail(h, rc, "tensor-core Gram launch failed");
+        CK(cudaGetLastError());
+        FinQArgs f{};
+        f.G = p.G;
+        f.scale = p.scale;
+        f.rot = t.rot;
+        f.n_chan = h->n_chan;
+        f.n_in = h->n_in;
+        f.count = count;
+        f.fp8 = g.fp8;
+        f.R = R;
+        {
+            Timed t_(h, 3, st);
+            launch_finalize_q(f, st);
+        }
+        CK(cudaGetLastError());
+        launch_scale_from_vis(R, h->n_in, h->n_in_pad, h->n_chan, g.fp8 ? 64.f : 32.f, p.scale, st);
+        ++h->launches;
+        CK(cudaGetLastError());
+        if (F) {
+            const int w = h->flag_window < h->n_chan ? h->flag_window : h->n_chan;
+            {
+                Timed t_(h, 4, st);
+                launch_mad_flags(R, F, 1, h->n_chan, h->n_in, w, (float)h->flag_sigma, st);
+            }
+            CK(cudaGetLastError());
+        }
+        return CORR_OK;
+    }
     FinArgs f{};
     f.part = p.part;
     f.rot = t.rot;
@@ -613,6 +718,9 @@ int pop_results(corr_t h, std::deque<int>& q, bool vis, void* out, int max_int, 
 void free_pipe(Pipe& p) {
     if (p.V) cudaFree(p.V);
     if (p.Z) cudaFree(p.Z);
+    if (p.Q) cudaFree(p.Q);
+    if (p.G) cudaFree(p.G);
+    if (p.scale) cudaFree(p.scale);
     if (p.part) cudaFree(p.part);
     p = Pipe{};
 }
@@ -747,7 +855,9 @@ int corr_set_option(corr_t h, const char* key, double v) {
         if (h->stream_alloc) return fail(h, CORR_ESTATE, "chunk must be set before buffers exist");
         h->chunk = (long long)v;
     } else if (k == "precision") {
-        if (v != CORR_FP32) return fail(h, CORR_EINVAL, "precision: only CORR_FP32 in this build");
+        if (v != CORR_FP32 && v != CORR_INT8 && v != CORR_FP8) return fail(h, CORR_EINVAL, "precision: 0, 1 or 2");
+        if (v != CORR_FP32 && h->n_in > 64) return fail(h, CORR_EINVAL, "reduced precision needs n_in <= 64");
+        if (h->stream_alloc || h->pd.V) return fail(h, CORR_ESTATE, "precision must be set before buffers exist");
         h->precision = (int)v;
     } else if (k == "stage_timing") {
         h->timer.on = v != 0;
@@ -819,6 +929,7 @@ int corr_reset(corr_t h) {
     h->stage_base = h->stage_len = 0;
     h->n_pushed = 0;
     h->ps.s_next = h->ps.s_xdone = 0;
+    h->ps.have_scale = false;
     h->q_vis.clear();
     h->q_flag.clear();
     for (Slot& s : h->slots) s.in_vis = s.in_flag = false;
@@ -861,6 +972,7 @@ int corr_run_dev(corr_t h, const int8_t* d_samples, size_t n_samples, size_t str
     if (need > max_int) return fail(h, CORR_EINVAL, "max_int too small for the stream");
     CKRET(alloc_pipe(h, h->pd));
     h->pd.s_next = h->pd.s_xdone = 0;
+    h->pd.have_scale = false;
     StreamView sv;
     sv.x = d_samples;
     sv.stride = (long long)stride;
