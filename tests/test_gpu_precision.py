@@ -59,10 +59,11 @@ def test_precision_run_matches_oracle(prec, name, n_ant, n_chan, n_int):
     assert np.abs(rho_g - rho_o).max() < 5e-3
     Rq, _ = rq.correlate_quantized(x, n_chan, 4, n_int, tau, phi, dtype=name)
     assert np.abs(rho_g - fx.normalised_coefficients(Rq)).max() < 1e-3
-    # autocorrelations (powers) agree with the full-precision oracle to the
-    # quantisation noise level
-    da = np.einsum('ikaa->ika', Rg).real / np.einsum('ikaa->ika', Ro).real
-    assert np.abs(da - 1).max() < 0.02
+    # autocorrelation powers follow the emulated requantisation closely (the
+    # first integration's scales come from 64 spectra that include the filter
+    # bank's start-up, so its powers sit a few percent below full precision)
+    da = np.einsum('ikaa->ika', Rg).real / np.einsum('ikaa->ika', Rq).real
+    assert np.abs(da - 1).max() < 2e-3
 
 
 def test_precision_streaming_chunking_is_bit_identical():
@@ -72,13 +73,14 @@ def test_precision_streaming_chunking_is_bit_identical():
     S = M * (n_int * 2 + 37) + 11
     x, tau, phi = _stream(n_ant, 2, S, seed=5)
     outs = []
-    for sizes in ([S], [1000, 7, 33333] + [S - 41340]):
+    for sizes in ([S], [1000, 7, 33333] + [S - 34340]):
         c = Correlator(n_ant, 2, n_chan, 4, n_int, precision=1, chunk=5000)
         c.set_delays(tau, phi)
         pos = 0
         for n in sizes:
             c.push(x[:, pos:pos + n])
             pos += n
+        assert pos == S
         c.flush()
         outs.append((c.get_vis(), c.get_flags()))
     assert np.array_equal(outs[0][0], outs[1][0])
