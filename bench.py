@@ -40,6 +40,9 @@ WORKLOADS = {
                     "MAD sigma 5 / 64 ch"),
     "c1": dict(n_ant=4, n_pol=1, n_chan=1024, taps=4, n_int=512, samples=1 << 22, chunk=1 << 22,
                desc="4 ant x 1 pol int8 real, 2^22 samples/input, 4-tap PFB, 1024 ch, n_int 512"),
+    "c3": dict(n_ant=32, n_pol=2, n_chan=1024, taps=4, n_int=4096, samples=1 << 26, chunk=1 << 22,
+               desc="32 ant x 2 pol int8 real, 2^26 samples/input (4 GiB), 4-tap PFB, 1024 ch, n_int 4096, "
+                    "requantised to int8 (tensor-core X, BF16 MMA) vs the plain FP32 path"),
 }
 
 # Stages reported by corr_stage_times, their kernels, and the algorithmic bytes
@@ -47,16 +50,22 @@ WORKLOADS = {
 #   FIR  reads 1 B int8, writes z = (y_a, y_b) as FP32: 4 B;
 #   FFT  reads z (4 B) and writes one complex64 per channel per input (4 B);
 #   X    reads the channelised spectra (4 B); finalise / flag: per integration.
-STAGES = ["fir", "fft", "xengine", "finalize", "flag"]
-KERNELS = {"fir": "fir_kernel<4>", "fft": "fft_kernel<8192,false>", "xengine": "xengine_small_kernel<2>",
-           "finalize": "finalize_kernel", "flag": "mad_flag_kernel"}
-BYTES_PER_SAMPLE = {"fir": 5.0, "fft": 8.0, "xengine": 4.0, "finalize": 0.0, "flag": 0.0}
+#   requant reads the spectra (4 B) and writes one code per component (1 B
+#   e4m3, 2 B int8-as-BF16); the tensor-core Gram reads the codes.
+STAGES = ["fir", "fft", "xengine", "finalize", "flag", "requant", "gram"]
+KERNELS = {"fir": "fir_kernel<4>", "fft": "fft_kernel<M,false>", "xengine": "xengine_kernel",
+           "finalize": "finalize_kernel", "flag": "mad_flag_kernel", "requant": "requant_kernel",
+           "gram": "gram_kernel (tcgen05)"}
+BYTES_PER_SAMPLE = {"fir": 5.0, "fft": 8.0, "xengine": 4.0, "finalize": 0.0, "flag": 0.0, "requant": 6.0,
+                    "gram": 2.0}
 
 
 def _spec(wl, rank, samples):
-    from fxsynth import config_c1, config_c2
+    from fxsynth import config_c1, config_c2, config_c3
     if wl == "c2":
         return config_c2(seed=2000 + rank, n_samples=samples, M=2 * WORKLOADS[wl]["n_chan"])
+    if wl == "c3":
+        return config_c3(seed=3000 + rank, n_samples=samples)
     return config_c1(seed=1000 + rank, n_samples=samples)
 
 
@@ -113,32 +122,41 @@ def _peaks():
         return {}
 
 
-def cpu_baseline(wl, n_integrations=4):
+def cpu_baseline(wl, n_integrations=None):
     """Time the FP64 oracle, as it stands, on a bounded sample of the workload:
-    the first ``n_integrations`` integrations of one stream, one thread."""
+    the first integrations of one stream (about 10-30 s of work), one thread."""
     W = WORKLOADS[wl]
     M = 2 * W["n_chan"]
+    if n_integrations is None:
+        n_integrations = 4
     samples = M * W["n_int"] * n_integrations
+    partial = False
+    if wl == "c3":
+        # 64-input integrations take minutes in the oracle: time 256 spectra
+        # (one partial integration; the work per sample is the same)
+        samples, partial = M * 256, True
     code = (
         "import sys, time, json, numpy as np\n"
         "sys.path.insert(0, %r)\n"
-        "from fxsynth import config_c1, config_c2, make_stream\n"
+        "from fxsynth import config_c1, config_c2, config_c3, make_stream\n"
         "from oracle import fx_oracle as fx\n"
-        "spec = (config_c2(seed=2000, n_samples=%d, M=%d) if %r == 'c2' else config_c1(seed=1000, n_samples=%d))\n"
+        "wl = %r\n"
+        "spec = (config_c2(seed=2000, n_samples=%d, M=%d) if wl == 'c2' else\n"
+        "        config_c3(seed=3000, n_samples=%d) if wl == 'c3' else config_c1(seed=1000, n_samples=%d))\n"
         "x = make_stream(spec)\n"
         "t0 = time.perf_counter()\n"
-        "R, F, T = fx.correlate(x, %d, %d, %d, spec.tau, spec.phi)\n"
+        "R, F, T = fx.correlate(x, %d, %d, %d, spec.tau, spec.phi, partial=%r)\n"
         "dt = time.perf_counter() - t0\n"
         "print(json.dumps({'seconds': dt, 'bytes': int(x.size), 'n_int': int(R.shape[0])}))\n"
-    ) % (ROOT, samples, M, wl, samples, W["n_chan"], W["taps"], W["n_int"])
+    ) % (ROOT, wl, samples, M, samples, samples, W["n_chan"], W["taps"], W["n_int"], partial)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
         return {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else "failed"}
     d = json.loads(r.stdout.strip().splitlines()[-1])
     return {"value": d["bytes"] / d["seconds"] / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": "first %d integrations of one stream (%d MiB int8), FP64 numpy oracle, 1 thread, %.1f s"
-                      % (d["n_int"], d["bytes"] >> 20, d["seconds"])}
+            "sample": "first %d spectra of one stream (%d MiB int8), FP64 numpy oracle, 1 thread, %.1f s"
+                      % (samples // M, d["bytes"] >> 20, d["seconds"])}
 
 
 def run_reference(args, rank, world):
@@ -195,6 +213,9 @@ def main():
     ap.add_argument("--samples", type=int, default=0, help="override samples per input")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--precision", type=int, default=None,
+                    help="0 FP32 CUDA-core X, 1 int8 / 2 e4m3 tensor-core X (default: FP32, int8 for c3)")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -223,7 +244,8 @@ def main():
     n_in = W["n_ant"] * W["n_pol"]
     spec = _spec(args.workload, rank, S)
     x = make_stream_torch(spec, device=dev)
-    c = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"])
+    prec = args.precision if args.precision is not None else (1 if args.workload == "c3" else 0)
+    c = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"], precision=prec)
     c.set_delays(spec.tau, spec.phi)
     n_intg = c.n_integrations(S)
     vis = torch.empty((n_intg, W["n_chan"], n_in, n_in), dtype=torch.complex64, device=dev)
@@ -258,10 +280,35 @@ def main():
     bytes_step = n_in * S
     value = world * bytes_step / (ms * 1e-3) / 1e9
 
+    # ---- the plain FP32 path on the same stream (the metric's denominator) ----
+    plain = None
+    if prec != 0 and not args.no_plain:
+        cp = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"])
+        cp.set_delays(spec.tau, spec.phi)
+        for _ in range(max(1, args.warmup)):
+            cp.run_dev(x, vis, flags)
+        torch.cuda.synchronize(dev)
+        barrier()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(args.steps):
+            cp.run_dev(x, vis, flags)
+        p1.record(stream)
+        torch.cuda.synchronize(dev)
+        pms = p0.elapsed_time(p1) / args.steps
+        if world > 1:
+            t = torch.tensor([pms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            pms = float(t.item())
+        pval = world * bytes_step / (pms * 1e-3) / 1e9
+        plain = {"value": pval, "ms_per_step": pms, "ratio": value / pval}
+        cp.close()
+
     # ---- end to end through the public host API ----
     e2e = None
     if not args.no_e2e:
-        ce = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"], chunk=W["chunk"])
+        ce = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"], chunk=W["chunk"],
+                        precision=prec)
         ce.set_delays(spec.tau, spec.phi)
         host = torch.empty((n_in, S), dtype=torch.int8, pin_memory=True)
         host.copy_(x)
@@ -302,11 +349,14 @@ def main():
     hbm = hbm or 6800.0
     total_stage = sum(stage_ms) or 1.0
     share = {k: stage_ms[i] / total_stage for i, k in enumerate(STAGES)}
-    dom = max((k for k in STAGES if BYTES_PER_SAMPLE[k] > 0), key=lambda k: share[k])
+    bps = dict(BYTES_PER_SAMPLE)
+    if prec == 2:
+        bps.update(requant=5.0, gram=1.0)
+    dom = max((k for k in STAGES if bps[k] > 0), key=lambda k: share[k])
     di = STAGES.index(dom)
     n_spec = S // (2 * W["n_chan"])
     samples_timed = args.steps * n_spec * 2 * W["n_chan"] * n_in
-    bytes_per_launch = BYTES_PER_SAMPLE[dom] * samples_timed / max(1, stage_n[di])
+    bytes_per_launch = bps[dom] * samples_timed / max(1, stage_n[di])
     avg_ms = stage_ms[di] / max(1, stage_n[di])
     achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
     roofline = {"kernel": KERNELS[dom], "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -320,11 +370,15 @@ def main():
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload + ": " + W["desc"], "path": "plain FP32 (CUDA-core X)",
+            "config": {"workload": args.workload + ": " + W["desc"],
+                       "path": ["plain FP32 (CUDA-core X)", "int8 requantised, tcgen05 X (BF16 MMA)",
+                                "e4m3 requantised, tcgen05 X"][prec],
                        "samples_per_input": S, "l2": "inputs (%d MiB/step) larger than L2" % (bytes_step >> 20),
                        "parallelism": "replicas" if world > 1 else "single"},
             "gpu_launches": launches, "clocks": clk, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
         }
+        if plain is not None:
+            out["plain_fp32"] = plain
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()

@@ -85,7 +85,14 @@ const char* corr_last_error(corr_t h);
  *                 (min(window, n_chan) is used)
  *   "max_delay"   (samples, default 4096)     bound on |coarse delay|
  *   "chunk"       (samples/input, default 1<<23) largest device batch
- *   "precision"   (CORR_FP32 / CORR_INT8 / CORR_FP8, default FP32)
+ *   "precision"   (CORR_FP32 / CORR_INT8 / CORR_FP8, default FP32): FP32
+ *                 CUDA-core X-engine, or channelised voltages requantised to
+ *                 int8 (carried as BF16) / e4m3 with one scale per (input,
+ *                 channel) fixed per integration, correlated on tcgen05
+ *                 tensor cores (n_in <= 64).  Scales: first integration from
+ *                 the mean power of its first min(n_int, 64) spectra
+ *                 (sigma = sqrt(P/2)/g, g = 32 int8, 64 e4m3), later ones
+ *                 from the previous integration's autocorrelations.
  *   "result_slots" (default 8)               pinned result FIFO depth (grows)
  *   "stage_timing" (0/1, default 0; may change at any time)  per-stage events
  */
@@ -216,7 +223,8 @@ long long corr_kernel_launches(corr_t h);
  * With option "stage_timing" = 1 every kernel launch is bracketed by CUDA
  * events on its own stream.  This call waits for those events and returns,
  * for stages 0 FIR, 1 FFT (the two F-engine kernels), 2 X-engine,
- * 3 finalise, 4 flagging (first n_stages entries), the milliseconds and
+ * 3 finalise, 4 flagging, 5 requantise, 6 tensor-core Gram (first n_stages
+ * entries), the milliseconds and
  * launch counts accumulated since the previous call, then clears them.
  * ms / counts may be NULL.
  */

@@ -291,10 +291,11 @@ class Correlator:
         return st.value
 
     def stage_times(self):
-        """(ms, counts) per stage (FIR, FFT, X, finalise, flag) since the last call."""
-        ms = (ctypes.c_double * 5)()
-        n = (ctypes.c_longlong * 5)()
-        self._check(self._L.corr_stage_times(self._h, ms, n, 5))
+        """(ms, counts) per stage (FIR, FFT, X, finalise, flag, requantise, tensor-core
+        Gram) since the last call."""
+        ms = (ctypes.c_double * 7)()
+        n = (ctypes.c_longlong * 7)()
+        self._check(self._L.corr_stage_times(self._h, ms, n, 7))
         return list(ms), list(n)
 
     @property

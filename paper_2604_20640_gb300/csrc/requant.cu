@@ -6,8 +6,9 @@
 // holds Im U_a / sigma_a[k], t the spectrum index inside the integration:
 // int8 codes (round half to even, saturate at +-127) carried as BF16, which
 // holds them exactly, or e4m3 (satfinite) bytes.  A CTA
-// transposes one channel x 64 spectra through shared memory so that both
-// the reads (inputs contiguous) and the writes (time contiguous) coalesce.
+// covers one channel x 64 spectra; a thread owns one input and a run of
+// spectra, so reads coalesce across inputs and every row gets whole
+// 32-byte sectors of codes.
 // The scales are fixed for a whole integration: the first integration of a
 // stream takes them from the mean power of its first spectra, later ones
 // from the previous integration's autocorrelations.
@@ -37,65 +38,71 @@ __device__ __forceinline__ uint16_t code_bf16(uint8_t q) {
     return __bfloat16_as_ushort(__float2bfloat16_rn((float)(int8_t)q));
 }
 
+// One thread: input a, a run of RUN consecutive spectra (one 32-byte sector
+// of codes per row: 16 BF16 or 32 e4m3).  Reads are coalesced across inputs,
+// each row's codes are written with two 16-byte stores.
+template <bool FP8>
 __global__ void __launch_bounds__(256) requant_kernel(const RequantArgs A) {
-    __shared__ __align__(16) uint8_t T[128][kTileS];
+    constexpr int RUN = FP8 ? 32 : 16;
     const int k = blockIdx.x;
-    const long long s0 = A.s_begin + (long long)blockIdx.y * kTileS;
-    int ns = (int)(A.s_end - s0);
-    if (ns > kTileS) ns = kTileS;
     const int N = A.n_in;
-    for (int idx = threadIdx.x; idx < N * kTileS; idx += blockDim.x) {
-        const int a = idx % N, i = idx / N;
-        if (i >= ns) continue;
-        const long long slot = (s0 + i - A.v_origin) & A.v_mask;
-        const float2 u = A.V[((size_t)slot * A.n_chan + k) * A.n_in_pad + a];
+    const int runs = kTileS / RUN;
+    const long long s0 = A.s_begin + (long long)blockIdx.y * kTileS;
+    for (int idx = threadIdx.x; idx < N * runs; idx += blockDim.x) {
+        const int a = idx % N, r = idx / N;
+        const long long sb = s0 + (long long)r * RUN;
+        if (sb >= A.s_end) continue;
+        const int ns = (int)((A.s_end - sb) < RUN ? (A.s_end - sb) : RUN);
         const float inv = 1.0f / A.scale[(size_t)a * A.n_chan + k];
-        const float xr = u.x * inv, xi = u.y * inv;
-        T[a][i] = A.fp8 ? q_e4m3(xr) : q_int8(xr);
-        T[N + a][i] = A.fp8 ? q_e4m3(xi) : q_int8(xi);
-    }
-    __syncthreads();
-    const long long col0 = s0 - A.int_start;
-    if (A.fp8) {
-        uint8_t* Qk = A.Q + (size_t)k * 128 * A.k_pitch;
-        if ((col0 & 15) == 0) {
-            const int chunks = (ns + 15) / 16;
-            for (int idx = threadIdx.x; idx < 2 * N * chunks; idx += blockDim.x) {
-                const int r = idx / chunks, c = idx % chunks;
-                uint8_t* dst = Qk + (size_t)r * A.k_pitch + col0 + 16 * c;
-                if (16 * c + 16 <= ns) {
-                    *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(&T[r][16 * c]);
-                } else {
-                    for (int j = 16 * c; j < ns; ++j) Qk[(size_t)r * A.k_pitch + col0 + j] = T[r][j];
-                }
+        // codes packed little-endian into 8 words per row (one 32-byte sector)
+        uint32_t wr[8], wi[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            wr[j] = 0u;
+            wi[j] = 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < RUN; ++i) {
+            float2 u = make_float2(0.f, 0.f);
+            if (i < ns) {
+                const long long slot = (sb + i - A.v_origin) & A.v_mask;
+                u = A.V[((size_t)slot * A.n_chan + k) * A.n_in_pad + a];
             }
-        } else {
-            for (int idx = threadIdx.x; idx < 2 * N * ns; idx += blockDim.x) {
-                const int r = idx / ns, j = idx % ns;
-                Qk[(size_t)r * A.k_pitch + col0 + j] = T[r][j];
+            uint32_t cr, ci;
+            if constexpr (FP8) {
+                cr = q_e4m3(u.x * inv);
+                ci = q_e4m3(u.y * inv);
+                wr[i / 4] |= cr << (8 * (i % 4));
+                wi[i / 4] |= ci << (8 * (i % 4));
+            } else {
+                cr = code_bf16(q_int8(u.x * inv));
+                ci = code_bf16(q_int8(u.y * inv));
+                wr[i / 2] |= cr << (16 * (i % 2));
+                wi[i / 2] |= ci << (16 * (i % 2));
             }
         }
-    } else {
-        uint16_t* Qk = reinterpret_cast<uint16_t*>(A.Q + (size_t)k * 128 * A.k_pitch);
-        const int pitch = A.k_pitch / 2;
-        if ((col0 & 7) == 0) {
-            const int chunks = (ns + 7) / 8;
-            for (int idx = threadIdx.x; idx < 2 * N * chunks; idx += blockDim.x) {
-                const int r = idx / chunks, c = idx % chunks;
-                uint16_t* dst = Qk + (size_t)r * pitch + col0 + 8 * c;
-                if (8 * c + 8 <= ns) {
-                    uint16_t v[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) v[j] = code_bf16(T[r][8 * c + j]);
-                    *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(v);
-                } else {
-                    for (int j = 8 * c; j < ns; ++j) Qk[(size_t)r * pitch + col0 + j] = code_bf16(T[r][j]);
-                }
-            }
+        constexpr int EB = FP8 ? 1 : 2;
+        const long long col = sb - A.int_start;
+        uint8_t* row_re = A.Q + ((size_t)k * 128 + a) * A.k_pitch + col * EB;
+        uint8_t* row_im = A.Q + ((size_t)k * 128 + N + a) * A.k_pitch + col * EB;
+        if (ns == RUN && ((col * EB) & 15) == 0) {
+            uint4* dr = reinterpret_cast<uint4*>(row_re);
+            uint4* di = reinterpret_cast<uint4*>(row_im);
+            dr[0] = make_uint4(wr[0], wr[1], wr[2], wr[3]);
+            dr[1] = make_uint4(wr[4], wr[5], wr[6], wr[7]);
+            di[0] = make_uint4(wi[0], wi[1], wi[2], wi[3]);
+            di[1] = make_uint4(wi[4], wi[5], wi[6], wi[7]);
         } else {
-            for (int idx = threadIdx.x; idx < 2 * N * ns; idx += blockDim.x) {
-                const int r = idx / ns, j = idx % ns;
-                Qk[(size_t)r * pitch + col0 + j] = code_bf16(T[r][j]);
+#pragma unroll
+            for (int i = 0; i < RUN; ++i) {
+                if (i < ns) {
+#pragma unroll
+                    for (int e = 0; e < EB; ++e) {
+                        const int bitpos = 8 * (i * EB + e);
+                        row_re[i * EB + e] = (uint8_t)(wr[bitpos / 32] >> (bitpos % 32));
+                        row_im[i * EB + e] = (uint8_t)(wi[bitpos / 32] >> (bitpos % 32));
+                    }
+                }
             }
         }
     }
@@ -166,7 +173,8 @@ void launch_requant(const RequantArgs& a, cudaStream_t st) {
     const long long n = a.s_end - a.s_begin;
     if (n <= 0) return;
     dim3 grid((unsigned)a.n_chan, (unsigned)((n + kTileS - 1) / kTileS));
-    requant_kernel<<<grid, 256, 0, st>>>(a);
+    if (a.fp8) requant_kernel<true><<<grid, 256, 0, st>>>(a);
+    else requant_kernel<false><<<grid, 256, 0, st>>>(a);
 }
 
 void launch_scale_from_ring(const float2* V, long long v_origin, long long v_mask, long long s0, int n, int n_in,
