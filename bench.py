@@ -40,6 +40,11 @@ WORKLOADS = {
                     "MAD sigma 5 / 64 ch"),
     "c1": dict(n_ant=4, n_pol=1, n_chan=1024, taps=4, n_int=512, samples=1 << 22, chunk=1 << 22,
                desc="4 ant x 1 pol int8 real, 2^22 samples/input, 4-tap PFB, 1024 ch, n_int 512"),
+    "c4": dict(n_ant=0, n_pol=2, n_chan=0, taps=4, n_int=0, samples=1 << 24, chunk=1 << 22,
+               desc="8 sub-array streams (n_ant, n_chan, n_int) = " + str([(4, 512, 4096), (6, 1024, 2048),
+                    (8, 2048, 1024), (12, 4096, 512), (16, 8192, 256), (24, 512, 1024), (32, 1024, 512),
+                    (32, 2048, 256)]) + " x 2 pols, 2^24 int8 samples/input (4.5 GB), one captured graph, "
+                    "autotuned rings vs separate ungraphed runs"),
     "c3": dict(n_ant=32, n_pol=2, n_chan=1024, taps=4, n_int=4096, samples=1 << 26, chunk=1 << 22,
                desc="32 ant x 2 pol int8 real, 2^26 samples/input (4 GiB), 4-tap PFB, 1024 ch, n_int 4096, "
                     "requantised to int8 (tensor-core X, BF16 MMA) vs the plain FP32 path"),
@@ -203,6 +208,101 @@ def run_reference(args, rank, world):
     print(json.dumps(out))
 
 
+TENSOR_MIN_INPUTS = 24
+
+
+def run_batched(args, rank, world, local):
+    """Eight uneven sub-array streams: one captured graph (autotuned) vs the
+    same streams run one after another without a graph (default tuning)."""
+    import tempfile
+    import torch
+    import torch.distributed as dist
+    from paper_2604_20640_gb300 import Correlator, Group
+    from fxsynth import config_c4_streams
+    from fxsynth.streams_torch import make_stream_torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    S = args.samples or WORKLOADS["c4"]["samples"]
+    specs = config_c4_streams(seed=4000 + 100 * rank, n_samples=S)
+    from fxsynth.streams import C4_SHAPES
+    members, plains, xs, vis, flags = [], [], [], [], []
+    for spec, (na, nc, ni) in zip(specs, C4_SHAPES):
+        # chosen form: tensor-core X-engine (int8 codes) once N is large
+        prec = 1 if 2 * na >= TENSOR_MIN_INPUTS else 0
+        c = Correlator(na, 2, nc, 4, ni, precision=prec)
+        c.set_delays(spec.tau, spec.phi)
+        cp = Correlator(na, 2, nc, 4, ni)
+        cp.set_delays(spec.tau, spec.phi)
+        x = make_stream_torch(spec, device=dev)
+        n = max(1, c.n_integrations(S))
+        members.append(c)
+        plains.append(cp)
+        xs.append(x)
+        vis.append(torch.empty((n, nc, 2 * na, 2 * na), dtype=torch.complex64, device=dev))
+        flags.append(torch.empty((n, nc, 2 * na, 2 * na), dtype=torch.uint8, device=dev))
+    bytes_step = sum(x.numel() for x in xs)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        if world > 1:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # plain: one stream after another, no graph, default tuning
+    def plain():
+        for c, x, v, f in zip(plains, xs, vis, flags):
+            c.run_dev(x, v, f)
+    ms_plain = timed(plain, args.steps)
+    # chosen: autotuned rings, one captured graph of all eight pipelines
+    cache = os.path.join(tempfile.gettempdir(), "corr_tune_%d.txt" % os.getpid())
+    for c, x in zip(members, xs):
+        c.autotune(x, cache)
+    g = Group(members)
+    g.run_dev(xs, vis, flags)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    l0 = g._L.corr_kernel_launches(g._h)
+    ms = timed(lambda: g.run_dev(xs, vis, flags), args.steps)
+    launches = (g._L.corr_kernel_launches(g._h) - l0) * args.steps // (args.steps + args.warmup)
+    clk = clocks.stop()
+    value = world * bytes_step / (ms * 1e-3) / 1e9
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "c4: " + WORKLOADS["c4"]["desc"], "samples_per_input": S,
+                       "l2": "inputs (%d MiB/step) larger than L2" % (bytes_step >> 20),
+                       "tuning": [c.tuning() for c in members],
+                       "path": "one captured graph; tensor-core X (int8) for members with >= %d inputs, "
+                               "CUDA-core FP32 X below" % TENSOR_MIN_INPUTS},
+            "gpu_launches": int(launches), "clocks": clk,
+            "plain_fp32": {"value": world * bytes_step / (ms_plain * 1e-3) / 1e9, "ms_per_step": ms_plain,
+                           "ratio": ms_plain / ms},
+        }
+        print(json.dumps(out))
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -223,6 +323,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "c4":
+        run_batched(args, rank, world, local)
         return
 
     import torch

@@ -95,6 +95,9 @@ const char* corr_last_error(corr_t h);
  *                 from the previous integration's autocorrelations.
  *   "result_slots" (default 8)               pinned result FIFO depth (grows)
  *   "stage_timing" (0/1, default 0; may change at any time)  per-stage events
+ *   "ring_mb"      (1..4096, default 32)  MiB of each on-device spectrum ring
+ *   "fir_spt"      (0 = automatic, 1..256; may change at any time)
+ *                  spectra each FIR thread filters
  */
 int corr_set_option(corr_t h, const char* key, double value);
 
@@ -210,6 +213,37 @@ int corr_gram_dev(corr_t h, const void* d_Q, int n_chan, int k_pitch, int K, int
  * status word (CORR_OK or CORR_ETIMEDOUT from a bounded wait) and clear it.
  */
 int corr_device_status(corr_t h, int* status);
+
+/*
+ * Batched sub-array streams.  corr_group_create bundles n (<= 64) existing
+ * handles (their shapes may all differ) into a group handle; the members
+ * stay owned by the caller and must outlive the group.
+ * corr_group_run_dev runs corr_run_dev for every member (stream i:
+ * d_samples[i], n_samples[i], strides[i] -> d_vis[i], d_flags[i] (d_flags may
+ * be NULL), complete integrations only) as parallel branches of one CUDA
+ * graph, launched on `stream`; n_out[i] (may be NULL) receives the
+ * integrations written.  The first call (and any call whose pointers or
+ * sizes differ from the last capture) runs each member once uncaptured,
+ * then captures the graph; later calls replay it.  Do not run members on
+ * their own while a group call may still be executing.
+ */
+int corr_group_create(corr_t* group, const corr_t* members, int n);
+int corr_group_run_dev(corr_t group, const int8_t* const* d_samples, const size_t* n_samples,
+                       const size_t* strides, float* const* d_vis, uint8_t* const* d_flags,
+                       const int* max_int, int* n_out, void* stream);
+
+/*
+ * corr_autotune -- pick the ring capacity ("ring_mb" 16/32/64) and the FIR
+ * run length ("fir_spt" auto/4/8/16) of a handle by timing corr_run_dev on
+ * up to two integrations of a device sample (results do not depend on
+ * either choice).  cache_path (may be NULL) is a text file of
+ * "gpu n_in n_chan taps n_int precision ring_mb fir_spt" lines: a matching
+ * line is applied without timing, a new choice is appended.
+ * corr_get_tuning reports the current values.
+ */
+int corr_autotune(corr_t h, const int8_t* d_samples, size_t n_samples, size_t input_stride,
+                  const char* cache_path, void* stream);
+int corr_get_tuning(corr_t h, int* ring_mb, int* fir_spt);
 
 /* Shapes of a handle: n_in, n_chan, taps, n_int, n_in_pad (any may be NULL). */
 int corr_shape(corr_t h, int* n_in, int* n_chan, int* taps, int* n_int, int* n_in_pad);

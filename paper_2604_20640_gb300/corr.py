@@ -33,7 +33,8 @@ EXPORTED = [
     "corr_push", "corr_push_dev", "corr_flush", "corr_reset", "corr_get_vis", "corr_get_flags",
     "corr_pending", "corr_run_dev", "corr_fengine_dev", "corr_xengine_dev", "corr_flag_dev",
     "corr_shape", "corr_kernel_launches", "corr_stage_times", "corr_xengine_noalloc",
-    "corr_gram_dev", "corr_device_status",
+    "corr_gram_dev", "corr_device_status", "corr_group_create", "corr_group_run_dev", "corr_autotune",
+    "corr_get_tuning",
 ]
 
 
@@ -83,6 +84,10 @@ def load_library(path: str = LIB_PATH):
         "corr_xengine_noalloc": (_i, [_vp, _i, _i, _i, _vp, _vp]),
         "corr_gram_dev": (_i, [_vp, _vp, _i, _i, _i, _i, _vp, _vp]),
         "corr_device_status": (_i, [_vp, ctypes.POINTER(_i)]),
+        "corr_group_create": (_i, [ctypes.POINTER(_vp), _vp, _i]),
+        "corr_group_run_dev": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "corr_autotune": (_i, [_vp, _vp, _sz, _sz, ctypes.c_char_p, _vp]),
+        "corr_get_tuning": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -108,6 +113,46 @@ def _dev_ptr(t, dtype_name: str):
     if not t.is_contiguous() and dtype_name != "samples":
         raise CorrError(CORR_EINVAL, "device buffer must be contiguous")
     return t.data_ptr()
+
+
+class Group:
+    """Batched sub-array streams run as one captured CUDA graph."""
+
+    def __init__(self, members):
+        self._L = load_library()
+        self.members = list(members)
+        arr = (_vp * len(self.members))(*[m._h.value for m in self.members])
+        h = _vp()
+        rc = self._L.corr_group_create(ctypes.byref(h), arr, len(self.members))
+        if rc != CORR_OK:
+            raise CorrError(rc, self._L.corr_last_error(None).decode())
+        self._h = h
+
+    def run_dev(self, samples, vis, flags=None, stream=None):
+        n = len(self.members)
+        ptrs = (_vp * n)(*[_dev_ptr(x, "samples") for x in samples])
+        ns = (_sz * n)(*[x.shape[1] for x in samples])
+        st = (_sz * n)(*[x.stride(0) for x in samples])
+        vp = (_vp * n)(*[_dev_ptr(v, "vis") for v in vis])
+        fp = (_vp * n)(*[_dev_ptr(f, "flags") for f in flags]) if flags is not None else None
+        mx = (_i * n)(*[v.numel() * v.element_size() // (8 * m.n_chan * m.n_in * m.n_in)
+                        for v, m in zip(vis, self.members)])
+        out = (_i * n)()
+        rc = self._L.corr_group_run_dev(self._h, ptrs, ns, st, vp, fp, mx, out, _stream_ptr(stream))
+        if rc != CORR_OK:
+            raise CorrError(rc, self._L.corr_last_error(self._h).decode())
+        return list(out)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.corr_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def xengine_noalloc(V, n_spec: int, n_in: int, n_chan: int, vis_out, stream=None):
@@ -279,6 +324,17 @@ class Correlator:
     def flag_dev(self, vis, n_vis: int, flags_out, stream=None):
         self._check(self._L.corr_flag_dev(self._h, _dev_ptr(vis, "vis"), int(n_vis),
                                           _dev_ptr(flags_out, "flags"), _stream_ptr(stream)))
+
+    def autotune(self, samples, cache_path: Optional[str] = None, stream=None):
+        """Pick ring size and FIR run length by timing (corr_autotune)."""
+        cp = cache_path.encode() if cache_path else None
+        self._check(self._L.corr_autotune(self._h, _dev_ptr(samples, "samples"), samples.shape[1],
+                                          samples.stride(0), cp, _stream_ptr(stream)))
+
+    def tuning(self):
+        r, s = _i(), _i()
+        self._check(self._L.corr_get_tuning(self._h, ctypes.byref(r), ctypes.byref(s)))
+        return r.value, s.value
 
     def gram_dev(self, Q, n_chan: int, k_pitch: int, K: int, dtype: int, G_out, stream=None):
         """Tensor-core Gram matrices of Q (see corr_gram_dev in include/corr.h)."""

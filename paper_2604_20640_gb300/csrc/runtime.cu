@@ -104,6 +104,20 @@ struct corr_s {
     long long chunk = 1LL << 23;
     int precision = CORR_FP32;
     int result_slots = 8;
+    int ring_mb = 32;            // tunable: ring capacity of Z and V (MiB each)
+    int fir_spt = 0;             // tunable: spectra per FIR thread (0 = automatic)
+    // group of handles run as one captured graph (corr_group_create)
+    bool is_group = false;
+    std::vector<corr_s*> members;
+    std::vector<cudaStream_t> mstreams;
+    std::vector<cudaEvent_t> mjoin;
+    cudaEvent_t gfork = nullptr;
+    cudaStream_t gorigin = nullptr;  // capture / launch stream of a group
+    cudaEvent_t gin = nullptr, gout = nullptr;
+    long long graph_kernels = 0;     // kernels in one replay of the group graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<const void*> gkey;   // pointers/sizes the graph was captured with
     // constant tables
     float* d_h = nullptr;
     float2* d_tw = nullptr;
@@ -259,11 +273,12 @@ int choose_fir_spt(long long n_spec, int n_pairs, int M, int taps) {
 
 int alloc_pipe(corr_t h, Pipe& p) {
     if (p.V) return CORR_OK;
+    const unsigned long long ring_bytes = (unsigned long long)h->ring_mb << 20;
     // Power-of-two rings of about 32 MiB each, so that the FIR output and the
     // channelised spectra both stay in L2 between the kernels.
     const size_t per_spec = (size_t)h->n_chan * h->n_in_pad * sizeof(float2);
     long long cap = 1;
-    while (cap * 2 * per_spec <= (32ull << 20) && cap < 4096) cap *= 2;
+    while (cap * 2 * per_spec <= ring_bytes && cap < 4096) cap *= 2;
     while (cap < h->G) cap *= 2;
     // the reduced-precision scale pre-pass reads the first 64 spectra from the ring
     while (h->precision != CORR_FP32 && cap < 64) cap *= 2;
@@ -304,7 +319,7 @@ int launch_f(corr_t h, const StreamView& sv, const Tables& t, float2* Z, long lo
     a.lgM = 0;
     while ((1 << a.lgM) < h->M) ++a.lgM;
     a.taps = h->taps;
-    a.spt = choose_fir_spt(s_end - s_begin, a.n_pairs, h->M, h->taps);
+    a.spt = h->fir_spt > 0 ? h->fir_spt : choose_fir_spt(s_end - s_begin, a.n_pairs, h->M, h->taps);
     {
         Timed t_(h, 0, st);
         launch_fir(a, st);
@@ -790,6 +805,25 @@ int corr_create(corr_t* out, int n_ant, int n_pol, int n_chan, int taps, int n_i
 int corr_destroy(corr_t h) {
     if (!h) return CORR_OK;
     DeviceGuard g(h->dev);
+    if (h->is_group) {
+        for (cudaStream_t s : h->mstreams) {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+        for (cudaEvent_t e : h->mjoin) cudaEventDestroy(e);
+        if (h->gfork) cudaEventDestroy(h->gfork);
+        if (h->gorigin) {
+            cudaStreamSynchronize(h->gorigin);
+            cudaStreamDestroy(h->gorigin);
+        }
+        if (h->gin) cudaEventDestroy(h->gin);
+        if (h->gout) cudaEventDestroy(h->gout);
+        if (h->gexec) cudaGraphExecDestroy(h->gexec);
+        if (h->graph) cudaGraphDestroy(h->graph);
+        cudaGetLastError();
+        delete h;
+        return CORR_OK;
+    }
     if (h->s_comp) cudaStreamSynchronize(h->s_comp);
     if (h->s_copy) cudaStreamSynchronize(h->s_copy);
     for (Slot& s : h->slots) {
@@ -838,7 +872,7 @@ const char* corr_last_error(corr_t h) {
 int corr_set_option(corr_t h, const char* key, double v) {
     if (!h || !key) return fail(h, CORR_EINVAL, "NULL argument");
     const std::string k(key);
-    if (h->started && k != "stage_timing")
+    if (h->started && k != "stage_timing" && k != "fir_spt")
         return fail(h, CORR_ESTATE, "options must be set before the first push");
     if (k == "flag_sigma") {
         if (!(v > 0)) return fail(h, CORR_EINVAL, "flag_sigma must be > 0");
@@ -859,6 +893,15 @@ int corr_set_option(corr_t h, const char* key, double v) {
         if (v != CORR_FP32 && h->n_in > 64) return fail(h, CORR_EINVAL, "reduced precision needs n_in <= 64");
         if (h->stream_alloc || h->pd.V) return fail(h, CORR_ESTATE, "precision must be set before buffers exist");
         h->precision = (int)v;
+    } else if (k == "ring_mb") {
+        if (v < 1 || v > 4096) return fail(h, CORR_EINVAL, "ring_mb out of range");
+        if (h->stream_alloc) return fail(h, CORR_ESTATE, "ring_mb must be set before the first push");
+        h->ring_mb = (int)v;
+        free_pipe(h->pd);
+    } else if (k == "fir_spt") {
+        if (v < 0 || v > 256) return fail(h, CORR_EINVAL, "fir_spt out of range");
+        h->fir_spt = (int)v;
+        return CORR_OK;
     } else if (k == "stage_timing") {
         h->timer.on = v != 0;
         return CORR_OK;
@@ -963,6 +1006,7 @@ int corr_pending(corr_t h, int* n) {
 int corr_run_dev(corr_t h, const int8_t* d_samples, size_t n_samples, size_t stride, float* d_vis,
                  uint8_t* d_flags, int max_int, int include_partial, int* n_out, void* stream) {
     if (!h) return fail(h, CORR_EINVAL, "NULL handle");
+    if (h->is_group) return fail(h, CORR_EINVAL, "use corr_group_run_dev on a group");
     DeviceGuard g(h->dev);
     if (n_out) *n_out = 0;
     if (!d_samples || !d_vis) return fail(h, CORR_EINVAL, "NULL buffer");
@@ -1099,6 +1143,258 @@ int corr_gram_dev(corr_t h, const void* d_Q, int n_chan, int k_pitch, int K, int
     }
     if (rc != CORR_OK) return fail(h, rc, "gram: bad layout (k_pitch multiple of 128 bytes, 16-byte aligned Q)");
     CK(cudaGetLastError());
+    return CORR_OK;
+}
+
+// ---- batched sub-array streams: one captured graph --------------------------
+
+int corr_group_create(corr_t* out, const corr_t* members, int n) {
+    if (!out || !members || n < 1 || n > 64) return fail(nullptr, CORR_EINVAL, "bad group arguments");
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!members[i] || members[i]->is_group) return fail(nullptr, CORR_EINVAL, "group members must be handles");
+        for (int j = 0; j < i; ++j)
+            if (members[j] == members[i]) return fail(nullptr, CORR_EINVAL, "duplicate group member");
+        if (members[i]->dev != members[0]->dev) return fail(nullptr, CORR_EINVAL, "members on different devices");
+    }
+    corr_t g = new corr_s();
+    g->is_group = true;
+    g->dev = members[0]->dev;
+    DeviceGuard dg(g->dev);
+    g->members.assign(members, members + n);
+    g->mstreams.resize(n, nullptr);
+    g->mjoin.resize(n, nullptr);
+    bool ok = cudaEventCreateWithFlags(&g->gfork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&g->gin, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&g->gout, cudaEventDisableTiming) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&g->gorigin, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; i < n && ok; ++i)
+        ok = cudaStreamCreateWithFlags(&g->mstreams[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&g->mjoin[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        corr_destroy(g);
+        return fail(nullptr, CORR_ECUDA, "group stream/event creation failed");
+    }
+    *out = g;
+    return CORR_OK;
+}
+
+int corr_group_run_dev(corr_t g, const int8_t* const* d_samples, const size_t* n_samples, const size_t* strides,
+                       float* const* d_vis, uint8_t* const* d_flags, const int* max_int, int* n_out, void* stream) {
+    if (!g || !g->is_group) return fail(g, CORR_EINVAL, "not a group");
+    if (!d_samples || !n_samples || !strides || !d_vis || !max_int) return fail(g, CORR_EINVAL, "NULL argument");
+    corr_t h = g;   // error reporting target of the CK macro
+    DeviceGuard dg(g->dev);
+    const int n = (int)g->members.size();
+    // Work is captured and launched on the group's own stream, ordered after
+    // the caller's stream and before its later work.
+    cudaStream_t user = static_cast<cudaStream_t>(stream);
+    cudaStream_t origin = g->gorigin;
+    CK(cudaEventRecord(g->gin, user));
+    CK(cudaStreamWaitEvent(origin, g->gin, 0));
+    // The graph replays fixed pointers and sizes: capture again if they change.
+    std::vector<const void*> key;
+    for (int i = 0; i < n; ++i) {
+        key.push_back(d_samples[i]);
+        key.push_back(reinterpret_cast<const void*>(n_samples[i]));
+        key.push_back(reinterpret_cast<const void*>(strides[i]));
+        key.push_back(d_vis[i]);
+        key.push_back(d_flags ? d_flags[i] : nullptr);
+        key.push_back(reinterpret_cast<const void*>((size_t)max_int[i]));
+    }
+    if (!g->gexec || key != g->gkey) {
+        if (g->gexec) {
+            cudaGraphExecDestroy(g->gexec);
+            g->gexec = nullptr;
+        }
+        if (g->graph) {
+            cudaGraphDestroy(g->graph);
+            g->graph = nullptr;
+        }
+        // Uncaptured run first: allocates every member's buffers and
+        // configures its kernels, so the capture records launches only.
+        for (int i = 0; i < n; ++i) {
+            int got = 0;
+            corr_t m = g->members[i];
+            const bool timing = m->timer.on;
+            m->timer.on = false;
+            const int rc = corr_run_dev(m, d_samples[i], n_samples[i], strides[i], d_vis[i],
+                                        d_flags ? d_flags[i] : nullptr, max_int[i], 0, &got, origin);
+            m->timer.on = timing;
+            if (rc != CORR_OK) return fail(g, rc, std::string("member ") + std::to_string(i) + ": " + m->err);
+        }
+        CK(cudaStreamSynchronize(origin));
+        CK(cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal));
+        long long k0 = 0;
+        for (int i = 0; i < n; ++i) k0 += g->members[i]->launches;
+        int rc = CORR_OK;
+        if (cudaEventRecord(g->gfork, origin) != cudaSuccess) rc = CORR_ECUDA;
+        for (int i = 0; i < n && rc == CORR_OK; ++i) {
+            corr_t m = g->members[i];
+            if (cudaStreamWaitEvent(g->mstreams[i], g->gfork, 0) != cudaSuccess) {
+                rc = CORR_ECUDA;
+                break;
+            }
+            const bool timing = m->timer.on;
+            m->timer.on = false;
+            int got = 0;
+            rc = corr_run_dev(m, d_samples[i], n_samples[i], strides[i], d_vis[i], d_flags ? d_flags[i] : nullptr,
+                              max_int[i], 0, &got, g->mstreams[i]);
+            m->timer.on = timing;
+            if (rc == CORR_OK && (cudaEventRecord(g->mjoin[i], g->mstreams[i]) != cudaSuccess ||
+                                  cudaStreamWaitEvent(origin, g->mjoin[i], 0) != cudaSuccess))
+                rc = CORR_ECUDA;
+        }
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(origin, &graph);
+        if (rc != CORR_OK || ec != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return fail(g, rc != CORR_OK ? rc : CORR_ECUDA, "graph capture of the group failed");
+        }
+        g->graph = graph;
+        long long k1 = 0;
+        for (int i = 0; i < n; ++i) k1 += g->members[i]->launches;
+        g->graph_kernels = k1 - k0;
+        CK(cudaGraphInstantiate(&g->gexec, g->graph, 0));
+        g->gkey = key;
+    }
+    CK(cudaGraphLaunch(g->gexec, origin));
+    CK(cudaEventRecord(g->gout, origin));
+    CK(cudaStreamWaitEvent(user, g->gout, 0));
+    for (int i = 0; i < n; ++i) {
+        if (n_out) {
+            const long long n_spec = (long long)(n_samples[i] / (size_t)g->members[i]->M);
+            n_out[i] = (int)(n_spec / g->members[i]->n_int);
+        }
+    }
+    g->launches += g->graph_kernels;
+    return CORR_OK;
+}
+
+// ---- autotuner ------------------------------------------------------------
+
+namespace {
+
+std::string tune_key(corr_t h) {
+    cudaDeviceProp prop;
+    std::string name = "gpu";
+    if (cudaGetDeviceProperties(&prop, h->dev) == cudaSuccess) name = prop.name;
+    for (char& c : name)
+        if (c == ' ') c = '_';
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "%s %d %d %d %d %d", name.c_str(), h->n_in, h->n_chan, h->taps, h->n_int,
+                  h->precision);
+    return buf;
+}
+
+bool tune_lookup(const char* path, const std::string& key, int* ring_mb, int* fir_spt) {
+    if (!path) return false;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    while (std::fgets(line, sizeof(line), f)) {
+        std::string l(line);
+        if (l.compare(0, key.size(), key) == 0 && l.size() > key.size() && l[key.size()] == ' ') {
+            int r = 0, sp = 0;
+            if (std::sscanf(l.c_str() + key.size(), "%d %d", &r, &sp) == 2) {
+                *ring_mb = r;
+                *fir_spt = sp;
+                found = true;
+            }
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+}  // namespace
+
+int corr_autotune(corr_t h, const int8_t* d_samples, size_t n_samples, size_t stride, const char* cache_path,
+                  void* stream) {
+    if (!h || h->is_group) return fail(h, CORR_EINVAL, "autotune needs a correlator handle");
+    if (!d_samples || stride < n_samples) return fail(h, CORR_EINVAL, "bad sample buffer");
+    DeviceGuard dg(h->dev);
+    const std::string key = tune_key(h);
+    int ring = 0, spt = 0;
+    if (tune_lookup(cache_path, key, &ring, &spt)) {
+        if (ring != h->ring_mb) {
+            h->ring_mb = ring;
+            free_pipe(h->pd);
+        }
+        h->fir_spt = spt;
+        return CORR_OK;
+    }
+    // Time every candidate on (at most) two integrations of the sample.
+    size_t n_use = (size_t)h->M * (size_t)h->n_int * 2;
+    if (n_use > n_samples) n_use = n_samples;
+    const long long n_spec = (long long)(n_use / (size_t)h->M);
+    const int n_out = (int)(n_spec / h->n_int) > 0 ? (int)(n_spec / h->n_int) : 1;
+    float2* vis = nullptr;
+    uint8_t* flags = nullptr;
+    CK(cudaMalloc(&vis, sizeof(float2) * vis_elems(h) * n_out));
+    CK(cudaMalloc(&flags, vis_elems(h) * n_out));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int rings[] = {16, 32, 64};
+    const int spts[] = {0, 4, 8, 16};
+    float best = 1e30f;
+    int best_ring = h->ring_mb, best_spt = h->fir_spt;
+    int rc = CORR_OK;
+    for (int r : rings) {
+        for (int sp : spts) {
+            if (r != h->ring_mb) {
+                h->ring_mb = r;
+                free_pipe(h->pd);
+            }
+            h->fir_spt = sp;
+            int got = 0;
+            rc = corr_run_dev(h, d_samples, n_use, stride, reinterpret_cast<float*>(vis), flags, n_out, 0, &got,
+                              stream);
+            if (rc != CORR_OK) break;
+            cudaEventRecord(e0, st);
+            for (int rep = 0; rep < 2 && rc == CORR_OK; ++rep)
+                rc = corr_run_dev(h, d_samples, n_use, stride, reinterpret_cast<float*>(vis), flags, n_out, 0, &got,
+                                  stream);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rc == CORR_OK && ms < best) {
+                best = ms;
+                best_ring = r;
+                best_spt = sp;
+            }
+        }
+        if (rc != CORR_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(vis);
+    cudaFree(flags);
+    if (rc != CORR_OK) return rc;
+    if (best_ring != h->ring_mb) {
+        h->ring_mb = best_ring;
+        free_pipe(h->pd);
+    }
+    h->fir_spt = best_spt;
+    if (cache_path) {
+        FILE* f = std::fopen(cache_path, "a");
+        if (f) {
+            std::fprintf(f, "%s %d %d\n", key.c_str(), best_ring, best_spt);
+            std::fclose(f);
+        }
+    }
+    return CORR_OK;
+}
+
+int corr_get_tuning(corr_t h, int* ring_mb, int* fir_spt) {
+    if (!h) return fail(h, CORR_EINVAL, "NULL handle");
+    if (ring_mb) *ring_mb = h->ring_mb;
+    if (fir_spt) *fir_spt = h->fir_spt;
     return CORR_OK;
 }
 
