@@ -245,6 +245,56 @@ int corr_autotune(corr_t h, const int8_t* d_samples, size_t n_samples, size_t in
                   const char* cache_path, void* stream);
 int corr_get_tuning(corr_t h, int* ring_mb, int* fir_spt);
 
+/*
+ * corr_spectrogram_dev -- autocorrelation power of every input in tiles of
+ * 64 rows x 256 channels (the (time x channel) dynamic spectra of Sec. 5):
+ * row r of input a holds mean_{s in [r n_row, (r+1) n_row)} |Y_a,s[k]|^2 from
+ * this F-engine (no fine-delay factor: it has unit modulus), for
+ * rows = 64 floor(n_spec / (64 n_row)) rows, n_spec = floor(n_samples / M):
+ * whole tiles only, later spectra are not read.  n_chan must be a multiple
+ * of 256 and rows >= 64, else CORR_EINVAL.  d_tiles: [n_in][rows/64]
+ * [n_chan/256][64][256] FP32 (device, caller-owned, overwritten).
+ */
+int corr_spectrogram_dev(corr_t h, const int8_t* d_samples, size_t n_samples, size_t input_stride, int n_row,
+                         float* d_tiles, void* stream);
+
+/*
+ * Learned RFI flagger (the paper has none: it is the build's counterpart of
+ * the MAD flagging of Eq. 2, Sec. 7, on the dynamic spectra of Sec. 5).
+ * A 5x5 convolutional net, channels 1 -> 32 -> 32 -> 32 -> 1, zero padding
+ * 2, ReLU after the hidden layers, a logistic output per pixel (52,897
+ * parameters), on tiles of 64 x 256 pixels x = ln(P / median(P)) of
+ * autocorrelation power P.  BF16 operands, FP32 accumulation on tcgen05
+ * tensor cores; FP32 master weights trained with Adam on the mean binary
+ * cross-entropy.  Parameters are flattened layer by layer as w[o][c][u][v]
+ * then b[o].
+ *   corr_flagnet_prepare    d_power [B][64][256] -> d_x (the network input)
+ *   corr_flagnet_forward    d_x -> d_logits [B][64][256]
+ *   corr_flagnet_loss_grad  mean loss and (host) gradients, no update
+ *   corr_flagnet_train_step one Adam step (lr), returns the loss
+ *   corr_flagnet_flag       flags of B power tiles: the net's (p > 1/2) when
+ *                           the tile confidence mean|2p-1| >= c_min, else
+ *                           Eq. 2 along each row over 64-channel windows;
+ *                           d_conf [B] (may be NULL) receives the confidences
+ *   corr_flagnet_status     device status word (CORR_ETIMEDOUT on a stalled
+ *                           tensor-core pipeline), cleared on read
+ */
+typedef struct corr_flagnet_s* corr_flagnet_t;
+int corr_flagnet_create(corr_flagnet_t* out);
+int corr_flagnet_destroy(corr_flagnet_t net);
+int corr_flagnet_num_params(size_t* n);
+int corr_flagnet_set_params(corr_flagnet_t net, const float* params, size_t n);
+int corr_flagnet_get_params(corr_flagnet_t net, float* params, size_t n);
+int corr_flagnet_prepare(corr_flagnet_t net, const float* d_power, int n_tiles, float* d_x, void* stream);
+int corr_flagnet_forward(corr_flagnet_t net, const float* d_x, int n_tiles, float* d_logits, void* stream);
+int corr_flagnet_loss_grad(corr_flagnet_t net, const float* d_x, const uint8_t* d_truth, int n_tiles, float* loss,
+                           float* grads, size_t n, void* stream);
+int corr_flagnet_train_step(corr_flagnet_t net, const float* d_x, const uint8_t* d_truth, int n_tiles, float lr,
+                            float* loss, void* stream);
+int corr_flagnet_flag(corr_flagnet_t net, const float* d_power, int n_tiles, float c_min, float sigma,
+                      uint8_t* d_flags, float* d_conf, void* stream);
+int corr_flagnet_status(corr_flagnet_t net, int* status);
+
 /* Shapes of a handle: n_in, n_chan, taps, n_int, n_in_pad (any may be NULL). */
 int corr_shape(corr_t h, int* n_in, int* n_chan, int* taps, int* n_int, int* n_in_pad);
 

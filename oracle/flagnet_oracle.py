@@ -99,6 +99,40 @@ def loss_and_grads(params, x: np.ndarray, t: np.ndarray):
     return L, grads
 
 
+def flatten_params(params) -> np.ndarray:
+    """One vector, layer by layer: w[o][c][u][v] then b[o]."""
+    return np.concatenate([np.concatenate([w.ravel(), b.ravel()]) for w, b in params])
+
+
+def unflatten_params(vec: np.ndarray):
+    out, off = [], 0
+    for ci, co in LAYERS:
+        nw = co * ci * KS * KS
+        out.append((np.asarray(vec[off:off + nw], np.float64).reshape(co, ci, KS, KS),
+                    np.asarray(vec[off + nw:off + nw + co], np.float64)))
+        off += nw + co
+    return out
+
+
+def dynamic_spectrum(x: np.ndarray, n_chan: int, taps: int, n_row: int, tau=None) -> np.ndarray:
+    """Autocorrelation power P[a][r][k] = mean over spectra s in
+    [r n_row, (r + 1) n_row) of |V_a,s[k]|^2, r < floor(n_spec / n_row): the
+    (time x channel) dynamic spectra of Sec. 5, from the F-engine of
+    Sec. 4.2 (coarse and fine delay as in Eq. 1; the phase factor has unit
+    modulus and drops out)."""
+    V = fx.f_engine(x, n_chan, taps, tau, None)
+    n_in, n_spec, _ = V.shape
+    rows = n_spec // n_row
+    p = np.abs(V[:, :rows * n_row, :]) ** 2
+    return p.reshape(n_in, rows, n_row, n_chan).mean(axis=2)
+
+
+def to_tiles(P: np.ndarray, th: int = 64, tw: int = 256) -> np.ndarray:
+    """[n_in][rows][n_chan] -> [n_in][rows / th][n_chan / tw][th][tw]."""
+    n_in, rows, n_chan = P.shape
+    return P.reshape(n_in, rows // th, th, n_chan // tw, tw).transpose(0, 1, 3, 2, 4)
+
+
 def tile_input(power: np.ndarray) -> np.ndarray:
     """ln(P / median(P)) per tile; power [..., H, W] > 0."""
     med = np.median(power.reshape(*power.shape[:-2], -1), axis=-1)[..., None, None]

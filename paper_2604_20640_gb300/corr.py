@@ -34,7 +34,10 @@ EXPORTED = [
     "corr_pending", "corr_run_dev", "corr_fengine_dev", "corr_xengine_dev", "corr_flag_dev",
     "corr_shape", "corr_kernel_launches", "corr_stage_times", "corr_xengine_noalloc",
     "corr_gram_dev", "corr_device_status", "corr_group_create", "corr_group_run_dev", "corr_autotune",
-    "corr_get_tuning",
+    "corr_get_tuning", "corr_spectrogram_dev", "corr_flagnet_create", "corr_flagnet_destroy",
+    "corr_flagnet_num_params", "corr_flagnet_set_params", "corr_flagnet_get_params", "corr_flagnet_prepare",
+    "corr_flagnet_forward", "corr_flagnet_loss_grad", "corr_flagnet_train_step", "corr_flagnet_flag",
+    "corr_flagnet_status",
 ]
 
 
@@ -88,6 +91,18 @@ def load_library(path: str = LIB_PATH):
         "corr_group_run_dev": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
         "corr_autotune": (_i, [_vp, _vp, _sz, _sz, ctypes.c_char_p, _vp]),
         "corr_get_tuning": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+        "corr_spectrogram_dev": (_i, [_vp, _vp, _sz, _sz, _i, _vp, _vp]),
+        "corr_flagnet_create": (_i, [ctypes.POINTER(_vp)]),
+        "corr_flagnet_destroy": (_i, [_vp]),
+        "corr_flagnet_num_params": (_i, [ctypes.POINTER(_sz)]),
+        "corr_flagnet_set_params": (_i, [_vp, _vp, _sz]),
+        "corr_flagnet_get_params": (_i, [_vp, _vp, _sz]),
+        "corr_flagnet_prepare": (_i, [_vp, _vp, _i, _vp, _vp]),
+        "corr_flagnet_forward": (_i, [_vp, _vp, _i, _vp, _vp]),
+        "corr_flagnet_loss_grad": (_i, [_vp, _vp, _vp, _i, ctypes.POINTER(ctypes.c_float), _vp, _sz, _vp]),
+        "corr_flagnet_train_step": (_i, [_vp, _vp, _vp, _i, ctypes.c_float, ctypes.POINTER(ctypes.c_float), _vp]),
+        "corr_flagnet_flag": (_i, [_vp, _vp, _i, ctypes.c_float, ctypes.c_float, _vp, _vp, _vp]),
+        "corr_flagnet_status": (_i, [_vp, ctypes.POINTER(_i)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -341,6 +356,13 @@ class Correlator:
         self._check(self._L.corr_gram_dev(self._h, _dev_ptr(Q, "Q"), int(n_chan), int(k_pitch), int(K),
                                           int(dtype), _dev_ptr(G_out, "G"), _stream_ptr(stream)))
 
+    def spectrogram_dev(self, samples, n_row: int, tiles_out, stream=None):
+        """Autocorrelation-power tiles [n_in][rows/64][n_chan/256][64][256] (FP32)."""
+        rc = self._L.corr_spectrogram_dev(self._h, _dev_ptr(samples, "samples"), samples.shape[1],
+                                          samples.stride(0), n_row, _dev_ptr(tiles_out, "tiles"),
+                                          _stream_ptr(stream))
+        self._check(rc)
+
     def device_status(self) -> int:
         st = _i()
         self._check(self._L.corr_device_status(self._h, ctypes.byref(st)))
@@ -357,3 +379,79 @@ class Correlator:
     @property
     def launches(self) -> int:
         return int(self._L.corr_kernel_launches(self._h))
+
+
+class FlagNet:
+    """Learned RFI flagger on (64 x 256) tiles of autocorrelation power, with
+    the Eq. 2 MAD rule as the fallback on tiles of low confidence."""
+
+    TILE = (64, 256)
+
+    def __init__(self, params: Optional[np.ndarray] = None):
+        self._L = load_library()
+        h = _vp()
+        rc = self._L.corr_flagnet_create(ctypes.byref(h))
+        if rc != CORR_OK:
+            raise CorrError(rc, self._L.corr_last_error(None).decode())
+        self._h = h
+        n = _sz()
+        self._L.corr_flagnet_num_params(ctypes.byref(n))
+        self.n_params = n.value
+        if params is not None:
+            self.set_params(params)
+
+    def _check(self, rc: int):
+        if rc != CORR_OK:
+            raise CorrError(rc, self._L.corr_last_error(None).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.corr_flagnet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params: np.ndarray):
+        p = np.ascontiguousarray(params, np.float32)
+        self._check(self._L.corr_flagnet_set_params(self._h, p.ctypes.data, p.size))
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(self.n_params, np.float32)
+        self._check(self._L.corr_flagnet_get_params(self._h, p.ctypes.data, p.size))
+        return p
+
+    def prepare(self, power, x_out, stream=None):
+        self._check(self._L.corr_flagnet_prepare(self._h, _dev_ptr(power, "power"), power.shape[0],
+                                                 _dev_ptr(x_out, "x"), _stream_ptr(stream)))
+
+    def forward(self, x, logits_out, stream=None):
+        self._check(self._L.corr_flagnet_forward(self._h, _dev_ptr(x, "x"), x.shape[0],
+                                                 _dev_ptr(logits_out, "logits"), _stream_ptr(stream)))
+
+    def loss_grad(self, x, truth, stream=None):
+        loss = ctypes.c_float()
+        g = np.empty(self.n_params, np.float32)
+        self._check(self._L.corr_flagnet_loss_grad(self._h, _dev_ptr(x, "x"), _dev_ptr(truth, "truth"), x.shape[0],
+                                                   ctypes.byref(loss), g.ctypes.data, g.size, _stream_ptr(stream)))
+        return loss.value, g
+
+    def train_step(self, x, truth, lr: float, stream=None) -> float:
+        loss = ctypes.c_float()
+        self._check(self._L.corr_flagnet_train_step(self._h, _dev_ptr(x, "x"), _dev_ptr(truth, "truth"), x.shape[0],
+                                                    lr, ctypes.byref(loss), _stream_ptr(stream)))
+        return loss.value
+
+    def flag(self, power, flags_out, conf_out=None, c_min: float = 0.9, sigma: float = 5.0, stream=None):
+        self._check(self._L.corr_flagnet_flag(self._h, _dev_ptr(power, "power"), power.shape[0], c_min, sigma,
+                                              _dev_ptr(flags_out, "flags"),
+                                              _dev_ptr(conf_out, "conf") if conf_out is not None else None,
+                                              _stream_ptr(stream)))
+
+    def status(self) -> int:
+        st = _i()
+        self._check(self._L.corr_flagnet_status(self._h, ctypes.byref(st)))
+        return st.value

@@ -120,6 +120,21 @@ struct FinQArgs {
 };
 
 int launch_gram(const GramArgs& a, cudaStream_t st);
+
+// General tensor-core GEMM, D[s][m][n] = sum_{k in split s} A[m][k] B[n][k]:
+// A [M rows][lda bytes] and B [N rows][ldb bytes] BF16, K-major; D FP32
+// partial sums per K split ([splits][M][N]); N in {16, 32, 64}.
+struct GemmArgs {
+    const void* A;
+    const void* B;
+    int M, N, K, lda, ldb;
+    int splits, k_per_split;   // k_per_split a multiple of 64
+    float* D;
+    int* status;
+};
+int launch_gemm(const GemmArgs& a, cudaStream_t st);
+// out[m][n] = sum over splits of D[s][m][n], fixed order
+void launch_split_sum(const float* D, int splits, long long mn, float* out, cudaStream_t st);
 size_t gram_smem_bytes();
 void launch_requant(const RequantArgs& a, cudaStream_t st);
 void launch_finalize_q(const FinQArgs& a, cudaStream_t st);
@@ -130,6 +145,11 @@ void launch_scale_from_ring(const float2* V, long long v_origin, long long v_mas
 // scale[a][k] = 2 sqrt(R_aa[k] / 2) / gain (U = 2V) from an integration's R.
 void launch_scale_from_vis(const float2* R, int n_in, int n_in_pad, int n_chan, float gain, float* scale,
                            cudaStream_t st);
+
+// Autocorrelation-power tiles (64 rows of n_row spectra x 256 channels) of
+// spectra [s_begin, s_end) of the ring, accumulated into `tiles`.
+void launch_spectrogram(const float2* V, long long v_mask, int n_chan, int n_in, int n_in_pad, long long s_begin,
+                        long long s_end, int n_row, int rows, float* tiles, cudaStream_t st);
 
 void launch_fir(const FirArgs& a, cudaStream_t st);
 void launch_fft(const FftArgs& a, cudaStream_t st);

@@ -1,0 +1,669 @@
+// Learned RFI flagger: a 4-layer 5x5 convolutional network (1 -> 32 -> 32 ->
+// 32 -> 1 channels, ReLU, logistic output) over (time x channel) tiles of
+// autocorrelation power, trained and run on the GPU, with the MAD rule of
+// Eq. 2 (Sec. 7) as the fallback on tiles where the network is not confident.
+//
+// Every convolution is an im2col product on the tcgen05 GEMM (BF16 operands,
+// FP32 accumulation):
+//   forward   Z[p][o]   = sum_k A[p][k] Wf[o][k],   A = im2col(X), k = (5u+v) C + c
+//   data grad dX[p][c]  = sum_k A'[p][k] Wd[c][k],  A' = im2col of dZ at negated offsets
+//   weight    dW^T[k][o] = sum_p A^T[k][p] dZ^T[o][p]  (K = pixels, split over CTAs)
+// Activations are NHWC BF16; FP32 master weights with Adam.
+#include "corr.h"
+#include "corr_internal.h"
+
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+namespace corr {
+namespace {
+
+constexpr int TH = 64, TW = 256, TPIX = TH * TW;   // tile: 64 rows (time) x 256 channels
+constexpr int NL = 4;
+constexpr int CI[NL] = {1, 32, 32, 32};
+constexpr int CO[NL] = {32, 32, 32, 1};
+
+__host__ __device__ inline int kpad(int k) { return (k + 63) / 64 * 64; }
+__host__ __device__ inline int npad(int co) { return co < 16 ? 16 : co; }
+
+__device__ __forceinline__ uint16_t f2bf(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ float bf2f(uint16_t x) { return __bfloat162float(__ushort_as_bfloat16(x)); }
+
+// A[p][k] = X[n][i+u-2][j+v-2][c] (k = (5u+v) C + c < 25 C, else 0); sgn = -1
+// gives the negated offsets of the data-gradient product.
+__global__ void im2col_kernel(const uint16_t* X, int C, int P, int Kp, int sgn, uint16_t* A) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)P * Kp) return;
+    const int p = (int)(idx / Kp), k = (int)(idx % Kp);
+    uint16_t v = 0;
+    if (k < 25 * C) {
+        const int c = k % C, uv = k / C, u = uv / 5, w = uv % 5;
+        const int n = p / TPIX, ij = p % TPIX, i = ij / TW, j = ij % TW;
+        const int ii = i + sgn * (u - 2), jj = j + sgn * (w - 2);
+        if (ii >= 0 && ii < TH && jj >= 0 && jj < TW) v = X[((size_t)n * TPIX + ii * TW + jj) * C + c];
+    }
+    A[idx] = v;
+}
+
+// AT[k][p] = A[p][k] (the im2col operand of the weight gradient, K = pixels).
+__global__ void im2colT_kernel(const uint16_t* X, int C, int P, int Kp, uint16_t* AT) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)P * Kp) return;
+    const int k = (int)(idx / P), p = (int)(idx % P);
+    uint16_t v = 0;
+    if (k < 25 * C) {
+        const int c = k % C, uv = k / C, u = uv / 5, w = uv % 5;
+        const int n = p / TPIX, ij = p % TPIX, i = ij / TW, j = ij % TW;
+        const int ii = i + u - 2, jj = j + w - 2;
+        if (ii >= 0 && ii < TH && jj >= 0 && jj < TW) v = X[((size_t)n * TPIX + ii * TW + jj) * C + c];
+    }
+    AT[idx] = v;
+}
+
+__global__ void input_bf16_kernel(const float* x, int P, uint16_t* X) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < P) X[p] = f2bf(x[p]);
+}
+
+// z = D + b; hidden layers store BF16 ReLU(z), the last layer the logit.
+__global__ void fwd_epilogue_kernel(const float* D, int P, int Co, int Np, const float* b, bool last,
+                                    uint16_t* act, float* logit) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)P * Co) return;
+    const int p = (int)(idx / Co), o = (int)(idx % Co);
+    const float z = D[(size_t)p * Np + o] + b[o];
+    if (last) logit[p] = z;
+    else act[idx] = f2bf(fmaxf(z, 0.f));
+}
+
+// dz = (sigmoid(z) - t) / P_total as FP32 and BF16 (NHWC and transposed),
+// plus per-block partial sums of the loss softplus(z) - t z.
+__global__ void loss_grad_kernel(const float* z, const uint8_t* t, int P, float inv_total, float* dz32,
+                                 uint16_t* dz, uint16_t* dzT, float* loss_part) {
+    __shared__ float red[256];
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    float l = 0.f;
+    if (p < P) {
+        const float zz = z[p], tt = t[p] ? 1.f : 0.f;
+        const float s = 1.f / (1.f + expf(-zz));
+        const float g = (s - tt) * inv_total;
+        dz32[p] = g;
+        dz[p] = f2bf(g);
+        dzT[p] = f2bf(g);
+        l = fmaxf(zz, 0.f) + log1pf(expf(-fabsf(zz))) - tt * zz;
+    }
+    red[threadIdx.x] = l;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0];
+}
+
+// dz_prev[p][c] = D[p][c] * (act[p][c] > 0) in FP32, BF16 and transposed BF16.
+__global__ void relu_grad_kernel(const float* D, const uint16_t* act, int P, int C, float* dz32, uint16_t* dz,
+                                 uint16_t* dzT) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)P * C) return;
+    const int p = (int)(idx / C), c = (int)(idx % C);
+    const float g = bf2f(act[idx]) > 0.f ? D[(size_t)p * 32 + c] : 0.f;
+    dz32[idx] = g;
+    dz[idx] = f2bf(g);
+    dzT[(size_t)c * P + p] = f2bf(g);
+}
+
+// Fixed-order column sums: out[c] = sum_p g[p][c].
+__global__ void colsum_kernel(const float* g, int P, int C, float* out) {
+    __shared__ float red[256];
+    const int c = blockIdx.x;
+    float acc = 0.f;
+    for (int p = threadIdx.x; p < P; p += blockDim.x) acc += g[(size_t)p * C + c];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = red[0];
+}
+
+__global__ void sum_kernel(const float* x, int n, float* out) {
+    __shared__ float red[256];
+    float acc = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += x[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+// dW[o][c][u][v] = DW[(5u+v) C + c][o] (the weight-gradient product).
+__global__ void gather_dw_kernel(const float* DW, int C, int Co, int Np, float* dw) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= Co * C * 25) return;
+    const int o = idx / (C * 25), r = idx % (C * 25), c = r / 25, uv = r % 25;
+    dw[idx] = DW[(size_t)(uv * C + c) * Np + o];
+}
+
+__global__ void adam_kernel(float* w, const float* g, float* m, float* v, int n, float lr, float b1, float b2,
+                            float c1, float c2, float eps) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// Wf[o][(5u+v) C + c] = w[o][c][u][v]; Wd[c][(5u+v) Co + o] = w[o][c][u][v] (BF16).
+__global__ void pack_weights_kernel(const float* w, int C, int Co, int Kf, int Kd, uint16_t* wf, uint16_t* wd) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= Co * C * 25) return;
+    const int o = idx / (C * 25), r = idx % (C * 25), c = r / 25, uv = r % 25;
+    const uint16_t b = f2bf(w[idx]);
+    wf[(size_t)o * Kf + uv * C + c] = b;
+    if (wd) wd[(size_t)c * Kd + uv * Co + o] = b;
+}
+
+// x = ln(P / median(P)) per tile; exact median (mean of the two middle
+// order statistics) by a bitonic sort of the tile in shared memory.
+__global__ void __launch_bounds__(1024) normalize_kernel(const float* power, float* x) {
+    extern __shared__ float sv[];
+    const float* P = power + (size_t)blockIdx.x * TPIX;
+    for (int i = threadIdx.x; i < TPIX; i += blockDim.x) sv[i] = P[i];
+    __syncthreads();
+    for (int k = 2; k <= TPIX; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < TPIX; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & k) == 0;
+                    const float a = sv[i], b = sv[l];
+                    if ((a > b) == up) {
+                        sv[i] = b;
+                        sv[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const float med = 0.5f * (sv[TPIX / 2 - 1] + sv[TPIX / 2]);
+    const float inv = med > 0.f ? 1.f / med : 1.f;
+    for (int i = threadIdx.x; i < TPIX; i += blockDim.x)
+        x[(size_t)blockIdx.x * TPIX + i] = logf(fmaxf(P[i] * inv, 1e-30f));
+}
+
+// Per tile: confidence = mean |2p - 1|, p = sigmoid(logit).
+__global__ void confidence_kernel(const float* logit, float* conf) {
+    __shared__ float red[256];
+    const float* z = logit + (size_t)blockIdx.x * TPIX;
+    float acc = 0.f;
+    for (int i = threadIdx.x; i < TPIX; i += blockDim.x) acc += fabsf(2.f / (1.f + expf(-z[i])) - 1.f);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) conf[blockIdx.x] = red[0] / (float)TPIX;
+}
+
+__device__ float warp_median64(const float* v, float* sorted, int lane) {
+    for (int c = lane; c < 64; c += 32) {
+        const float x = v[c];
+        int rank = 0;
+        for (int d = 0; d < 64; ++d) {
+            const float y = v[d];
+            rank += (y < x) || (y == x && d < c);
+        }
+        sorted[rank] = x;
+    }
+    __syncwarp();
+    const float med = 0.5f * (sorted[31] + sorted[32]);
+    __syncwarp();
+    return med;
+}
+
+// Flags of a tile: the network's (p > 1/2) when conf >= c_min, else Eq. 2
+// along each row over aligned windows of 64 channels.  One warp per (tile,
+// row, window).
+__global__ void final_flags_kernel(const float* power, const float* logit, const float* conf, int B, float c_min,
+                                   float sigma, uint8_t* flags) {
+    __shared__ float sm[4][3][64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long item = (long long)blockIdx.x * 4 + warp;
+    if (item >= (long long)B * TH * (TW / 64)) return;
+    const int win = (int)(item % (TW / 64));
+    const int r = (int)((item / (TW / 64)) % TH);
+    const int t = (int)(item / ((TW / 64) * TH));
+    const size_t base = (size_t)t * TPIX + (size_t)r * TW + win * 64;
+    if (conf[t] >= c_min) {
+        for (int c = lane; c < 64; c += 32) flags[base + c] = logit[base + c] > 0.f ? 1 : 0;
+        return;
+    }
+    float* vA = sm[warp][0];
+    float* vS = sm[warp][1];
+    float* vD = sm[warp][2];
+    for (int c = lane; c < 64; c += 32) vA[c] = power[base + c];
+    __syncwarp();
+    const float med = warp_median64(vA, vS, lane);
+    for (int c = lane; c < 64; c += 32) vD[c] = fabsf(vA[c] - med);
+    __syncwarp();
+    const float mad = warp_median64(vD, vS, lane);
+    const float T = med + sigma * mad * 1.4826f;
+    for (int c = lane; c < 64; c += 32) flags[base + c] = vA[c] > T ? 1 : 0;
+}
+
+// Autocorrelation power of row `row` (n_row spectra) for input a and channel
+// k, mean |Y|^2 = |U|^2 / 4 (U = 2Y from the F-engine), accumulated in tile
+// order: tile (a, row / 64, k / 256), pixel (row % 64, k % 256).
+__global__ void spectrogram_kernel(const float2* V, long long v_mask, int n_chan, int n_in_pad, long long s_begin,
+                                   long long s_end, int n_row, int rows, float* tiles) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int a = blockIdx.y;
+    if (k >= n_chan) return;
+    const int n_cb = n_chan / TW, n_rb = rows / TH;
+    long long s = s_begin;
+    while (s < s_end) {
+        const long long row = s / n_row;
+        long long e = (row + 1) * n_row;
+        if (e > s_end) e = s_end;
+        float acc = 0.f;
+        for (long long q = s; q < e; ++q) {
+            const float2 u = V[(((q & v_mask) * n_chan) + k) * n_in_pad + a];
+            acc = fmaf(u.x, u.x, fmaf(u.y, u.y, acc));
+        }
+        const size_t t = ((size_t)a * n_rb + row / TH) * n_cb + k / TW;
+        tiles[t * TPIX + (size_t)(row % TH) * TW + (k % TW)] += acc * (0.25f / (float)n_row);
+        s = e;
+    }
+}
+
+}  // namespace
+
+void launch_spectrogram(const float2* V, long long v_mask, int n_chan, int n_in, int n_in_pad, long long s_begin,
+                        long long s_end, int n_row, int rows, float* tiles, cudaStream_t st) {
+    dim3 grid((unsigned)((n_chan + 127) / 128), (unsigned)n_in);
+    spectrogram_kernel<<<grid, 128, 0, st>>>(V, v_mask, n_chan, n_in_pad, s_begin, s_end, n_row, rows, tiles);
+}
+
+}  // namespace corr
+
+// ---------------------------------------------------------------------------
+// C ABI of the flagger
+
+using namespace corr;
+
+struct corr_flagnet_s {
+    int dev = 0;
+    float* w[NL] = {};
+    float* b[NL] = {};
+    float* mw[NL] = {};
+    float* vw[NL] = {};
+    float* mb[NL] = {};
+    float* vb[NL] = {};
+    float* gw[NL] = {};
+    float* gb[NL] = {};
+    uint16_t* wf[NL] = {};   // [npad(Co)][kpad(25 Ci)]
+    uint16_t* wd[NL] = {};   // [Ci][kpad(25 Co)]
+    long long steps = 0;
+    int cap = 0;             // tiles the workspace holds
+    uint16_t* act[NL + 1] = {};   // act[0] input BF16 [P], act[l] [P][32]
+    float* logit = nullptr;
+    uint16_t* A = nullptr;   // im2col scratch (largest: P x 832 or 832 x P)
+    float* D = nullptr;      // GEMM output / partial sums
+    float* D2 = nullptr;
+    float* dz32 = nullptr;
+    uint16_t* dz = nullptr;
+    uint16_t* dzT = nullptr;
+    float* loss_part = nullptr;
+    float* scalar = nullptr;
+    float* norm = nullptr;
+    float* conf = nullptr;
+    int* status = nullptr;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_fn_err;
+
+int ffail(corr_flagnet_t n, int code, const std::string& m) {
+    if (n) n->err = m;
+    else g_fn_err = m;
+    corr::set_global_error(m);
+    return code;
+}
+
+#define FK(call)                                                                                 \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) return ffail(net, CORR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+inline unsigned blocks(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+int ensure_ws(corr_flagnet_t net, int B) {
+    if (B <= net->cap) return CORR_OK;
+    auto fr = [](void* p) { if (p) cudaFree(p); };
+    for (int l = 0; l <= NL; ++l) fr(net->act[l]);
+    fr(net->logit); fr(net->A); fr(net->D); fr(net->D2); fr(net->dz32); fr(net->dz); fr(net->dzT);
+    fr(net->loss_part); fr(net->norm); fr(net->conf);
+    const size_t P = (size_t)B * TPIX;
+    FK(cudaMalloc(&net->act[0], P * 2));
+    for (int l = 1; l <= NL; ++l) FK(cudaMalloc(&net->act[l], P * 32 * 2));
+    FK(cudaMalloc(&net->logit, P * 4));
+    FK(cudaMalloc(&net->A, P * 832 * 2));
+    const int splits = 64;
+    FK(cudaMalloc(&net->D, std::max(P * 32, (size_t)splits * 896 * 32) * 4));
+    FK(cudaMalloc(&net->D2, (size_t)896 * 32 * 4));
+    FK(cudaMalloc(&net->dz32, P * 32 * 4));
+    FK(cudaMalloc(&net->dz, P * 32 * 2));
+    FK(cudaMalloc(&net->dzT, P * 32 * 2));
+    FK(cudaMemset(net->dzT, 0, P * 32 * 2));
+    FK(cudaMalloc(&net->loss_part, blocks(P) * 4));
+    FK(cudaMalloc(&net->norm, P * 4));
+    FK(cudaMalloc(&net->conf, (size_t)B * 4));
+    net->cap = B;
+    return CORR_OK;
+}
+
+int repack(corr_flagnet_t net, cudaStream_t st) {
+    for (int l = 0; l < NL; ++l) {
+        const int n = CO[l] * CI[l] * 25;
+        pack_weights_kernel<<<blocks(n), 256, 0, st>>>(net->w[l], CI[l], CO[l], kpad(25 * CI[l]), kpad(25 * CO[l]),
+                                                       net->wf[l], l > 0 ? net->wd[l] : nullptr);
+    }
+    FK(cudaGetLastError());
+    return CORR_OK;
+}
+
+int gemm(corr_flagnet_t net, const void* A, const void* Bm, int M, int N, int K, int lda, int ldb, int splits,
+         float* D, float* out, cudaStream_t st) {
+    GemmArgs g{};
+    g.A = A;
+    g.B = Bm;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.lda = lda;
+    g.ldb = ldb;
+    g.splits = splits;
+    g.k_per_split = ((K + splits - 1) / splits + 63) / 64 * 64;
+    g.D = D;
+    g.status = net->status;
+    const int rc = launch_gemm(g, st);
+    if (rc != CORR_OK) return ffail(net, rc, "flagnet GEMM: bad layout");
+    FK(cudaGetLastError());
+    if (splits > 1) launch_split_sum(D, splits, (long long)M * N, out, st);
+    FK(cudaGetLastError());
+    return CORR_OK;
+}
+
+// Forward pass over B normalised tiles x [B][64][256] -> logits.
+int forward(corr_flagnet_t net, const float* x, int B, cudaStream_t st) {
+    const int P = B * TPIX;
+    input_bf16_kernel<<<blocks(P), 256, 0, st>>>(x, P, net->act[0]);
+    for (int l = 0; l < NL; ++l) {
+        const int C = CI[l], Kp = kpad(25 * C), Np = npad(CO[l]);
+        im2col_kernel<<<blocks((long long)P * Kp), 256, 0, st>>>(net->act[l], C, P, Kp, 1, net->A);
+        int rc = gemm(net, net->A, net->wf[l], P, Np, Kp, Kp * 2, Kp * 2, 1, net->D, nullptr, st);
+        if (rc != CORR_OK) return rc;
+        fwd_epilogue_kernel<<<blocks((long long)P * CO[l]), 256, 0, st>>>(net->D, P, CO[l], Np, net->b[l], l == NL - 1,
+                                                                          net->act[l + 1], net->logit);
+    }
+    FK(cudaGetLastError());
+    return CORR_OK;
+}
+
+// Loss and gradients (into gw/gb) for B tiles; loss summed on the device.
+int backward(corr_flagnet_t net, const uint8_t* truth, int B, cudaStream_t st) {
+    const int P = B * TPIX;
+    // rows 1..15 of the transposed gradient are the zero padding of the
+    // 1-channel output layer's weight-gradient operand
+    FK(cudaMemsetAsync(net->dzT + P, 0, (size_t)15 * P * 2, st));
+    loss_grad_kernel<<<blocks(P), 256, 0, st>>>(net->logit, truth, P, 1.0f / (float)P, net->dz32, net->dz, net->dzT,
+                                                net->loss_part);
+    sum_kernel<<<1, 256, 0, st>>>(net->loss_part, (int)blocks(P), net->scalar);
+    for (int l = NL - 1; l >= 0; --l) {
+        const int C = CI[l], Co = CO[l], Kp = kpad(25 * C), Np = npad(Co);
+        // bias gradient
+        colsum_kernel<<<Co, 256, 0, st>>>(net->dz32, P, Co, net->gb[l]);
+        // weight gradient: DW[Kp][Np] = A^T[Kp][P] . dZ^T[Np][P]
+        im2colT_kernel<<<blocks((long long)P * Kp), 256, 0, st>>>(net->act[l], C, P, Kp, net->A);
+        const int splits = 64;
+        int rc = gemm(net, net->A, net->dzT, Kp, Np, P, P * 2, P * 2, splits, net->D, net->D2, st);
+        if (rc != CORR_OK) return rc;
+        gather_dw_kernel<<<blocks(Co * C * 25), 256, 0, st>>>(net->D2, C, Co, Np, net->gw[l]);
+        if (l == 0) break;
+        // data gradient: dX[P][C] = A'[P][Kd] . Wd[C][Kd], then ReLU of layer l-1
+        const int Kd = kpad(25 * Co);
+        im2col_kernel<<<blocks((long long)P * Kd), 256, 0, st>>>(net->dz, Co, P, Kd, -1, net->A);
+        rc = gemm(net, net->A, net->wd[l], P, 32, Kd, Kd * 2, Kd * 2, 1, net->D, nullptr, st);
+        if (rc != CORR_OK) return rc;
+        relu_grad_kernel<<<blocks((long long)P * C), 256, 0, st>>>(net->D, net->act[l], P, C, net->dz32, net->dz,
+                                                                   net->dzT);
+    }
+    FK(cudaGetLastError());
+    return CORR_OK;
+}
+
+size_t n_params() {
+    size_t n = 0;
+    for (int l = 0; l < NL; ++l) n += (size_t)CO[l] * CI[l] * 25 + CO[l];
+    return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+int corr_flagnet_create(corr_flagnet_t* out) {
+    if (!out) return ffail(nullptr, CORR_EINVAL, "out is NULL");
+    *out = nullptr;
+    corr_flagnet_t net = new corr_flagnet_s();
+    cudaGetDevice(&net->dev);
+    auto bad = [&](int code, const char* m) {
+        corr_flagnet_destroy(net);
+        return ffail(nullptr, code, m);
+    };
+    for (int l = 0; l < NL; ++l) {
+        const size_t nw = (size_t)CO[l] * CI[l] * 25;
+        float** fs[] = {&net->w[l], &net->mw[l], &net->vw[l], &net->gw[l]};
+        for (float** f : fs)
+            if (cudaMalloc(f, nw * 4) != cudaSuccess || cudaMemset(*f, 0, nw * 4) != cudaSuccess)
+                return bad(CORR_ENOMEM, "flagnet allocation failed");
+        float** bs[] = {&net->b[l], &net->mb[l], &net->vb[l], &net->gb[l]};
+        for (float** f : bs)
+            if (cudaMalloc(f, CO[l] * 4) != cudaSuccess || cudaMemset(*f, 0, CO[l] * 4) != cudaSuccess)
+                return bad(CORR_ENOMEM, "flagnet allocation failed");
+        const size_t wfb = (size_t)npad(CO[l]) * kpad(25 * CI[l]) * 2;
+        if (cudaMalloc(&net->wf[l], wfb) != cudaSuccess || cudaMemset(net->wf[l], 0, wfb) != cudaSuccess)
+            return bad(CORR_ENOMEM, "flagnet allocation failed");
+        if (l > 0) {
+            const size_t wdb = (size_t)32 * kpad(25 * CO[l]) * 2;
+            if (cudaMalloc(&net->wd[l], wdb) != cudaSuccess || cudaMemset(net->wd[l], 0, wdb) != cudaSuccess)
+                return bad(CORR_ENOMEM, "flagnet allocation failed");
+        }
+    }
+    if (cudaMalloc(&net->scalar, 4) != cudaSuccess || cudaMalloc(&net->status, 4) != cudaSuccess ||
+        cudaMemset(net->status, 0, 4) != cudaSuccess)
+        return bad(CORR_ENOMEM, "flagnet allocation failed");
+    *out = net;
+    return CORR_OK;
+}
+
+int corr_flagnet_destroy(corr_flagnet_t net) {
+    if (!net) return CORR_OK;
+    cudaDeviceSynchronize();
+    for (int l = 0; l < NL; ++l) {
+        void* ps[] = {net->w[l], net->b[l], net->mw[l], net->vw[l], net->mb[l], net->vb[l], net->gw[l], net->gb[l],
+                      net->wf[l], net->wd[l]};
+        for (void* p : ps)
+            if (p) cudaFree(p);
+    }
+    for (int l = 0; l <= NL; ++l)
+        if (net->act[l]) cudaFree(net->act[l]);
+    void* ws[] = {net->logit, net->A, net->D, net->D2, net->dz32, net->dz, net->dzT, net->loss_part, net->scalar,
+                  net->norm, net->conf, net->status};
+    for (void* p : ws)
+        if (p) cudaFree(p);
+    cudaGetLastError();
+    delete net;
+    return CORR_OK;
+}
+
+int corr_flagnet_num_params(size_t* n) {
+    if (!n) return CORR_EINVAL;
+    *n = n_params();
+    return CORR_OK;
+}
+
+int corr_flagnet_set_params(corr_flagnet_t net, const float* params, size_t n) {
+    if (!net || !params || n != n_params()) return ffail(net, CORR_EINVAL, "params: wrong size");
+    size_t off = 0;
+    for (int l = 0; l < NL; ++l) {
+        const size_t nw = (size_t)CO[l] * CI[l] * 25;
+        FK(cudaMemcpy(net->w[l], params + off, nw * 4, cudaMemcpyHostToDevice));
+        off += nw;
+        FK(cudaMemcpy(net->b[l], params + off, CO[l] * 4, cudaMemcpyHostToDevice));
+        off += CO[l];
+        FK(cudaMemset(net->mw[l], 0, nw * 4));
+        FK(cudaMemset(net->vw[l], 0, nw * 4));
+        FK(cudaMemset(net->mb[l], 0, CO[l] * 4));
+        FK(cudaMemset(net->vb[l], 0, CO[l] * 4));
+    }
+    net->steps = 0;
+    return repack(net, nullptr) == CORR_OK ? (cudaDeviceSynchronize() == cudaSuccess ? CORR_OK : CORR_ECUDA)
+                                            : CORR_ECUDA;
+}
+
+int corr_flagnet_get_params(corr_flagnet_t net, float* params, size_t n) {
+    if (!net || !params || n != n_params()) return ffail(net, CORR_EINVAL, "params: wrong size");
+    FK(cudaDeviceSynchronize());
+    size_t off = 0;
+    for (int l = 0; l < NL; ++l) {
+        const size_t nw = (size_t)CO[l] * CI[l] * 25;
+        FK(cudaMemcpy(params + off, net->w[l], nw * 4, cudaMemcpyDeviceToHost));
+        off += nw;
+        FK(cudaMemcpy(params + off, net->b[l], CO[l] * 4, cudaMemcpyDeviceToHost));
+        off += CO[l];
+    }
+    return CORR_OK;
+}
+
+int corr_flagnet_prepare(corr_flagnet_t net, const float* d_power, int B, float* d_x, void* stream) {
+    if (!net || !d_power || !d_x || B < 1) return ffail(net, CORR_EINVAL, "bad argument");
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(normalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TPIX * 4);
+        attr = true;
+    }
+    normalize_kernel<<<B, 1024, TPIX * 4, static_cast<cudaStream_t>(stream)>>>(d_power, d_x);
+    FK(cudaGetLastError());
+    return CORR_OK;
+}
+
+int corr_flagnet_forward(corr_flagnet_t net, const float* d_x, int B, float* d_logits, void* stream) {
+    if (!net || !d_x || !d_logits || B < 1) return ffail(net, CORR_EINVAL, "bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = ensure_ws(net, B);
+    if (rc != CORR_OK) return rc;
+    rc = forward(net, d_x, B, st);
+    if (rc != CORR_OK) return rc;
+    FK(cudaMemcpyAsync(d_logits, net->logit, (size_t)B * TPIX * 4, cudaMemcpyDeviceToDevice, st));
+    return CORR_OK;
+}
+
+int corr_flagnet_loss_grad(corr_flagnet_t net, const float* d_x, const uint8_t* d_truth, int B, float* loss,
+                           float* grads, size_t n, void* stream) {
+    if (!net || !d_x || !d_truth || B < 1) return ffail(net, CORR_EINVAL, "bad argument");
+    if (grads && n != n_params()) return ffail(net, CORR_EINVAL, "grads: wrong size");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = ensure_ws(net, B);
+    if (rc != CORR_OK) return rc;
+    if ((rc = forward(net, d_x, B, st)) != CORR_OK) return rc;
+    if ((rc = backward(net, d_truth, B, st)) != CORR_OK) return rc;
+    FK(cudaStreamSynchronize(st));
+    if (loss) {
+        float s = 0.f;
+        FK(cudaMemcpy(&s, net->scalar, 4, cudaMemcpyDeviceToHost));
+        *loss = s / (float)((size_t)B * TPIX);
+    }
+    if (grads) {
+        size_t off = 0;
+        for (int l = 0; l < NL; ++l) {
+            const size_t nw = (size_t)CO[l] * CI[l] * 25;
+            FK(cudaMemcpy(grads + off, net->gw[l], nw * 4, cudaMemcpyDeviceToHost));
+            off += nw;
+            FK(cudaMemcpy(grads + off, net->gb[l], CO[l] * 4, cudaMemcpyDeviceToHost));
+            off += CO[l];
+        }
+    }
+    return CORR_OK;
+}
+
+int corr_flagnet_train_step(corr_flagnet_t net, const float* d_x, const uint8_t* d_truth, int B, float lr,
+                            float* loss, void* stream) {
+    if (!net || !d_x || !d_truth || B < 1 || !(lr > 0)) return ffail(net, CORR_EINVAL, "bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = ensure_ws(net, B);
+    if (rc != CORR_OK) return rc;
+    if ((rc = forward(net, d_x, B, st)) != CORR_OK) return rc;
+    if ((rc = backward(net, d_truth, B, st)) != CORR_OK) return rc;
+    ++net->steps;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - std::pow(b1, (float)net->steps), c2 = 1.f - std::pow(b2, (float)net->steps);
+    for (int l = 0; l < NL; ++l) {
+        const int nw = CO[l] * CI[l] * 25;
+        adam_kernel<<<blocks(nw), 256, 0, st>>>(net->w[l], net->gw[l], net->mw[l], net->vw[l], nw, lr, b1, b2, c1, c2,
+                                                1e-8f);
+        adam_kernel<<<blocks(CO[l]), 256, 0, st>>>(net->b[l], net->gb[l], net->mb[l], net->vb[l], CO[l], lr, b1, b2, c1,
+                                                   c2, 1e-8f);
+    }
+    FK(cudaGetLastError());
+    if ((rc = repack(net, st)) != CORR_OK) return rc;
+    if (loss) {
+        float s = 0.f;
+        FK(cudaMemcpyAsync(&s, net->scalar, 4, cudaMemcpyDeviceToHost, st));
+        FK(cudaStreamSynchronize(st));
+        *loss = s / (float)((size_t)B * TPIX);
+    }
+    return CORR_OK;
+}
+
+int corr_flagnet_flag(corr_flagnet_t net, const float* d_power, int B, float c_min, float sigma, uint8_t* d_flags,
+                      float* d_conf, void* stream) {
+    if (!net || !d_power || !d_flags || B < 1) return ffail(net, CORR_EINVAL, "bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = ensure_ws(net, B);
+    if (rc != CORR_OK) return rc;
+    if ((rc = corr_flagnet_prepare(net, d_power, B, net->norm, stream)) != CORR_OK) return rc;
+    if ((rc = forward(net, net->norm, B, st)) != CORR_OK) return rc;
+    confidence_kernel<<<B, 256, 0, st>>>(net->logit, net->conf);
+    const long long items = (long long)B * TH * (TW / 64);
+    final_flags_kernel<<<blocks(items, 4), 128, 0, st>>>(d_power, net->logit, net->conf, B, c_min, sigma, d_flags);
+    FK(cudaGetLastError());
+    if (d_conf) FK(cudaMemcpyAsync(d_conf, net->conf, (size_t)B * 4, cudaMemcpyDeviceToDevice, st));
+    return CORR_OK;
+}
+
+int corr_flagnet_status(corr_flagnet_t net, int* status) {
+    if (!net || !status) return ffail(net, CORR_EINVAL, "bad argument");
+    FK(cudaDeviceSynchronize());
+    FK(cudaMemcpy(status, net->status, 4, cudaMemcpyDeviceToHost));
+    FK(cudaMemset(net->status, 0, 4));
+    return CORR_OK;
+}
+
+}  // extern "C"

@@ -22,19 +22,21 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include "tc_common.cuh"
+
 #include <cstdio>
 
 namespace corr {
 
 namespace {
 
+using namespace tc;
+
 constexpr int kRows = 128;
 constexpr int kKTile = 128;                      // bytes of K per stage
 constexpr int kStages = 6;
 constexpr int kStageBytes = kRows * kKTile;      // 16 KiB
 constexpr uint32_t kTmemCols = 128;
-constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
-
 struct __align__(8) GramShared {
     uint64_t full[kStages];
     uint64_t empty[kStages];
@@ -42,67 +44,6 @@ struct __align__(8) GramShared {
     uint32_t tmem_addr;
     int abort;
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ unsigned long long globaltimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Wait for the phase of `bar` with the given parity; false after kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    if (mbar_try(bar, parity)) return true;
-    const unsigned long long t0 = globaltimer();
-    while (!mbar_try(bar, parity)) {
-        if (globaltimer() - t0 > kWaitNs) return false;
-    }
-    return true;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-        "[%4];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes, 8-row groups 1024 bytes apart (the layout TMA writes).
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);        // start address
-    d |= (uint64_t)(16 >> 4) << 16;                  // leading byte offset (unused here)
-    d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
-    d |= (uint64_t)1 << 46;                          // descriptor version
-    d |= (uint64_t)2 << 61;                          // 128-byte swizzle
-    return d;
-}
 
 // Instruction descriptor: dense, K-major A and B, M = N = 128, FP32
 // accumulator; A/B format BF16 (kind::f16) or E4M3 (kind::f8f6f4).
@@ -130,27 +71,6 @@ __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uin
             : "memory");
     }
 }
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     smem_u32(bar))
-                 : "memory");
-}
-
-#define CORR_R8(i) "=r"(r[i + 0]), "=r"(r[i + 1]), "=r"(r[i + 2]), "=r"(r[i + 3]), \
-                   "=r"(r[i + 4]), "=r"(r[i + 5]), "=r"(r[i + 6]), "=r"(r[i + 7])
-
-// 32 consecutive 32-bit TMEM columns of this warp's 32 lanes.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : CORR_R8(0), CORR_R8(8), CORR_R8(16), CORR_R8(24)
-        : "r"(taddr)
-        : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-#undef CORR_R8
 
 template <bool FP8>
 __global__ void __launch_bounds__(128, 1) gram_kernel(const __grid_constant__ CUtensorMap tmap, GramArgs A) {
@@ -247,7 +167,9 @@ __global__ void __launch_bounds__(128, 1) gram_kernel(const __grid_constant__ CU
     }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+}  // namespace
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
         void* p = nullptr;
@@ -260,8 +182,6 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-}  // namespace
-
 size_t gram_smem_bytes() { return (size_t)kStages * kStageBytes + sizeof(GramShared) + 1024; }
 
 int launch_gram(const GramArgs& a, cudaStream_t st) {
@@ -269,7 +189,7 @@ int launch_gram(const GramArgs& a, cudaStream_t st) {
     const int eb = a.fp8 ? 1 : 2;
     if (a.k_pitch % 128 != 0 || (long long)a.K * eb > a.k_pitch) return CORR_EINVAL;
     if ((reinterpret_cast<uintptr_t>(a.Q) & 15) != 0) return CORR_EINVAL;
-    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return CORR_ECUDA;
     CUtensorMap map;
     // dim 0: K columns (elements, only the valid ones: later columns read as

@@ -1038,7 +1038,6 @@ int corr_fengine_dev(corr_t h, const int8_t* d_samples, size_t n_samples, size_t
     if (n_spec == 0) return CORR_OK;
     if (n_spec > h->z_f_spectra) {
         cudaFree(h->d_z_f);
-    cudaFree(h->d_status);
         h->d_z_f = nullptr;
         CK(cudaMalloc(&h->d_z_f, sizeof(float2) * (size_t)n_spec * h->n_in_pad * h->n_chan));
         h->z_f_spectra = n_spec;
@@ -1395,6 +1394,32 @@ int corr_get_tuning(corr_t h, int* ring_mb, int* fir_spt) {
     if (!h) return fail(h, CORR_EINVAL, "NULL handle");
     if (ring_mb) *ring_mb = h->ring_mb;
     if (fir_spt) *fir_spt = h->fir_spt;
+    return CORR_OK;
+}
+
+int corr_spectrogram_dev(corr_t h, const int8_t* d_samples, size_t n_samples, size_t stride, int n_row,
+                         float* d_tiles, void* stream) {
+    if (!h || h->is_group) return fail(h, CORR_EINVAL, "NULL handle");
+    DeviceGuard dg(h->dev);
+    if (!d_samples || !d_tiles || n_row < 1 || stride < n_samples) return fail(h, CORR_EINVAL, "bad argument");
+    const long long n_spec = (long long)(n_samples / (size_t)h->M);
+    const long long rows = n_spec / n_row / 64 * 64;
+    if (rows < 64 || h->n_chan % 256) return fail(h, CORR_EINVAL, "need >= 64 rows and n_chan % 256 == 0");
+    CKRET(alloc_pipe(h, h->pd));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaMemsetAsync(d_tiles, 0, sizeof(float) * (size_t)h->n_in * rows * h->n_chan, st));
+    StreamView sv{d_samples, (long long)stride, 0, (long long)n_samples};
+    const long long s_total = rows * n_row;
+    for (long long s0 = 0; s0 < s_total; s0 += h->pd.v_cap) {
+        long long s1 = s0 + h->pd.v_cap;
+        if (s1 > s_total) s1 = s_total;
+        CKRET(launch_f(h, sv, h->tab_direct, h->pd.Z, 0, h->pd.v_cap - 1, h->pd.V, 0, h->pd.v_cap - 1, nullptr, s0, s1,
+                       st));
+        launch_spectrogram(h->pd.V, h->pd.v_cap - 1, h->n_chan, h->n_in, h->n_in_pad, s0, s1, n_row, (int)rows,
+                           d_tiles, st);
+        ++h->launches;
+        CK(cudaGetLastError());
+    }
     return CORR_OK;
 }
 

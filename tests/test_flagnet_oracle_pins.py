@@ -2,6 +2,8 @@
 gradients against finite differences in FP64, the loss against its direct
 formula, and the MAD fallback against the Eq. 2 oracle."""
 
+import math
+
 import numpy as np
 import pytest
 
@@ -83,3 +85,58 @@ def test_tile_input_and_confidence():
     assert fn.confidence(np.array([[0.0, 1.0], [0.5, 0.5]])) == 0.5
     pr, rc = fn.precision_recall(np.array([1, 1, 0, 0]), np.array([1, 0, 1, 0]))
     assert pr == 0.5 and rc == 0.5
+
+
+def test_params_flatten_order_and_roundtrip():
+    params = fn.init_params(7)
+    v = fn.flatten_params(params)
+    assert v.size == 52897
+    # layer 0: 32 x 1 x 5 x 5 weights, then 32 biases; layer 1 starts at 832
+    assert v[0] == params[0][0][0, 0, 0, 0] and v[7] == params[0][0][0, 0, 1, 2]
+    assert v[25] == params[0][0][1, 0, 0, 0] and v[800] == params[0][1][0]
+    assert v[832 + 25 * 3 + 5 * 4 + 1] == params[1][0][0, 3, 4, 1]
+    back = fn.unflatten_params(v)
+    for (w, b), (w2, b2) in zip(params, back):
+        assert np.array_equal(w, w2) and np.array_equal(b, b2)
+
+
+def test_dynamic_spectrum_tone_closed_form():
+    # A tone A cos(2 pi k0 n / M + theta) at a channel centre gives
+    # |Y[k0]|^2 = |A/2 e^{j theta} G(0) + A/2 e^{-j theta} G(2 k0)|^2 in every
+    # spectrum after the P - 1 filter-fill spectra (G the folded-filter DFT).
+    M, P, k0, A, theta, n_row = 64, 4, 5, 37.0, 0.7, 4
+    n = np.arange(M * 24)
+    x = (A * np.cos(2 * np.pi * k0 * n / M + theta))[None, :]
+    D = fn.dynamic_spectrum(x, M // 2, P, n_row)
+    h = fx.pfb_coefficients(M, P)
+    g = h.reshape(P, M).sum(axis=0)
+    m = np.arange(M)
+    y = (A / 2) * np.exp(1j * theta) * g.sum() + \
+        (A / 2) * np.exp(-1j * theta) * np.sum(g * np.exp(-4j * np.pi * k0 * m / M))
+    assert D.shape == (1, 6, 32)
+    for r in range(1, 6):
+        assert abs(D[0, r, k0] - abs(y) ** 2) < 1e-9 * abs(y) ** 2
+        assert np.argmax(D[0, r]) == k0
+
+
+def test_dynamic_spectrum_white_noise_level_and_delay_invariance():
+    # E P = sigma^2 sum h^2 away from DC; an integer delay only shifts time.
+    M, P, sig, n_row = 64, 4, 3.0, 50
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((1, M * 4000)) * sig
+    D = fn.dynamic_spectrum(x, M // 2, P, n_row)[0, 1:, 1:]
+    expect = sig ** 2 * np.sum(fx.pfb_coefficients(M, P) ** 2)
+    se = D.std() / math.sqrt(D.size)
+    assert abs(D.mean() - expect) < 5 * se
+    x2 = np.concatenate([np.zeros((1, 3 * M)), x[:, :M * 200]], axis=1)
+    D2 = fn.dynamic_spectrum(x2, M // 2, P, 1, tau=np.array([3.0 * M]))
+    D1 = fn.dynamic_spectrum(x[:, :M * 200], M // 2, P, 1)
+    np.testing.assert_allclose(D2[0, :190], D1[0, :190], rtol=1e-9, atol=1e-9)
+
+
+def test_to_tiles_index_map():
+    P = np.arange(2 * 128 * 512, dtype=float).reshape(2, 128, 512)
+    T = fn.to_tiles(P)
+    assert T.shape == (2, 2, 2, 64, 256)
+    # input 1, row 64 + 3, channel 256 + 7 -> tile (1, 1, 1), pixel (3, 7)
+    assert T[1, 1, 1, 3, 7] == P[1, 67, 263] == 1 * 128 * 512 + 67 * 512 + 263
