@@ -45,6 +45,11 @@ WORKLOADS = {
                     (8, 2048, 1024), (12, 4096, 512), (16, 8192, 256), (24, 512, 1024), (32, 1024, 512),
                     (32, 2048, 256)]) + " x 2 pols, 2^24 int8 samples/input (4.5 GB), one captured graph, "
                     "autotuned rings vs separate ungraphed runs"),
+    "c5": dict(n_ant=32, n_pol=1, n_chan=4096, taps=4, n_int=256, samples=64 * 256 * 8192, chunk=1 << 22,
+               desc="32 inputs int8 real, 64 rows x 256 spectra x 8192 samples/input (4 GiB), 4-tap PFB, "
+                    "4096 ch, dynamic spectra of 256-spectrum rows in 64 x 256 tiles (512 tiles), learned "
+                    "flagger (5x5 conv 1-32-32-32-1, BF16 tcgen05) with MAD fallback below confidence 0.9; "
+                    "noise + tones / chirps 0-30 dB + bursts 0-8 dB"),
     "c3": dict(n_ant=32, n_pol=2, n_chan=1024, taps=4, n_int=4096, samples=1 << 26, chunk=1 << 22,
                desc="32 ant x 2 pol int8 real, 2^26 samples/input (4 GiB), 4-tap PFB, 1024 ch, n_int 4096, "
                     "requantised to int8 (tensor-core X, BF16 MMA) vs the plain FP32 path"),
@@ -57,12 +62,13 @@ WORKLOADS = {
 #   X    reads the channelised spectra (4 B); finalise / flag: per integration.
 #   requant reads the spectra (4 B) and writes one code per component (1 B
 #   e4m3, 2 B int8-as-BF16); the tensor-core Gram reads the codes.
-STAGES = ["fir", "fft", "xengine", "finalize", "flag", "requant", "gram"]
+#   spectrogram reads the channelised spectra (4 B) for the flagger's tiles.
+STAGES = ["fir", "fft", "xengine", "finalize", "flag", "requant", "gram", "spectrogram"]
 KERNELS = {"fir": "fir_kernel<4>", "fft": "fft_kernel<M,false>", "xengine": "xengine_kernel",
            "finalize": "finalize_kernel", "flag": "mad_flag_kernel", "requant": "requant_kernel",
-           "gram": "gram_kernel (tcgen05)"}
+           "gram": "gram_kernel (tcgen05)", "spectrogram": "spectrogram_kernel"}
 BYTES_PER_SAMPLE = {"fir": 5.0, "fft": 8.0, "xengine": 4.0, "finalize": 0.0, "flag": 0.0, "requant": 6.0,
-                    "gram": 2.0}
+                    "gram": 2.0, "spectrogram": 4.0}
 
 
 def _spec(wl, rank, samples):
@@ -164,8 +170,36 @@ def cpu_baseline(wl, n_integrations=None):
                       % (samples // M, d["bytes"] >> 20, d["seconds"])}
 
 
+def run_reference_c5(args):
+    W = WORKLOADS["c5"]
+    secs = []
+    for i in range(args.warmup + args.steps):
+        d, spb = c5_cpu_sample()
+        if d is None:
+            print(json.dumps({"impl": "reference", "unavailable": "oracle run failed: " + spb}))
+            return
+        if i >= args.warmup:
+            secs.append(spb)
+    spb = sum(secs) / len(secs)
+    val = 1.0 / spb / 1e9
+    ms = spb * 32 * W["samples"] * 1e3
+    sample = ("per step: dynamic spectrum of one input over 16 rows + FP64 net forward and MAD on one tile, "
+              "scaled to the 32-input batch, FP64 numpy oracle, 1 thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "c5: " + W["desc"], "sample": sample, "l2": "host CPU path"},
+        "cpu_baseline": {"value": val, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
 def run_reference(args, rank, world):
     if rank != 0:
+        return
+    if args.workload == "c5":
+        run_reference_c5(args)
         return
     W = WORKLOADS[args.workload]
     M = 2 * W["n_chan"]
@@ -303,6 +337,196 @@ def run_batched(args, rank, world, local):
         dist.destroy_process_group()
 
 
+C5_C_MIN = 0.9
+C5_TRAIN_STEPS = 600
+
+
+def c5_cpu_sample():
+    """Oracle time per input byte of the flagging workload on a bounded
+    sample: the dynamic spectrum of one input over 16 rows (33.5 M samples),
+    then the net's FP64 forward pass and the MAD rule on one tile (a tile
+    covers 8.4 M samples of one input), one thread."""
+    code = (
+        "import sys, time, json, numpy as np\n"
+        "sys.path.insert(0, %r)\n"
+        "from fxsynth.streams import StreamSpec, make_stream\n"
+        "from oracle import flagnet_oracle as fn\n"
+        "x = make_stream(StreamSpec(n_ant=1, n_pol=1, n_samples=16 * 256 * 8192, seed=5, src_frac=0.0))\n"
+        "t0 = time.perf_counter()\n"
+        "P = fn.dynamic_spectrum(x, 4096, 4, 256)\n"
+        "t1 = time.perf_counter()\n"
+        "tile = np.concatenate([P[0]] * 4, axis=0)[:, :256]\n"
+        "z, _ = fn.forward(fn.init_params(0), fn.tile_input(tile)[None, None])\n"
+        "f = fn.mad_tile_flags(tile[None])\n"
+        "t2 = time.perf_counter()\n"
+        "print(json.dumps({'spec_s': t1 - t0, 'spec_samples': int(x.size), 'tile_s': t2 - t1}))\n"
+    ) % ROOT
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        return None, (r.stderr.strip().splitlines() or ["?"])[-1]
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    sec_per_byte = d["spec_s"] / d["spec_samples"] + d["tile_s"] / (64 * 256 * 8192 / 16)
+    return d, sec_per_byte
+
+
+def run_flagger(args, rank, world, local):
+    """Dynamic spectra + learned flagger: F-engine (PFB + FFT) -> 256-spectrum
+    power rows -> 64 x 256 tiles -> net (MAD on tiles below confidence 0.9)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2604_20640_gb300 import Correlator, FlagNet
+    from paper_2604_20640_gb300 import flagger, train_flagnet
+    from fxsynth.rfi_torch import RfiSpec, make_rfi_batch, noise_only
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    W = WORKLOADS["c5"]
+    n_row = 256
+    spec = RfiSpec(n_in=32, n_chan=W["n_chan"], n_row=n_row, seed=5000 + 100 * rank)
+    S = spec.n_samples
+    # --- the net: trained here on F-engine tiles of other seeds (8-input batches)
+    t_train = time.time()
+    src = train_flagnet.TileSource(n_in=8, n_chan=W["n_chan"], n_row=n_row, seed=7000 + 100 * rank, device=dev)
+    net = FlagNet(train_flagnet.init_params(0))
+    losses = train_flagnet.train(net, src, args.train_steps, 32, 1e-3)
+    t_train = time.time() - t_train
+    del src
+    # --- the measured batch and its truth (held out)
+    corr = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"])
+    one = Correlator(1, 1, W["n_chan"], W["taps"], W["n_int"])
+    level = flagger.noise_level(one, noise_only(spec, S, dev), n_row)
+    one.close()
+    b = make_rfi_batch(spec, 0, dev)
+    x = b["total"]
+    truth, t_nb, t_bb = flagger.truth_tiles(corr, b["nb"], b["bb"], b["g_nb"], b["g_bb"], level, n_row,
+                                            train_flagnet.TRUTH_FRACTION)
+    del b["nb"], b["bb"]
+    power = flagger.power_tiles(corr, x, n_row)
+    quality = train_flagnet.evaluate(net, power, truth, t_nb, t_bb, C5_C_MIN)
+    quality.update({"train_steps": args.train_steps, "train_tiles": 32 * args.train_steps,
+                    "train_seconds": round(t_train, 1),
+                    "loss_first_last": [float(np.mean(losses[:10])), float(np.mean(losses[-50:]))]})
+    B = power.shape[0]
+    flags = torch.empty((B, 64, 256), dtype=torch.uint8, device=dev)
+    conf = torch.empty(B, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        flagger.power_tiles(corr, x, n_row, out=power)
+        net.flag(power, flags, conf, c_min=C5_C_MIN)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    l0 = corr.launches + net.launches
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    launches = corr.launches + net.launches - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    bytes_step = spec.n_in * S
+    value = world * bytes_step / (ms * 1e-3) / 1e9
+    # --- per-stage split (one more instrumented pass, not in the timed region)
+    corr.set_option("stage_timing", 1)
+    corr.stage_times()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flagger.power_tiles(corr, x, n_row, out=power)
+    f0.record(stream)
+    net.flag(power, flags, conf, c_min=C5_C_MIN)
+    f1.record(stream)
+    torch.cuda.synchronize(dev)
+    stage_ms, stage_n = corr.stage_times()
+    corr.set_option("stage_timing", 0)
+    flag_ms = f0.elapsed_time(f1)
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    bf16 = peaks.get("bf16_tflops") or 1900.0
+    share = {k: stage_ms[i] for i, k in enumerate(STAGES) if stage_ms[i] > 0}
+    share["flagger"] = flag_ms
+    tot = sum(share.values()) or 1.0
+    share = {k: v / tot for k, v in share.items()}
+    flops_tile = 2.0 * 64 * 256 * 25 * (1 * 32 + 32 * 32 + 32 * 32 + 32 * 1)
+    dom = max((k for k in ("fir", "fft", "spectrogram")), key=lambda k: share.get(k, 0.0))
+    di = STAGES.index(dom)
+    n_samples_pass = bytes_step
+    bytes_per_launch = BYTES_PER_SAMPLE[dom] * n_samples_pass / max(1, stage_n[di])
+    avg_ms = stage_ms[di] / max(1, stage_n[di])
+    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+    roofline = {"kernel": KERNELS[dom], "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "peak_source": "measured" if peaks else "fallback",
+                "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms, "launches": stage_n[di],
+                "stage_share": share,
+                "flagger": {"bound": "tensor", "ms": flag_ms, "tiles": B,
+                            "achieved_tflops": flops_tile * B / (flag_ms * 1e-3) / 1e12, "peak": bf16,
+                            "unit": "TFLOP/s", "frac": flops_tile * B / (flag_ms * 1e-3) / 1e12 / bf16,
+                            "flop_per_tile": flops_tile}}
+    # --- end to end: pinned host input, H2D + dynamic spectra + flagger + D2H flags
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty((spec.n_in, S), dtype=torch.int8, pin_memory=True)
+        host.copy_(x)
+        fh = torch.empty((B, 64, 256), dtype=torch.uint8, pin_memory=True)
+
+        def e2e_step():
+            x.copy_(host, non_blocking=True)
+            step()
+            fh.copy_(flags, non_blocking=True)
+            torch.cuda.current_stream(dev).synchronize()
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        ems = (time.perf_counter() - t0) * 1e3 / args.steps
+        if world > 1:
+            t = torch.tensor([ems], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * bytes_step / (ems * 1e-3) / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": int(fh.numel()), "ms_per_step": ems}
+        del host
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu:
+            d, spb = c5_cpu_sample()
+            if d is None:
+                cpu = {"error": spb}
+            else:
+                cpu = {"value": 1.0 / spb / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                       "sample": "dynamic spectrum of one input over 16 rows (%d MiB int8, %.1f s) + FP64 net "
+                                 "forward and MAD on one tile (%.1f s), scaled per input byte, 1 thread"
+                                 % (d["spec_samples"] >> 20, d["spec_s"], d["tile_s"])}
+        out = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
+            "config": {"workload": "c5: " + W["desc"], "samples_per_input": S, "tiles": B,
+                       "l2": "inputs (%d MiB/step) larger than L2" % (bytes_step >> 20),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "gpu_launches": int(launches), "clocks": clk, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
+            "flagger_quality": quality,
+        }
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -316,6 +540,7 @@ def main():
     ap.add_argument("--precision", type=int, default=None,
                     help="0 FP32 CUDA-core X, 1 int8 / 2 e4m3 tensor-core X (default: FP32, int8 for c3)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
+    ap.add_argument("--train-steps", type=int, default=C5_TRAIN_STEPS, help="c5: Adam steps before timing")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -326,6 +551,9 @@ def main():
         return
     if args.workload == "c4":
         run_batched(args, rank, world, local)
+        return
+    if args.workload == "c5":
+        run_flagger(args, rank, world, local)
         return
 
     import torch

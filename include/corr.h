@@ -266,12 +266,14 @@ int corr_spectrogram_dev(corr_t h, const int8_t* d_samples, size_t n_samples, si
  * parameters), on tiles of 64 x 256 pixels x = ln(P / median(P)) of
  * autocorrelation power P.  BF16 operands, FP32 accumulation on tcgen05
  * tensor cores; FP32 master weights trained with Adam on the mean binary
- * cross-entropy.  Parameters are flattened layer by layer as w[o][c][u][v]
+ * cross-entropy.  Inference runs any n_tiles in passes of 64 tiles; the
+ * handle keeps a workspace of about 2.5 GB for them.  Parameters are flattened layer by layer as w[o][c][u][v]
  * then b[o].
  *   corr_flagnet_prepare    d_power [B][64][256] -> d_x (the network input)
  *   corr_flagnet_forward    d_x -> d_logits [B][64][256]
  *   corr_flagnet_loss_grad  mean loss and (host) gradients, no update
  *   corr_flagnet_train_step one Adam step (lr), returns the loss
+ *                           (both: 1 <= n_tiles <= 64, else CORR_EINVAL)
  *   corr_flagnet_flag       flags of B power tiles: the net's (p > 1/2) when
  *                           the tile confidence mean|2p-1| >= c_min, else
  *                           Eq. 2 along each row over 64-channel windows;
@@ -294,6 +296,8 @@ int corr_flagnet_train_step(corr_flagnet_t net, const float* d_x, const uint8_t*
 int corr_flagnet_flag(corr_flagnet_t net, const float* d_power, int n_tiles, float c_min, float sigma,
                       uint8_t* d_flags, float* d_conf, void* stream);
 int corr_flagnet_status(corr_flagnet_t net, int* status);
+/* Kernels this handle has launched since it was created. */
+long long corr_flagnet_kernel_launches(corr_flagnet_t net);
 
 /* Shapes of a handle: n_in, n_chan, taps, n_int, n_in_pad (any may be NULL). */
 int corr_shape(corr_t h, int* n_in, int* n_chan, int* taps, int* n_int, int* n_in_pad);
@@ -307,8 +311,8 @@ long long corr_kernel_launches(corr_t h);
  * With option "stage_timing" = 1 every kernel launch is bracketed by CUDA
  * events on its own stream.  This call waits for those events and returns,
  * for stages 0 FIR, 1 FFT (the two F-engine kernels), 2 X-engine,
- * 3 finalise, 4 flagging, 5 requantise, 6 tensor-core Gram (first n_stages
- * entries), the milliseconds and
+ * 3 finalise, 4 flagging, 5 requantise, 6 tensor-core Gram, 7 dynamic
+ * spectrum (first n_stages entries, at most 8), the milliseconds and
  * launch counts accumulated since the previous call, then clears them.
  * ms / counts may be NULL.
  */

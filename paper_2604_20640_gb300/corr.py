@@ -37,7 +37,7 @@ EXPORTED = [
     "corr_get_tuning", "corr_spectrogram_dev", "corr_flagnet_create", "corr_flagnet_destroy",
     "corr_flagnet_num_params", "corr_flagnet_set_params", "corr_flagnet_get_params", "corr_flagnet_prepare",
     "corr_flagnet_forward", "corr_flagnet_loss_grad", "corr_flagnet_train_step", "corr_flagnet_flag",
-    "corr_flagnet_status",
+    "corr_flagnet_status", "corr_flagnet_kernel_launches",
 ]
 
 
@@ -103,6 +103,7 @@ def load_library(path: str = LIB_PATH):
         "corr_flagnet_train_step": (_i, [_vp, _vp, _vp, _i, ctypes.c_float, ctypes.POINTER(ctypes.c_float), _vp]),
         "corr_flagnet_flag": (_i, [_vp, _vp, _i, ctypes.c_float, ctypes.c_float, _vp, _vp, _vp]),
         "corr_flagnet_status": (_i, [_vp, ctypes.POINTER(_i)]),
+        "corr_flagnet_kernel_launches": (_ll, [_vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -370,10 +371,10 @@ class Correlator:
 
     def stage_times(self):
         """(ms, counts) per stage (FIR, FFT, X, finalise, flag, requantise, tensor-core
-        Gram) since the last call."""
-        ms = (ctypes.c_double * 7)()
-        n = (ctypes.c_longlong * 7)()
-        self._check(self._L.corr_stage_times(self._h, ms, n, 7))
+        Gram, dynamic spectrum) since the last call."""
+        ms = (ctypes.c_double * 8)()
+        n = (ctypes.c_longlong * 8)()
+        self._check(self._L.corr_stage_times(self._h, ms, n, 8))
         return list(ms), list(n)
 
     @property
@@ -455,3 +456,7 @@ class FlagNet:
         st = _i()
         self._check(self._L.corr_flagnet_status(self._h, ctypes.byref(st)))
         return st.value
+
+    @property
+    def launches(self) -> int:
+        return int(self._L.corr_flagnet_kernel_launches(self._h))

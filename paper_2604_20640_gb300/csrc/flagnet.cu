@@ -14,6 +14,7 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -23,6 +24,7 @@ namespace {
 
 constexpr int TH = 64, TW = 256, TPIX = TH * TW;   // tile: 64 rows (time) x 256 channels
 constexpr int NL = 4;
+constexpr int kChunk = 64;   // tiles per pass through the network (workspace bound)
 constexpr int CI[NL] = {1, 32, 32, 32};
 constexpr int CO[NL] = {32, 32, 32, 1};
 
@@ -317,6 +319,7 @@ struct corr_flagnet_s {
     uint16_t* wf[NL] = {};   // [npad(Co)][kpad(25 Ci)]
     uint16_t* wd[NL] = {};   // [Ci][kpad(25 Co)]
     long long steps = 0;
+    long long launches = 0;  // kernels launched by this handle
     int cap = 0;             // tiles the workspace holds
     uint16_t* act[NL + 1] = {};   // act[0] input BF16 [P], act[l] [P][32]
     float* logit = nullptr;
@@ -379,6 +382,7 @@ int ensure_ws(corr_flagnet_t net, int B) {
 }
 
 int repack(corr_flagnet_t net, cudaStream_t st) {
+    net->launches += NL;
     for (int l = 0; l < NL; ++l) {
         const int n = CO[l] * CI[l] * 25;
         pack_weights_kernel<<<blocks(n), 256, 0, st>>>(net->w[l], CI[l], CO[l], kpad(25 * CI[l]), kpad(25 * CO[l]),
@@ -413,6 +417,7 @@ int gemm(corr_flagnet_t net, const void* A, const void* Bm, int M, int N, int K,
 // Forward pass over B normalised tiles x [B][64][256] -> logits.
 int forward(corr_flagnet_t net, const float* x, int B, cudaStream_t st) {
     const int P = B * TPIX;
+    net->launches += 1 + 3 * NL;
     input_bf16_kernel<<<blocks(P), 256, 0, st>>>(x, P, net->act[0]);
     for (int l = 0; l < NL; ++l) {
         const int C = CI[l], Kp = kpad(25 * C), Np = npad(CO[l]);
@@ -429,6 +434,7 @@ int forward(corr_flagnet_t net, const float* x, int B, cudaStream_t st) {
 // Loss and gradients (into gw/gb) for B tiles; loss summed on the device.
 int backward(corr_flagnet_t net, const uint8_t* truth, int B, cudaStream_t st) {
     const int P = B * TPIX;
+    net->launches += 2 + NL * 5 + (NL - 1) * 3;
     // rows 1..15 of the transposed gradient are the zero padding of the
     // 1-channel output layer's weight-gradient operand
     FK(cudaMemsetAsync(net->dzT + P, 0, (size_t)15 * P * 2, st));
@@ -570,6 +576,7 @@ int corr_flagnet_prepare(corr_flagnet_t net, const float* d_power, int B, float*
         attr = true;
     }
     normalize_kernel<<<B, 1024, TPIX * 4, static_cast<cudaStream_t>(stream)>>>(d_power, d_x);
+    ++net->launches;
     FK(cudaGetLastError());
     return CORR_OK;
 }
@@ -577,17 +584,21 @@ int corr_flagnet_prepare(corr_flagnet_t net, const float* d_power, int B, float*
 int corr_flagnet_forward(corr_flagnet_t net, const float* d_x, int B, float* d_logits, void* stream) {
     if (!net || !d_x || !d_logits || B < 1) return ffail(net, CORR_EINVAL, "bad argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int rc = ensure_ws(net, B);
+    int rc = ensure_ws(net, std::min(B, kChunk));
     if (rc != CORR_OK) return rc;
-    rc = forward(net, d_x, B, st);
-    if (rc != CORR_OK) return rc;
-    FK(cudaMemcpyAsync(d_logits, net->logit, (size_t)B * TPIX * 4, cudaMemcpyDeviceToDevice, st));
+    for (int t0 = 0; t0 < B; t0 += kChunk) {
+        const int n = std::min(kChunk, B - t0);
+        rc = forward(net, d_x + (size_t)t0 * TPIX, n, st);
+        if (rc != CORR_OK) return rc;
+        FK(cudaMemcpyAsync(d_logits + (size_t)t0 * TPIX, net->logit, (size_t)n * TPIX * 4, cudaMemcpyDeviceToDevice,
+                           st));
+    }
     return CORR_OK;
 }
 
 int corr_flagnet_loss_grad(corr_flagnet_t net, const float* d_x, const uint8_t* d_truth, int B, float* loss,
                            float* grads, size_t n, void* stream) {
-    if (!net || !d_x || !d_truth || B < 1) return ffail(net, CORR_EINVAL, "bad argument");
+    if (!net || !d_x || !d_truth || B < 1 || B > kChunk) return ffail(net, CORR_EINVAL, "bad argument");
     if (grads && n != n_params()) return ffail(net, CORR_EINVAL, "grads: wrong size");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = ensure_ws(net, B);
@@ -615,7 +626,8 @@ int corr_flagnet_loss_grad(corr_flagnet_t net, const float* d_x, const uint8_t* 
 
 int corr_flagnet_train_step(corr_flagnet_t net, const float* d_x, const uint8_t* d_truth, int B, float lr,
                             float* loss, void* stream) {
-    if (!net || !d_x || !d_truth || B < 1 || !(lr > 0)) return ffail(net, CORR_EINVAL, "bad argument");
+    if (!net || !d_x || !d_truth || B < 1 || B > kChunk || !(lr > 0))
+        return ffail(net, CORR_EINVAL, "bad argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = ensure_ws(net, B);
     if (rc != CORR_OK) return rc;
@@ -632,6 +644,7 @@ int corr_flagnet_train_step(corr_flagnet_t net, const float* d_x, const uint8_t*
                                                    c2, 1e-8f);
     }
     FK(cudaGetLastError());
+    net->launches += 2 * NL;
     if ((rc = repack(net, st)) != CORR_OK) return rc;
     if (loss) {
         float s = 0.f;
@@ -646,17 +659,25 @@ int corr_flagnet_flag(corr_flagnet_t net, const float* d_power, int B, float c_m
                       float* d_conf, void* stream) {
     if (!net || !d_power || !d_flags || B < 1) return ffail(net, CORR_EINVAL, "bad argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int rc = ensure_ws(net, B);
+    int rc = ensure_ws(net, std::min(B, kChunk));
     if (rc != CORR_OK) return rc;
-    if ((rc = corr_flagnet_prepare(net, d_power, B, net->norm, stream)) != CORR_OK) return rc;
-    if ((rc = forward(net, net->norm, B, st)) != CORR_OK) return rc;
-    confidence_kernel<<<B, 256, 0, st>>>(net->logit, net->conf);
-    const long long items = (long long)B * TH * (TW / 64);
-    final_flags_kernel<<<blocks(items, 4), 128, 0, st>>>(d_power, net->logit, net->conf, B, c_min, sigma, d_flags);
-    FK(cudaGetLastError());
-    if (d_conf) FK(cudaMemcpyAsync(d_conf, net->conf, (size_t)B * 4, cudaMemcpyDeviceToDevice, st));
+    for (int t0 = 0; t0 < B; t0 += kChunk) {
+        const int n = std::min(kChunk, B - t0);
+        const float* pw = d_power + (size_t)t0 * TPIX;
+        if ((rc = corr_flagnet_prepare(net, pw, n, net->norm, stream)) != CORR_OK) return rc;
+        if ((rc = forward(net, net->norm, n, st)) != CORR_OK) return rc;
+        confidence_kernel<<<n, 256, 0, st>>>(net->logit, net->conf);
+        net->launches += 2;
+        const long long items = (long long)n * TH * (TW / 64);
+        final_flags_kernel<<<blocks(items, 4), 128, 0, st>>>(pw, net->logit, net->conf, n, c_min, sigma,
+                                                              d_flags + (size_t)t0 * TPIX);
+        FK(cudaGetLastError());
+        if (d_conf) FK(cudaMemcpyAsync(d_conf + t0, net->conf, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+    }
     return CORR_OK;
 }
+
+long long corr_flagnet_kernel_launches(corr_flagnet_t net) { return net ? net->launches : 0; }
 
 int corr_flagnet_status(corr_flagnet_t net, int* status) {
     if (!net || !status) return ffail(net, CORR_EINVAL, "bad argument");

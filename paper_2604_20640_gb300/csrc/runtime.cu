@@ -57,7 +57,7 @@ struct Tables {
 // Optional CUDA-event brackets around every kernel launch, per stage
 // (0 FIR, 1 FFT, 2 X-engine, 3 finalise, 4 flag, 5 requantise, 6 tensor-core
 // Gram).
-constexpr int kStages = 7;
+constexpr int kStages = 8;
 struct StageTimer {
     bool on = false;
     std::vector<cudaEvent_t> pool;
@@ -1415,9 +1415,11 @@ int corr_spectrogram_dev(corr_t h, const int8_t* d_samples, size_t n_samples, si
         if (s1 > s_total) s1 = s_total;
         CKRET(launch_f(h, sv, h->tab_direct, h->pd.Z, 0, h->pd.v_cap - 1, h->pd.V, 0, h->pd.v_cap - 1, nullptr, s0, s1,
                        st));
-        launch_spectrogram(h->pd.V, h->pd.v_cap - 1, h->n_chan, h->n_in, h->n_in_pad, s0, s1, n_row, (int)rows,
-                           d_tiles, st);
-        ++h->launches;
+        {
+            Timed t_(h, 7, st);
+            launch_spectrogram(h->pd.V, h->pd.v_cap - 1, h->n_chan, h->n_in, h->n_in_pad, s0, s1, n_row, (int)rows,
+                               d_tiles, st);
+        }
         CK(cudaGetLastError());
     }
     return CORR_OK;

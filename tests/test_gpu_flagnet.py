@@ -192,3 +192,32 @@ def test_training_learns_and_beats_mad(lib):
     print("net precision %.3f recall %.3f | MAD precision %.3f recall %.3f" % (p_net, r_net, p_mad, r_mad))
     assert r_net > r_mad + 0.15
     assert p_net > 0.8
+
+
+def test_noise_level_matches_filter_energy(lib):
+    # E|Y_k|^2 = sigma_q^2 sum_n h[n]^2 for white noise away from DC, with
+    # sigma_q^2 = 16^2 + 1/12 for int8-rounded N(0, 16^2) (no clipping at 8 sigma)
+    from fxsynth.rfi_torch import RfiSpec, noise_only
+    from paper_2604_20640_gb300 import flagger
+    spec = RfiSpec(n_in=1, n_chan=1024, n_row=64)
+    one = lib.Correlator(1, 1, 1024, 4, 64)
+    lvl = flagger.noise_level(one, noise_only(spec, spec.n_samples, "cuda"), 64).cpu().numpy()
+    expect = (16.0 ** 2 + 1.0 / 12) * np.sum(fx.pfb_coefficients(2048, 4) ** 2)
+    # 64 rows x 64 spectra per channel: relative standard error 1/64 per channel
+    assert abs(np.mean(lvl[4:-4]) / expect - 1) < 3e-3
+    assert np.max(np.abs(lvl[4:-4] / expect - 1)) < 6 / 64
+
+
+def test_c5_pipeline_trained_net_beats_mad(lib):
+    from paper_2604_20640_gb300 import train_flagnet
+    src = train_flagnet.TileSource(n_in=4, n_chan=1024, n_row=64, seed=321)
+    net = lib.FlagNet(train_flagnet.init_params(0))
+    losses = train_flagnet.train(net, src, 400, 32, 1e-3)
+    assert np.mean(losses[-40:]) < 0.5 * np.mean(losses[:5])
+    p, t, tn, tb, _ = src.batch(10 ** 6, with_parts=True)
+    q = train_flagnet.evaluate(net, p, t, tn, tb)
+    print(q)
+    assert 0.005 < q["truth_fraction"] < 0.5
+    assert q["net"]["recall"] > q["mad"]["recall"] + 0.1
+    assert q["net"]["precision"] > 0.8
+    assert q["net"]["recall_broadband"] > q["mad"]["recall_broadband"]
