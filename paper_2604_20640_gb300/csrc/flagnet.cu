@@ -34,35 +34,97 @@ __host__ __device__ inline int npad(int co) { return co < 16 ? 16 : co; }
 __device__ __forceinline__ uint16_t f2bf(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ float bf2f(uint16_t x) { return __bfloat162float(__ushort_as_bfloat16(x)); }
 
-// A[p][k] = X[n][i+u-2][j+v-2][c] (k = (5u+v) C + c < 25 C, else 0); sgn = -1
+// A[p][k] = X[n][i+u-2][j+v-2][c] (k = (5u+v) C + c < 25 C, else 0) for
+// C = 32: one 16-byte chunk (8 channels of one tap) per thread.  sgn = -1
 // gives the negated offsets of the data-gradient product.
-__global__ void im2col_kernel(const uint16_t* X, int C, int P, int Kp, int sgn, uint16_t* A) {
+__global__ void im2col32_kernel(const uint4* X, int P, int sgn, uint4* A) {
+    constexpr int KP = 832, SL = KP / 8, CS = 4;     // 104 chunks per row, 4 per pixel
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)P * Kp) return;
-    const int p = (int)(idx / Kp), k = (int)(idx % Kp);
-    uint16_t v = 0;
-    if (k < 25 * C) {
-        const int c = k % C, uv = k / C, u = uv / 5, w = uv % 5;
+    if (idx >= (long long)P * SL) return;
+    const int p = (int)(idx / SL), s = (int)(idx % SL);
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (s < 25 * CS) {
+        const int tap = s >> 2, c8 = s & 3, u = tap / 5, w = tap % 5;
         const int n = p / TPIX, ij = p % TPIX, i = ij / TW, j = ij % TW;
         const int ii = i + sgn * (u - 2), jj = j + sgn * (w - 2);
-        if (ii >= 0 && ii < TH && jj >= 0 && jj < TW) v = X[((size_t)n * TPIX + ii * TW + jj) * C + c];
+        if (ii >= 0 && ii < TH && jj >= 0 && jj < TW) v = X[((size_t)n * TPIX + ii * TW + jj) * CS + c8];
     }
     A[idx] = v;
 }
 
-// AT[k][p] = A[p][k] (the im2col operand of the weight gradient, K = pixels).
-__global__ void im2colT_kernel(const uint16_t* X, int C, int P, int Kp, uint16_t* AT) {
+// The same for C = 1 (K = 25 taps padded to 64): 8 taps per thread.
+__global__ void im2col1_kernel(const uint16_t* X, int P, int sgn, uint4* A) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)P * Kp) return;
-    const int k = (int)(idx / P), p = (int)(idx % P);
-    uint16_t v = 0;
-    if (k < 25 * C) {
-        const int c = k % C, uv = k / C, u = uv / 5, w = uv % 5;
-        const int n = p / TPIX, ij = p % TPIX, i = ij / TW, j = ij % TW;
-        const int ii = i + u - 2, jj = j + w - 2;
-        if (ii >= 0 && ii < TH && jj >= 0 && jj < TW) v = X[((size_t)n * TPIX + ii * TW + jj) * C + c];
+    if (idx >= (long long)P * 8) return;
+    const int p = (int)(idx >> 3), s = (int)(idx & 7);
+    const int n = p / TPIX, ij = p % TPIX, i = ij / TW, j = ij % TW;
+    uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int k = s * 8 + e;
+        if (k < 25) {
+            const int ii = i + sgn * (k / 5 - 2), jj = j + sgn * (k % 5 - 2);
+            if (ii >= 0 && ii < TH && jj >= 0 && jj < TW)
+                w[e >> 1] |= (uint32_t)X[(size_t)n * TPIX + ii * TW + jj] << (16 * (e & 1));
+        }
     }
-    AT[idx] = v;
+    A[idx] = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// AT[k][p] = A[p][k] for C = 32 (the weight-gradient operand, K = pixels):
+// one CTA per 64-pixel row segment stages the 5 x 68-pixel neighbourhood in
+// shared memory (channel stride padded to 34), then writes each k-row's 64
+// pixels as 8 coalesced 16-byte chunks.
+constexpr int kSegPix = 64, kHalo = kSegPix + 4, kCPad = 34;
+__global__ void __launch_bounds__(256) im2colT32_kernel(const uint16_t* X, int P, uint16_t* AT) {
+    __shared__ uint32_t sx[5 * kHalo * kCPad / 2];
+    const int p0 = blockIdx.x * kSegPix;
+    const int n = p0 / TPIX, i = (p0 % TPIX) / TW, j0 = p0 % TW;
+    // stage: (u, jj, c8) chunks of 8 channels
+    for (int t = threadIdx.x; t < 5 * kHalo * 4; t += blockDim.x) {
+        const int c8 = t & 3, jj = (t >> 2) % kHalo, u = (t >> 2) / kHalo;
+        const int ii = i + u - 2, jx = j0 + jj - 2;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (ii >= 0 && ii < TH && jx >= 0 && jx < TW)
+            v = reinterpret_cast<const uint4*>(X + ((size_t)n * TPIX + ii * TW + jx) * 32)[c8];
+        uint32_t* d = sx + ((u * kHalo + jj) * kCPad + c8 * 8) / 2;
+        d[0] = v.x;
+        d[1] = v.y;
+        d[2] = v.z;
+        d[3] = v.w;
+    }
+    __syncthreads();
+    const uint16_t* s16 = reinterpret_cast<const uint16_t*>(sx);
+    for (int t = threadIdx.x; t < 832 * 8; t += blockDim.x) {
+        const int g = t & 7, k = t >> 3;
+        uint32_t w[4] = {0, 0, 0, 0};
+        if (k < 800) {
+            const int tap = k >> 5, c = k & 31, u = tap / 5, v = tap % 5;
+            const uint16_t* src = s16 + (u * kHalo + g * 8 + v) * kCPad + c;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) w[e >> 1] |= (uint32_t)src[e * kCPad] << (16 * (e & 1));
+        }
+        *reinterpret_cast<uint4*>(AT + (size_t)k * P + p0 + g * 8) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// AT[k][p] for C = 1 (k < 25 taps, rows up to 64 zero): 8 pixels per thread.
+__global__ void im2colT1_kernel(const uint16_t* X, int P, uint16_t* AT) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)P * 8) return;
+    const int k = (int)(idx / (P / 8)), p = (int)(idx % (P / 8)) * 8;
+    const int n = p / TPIX, ij = p % TPIX, i = ij / TW, j = ij % TW;
+    uint32_t w[4] = {0, 0, 0, 0};
+    if (k < 25) {
+        const int ii = i + k / 5 - 2;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int jj = j + e + k % 5 - 2;
+            if (ii >= 0 && ii < TH && jj >= 0 && jj < TW)
+                w[e >> 1] |= (uint32_t)X[(size_t)n * TPIX + ii * TW + jj] << (16 * (e & 1));
+        }
+    }
+    *reinterpret_cast<uint4*>(AT + (size_t)k * P + p) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 __global__ void input_bf16_kernel(const float* x, int P, uint16_t* X) {
@@ -268,12 +330,14 @@ __global__ void final_flags_kernel(const float* power, const float* logit, const
 
 // Autocorrelation power of row `row` (n_row spectra) for input a and channel
 // k, mean |Y|^2 = |U|^2 / 4 (U = 2Y from the F-engine), accumulated in tile
-// order: tile (a, row / 64, k / 256), pixel (row % 64, k % 256).
-__global__ void spectrogram_kernel(const float2* V, long long v_mask, int n_chan, int n_in_pad, long long s_begin,
-                                   long long s_end, int n_row, int rows, float* tiles) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const int a = blockIdx.y;
-    if (k >= n_chan) return;
+// order: tile (a, row / 64, k / 256), pixel (row % 64, k % 256).  One thread
+// per (k, a), inputs fastest, so a warp reads contiguous spectra.
+__global__ void spectrogram_kernel(const float2* V, long long v_mask, int n_chan, int n_in, int n_in_pad,
+                                   long long s_begin, long long s_end, int n_row, int rows, float* tiles) {
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long long)n_chan * n_in_pad) return;
+    const int k = (int)(id / n_in_pad), a = (int)(id % n_in_pad);
+    if (a >= n_in) return;
     const int n_cb = n_chan / TW, n_rb = rows / TH;
     long long s = s_begin;
     while (s < s_end) {
@@ -295,8 +359,9 @@ __global__ void spectrogram_kernel(const float2* V, long long v_mask, int n_chan
 
 void launch_spectrogram(const float2* V, long long v_mask, int n_chan, int n_in, int n_in_pad, long long s_begin,
                         long long s_end, int n_row, int rows, float* tiles, cudaStream_t st) {
-    dim3 grid((unsigned)((n_chan + 127) / 128), (unsigned)n_in);
-    spectrogram_kernel<<<grid, 128, 0, st>>>(V, v_mask, n_chan, n_in_pad, s_begin, s_end, n_row, rows, tiles);
+    const long long n = (long long)n_chan * n_in_pad;
+    spectrogram_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(V, v_mask, n_chan, n_in, n_in_pad, s_begin, s_end,
+                                                                      n_row, rows, tiles);
 }
 
 }  // namespace corr
@@ -392,6 +457,15 @@ int repack(corr_flagnet_t net, cudaStream_t st) {
     return CORR_OK;
 }
 
+// im2col of NHWC BF16 activations with C = 1 or 32 channels.
+void im2col(const uint16_t* X, int C, int P, int sgn, uint16_t* A, cudaStream_t st) {
+    if (C == 32)
+        im2col32_kernel<<<blocks((long long)P * 104), 256, 0, st>>>(reinterpret_cast<const uint4*>(X), P, sgn,
+                                                                    reinterpret_cast<uint4*>(A));
+    else
+        im2col1_kernel<<<blocks((long long)P * 8), 256, 0, st>>>(X, P, sgn, reinterpret_cast<uint4*>(A));
+}
+
 int gemm(corr_flagnet_t net, const void* A, const void* Bm, int M, int N, int K, int lda, int ldb, int splits,
          float* D, float* out, cudaStream_t st) {
     GemmArgs g{};
@@ -421,7 +495,7 @@ int forward(corr_flagnet_t net, const float* x, int B, cudaStream_t st) {
     input_bf16_kernel<<<blocks(P), 256, 0, st>>>(x, P, net->act[0]);
     for (int l = 0; l < NL; ++l) {
         const int C = CI[l], Kp = kpad(25 * C), Np = npad(CO[l]);
-        im2col_kernel<<<blocks((long long)P * Kp), 256, 0, st>>>(net->act[l], C, P, Kp, 1, net->A);
+        im2col(net->act[l], C, P, 1, net->A, st);
         int rc = gemm(net, net->A, net->wf[l], P, Np, Kp, Kp * 2, Kp * 2, 1, net->D, nullptr, st);
         if (rc != CORR_OK) return rc;
         fwd_epilogue_kernel<<<blocks((long long)P * CO[l]), 256, 0, st>>>(net->D, P, CO[l], Np, net->b[l], l == NL - 1,
@@ -446,7 +520,8 @@ int backward(corr_flagnet_t net, const uint8_t* truth, int B, cudaStream_t st) {
         // bias gradient
         colsum_kernel<<<Co, 256, 0, st>>>(net->dz32, P, Co, net->gb[l]);
         // weight gradient: DW[Kp][Np] = A^T[Kp][P] . dZ^T[Np][P]
-        im2colT_kernel<<<blocks((long long)P * Kp), 256, 0, st>>>(net->act[l], C, P, Kp, net->A);
+        if (C == 32) im2colT32_kernel<<<P / kSegPix, 256, 0, st>>>(net->act[l], P, net->A);
+        else im2colT1_kernel<<<blocks((long long)P * 8), 256, 0, st>>>(net->act[l], P, net->A);
         const int splits = 64;
         int rc = gemm(net, net->A, net->dzT, Kp, Np, P, P * 2, P * 2, splits, net->D, net->D2, st);
         if (rc != CORR_OK) return rc;
@@ -454,7 +529,7 @@ int backward(corr_flagnet_t net, const uint8_t* truth, int B, cudaStream_t st) {
         if (l == 0) break;
         // data gradient: dX[P][C] = A'[P][Kd] . Wd[C][Kd], then ReLU of layer l-1
         const int Kd = kpad(25 * Co);
-        im2col_kernel<<<blocks((long long)P * Kd), 256, 0, st>>>(net->dz, Co, P, Kd, -1, net->A);
+        im2col(net->dz, Co, P, -1, net->A, st);
         rc = gemm(net, net->A, net->wd[l], P, 32, Kd, Kd * 2, Kd * 2, 1, net->D, nullptr, st);
         if (rc != CORR_OK) return rc;
         relu_grad_kernel<<<blocks((long long)P * C), 256, 0, st>>>(net->D, net->act[l], P, C, net->dz32, net->dz,
