@@ -302,6 +302,18 @@ __device__ __forceinline__ FirInput fir_input(const FirArgs& A, int in, bool has
     return r;
 }
 
+// Four int8 samples of one input row from stream index n, each read only
+// inside [lo, vhi) (zero elsewhere).  Out of line: only the first and last
+// frames of a stream take this path.
+__device__ __noinline__ uint32_t load4_checked(const int8_t* row, long long lo, long long vhi, long long n) {
+    uint32_t v = 0;
+    for (int b = 0; b < 4; ++b) {
+        const long long i = n + b;
+        if (i >= lo && i < vhi) v |= (uint32_t)(uint8_t)row[i] << (8 * b);
+    }
+    return v;
+}
+
 // Raw int8 word (4 branches) of frame f of one input; zero before the stream.
 __device__ __forceinline__ uint32_t fir_word(const FirArgs& A, const FirInput& I, long long f) {
     uint32_t w = 0u;
@@ -310,7 +322,9 @@ __device__ __forceinline__ uint32_t fir_word(const FirArgs& A, const FirInput& I
             const uint32_t* q = I.q + (f << (A.lgM - 2));
             w = __funnelshift_r(__ldg(q), __ldg(q + 1), I.sh);
         } else {
-            w = load4(A.src, I.in, f * A.M + I.n0);
+            const long long lo = A.src.base > 0 ? A.src.base : 0;
+            w = load4_checked(A.src.x + (long long)I.in * A.src.stride - A.src.base, lo, A.src.vhi,
+                              f * A.M + I.n0);
         }
     }
     return w;
@@ -320,88 +334,117 @@ __device__ __forceinline__ void fir_frame(const FirArgs& A, const FirInput& I, l
     unpack4(fir_word(A, I, f), x);
 }
 
-// y_s[m] = sum_p h[pM + m] x'[(s - P + 1 + p) M + m] for 4 branches of both
-// inputs of a pair, over spectra [s_lo, s_hi).  The window holds frames
+// Packed FP32 pairs (sm_100+): two lanes of one 64-bit register per op.
+__device__ __forceinline__ unsigned long long f2u(float2 v) {
+    return (unsigned long long)__float_as_uint(v.x) | ((unsigned long long)__float_as_uint(v.y) << 32);
+}
+__device__ __forceinline__ float2 u2f(unsigned long long u) {
+    return make_float2(__uint_as_float((unsigned)u), __uint_as_float((unsigned)(u >> 32)));
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)), "l"(f2u(c)));
+    return u2f(r);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(r);
+}
+
+// Exact int8 -> float for four packed samples as two float pairs (the
+// mantissa trick of unpack4 with packed subtractions).
+__device__ __forceinline__ void unpack4x2(uint32_t w, float2& lo, float2& hi) {
+    const uint32_t f = w ^ 0x80808080u;
+    const float2 bias = make_float2(8388736.0f, 8388736.0f);
+    lo = sub2(make_float2(__int_as_float((int)__byte_perm(f, 0x4B000000u, 0x7440)),
+                          __int_as_float((int)__byte_perm(f, 0x4B000000u, 0x7441))), bias);
+    hi = sub2(make_float2(__int_as_float((int)__byte_perm(f, 0x4B000000u, 0x7442)),
+                          __int_as_float((int)__byte_perm(f, 0x4B000000u, 0x7443))), bias);
+}
+
+// y_s[m] = sum_p h[pM + m] x'[(s - P + 1 + p) M + m] for 4 branches of one
+// input over spectra [s_lo, s_hi).  Lanes 2q and 2q+1 of a warp take the
+// same branches of the two inputs of a pair and swap half their outputs with
+// one shuffle each, so that every lane stores two packed points
+// z[m] = (y_a[m], y_b[m]) as one 16-byte word.  The window holds frames
 // s-P+1 .. s in a circular register array indexed at compile time: spectra
-// are processed in steps of P so frame f always sits in slot (f - base) mod P.
+// are processed in blocks of P so frame f always sits in slot (f - base) mod
+// P.  Inside the frames whose words are in bounds for this thread the block
+// loop runs without checks; ring slots advance in 32-bit arithmetic.
 template <int P>
-__global__ void __launch_bounds__(kFirThreads, P <= 4 ? 3 : 1) fir_kernel(const FirArgs A) {
+__global__ void __launch_bounds__(kFirThreads, P <= 4 ? 3 : (P <= 8 ? 2 : 1)) fir_kernel(const FirArgs A) {
     const int M = A.M;
-    const int g = blockIdx.x * kFirThreads + threadIdx.x;
-    if (g >= (M >> 2)) return;
-    const int m0 = 4 * g;
+    const int t = blockIdx.x * kFirThreads + threadIdx.x;   // (branch group, input of pair)
+    if (t >= (M >> 1)) return;
+    const int odd = t & 1;
+    const int m0 = 4 * (t >> 1);
     const int pair = blockIdx.y;
-    const int a = 2 * pair, b = a + 1;
+    const int in = 2 * pair + odd;
     const long long s_lo = A.s_begin + (long long)blockIdx.z * A.spt;
     long long s_hi = s_lo + A.spt;
     if (s_hi > A.s_end) s_hi = A.s_end;
-    if (s_lo >= s_hi) return;
-    const FirInput Ia = fir_input(A, a, a < A.n_in, m0, A.coarse[a]);
-    const FirInput Ib = fir_input(A, b, b < A.n_in, m0, A.coarse[b]);
+    if (s_lo >= s_hi) return;   // uniform over the CTA
+    const bool has = in < A.n_in;
+    const FirInput I = fir_input(A, in, has, m0, has ? A.coarse[in] : 0);
 
-    float hr[P][4];
+    float2 h[P][2];
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        const float4 t = __ldg(reinterpret_cast<const float4*>(A.h + (size_t)p * M + m0));
-        hr[p][0] = t.x; hr[p][1] = t.y; hr[p][2] = t.z; hr[p][3] = t.w;
+        const float4 v = __ldg(reinterpret_cast<const float4*>(A.h + (size_t)p * M + m0));
+        h[p][0] = make_float2(v.x, v.y);
+        h[p][1] = make_float2(v.z, v.w);
     }
-    float wa[P][4], wb[P][4];
+    float2 w[P][2];
     const long long base_f = s_lo - (P - 1);
 #pragma unroll
-    for (int q = 0; q < P - 1; ++q) {
-        fir_frame(A, Ia, base_f + q, wa[q]);
-        fir_frame(A, Ib, base_f + q, wb[q]);
+    for (int q = 0; q < P - 1; ++q) unpack4x2(fir_word(A, I, base_f + q), w[q][0], w[q][1]);
+    // even lanes store branches m0, m0+1; odd lanes m0+2, m0+3
+    float2* const zp = A.Z + (size_t)pair * M + m0 + 2 * odd;
+    const unsigned zstride = (unsigned)(A.n_pairs * M);
+    const unsigned zmask = (unsigned)A.z_mask;
+    unsigned slot = (unsigned)((s_lo - A.z_origin) & A.z_mask);
+    const int step = M >> 2;
+    // frames s0 .. s0+P-1 are unchecked when all lie in [f_safe_lo, f_safe_hi]
+    const long long f_safe_lo = I.f_lo < 0 ? 0 : I.f_lo;
+    long long s_fast_end = I.f_hi - (P - 1) + 1;        // blocks starting below this are safe
+    if (s_fast_end > s_hi - (P - 1)) s_fast_end = s_hi - (P - 1);
+
+    auto emit = [&](int q, uint32_t word) {
+        unpack4x2(word, w[(q + P - 1) % P][0], w[(q + P - 1) % P][1]);
+        float2 y0 = make_float2(0.f, 0.f), y1 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const int sl = (q + p) % P;            // frame s - P + 1 + p
+            y0 = fma2(h[p][0], w[sl][0], y0);
+            y1 = fma2(h[p][1], w[sl][1], y1);
+        }
+        const float x0 = __shfl_xor_sync(0xffffffffu, odd ? y0.x : y1.x, 1);
+        const float x1 = __shfl_xor_sync(0xffffffffu, odd ? y0.y : y1.y, 1);
+        const float4 o = odd ? make_float4(x0, y1.x, x1, y1.y) : make_float4(y0.x, x0, y0.y, x1);
+        *reinterpret_cast<float4*>(zp + (size_t)slot * zstride) = o;
+        slot = (slot + 1) & zmask;
+    };
+
+    long long s0 = s_lo;
+    if (has && s0 >= f_safe_lo) {
+        const uint32_t* qp = I.q + (s0 << (A.lgM - 2));
+        for (; s0 < s_fast_end; s0 += P) {
+            uint32_t r[P];
+#pragma unroll
+            for (int q = 0; q < P; ++q) r[q] = __funnelshift_r(__ldg(qp + q * step), __ldg(qp + q * step + 1), I.sh);
+            qp += P * step;
+#pragma unroll
+            for (int q = 0; q < P; ++q) emit(q, r[q]);
+        }
     }
-    float2* zp = A.Z + (size_t)pair * M + m0;
-    const size_t zstride = (size_t)A.n_pairs * M;
-    long long f_safe_lo = Ia.f_lo > Ib.f_lo ? Ia.f_lo : Ib.f_lo;
-    long long f_safe_hi = Ia.f_hi < Ib.f_hi ? Ia.f_hi : Ib.f_hi;
-    if (f_safe_lo < 0) f_safe_lo = 0;
-    for (long long s0 = s_lo; s0 < s_hi; s0 += P) {
-        // Issue the loads of the block's P new frames first (independent of
-        // the arithmetic below), then consume them.  Inside the safe frame
-        // range of both inputs no bounds checks are needed.
-        uint32_t ra[P], rb[P];
-        if (s0 >= f_safe_lo && s0 + P - 1 <= f_safe_hi && s0 + P <= s_hi) {
-            const uint32_t* qa = Ia.q + (s0 << (A.lgM - 2));
-            const uint32_t* qb = Ib.q + (s0 << (A.lgM - 2));
-            const int step = M >> 2;
+    for (; s0 < s_hi; s0 += P) {
+        uint32_t r[P];
 #pragma unroll
-            for (int q = 0; q < P; ++q) {
-                ra[q] = Ia.has ? __funnelshift_r(__ldg(qa + q * step), __ldg(qa + q * step + 1), Ia.sh) : 0u;
-                rb[q] = Ib.has ? __funnelshift_r(__ldg(qb + q * step), __ldg(qb + q * step + 1), Ib.sh) : 0u;
-            }
-        } else {
+        for (int q = 0; q < P; ++q) r[q] = (s0 + q < s_hi) ? fir_word(A, I, s0 + q) : 0u;
 #pragma unroll
-            for (int q = 0; q < P; ++q) {
-                const long long s = s0 + q;
-                ra[q] = s < s_hi ? fir_word(A, Ia, s) : 0u;
-                rb[q] = s < s_hi ? fir_word(A, Ib, s) : 0u;
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < P; ++q) {
-            const long long s = s0 + q;
-            if (s < s_hi) {
-                const int slot_new = (q + P - 1) % P;      // frame s
-                unpack4(ra[q], wa[slot_new]);
-                unpack4(rb[q], wb[slot_new]);
-                float ya[4] = {0.f, 0.f, 0.f, 0.f}, yb[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    const int sl = (q + p) % P;            // frame s - P + 1 + p
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        ya[i] = fmaf(hr[p][i], wa[sl][i], ya[i]);
-                        yb[i] = fmaf(hr[p][i], wb[sl][i], yb[i]);
-                    }
-                }
-                const long long zs = (s - A.z_origin) & A.z_mask;
-                float4* o = reinterpret_cast<float4*>(zp + (size_t)zs * zstride);
-                o[0] = make_float4(ya[0], yb[0], ya[1], yb[1]);
-                o[1] = make_float4(ya[2], yb[2], ya[3], yb[3]);
-            }
-        }
+        for (int q = 0; q < P; ++q)
+            if (s0 + q < s_hi) emit(q, r[q]);   // uniform over the CTA
     }
 }
 
@@ -513,16 +556,22 @@ std::vector<float2> fft_twiddle_table(int M) {
 
 template <int M, bool ROT>
 static void launch_fft_m(const FftArgs& a, cudaStream_t st) {
-    static bool attr_set = false;
+    static int resident = 0;     // CTAs per SM at this kernel's registers and shared memory
+    static int sms = 0;
     const size_t smem = FftCfg<M>::SMEM;
-    if (!attr_set) {
+    if (!resident) {
         cudaFuncSetAttribute(fft_kernel<M, ROT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_set = true;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, fft_kernel<M, ROT>, FftCfg<M>::THREADS, smem);
+        if (resident < 1) resident = 1;
+        if (sms < 1) sms = 152;
     }
-    // One CTA per SM, each looping over a run of spectra of one pair.
+    // One wave of resident CTAs, each looping over a run of spectra of one pair.
     const long long n = a.s_end - a.s_begin;
     const int n_pairs = a.n_in_pad / 2;
-    long long runs = (152LL + n_pairs - 1) / n_pairs;
+    long long runs = ((long long)sms * resident + n_pairs - 1) / n_pairs;
     if (runs > n) runs = n;
     if (runs < 1) runs = 1;
     FftArgs b = a;
@@ -558,7 +607,7 @@ void launch_fft(const FftArgs& a, cudaStream_t st) {
 void launch_fir(const FirArgs& a, cudaStream_t st) {
     const long long n = a.s_end - a.s_begin;
     if (n <= 0) return;
-    dim3 grid((unsigned)((a.M / 4 + kFirThreads - 1) / kFirThreads), (unsigned)a.n_pairs,
+    dim3 grid((unsigned)((a.M / 2 + kFirThreads - 1) / kFirThreads), (unsigned)a.n_pairs,
               (unsigned)((n + a.spt - 1) / a.spt));
     switch (a.taps) {
 #define CORR_FIR(P) case P: fir_kernel<P><<<grid, kFirThreads, 0, st>>>(a); break;

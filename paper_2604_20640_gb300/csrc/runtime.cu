@@ -263,7 +263,7 @@ int choose_spt(long long n_spec, int n_pairs) {
 // Spectra per FIR thread: long runs amortise the P-1 frames of warm-up,
 // but keep at least ~2 waves of CTAs on 152 SMs.
 int choose_fir_spt(long long n_spec, int n_pairs, int M, int taps) {
-    const long long ctas_per_run = (long long)((M / 4 + 255) / 256) * n_pairs;
+    const long long ctas_per_run = (long long)((M / 2 + 255) / 256) * n_pairs;
     long long spt = 16;
     while (spt > 1 && ((n_spec + spt - 1) / spt) * ctas_per_run < 3 * 152) spt /= 2;
     if (spt < 1) spt = 1;
@@ -320,11 +320,6 @@ int launch_f(corr_t h, const StreamView& sv, const Tables& t, float2* Z, long lo
     while ((1 << a.lgM) < h->M) ++a.lgM;
     a.taps = h->taps;
     a.spt = h->fir_spt > 0 ? h->fir_spt : choose_fir_spt(s_end - s_begin, a.n_pairs, h->M, h->taps);
-    {
-        Timed t_(h, 0, st);
-        launch_fir(a, st);
-    }
-    CK(cudaGetLastError());
     FftArgs f{};
     f.Z = Z;
     f.z_origin = z_origin;
@@ -339,6 +334,11 @@ int launch_f(corr_t h, const StreamView& sv, const Tables& t, float2* Z, long lo
     f.n_in_pad = h->n_in_pad;
     f.M = h->M;
     f.spt = choose_spt(s_end - s_begin, h->n_in_pad / 2);
+    {
+        Timed t_(h, 0, st);
+        launch_fir(a, st);
+    }
+    CK(cudaGetLastError());
     {
         Timed t_(h, 1, st);
         launch_fft(f, st);
