@@ -73,11 +73,12 @@ BYTES_PER_SAMPLE = {"fir": 5.0, "fft": 8.0, "xengine": 4.0, "finalize": 0.0, "fl
 
 def _spec(wl, rank, samples):
     from fxsynth import config_c1, config_c2, config_c3
+    from paper_2604_20640_gb300.replicas import rank_seed
     if wl == "c2":
-        return config_c2(seed=2000 + rank, n_samples=samples, M=2 * WORKLOADS[wl]["n_chan"])
+        return config_c2(seed=rank_seed(2000, rank, 1), n_samples=samples, M=2 * WORKLOADS[wl]["n_chan"])
     if wl == "c3":
-        return config_c3(seed=3000 + rank, n_samples=samples)
-    return config_c1(seed=1000 + rank, n_samples=samples)
+        return config_c3(seed=rank_seed(3000, rank, 1), n_samples=samples)
+    return config_c1(seed=rank_seed(1000, rank, 1), n_samples=samples)
 
 
 class ClockSampler:
@@ -252,6 +253,7 @@ def run_batched(args, rank, world, local):
     import torch
     import torch.distributed as dist
     from paper_2604_20640_gb300 import Correlator, Group
+    from paper_2604_20640_gb300.replicas import rank_seed, max_over_ranks, job_rate
     from fxsynth import config_c4_streams
     from fxsynth.streams_torch import make_stream_torch
 
@@ -260,7 +262,7 @@ def run_batched(args, rank, world, local):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
     S = args.samples or WORKLOADS["c4"]["samples"]
-    specs = config_c4_streams(seed=4000 + 100 * rank, n_samples=S)
+    specs = config_c4_streams(seed=rank_seed(4000, rank), n_samples=S)
     from fxsynth.streams import C4_SHAPES
     members, plains, xs, vis, flags = [], [], [], [], []
     for spec, (na, nc, ni) in zip(specs, C4_SHAPES):
@@ -293,10 +295,7 @@ def run_batched(args, rank, world, local):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1) / steps
-        if world > 1:
-            t = torch.tensor([ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dist if world > 1 else None, dev)
         return ms
 
     # plain: one stream after another, no graph, default tuning
@@ -316,7 +315,7 @@ def run_batched(args, rank, world, local):
     ms = timed(lambda: g.run_dev(xs, vis, flags), args.steps)
     launches = (g._L.corr_kernel_launches(g._h) - l0) * args.steps // (args.steps + args.warmup)
     clk = clocks.stop()
-    value = world * bytes_step / (ms * 1e-3) / 1e9
+    value = job_rate(bytes_step, world, ms)
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -328,7 +327,7 @@ def run_batched(args, rank, world, local):
                        "path": "one captured graph; tensor-core X (int8) for members with >= %d inputs, "
                                "CUDA-core FP32 X below" % TENSOR_MIN_INPUTS},
             "gpu_launches": int(launches), "clocks": clk,
-            "plain_fp32": {"value": world * bytes_step / (ms_plain * 1e-3) / 1e9, "ms_per_step": ms_plain,
+            "plain_fp32": {"value": job_rate(bytes_step, world, ms_plain), "ms_per_step": ms_plain,
                            "ratio": ms_plain / ms},
         }
         print(json.dumps(out))
@@ -378,6 +377,7 @@ def run_flagger(args, rank, world, local):
     import torch.distributed as dist
     from paper_2604_20640_gb300 import Correlator, FlagNet
     from paper_2604_20640_gb300 import flagger, train_flagnet
+    from paper_2604_20640_gb300.replicas import rank_seed, max_over_ranks, job_rate
     from fxsynth.rfi_torch import RfiSpec, make_rfi_batch, noise_only
 
     torch.cuda.set_device(local)
@@ -386,11 +386,11 @@ def run_flagger(args, rank, world, local):
         dist.init_process_group("nccl", device_id=dev)
     W = WORKLOADS["c5"]
     n_row = 256
-    spec = RfiSpec(n_in=32, n_chan=W["n_chan"], n_row=n_row, seed=5000 + 100 * rank)
+    spec = RfiSpec(n_in=32, n_chan=W["n_chan"], n_row=n_row, seed=rank_seed(5000, rank))
     S = spec.n_samples
     # --- the net: trained here on F-engine tiles of other seeds (8-input batches)
     t_train = time.time()
-    src = train_flagnet.TileSource(n_in=8, n_chan=W["n_chan"], n_row=n_row, seed=7000 + 100 * rank, device=dev)
+    src = train_flagnet.TileSource(n_in=8, n_chan=W["n_chan"], n_row=n_row, seed=rank_seed(7000, rank), device=dev)
     net = FlagNet(train_flagnet.init_params(0))
     losses = train_flagnet.train(net, src, args.train_steps, 32, 1e-3)
     t_train = time.time() - t_train
@@ -435,12 +435,9 @@ def run_flagger(args, rank, world, local):
     clk = clocks.stop()
     launches = corr.launches + net.launches - l0
     ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist if world > 1 else None, dev)
     bytes_step = spec.n_in * S
-    value = world * bytes_step / (ms * 1e-3) / 1e9
+    value = job_rate(bytes_step, world, ms)
     # --- per-stage split (one more instrumented pass, not in the timed region)
     corr.set_option("stage_timing", 1)
     corr.stage_times()
@@ -494,11 +491,8 @@ def run_flagger(args, rank, world, local):
         for _ in range(args.steps):
             e2e_step()
         ems = (time.perf_counter() - t0) * 1e3 / args.steps
-        if world > 1:
-            t = torch.tensor([ems], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": world * bytes_step / (ems * 1e-3) / 1e9, "unit": "GB/s",
+        ems = max_over_ranks(ems, dist if world > 1 else None, dev)
+        e2e = {"value": job_rate(bytes_step, world, ems), "unit": "GB/s",
                "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": int(fh.numel()), "ms_per_step": ems}
         del host
     if rank == 0:
@@ -559,6 +553,7 @@ def main():
     import torch
     import torch.distributed as dist
     from paper_2604_20640_gb300 import Correlator
+    from paper_2604_20640_gb300.replicas import max_over_ranks, job_rate
     from fxsynth.streams_torch import make_stream_torch
 
     torch.cuda.set_device(local)
@@ -604,12 +599,9 @@ def main():
     ms = e0.elapsed_time(e1) / args.steps
     stage_ms, stage_n = c.stage_times()
     c.set_option("stage_timing", 0)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist if world > 1 else None, dev)
     bytes_step = n_in * S
-    value = world * bytes_step / (ms * 1e-3) / 1e9
+    value = job_rate(bytes_step, world, ms)
 
     # ---- the plain FP32 path on the same stream (the metric's denominator) ----
     plain = None
@@ -627,11 +619,8 @@ def main():
         p1.record(stream)
         torch.cuda.synchronize(dev)
         pms = p0.elapsed_time(p1) / args.steps
-        if world > 1:
-            t = torch.tensor([pms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            pms = float(t.item())
-        pval = world * bytes_step / (pms * 1e-3) / 1e9
+        pms = max_over_ranks(pms, dist if world > 1 else None, dev)
+        pval = job_rate(bytes_step, world, pms)
         plain = {"value": pval, "ms_per_step": pms, "ratio": value / pval}
         cp.close()
 
@@ -663,11 +652,8 @@ def main():
         t1 = time.perf_counter()
         barrier()
         ems = (t1 - t0) * 1e3 / args.steps
-        if world > 1:
-            t = torch.tensor([ems], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": world * bytes_step / (ems * 1e-3) / 1e9, "unit": "GB/s",
+        ems = max_over_ranks(ems, dist if world > 1 else None, dev)
+        e2e = {"value": job_rate(bytes_step, world, ems), "unit": "GB/s",
                "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": int(v.nbytes + f.nbytes),
                "ms_per_step": ems}
         ce.close()

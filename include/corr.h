@@ -98,6 +98,11 @@ const char* corr_last_error(corr_t h);
  *   "ring_mb"      (1..4096, default 32)  MiB of each on-device spectrum ring
  *   "fir_spt"      (0 = automatic, 1..256; may change at any time)
  *                  spectra each FIR thread filters
+ *   "window"       (0 Hann, default; 1 Kaiser; 2 unit coefficients) taper
+ *                  of the prototype filter h = taper x sinc (Sec. 4.2; the
+ *                  8-tap Kaiser of Fig. 4); 2 with taps = 1 is the plain
+ *                  per-frame DFT.  Rebuilds the filter; before the first push.
+ *   "kaiser_beta"  (0..50, default 8)  Kaiser parameter
  */
 int corr_set_option(corr_t h, const char* key, double value);
 
@@ -298,6 +303,16 @@ int corr_flagnet_flag(corr_flagnet_t net, const float* d_power, int n_tiles, flo
 int corr_flagnet_status(corr_flagnet_t net, int* status);
 /* Kernels this handle has launched since it was created. */
 long long corr_flagnet_kernel_launches(corr_flagnet_t net);
+
+/*
+ * corr_tile_mad_dev -- Eq. 2 (sigma, 1.4826 MAD scale, strict A > T) on
+ * (time x channel) power tiles [n_tiles][64][256] (device FP32 in, device
+ * uint8 flags out, same layout): axes bit 1 along each row over aligned
+ * 64-channel windows (the paper's direction), bit 2 along each channel over
+ * the tile's 64 rows (the time direction, where broadband bursts stand
+ * out); 3 = the union.  Stateless; CORR_EINVAL on bad arguments.
+ */
+int corr_tile_mad_dev(const float* d_power, int n_tiles, float sigma, int axes, uint8_t* d_flags, void* stream);
 
 /* Shapes of a handle: n_in, n_chan, taps, n_int, n_in_pad (any may be NULL). */
 int corr_shape(corr_t h, int* n_in, int* n_chan, int* taps, int* n_int, int* n_in_pad);

@@ -144,17 +144,24 @@ def confidence(p: np.ndarray) -> np.ndarray:
     return np.mean(np.abs(2.0 * p - 1.0), axis=(-2, -1))
 
 
-def mad_tile_flags(power: np.ndarray, sigma: float = 5.0, window: int = 64) -> np.ndarray:
-    """Eq. 2 along each row of a tile over aligned windows of `window` channels."""
+def mad_tile_flags(power: np.ndarray, sigma: float = 5.0, window: int = 64, axes: int = 1) -> np.ndarray:
+    """Eq. 2 on (time x channel) tiles.  axes & 1: along each row over
+    aligned windows of ``window`` channels; axes & 2: along each channel over
+    the tile's rows (the time direction); both: the union of the two."""
     H, W = power.shape[-2:]
     out = np.zeros(power.shape, np.uint8)
     flat = power.reshape(-1, H, W)
     of = out.reshape(-1, H, W)
     for t in range(flat.shape[0]):
-        for r in range(H):
-            for k0 in range(0, W, window):
-                seg = flat[t, r, k0:k0 + window]
-                of[t, r, k0:k0 + window] = seg > fx.mad_threshold(seg, sigma)
+        if axes & 1:
+            for r in range(H):
+                for k0 in range(0, W, window):
+                    seg = flat[t, r, k0:k0 + window]
+                    of[t, r, k0:k0 + window] |= (seg > fx.mad_threshold(seg, sigma)).astype(np.uint8)
+        if axes & 2:
+            for k in range(W):
+                seg = flat[t, :, k]
+                of[t, :, k] |= (seg > fx.mad_threshold(seg, sigma)).astype(np.uint8)
     return out
 
 

@@ -54,13 +54,49 @@ MAD_TO_SIGMA = 1.4826   # Eq. 2
 # F-engine
 # --------------------------------------------------------------------------
 
-def pfb_coefficients(M: int, P: int) -> np.ndarray:
-    """Prototype FIR h[n], n = 0 .. P*M-1 (Sec. 4.2 PFB weighting; reading 1)."""
+def bessel_i0(x) -> np.ndarray:
+    """Modified Bessel function of the first kind, order 0, from its power
+    series I0(x) = sum_k ((x/2)^k / k!)^2 (all terms positive), summed until
+    a term no longer changes the FP64 sum."""
+    x = np.asarray(x, np.float64)
+    q = (x / 2.0) ** 2
+    term = np.ones_like(x)
+    total = np.ones_like(x)
+    k = 0
+    while True:
+        k += 1
+        term = term * q / (k * k)
+        if np.all(term <= 1e-17 * total):
+            return total
+        total = total + term
+
+
+def pfb_window(L: int, kind: str = "hann", beta: float = 8.0) -> np.ndarray:
+    """Taper of the prototype filter, n = 0 .. L-1: symmetric Hann
+    0.5 - 0.5 cos(2 pi n / (L-1)) (reading 1), or Kaiser
+    I0(beta sqrt(1 - (2n/(L-1) - 1)^2)) / I0(beta) (the 8-tap, beta = 8
+    window of Fig. 4)."""
+    n = np.arange(L, dtype=np.float64)
+    if kind == "hann":
+        return 0.5 - 0.5 * np.cos(2.0 * np.pi * n / (L - 1))
+    if kind == "kaiser":
+        r = 2.0 * n / (L - 1) - 1.0
+        return bessel_i0(beta * np.sqrt(np.maximum(0.0, 1.0 - r * r))) / bessel_i0(np.array(beta))
+    raise ValueError(kind)
+
+
+def pfb_coefficients(M: int, P: int, window: str = "hann", beta: float = 8.0) -> np.ndarray:
+    """Prototype FIR h[n], n = 0 .. P*M-1 (Sec. 4.2 PFB weighting; reading 1):
+    the taper times a sinc of cutoff 1/M centred at (L-1)/2.  ``window =
+    "none"`` gives h = 1 (with P = 1 the plain per-frame DFT, the
+    rectangular-FFT reference of Fig. 4)."""
     L = P * M
     if L < 2:
         raise ValueError("P*M must be at least 2")
+    if window == "none":
+        return np.ones(L)
     n = np.arange(L, dtype=np.float64)
-    w = 0.5 - 0.5 * np.cos(2.0 * np.pi * n / (L - 1))
+    w = pfb_window(L, window, beta)
     x = (n - (L - 1) / 2.0) / M
     sinc = np.ones(L)
     nz = x != 0.0
@@ -121,7 +157,8 @@ def fine_correct(Y: np.ndarray, r: float, phi: float, M: int) -> np.ndarray:
 
 
 def f_engine(x: np.ndarray, n_chan: int, taps: int, tau=None, phi=None,
-             h: Optional[np.ndarray] = None, brute: bool = False) -> np.ndarray:
+             h: Optional[np.ndarray] = None, brute: bool = False, pfb_window: str = "hann",
+             beta: float = 8.0) -> np.ndarray:
     """Channelised, delay-corrected voltages V[a][s][k] (complex128).
 
     ``x`` is ``[n_in][S]``; ``tau`` total delays in samples, ``phi`` instrument
@@ -131,7 +168,7 @@ def f_engine(x: np.ndarray, n_chan: int, taps: int, tau=None, phi=None,
     n_in = x.shape[0]
     M = 2 * n_chan
     if h is None:
-        h = pfb_coefficients(M, taps)
+        h = pfb_coefficients(M, taps, pfb_window, beta)
     tau = np.zeros(n_in) if tau is None else np.asarray(tau, np.float64)
     phi = np.zeros(n_in) if phi is None else np.asarray(phi, np.float64)
     d, r = split_delay(tau)
@@ -244,7 +281,7 @@ def mad_flags(R: np.ndarray, sigma: float = 5.0, window: int = 64):
 
 def correlate(x: np.ndarray, n_chan: int, taps: int, n_int: int, tau=None, phi=None,
               sigma: float = 5.0, window: int = 64, partial: bool = False,
-              schedule: Optional[Sequence[tuple]] = None):
+              schedule: Optional[Sequence[tuple]] = None, pfb_window: str = "hann", beta: float = 8.0):
     """Visibilities R[i][k][a][b] and MAD flags for a whole stream (Algorithm 1).
 
     ``schedule`` optionally gives one ``(tau, phi)`` per integration (a delay
@@ -252,7 +289,7 @@ def correlate(x: np.ndarray, n_chan: int, taps: int, n_int: int, tau=None, phi=N
     hold throughout.
     """
     if schedule is None:
-        V = f_engine(x, n_chan, taps, tau, phi)
+        V = f_engine(x, n_chan, taps, tau, phi, pfb_window=pfb_window, beta=beta)
     else:
         M = 2 * n_chan
         n_spec = np.asarray(x).shape[1] // M
@@ -264,7 +301,7 @@ def correlate(x: np.ndarray, n_chan: int, taps: int, n_int: int, tau=None, phi=N
                 break
             key = (tuple(np.asarray(t, np.float64)), tuple(np.asarray(p, np.float64)))
             if key not in cache:
-                cache[key] = f_engine(x, n_chan, taps, t, p)
+                cache[key] = f_engine(x, n_chan, taps, t, p, pfb_window=pfb_window, beta=beta)
             if V is None:
                 V = np.empty_like(cache[key])
             V[:, s0:s1] = cache[key][:, s0:s1]

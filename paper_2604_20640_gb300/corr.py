@@ -37,7 +37,7 @@ EXPORTED = [
     "corr_get_tuning", "corr_spectrogram_dev", "corr_flagnet_create", "corr_flagnet_destroy",
     "corr_flagnet_num_params", "corr_flagnet_set_params", "corr_flagnet_get_params", "corr_flagnet_prepare",
     "corr_flagnet_forward", "corr_flagnet_loss_grad", "corr_flagnet_train_step", "corr_flagnet_flag",
-    "corr_flagnet_status", "corr_flagnet_kernel_launches",
+    "corr_flagnet_status", "corr_flagnet_kernel_launches", "corr_tile_mad_dev",
 ]
 
 
@@ -104,6 +104,7 @@ def load_library(path: str = LIB_PATH):
         "corr_flagnet_flag": (_i, [_vp, _vp, _i, ctypes.c_float, ctypes.c_float, _vp, _vp, _vp]),
         "corr_flagnet_status": (_i, [_vp, ctypes.POINTER(_i)]),
         "corr_flagnet_kernel_launches": (_ll, [_vp]),
+        "corr_tile_mad_dev": (_i, [_vp, _i, ctypes.c_float, _i, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -380,6 +381,16 @@ class Correlator:
     @property
     def launches(self) -> int:
         return int(self._L.corr_kernel_launches(self._h))
+
+
+def tile_mad(power, flags_out, axes: int = 1, sigma: float = 5.0, stream=None):
+    """Eq. 2 on power tiles [B][64][256]: axes 1 along channels (per row,
+    64-channel windows), 2 along time (per channel), 3 both (union)."""
+    L = load_library()
+    rc = L.corr_tile_mad_dev(_dev_ptr(power, "power"), power.shape[0], sigma, axes, _dev_ptr(flags_out, "flags"),
+                             _stream_ptr(stream))
+    if rc != CORR_OK:
+        raise CorrError(rc, L.corr_last_error(None).decode())
 
 
 class FlagNet:

@@ -299,8 +299,8 @@ __device__ float warp_median64(const float* v, float* sorted, int lane) {
 }
 
 // Flags of a tile: the network's (p > 1/2) when conf >= c_min, else Eq. 2
-// along each row over aligned windows of 64 channels.  One warp per (tile,
-// row, window).
+// along each row over aligned windows of 64 channels (always Eq. 2 when
+// conf is null).  One warp per (tile, row, window).
 __global__ void final_flags_kernel(const float* power, const float* logit, const float* conf, int B, float c_min,
                                    float sigma, uint8_t* flags) {
     __shared__ float sm[4][3][64];
@@ -311,7 +311,7 @@ __global__ void final_flags_kernel(const float* power, const float* logit, const
     const int r = (int)((item / (TW / 64)) % TH);
     const int t = (int)(item / ((TW / 64) * TH));
     const size_t base = (size_t)t * TPIX + (size_t)r * TW + win * 64;
-    if (conf[t] >= c_min) {
+    if (conf && conf[t] >= c_min) {
         for (int c = lane; c < 64; c += 32) flags[base + c] = logit[base + c] > 0.f ? 1 : 0;
         return;
     }
@@ -326,6 +326,33 @@ __global__ void final_flags_kernel(const float* power, const float* logit, const
     const float mad = warp_median64(vD, vS, lane);
     const float T = med + sigma * mad * 1.4826f;
     for (int c = lane; c < 64; c += 32) flags[base + c] = vA[c] > T ? 1 : 0;
+}
+
+// Eq. 2 along time: per (tile, channel) over the tile's 64 rows; the flags
+// are OR-ed into `flags` when `accumulate` is set.  One warp per item.
+__global__ void mad_time_kernel(const float* power, int B, float sigma, bool accumulate, uint8_t* flags) {
+    __shared__ float sm[4][3][64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long item = (long long)blockIdx.x * 4 + warp;
+    if (item >= (long long)B * TW) return;
+    const int k = (int)(item % TW);
+    const int t = (int)(item / TW);
+    const size_t base = (size_t)t * TPIX + k;
+    float* vA = sm[warp][0];
+    float* vS = sm[warp][1];
+    float* vD = sm[warp][2];
+    for (int r = lane; r < TH; r += 32) vA[r] = power[base + (size_t)r * TW];
+    __syncwarp();
+    const float med = warp_median64(vA, vS, lane);
+    for (int r = lane; r < TH; r += 32) vD[r] = fabsf(vA[r] - med);
+    __syncwarp();
+    const float mad = warp_median64(vD, vS, lane);
+    const float T = med + sigma * mad * 1.4826f;
+    for (int r = lane; r < TH; r += 32) {
+        const uint8_t f = vA[r] > T ? 1 : 0;
+        uint8_t* o = flags + base + (size_t)r * TW;
+        *o = accumulate ? (uint8_t)(*o | f) : f;
+    }
 }
 
 // Autocorrelation power of row `row` (n_row spectra) for input a and channel
@@ -753,6 +780,23 @@ int corr_flagnet_flag(corr_flagnet_t net, const float* d_power, int B, float c_m
 }
 
 long long corr_flagnet_kernel_launches(corr_flagnet_t net) { return net ? net->launches : 0; }
+
+int corr_tile_mad_dev(const float* d_power, int n_tiles, float sigma, int axes, uint8_t* d_flags, void* stream) {
+    corr_flagnet_t net = nullptr;
+    if (!d_power || !d_flags || n_tiles < 1 || axes < 1 || axes > 3 || !(sigma > 0))
+        return ffail(nullptr, CORR_EINVAL, "bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (axes & 1) {
+        const long long items = (long long)n_tiles * TH * (TW / 64);
+        final_flags_kernel<<<blocks(items, 4), 128, 0, st>>>(d_power, nullptr, nullptr, n_tiles, 0.f, sigma, d_flags);
+    }
+    if (axes & 2) {
+        const long long items = (long long)n_tiles * TW;
+        mad_time_kernel<<<blocks(items, 4), 128, 0, st>>>(d_power, n_tiles, sigma, (axes & 1) != 0, d_flags);
+    }
+    FK(cudaGetLastError());
+    return CORR_OK;
+}
 
 int corr_flagnet_status(corr_flagnet_t net, int* status) {
     if (!net || !status) return ffail(net, CORR_EINVAL, "bad argument");

@@ -10,6 +10,7 @@
 #include "corr.h"
 #include "corr_internal.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -106,6 +107,8 @@ struct corr_s {
     int result_slots = 8;
     int ring_mb = 32;            // tunable: ring capacity of Z and V (MiB each)
     int fir_spt = 0;             // tunable: spectra per FIR thread (0 = automatic)
+    int window = 0;              // PFB taper: 0 Hann, 1 Kaiser, 2 unit coefficients
+    double kaiser_beta = 8.0;
     // group of handles run as one captured graph (corr_group_create)
     bool is_group = false;
     std::vector<corr_s*> members;
@@ -198,12 +201,41 @@ size_t vis_elems(const corr_s* h) { return (size_t)h->n_chan * h->n_in * h->n_in
 
 // Polyphase prototype (Sec. 4.2 PFB weighting): symmetric Hann window times
 // a sinc with cutoff 1/M centred on the filter, evaluated in FP64.
-std::vector<float> make_filter(int M, int P) {
+// I0(x) by its power series sum_k ((x/2)^k / k!)^2, in FP64.
+double bessel_i0(double x) {
+    const double q = 0.25 * x * x;
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 500; ++k) {
+        term *= q / ((double)k * k);
+        sum += term;
+        if (term <= 1e-17 * sum) break;
+    }
+    return sum;
+}
+
+// Polyphase prototype (Sec. 4.2 PFB weighting), evaluated in FP64: a
+// symmetric taper (Hann, or Kaiser with parameter beta as in Fig. 4) times a
+// sinc with cutoff 1/M centred on the filter; window 2 gives unit
+// coefficients (with one tap, the plain per-frame DFT).
+std::vector<float> make_filter(int M, int P, int window, double beta) {
     const int L = M * P;
     std::vector<float> h(L);
     const double pi = 3.14159265358979323846;
+    const double i0b = bessel_i0(beta);
     for (int n = 0; n < L; ++n) {
-        const double w = (L > 1) ? 0.5 - 0.5 * std::cos(2.0 * pi * n / (double)(L - 1)) : 1.0;
+        if (window == 2) {
+            h[n] = 1.0f;
+            continue;
+        }
+        double w = 1.0;
+        if (L > 1) {
+            if (window == 1) {
+                const double r = 2.0 * n / (double)(L - 1) - 1.0;
+                w = bessel_i0(beta * std::sqrt(std::max(0.0, 1.0 - r * r))) / i0b;
+            } else {
+                w = 0.5 - 0.5 * std::cos(2.0 * pi * n / (double)(L - 1));
+            }
+        }
         const double x = (n - 0.5 * (L - 1)) / (double)M;
         const double sn = (x == 0.0) ? 1.0 : std::sin(pi * x) / (pi * x);
         h[n] = (float)(w * sn);
@@ -778,7 +810,7 @@ int corr_create(corr_t* out, int n_ant, int n_pol, int n_chan, int taps, int n_i
         return fail(nullptr, code, m);
     };
     if (e != cudaSuccess) return bail(CORR_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    const std::vector<float> hf = make_filter(h->M, taps);
+    const std::vector<float> hf = make_filter(h->M, taps, h->window, h->kaiser_beta);
     const std::vector<float2> tw = corr::fft_twiddle_table(h->M);
     if (cudaStreamCreateWithFlags(&h->s_comp, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&h->s_copy, cudaStreamNonBlocking) != cudaSuccess ||
@@ -905,6 +937,13 @@ int corr_set_option(corr_t h, const char* key, double v) {
     } else if (k == "stage_timing") {
         h->timer.on = v != 0;
         return CORR_OK;
+    } else if (k == "window" || k == "kaiser_beta") {
+        if (k == "window" && v != 0 && v != 1 && v != 2) return fail(h, CORR_EINVAL, "window: 0 Hann, 1 Kaiser, 2 none");
+        if (k == "kaiser_beta" && !(v >= 0 && v <= 50)) return fail(h, CORR_EINVAL, "kaiser_beta out of range");
+        if (k == "window") h->window = (int)v;
+        else h->kaiser_beta = v;
+        const std::vector<float> hf = make_filter(h->M, h->taps, h->window, h->kaiser_beta);
+        CK(cudaMemcpy(h->d_h, hf.data(), hf.size() * sizeof(float), cudaMemcpyHostToDevice));
     } else if (k == "result_slots") {
         if (v < 1 || v > 4096) return fail(h, CORR_EINVAL, "result_slots out of range");
         h->result_slots = (int)v;

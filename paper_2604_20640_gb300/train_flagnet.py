@@ -82,11 +82,19 @@ def _pr(pred, truth):
 
 def evaluate(net: FlagNet, power, truth, t_nb, t_bb, c_min: float = 0.9):
     """dict of precision / recall (overall, narrowband-only and broadband-only
-    truth) for the net alone, MAD alone and the hybrid at ``c_min``."""
+    truth) for the net alone, MAD alone (along channels as in the paper,
+    along time, and their union) and the hybrid at ``c_min``."""
+    import torch
+    from .corr import tile_mad
     out = {}
     t = truth.bool()
-    for name, cm in (("net", -1.0), ("mad", 2.0), ("hybrid", c_min)):
-        f, conf = flagger.flag(net, power, c_min=cm)
+    for name, cm in (("net", -1.0), ("mad", 2.0), ("mad_time", None), ("mad_union", None), ("hybrid", c_min)):
+        if cm is None:
+            f = torch.empty(power.shape, dtype=torch.uint8, device=power.device)
+            tile_mad(power, f, axes=2 if name == "mad_time" else 3)
+            conf = None
+        else:
+            f, conf = flagger.flag(net, power, c_min=cm)
         f = f.bool()
         p, r = _pr(f, t)
         _, r_nb = _pr(f, t_nb.bool())

@@ -140,3 +140,18 @@ def test_to_tiles_index_map():
     assert T.shape == (2, 2, 2, 64, 256)
     # input 1, row 64 + 3, channel 256 + 7 -> tile (1, 1, 1), pixel (3, 7)
     assert T[1, 1, 1, 3, 7] == P[1, 67, 263] == 1 * 128 * 512 + 67 * 512 + 263
+
+
+def test_time_direction_mad_is_eq2_per_channel_and_union():
+    rng = np.random.default_rng(8)
+    P = rng.rayleigh(1.0, (2, 64, 128)) + 0.1
+    P[1, 10:12, :] += 30.0          # a broadband burst: rows 10-11 raised in every channel
+    F_row = fn.mad_tile_flags(P, axes=1)
+    F_time = fn.mad_tile_flags(P, axes=2)
+    F_both = fn.mad_tile_flags(P, axes=3)
+    assert F_time[1, 10:12, :].all()                  # seen along time
+    assert F_row[1, 10:12, :].sum() < 0.1 * 2 * 128   # not along the raised row itself
+    assert np.array_equal(F_both, F_row | F_time)
+    for k in (0, 77):
+        seg = P[0, :, k]
+        assert np.array_equal(F_time[0, :, k], (seg > fx.mad_threshold(seg, 5.0)).astype(np.uint8))

@@ -316,3 +316,54 @@ def test_push_dev_matches_push():
     c2.push_dev(xd[:, 5000:])
     c2.flush()
     assert np.array_equal(c1.get_vis(), c2.get_vis())
+
+
+@pytest.mark.parametrize("window,wname,taps", [(1, "kaiser", 8), (1, "kaiser", 4), (2, "none", 1), (0, "hann", 8)])
+def test_fengine_window_options_match_oracle(window, wname, taps):
+    n_chan, n_in = 512, 3
+    M = 2 * n_chan
+    S = M * 30 + 5
+    tau = np.array([0.0, 7.0, 21.3])
+    phi = np.array([0.0, 1.0, -0.5])
+    x = _stream(n_in, S, seed=40 + taps, tau=tau, phi=phi)
+    c = _corr(n_in, 1, n_chan, taps, 8)
+    c.set_option("window", window)
+    c.set_option("kaiser_beta", 8.0)
+    c.set_delays(tau, phi)
+    Vg = _fengine(c, x, 0, 30)
+    Vo = fx.f_engine(x, n_chan, taps, tau, phi, pfb_window=wname, beta=8.0)
+    for a in range(n_in):
+        num = np.linalg.norm(Vg[:, :, a] - Vo[a], axis=1)
+        den = np.linalg.norm(Vo[a], axis=1)
+        assert np.all(num <= 1e-5 * den + 1e-6)
+    R, F = _run_dev(c, x, True)
+    Ro, Fo, To = fx.correlate(x, n_chan, taps, 8, tau, phi, partial=True, pfb_window=wname, beta=8.0)
+    assert _vis_err(R, Ro).max() < 1e-5
+    assert _flags_ok(F, Ro, Fo, To).all()
+
+
+def test_leakage_of_the_gpu_filter_banks():
+    """Channel response measured through the GPU F-engine with a tone swept
+    across one channel (Fig. 4's comparison): worst response two or more
+    channels away, and the scalloping at the channel edge, for the plain FFT
+    (window 2, one tap), the 4-tap Hann PFB and the 8-tap Kaiser PFB."""
+    n_chan = 256
+    M = 2 * n_chan
+    k0 = 64
+    offsets = np.linspace(-0.5, 0.5, 21)
+    S = M * 40
+    n = np.arange(S)
+    x = np.stack([np.round(100 * np.cos(2 * np.pi * (k0 + d) * n / M)) for d in offsets]).astype(np.int8)
+    out = {}
+    for name, window, taps in (("fft", 2, 1), ("hann4", 0, 4), ("kaiser8", 1, 8)):
+        c = _corr(len(offsets), 1, n_chan, taps, 8)
+        c.set_option("window", window)
+        V = _fengine(c, x, 16, 16)[:, :, :len(offsets)]
+        P = np.mean(np.abs(V) ** 2, axis=0)          # [n_chan][tone]
+        peak = P[k0, offsets.size // 2]
+        far = np.max(np.delete(P, np.arange(k0 - 2, k0 + 3), axis=0)) / peak
+        edge = P[k0, 0] / peak
+        out[name] = (10 * np.log10(far), 10 * np.log10(edge))
+    print({k: ("far %.1f dB" % v[0], "edge %.2f dB" % v[1]) for k, v in out.items()})
+    assert out["fft"][0] > -20.0                     # rectangular: high sidelobes
+    assert out["hann4"][0] < -35.0 and out["kaiser8"][0] < out["hann4"][0]

@@ -58,6 +58,37 @@ def test_pfb_leakage_below_rectangular():
     assert abs(10 * np.log10(edge) + 6.0) < 0.5
 
 
+def test_bessel_i0_and_kaiser_window_match_library():
+    x = np.linspace(0.0, 30.0, 301)
+    np.testing.assert_allclose(fx.bessel_i0(x), np.i0(x), rtol=1e-14, atol=0)
+    for L, beta in [(16, 8.0), (65536, 8.0), (1000, 3.5), (7, 0.0)]:
+        np.testing.assert_allclose(fx.pfb_window(L, "kaiser", beta), np.kaiser(L, beta), rtol=0, atol=1e-13)
+
+
+def _channel_response(h, M, delta):
+    n = np.arange(h.size)
+    return np.abs(np.exp(-2j * np.pi * np.outer(delta, n) / M) @ h) ** 2 / h.sum() ** 2
+
+
+def test_kaiser_8_tap_pfb_leakage_below_hann_4_tap():
+    # Fig. 4's 8-tap Kaiser (beta = 8) prototype: far sidelobes well below the
+    # 4-tap Hann-sinc and far below the rectangular FFT; its passband is
+    # flatter (smaller scalloping at the channel edge).
+    M = 64
+    hk = fx.pfb_coefficients(M, 8, "kaiser", 8.0)
+    hh = fx.pfb_coefficients(M, 4)
+    assert np.allclose(hk, hk[::-1], atol=1e-15)
+    far = np.linspace(2.0, M / 2, 3000)
+    lk = 10 * np.log10(_channel_response(hk, M, far).max())
+    lh = 10 * np.log10(_channel_response(hh, M, far).max())
+    assert lk < -60.0 and lk < lh - 10.0
+    edge_k = 10 * np.log10(_channel_response(hk, M, np.array([0.5]))[0])
+    edge_h = 10 * np.log10(_channel_response(hh, M, np.array([0.5]))[0])
+    assert abs(edge_k + 6.0) < 1.0 and abs(edge_h + 6.0) < 0.5
+    # "none" with one tap is the plain DFT's unit coefficients
+    assert np.array_equal(fx.pfb_coefficients(M, 1, "none"), np.ones(M))
+
+
 # --------------------------------------------------------------------------
 # Channeliser
 # --------------------------------------------------------------------------
