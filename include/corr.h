@@ -254,7 +254,9 @@ int corr_get_tuning(corr_t h, int* ring_mb, int* fir_spt);
  * corr_spectrogram_dev -- autocorrelation power of every input in tiles of
  * 64 rows x 256 channels (the (time x channel) dynamic spectra of Sec. 5):
  * row r of input a holds mean_{s in [r n_row, (r+1) n_row)} |Y_a,s[k]|^2 from
- * this F-engine (no fine-delay factor: it has unit modulus), for
+ * this F-engine (no fine-delay factor: it has unit modulus; the FFT kernel
+ * accumulates the powers, no spectra are stored; FP32 sums, so the order of
+ * the additions across the F-engine's work split is not fixed), for
  * rows = 64 floor(n_spec / (64 n_row)) rows, n_spec = floor(n_samples / M):
  * whole tiles only, later spectra are not read.  n_chan must be a multiple
  * of 256 and rows >= 64, else CORR_EINVAL.  d_tiles: [n_in][rows/64]
@@ -326,8 +328,9 @@ long long corr_kernel_launches(corr_t h);
  * With option "stage_timing" = 1 every kernel launch is bracketed by CUDA
  * events on its own stream.  This call waits for those events and returns,
  * for stages 0 FIR, 1 FFT (the two F-engine kernels), 2 X-engine,
- * 3 finalise, 4 flagging, 5 requantise, 6 tensor-core Gram, 7 dynamic
- * spectrum (first n_stages entries, at most 8), the milliseconds and
+ * 3 finalise, 4 flagging, 5 requantise, 6 tensor-core Gram (first
+ * n_stages entries, at most 7; the dynamic spectra of
+ * corr_spectrogram_dev are accumulated by the FFT kernel), the milliseconds and
  * launch counts accumulated since the previous call, then clears them.
  * ms / counts may be NULL.
  */

@@ -372,10 +372,10 @@ class Correlator:
 
     def stage_times(self):
         """(ms, counts) per stage (FIR, FFT, X, finalise, flag, requantise, tensor-core
-        Gram, dynamic spectrum) since the last call."""
-        ms = (ctypes.c_double * 8)()
-        n = (ctypes.c_longlong * 8)()
-        self._check(self._L.corr_stage_times(self._h, ms, n, 8))
+        Gram) since the last call."""
+        ms = (ctypes.c_double * 7)()
+        n = (ctypes.c_longlong * 7)()
+        self._check(self._L.corr_stage_times(self._h, ms, n, 7))
         return list(ms), list(n)
 
     @property

@@ -1,0 +1,284 @@
+// Implicit-GEMM 5x5 convolution on tcgen05 for the learned flagger's
+// 32-channel layers (no im2col buffer):
+//   Z[p][o] = sum_{u,v} sum_c X[n][i + s(u-2)][j + s(v-2)][c] W[o][(5u+v) 32 + c]
+// with s = +1 (forward) or -1 (the data gradient, whose operand is the
+// output gradient and whose weights are the transposed layout).
+//
+// X is NHWC BF16 [n][64][256][32].  One M tile is 128 pixels of one image
+// row; its A operand for tap (u, v) is the 128 x 32 block of X at row
+// i + s(u-2), columns j0 + s(v-2) .. +127, loaded by one 4D TMA box (64-byte
+// rows, 64-byte swizzle).  Pixels outside the image come back as zeros from
+// the TMA's out-of-bounds fill, which is exactly the convolution's zero
+// padding.  All 25 taps' weights (BN x 32 each) stay resident in shared
+// memory.  K per M tile = 25 taps x 32 channels = 50 MMAs of K = 16.
+//
+// Warp roles (192 threads): warp 0 lane 0 issues TMA into a ring of A
+// stages, warp 1 lane 0 issues tcgen05.mma into one of two TMEM accumulators
+// (M = 128, N = BN), warps 2-5 drain the other accumulator (bias, ReLU, BF16
+// NHWC store; or the FP32 logit; or raw FP32).  CTAs are persistent over M
+// tiles.  Every wait is bounded by %globaltimer; on expiry the CTA records
+// CORR_ETIMEDOUT, stops issuing, frees its TMEM and returns.
+#include "corr.h"
+#include "corr_internal.h"
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include "tc_common.cuh"
+
+namespace corr {
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
+
+namespace {
+
+using namespace tc;
+
+constexpr int kImgH = 64, kImgW = 256, kCh = 32;
+constexpr int kTaps = 25;
+constexpr int kAStages = 6;
+constexpr int kATile = 128 * kCh * 2;        // 8 KiB: 128 pixels x 32 channels BF16
+constexpr int kConvThreads = 192;
+
+struct __align__(8) ConvShared {
+    uint64_t full[kAStages];
+    uint64_t empty[kAStages];
+    uint64_t wfull;
+    uint64_t acc_full[2];
+    uint64_t acc_empty[2];
+    uint32_t tmem_addr;
+    int abort;
+};
+
+template <int BN>
+__host__ __device__ constexpr uint32_t conv_idesc() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+template <int BN>
+__host__ __device__ constexpr size_t conv_smem() {
+    // 1024-byte alignment slack, A ring, resident weights, 8 KiB guard, barriers
+    return 1024 + (size_t)kAStages * kATile + (size_t)kTaps * BN * 64 + 8192 + sizeof(ConvShared);
+}
+
+template <int BN>
+__device__ __forceinline__ void conv_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(conv_idesc<BN>()), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ bool aborted(ConvShared* sh) { return *(volatile int*)&sh->abort != 0; }
+
+template <int BN>
+__global__ void __launch_bounds__(kConvThreads, 1)
+    conv_kernel(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtensorMap tw, ConvArgs A) {
+    constexpr int kWTile = BN * 64;
+    constexpr uint32_t kCols = 2 * BN < 32 ? 32 : 2 * BN;
+    extern __shared__ __align__(1024) uint8_t csm_raw[];
+    uint8_t* a_st = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(csm_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* w_st = a_st + kAStages * kATile;
+    ConvShared* sh = reinterpret_cast<ConvShared*>(w_st + kTaps * kWTile + 8192);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_mt = A.n_images * kImgH * 2;
+    const int my_count = (int)blockIdx.x < n_mt ? (n_mt - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kAStages; ++s) {
+            mbar_init(&sh->full[s], 1);
+            mbar_init(&sh->empty[s], 1);
+        }
+        mbar_init(&sh->wfull, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&sh->acc_full[b], 1);
+            mbar_init(&sh->acc_empty[b], 4);
+        }
+        sh->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&sh->tmem_addr)),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = sh->tmem_addr;
+
+    if (warp == 0 && lane == 0) {
+        // ---- TMA producer: resident weights, then the A ring
+        mbar_expect_tx(&sh->wfull, kTaps * kWTile);
+        for (int t = 0; t < kTaps; ++t) tma_load_2d(w_st + t * kWTile, &tw, &sh->wfull, t * kCh, 0);
+        int it = 0;
+        for (int lt = 0; lt < my_count && !aborted(sh); ++lt) {
+            const int mt = (int)blockIdx.x + lt * (int)gridDim.x;
+            const int n = mt / (kImgH * 2), rem = mt % (kImgH * 2);
+            const int i = rem >> 1, j0 = (rem & 1) * 128;
+            for (int tap = 0; tap < kTaps; ++tap, ++it) {
+                const int s = it % kAStages;
+                const uint32_t ph = (uint32_t)(it / kAStages) & 1u;
+                if (!mbar_wait(&sh->empty[s], ph ^ 1u)) {
+                    sh->abort = 1;
+                    break;
+                }
+                const int u = tap / 5, v = tap % 5;
+                mbar_expect_tx(&sh->full[s], kATile);
+                tma_load_4d(a_st + s * kATile, &tx, &sh->full[s], 0, j0 + A.sgn * (v - 2), i + A.sgn * (u - 2), n);
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer
+        if (!mbar_wait(&sh->wfull, 0)) sh->abort = 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        int it = 0;
+        for (int lt = 0; lt < my_count && !aborted(sh); ++lt) {
+            const int b = lt & 1;
+            const uint32_t use = (uint32_t)(lt >> 1);
+            if (!mbar_wait(&sh->acc_empty[b], (use & 1u) ^ 1u)) {
+                sh->abort = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t d = tmem + (uint32_t)(b * BN);
+            bool ok = true;
+            for (int tap = 0; tap < kTaps; ++tap, ++it) {
+                const int s = it % kAStages;
+                const uint32_t ph = (uint32_t)(it / kAStages) & 1u;
+                if (!mbar_wait(&sh->full[s], ph)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint64_t da = sdesc64(smem_u32(a_st + s * kATile));
+                const uint64_t db = sdesc64(smem_u32(w_st + tap * kWTile));
+                conv_mma<BN>(d, da, db, tap != 0 ? 1u : 0u);
+                conv_mma<BN>(d, da + 2, db + 2, 1u);     // second 16 channels: +32 bytes
+                mma_commit(&sh->empty[s]);
+            }
+            if (!ok) {
+                sh->abort = 1;
+                break;
+            }
+            mma_commit(&sh->acc_full[b]);
+        }
+    } else if (warp >= 2) {
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31
+        const int q = warp & 3;
+        const int row = q * 32 + lane;
+        for (int lt = 0; lt < my_count; ++lt) {
+            const int b = lt & 1;
+            const uint32_t use = (uint32_t)(lt >> 1);
+            bool ready = !aborted(sh) && mbar_wait(&sh->acc_full[b], use & 1u);
+            ready = __all_sync(0xffffffffu, ready);
+            if (!ready) {
+                if (lane == 0) sh->abort = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            uint32_t r[32];
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN);
+            if constexpr (BN == 32) {
+                tmem_ld32(taddr, r);
+            } else {
+                uint32_t r16[16];
+                tmem_ld16(taddr, r16);
+#pragma unroll
+                for (int c = 0; c < 16; ++c) r[c] = r16[c];
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh->acc_empty[b]);
+            const int mt = (int)blockIdx.x + lt * (int)gridDim.x;
+            const int n = mt / (kImgH * 2), rem = mt % (kImgH * 2);
+            const size_t p = (size_t)n * (kImgH * kImgW) + (size_t)(rem >> 1) * kImgW + (rem & 1) * 128 + row;
+            if (A.mode == 0) {
+                // hidden layer: BF16 ReLU(z + b), 32 channels = 64 bytes
+                uint32_t pk[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const float z0 = fmaxf(__uint_as_float(r[2 * c]) + __ldg(A.bias + 2 * c), 0.f);
+                    const float z1 = fmaxf(__uint_as_float(r[2 * c + 1]) + __ldg(A.bias + 2 * c + 1), 0.f);
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(z0, z1);
+                    pk[c] = *reinterpret_cast<const uint32_t*>(&h);
+                }
+                uint4* o = reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(A.out) + p * kCh);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) o[v] = make_uint4(pk[4 * v], pk[4 * v + 1], pk[4 * v + 2], pk[4 * v + 3]);
+            } else if (A.mode == 1) {
+                reinterpret_cast<float*>(A.out)[p] = __uint_as_float(r[0]) + __ldg(A.bias);
+            } else {
+                float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(A.out) + p * BN);
+#pragma unroll
+                for (int v = 0; v < BN / 4; ++v)
+                    o[v] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
+                                       __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
+            }
+        }
+    }
+    __syncwarp();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0 && sh->abort && A.status) atomicExch(A.status, CORR_ETIMEDOUT);
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+    }
+}
+
+bool encode(CUtensorMap* map, CUtensorMapDataType dt, cuuint32_t rank, const void* base, const cuuint64_t* dims,
+            const cuuint64_t* strides, const cuuint32_t* box) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    return enc(map, dt, rank, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN>
+int launch_bn(const ConvArgs& a, cudaStream_t st) {
+    CUtensorMap tx, tw;
+    const cuuint64_t xd[4] = {(cuuint64_t)kCh, (cuuint64_t)kImgW, (cuuint64_t)kImgH, (cuuint64_t)a.n_images};
+    const cuuint64_t xs[3] = {(cuuint64_t)kCh * 2, (cuuint64_t)kCh * 2 * kImgW, (cuuint64_t)kCh * 2 * kImgW * kImgH};
+    const cuuint32_t xb[4] = {(cuuint32_t)kCh, 128, 1, 1};
+    const cuuint64_t wd[2] = {(cuuint64_t)a.kp, (cuuint64_t)BN};
+    const cuuint64_t ws[1] = {(cuuint64_t)a.kp * 2};
+    const cuuint32_t wb[2] = {(cuuint32_t)kCh, (cuuint32_t)BN};
+    if (!encode(&tx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, a.X, xd, xs, xb) ||
+        !encode(&tw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a.W, wd, ws, wb))
+        return CORR_EINVAL;
+    static int resident = 0, sms = 0;
+    const size_t smem = conv_smem<BN>();
+    if (!resident) {
+        cudaFuncSetAttribute(conv_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, conv_kernel<BN>, kConvThreads, smem);
+        if (resident < 1) resident = 1;
+        if (sms < 1) sms = 152;
+    }
+    const int n_mt = a.n_images * kImgH * 2;
+    int grid = sms * resident;
+    if (grid > n_mt) grid = n_mt;
+    conv_kernel<BN><<<grid, kConvThreads, smem, st>>>(tx, tw, a);
+    return CORR_OK;
+}
+
+}  // namespace
+
+int launch_conv(const ConvArgs& a, cudaStream_t st) {
+    if (a.n_images <= 0) return CORR_OK;
+    if (!a.X || !a.W || !a.out || (a.sgn != 1 && a.sgn != -1) || a.kp < kTaps * kCh || a.kp % 8) return CORR_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(a.X) & 15) || (reinterpret_cast<uintptr_t>(a.W) & 15)) return CORR_EINVAL;
+    if (a.bn == 32 && (a.mode == 0 || a.mode == 2)) return launch_bn<32>(a, st);
+    if (a.bn == 16 && (a.mode == 1 || a.mode == 2)) return launch_bn<16>(a, st);
+    return CORR_EINVAL;
+}
+
+}  // namespace corr

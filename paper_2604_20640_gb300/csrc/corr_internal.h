@@ -55,6 +55,11 @@ struct FftArgs {
     long long v_mask;
     long long s_begin, s_end;
     int n_in_pad, M, spt;
+    // power mode (tiles set): instead of V, accumulate mean |Y|^2 over rows
+    // of n_row spectra into dynamic-spectrum tiles [n_in][rows/64][n_chan/256]
+    // [64][256] (atomic adds; the caller zeroes them)
+    float* tiles;
+    int n_row, rows, n_in;
 };
 
 // X-engine launch: groups of spectra, each group summed into one partial
@@ -134,6 +139,20 @@ struct GemmArgs {
 };
 int launch_gemm(const GemmArgs& a, cudaStream_t st);
 // out[m][n] = sum over splits of D[s][m][n], fixed order
+// Implicit-GEMM 5x5 convolution of NHWC BF16 images [n_images][64][256][32]
+// (see conv_tc.cu).  W: [bn][kp] BF16 K-major, k = (5u+v) 32 + c.  mode 0:
+// out = BF16 ReLU(z + bias) [P][32] (bn 32); mode 1: out = FP32 z + bias[0]
+// [P] (bn 16); mode 2: out = FP32 z [P][bn].  sgn -1 negates the tap offsets.
+struct ConvArgs {
+    const void* X;
+    const void* W;
+    int kp, n_images, bn, sgn, mode;
+    const float* bias;
+    void* out;
+    int* status;
+};
+int launch_conv(const ConvArgs& a, cudaStream_t st);
+
 void launch_split_sum(const float* D, int splits, long long mn, float* out, cudaStream_t st);
 size_t gram_smem_bytes();
 void launch_requant(const RequantArgs& a, cudaStream_t st);
@@ -145,11 +164,6 @@ void launch_scale_from_ring(const float2* V, long long v_origin, long long v_mas
 // scale[a][k] = 2 sqrt(R_aa[k] / 2) / gain (U = 2V) from an integration's R.
 void launch_scale_from_vis(const float2* R, int n_in, int n_in_pad, int n_chan, float gain, float* scale,
                            cudaStream_t st);
-
-// Autocorrelation-power tiles (64 rows of n_row spectra x 256 channels) of
-// spectra [s_begin, s_end) of the ring, accumulated into `tiles`.
-void launch_spectrogram(const float2* V, long long v_mask, int n_chan, int n_in, int n_in_pad, long long s_begin,
-                        long long s_end, int n_row, int rows, float* tiles, cudaStream_t st);
 
 void launch_fir(const FirArgs& a, cudaStream_t st);
 void launch_fft(const FftArgs& a, cudaStream_t st);

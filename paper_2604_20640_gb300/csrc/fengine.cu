@@ -232,38 +232,6 @@ __host__ __device__ constexpr int tw_smem_entries() {
     return M <= 16 ? 16 : tw_offset(M, M / 16);
 }
 
-// Four consecutive int8 samples of one input from stream index n0 as one
-// little-endian word; zero outside the valid window.
-__device__ __forceinline__ uint32_t load4(const StreamView& sv, int a, long long n0) {
-    const long long lo = sv.base > 0 ? sv.base : 0;
-    const int8_t* row = sv.x + (long long)a * sv.stride - sv.base;  // stream index 0
-    const uintptr_t addr = reinterpret_cast<uintptr_t>(row + n0);
-    const int c = (int)(addr & 3);
-    if (n0 - c >= lo && n0 - c + 8 <= sv.vhi) {
-        const uint32_t* q = reinterpret_cast<const uint32_t*>(addr - c);
-        const uint32_t w0 = __ldg(q);
-        const uint32_t w1 = c ? __ldg(q + 1) : 0u;
-        return __funnelshift_r(w0, w1, 8 * c);
-    }
-    uint32_t v = 0;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        const long long n = n0 + b;
-        if (n >= lo && n < sv.vhi) v |= (uint32_t)(uint8_t)row[n] << (8 * b);
-    }
-    return v;
-}
-
-// Exact int8 -> float: flip the sign bit, place the byte in the mantissa of
-// 2^23, subtract 2^23 + 128.
-__device__ __forceinline__ void unpack4(uint32_t w, float (&x)[4]) {
-    const uint32_t f = w ^ 0x80808080u;
-    x[0] = __int_as_float((int)__byte_perm(f, 0x4B000000u, 0x7440)) - 8388736.0f;
-    x[1] = __int_as_float((int)__byte_perm(f, 0x4B000000u, 0x7441)) - 8388736.0f;
-    x[2] = __int_as_float((int)__byte_perm(f, 0x4B000000u, 0x7442)) - 8388736.0f;
-    x[3] = __int_as_float((int)__byte_perm(f, 0x4B000000u, 0x7443)) - 8388736.0f;
-}
-
 constexpr int kFirThreads = 256;
 
 // Per-input state of one FIR thread: an aligned word pointer at frame 0 for
@@ -330,10 +298,6 @@ __device__ __forceinline__ uint32_t fir_word(const FirArgs& A, const FirInput& I
     return w;
 }
 
-__device__ __forceinline__ void fir_frame(const FirArgs& A, const FirInput& I, long long f, float (&x)[4]) {
-    unpack4(fir_word(A, I, f), x);
-}
-
 // Packed FP32 pairs (sm_100+): two lanes of one 64-bit register per op.
 __device__ __forceinline__ unsigned long long f2u(float2 v) {
     return (unsigned long long)__float_as_uint(v.x) | ((unsigned long long)__float_as_uint(v.y) << 32);
@@ -352,8 +316,9 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
     return u2f(r);
 }
 
-// Exact int8 -> float for four packed samples as two float pairs (the
-// mantissa trick of unpack4 with packed subtractions).
+// Exact int8 -> float for four packed samples as two float pairs: flip each
+// byte's sign bit, place it in the low mantissa bits of 2^23, and subtract
+// 2^23 + 128 with one packed subtraction per pair.
 __device__ __forceinline__ void unpack4x2(uint32_t w, float2& lo, float2& hi) {
     const uint32_t f = w ^ 0x80808080u;
     const float2 bias = make_float2(8388736.0f, 8388736.0f);
@@ -466,7 +431,8 @@ __device__ __forceinline__ const float2* fft_input(const FftArgs& A, long long s
     return A.Z + ((size_t)zs * n_pairs + pair) * M;
 }
 
-template <int M, bool ROT>
+// MODE 0: store U = 2Y; 1: store the rotated V; 2: accumulate power tiles.
+template <int M, int MODE>
 __global__ void __launch_bounds__(FftCfg<M>::THREADS, 1) fft_kernel(const FftArgs A) {
     using C = FftCfg<M>;
     extern __shared__ float2 smem[];
@@ -495,6 +461,11 @@ __global__ void __launch_bounds__(FftCfg<M>::THREADS, 1) fft_kernel(const FftArg
     }
     __syncthreads();
 
+    // power mode: channels tid + i blockDim per thread
+    constexpr int PCH = MODE == 2 ? ((n_chan + C::THREADS - 1) / C::THREADS) : 1;
+    float pa[PCH], pb[PCH];
+#pragma unroll
+    for (int i = 0; i < PCH; ++i) pa[i] = pb[i] = 0.f;
     float2 cur[16];
     load_first<M>(cur, fft_input<M>(A, s_lo, pair, n_pairs), tid);
     for (long long s = s_lo; s < s_hi; ++s) {
@@ -506,22 +477,60 @@ __global__ void __launch_bounds__(FftCfg<M>::THREADS, 1) fft_kernel(const FftArg
         if (tid < C::NACT) pass_compute_store<M, R0, 1, TW_NONE>(zbuf, cur, tws, twr, tid);
         __syncthreads();
         later_passes<M, R0, C::REGTW>(zbuf, tws, twr, tid, A.tw);
-        const long long slot = (s - A.v_origin) & A.v_mask;
-        float4* Vout = reinterpret_cast<float4*>(A.V + (size_t)slot * n_chan * A.n_in_pad + a);
-        for (int k = tid; k < n_chan; k += blockDim.x) {
-            const float2 zk = zbuf[pidx(k)];
-            const float2 zm = zbuf[pidx((M - k) & (M - 1))];
-            const float2 S = make_float2(zk.x + zm.x, zk.y - zm.y);
-            const float2 D = make_float2(zk.x - zm.x, zk.y + zm.y);
-            float4 out;
-            if constexpr (ROT) {
-                const float2 va = cmul(S, __ldg(A.phasor + (size_t)a * n_chan + k));
-                const float2 vb = cmul(D, __ldg(A.phasor + (size_t)(a + 1) * n_chan + k));
-                out = make_float4(va.x, va.y, vb.x, vb.y);
-            } else {
-                out = make_float4(S.x, S.y, D.y, -D.x);
+        if constexpr (MODE == 2) {
+            // |Y_a|^2 = |S|^2 / 4, |Y_b|^2 = |D|^2 / 4, summed over the row
+#pragma unroll
+            for (int i = 0; i < PCH; ++i) {
+                const int k = tid + i * (int)blockDim.x;
+                if (k < n_chan) {
+                    const float2 zk = zbuf[pidx(k)];
+                    const float2 zm = zbuf[pidx((M - k) & (M - 1))];
+                    const float sx = zk.x + zm.x, sy = zk.y - zm.y;
+                    const float dx = zk.x - zm.x, dy = zk.y + zm.y;
+                    pa[i] = fmaf(sx, sx, fmaf(sy, sy, pa[i]));
+                    pb[i] = fmaf(dx, dx, fmaf(dy, dy, pb[i]));
+                }
             }
-            Vout[(size_t)k * (A.n_in_pad >> 1)] = out;
+            const long long row = s / A.n_row;
+            if (s + 1 == s_hi || (s + 1) % A.n_row == 0) {
+                const float sc = 0.25f / (float)A.n_row;
+                const int n_cb = n_chan / 256, n_rb = A.rows / 64;
+#pragma unroll
+                for (int i = 0; i < PCH; ++i) {
+                    const int k = tid + i * (int)blockDim.x;
+                    if (k < n_chan) {
+                        const size_t px = (size_t)(row % 64) * 256 + (k % 256);
+                        if (a < A.n_in) {
+                            const size_t ta = ((size_t)a * n_rb + row / 64) * n_cb + k / 256;
+                            atomicAdd(A.tiles + ta * 16384 + px, pa[i] * sc);
+                        }
+                        if (a + 1 < A.n_in) {
+                            const size_t tb = ((size_t)(a + 1) * n_rb + row / 64) * n_cb + k / 256;
+                            atomicAdd(A.tiles + tb * 16384 + px, pb[i] * sc);
+                        }
+                    }
+                    pa[i] = 0.f;
+                    pb[i] = 0.f;
+                }
+            }
+        } else {
+            const long long slot = (s - A.v_origin) & A.v_mask;
+            float4* Vout = reinterpret_cast<float4*>(A.V + (size_t)slot * n_chan * A.n_in_pad + a);
+            for (int k = tid; k < n_chan; k += blockDim.x) {
+                const float2 zk = zbuf[pidx(k)];
+                const float2 zm = zbuf[pidx((M - k) & (M - 1))];
+                const float2 S = make_float2(zk.x + zm.x, zk.y - zm.y);
+                const float2 D = make_float2(zk.x - zm.x, zk.y + zm.y);
+                float4 out;
+                if constexpr (MODE == 1) {
+                    const float2 va = cmul(S, __ldg(A.phasor + (size_t)a * n_chan + k));
+                    const float2 vb = cmul(D, __ldg(A.phasor + (size_t)(a + 1) * n_chan + k));
+                    out = make_float4(va.x, va.y, vb.x, vb.y);
+                } else {
+                    out = make_float4(S.x, S.y, D.y, -D.x);
+                }
+                Vout[(size_t)k * (A.n_in_pad >> 1)] = out;
+            }
         }
         __syncthreads();
         if constexpr (C::REGTW) {
@@ -554,17 +563,17 @@ std::vector<float2> fft_twiddle_table(int M) {
     return t;
 }
 
-template <int M, bool ROT>
+template <int M, int MODE>
 static void launch_fft_m(const FftArgs& a, cudaStream_t st) {
     static int resident = 0;     // CTAs per SM at this kernel's registers and shared memory
     static int sms = 0;
     const size_t smem = FftCfg<M>::SMEM;
     if (!resident) {
-        cudaFuncSetAttribute(fft_kernel<M, ROT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(fft_kernel<M, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, fft_kernel<M, ROT>, FftCfg<M>::THREADS, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, fft_kernel<M, MODE>, FftCfg<M>::THREADS, smem);
         if (resident < 1) resident = 1;
         if (sms < 1) sms = 152;
     }
@@ -577,31 +586,32 @@ static void launch_fft_m(const FftArgs& a, cudaStream_t st) {
     FftArgs b = a;
     b.spt = (int)((n + runs - 1) / runs);
     dim3 grid((unsigned)((n + b.spt - 1) / b.spt), (unsigned)n_pairs);
-    fft_kernel<M, ROT><<<grid, FftCfg<M>::THREADS, smem, st>>>(b);
+    fft_kernel<M, MODE><<<grid, FftCfg<M>::THREADS, smem, st>>>(b);
 }
 
-template <bool ROT>
-static void launch_fft_rot(const FftArgs& a, cudaStream_t st) {
+template <int MODE>
+static void launch_fft_mode(const FftArgs& a, cudaStream_t st) {
     switch (a.M) {
-        case 16: launch_fft_m<16, ROT>(a, st); break;
-        case 32: launch_fft_m<32, ROT>(a, st); break;
-        case 64: launch_fft_m<64, ROT>(a, st); break;
-        case 128: launch_fft_m<128, ROT>(a, st); break;
-        case 256: launch_fft_m<256, ROT>(a, st); break;
-        case 512: launch_fft_m<512, ROT>(a, st); break;
-        case 1024: launch_fft_m<1024, ROT>(a, st); break;
-        case 2048: launch_fft_m<2048, ROT>(a, st); break;
-        case 4096: launch_fft_m<4096, ROT>(a, st); break;
-        case 8192: launch_fft_m<8192, ROT>(a, st); break;
-        case 16384: launch_fft_m<16384, ROT>(a, st); break;
+        case 16: launch_fft_m<16, MODE>(a, st); break;
+        case 32: launch_fft_m<32, MODE>(a, st); break;
+        case 64: launch_fft_m<64, MODE>(a, st); break;
+        case 128: launch_fft_m<128, MODE>(a, st); break;
+        case 256: launch_fft_m<256, MODE>(a, st); break;
+        case 512: launch_fft_m<512, MODE>(a, st); break;
+        case 1024: launch_fft_m<1024, MODE>(a, st); break;
+        case 2048: launch_fft_m<2048, MODE>(a, st); break;
+        case 4096: launch_fft_m<4096, MODE>(a, st); break;
+        case 8192: launch_fft_m<8192, MODE>(a, st); break;
+        case 16384: launch_fft_m<16384, MODE>(a, st); break;
         default: break;
     }
 }
 
 void launch_fft(const FftArgs& a, cudaStream_t st) {
     if (a.s_end <= a.s_begin) return;
-    if (a.phasor) launch_fft_rot<true>(a, st);
-    else launch_fft_rot<false>(a, st);
+    if (a.tiles) launch_fft_mode<2>(a, st);
+    else if (a.phasor) launch_fft_mode<1>(a, st);
+    else launch_fft_mode<0>(a, st);
 }
 
 void launch_fir(const FirArgs& a, cudaStream_t st) {

@@ -355,41 +355,7 @@ __global__ void mad_time_kernel(const float* power, int B, float sigma, bool acc
     }
 }
 
-// Autocorrelation power of row `row` (n_row spectra) for input a and channel
-// k, mean |Y|^2 = |U|^2 / 4 (U = 2Y from the F-engine), accumulated in tile
-// order: tile (a, row / 64, k / 256), pixel (row % 64, k % 256).  One thread
-// per (k, a), inputs fastest, so a warp reads contiguous spectra.
-__global__ void spectrogram_kernel(const float2* V, long long v_mask, int n_chan, int n_in, int n_in_pad,
-                                   long long s_begin, long long s_end, int n_row, int rows, float* tiles) {
-    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= (long long)n_chan * n_in_pad) return;
-    const int k = (int)(id / n_in_pad), a = (int)(id % n_in_pad);
-    if (a >= n_in) return;
-    const int n_cb = n_chan / TW, n_rb = rows / TH;
-    long long s = s_begin;
-    while (s < s_end) {
-        const long long row = s / n_row;
-        long long e = (row + 1) * n_row;
-        if (e > s_end) e = s_end;
-        float acc = 0.f;
-        for (long long q = s; q < e; ++q) {
-            const float2 u = V[(((q & v_mask) * n_chan) + k) * n_in_pad + a];
-            acc = fmaf(u.x, u.x, fmaf(u.y, u.y, acc));
-        }
-        const size_t t = ((size_t)a * n_rb + row / TH) * n_cb + k / TW;
-        tiles[t * TPIX + (size_t)(row % TH) * TW + (k % TW)] += acc * (0.25f / (float)n_row);
-        s = e;
-    }
-}
-
 }  // namespace
-
-void launch_spectrogram(const float2* V, long long v_mask, int n_chan, int n_in, int n_in_pad, long long s_begin,
-                        long long s_end, int n_row, int rows, float* tiles, cudaStream_t st) {
-    const long long n = (long long)n_chan * n_in_pad;
-    spectrogram_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(V, v_mask, n_chan, n_in, n_in_pad, s_begin, s_end,
-                                                                      n_row, rows, tiles);
-}
 
 }  // namespace corr
 
@@ -515,18 +481,43 @@ int gemm(corr_flagnet_t net, const void* A, const void* Bm, int M, int N, int K,
     return CORR_OK;
 }
 
-// Forward pass over B normalised tiles x [B][64][256] -> logits.
+int conv(corr_flagnet_t net, const uint16_t* X, const uint16_t* W, int B, int bn, int sgn, int mode,
+         const float* bias, void* out, cudaStream_t st) {
+    ConvArgs c{};
+    c.X = X;
+    c.W = W;
+    c.kp = 832;
+    c.n_images = B;
+    c.bn = bn;
+    c.sgn = sgn;
+    c.mode = mode;
+    c.bias = bias;
+    c.out = out;
+    c.status = net->status;
+    const int rc = launch_conv(c, st);
+    if (rc != CORR_OK) return ffail(net, rc, "flagnet convolution: bad layout");
+    ++net->launches;
+    FK(cudaGetLastError());
+    return CORR_OK;
+}
+
+// Forward pass over B normalised tiles x [B][64][256] -> logits.  The
+// 1-channel first layer is an im2col product (K = 25 taps padded to 64);
+// the 32-channel layers are implicit-GEMM convolutions.
 int forward(corr_flagnet_t net, const float* x, int B, cudaStream_t st) {
     const int P = B * TPIX;
-    net->launches += 1 + 3 * NL;
+    net->launches += 4;
     input_bf16_kernel<<<blocks(P), 256, 0, st>>>(x, P, net->act[0]);
-    for (int l = 0; l < NL; ++l) {
-        const int C = CI[l], Kp = kpad(25 * C), Np = npad(CO[l]);
-        im2col(net->act[l], C, P, 1, net->A, st);
-        int rc = gemm(net, net->A, net->wf[l], P, Np, Kp, Kp * 2, Kp * 2, 1, net->D, nullptr, st);
+    im2col(net->act[0], 1, P, 1, net->A, st);
+    int rc = gemm(net, net->A, net->wf[0], P, 32, 64, 128, 128, 1, net->D, nullptr, st);
+    if (rc != CORR_OK) return rc;
+    fwd_epilogue_kernel<<<blocks((long long)P * 32), 256, 0, st>>>(net->D, P, 32, 32, net->b[0], false, net->act[1],
+                                                                   net->logit);
+    for (int l = 1; l < NL; ++l) {
+        const bool last = l == NL - 1;
+        rc = conv(net, net->act[l], net->wf[l], B, last ? 16 : 32, 1, last ? 1 : 0, net->b[l],
+                  last ? static_cast<void*>(net->logit) : static_cast<void*>(net->act[l + 1]), st);
         if (rc != CORR_OK) return rc;
-        fwd_epilogue_kernel<<<blocks((long long)P * CO[l]), 256, 0, st>>>(net->D, P, CO[l], Np, net->b[l], l == NL - 1,
-                                                                          net->act[l + 1], net->logit);
     }
     FK(cudaGetLastError());
     return CORR_OK;
@@ -535,7 +526,7 @@ int forward(corr_flagnet_t net, const float* x, int B, cudaStream_t st) {
 // Loss and gradients (into gw/gb) for B tiles; loss summed on the device.
 int backward(corr_flagnet_t net, const uint8_t* truth, int B, cudaStream_t st) {
     const int P = B * TPIX;
-    net->launches += 2 + NL * 5 + (NL - 1) * 3;
+    net->launches += 2 + NL * 5 + 3 + 2;   // + the implicit convolutions, counted in conv()
     // rows 1..15 of the transposed gradient are the zero padding of the
     // 1-channel output layer's weight-gradient operand
     FK(cudaMemsetAsync(net->dzT + P, 0, (size_t)15 * P * 2, st));
@@ -554,10 +545,15 @@ int backward(corr_flagnet_t net, const uint8_t* truth, int B, cudaStream_t st) {
         if (rc != CORR_OK) return rc;
         gather_dw_kernel<<<blocks(Co * C * 25), 256, 0, st>>>(net->D2, C, Co, Np, net->gw[l]);
         if (l == 0) break;
-        // data gradient: dX[P][C] = A'[P][Kd] . Wd[C][Kd], then ReLU of layer l-1
+        // data gradient: dX[P][C] = sum over taps at negated offsets of dZ . Wd,
+        // then the ReLU mask of layer l-1
         const int Kd = kpad(25 * Co);
-        im2col(net->dz, Co, P, -1, net->A, st);
-        rc = gemm(net, net->A, net->wd[l], P, 32, Kd, Kd * 2, Kd * 2, 1, net->D, nullptr, st);
+        if (Co == 32) {
+            rc = conv(net, net->dz, net->wd[l], B, 32, -1, 2, nullptr, net->D, st);
+        } else {
+            im2col(net->dz, Co, P, -1, net->A, st);
+            rc = gemm(net, net->A, net->wd[l], P, 32, Kd, Kd * 2, Kd * 2, 1, net->D, nullptr, st);
+        }
         if (rc != CORR_OK) return rc;
         relu_grad_kernel<<<blocks((long long)P * C), 256, 0, st>>>(net->D, net->act[l], P, C, net->dz32, net->dz,
                                                                    net->dzT);

@@ -58,7 +58,7 @@ struct Tables {
 // Optional CUDA-event brackets around every kernel launch, per stage
 // (0 FIR, 1 FFT, 2 X-engine, 3 finalise, 4 flag, 5 requantise, 6 tensor-core
 // Gram).
-constexpr int kStages = 8;
+constexpr int kStages = 7;
 struct StageTimer {
     bool on = false;
     std::vector<cudaEvent_t> pool;
@@ -335,7 +335,7 @@ int alloc_pipe(corr_t h, Pipe& p) {
 // V ring.  `phasor` set -> rotated V (stage call); else U = 2Y (pipeline).
 int launch_f(corr_t h, const StreamView& sv, const Tables& t, float2* Z, long long z_origin, long long z_mask,
              float2* V, long long v_origin, long long v_mask, const float2* phasor, long long s_begin,
-             long long s_end, cudaStream_t st) {
+             long long s_end, cudaStream_t st, float* tiles = nullptr, int n_row = 0, int rows = 0) {
     FirArgs a{};
     a.src = sv;
     a.h = h->d_h;
@@ -366,6 +366,10 @@ int launch_f(corr_t h, const StreamView& sv, const Tables& t, float2* Z, long lo
     f.n_in_pad = h->n_in_pad;
     f.M = h->M;
     f.spt = choose_spt(s_end - s_begin, h->n_in_pad / 2);
+    f.tiles = tiles;
+    f.n_row = n_row;
+    f.rows = rows;
+    f.n_in = h->n_in;
     {
         Timed t_(h, 0, st);
         launch_fir(a, st);
@@ -1452,13 +1456,9 @@ int corr_spectrogram_dev(corr_t h, const int8_t* d_samples, size_t n_samples, si
     for (long long s0 = 0; s0 < s_total; s0 += h->pd.v_cap) {
         long long s1 = s0 + h->pd.v_cap;
         if (s1 > s_total) s1 = s_total;
+        // the FFT accumulates the tiles directly (no spectra ring traffic)
         CKRET(launch_f(h, sv, h->tab_direct, h->pd.Z, 0, h->pd.v_cap - 1, h->pd.V, 0, h->pd.v_cap - 1, nullptr, s0, s1,
-                       st));
-        {
-            Timed t_(h, 7, st);
-            launch_spectrogram(h->pd.V, h->pd.v_cap - 1, h->n_chan, h->n_in, h->n_in_pad, s0, s1, n_row, (int)rows,
-                               d_tiles, st);
-        }
+                       st, d_tiles, n_row, (int)rows));
         CK(cudaGetLastError());
     }
     return CORR_OK;
