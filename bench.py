@@ -70,6 +70,13 @@ BYTES_PER_SAMPLE = {"fir": 5.0, "fft": 8.0, "xengine": 4.0, "finalize": 0.0, "fl
                     "gram": 2.0}
 
 
+# DRAM read + write per input sample of a kernel, from one ncu capture of the
+# same launch shape (profiles/fir_fft_c2_small_ncu.md: 35.12 MB per FFT
+# launch of 128 spectra x 4 pairs = 8.39 M samples, cold cache).  Reported as
+# the roofline's `traffic` only for the workload and kernel it was taken on.
+TRAFFIC_PER_SAMPLE = {("c2", "fft"): 35.12e6 / 8388608}
+
+
 def _spec(wl, rank, samples):
     from fxsynth import config_c1, config_c2, config_c3
     from paper_2604_20640_gb300.replicas import rank_seed
@@ -678,8 +685,10 @@ def main():
     bytes_per_launch = bps[dom] * samples_timed / max(1, stage_n[di])
     avg_ms = stage_ms[di] / max(1, stage_n[di])
     achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+    tps = TRAFFIC_PER_SAMPLE.get((args.workload, dom))
+    traffic = tps * samples_timed / max(1, stage_n[di]) if tps and prec == 0 else None
     roofline = {"kernel": KERNELS[dom], "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "peak_source": peak_src,
+                "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_src,
                 "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms, "launches": stage_n[di],
                 "stage_share": share}
 
