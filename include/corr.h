@@ -316,6 +316,27 @@ long long corr_flagnet_kernel_launches(corr_flagnet_t net);
  */
 int corr_tile_mad_dev(const float* d_power, int n_tiles, float sigma, int axes, uint8_t* d_flags, void* stream);
 
+/*
+ * corr_calibrate_dev -- delay and phase calibration (Sec. 7, Eq. 3) from the
+ * visibilities of one integration d_vis [n_chan][n_in][n_in] (complex64,
+ * device, as corr_run_dev writes them), for every baseline (ref, a):
+ *   1. coarse delay: the peak of the delay spectrum
+ *      |sum_k R_k exp(-j 2 pi k t / M)| over t = -T .. T in quarter samples
+ *      (T = ceil(max_delay), M = 2 n_chan);
+ *   2. fine delay: weighted (|R_k|) linear fit to the unwrapped phase of the
+ *      coarse-corrected visibilities, tau = t + (M / 2 pi) d phase / d k;
+ *   3. residual phase: phi = -arg of the mean complex vector after removing
+ *      the delay.
+ * Channels outside [k_lo, k_hi) or flagged in d_flags (same layout, may be
+ * NULL) are left out.  tau[n_in], phi[n_in] (host, caller-owned) receive
+ * samples and radians relative to input ref (0 there; NaN for a baseline
+ * with no usable channel) in the convention of corr_set_delays, so that
+ * applying them flattens the phases.  Synchronous on `stream`.  The paper
+ * fits in FP64; steps 2-3 run in FP64, the delay-spectrum search in FP32.
+ */
+int corr_calibrate_dev(const float* d_vis, const uint8_t* d_flags, int n_chan, int n_in, int ref, int k_lo, int k_hi,
+                       double max_delay, double* tau, double* phi, void* stream);
+
 /* Shapes of a handle: n_in, n_chan, taps, n_int, n_in_pad (any may be NULL). */
 int corr_shape(corr_t h, int* n_in, int* n_chan, int* taps, int* n_int, int* n_in_pad);
 

@@ -22,7 +22,12 @@ Readings (also listed in the design notes):
   (unflagged) or 0 (flagged or outside [k_lo, k_hi)); the first maximum of
   its magnitude wins.
 * The fine fit weights channels by |R|, on the phase of R[k] with the coarse
-  slope removed, unwrapped along k in channel order.
+  slope removed.  The phase is unwrapped about the band's mean vector c0
+  (psi_k = arg c0 + wrap(arg R_k - arg c0)): the coarse step leaves at most
+  1/8 sample of delay, i.e. at most pi/8 of drift across the band, so there
+  is no 2 pi ambiguity to resolve, and an isolated channel whose noisy phase
+  sits near +-pi stays one outlier instead of adding 2 pi to every later
+  channel as a sequential unwrap would.  On noise-free data the two agree.
 """
 
 from __future__ import annotations
@@ -49,7 +54,8 @@ def calibrate_baseline(R: np.ndarray, M: int, mask: np.ndarray, max_delay: float
     k = np.arange(R.size, dtype=np.float64)
     sel = mask.astype(bool)
     Rc = R * np.exp(-2j * np.pi * k * t_c / M)
-    psi = np.unwrap(np.angle(Rc[sel]))
+    c0 = np.sum(Rc[sel])
+    psi = np.angle(c0) + np.angle(Rc[sel] * np.conj(c0))
     wk = np.abs(R[sel])
     # weighted least squares psi = c + b k
     kk = k[sel]

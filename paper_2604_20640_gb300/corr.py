@@ -37,7 +37,7 @@ EXPORTED = [
     "corr_get_tuning", "corr_spectrogram_dev", "corr_flagnet_create", "corr_flagnet_destroy",
     "corr_flagnet_num_params", "corr_flagnet_set_params", "corr_flagnet_get_params", "corr_flagnet_prepare",
     "corr_flagnet_forward", "corr_flagnet_loss_grad", "corr_flagnet_train_step", "corr_flagnet_flag",
-    "corr_flagnet_status", "corr_flagnet_kernel_launches", "corr_tile_mad_dev",
+    "corr_flagnet_status", "corr_flagnet_kernel_launches", "corr_tile_mad_dev", "corr_calibrate_dev",
 ]
 
 
@@ -105,6 +105,7 @@ def load_library(path: str = LIB_PATH):
         "corr_flagnet_status": (_i, [_vp, ctypes.POINTER(_i)]),
         "corr_flagnet_kernel_launches": (_ll, [_vp]),
         "corr_tile_mad_dev": (_i, [_vp, _i, ctypes.c_float, _i, _vp, _vp]),
+        "corr_calibrate_dev": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _d, _vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -391,6 +392,24 @@ def tile_mad(power, flags_out, axes: int = 1, sigma: float = 5.0, stream=None):
                              _stream_ptr(stream))
     if rc != CORR_OK:
         raise CorrError(rc, L.corr_last_error(None).decode())
+
+
+def calibrate(vis, flags=None, ref: int = 0, k_lo: int = 0, k_hi: Optional[int] = None, max_delay: float = 64.0,
+              stream=None):
+    """(tau [n_in], phi [n_in]) from one integration's visibilities
+    vis [n_chan][n_in][n_in] (complex64, CUDA) -- the delay-spectrum peak,
+    the weighted fit to the unwrapped phase and the residual phase of Sec. 7,
+    in the convention of Correlator.set_delays."""
+    L = load_library()
+    n_chan, n_in = vis.shape[0], vis.shape[1]
+    tau = np.empty(n_in)
+    phi = np.empty(n_in)
+    rc = L.corr_calibrate_dev(_dev_ptr(vis, "vis"), _dev_ptr(flags, "flags") if flags is not None else None,
+                              n_chan, n_in, ref, k_lo, n_chan if k_hi is None else k_hi, float(max_delay),
+                              tau.ctypes.data, phi.ctypes.data, _stream_ptr(stream))
+    if rc != CORR_OK:
+        raise CorrError(rc, L.corr_last_error(None).decode())
+    return tau, phi
 
 
 class FlagNet:

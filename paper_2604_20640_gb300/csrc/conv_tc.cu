@@ -5,12 +5,17 @@
 // output gradient and whose weights are the transposed layout).
 //
 // X is NHWC BF16 [n][64][256][32].  One M tile is 128 pixels of one image
-// row; its A operand for tap (u, v) is the 128 x 32 block of X at row
-// i + s(u-2), columns j0 + s(v-2) .. +127, loaded by one 4D TMA box (64-byte
-// rows, 64-byte swizzle).  Pixels outside the image come back as zeros from
-// the TMA's out-of-bounds fill, which is exactly the convolution's zero
-// padding.  All 25 taps' weights (BN x 32 each) stay resident in shared
-// memory.  K per M tile = 25 taps x 32 channels = 50 MMAs of K = 16.
+// row.  For each of the five kernel rows u the producer loads the halo row
+// segment X[n][i + s(u-2)][j0-2 .. j0+129][0..31] once, with a 5D TMA box
+// that lays it out as the K-major no-swizzle operand format: core matrices
+// of 8 consecutive pixels x 8 channels (16 bytes) stored contiguously,
+// [channel group][pixel][8 channels].  The A operand of tap (u, v) is then
+// the same buffer with its start moved by 2 + s(v-2) pixels (16 bytes each):
+// five taps per load, 42 KiB of operand traffic per M tile instead of 200.
+// Pixels outside the image come back as zeros from the TMA's out-of-bounds
+// fill, which is exactly the convolution's zero padding.  All 25 taps'
+// weights (BN x 32 each, 64-byte swizzle) stay resident in shared memory.
+// K per M tile = 25 taps x 32 channels = 50 MMAs of K = 16.
 //
 // Warp roles (192 threads): warp 0 lane 0 issues TMA into a ring of A
 // stages, warp 1 lane 0 issues tcgen05.mma into one of two TMEM accumulators
@@ -38,7 +43,9 @@ using namespace tc;
 constexpr int kImgH = 64, kImgW = 256, kCh = 32;
 constexpr int kTaps = 25;
 constexpr int kAStages = 6;
-constexpr int kATile = 128 * kCh * 2;        // 8 KiB: 128 pixels x 32 channels BF16
+constexpr int kHalo = 132;                   // 128 pixels + 2 on each side
+constexpr int kGroupBytes = kHalo * 16;      // one 8-channel group of the halo row: 2112 bytes
+constexpr int kATile = 4 * kGroupBytes;      // 8448 bytes: 132 pixels x 32 channels BF16
 constexpr int kConvThreads = 192;
 
 struct __align__(8) ConvShared {
@@ -58,8 +65,8 @@ __host__ __device__ constexpr uint32_t conv_idesc() {
 
 template <int BN>
 __host__ __device__ constexpr size_t conv_smem() {
-    // 1024-byte alignment slack, A ring, resident weights, 8 KiB guard, barriers
-    return 1024 + (size_t)kAStages * kATile + (size_t)kTaps * BN * 64 + 8192 + sizeof(ConvShared);
+    // 1024-byte alignment slack twice, A ring, resident weights, 8 KiB guard, barriers
+    return 2048 + (size_t)kAStages * kATile + (size_t)kTaps * BN * 64 + 8192 + sizeof(ConvShared);
 }
 
 template <int BN>
@@ -80,7 +87,8 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     constexpr uint32_t kCols = 2 * BN < 32 ? 32 : 2 * BN;
     extern __shared__ __align__(1024) uint8_t csm_raw[];
     uint8_t* a_st = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(csm_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t* w_st = a_st + kAStages * kATile;
+    uint8_t* w_st = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(a_st + kAStages * kATile) + 1023) &
+                                               ~uintptr_t(1023));
     ConvShared* sh = reinterpret_cast<ConvShared*>(w_st + kTaps * kWTile + 8192);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_mt = A.n_images * kImgH * 2;
@@ -120,16 +128,16 @@ __global__ void __launch_bounds__(kConvThreads, 1)
             const int mt = (int)blockIdx.x + lt * (int)gridDim.x;
             const int n = mt / (kImgH * 2), rem = mt % (kImgH * 2);
             const int i = rem >> 1, j0 = (rem & 1) * 128;
-            for (int tap = 0; tap < kTaps; ++tap, ++it) {
+            for (int u = 0; u < 5; ++u, ++it) {
                 const int s = it % kAStages;
                 const uint32_t ph = (uint32_t)(it / kAStages) & 1u;
                 if (!mbar_wait(&sh->empty[s], ph ^ 1u)) {
                     sh->abort = 1;
                     break;
                 }
-                const int u = tap / 5, v = tap % 5;
                 mbar_expect_tx(&sh->full[s], kATile);
-                tma_load_4d(a_st + s * kATile, &tx, &sh->full[s], 0, j0 + A.sgn * (v - 2), i + A.sgn * (u - 2), n);
+                // box {8 channels, 132 pixels, 4 channel groups, 1 row, 1 image}
+                tma_load_5d(a_st + s * kATile, &tx, &sh->full[s], 0, j0 - 2, 0, i + A.sgn * (u - 2), n);
             }
         }
     } else if (warp == 1 && lane == 0) {
@@ -147,7 +155,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t d = tmem + (uint32_t)(b * BN);
             bool ok = true;
-            for (int tap = 0; tap < kTaps; ++tap, ++it) {
+            for (int u = 0; u < 5; ++u, ++it) {
                 const int s = it % kAStages;
                 const uint32_t ph = (uint32_t)(it / kAStages) & 1u;
                 if (!mbar_wait(&sh->full[s], ph)) {
@@ -155,10 +163,18 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint64_t da = sdesc64(smem_u32(a_st + s * kATile));
-                const uint64_t db = sdesc64(smem_u32(w_st + tap * kWTile));
-                conv_mma<BN>(d, da, db, tap != 0 ? 1u : 0u);
-                conv_mma<BN>(d, da + 2, db + 2, 1u);     // second 16 channels: +32 bytes
+                const uint32_t a0 = smem_u32(a_st + s * kATile);
+#pragma unroll
+                for (int v = 0; v < 5; ++v) {
+                    const int tap = 5 * u + v;
+                    // tap (u, v) reads pixels j0 + s(v-2) .. : 2 + s(v-2) rows into the halo
+                    const uint32_t off = (uint32_t)(2 + A.sgn * (v - 2)) * 16u;
+                    const uint64_t da = sdesc_plain(a0 + off, kGroupBytes, 128);
+                    const uint64_t db = sdesc64(smem_u32(w_st + tap * kWTile));
+                    conv_mma<BN>(d, da, db, tap != 0 ? 1u : 0u);
+                    // channels 16..31: two 8-channel groups further in K, +32 bytes in the weights
+                    conv_mma<BN>(d, sdesc_plain(a0 + off + 2 * kGroupBytes, kGroupBytes, 128), db + 2, 1u);
+                }
                 mma_commit(&sh->empty[s]);
             }
             if (!ok) {
@@ -231,31 +247,35 @@ __global__ void __launch_bounds__(kConvThreads, 1)
 }
 
 bool encode(CUtensorMap* map, CUtensorMapDataType dt, cuuint32_t rank, const void* base, const cuuint64_t* dims,
-            const cuuint64_t* strides, const cuuint32_t* box) {
+            const cuuint64_t* strides, const cuuint32_t* box, CUtensorMapSwizzle swz) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
     cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    return enc(map, dt, rank, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return enc(map, dt, rank, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <int BN>
 int launch_bn(const ConvArgs& a, cudaStream_t st) {
     CUtensorMap tx, tw;
-    const cuuint64_t xd[4] = {(cuuint64_t)kCh, (cuuint64_t)kImgW, (cuuint64_t)kImgH, (cuuint64_t)a.n_images};
-    const cuuint64_t xs[3] = {(cuuint64_t)kCh * 2, (cuuint64_t)kCh * 2 * kImgW, (cuuint64_t)kCh * 2 * kImgW * kImgH};
-    const cuuint32_t xb[4] = {(cuuint32_t)kCh, 128, 1, 1};
+    // X viewed as [n][row][channel group g][pixel][8 channels]: dims (fastest
+    // first) 8 channels, 256 pixels (64 B apart), 4 groups (16 B apart), 64
+    // rows, n images
+    const cuuint64_t xd[5] = {8, (cuuint64_t)kImgW, 4, (cuuint64_t)kImgH, (cuuint64_t)a.n_images};
+    const cuuint64_t xs[4] = {(cuuint64_t)kCh * 2, 16, (cuuint64_t)kCh * 2 * kImgW, (cuuint64_t)kCh * 2 * kImgW * kImgH};
+    const cuuint32_t xb[5] = {8, (cuuint32_t)kHalo, 4, 1, 1};
     const cuuint64_t wd[2] = {(cuuint64_t)a.kp, (cuuint64_t)BN};
     const cuuint64_t ws[1] = {(cuuint64_t)a.kp * 2};
     const cuuint32_t wb[2] = {(cuuint32_t)kCh, (cuuint32_t)BN};
-    if (!encode(&tx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, a.X, xd, xs, xb) ||
-        !encode(&tw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a.W, wd, ws, wb))
+    if (!encode(&tx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, a.X, xd, xs, xb, CU_TENSOR_MAP_SWIZZLE_NONE) ||
+        !encode(&tw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a.W, wd, ws, wb, CU_TENSOR_MAP_SWIZZLE_64B))
         return CORR_EINVAL;
     static int resident = 0, sms = 0;
     const size_t smem = conv_smem<BN>();
     if (!resident) {
         cudaFuncSetAttribute(conv_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(conv_kernel<BN>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -74,6 +74,27 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
+                                            int c3, int c4) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5, %6}], [%7];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor, K-major operand without swizzle: core
+// matrices of 8 rows x 16 bytes stored contiguously, `lbo` bytes between
+// core matrices adjacent in K, `sbo` bytes between 8-row groups.
+__device__ __forceinline__ uint64_t sdesc_plain(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);        // start address
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;      // leading byte offset (K direction)
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;      // stride byte offset (M/N direction)
+    d |= (uint64_t)1 << 46;                          // descriptor version
+    return d;                                        // layout type 0: no swizzle
+}
+
 // Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, rows of
 // 64 bytes, 8-row groups 512 bytes apart (the layout TMA writes for a
 // 64-byte inner box with CU_TENSOR_MAP_SWIZZLE_64B).

@@ -55,3 +55,19 @@ def test_recovers_injected_delays_and_flattens_phase():
         assert abs(np.angle(np.mean(np.exp(1j * ph)))) < 0.05
         t2, _ = co.calibrate_baseline(R2[0, :, 0, a], M, np.arange(n_chan) >= 8, 48.0)
         assert abs(t2) < 0.05
+
+
+def test_unwrap_about_the_mean_matches_sequential_unwrap_when_clean_and_resists_outliers():
+    n_chan = 1024
+    M = 2 * n_chan
+    k = np.arange(n_chan)
+    R = 5.0 * np.exp(1j * (2 * np.pi * k * 3.1 / M - 0.4))
+    mask = np.ones(n_chan, bool)
+    t1, p1 = co.calibrate_baseline(R, M, mask, 16.0)
+    assert abs(t1 - 3.1) < 1e-9 and abs(p1 - 0.4) < 1e-9
+    # one weak channel with its phase flipped: a sequential unwrap of the
+    # residual phase would carry a 2 pi step into the whole upper band
+    R2 = R.copy()
+    R2[300] = -0.05 * R[300] * np.exp(0.2j)
+    t2, p2 = co.calibrate_baseline(R2, M, mask, 16.0)
+    assert abs(t2 - 3.1) < 1e-3 and abs(p2 - 0.4) < 1e-3
