@@ -132,9 +132,15 @@ struct corr_s {
     cudaStream_t s_comp = nullptr, s_copy = nullptr;
     cudaEvent_t ev_h2d = nullptr, ev_comp = nullptr;
     bool started = false, flushed = false, stream_alloc = false;
-    int8_t* d_stage = nullptr;
-    int8_t* d_tmp = nullptr;
-    long long stage_cap = 0, stage_base = 0, stage_len = 0, tmp_cap = 0;
+    // Host pushes land in two staging buffers used in turn: the next chunk is
+    // copied (behind the history it needs) into the buffer the F-engine is
+    // not reading, so host->device copies overlap the correlation.
+    int8_t* d_stage_buf[2] = {nullptr, nullptr};
+    int8_t* d_stage = nullptr;           // the current buffer
+    int cur_buf = 0;
+    cudaEvent_t ev_buf[2] = {nullptr, nullptr};   // after the last kernels that read buffer b
+    bool buf_read[2] = {false, false};
+    long long stage_cap = 0, stage_base = 0, stage_len = 0;
     int8_t* h_pin = nullptr;
     long long pin_cap = 0;
     long long n_pushed = 0;
@@ -639,42 +645,41 @@ int ensure_stream_alloc(corr_t h) {
     if (h->stream_alloc) return CORR_OK;
     const long long keep = (long long)(h->taps + 1) * h->M + 2 * h->max_delay + 64;
     h->stage_cap = ((h->chunk + keep + 15) / 16) * 16;
-    h->tmp_cap = ((keep + 15) / 16) * 16;
-    CK(cudaMalloc(&h->d_stage, (size_t)h->stage_cap * h->n_in));
-    CK(cudaMalloc(&h->d_tmp, (size_t)h->tmp_cap * h->n_in));
-    CK(cudaMemset(h->d_stage, 0, (size_t)h->stage_cap * h->n_in));
+    for (int b = 0; b < 2; ++b) {
+        CK(cudaMalloc(&h->d_stage_buf[b], (size_t)h->stage_cap * h->n_in));
+        CK(cudaMemset(h->d_stage_buf[b], 0, (size_t)h->stage_cap * h->n_in));
+        CK(cudaEventCreateWithFlags(&h->ev_buf[b], cudaEventDisableTiming));
+        h->buf_read[b] = false;
+    }
+    h->cur_buf = 0;
+    h->d_stage = h->d_stage_buf[0];
     CKRET(alloc_pipe(h, h->ps));
     while ((int)h->slots.size() < h->result_slots) CKRET(add_slot(h));
     h->stream_alloc = true;
     return CORR_OK;
 }
 
-// Keep the samples still needed by unprocessed spectra at the front of the
-// staging buffer so that `need` more samples fit behind them.
+// Make room for `need` more samples: when the current staging buffer is
+// full, switch to the other one, with the samples still needed by
+// unprocessed spectra copied to its front.  The other buffer is reused only
+// after the kernels that last read it have finished (ev_buf); the history
+// copy itself runs on the copy stream behind the copies that wrote it.
 int make_room(corr_t h, long long need) {
     if (h->stage_len + need <= h->stage_cap) return CORR_OK;
     long long keep_lo = (h->ps.s_next - h->taps + 1) * (long long)h->M - h->max_delay;
     if (keep_lo < h->stage_base) keep_lo = h->stage_base;
     const long long off = keep_lo - h->stage_base;
     const long long keep = h->stage_len - off;
-    if (keep + need > h->stage_cap || keep > h->tmp_cap)
-        return fail(h, CORR_EINVAL, "internal: staging buffer too small");
-    if (keep > 0 && off > 0) {
-        if (off >= keep) {
-            CK(cudaMemcpy2DAsync(h->d_stage, h->stage_cap, h->d_stage + off, h->stage_cap, keep, h->n_in,
-                                 cudaMemcpyDeviceToDevice, h->s_comp));
-        } else {
-            CK(cudaMemcpy2DAsync(h->d_tmp, h->tmp_cap, h->d_stage + off, h->stage_cap, keep, h->n_in,
-                                 cudaMemcpyDeviceToDevice, h->s_comp));
-            CK(cudaMemcpy2DAsync(h->d_stage, h->stage_cap, h->d_tmp, h->tmp_cap, keep, h->n_in,
-                                 cudaMemcpyDeviceToDevice, h->s_comp));
-        }
-    }
+    if (keep + need > h->stage_cap) return fail(h, CORR_EINVAL, "internal: staging buffer too small");
+    const int nb = 1 - h->cur_buf;
+    if (h->buf_read[nb]) CK(cudaStreamWaitEvent(h->s_copy, h->ev_buf[nb], 0));
+    if (keep > 0)
+        CK(cudaMemcpy2DAsync(h->d_stage_buf[nb], h->stage_cap, h->d_stage + off, h->stage_cap, keep, h->n_in,
+                             cudaMemcpyDeviceToDevice, h->s_copy));
+    h->cur_buf = nb;
+    h->d_stage = h->d_stage_buf[nb];
     h->stage_base = keep_lo;
     h->stage_len = keep;
-    // Later host->device copies overwrite regions the queued kernels read.
-    CK(cudaEventRecord(h->ev_comp, h->s_comp));
-    CK(cudaStreamWaitEvent(h->s_copy, h->ev_comp, 0));
     return CORR_OK;
 }
 
@@ -684,8 +689,11 @@ int process_stream(corr_t h, bool final) {
     sv.stride = h->stage_cap;
     sv.base = h->stage_base;
     sv.vhi = h->n_pushed;
-    return drive(h, h->ps, sv, h->tab_stream, ready_spectra(h, final), final, true, sink_stream, nullptr,
-                 h->s_comp);
+    CKRET(drive(h, h->ps, sv, h->tab_stream, ready_spectra(h, final), final, true, sink_stream, nullptr,
+                h->s_comp));
+    CK(cudaEventRecord(h->ev_buf[h->cur_buf], h->s_comp));
+    h->buf_read[h->cur_buf] = true;
+    return CORR_OK;
 }
 
 int push_common(corr_t h, const int8_t* src, size_t n, size_t stride, bool on_device, cudaStream_t ust) {
@@ -888,8 +896,10 @@ int corr_destroy(corr_t h) {
     cudaFree(h->tab_direct.coarse);
     cudaFree(h->d_z_f);
     cudaFree(h->d_status);
-    cudaFree(h->d_stage);
-    cudaFree(h->d_tmp);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(h->d_stage_buf[b]);
+        if (h->ev_buf[b]) cudaEventDestroy(h->ev_buf[b]);
+    }
     if (h->h_pin) cudaFreeHost(h->h_pin);
     if (h->ev_h2d) cudaEventDestroy(h->ev_h2d);
     if (h->ev_comp) cudaEventDestroy(h->ev_comp);
@@ -1013,6 +1023,9 @@ int corr_reset(corr_t h) {
     if (h->s_copy) CK(cudaStreamSynchronize(h->s_copy));
     h->started = h->flushed = false;
     h->stage_base = h->stage_len = 0;
+    h->cur_buf = 0;
+    h->d_stage = h->d_stage_buf[0];
+    h->buf_read[0] = h->buf_read[1] = false;
     h->n_pushed = 0;
     h->ps.s_next = h->ps.s_xdone = 0;
     h->ps.have_scale = false;
