@@ -544,6 +544,8 @@ def main():
                     help="0 FP32 CUDA-core X, 1 int8 / 2 e4m3 tensor-core X (default: FP32, int8 for c3)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--train-steps", type=int, default=C5_TRAIN_STEPS, help="c5: Adam steps before timing")
+    ap.add_argument("--bits", type=int, default=8, choices=[8, 16],
+                    help="c1-c3: 16 = the 16-bit padded recorder mode (the same stream scaled to 14-bit values)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -579,8 +581,11 @@ def main():
     n_in = W["n_ant"] * W["n_pol"]
     spec = _spec(args.workload, rank, S)
     x = make_stream_torch(spec, device=dev)
+    if args.bits == 16:
+        x = x.to(torch.int16) * 64          # 14-bit values in int16 containers
     prec = args.precision if args.precision is not None else (1 if args.workload == "c3" else 0)
-    c = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"], precision=prec)
+    c = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"], precision=prec,
+                   sample_bits=args.bits)
     c.set_delays(spec.tau, spec.phi)
     n_intg = c.n_integrations(S)
     vis = torch.empty((n_intg, W["n_chan"], n_in, n_in), dtype=torch.complex64, device=dev)
@@ -609,13 +614,13 @@ def main():
     stage_ms, stage_n = c.stage_times()
     c.set_option("stage_timing", 0)
     ms = max_over_ranks(ms, dist if world > 1 else None, dev)
-    bytes_step = n_in * S
+    bytes_step = n_in * S * (args.bits // 8)
     value = job_rate(bytes_step, world, ms)
 
     # ---- the plain FP32 path on the same stream (the metric's denominator) ----
     plain = None
     if prec != 0 and not args.no_plain:
-        cp = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"])
+        cp = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"], sample_bits=args.bits)
         cp.set_delays(spec.tau, spec.phi)
         for _ in range(max(1, args.warmup)):
             cp.run_dev(x, vis, flags)
@@ -637,9 +642,9 @@ def main():
     e2e = None
     if not args.no_e2e:
         ce = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"], chunk=W["chunk"],
-                        precision=prec)
+                        precision=prec, sample_bits=args.bits)
         ce.set_delays(spec.tau, spec.phi)
-        host = torch.empty((n_in, S), dtype=torch.int8, pin_memory=True)
+        host = torch.empty((n_in, S), dtype=x.dtype, pin_memory=True)
         host.copy_(x)
         chunk = W["chunk"]
 
@@ -676,6 +681,8 @@ def main():
     total_stage = sum(stage_ms) or 1.0
     share = {k: stage_ms[i] / total_stage for i, k in enumerate(STAGES)}
     bps = dict(BYTES_PER_SAMPLE)
+    if args.bits == 16:
+        bps["fir"] += 1.0          # the FIR reads 2 bytes per sample
     if prec == 2:
         bps.update(requant=5.0, gram=1.0)
     dom = max((k for k in STAGES if bps[k] > 0), key=lambda k: share[k])
@@ -701,7 +708,8 @@ def main():
             "config": {"workload": args.workload + ": " + W["desc"],
                        "path": ["plain FP32 (CUDA-core X)", "int8 requantised, tcgen05 X (BF16 MMA)",
                                 "e4m3 requantised, tcgen05 X"][prec],
-                       "samples_per_input": S, "l2": "inputs (%d MiB/step) larger than L2" % (bytes_step >> 20),
+                       "samples_per_input": S, "sample_bits": args.bits,
+                       "l2": "inputs (%d MiB/step) larger than L2" % (bytes_step >> 20),
                        "parallelism": "replicas" if world > 1 else "single"},
             "gpu_launches": launches, "clocks": clk, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
         }

@@ -16,7 +16,10 @@ Recipe (all randomness from a Philox bit generator keyed by ``seed``):
 * broadband bursts: each ``burst_frame``-sample frame carries, with
   probability ``burst_frac``, extra white noise of power ``burst_gain`` times
   the receiver noise, common to all inputs;
-* everything summed, rounded half-to-even and clipped to [-128, 127].
+* everything summed, rounded half-to-even and clipped to [-128, 127]
+  (``bits`` = 8, int8 output; the 8-bit truncated recorder mode), or to
+  [-2^(bits-1), 2^(bits-1) - 1] stored as int16 for larger ``bits`` (14: the
+  ADC width of the 16-bit padded recorder mode).
 
 The module holds no part of the correlator (no filter bank, channeliser,
 correlator or flagger).
@@ -48,6 +51,7 @@ class StreamSpec:
     burst_frame: int = 2048
     burst_gain: float = 10.0
     block: int = 1 << 16
+    bits: int = 8
 
     @property
     def n_in(self) -> int:
@@ -121,7 +125,8 @@ def make_stream(spec: StreamSpec, return_float: bool = False):
         for fr in hit:
             a0 = fr * spec.burst_frame
             x[:, a0:a0 + spec.burst_frame] += rng.standard_normal(spec.burst_frame)[None, :] * g
-    q = np.clip(np.rint(x), -128, 127).astype(np.int8)
+    lim = 1 << (spec.bits - 1)
+    q = np.clip(np.rint(x), -lim, lim - 1).astype(np.int8 if spec.bits <= 8 else np.int16)
     if return_float:
         return q, x
     return q

@@ -21,7 +21,8 @@ def make_stream_torch(spec: StreamSpec, device="cuda", block: int = 1 << 22) -> 
     n_in, S = spec.n_in, spec.n_samples
     g = torch.Generator(device=device)
     g.manual_seed(int(spec.seed) & ((1 << 63) - 1))
-    out = torch.empty((n_in, S), dtype=torch.int8, device=device)
+    lim = 1 << (spec.bits - 1)
+    out = torch.empty((n_in, S), dtype=torch.int8 if spec.bits <= 8 else torch.int16, device=device)
     B = min(block, S)
     if spec.burst_frac > 0:
         B = max(spec.burst_frame, (B // spec.burst_frame) * spec.burst_frame)
@@ -61,5 +62,5 @@ def make_stream_torch(spec: StreamSpec, device="cuda", block: int = 1 << 22) -> 
             burst = torch.randn((nf, spec.burst_frame), generator=g, device=device) * (
                 math.sqrt(spec.burst_gain) * spec.sigma)
             x += (burst * hit[:, None]).reshape(1, B)
-        out[:, b0:b0 + n] = torch.clamp(torch.round(x[:, :n]), -128, 127).to(torch.int8)
+        out[:, b0:b0 + n] = torch.clamp(torch.round(x[:, :n]), -lim, lim - 1).to(out.dtype)
     return out

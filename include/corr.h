@@ -4,7 +4,7 @@
  * The library computes, on one GPU, the hot path of an FX software correlator
  * (arXiv 2604.20640):
  *
- *   F-engine  (Sec. 4.2, "F-engine (PFB and FFT)"): int8 samples -> P-tap
+ *   F-engine  (Sec. 4.2, "F-engine (PFB and FFT)"): int8 or int16 samples -> P-tap
  *             windowed-sinc polyphase FIR over M = 2*n_chan branches -> M-point
  *             real FFT (channels 0 .. n_chan-1, DC kept, Nyquist dropped),
  *             with the geometric delay of Eq. 1 (Sec. 4.1) removed per input
@@ -22,8 +22,9 @@
  *   - Every call returns a status (CORR_OK = 0 or a negative CORR_E* code)
  *     and never aborts; corr_last_error() gives a message for the last
  *     failure on that handle (or on handle creation when h is NULL).
- *   - Inputs are n_in = n_ant * n_pol planes of int8 samples, input index
- *     a = ant * n_pol + pol; plane a starts at samples + a * input_stride.
+ *   - Inputs are n_in = n_ant * n_pol planes of samples (int8, or int16 with
+ *     option "sample_bits" = 16), input index a = ant * n_pol + pol; plane a
+ *     starts input_stride samples after plane a-1.
  *   - Visibilities are complex64 stored as interleaved float pairs
  *     (re, im), layout [integration][n_chan][n_in][n_in]; flags are uint8
  *     in the same layout (symmetric in a, b).
@@ -98,6 +99,12 @@ const char* corr_last_error(corr_t h);
  *   "ring_mb"      (1..4096, default 32)  MiB of each on-device spectrum ring
  *   "fir_spt"      (0 = automatic, 1..256; may change at any time)
  *                  spectra each FIR thread filters
+ *   "sample_bits"  (8, default; or 16)  input sample type of every call that
+ *                  takes samples: int8 (the 8-bit truncated recorder mode of
+ *                  Sec. 3) or little-endian int16 (the 16-bit padded mode,
+ *                  14-bit ADC values, Sec. 3); sample pointers are `const
+ *                  void*`, counts and strides are in samples.  Before the
+ *                  first push.
  *   "window"       (0 Hann, default; 1 Kaiser; 2 unit coefficients) taper
  *                  of the prototype filter h = taper x sinc (Sec. 4.2; the
  *                  8-tap Kaiser of Fig. 4); 2 with taps = 1 is the plain
@@ -125,13 +132,13 @@ int corr_set_delays(corr_t h, const double* delay_samples, const double* phase_r
  * integrations are finalised, flagged and queued for corr_get_vis /
  * corr_get_flags.  Any chunking of a stream gives bit-identical results.
  */
-int corr_push(corr_t h, const int8_t* samples, size_t n_per_input, size_t input_stride);
+int corr_push(corr_t h, const void* samples, size_t n_per_input, size_t input_stride);
 
 /*
  * corr_push_dev -- as corr_push, from device memory d_samples (caller-owned,
  * planar with input_stride), work queued on `stream`.  No host sync.
  */
-int corr_push_dev(corr_t h, const int8_t* d_samples, size_t n_per_input,
+int corr_push_dev(corr_t h, const void* d_samples, size_t n_per_input,
                   size_t input_stride, void* stream);
 
 /*
@@ -170,7 +177,7 @@ int corr_pending(corr_t h, int* n);
  * n <= max_int (CORR_EINVAL if too small).  *n_out = integrations written.
  * Work is queued on `stream`; the handle's streaming state is untouched.
  */
-int corr_run_dev(corr_t h, const int8_t* d_samples, size_t n_samples, size_t input_stride,
+int corr_run_dev(corr_t h, const void* d_samples, size_t n_samples, size_t input_stride,
                  float* d_vis, uint8_t* d_flags, int max_int, int include_partial,
                  int* n_out, void* stream);
 
@@ -189,7 +196,7 @@ int corr_run_dev(corr_t h, const int8_t* d_samples, size_t n_samples, size_t inp
  *   complex64.  Sec. 4.2 X-engine.
  * corr_flag_dev -- MAD flags (Eq. 2) of n_vis integrations d_vis into d_flags.
  */
-int corr_fengine_dev(corr_t h, const int8_t* d_samples, size_t n_samples, size_t input_stride,
+int corr_fengine_dev(corr_t h, const void* d_samples, size_t n_samples, size_t input_stride,
                      long long s0, int n_spec, float* d_V, void* stream);
 int corr_xengine_dev(corr_t h, const float* d_V, int n_spec, float* d_vis, void* stream);
 int corr_flag_dev(corr_t h, const float* d_vis, int n_vis, uint8_t* d_flags, void* stream);
@@ -233,7 +240,7 @@ int corr_device_status(corr_t h, int* status);
  * their own while a group call may still be executing.
  */
 int corr_group_create(corr_t* group, const corr_t* members, int n);
-int corr_group_run_dev(corr_t group, const int8_t* const* d_samples, const size_t* n_samples,
+int corr_group_run_dev(corr_t group, const void* const* d_samples, const size_t* n_samples,
                        const size_t* strides, float* const* d_vis, uint8_t* const* d_flags,
                        const int* max_int, int* n_out, void* stream);
 
@@ -246,7 +253,7 @@ int corr_group_run_dev(corr_t group, const int8_t* const* d_samples, const size_
  * line is applied without timing, a new choice is appended.
  * corr_get_tuning reports the current values.
  */
-int corr_autotune(corr_t h, const int8_t* d_samples, size_t n_samples, size_t input_stride,
+int corr_autotune(corr_t h, const void* d_samples, size_t n_samples, size_t input_stride,
                   const char* cache_path, void* stream);
 int corr_get_tuning(corr_t h, int* ring_mb, int* fir_spt);
 
@@ -262,7 +269,7 @@ int corr_get_tuning(corr_t h, int* ring_mb, int* fir_spt);
  * of 256 and rows >= 64, else CORR_EINVAL.  d_tiles: [n_in][rows/64]
  * [n_chan/256][64][256] FP32 (device, caller-owned, overwritten).
  */
-int corr_spectrogram_dev(corr_t h, const int8_t* d_samples, size_t n_samples, size_t input_stride, int n_row,
+int corr_spectrogram_dev(corr_t h, const void* d_samples, size_t n_samples, size_t input_stride, int n_row,
                          float* d_tiles, void* stream);
 
 /*

@@ -198,6 +198,7 @@ class Correlator:
         self.n_in = n_ant * n_pol
         self.n_in_pad = (self.n_in + 3) // 4 * 4
         self.M = 2 * n_chan
+        self.sample_bits = 8
         for k, v in options.items():
             self.set_option(k, v)
 
@@ -227,6 +228,12 @@ class Correlator:
     # -- configuration ----------------------------------------------------
     def set_option(self, key: str, value: float):
         self._check(self._L.corr_set_option(self._h, key.encode(), float(value)))
+        if key == "sample_bits":
+            self.sample_bits = int(value)
+
+    def _sample_types(self):
+        import torch
+        return (np.int16, torch.int16) if self.sample_bits == 16 else (np.int8, torch.int8)
 
     def set_delays(self, tau, phi=None):
         tau = np.ascontiguousarray(tau, dtype=np.float64)
@@ -242,14 +249,16 @@ class Correlator:
 
     # -- streaming --------------------------------------------------------
     def push(self, samples):
-        """Append host samples ``[n_in][n]`` (int8 numpy array or CPU tensor)."""
+        """Append host samples ``[n_in][n]`` (numpy array or CPU tensor of the
+        handle's sample type: int8, or int16 with sample_bits=16)."""
+        np_t = np.int16 if self.sample_bits == 16 else np.int8
         try:
             import torch
             if isinstance(samples, torch.Tensor):
                 if samples.is_cuda:
                     return self.push_dev(samples)
-                if samples.dtype != torch.int8 or samples.dim() != 2 or samples.shape[0] != self.n_in:
-                    raise CorrError(CORR_EINVAL, "samples must be int8 [n_in][n]")
+                if samples.dtype != self._sample_types()[1] or samples.dim() != 2 or samples.shape[0] != self.n_in:
+                    raise CorrError(CORR_EINVAL, "samples must be %s [n_in][n]" % np.dtype(np_t).name)
                 if samples.stride(1) != 1:
                     raise CorrError(CORR_EINVAL, "samples rows must be contiguous")
                 self._check(self._L.corr_push(self._h, samples.data_ptr(), samples.shape[1],
@@ -258,16 +267,18 @@ class Correlator:
         except ImportError:
             pass
         a = np.asarray(samples)
-        if a.dtype != np.int8 or a.ndim != 2 or a.shape[0] != self.n_in:
-            raise CorrError(CORR_EINVAL, "samples must be int8 [n_in][n]")
-        if a.strides[1] != 1:
+        if a.dtype != np_t or a.ndim != 2 or a.shape[0] != self.n_in:
+            raise CorrError(CORR_EINVAL, "samples must be %s [n_in][n]" % np.dtype(np_t).name)
+        if a.strides[1] != a.itemsize or a.strides[0] % a.itemsize:
             a = np.ascontiguousarray(a)
-        self._check(self._L.corr_push(self._h, a.ctypes.data, a.shape[1], a.strides[0]))
+        self._check(self._L.corr_push(self._h, a.ctypes.data, a.shape[1], a.strides[0] // a.itemsize))
 
     def push_dev(self, samples, stream=None):
-        """Append device samples (CUDA int8 tensor ``[n_in][n]``, rows contiguous)."""
-        if samples.dim() != 2 or samples.shape[0] != self.n_in or samples.stride(1) != 1:
-            raise CorrError(CORR_EINVAL, "samples must be int8 [n_in][n] with contiguous rows")
+        """Append device samples (CUDA tensor ``[n_in][n]`` of the handle's
+        sample type, rows contiguous)."""
+        if samples.dim() != 2 or samples.shape[0] != self.n_in or samples.stride(1) != 1 or \
+                samples.dtype != self._sample_types()[1]:
+            raise CorrError(CORR_EINVAL, "samples must be [n_in][n] of the sample type with contiguous rows")
         self._check(self._L.corr_push_dev(self._h, _dev_ptr(samples, "samples"), samples.shape[1],
                                           samples.stride(0), _stream_ptr(stream)))
 

@@ -13,10 +13,11 @@ namespace corr {
 // sample with stream index n lives at x[a * stride + (n - base)] for
 // max(0, base) <= n < vhi; every other index reads as zero.
 struct StreamView {
-    const int8_t* x;
-    long long stride;
+    const int8_t* x;          // byte address of the [n_in][stride] sample planes
+    long long stride;         // samples between input planes
     long long base;
     long long vhi;
+    int es;                   // bytes per sample: 1 (int8) or 2 (int16)
 };
 
 // Ring slots: spectrum s lives in slot (s - origin) & mask.  Rings that wrap

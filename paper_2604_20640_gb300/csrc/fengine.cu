@@ -235,9 +235,10 @@ __host__ __device__ constexpr int tw_smem_entries() {
 constexpr int kFirThreads = 256;
 
 // Per-input state of one FIR thread: an aligned word pointer at frame 0 for
-// branches m0..m0+3 shifted by the coarse delay, the byte offset inside the
-// word, and the frames [f_lo, f_hi] whose two words lie inside the valid
-// window (no bounds checks needed there).
+// branches m0..m0+3 shifted by the coarse delay, the bit offset inside the
+// word, and the frames [f_lo, f_hi] whose words lie inside the valid window
+// (no bounds checks needed there).  Four samples are one 32-bit raw word for
+// int8 input (two words read) and a pair of words for int16 (three read).
 struct FirInput {
     const uint32_t* q;
     int sh;
@@ -247,22 +248,37 @@ struct FirInput {
     bool has;
 };
 
+template <int ES>
+struct Raw4;
+template <>
+struct Raw4<1> {
+    using T = uint32_t;
+};
+template <>
+struct Raw4<2> {
+    using T = uint2;
+};
+
+template <int ES>
 __device__ __forceinline__ FirInput fir_input(const FirArgs& A, int in, bool has, int m0, int d) {
+    constexpr int kWords = ES == 1 ? 2 : 3;          // words a raw value reads
     FirInput r;
     r.in = in;
     r.has = has;
     r.n0 = (long long)m0 + d;
     const long long lo = A.src.base > 0 ? A.src.base : 0;
-    const int8_t* p0 = A.src.x + (long long)in * A.src.stride - A.src.base + r.n0;   // frame 0
+    const int8_t* p0 = A.src.x + ((long long)in * A.src.stride - A.src.base + r.n0) * ES;   // frame 0
     const int c = (int)(reinterpret_cast<uintptr_t>(p0) & 3);
     r.q = reinterpret_cast<const uint32_t*>(p0 - c);
     r.sh = 8 * c;
-    // frame f is safe when n0 + f M - c >= lo and n0 + f M - c + 8 <= vhi;
-    // M = 2^lgM, so ceil / floor division are arithmetic shifts.
-    const long long a_lo = lo - r.n0 + c;
-    const long long a_hi = A.src.vhi - 8 - r.n0 + c;
-    r.f_lo = (a_lo + A.M - 1) >> A.lgM;
-    r.f_hi = a_hi >> A.lgM;
+    // frame f is safe when its words, bytes (n0 + f M) ES - c .. + 4 kWords,
+    // lie in [lo ES, vhi ES); M ES = 2^(lgM + ES - 1), so ceil / floor
+    // division are arithmetic shifts.
+    const int lg = A.lgM + (ES - 1);
+    const long long a_lo = lo * ES - r.n0 * ES + c;
+    const long long a_hi = A.src.vhi * ES - 4 * kWords - r.n0 * ES + c;
+    r.f_lo = (a_lo + ((long long)A.M * ES) - 1) >> lg;
+    r.f_hi = a_hi >> lg;
     if (!has) {
         r.f_lo = -(1LL << 62);
         r.f_hi = 1LL << 62;
@@ -270,10 +286,10 @@ __device__ __forceinline__ FirInput fir_input(const FirArgs& A, int in, bool has
     return r;
 }
 
-// Four int8 samples of one input row from stream index n, each read only
-// inside [lo, vhi) (zero elsewhere).  Out of line: only the first and last
-// frames of a stream take this path.
-__device__ __noinline__ uint32_t load4_checked(const int8_t* row, long long lo, long long vhi, long long n) {
+// Four samples of one input row from stream index n, each read only inside
+// [lo, vhi) (zero elsewhere), packed as the raw value of the fast path.  Out
+// of line: only the first and last frames of a stream take this path.
+__device__ __noinline__ uint32_t load4_checked8(const int8_t* row, long long lo, long long vhi, long long n) {
     uint32_t v = 0;
     for (int b = 0; b < 4; ++b) {
         const long long i = n + b;
@@ -282,17 +298,37 @@ __device__ __noinline__ uint32_t load4_checked(const int8_t* row, long long lo, 
     return v;
 }
 
-// Raw int8 word (4 branches) of frame f of one input; zero before the stream.
-__device__ __forceinline__ uint32_t fir_word(const FirArgs& A, const FirInput& I, long long f) {
-    uint32_t w = 0u;
+__device__ __noinline__ uint2 load4_checked16(const int16_t* row, long long lo, long long vhi, long long n) {
+    uint32_t v[2] = {0u, 0u};
+    for (int b = 0; b < 4; ++b) {
+        const long long i = n + b;
+        if (i >= lo && i < vhi) v[b >> 1] |= (uint32_t)(uint16_t)row[i] << (16 * (b & 1));
+    }
+    return make_uint2(v[0], v[1]);
+}
+
+// Raw value (4 branches) of frame f of one input; zero before the stream.
+template <int ES>
+__device__ __forceinline__ typename Raw4<ES>::T fir_word(const FirArgs& A, const FirInput& I, long long f) {
+    using R = typename Raw4<ES>::T;
+    R w{};
     if (I.has && f >= 0) {
+        const long long lo = A.src.base > 0 ? A.src.base : 0;
+        const long long n = f * A.M + I.n0;
         if (f >= I.f_lo && f <= I.f_hi) {
-            const uint32_t* q = I.q + (f << (A.lgM - 2));
-            w = __funnelshift_r(__ldg(q), __ldg(q + 1), I.sh);
+            const uint32_t* q = I.q + ((f * A.M * ES) >> 2);
+            if constexpr (ES == 1) {
+                w = __funnelshift_r(__ldg(q), __ldg(q + 1), I.sh);
+            } else {
+                const uint32_t a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+                w = make_uint2(__funnelshift_r(a, b, I.sh), __funnelshift_r(b, c, I.sh));
+            }
+        } else if constexpr (ES == 1) {
+            w = load4_checked8(A.src.x + (long long)I.in * A.src.stride - A.src.base, lo, A.src.vhi, n);
         } else {
-            const long long lo = A.src.base > 0 ? A.src.base : 0;
-            w = load4_checked(A.src.x + (long long)I.in * A.src.stride - A.src.base, lo, A.src.vhi,
-                              f * A.M + I.n0);
+            w = load4_checked16(reinterpret_cast<const int16_t*>(A.src.x) + (long long)I.in * A.src.stride -
+                                    A.src.base,
+                                lo, A.src.vhi, n);
         }
     }
     return w;
@@ -328,6 +364,21 @@ __device__ __forceinline__ void unpack4x2(uint32_t w, float2& lo, float2& hi) {
                           __int_as_float((int)__byte_perm(f, 0x4B000000u, 0x7443))), bias);
 }
 
+// Exact int16 -> float for two packed samples: flip each sample's sign bit,
+// place it in the low 16 mantissa bits of 2^23, subtract 2^23 + 32768.
+__device__ __forceinline__ float2 unpack2x16(uint32_t w) {
+    const uint32_t f = w ^ 0x80008000u;
+    return sub2(make_float2(__int_as_float((int)__byte_perm(f, 0x4B000000u, 0x7610)),
+                            __int_as_float((int)__byte_perm(f, 0x4B000000u, 0x7632))),
+                make_float2(8421376.0f, 8421376.0f));
+}
+
+__device__ __forceinline__ void unpack_raw(uint32_t w, float2& lo, float2& hi) { unpack4x2(w, lo, hi); }
+__device__ __forceinline__ void unpack_raw(uint2 w, float2& lo, float2& hi) {
+    lo = unpack2x16(w.x);
+    hi = unpack2x16(w.y);
+}
+
 // y_s[m] = sum_p h[pM + m] x'[(s - P + 1 + p) M + m] for 4 branches of one
 // input over spectra [s_lo, s_hi).  Lanes 2q and 2q+1 of a warp take the
 // same branches of the two inputs of a pair and swap half their outputs with
@@ -337,8 +388,9 @@ __device__ __forceinline__ void unpack4x2(uint32_t w, float2& lo, float2& hi) {
 // are processed in blocks of P so frame f always sits in slot (f - base) mod
 // P.  Inside the frames whose words are in bounds for this thread the block
 // loop runs without checks; ring slots advance in 32-bit arithmetic.
-template <int P>
+template <int P, int ES>
 __global__ void __launch_bounds__(kFirThreads, P <= 4 ? 3 : (P <= 8 ? 2 : 1)) fir_kernel(const FirArgs A) {
+    using R = typename Raw4<ES>::T;
     const int M = A.M;
     const int t = blockIdx.x * kFirThreads + threadIdx.x;   // (branch group, input of pair)
     if (t >= (M >> 1)) return;
@@ -351,7 +403,7 @@ __global__ void __launch_bounds__(kFirThreads, P <= 4 ? 3 : (P <= 8 ? 2 : 1)) fi
     if (s_hi > A.s_end) s_hi = A.s_end;
     if (s_lo >= s_hi) return;   // uniform over the CTA
     const bool has = in < A.n_in;
-    const FirInput I = fir_input(A, in, has, m0, has ? A.coarse[in] : 0);
+    const FirInput I = fir_input<ES>(A, in, has, m0, has ? A.coarse[in] : 0);
 
     float2 h[P][2];
 #pragma unroll
@@ -363,20 +415,20 @@ __global__ void __launch_bounds__(kFirThreads, P <= 4 ? 3 : (P <= 8 ? 2 : 1)) fi
     float2 w[P][2];
     const long long base_f = s_lo - (P - 1);
 #pragma unroll
-    for (int q = 0; q < P - 1; ++q) unpack4x2(fir_word(A, I, base_f + q), w[q][0], w[q][1]);
+    for (int q = 0; q < P - 1; ++q) unpack_raw(fir_word<ES>(A, I, base_f + q), w[q][0], w[q][1]);
     // even lanes store branches m0, m0+1; odd lanes m0+2, m0+3
     float2* const zp = A.Z + (size_t)pair * M + m0 + 2 * odd;
     const unsigned zstride = (unsigned)(A.n_pairs * M);
     const unsigned zmask = (unsigned)A.z_mask;
     unsigned slot = (unsigned)((s_lo - A.z_origin) & A.z_mask);
-    const int step = M >> 2;
+    const int step = (M * ES) >> 2;                 // words per frame
     // frames s0 .. s0+P-1 are unchecked when all lie in [f_safe_lo, f_safe_hi]
     const long long f_safe_lo = I.f_lo < 0 ? 0 : I.f_lo;
     long long s_fast_end = I.f_hi - (P - 1) + 1;        // blocks starting below this are safe
     if (s_fast_end > s_hi - (P - 1)) s_fast_end = s_hi - (P - 1);
 
-    auto emit = [&](int q, uint32_t word) {
-        unpack4x2(word, w[(q + P - 1) % P][0], w[(q + P - 1) % P][1]);
+    auto emit = [&](int q, R word) {
+        unpack_raw(word, w[(q + P - 1) % P][0], w[(q + P - 1) % P][1]);
         float2 y0 = make_float2(0.f, 0.f), y1 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
@@ -393,20 +445,27 @@ __global__ void __launch_bounds__(kFirThreads, P <= 4 ? 3 : (P <= 8 ? 2 : 1)) fi
 
     long long s0 = s_lo;
     if (has && s0 >= f_safe_lo) {
-        const uint32_t* qp = I.q + (s0 << (A.lgM - 2));
+        const uint32_t* qp = I.q + ((s0 * M * ES) >> 2);
         for (; s0 < s_fast_end; s0 += P) {
-            uint32_t r[P];
+            R r[P];
 #pragma unroll
-            for (int q = 0; q < P; ++q) r[q] = __funnelshift_r(__ldg(qp + q * step), __ldg(qp + q * step + 1), I.sh);
+            for (int q = 0; q < P; ++q) {
+                if constexpr (ES == 1) {
+                    r[q] = __funnelshift_r(__ldg(qp + q * step), __ldg(qp + q * step + 1), I.sh);
+                } else {
+                    const uint32_t a = __ldg(qp + q * step), b = __ldg(qp + q * step + 1), c = __ldg(qp + q * step + 2);
+                    r[q] = make_uint2(__funnelshift_r(a, b, I.sh), __funnelshift_r(b, c, I.sh));
+                }
+            }
             qp += P * step;
 #pragma unroll
             for (int q = 0; q < P; ++q) emit(q, r[q]);
         }
     }
     for (; s0 < s_hi; s0 += P) {
-        uint32_t r[P];
+        R r[P];
 #pragma unroll
-        for (int q = 0; q < P; ++q) r[q] = (s0 + q < s_hi) ? fir_word(A, I, s0 + q) : 0u;
+        for (int q = 0; q < P; ++q) r[q] = (s0 + q < s_hi) ? fir_word<ES>(A, I, s0 + q) : R{};
 #pragma unroll
         for (int q = 0; q < P; ++q)
             if (s0 + q < s_hi) emit(q, r[q]);   // uniform over the CTA
@@ -620,7 +679,11 @@ void launch_fir(const FirArgs& a, cudaStream_t st) {
     dim3 grid((unsigned)((a.M / 2 + kFirThreads - 1) / kFirThreads), (unsigned)a.n_pairs,
               (unsigned)((n + a.spt - 1) / a.spt));
     switch (a.taps) {
-#define CORR_FIR(P) case P: fir_kernel<P><<<grid, kFirThreads, 0, st>>>(a); break;
+#define CORR_FIR(P)                                                                    \
+    case P:                                                                            \
+        if (a.src.es == 2) fir_kernel<P, 2><<<grid, kFirThreads, 0, st>>>(a);          \
+        else fir_kernel<P, 1><<<grid, kFirThreads, 0, st>>>(a);                        \
+        break;
         CORR_FIR(1) CORR_FIR(2) CORR_FIR(3) CORR_FIR(4) CORR_FIR(5) CORR_FIR(6) CORR_FIR(7) CORR_FIR(8)
         CORR_FIR(9) CORR_FIR(10) CORR_FIR(11) CORR_FIR(12) CORR_FIR(13) CORR_FIR(14) CORR_FIR(15) CORR_FIR(16)
 #undef CORR_FIR

@@ -108,6 +108,7 @@ struct corr_s {
     int ring_mb = 32;            // tunable: ring capacity of Z and V (MiB each)
     int fir_spt = 0;             // tunable: spectra per FIR thread (0 = automatic)
     int window = 0;              // PFB taper: 0 Hann, 1 Kaiser, 2 unit coefficients
+    int es = 1;                  // bytes per input sample: 1 (int8) or 2 (int16, 16-bit padded mode)
     double kaiser_beta = 8.0;
     // group of handles run as one captured graph (corr_group_create)
     bool is_group = false;
@@ -646,8 +647,8 @@ int ensure_stream_alloc(corr_t h) {
     const long long keep = (long long)(h->taps + 1) * h->M + 2 * h->max_delay + 64;
     h->stage_cap = ((h->chunk + keep + 15) / 16) * 16;
     for (int b = 0; b < 2; ++b) {
-        CK(cudaMalloc(&h->d_stage_buf[b], (size_t)h->stage_cap * h->n_in));
-        CK(cudaMemset(h->d_stage_buf[b], 0, (size_t)h->stage_cap * h->n_in));
+        CK(cudaMalloc(&h->d_stage_buf[b], (size_t)h->stage_cap * h->n_in * h->es));
+        CK(cudaMemset(h->d_stage_buf[b], 0, (size_t)h->stage_cap * h->n_in * h->es));
         CK(cudaEventCreateWithFlags(&h->ev_buf[b], cudaEventDisableTiming));
         h->buf_read[b] = false;
     }
@@ -674,8 +675,8 @@ int make_room(corr_t h, long long need) {
     const int nb = 1 - h->cur_buf;
     if (h->buf_read[nb]) CK(cudaStreamWaitEvent(h->s_copy, h->ev_buf[nb], 0));
     if (keep > 0)
-        CK(cudaMemcpy2DAsync(h->d_stage_buf[nb], h->stage_cap, h->d_stage + off, h->stage_cap, keep, h->n_in,
-                             cudaMemcpyDeviceToDevice, h->s_copy));
+        CK(cudaMemcpy2DAsync(h->d_stage_buf[nb], h->stage_cap * h->es, h->d_stage + off * h->es, h->stage_cap * h->es,
+                             keep * h->es, h->n_in, cudaMemcpyDeviceToDevice, h->s_copy));
     h->cur_buf = nb;
     h->d_stage = h->d_stage_buf[nb];
     h->stage_base = keep_lo;
@@ -689,6 +690,7 @@ int process_stream(corr_t h, bool final) {
     sv.stride = h->stage_cap;
     sv.base = h->stage_base;
     sv.vhi = h->n_pushed;
+    sv.es = h->es;
     CKRET(drive(h, h->ps, sv, h->tab_stream, ready_spectra(h, final), final, true, sink_stream, nullptr,
                 h->s_comp));
     CK(cudaEventRecord(h->ev_buf[h->cur_buf], h->s_comp));
@@ -697,6 +699,7 @@ int process_stream(corr_t h, bool final) {
 }
 
 int push_common(corr_t h, const int8_t* src, size_t n, size_t stride, bool on_device, cudaStream_t ust) {
+    const size_t es = (size_t)h->es;   // src is a byte address; n, stride count samples
     if (h->flushed) return fail(h, CORR_ESTATE, "stream already flushed; call corr_reset");
     if (n == 0) return CORR_OK;
     if (!src) return fail(h, CORR_EINVAL, "samples is NULL");
@@ -717,23 +720,24 @@ int push_common(corr_t h, const int8_t* src, size_t n, size_t stride, bool on_de
     while (done < n) {
         const long long piece = (long long)std::min<size_t>(n - done, (size_t)h->chunk);
         CKRET(make_room(h, piece));
-        const int8_t* s = src + done;
-        size_t spitch = stride;
+        const int8_t* s = src + done * es;
+        size_t spitch = stride * es;
         cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         if (!on_device && !pinned) {
-            if (h->pin_cap < piece * h->n_in) {
+            if (h->pin_cap < piece * h->n_in * (long long)es) {
                 if (h->h_pin) cudaFreeHost(h->h_pin);
                 h->h_pin = nullptr;
-                CK(cudaHostAlloc(&h->h_pin, (size_t)piece * h->n_in, cudaHostAllocDefault));
-                h->pin_cap = piece * h->n_in;
+                CK(cudaHostAlloc(&h->h_pin, (size_t)piece * h->n_in * es, cudaHostAllocDefault));
+                h->pin_cap = piece * h->n_in * (long long)es;
             }
             for (int a = 0; a < h->n_in; ++a)
-                std::memcpy(h->h_pin + (size_t)a * piece, src + (size_t)a * stride + done, (size_t)piece);
+                std::memcpy(h->h_pin + (size_t)a * piece * es, src + ((size_t)a * stride + done) * es,
+                            (size_t)piece * es);
             s = h->h_pin;
-            spitch = (size_t)piece;
+            spitch = (size_t)piece * es;
         }
-        CK(cudaMemcpy2DAsync(h->d_stage + h->stage_len, h->stage_cap, s, spitch, (size_t)piece, h->n_in, kind,
-                             h->s_copy));
+        CK(cudaMemcpy2DAsync(h->d_stage + h->stage_len * (long long)es, h->stage_cap * es, s, spitch,
+                             (size_t)piece * es, h->n_in, kind, h->s_copy));
         CK(cudaEventRecord(h->ev_h2d, h->s_copy));
         CK(cudaStreamWaitEvent(h->s_comp, h->ev_h2d, 0));
         h->stage_len += piece;
@@ -951,6 +955,10 @@ int corr_set_option(corr_t h, const char* key, double v) {
     } else if (k == "stage_timing") {
         h->timer.on = v != 0;
         return CORR_OK;
+    } else if (k == "sample_bits") {
+        if (v != 8 && v != 16) return fail(h, CORR_EINVAL, "sample_bits: 8 or 16");
+        if (h->stream_alloc) return fail(h, CORR_ESTATE, "sample_bits must be set before the first push");
+        h->es = v == 16 ? 2 : 1;
     } else if (k == "window" || k == "kaiser_beta") {
         if (k == "window" && v != 0 && v != 1 && v != 2) return fail(h, CORR_EINVAL, "window: 0 Hann, 1 Kaiser, 2 none");
         if (k == "kaiser_beta" && !(v >= 0 && v <= 50)) return fail(h, CORR_EINVAL, "kaiser_beta out of range");
@@ -991,16 +999,16 @@ int corr_set_delays(corr_t h, const double* tau, const double* phi) {
     return CORR_OK;
 }
 
-int corr_push(corr_t h, const int8_t* samples, size_t n, size_t stride) {
+int corr_push(corr_t h, const void* samples, size_t n, size_t stride) {
     if (!h) return fail(h, CORR_EINVAL, "NULL handle");
     DeviceGuard g(h->dev);
-    return push_common(h, samples, n, stride, false, nullptr);
+    return push_common(h, static_cast<const int8_t*>(samples), n, stride, false, nullptr);
 }
 
-int corr_push_dev(corr_t h, const int8_t* d_samples, size_t n, size_t stride, void* stream) {
+int corr_push_dev(corr_t h, const void* d_samples, size_t n, size_t stride, void* stream) {
     if (!h) return fail(h, CORR_EINVAL, "NULL handle");
     DeviceGuard g(h->dev);
-    return push_common(h, d_samples, n, stride, true, static_cast<cudaStream_t>(stream));
+    return push_common(h, static_cast<const int8_t*>(d_samples), n, stride, true, static_cast<cudaStream_t>(stream));
 }
 
 int corr_flush(corr_t h) {
@@ -1059,7 +1067,7 @@ int corr_pending(corr_t h, int* n) {
     return CORR_OK;
 }
 
-int corr_run_dev(corr_t h, const int8_t* d_samples, size_t n_samples, size_t stride, float* d_vis,
+int corr_run_dev(corr_t h, const void* d_samples, size_t n_samples, size_t stride, float* d_vis,
                  uint8_t* d_flags, int max_int, int include_partial, int* n_out, void* stream) {
     if (!h) return fail(h, CORR_EINVAL, "NULL handle");
     if (h->is_group) return fail(h, CORR_EINVAL, "use corr_group_run_dev on a group");
@@ -1074,7 +1082,8 @@ int corr_run_dev(corr_t h, const int8_t* d_samples, size_t n_samples, size_t str
     h->pd.s_next = h->pd.s_xdone = 0;
     h->pd.have_scale = false;
     StreamView sv;
-    sv.x = d_samples;
+    sv.x = static_cast<const int8_t*>(d_samples);
+    sv.es = h->es;
     sv.stride = (long long)stride;
     sv.base = 0;
     sv.vhi = (long long)n_samples;
@@ -1085,7 +1094,7 @@ int corr_run_dev(corr_t h, const int8_t* d_samples, size_t n_samples, size_t str
     return CORR_OK;
 }
 
-int corr_fengine_dev(corr_t h, const int8_t* d_samples, size_t n_samples, size_t stride, long long s0,
+int corr_fengine_dev(corr_t h, const void* d_samples, size_t n_samples, size_t stride, long long s0,
                      int n_spec, float* d_V, void* stream) {
     if (!h) return fail(h, CORR_EINVAL, "NULL handle");
     DeviceGuard g(h->dev);
@@ -1098,7 +1107,7 @@ int corr_fengine_dev(corr_t h, const int8_t* d_samples, size_t n_samples, size_t
         CK(cudaMalloc(&h->d_z_f, sizeof(float2) * (size_t)n_spec * h->n_in_pad * h->n_chan));
         h->z_f_spectra = n_spec;
     }
-    StreamView sv{d_samples, (long long)stride, 0, (long long)n_samples};
+    StreamView sv{static_cast<const int8_t*>(d_samples), (long long)stride, 0, (long long)n_samples, h->es};
     CKRET(launch_f(h, sv, h->tab_direct, h->d_z_f, s0, -1LL, reinterpret_cast<float2*>(d_V), s0, -1LL,
                    h->tab_direct.phasor, s0, s0 + n_spec, static_cast<cudaStream_t>(stream)));
     return CORR_OK;
@@ -1234,7 +1243,7 @@ int corr_group_create(corr_t* out, const corr_t* members, int n) {
     return CORR_OK;
 }
 
-int corr_group_run_dev(corr_t g, const int8_t* const* d_samples, const size_t* n_samples, const size_t* strides,
+int corr_group_run_dev(corr_t g, const void* const* d_samples, const size_t* n_samples, const size_t* strides,
                        float* const* d_vis, uint8_t* const* d_flags, const int* max_int, int* n_out, void* stream) {
     if (!g || !g->is_group) return fail(g, CORR_EINVAL, "not a group");
     if (!d_samples || !n_samples || !strides || !d_vis || !max_int) return fail(g, CORR_EINVAL, "NULL argument");
@@ -1366,7 +1375,7 @@ bool tune_lookup(const char* path, const std::string& key, int* ring_mb, int* fi
 
 }  // namespace
 
-int corr_autotune(corr_t h, const int8_t* d_samples, size_t n_samples, size_t stride, const char* cache_path,
+int corr_autotune(corr_t h, const void* d_samples, size_t n_samples, size_t stride, const char* cache_path,
                   void* stream) {
     if (!h || h->is_group) return fail(h, CORR_EINVAL, "autotune needs a correlator handle");
     if (!d_samples || stride < n_samples) return fail(h, CORR_EINVAL, "bad sample buffer");
@@ -1453,7 +1462,7 @@ int corr_get_tuning(corr_t h, int* ring_mb, int* fir_spt) {
     return CORR_OK;
 }
 
-int corr_spectrogram_dev(corr_t h, const int8_t* d_samples, size_t n_samples, size_t stride, int n_row,
+int corr_spectrogram_dev(corr_t h, const void* d_samples, size_t n_samples, size_t stride, int n_row,
                          float* d_tiles, void* stream) {
     if (!h || h->is_group) return fail(h, CORR_EINVAL, "NULL handle");
     DeviceGuard dg(h->dev);
@@ -1464,7 +1473,7 @@ int corr_spectrogram_dev(corr_t h, const int8_t* d_samples, size_t n_samples, si
     CKRET(alloc_pipe(h, h->pd));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     CK(cudaMemsetAsync(d_tiles, 0, sizeof(float) * (size_t)h->n_in * rows * h->n_chan, st));
-    StreamView sv{d_samples, (long long)stride, 0, (long long)n_samples};
+    StreamView sv{static_cast<const int8_t*>(d_samples), (long long)stride, 0, (long long)n_samples, h->es};
     const long long s_total = rows * n_row;
     for (long long s0 = 0; s0 < s_total; s0 += h->pd.v_cap) {
         long long s1 = s0 + h->pd.v_cap;

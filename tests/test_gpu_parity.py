@@ -381,3 +381,61 @@ def test_leakage_of_the_gpu_filter_banks():
     assert out["kaiser8"]["adjacent"] < out["hann4"]["adjacent"] - 15.0
     assert out["hann4"]["beyond_2ch"] < -60.0 and out["kaiser8"]["beyond_2ch"] < -60.0
     assert abs(out["hann4"]["edge"] + 6.1) < 0.5 and abs(out["kaiser8"]["edge"] + 6.0) < 0.5
+
+
+# ---------------------------------------------------------------------------
+# 16-bit padded input (14-bit ADC values in int16, Sec. 3)
+# ---------------------------------------------------------------------------
+
+def _stream16(n_in, S, seed, tau=None, phi=None):
+    return make_stream(StreamSpec(n_ant=n_in, n_pol=1, n_samples=S, seed=seed, tau=tau, phi=phi, sigma=1000.0,
+                                  bits=14))
+
+
+@pytest.mark.parametrize("n_chan", [16, 256, 4096])
+def test_fengine_16bit_matches_oracle(n_chan):
+    M = 2 * n_chan
+    n_in, n_spec = 3, 9
+    S = M * n_spec + min(29, M - 1)
+    tau = np.array([0.0, 11.3, -5.6])
+    phi = np.array([0.2, -1.0, 2.0])
+    x = _stream16(n_in, S, seed=n_chan + 5, tau=tau, phi=phi)
+    assert x.dtype == np.int16 and np.abs(x).max() > 127
+    c = _corr(n_in, 1, n_chan, 4, 4, sample_bits=16)
+    c.set_delays(tau, phi)
+    Vg = _fengine(c, x, 0, n_spec)
+    Vo = fx.f_engine(x, n_chan, 4, tau, phi)
+    for a in range(n_in):
+        num = np.linalg.norm(Vg[:, :, a] - Vo[a], axis=1)
+        den = np.linalg.norm(Vo[a], axis=1)
+        assert np.all(num <= 1e-5 * den + 1e-6)
+
+
+def test_16bit_stream_run_push_and_widening():
+    n_chan, n_int, n_in = 256, 24, 4
+    M = 2 * n_chan
+    S = M * (n_int * 3 + 5) + 77
+    tau = np.array([0.0, 9.7, 33.2, -2.0])
+    phi = np.array([0.0, 0.5, -1.5, 2.5])
+    x = _stream16(n_in, S, seed=31, tau=tau, phi=phi)
+    c = _corr(n_in, 1, n_chan, 4, n_int, sample_bits=16)
+    c.set_delays(tau, phi)
+    R, F = _run_dev(c, x, True)
+    Ro, Fo, To = fx.correlate(x, n_chan, 4, n_int, tau, phi, partial=True)
+    assert _vis_err(R, Ro).max() < 1e-5
+    assert _flags_ok(F, Ro, Fo, To).all()
+    # host pushes in uneven pieces: bit-identical to the device run
+    c2 = _corr(n_in, 1, n_chan, 4, n_int, sample_bits=16, chunk=3000)
+    c2.set_delays(tau, phi)
+    _push_all(c2, x, [1000, 7, 33333, S - 34340])
+    c2.flush()
+    assert np.array_equal(c2.get_vis(), R)
+    # an int8 stream widened to int16 correlates bit-identically to the int8 path
+    x8 = _stream(n_in, S, seed=32, tau=tau, phi=phi)
+    c8 = _corr(n_in, 1, n_chan, 4, n_int)
+    c8.set_delays(tau, phi)
+    c16 = _corr(n_in, 1, n_chan, 4, n_int, sample_bits=16)
+    c16.set_delays(tau, phi)
+    R8, F8 = _run_dev(c8, x8, True)
+    R16, F16 = _run_dev(c16, x8.astype(np.int16), True)
+    assert np.array_equal(R8, R16) and np.array_equal(F8, F16)
