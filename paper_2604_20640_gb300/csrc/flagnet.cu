@@ -132,17 +132,6 @@ __global__ void input_bf16_kernel(const float* x, int P, uint16_t* X) {
     if (p < P) X[p] = f2bf(x[p]);
 }
 
-// z = D + b; hidden layers store BF16 ReLU(z), the last layer the logit.
-__global__ void fwd_epilogue_kernel(const float* D, int P, int Co, int Np, const float* b, bool last,
-                                    uint16_t* act, float* logit) {
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)P * Co) return;
-    const int p = (int)(idx / Co), o = (int)(idx % Co);
-    const float z = D[(size_t)p * Np + o] + b[o];
-    if (last) logit[p] = z;
-    else act[idx] = f2bf(fmaxf(z, 0.f));
-}
-
 // dz = (sigmoid(z) - t) / P_total as FP32 and BF16 (NHWC and transposed),
 // plus per-block partial sums of the loss softplus(z) - t z.
 __global__ void loss_grad_kernel(const float* z, const uint8_t* t, int P, float inv_total, float* dz32,
@@ -238,32 +227,117 @@ __global__ void pack_weights_kernel(const float* w, int C, int Co, int Kf, int K
     if (wd) wd[(size_t)c * Kd + uv * Co + o] = b;
 }
 
-// x = ln(P / median(P)) per tile; exact median (mean of the two middle
-// order statistics) by a bitonic sort of the tile in shared memory.
-__global__ void __launch_bounds__(1024) normalize_kernel(const float* power, float* x) {
-    extern __shared__ float sv[];
-    const float* P = power + (size_t)blockIdx.x * TPIX;
-    for (int i = threadIdx.x; i < TPIX; i += blockDim.x) sv[i] = P[i];
+// Layer 0 (1 -> 32 channels) on CUDA cores in FP32: one thread per pixel
+// takes its 5x5 neighbourhood of the FP32 input (zero outside the tile) and
+// forms all 32 outputs, then stores BF16 ReLU(z + b) NHWC (64 bytes).  With
+// one input channel the layer has 800 multiply-adds per pixel, too few to
+// feed the tensor cores through an im2col buffer.
+__global__ void __launch_bounds__(256) conv0_kernel(const float* x, int P, const float* w, const float* b,
+                                                    uint16_t* act) {
+    __shared__ float sw[32 * 25];
+    __shared__ float sb[32];
+    for (int i = threadIdx.x; i < 32 * 25; i += blockDim.x) sw[i] = w[i];
+    if (threadIdx.x < 32) sb[threadIdx.x] = b[threadIdx.x];
     __syncthreads();
-    for (int k = 2; k <= TPIX; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < TPIX; i += blockDim.x) {
-                const int l = i ^ j;
-                if (l > i) {
-                    const bool up = (i & k) == 0;
-                    const float a = sv[i], b = sv[l];
-                    if ((a > b) == up) {
-                        sv[i] = b;
-                        sv[l] = a;
-                    }
-                }
-            }
-            __syncthreads();
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int n = p / TPIX, ij = p % TPIX, i = ij / TW, j = ij % TW;
+    const float* xt = x + (size_t)n * TPIX;
+    float v[25];
+#pragma unroll
+    for (int u = 0; u < 5; ++u)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const int ii = i + u - 2, jj = j + q - 2;
+            v[5 * u + q] = (ii >= 0 && ii < TH && jj >= 0 && jj < TW) ? __ldg(xt + ii * TW + jj) : 0.f;
         }
+    uint32_t pk[16];
+#pragma unroll
+    for (int o = 0; o < 32; o += 2) {
+        float z0 = sb[o], z1 = sb[o + 1];
+#pragma unroll
+        for (int t = 0; t < 25; ++t) {
+            z0 = fmaf(sw[o * 25 + t], v[t], z0);
+            z1 = fmaf(sw[(o + 1) * 25 + t], v[t], z1);
+        }
+        const __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(z0, 0.f), fmaxf(z1, 0.f));
+        pk[o >> 1] = *reinterpret_cast<const uint32_t*>(&h);
     }
-    const float med = 0.5f * (sv[TPIX / 2 - 1] + sv[TPIX / 2]);
+    uint4* o4 = reinterpret_cast<uint4*>(act + (size_t)p * 32);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o4[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+}
+
+// Order-preserving 32-bit key of a float (larger float, larger key).
+__device__ __forceinline__ uint32_t fkey(float f) {
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+// x = ln(P / median(P)) per tile with the exact median (mean of the order
+// statistics of rank 8191 and 8192 of 16384) found by a radix select: four
+// passes of 8 bits over the order-preserving keys, each a 256-bin histogram
+// of the candidates sharing the prefix found so far.
+__global__ void __launch_bounds__(1024) median_normalize_kernel(const float* power, float* x) {
+    constexpr int PER = TPIX / 1024;          // 16 values per thread
+    __shared__ unsigned int hist[256];
+    __shared__ uint32_t s_prefix;
+    __shared__ int s_rank;
+    __shared__ uint32_t s_next;
+    const float* P = power + (size_t)blockIdx.x * TPIX;
+    uint32_t key[PER];
+#pragma unroll
+    for (int e = 0; e < PER; ++e) key[e] = fkey(P[threadIdx.x + e * 1024]);
+    if (threadIdx.x == 0) {
+        s_prefix = 0;
+        s_rank = TPIX / 2 - 1;
+        s_next = 0xFFFFFFFFu;
+    }
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 24 - 8 * pass;
+        if (threadIdx.x < 256) hist[threadIdx.x] = 0;
+        __syncthreads();
+        const uint32_t prefix = s_prefix;
+        const uint32_t pmask = pass == 0 ? 0u : (0xFFFFFFFFu << (shift + 8));
+#pragma unroll
+        for (int e = 0; e < PER; ++e)
+            if ((key[e] & pmask) == prefix) atomicAdd(&hist[(key[e] >> shift) & 0xFF], 1u);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int r = s_rank;
+            int d = 0;
+            while (r >= (int)hist[d]) {
+                r -= (int)hist[d];
+                ++d;
+            }
+            s_rank = r;
+            s_prefix = prefix | ((uint32_t)d << shift);
+        }
+        __syncthreads();
+    }
+    // s_prefix is the key of rank 8191; the rank-8192 value is the same key
+    // when it repeats beyond that rank, else the smallest larger key
+    const uint32_t k1 = s_prefix;
+    unsigned int cnt_le = 0;
+    uint32_t next = 0xFFFFFFFFu;
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {
+        if (key[e] <= k1) ++cnt_le;
+        else next = min(next, key[e]);
+    }
+    if (threadIdx.x == 0) hist[0] = 0;
+    __syncthreads();
+    atomicAdd(&hist[0], cnt_le);
+    atomicMin(&s_next, next);
+    __syncthreads();
+    const float v1 = fkey_inv(k1);
+    const float v2 = hist[0] > (unsigned)(TPIX / 2) ? v1 : fkey_inv(s_next);
+    const float med = 0.5f * (v1 + v2);
     const float inv = med > 0.f ? 1.f / med : 1.f;
-    for (int i = threadIdx.x; i < TPIX; i += blockDim.x)
+    for (int i = threadIdx.x; i < TPIX; i += 1024)
         x[(size_t)blockIdx.x * TPIX + i] = logf(fmaxf(P[i] * inv, 1e-30f));
 }
 
@@ -502,17 +576,18 @@ int conv(corr_flagnet_t net, const uint16_t* X, const uint16_t* W, int B, int bn
 }
 
 // Forward pass over B normalised tiles x [B][64][256] -> logits.  The
-// 1-channel first layer is an im2col product (K = 25 taps padded to 64);
-// the 32-channel layers are implicit-GEMM convolutions.
-int forward(corr_flagnet_t net, const float* x, int B, cudaStream_t st) {
+// 1-channel first layer runs on CUDA cores in FP32 (conv0_kernel); the
+// 32-channel layers are implicit-GEMM convolutions on the tensor cores.
+int forward(corr_flagnet_t net, const float* x, int B, cudaStream_t st, bool training) {
     const int P = B * TPIX;
-    net->launches += 4;
-    input_bf16_kernel<<<blocks(P), 256, 0, st>>>(x, P, net->act[0]);
-    im2col(net->act[0], 1, P, 1, net->A, st);
-    int rc = gemm(net, net->A, net->wf[0], P, 32, 64, 128, 128, 1, net->D, nullptr, st);
-    if (rc != CORR_OK) return rc;
-    fwd_epilogue_kernel<<<blocks((long long)P * 32), 256, 0, st>>>(net->D, P, 32, 32, net->b[0], false, net->act[1],
-                                                                   net->logit);
+    int rc = CORR_OK;
+    // the BF16 copy of the input is the weight-gradient operand of layer 0
+    if (training) {
+        input_bf16_kernel<<<blocks(P), 256, 0, st>>>(x, P, net->act[0]);
+        ++net->launches;
+    }
+    conv0_kernel<<<blocks(P), 256, 0, st>>>(x, P, net->w[0], net->b[0], net->act[1]);
+    ++net->launches;
     for (int l = 1; l < NL; ++l) {
         const bool last = l == NL - 1;
         rc = conv(net, net->act[l], net->wf[l], B, last ? 16 : 32, 1, last ? 1 : 0, net->b[l],
@@ -668,12 +743,7 @@ int corr_flagnet_get_params(corr_flagnet_t net, float* params, size_t n) {
 
 int corr_flagnet_prepare(corr_flagnet_t net, const float* d_power, int B, float* d_x, void* stream) {
     if (!net || !d_power || !d_x || B < 1) return ffail(net, CORR_EINVAL, "bad argument");
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(normalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TPIX * 4);
-        attr = true;
-    }
-    normalize_kernel<<<B, 1024, TPIX * 4, static_cast<cudaStream_t>(stream)>>>(d_power, d_x);
+    median_normalize_kernel<<<B, 1024, 0, static_cast<cudaStream_t>(stream)>>>(d_power, d_x);
     ++net->launches;
     FK(cudaGetLastError());
     return CORR_OK;
@@ -686,7 +756,7 @@ int corr_flagnet_forward(corr_flagnet_t net, const float* d_x, int B, float* d_l
     if (rc != CORR_OK) return rc;
     for (int t0 = 0; t0 < B; t0 += kChunk) {
         const int n = std::min(kChunk, B - t0);
-        rc = forward(net, d_x + (size_t)t0 * TPIX, n, st);
+        rc = forward(net, d_x + (size_t)t0 * TPIX, n, st, false);
         if (rc != CORR_OK) return rc;
         FK(cudaMemcpyAsync(d_logits + (size_t)t0 * TPIX, net->logit, (size_t)n * TPIX * 4, cudaMemcpyDeviceToDevice,
                            st));
@@ -701,7 +771,7 @@ int corr_flagnet_loss_grad(corr_flagnet_t net, const float* d_x, const uint8_t* 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = ensure_ws(net, B);
     if (rc != CORR_OK) return rc;
-    if ((rc = forward(net, d_x, B, st)) != CORR_OK) return rc;
+    if ((rc = forward(net, d_x, B, st, true)) != CORR_OK) return rc;
     if ((rc = backward(net, d_truth, B, st)) != CORR_OK) return rc;
     FK(cudaStreamSynchronize(st));
     if (loss) {
@@ -729,7 +799,7 @@ int corr_flagnet_train_step(corr_flagnet_t net, const float* d_x, const uint8_t*
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = ensure_ws(net, B);
     if (rc != CORR_OK) return rc;
-    if ((rc = forward(net, d_x, B, st)) != CORR_OK) return rc;
+    if ((rc = forward(net, d_x, B, st, true)) != CORR_OK) return rc;
     if ((rc = backward(net, d_truth, B, st)) != CORR_OK) return rc;
     ++net->steps;
     const float b1 = 0.9f, b2 = 0.999f;
@@ -763,7 +833,7 @@ int corr_flagnet_flag(corr_flagnet_t net, const float* d_power, int B, float c_m
         const int n = std::min(kChunk, B - t0);
         const float* pw = d_power + (size_t)t0 * TPIX;
         if ((rc = corr_flagnet_prepare(net, pw, n, net->norm, stream)) != CORR_OK) return rc;
-        if ((rc = forward(net, net->norm, n, st)) != CORR_OK) return rc;
+        if ((rc = forward(net, net->norm, n, st, false)) != CORR_OK) return rc;
         confidence_kernel<<<n, 256, 0, st>>>(net->logit, net->conf);
         net->launches += 2;
         const long long items = (long long)n * TH * (TW / 64);
