@@ -402,7 +402,8 @@ def run_flagger(args, rank, world, local):
     t_train = time.time() - t_train
     del src
     # --- the measured batch and its truth (held out)
-    corr = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"])
+    ring = {"ring_mb": args.ring_mb} if args.ring_mb else {}
+    corr = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"], **ring)
     one = Correlator(1, 1, W["n_chan"], W["taps"], W["n_int"])
     level = flagger.noise_level(one, noise_only(spec, S, dev), n_row)
     one.close()
@@ -544,6 +545,7 @@ def main():
                     help="0 FP32 CUDA-core X, 1 int8 / 2 e4m3 tensor-core X (default: FP32, int8 for c3)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--train-steps", type=int, default=C5_TRAIN_STEPS, help="c5: Adam steps before timing")
+    ap.add_argument("--ring-mb", type=int, default=0, help="c1-c3: spectrum ring size (MiB, 0 = library default)")
     ap.add_argument("--bits", type=int, default=8, choices=[8, 16],
                     help="c1-c3: 16 = the 16-bit padded recorder mode (the same stream scaled to 14-bit values)")
     args = ap.parse_args()
@@ -584,8 +586,13 @@ def main():
     if args.bits == 16:
         x = x.to(torch.int16) * 64          # 14-bit values in int16 containers
     prec = args.precision if args.precision is not None else (1 if args.workload == "c3" else 0)
+    ring = {"ring_mb": args.ring_mb} if args.ring_mb else {}
     c = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"], precision=prec,
-                   sample_bits=args.bits)
+                   sample_bits=args.bits, **ring)
+    if not args.ring_mb:
+        # ring size and FIR run length from the library's autotuner (untimed)
+        c.autotune(x)
+    tuning = c.tuning()
     c.set_delays(spec.tau, spec.phi)
     n_intg = c.n_integrations(S)
     vis = torch.empty((n_intg, W["n_chan"], n_in, n_in), dtype=torch.complex64, device=dev)
@@ -642,7 +649,7 @@ def main():
     e2e = None
     if not args.no_e2e:
         ce = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"], chunk=W["chunk"],
-                        precision=prec, sample_bits=args.bits)
+                        precision=prec, sample_bits=args.bits, ring_mb=tuning[0], fir_spt=tuning[1])
         ce.set_delays(spec.tau, spec.phi)
         host = torch.empty((n_in, S), dtype=x.dtype, pin_memory=True)
         host.copy_(x)
@@ -709,6 +716,7 @@ def main():
                        "path": ["plain FP32 (CUDA-core X)", "int8 requantised, tcgen05 X (BF16 MMA)",
                                 "e4m3 requantised, tcgen05 X"][prec],
                        "samples_per_input": S, "sample_bits": args.bits,
+                       "tuning": {"ring_mb": tuning[0], "fir_spt": tuning[1]},
                        "l2": "inputs (%d MiB/step) larger than L2" % (bytes_step >> 20),
                        "parallelism": "replicas" if world > 1 else "single"},
             "gpu_launches": launches, "clocks": clk, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,

@@ -96,7 +96,8 @@ const char* corr_last_error(corr_t h);
  *                 from the previous integration's autocorrelations.
  *   "result_slots" (default 8)               pinned result FIFO depth (grows)
  *   "stage_timing" (0/1, default 0; may change at any time)  per-stage events
- *   "ring_mb"      (1..4096, default 32)  MiB of each on-device spectrum ring
+ *   "ring_mb"      (1..4096, default 64)  MiB of each on-device spectrum ring
+ *                  (more spectra per launch; see corr_autotune)
  *   "fir_spt"      (0 = automatic, 1..256; may change at any time)
  *                  spectra each FIR thread filters
  *   "sample_bits"  (8, default; or 16)  input sample type of every call that
@@ -245,10 +246,10 @@ int corr_group_run_dev(corr_t group, const void* const* d_samples, const size_t*
                        const int* max_int, int* n_out, void* stream);
 
 /*
- * corr_autotune -- pick the ring capacity ("ring_mb" 16/32/64) and the FIR
- * run length ("fir_spt" auto/4/8/16) of a handle by timing corr_run_dev on
- * up to two integrations of a device sample (results do not depend on
- * either choice).  cache_path (may be NULL) is a text file of
+ * corr_autotune -- pick the ring capacity ("ring_mb" 32/64/128/256) and
+ * the FIR run length ("fir_spt" auto/8/16) of a handle by timing
+ * corr_run_dev on up to eight integrations of a device sample (results do
+ * not depend on either choice; larger rings mean larger launches).  cache_path (may be NULL) is a text file of
  * "gpu n_in n_chan taps n_int precision ring_mb fir_spt" lines: a matching
  * line is applied without timing, a new choice is appended.
  * corr_get_tuning reports the current values.

@@ -105,7 +105,7 @@ struct corr_s {
     long long chunk = 1LL << 23;
     int precision = CORR_FP32;
     int result_slots = 8;
-    int ring_mb = 32;            // tunable: ring capacity of Z and V (MiB each)
+    int ring_mb = 64;            // tunable: ring capacity of Z and V (MiB each)
     int fir_spt = 0;             // tunable: spectra per FIR thread (0 = automatic)
     int window = 0;              // PFB taper: 0 Hann, 1 Kaiser, 2 unit coefficients
     int es = 1;                  // bytes per input sample: 1 (int8) or 2 (int16, 16-bit padded mode)
@@ -1390,8 +1390,9 @@ int corr_autotune(corr_t h, const void* d_samples, size_t n_samples, size_t stri
         h->fir_spt = spt;
         return CORR_OK;
     }
-    // Time every candidate on (at most) two integrations of the sample.
-    size_t n_use = (size_t)h->M * (size_t)h->n_int * 2;
+    // Time every candidate on (at most) eight integrations of the sample:
+    // several fills of the largest ring.
+    size_t n_use = (size_t)h->M * (size_t)h->n_int * 8;
     if (n_use > n_samples) n_use = n_samples;
     const long long n_spec = (long long)(n_use / (size_t)h->M);
     const int n_out = (int)(n_spec / h->n_int) > 0 ? (int)(n_spec / h->n_int) : 1;
@@ -1403,8 +1404,8 @@ int corr_autotune(corr_t h, const void* d_samples, size_t n_samples, size_t stri
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    const int rings[] = {16, 32, 64};
-    const int spts[] = {0, 4, 8, 16};
+    const int rings[] = {32, 64, 128, 256};
+    const int spts[] = {0, 8, 16};
     float best = 1e30f;
     int best_ring = h->ring_mb, best_spt = h->fir_spt;
     int rc = CORR_OK;

@@ -86,7 +86,7 @@ def test_autotune_is_bit_identical_and_cached(tmp_path):
     cache = str(tmp_path / "tune.txt")
     c.autotune(xd, cache)
     ring, spt = c.tuning()
-    assert ring in (16, 32, 64) and spt in (0, 4, 8, 16)
+    assert ring in (32, 64, 128, 256) and spt in (0, 8, 16)
     assert os.path.exists(cache) and len(open(cache).read().strip().splitlines()) == 1
     vis.zero_()
     flags.zero_()
