@@ -50,7 +50,7 @@ WORKLOADS = {
                     "4096 ch, dynamic spectra of 256-spectrum rows in 64 x 256 tiles (512 tiles), learned "
                     "flagger (5x5 conv 1-32-32-32-1, BF16 tcgen05) with MAD fallback below confidence 0.9; "
                     "noise + tones / chirps 0-30 dB + bursts 0-8 dB"),
-    "c3": dict(n_ant=32, n_pol=2, n_chan=1024, taps=4, n_int=4096, samples=1 << 26, chunk=1 << 22,
+    "c3": dict(n_ant=32, n_pol=2, n_chan=1024, taps=4, n_int=4096, samples=1 << 26, chunk=1 << 24,
                desc="32 ant x 2 pol int8 real, 2^26 samples/input (4 GiB), 4-tap PFB, 1024 ch, n_int 4096, "
                     "requantised to int8 (tensor-core X, BF16 MMA) vs the plain FP32 path"),
 }
@@ -546,7 +546,8 @@ def main():
                     help="0 FP32 CUDA-core X, 1 int8 / 2 e4m3 tensor-core X (default: FP32, int8 for c3)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--train-steps", type=int, default=C5_TRAIN_STEPS, help="c5: Adam steps before timing")
-    ap.add_argument("--ring-mb", type=int, default=0, help="c1-c3: spectrum ring size (MiB, 0 = library default)")
+    ap.add_argument("--ring-mb", type=int, default=0, help="c1-c3: spectrum ring size (MiB, 0 = autotuned)")
+    ap.add_argument("--chunk", type=int, default=0, help="c1-c3 e2e: samples per input per push (0 = workload default)")
     ap.add_argument("--bits", type=int, default=8, choices=[8, 16],
                     help="c1-c3: 16 = the 16-bit padded recorder mode (the same stream scaled to 14-bit values)")
     args = ap.parse_args()
@@ -649,12 +650,12 @@ def main():
     # ---- end to end through the public host API ----
     e2e = None
     if not args.no_e2e:
-        ce = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"], chunk=W["chunk"],
+        ce = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"], chunk=args.chunk or W["chunk"],
                         precision=prec, sample_bits=args.bits, ring_mb=tuning[0], fir_spt=tuning[1])
         ce.set_delays(spec.tau, spec.phi)
         host = torch.empty((n_in, S), dtype=x.dtype, pin_memory=True)
         host.copy_(x)
-        chunk = W["chunk"]
+        chunk = args.chunk or W["chunk"]
 
         def e2e_step():
             for p in range(0, S, chunk):
