@@ -95,10 +95,12 @@ def make_rfi_batch(spec: RfiSpec, batch: int, device="cuda"):
                 ln = int(rng.integers(4, 65))
                 r0 = int(rng.integers(0, max(1, R - ln + 1)))
                 r1 = min(R, r0 + ln)
-            t = torch.arange(r0 * spr, r1 * spr, device=device, dtype=torch.float64)
-            cyc = torch.remainder(f * t, 1.0)
-            nb[r0 * spr:r1 * spr] += (_amp(spec.sigma, M, rng.uniform(*spec.nb_db)) *
-                                      torch.cos(2 * math.pi * cyc + rng.uniform(0, 2 * math.pi))).float()
+            # phase in exact 32-bit fixed point: (t f 2^32) mod 2^32, t < 2^27
+            fq = int(round(f * 2.0 ** 32)) & 0xFFFFFFFF
+            t = torch.arange(r0 * spr, r1 * spr, device=device, dtype=torch.int64)
+            ph = ((t * fq) & 0xFFFFFFFF).to(torch.float32) * (2 * math.pi / 2.0 ** 32)
+            nb[r0 * spr:r1 * spr] += _amp(spec.sigma, M, rng.uniform(*spec.nb_db)) * torch.cos(
+                ph + rng.uniform(0, 2 * math.pi))
         for _ in range(rng.poisson(spec.chirps_per_tile * n_tiles_per_input)):
             ln = int(rng.integers(16, 65))
             r0 = int(rng.integers(0, max(1, R - ln + 1)))
@@ -106,10 +108,20 @@ def make_rfi_batch(spec: RfiSpec, batch: int, device="cuda"):
             slope = rng.uniform(0.25, 4.0) * (1 if rng.random() < 0.5 else -1)    # channels per row
             f0 = (rng.uniform(0, spec.n_chan)) / M
             rate = slope / M / spr                                                # cycles / sample^2
-            t = torch.arange(0, (r1 - r0) * spr, device=device, dtype=torch.float64)
-            cyc = torch.remainder(f0 * t + 0.5 * rate * t * t, 1.0)
-            nb[r0 * spr:r1 * spr] += (_amp(spec.sigma, M, rng.uniform(*spec.nb_db)) *
-                                      torch.cos(2 * math.pi * cyc)).float()
+            # per block of 2^16 samples: start phase and local frequency in
+            # FP64, then the linear term in 32-bit fixed point and the small
+            # quadratic term (under one cycle per block) in FP32
+            n = (r1 - r0) * spr
+            blk = 1 << 16
+            t0 = torch.arange(0, n, blk, device=device, dtype=torch.float64)
+            ph0 = torch.remainder(f0 * t0 + 0.5 * rate * t0 * t0, 1.0)
+            fq = (torch.round(torch.remainder(f0 + rate * t0, 1.0) * 2.0 ** 32).to(torch.int64)) & 0xFFFFFFFF
+            tau = torch.arange(blk, device=device, dtype=torch.int64)
+            lin = ((fq[:, None] * tau[None, :]) & 0xFFFFFFFF).to(torch.float32) * (1.0 / 2.0 ** 32)
+            quad = (0.5 * rate) * tau.to(torch.float32) ** 2
+            cyc = ph0.to(torch.float32)[:, None] + lin + quad[None, :]
+            nb[r0 * spr:r1 * spr] += _amp(spec.sigma, M, rng.uniform(*spec.nb_db)) * torch.cos(
+                (2 * math.pi) * torch.remainder(cyc, 1.0)).reshape(-1)[:n]
         for _ in range(rng.poisson(spec.bursts_per_block * spec.row_blocks)):
             ln = int(rng.integers(1, 5))
             r0 = int(rng.integers(0, R - ln + 1))
