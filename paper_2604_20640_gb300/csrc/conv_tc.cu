@@ -280,6 +280,19 @@ int launch_bn(const ConvArgs& a, cudaStream_t st) {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, conv_kernel<BN>, kConvThreads, smem);
+        // the occupancy query can assume a smaller shared-memory carveout
+        // than the one requested; take the device's own limits as well
+        int smem_sm = 0, reserved = 0;
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+        cudaFuncAttributes fa{};
+        cudaFuncGetAttributes(&fa, conv_kernel<BN>);
+        int by_smem = smem_sm / (int)(smem + (size_t)reserved);
+        int by_regs = fa.numRegs > 0 ? 65536 / (fa.numRegs * kConvThreads) : 1;
+        int by_tmem = 512 / (int)(2 * BN < 32 ? 32 : 2 * BN);
+        int fit = by_smem < by_regs ? by_smem : by_regs;
+        if (by_tmem < fit) fit = by_tmem;
+        if (fit > resident) resident = fit;
         if (resident < 1) resident = 1;
         if (sms < 1) sms = 152;
     }
