@@ -158,7 +158,9 @@ int corr_reset(corr_t h);
  * (oldest first) into the caller's host buffer out
  * [max_int][n_chan][n_in][n_in] (vis: complex64 as float pairs; flags: uint8).
  * Visibilities and flags are popped independently, in the same order.
- * Blocks only until the oldest queued integration's copy has landed.
+ * Page-locked (pinned) out is filled by DMA straight from device memory;
+ * other host memory receives a copy of the library's pinned image.  Blocks
+ * only until the popped integrations' results have landed.
  * *n_got receives the count (0 and CORR_EAGAIN when none is queued).
  */
 int corr_get_vis(corr_t h, float* out, int max_int, int* n_got);

@@ -293,16 +293,46 @@ class Correlator:
         self._check(self._L.corr_pending(self._h, ctypes.byref(n)))
         return n.value
 
-    def get_vis(self, max_int: Optional[int] = None) -> np.ndarray:
+    def _result_out(self, out, max_int, np_t):
+        """Pointer and array view of a caller-provided result buffer
+        ``[>= max_int][n_chan][n_in][n_in]`` (numpy array or CPU tensor,
+        contiguous; a pinned tensor is filled by DMA)."""
+        shape = (self.n_chan, self.n_in, self.n_in)
+        if type(out).__module__.startswith("torch"):
+            import torch
+            torch_t = {np.complex64: torch.complex64, np.uint8: torch.uint8}[np_t]
+            if out.is_cuda or out.dtype != torch_t or tuple(out.shape[1:]) != shape or \
+                    not out.is_contiguous() or out.shape[0] < max_int:
+                raise CorrError(CORR_EINVAL, "out must be a contiguous CPU %s [>=%d]%s" % (torch_t, max_int, shape))
+            return out.data_ptr(), out
+        if not isinstance(out, np.ndarray) or out.dtype != np_t or out.shape[1:] != shape or \
+                not out.flags["C_CONTIGUOUS"] or out.shape[0] < max_int:
+            raise CorrError(CORR_EINVAL, "out must be a contiguous %s array [>=%d]%s" % (np.dtype(np_t).name, max_int, shape))
+        return out.ctypes.data, out
+
+    def get_vis(self, max_int: Optional[int] = None, out=None):
+        """Pop up to ``max_int`` (default: all pending) integrations' visibilities
+        ``[n][n_chan][n_in][n_in]`` complex64, into ``out`` when given (numpy
+        array or CPU tensor, returned sliced to the count)."""
         if max_int is None:
-            max_int = self.pending()
-        out = np.empty((max_int, self.n_chan, self.n_in, self.n_in), dtype=np.complex64)
+            max_int = self.pending() if out is None else min(self.pending(), out.shape[0])
+        if out is None:
+            out = np.empty((max_int, self.n_chan, self.n_in, self.n_in), dtype=np.complex64)
+        ptr, out = self._result_out(out, max_int, np.complex64)
         got = _i()
-        self._check(self._L.corr_get_vis(self._h, out.ctypes.data, max_int, ctypes.byref(got)),
+        self._check(self._L.corr_get_vis(self._h, ptr, max_int, ctypes.byref(got)),
                     allow=(CORR_OK, CORR_EAGAIN))
         return out[: got.value]
 
-    def get_flags(self, max_int: Optional[int] = None) -> np.ndarray:
+    def get_flags(self, max_int: Optional[int] = None, out=None):
+        """Pop up to ``max_int`` (default: all queued) integrations' flags
+        ``[n][n_chan][n_in][n_in]`` uint8, into ``out`` when given."""
+        if out is not None:
+            n = out.shape[0] if max_int is None else max_int
+            ptr, out = self._result_out(out, n, np.uint8)
+            got = _i()
+            self._check(self._L.corr_get_flags(self._h, ptr, n, ctypes.byref(got)), allow=(CORR_OK, CORR_EAGAIN))
+            return out[: got.value]
         if max_int is None:
             max_int = 1 << 20
             # flags FIFO may be longer than the vis FIFO; pop what is there

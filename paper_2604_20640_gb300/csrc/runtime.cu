@@ -130,8 +130,12 @@ struct corr_s {
     std::vector<double> tau_pend, phi_pend;  // waiting for an integration boundary
     bool pending = false;
     // streaming state
-    cudaStream_t s_comp = nullptr, s_copy = nullptr;
-    cudaEvent_t ev_h2d = nullptr, ev_comp = nullptr;
+    // s_comp runs the kernels, s_copy the input copies and s_out the result
+    // copies to the host: a result copy queued behind an input copy on a
+    // copy engine then holds up neither the kernels nor the next input.
+    // s_get carries copies into pinned buffers the caller pops into.
+    cudaStream_t s_comp = nullptr, s_copy = nullptr, s_out = nullptr, s_get = nullptr;
+    cudaEvent_t ev_h2d = nullptr, ev_comp = nullptr, ev_fin = nullptr;
     bool started = false, flushed = false, stream_alloc = false;
     // Host pushes land in two staging buffers used in turn: the next chunk is
     // copied (behind the history it needs) into the buffer the F-engine is
@@ -616,9 +620,13 @@ int sink_stream(corr_t h, void*, const Tables& t, long long, int count, int slot
     Slot& s = h->slots[idx];
     CKRET(finalize_into(h, h->ps, t, s.d_R, s.d_F, count, slots, st));
     const size_t ne = vis_elems(h);
-    CK(cudaMemcpyAsync(s.h_R, s.d_R, ne * sizeof(float2), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(s.h_F, s.d_F, ne, cudaMemcpyDeviceToHost, st));
-    CK(cudaEventRecord(s.ev, st));
+    // The slot is rewritten only after the host has taken its results
+    // (pop_results waits on s.ev), so the copies may trail the kernels.
+    CK(cudaEventRecord(h->ev_fin, st));
+    CK(cudaStreamWaitEvent(h->s_out, h->ev_fin, 0));
+    CK(cudaMemcpyAsync(s.h_R, s.d_R, ne * sizeof(float2), cudaMemcpyDeviceToHost, h->s_out));
+    CK(cudaMemcpyAsync(s.h_F, s.d_F, ne, cudaMemcpyDeviceToHost, h->s_out));
+    CK(cudaEventRecord(s.ev, h->s_out));
     s.in_vis = s.in_flag = true;
     h->q_vis.push_back(idx);
     h->q_flag.push_back(idx);
@@ -758,22 +766,49 @@ int pop_results(corr_t h, std::deque<int>& q, bool vis, void* out, int max_int, 
     if (n_got) *n_got = 0;
     if (max_int < 0) return fail(h, CORR_EINVAL, "max_int < 0");
     if (max_int > 0 && !out) return fail(h, CORR_EINVAL, "out is NULL");
-    int got = 0;
+    // A pinned destination takes the results straight from the device slots
+    // by DMA (on s_get, behind each slot's own event only); any other host
+    // memory gets a copy of the slot's pinned image.
+    bool pinned = false;
+    if (max_int > 0 && !q.empty()) {
+        cudaPointerAttributes attr;
+        pinned = cudaPointerGetAttributes(&attr, out) == cudaSuccess && attr.type == cudaMemoryTypeHost;
+        cudaGetLastError();
+    }
     const size_t ne = vis_elems(h);
+    const size_t bytes = vis ? ne * sizeof(float2) : ne;
+    int got = 0;
+    std::vector<int> taken;
+    int rc = CORR_OK;
     while (got < max_int && !q.empty()) {
         const int idx = q.front();
         Slot& s = h->slots[idx];
-        CK(cudaEventSynchronize(s.ev));
-        if (vis) {
-            std::memcpy(static_cast<float2*>(out) + (size_t)got * ne, s.h_R, ne * sizeof(float2));
-            s.in_vis = false;
+        char* dst = static_cast<char*>(out) + (size_t)got * bytes;
+        cudaError_t e;
+        if (pinned) {
+            e = cudaStreamWaitEvent(h->s_get, s.ev, 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(dst, vis ? static_cast<const void*>(s.d_R) : static_cast<const void*>(s.d_F),
+                                    bytes, cudaMemcpyDeviceToHost, h->s_get);
         } else {
-            std::memcpy(static_cast<uint8_t*>(out) + (size_t)got * ne, s.h_F, ne);
-            s.in_flag = false;
+            e = cudaEventSynchronize(s.ev);
+            if (e == cudaSuccess)
+                std::memcpy(dst, vis ? static_cast<const void*>(s.h_R) : static_cast<const void*>(s.h_F), bytes);
         }
+        if (e != cudaSuccess) {
+            rc = fail(h, CORR_ECUDA, std::string("result copy: ") + cudaGetErrorString(e));
+            break;
+        }
+        taken.push_back(idx);
         q.pop_front();
         ++got;
     }
+    if (pinned && !taken.empty()) {
+        const cudaError_t e = cudaStreamSynchronize(h->s_get);
+        if (e != cudaSuccess && rc == CORR_OK) rc = fail(h, CORR_ECUDA, std::string("result copy: ") + cudaGetErrorString(e));
+    }
+    for (int idx : taken) (vis ? h->slots[idx].in_vis : h->slots[idx].in_flag) = false;
+    if (rc != CORR_OK) return rc;
     if (n_got) *n_got = got;
     return got == 0 && max_int > 0 ? CORR_EAGAIN : CORR_OK;
 }
@@ -830,8 +865,11 @@ int corr_create(corr_t* out, int n_ant, int n_pol, int n_chan, int taps, int n_i
     const std::vector<float2> tw = corr::fft_twiddle_table(h->M);
     if (cudaStreamCreateWithFlags(&h->s_comp, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&h->s_copy, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->s_get, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_h2d, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_comp, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&h->ev_comp, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fin, cudaEventDisableTiming) != cudaSuccess)
         return bail(CORR_ECUDA, "stream/event creation failed");
     if (cudaMalloc(&h->d_h, hf.size() * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&h->d_tw, tw.size() * sizeof(float2)) != cudaSuccess)
@@ -874,6 +912,7 @@ int corr_destroy(corr_t h) {
     }
     if (h->s_comp) cudaStreamSynchronize(h->s_comp);
     if (h->s_copy) cudaStreamSynchronize(h->s_copy);
+    if (h->s_out) cudaStreamSynchronize(h->s_out);
     for (Slot& s : h->slots) {
         cudaFree(s.d_R);
         cudaFree(s.d_F);
@@ -907,8 +946,11 @@ int corr_destroy(corr_t h) {
     if (h->h_pin) cudaFreeHost(h->h_pin);
     if (h->ev_h2d) cudaEventDestroy(h->ev_h2d);
     if (h->ev_comp) cudaEventDestroy(h->ev_comp);
+    if (h->ev_fin) cudaEventDestroy(h->ev_fin);
     if (h->s_comp) cudaStreamDestroy(h->s_comp);
     if (h->s_copy) cudaStreamDestroy(h->s_copy);
+    if (h->s_out) cudaStreamDestroy(h->s_out);
+    if (h->s_get) cudaStreamDestroy(h->s_get);
     cudaGetLastError();
     delete h;
     return CORR_OK;
@@ -1029,6 +1071,7 @@ int corr_reset(corr_t h) {
     DeviceGuard g(h->dev);
     if (h->s_comp) CK(cudaStreamSynchronize(h->s_comp));
     if (h->s_copy) CK(cudaStreamSynchronize(h->s_copy));
+    if (h->s_out) CK(cudaStreamSynchronize(h->s_out));
     h->started = h->flushed = false;
     h->stage_base = h->stage_len = 0;
     h->cur_buf = 0;

@@ -318,6 +318,40 @@ def test_push_dev_matches_push():
     assert np.array_equal(c1.get_vis(), c2.get_vis())
 
 
+def test_results_popped_into_pinned_and_pageable_buffers_agree():
+    n_chan, n_int, n_in = 256, 8, 4
+    M = 2 * n_chan
+    S = M * n_int * 5 + 300
+    x = _stream(n_in, S, seed=23)
+    ref = _corr(n_in, 1, n_chan, 4, n_int)
+    ref.push(x)
+    ref.flush()
+    Rv, Rf = ref.get_vis(), ref.get_flags()
+    assert Rv.shape[0] == 5
+    c = _corr(n_in, 1, n_chan, 4, n_int)
+    c.push(x)
+    c.flush()
+    shape = (6, n_chan, n_in, n_in)
+    pv = torch.full(shape, 7 + 7j, dtype=torch.complex64).pin_memory()
+    pf = torch.full(shape, 9, dtype=torch.uint8).pin_memory()
+    v1 = c.get_vis(max_int=2, out=pv)                 # pinned: DMA from the device slots
+    f1 = c.get_flags(max_int=3, out=np.zeros(shape, np.uint8))   # pageable
+    assert v1.shape[0] == 2 and f1.shape[0] == 3
+    assert np.array_equal(v1.numpy(), Rv[:2]) and np.array_equal(f1, Rf[:3])
+    assert (pv[2:].numpy() == 7 + 7j).all()           # nothing written past the count
+    v2 = c.get_vis(out=np.zeros(shape, np.complex64))
+    f2 = c.get_flags(out=pf)
+    assert np.array_equal(v2, Rv[2:]) and np.array_equal(f2.numpy(), Rf[3:])
+    assert (pf[2:].numpy() == 9).all()
+    assert c.get_vis(out=pv).shape[0] == 0 and c.get_flags(out=pf).shape[0] == 0
+    from paper_2604_20640_gb300 import CorrError
+    for bad in (torch.zeros(shape, dtype=torch.complex64, device=DEV),       # device tensor
+                np.zeros((6, n_chan, n_in, n_in + 1), np.complex64),         # wrong shape
+                np.zeros(shape, np.complex128)):                              # wrong type
+        with pytest.raises(CorrError):
+            c.get_vis(max_int=1, out=bad)
+
+
 @pytest.mark.parametrize("window,wname,taps", [(1, "kaiser", 8), (1, "kaiser", 4), (2, "none", 1), (0, "hann", 8)])
 def test_fengine_window_options_match_oracle(window, wname, taps):
     n_chan, n_in = 512, 3
