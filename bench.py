@@ -664,8 +664,12 @@ def main():
     # ---- end to end through the public host API ----
     e2e = None
     if not args.no_e2e:
+        # The host issues every launch of the push path, once per ring pass,
+        # so it takes a ring of at least 128 MiB whatever the device-resident
+        # tuning chose (small rings make the pushes launch-bound).
+        ring_e2e = args.ring_mb or max(tuning[0], 128)
         ce = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"], chunk=args.chunk or W["chunk"],
-                        precision=prec, sample_bits=args.bits, ring_mb=tuning[0], fir_spt=tuning[1])
+                        precision=prec, sample_bits=args.bits, ring_mb=ring_e2e, fir_spt=tuning[1])
         ce.set_delays(spec.tau, spec.phi)
         host = torch.empty((n_in, S), dtype=x.dtype, pin_memory=True)
         host.copy_(x)
@@ -694,7 +698,7 @@ def main():
         barrier()
         ems = (t1 - t0) * 1e3 / args.steps
         ems = max_over_ranks(ems, dist if world > 1 else None, dev)
-        e2e = {"value": job_rate(bytes_step, world, ems), "unit": "GB/s",
+        e2e = {"value": job_rate(bytes_step, world, ems), "unit": "GB/s", "ring_mb": ring_e2e,
                "h2d_bytes_per_step": bytes_step,
                "d2h_bytes_per_step": int(v.numel() * v.element_size() + f.numel() * f.element_size()),
                "ms_per_step": ems}

@@ -476,6 +476,8 @@ template <int M>
 struct FftCfg {
     static constexpr int NACT = M / 16;
     static constexpr int THREADS = NACT < 32 ? 32 : NACT;
+    // CTAs per SM the register budget is held to (128 registers a thread).
+    static constexpr int MINB = THREADS >= 512 ? 1 : 65536 / 128 / THREADS;
     // With at most 512 threads the last pass's 15 twiddles (fixed per thread)
     // stay in registers and the next spectrum's first-pass input is
     // prefetched; one CTA per SM then has up to 128 registers per thread.
@@ -492,7 +494,7 @@ __device__ __forceinline__ const float2* fft_input(const FftArgs& A, long long s
 
 // MODE 0: store U = 2Y; 1: store the rotated V; 2: accumulate power tiles.
 template <int M, int MODE>
-__global__ void __launch_bounds__(FftCfg<M>::THREADS, 1) fft_kernel(const FftArgs A) {
+__global__ void __launch_bounds__(FftCfg<M>::THREADS, FftCfg<M>::MINB) fft_kernel(const FftArgs A) {
     using C = FftCfg<M>;
     extern __shared__ float2 smem[];
     float2* zbuf = smem;
@@ -636,10 +638,12 @@ static void launch_fft_m(const FftArgs& a, cudaStream_t st) {
         if (resident < 1) resident = 1;
         if (sms < 1) sms = 152;
     }
-    // One wave of resident CTAs, each looping over a run of spectra of one pair.
+    // One wave of resident CTAs, each looping over a run of spectra of one
+    // pair: runs x pairs never exceeds the resident slots (rounding up would
+    // leave a few CTAs for a second, nearly empty wave as long as the first).
     const long long n = a.s_end - a.s_begin;
     const int n_pairs = a.n_in_pad / 2;
-    long long runs = ((long long)sms * resident + n_pairs - 1) / n_pairs;
+    long long runs = (long long)sms * resident / n_pairs;
     if (runs > n) runs = n;
     if (runs < 1) runs = 1;
     FftArgs b = a;
