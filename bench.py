@@ -63,7 +63,7 @@ WORKLOADS = {
 #   requant reads the spectra (4 B) and writes one code per component (1 B
 #   e4m3, 2 B int8-as-BF16); the tensor-core Gram reads the codes.
 STAGES = ["fir", "fft", "xengine", "finalize", "flag", "requant", "gram"]
-KERNELS = {"fir": "fir_kernel<4>", "fft": "fft_kernel<M,false>", "xengine": "xengine_kernel",
+KERNELS = {"fir": "fir_kernel<4>", "fft": "fft_kernel<M,0>", "xengine": "xengine_kernel",
            "finalize": "finalize_kernel", "flag": "mad_flag_kernel", "requant": "requant_kernel",
            "gram": "gram_kernel (tcgen05)"}
 BYTES_PER_SAMPLE = {"fir": 5.0, "fft": 8.0, "xengine": 4.0, "finalize": 0.0, "flag": 0.0, "requant": 6.0,
@@ -403,8 +403,10 @@ def run_flagger(args, rank, world, local):
     t_train = time.time() - t_train
     del src
     # --- the measured batch and its truth (held out)
-    ring = {"ring_mb": args.ring_mb} if args.ring_mb else {}
-    corr = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"], **ring)
+    # 512 MiB rings: 256-spectrum launches (the dynamic spectra take 12.1 ms
+    # per 4 GiB batch against 15.1 ms with the 64 MiB default's 32-spectrum
+    # launches; no spectra ring is written in this mode)
+    corr = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"], ring_mb=args.ring_mb or 512)
     one = Correlator(1, 1, W["n_chan"], W["taps"], W["n_int"])
     level = flagger.noise_level(one, noise_only(spec, S, dev), n_row)
     one.close()
@@ -423,21 +425,42 @@ def run_flagger(args, rank, world, local):
     conf = torch.empty(B, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step():
+    fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(max(args.steps, 1))]
+
+    def step(i=None):
         flagger.power_tiles(corr, x, n_row, out=power)
+        if i is not None:
+            fev[i][0].record(stream)
         net.flag(power, flags, conf, c_min=C5_C_MIN)
+        if i is not None:
+            fev[i][1].record(stream)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
+    # --- stage shares from one untimed step with every F-engine stage
+    # bracketed; the timed steps bracket only the dominant kernel's launches
+    corr.set_option("stage_timing", 1)
+    corr.stage_times()
+    step(0)
+    torch.cuda.synchronize(dev)
+    share_ms, _ = corr.stage_times()
+    share = {k: share_ms[i] for i, k in enumerate(STAGES) if share_ms[i] > 0}
+    share["flagger"] = fev[0][0].elapsed_time(fev[0][1])
+    tot = sum(share.values()) or 1.0
+    share = {k: v / tot for k, v in share.items()}
+    dom = max((k for k in ("fir", "fft")), key=lambda k: share.get(k, 0.0))
+    di = STAGES.index(dom)
+    corr.set_option("stage_mask", 1 << di)
     if world > 1:
         dist.barrier()
     clocks = ClockSampler(local)
     l0 = corr.launches + net.launches
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
-        step()
+    for i in range(args.steps):
+        step(i)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
@@ -446,29 +469,15 @@ def run_flagger(args, rank, world, local):
     ms = max_over_ranks(ms, dist if world > 1 else None, dev)
     bytes_step = spec.n_in * S
     value = job_rate(bytes_step, world, ms)
-    # --- per-stage split (one more instrumented pass, not in the timed region)
-    corr.set_option("stage_timing", 1)
-    corr.stage_times()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    flagger.power_tiles(corr, x, n_row, out=power)
-    f0.record(stream)
-    net.flag(power, flags, conf, c_min=C5_C_MIN)
-    f1.record(stream)
-    torch.cuda.synchronize(dev)
     stage_ms, stage_n = corr.stage_times()
     corr.set_option("stage_timing", 0)
-    flag_ms = f0.elapsed_time(f1)
+    corr.set_option("stage_mask", 127)
+    flag_ms = sum(a.elapsed_time(b) for a, b in fev[:args.steps]) / max(1, args.steps)
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs") or 6800.0
     bf16 = peaks.get("bf16_tflops") or 1900.0
-    share = {k: stage_ms[i] for i, k in enumerate(STAGES) if stage_ms[i] > 0}
-    share["flagger"] = flag_ms
-    tot = sum(share.values()) or 1.0
-    share = {k: v / tot for k, v in share.items()}
     flops_tile = 2.0 * 64 * 256 * 25 * (1 * 32 + 32 * 32 + 32 * 32 + 32 * 1)
-    dom = max((k for k in ("fir", "fft")), key=lambda k: share.get(k, 0.0))
-    di = STAGES.index(dom)
-    n_samples_pass = bytes_step
+    n_samples_pass = bytes_step * args.steps
     # in the flagging pass the FFT reads z (4 B/sample) and keeps only the
     # powers (no spectra written)
     bps_c5 = {"fir": 5.0, "fft": 4.0}
@@ -536,6 +545,7 @@ def run_flagger(args, rank, world, local):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
             "config": {"workload": "c5: " + W["desc"], "samples_per_input": S, "tiles": B,
+                       "ring_mb": args.ring_mb or 512,
                        "l2": "inputs (%d MiB/step) larger than L2" % (bytes_step >> 20),
                        "parallelism": "replicas" if world > 1 else "single"},
             "gpu_launches": int(launches), "clocks": clk, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
@@ -618,8 +628,23 @@ def main():
     for _ in range(args.warmup):
         c.run_dev(x, vis, flags)
     torch.cuda.synchronize(dev)
+    # One untimed step with every stage bracketed by events gives the stage
+    # shares and the dominant kernel; the timed steps bracket only that
+    # kernel's launches (fewer events disturb the pipeline less).
+    bps = dict(BYTES_PER_SAMPLE)
+    if args.bits == 16:
+        bps["fir"] += 1.0          # the FIR reads 2 bytes per sample
+    if prec == 2:
+        bps.update(requant=5.0, gram=1.0)
     c.set_option("stage_timing", 1)
     c.stage_times()
+    c.run_dev(x, vis, flags)
+    share_ms, _ = c.stage_times()
+    total_stage = sum(share_ms) or 1.0
+    share = {k: share_ms[i] / total_stage for i, k in enumerate(STAGES)}
+    dom = max((k for k in STAGES if bps[k] > 0), key=lambda k: share[k])
+    di = STAGES.index(dom)
+    c.set_option("stage_mask", 1 << di)
     barrier()
     torch.cuda.synchronize(dev)
     clocks = ClockSampler(local)
@@ -636,6 +661,7 @@ def main():
     ms = e0.elapsed_time(e1) / args.steps
     stage_ms, stage_n = c.stage_times()
     c.set_option("stage_timing", 0)
+    c.set_option("stage_mask", 127)
     ms = max_over_ranks(ms, dist if world > 1 else None, dev)
     bytes_step = n_in * S * (args.bits // 8)
     value = job_rate(bytes_step, world, ms)
@@ -710,15 +736,6 @@ def main():
     hbm = peaks.get("hbm_gbs")
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
-    total_stage = sum(stage_ms) or 1.0
-    share = {k: stage_ms[i] / total_stage for i, k in enumerate(STAGES)}
-    bps = dict(BYTES_PER_SAMPLE)
-    if args.bits == 16:
-        bps["fir"] += 1.0          # the FIR reads 2 bytes per sample
-    if prec == 2:
-        bps.update(requant=5.0, gram=1.0)
-    dom = max((k for k in STAGES if bps[k] > 0), key=lambda k: share[k])
-    di = STAGES.index(dom)
     n_spec = S // (2 * W["n_chan"])
     samples_timed = args.steps * n_spec * 2 * W["n_chan"] * n_in
     bytes_per_launch = bps[dom] * samples_timed / max(1, stage_n[di])

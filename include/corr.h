@@ -96,6 +96,10 @@ const char* corr_last_error(corr_t h);
  *                 from the previous integration's autocorrelations.
  *   "result_slots" (default 8)               pinned result FIFO depth (grows)
  *   "stage_timing" (0/1, default 0; may change at any time)  per-stage events
+ *   "stage_mask"   (bit mask, default 127 = all; may change at any time)
+ *                  stages (numbered as in corr_stage_times) that
+ *                  stage_timing brackets; fewer events disturb the
+ *                  pipeline less
  *   "ring_mb"      (1..4096, default 64)  MiB of each on-device spectrum ring
  *                  (more spectra per launch; see corr_autotune)
  *   "fir_spt"      (0 = automatic, 1..256; may change at any time)

@@ -61,6 +61,7 @@ struct Tables {
 constexpr int kStages = 7;
 struct StageTimer {
     bool on = false;
+    int mask = (1 << kStages) - 1;   // stages bracketed while on
     std::vector<cudaEvent_t> pool;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> open[kStages];
     double ms[kStages] = {};
@@ -191,7 +192,7 @@ struct Timed {
     cudaStream_t st;
     cudaEvent_t e0 = nullptr;
     Timed(corr_t h_, int stage_, cudaStream_t st_) : h(h_), stage(stage_), st(st_) {
-        if (h->timer.on) {
+        if (h->timer.on && ((h->timer.mask >> stage) & 1)) {
             e0 = h->timer.take();
             cudaEventRecord(e0, st);
         }
@@ -964,7 +965,7 @@ const char* corr_last_error(corr_t h) {
 int corr_set_option(corr_t h, const char* key, double v) {
     if (!h || !key) return fail(h, CORR_EINVAL, "NULL argument");
     const std::string k(key);
-    if (h->started && k != "stage_timing" && k != "fir_spt")
+    if (h->started && k != "stage_timing" && k != "stage_mask" && k != "fir_spt")
         return fail(h, CORR_ESTATE, "options must be set before the first push");
     if (k == "flag_sigma") {
         if (!(v > 0)) return fail(h, CORR_EINVAL, "flag_sigma must be > 0");
@@ -996,6 +997,11 @@ int corr_set_option(corr_t h, const char* key, double v) {
         return CORR_OK;
     } else if (k == "stage_timing") {
         h->timer.on = v != 0;
+        return CORR_OK;
+    } else if (k == "stage_mask") {
+        if (v < 0 || v >= (double)(1 << kStages) || v != (double)(long long)v)
+            return fail(h, CORR_EINVAL, "stage_mask: bit mask of stages 0..6");
+        h->timer.mask = (int)v;
         return CORR_OK;
     } else if (k == "sample_bits") {
         if (v != 8 && v != 16) return fail(h, CORR_EINVAL, "sample_bits: 8 or 16");

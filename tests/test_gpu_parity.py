@@ -352,6 +352,33 @@ def test_results_popped_into_pinned_and_pageable_buffers_agree():
             c.get_vis(max_int=1, out=bad)
 
 
+def test_stage_times_and_stage_mask():
+    n_chan, n_int, n_in = 256, 8, 4
+    M = 2 * n_chan
+    S = M * n_int * 4
+    xd = torch.from_numpy(_stream(n_in, S, seed=5)).to(DEV)
+    c = _corr(n_in, 1, n_chan, 4, n_int)
+    vis = torch.empty((4, n_chan, n_in, n_in), dtype=torch.complex64, device=DEV)
+    flags = torch.empty((4, n_chan, n_in, n_in), dtype=torch.uint8, device=DEV)
+    c.set_option("stage_timing", 1)
+    c.stage_times()
+    c.run_dev(xd, vis, flags)
+    ms, n = c.stage_times()
+    assert all(n[i] > 0 and ms[i] > 0 for i in range(5)) and n[5] == n[6] == 0
+    c.set_option("stage_mask", 1 << 1)                # the FFT alone
+    c.run_dev(xd, vis, flags)
+    ms2, n2 = c.stage_times()
+    assert n2[1] == n[1] and ms2[1] > 0
+    assert all(n2[i] == 0 and ms2[i] == 0 for i in (0, 2, 3, 4, 5, 6))
+    c.set_option("stage_timing", 0)
+    c.run_dev(xd, vis, flags)
+    assert sum(c.stage_times()[1]) == 0
+    from paper_2604_20640_gb300 import CorrError
+    for bad in (-1, 128, 2.5):
+        with pytest.raises(CorrError):
+            c.set_option("stage_mask", bad)
+
+
 @pytest.mark.parametrize("window,wname,taps", [(1, "kaiser", 8), (1, "kaiser", 4), (2, "none", 1), (0, "hann", 8)])
 def test_fengine_window_options_match_oracle(window, wname, taps):
     n_chan, n_in = 512, 3
