@@ -704,19 +704,26 @@ def main():
         vis_h = torch.empty((n_intg + 1, W["n_chan"], n_in, n_in), dtype=torch.complex64, pin_memory=True)
         flags_h = torch.empty((n_intg + 1, W["n_chan"], n_in, n_in), dtype=torch.uint8, pin_memory=True)
 
+        phase = [0.0, 0.0]          # host seconds in the pushes / in flush + pops
+
         def e2e_step():
+            ta = time.perf_counter()
             for p in range(0, S, chunk):
                 ce.push(host[:, p:p + chunk])
+            tb = time.perf_counter()
             ce.flush()
             v = ce.get_vis(out=vis_h)
             f = ce.get_flags(out=flags_h)
             assert v.shape[0] == f.shape[0] >= n_intg
             ce.reset()
+            phase[0] += tb - ta
+            phase[1] += time.perf_counter() - tb
             return v, f
 
         for _ in range(max(1, args.warmup)):
             e2e_step()
         barrier()
+        phase[:] = [0.0, 0.0]
         t0 = time.perf_counter()
         for _ in range(args.steps):
             v, f = e2e_step()
@@ -727,7 +734,8 @@ def main():
         e2e = {"value": job_rate(bytes_step, world, ems), "unit": "GB/s", "ring_mb": ring_e2e,
                "h2d_bytes_per_step": bytes_step,
                "d2h_bytes_per_step": int(v.numel() * v.element_size() + f.numel() * f.element_size()),
-               "ms_per_step": ems}
+               "ms_per_step": ems, "push_ms": phase[0] * 1e3 / args.steps,
+               "flush_pop_ms": phase[1] * 1e3 / args.steps}
         ce.close()
         del host
 
