@@ -178,6 +178,35 @@ def cpu_baseline(wl, n_integrations=None):
                       % (samples // M, d["bytes"] >> 20, d["seconds"])}
 
 
+def c4_cpu_baseline():
+    """The FP64 oracle, as it stands, on the first 64 spectra of every
+    sub-array stream of the batching workload (one thread), per input byte."""
+    code = (
+        "import sys, time, json\n"
+        "sys.path.insert(0, %r)\n"
+        "from fxsynth import config_c4_streams, make_stream\n"
+        "from fxsynth.streams import C4_SHAPES\n"
+        "from oracle import fx_oracle as fx\n"
+        "secs, nbytes = 0.0, 0\n"
+        "for spec, (na, nc, ni) in zip(config_c4_streams(seed=4000, n_samples=64 * 2 * 8192), C4_SHAPES):\n"
+        "    spec.n_samples = 64 * 2 * nc\n"
+        "    x = make_stream(spec)\n"
+        "    t0 = time.perf_counter()\n"
+        "    fx.correlate(x, nc, 4, ni, spec.tau, spec.phi, partial=True)\n"
+        "    secs += time.perf_counter() - t0\n"
+        "    nbytes += int(x.size)\n"
+        "print(json.dumps({'seconds': secs, 'bytes': nbytes}))\n"
+    ) % (ROOT,)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else "failed"}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["bytes"] / d["seconds"] / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "first 64 spectra of each of the 8 sub-array streams (%d MiB int8), FP64 numpy "
+                      "oracle, 1 thread, %.1f s" % (d["bytes"] >> 20, d["seconds"])}
+
+
 def run_reference_c5(args):
     W = WORKLOADS["c5"]
     secs = []
@@ -271,10 +300,11 @@ def run_batched(args, rank, world, local):
     S = args.samples or WORKLOADS["c4"]["samples"]
     specs = config_c4_streams(seed=rank_seed(4000, rank), n_samples=S)
     from fxsynth.streams import C4_SHAPES
-    members, plains, xs, vis, flags = [], [], [], [], []
+    members, plains, xs, vis, flags, precs = [], [], [], [], [], []
     for spec, (na, nc, ni) in zip(specs, C4_SHAPES):
         # chosen form: tensor-core X-engine (int8 codes) once N is large
         prec = 1 if 2 * na >= TENSOR_MIN_INPUTS else 0
+        precs.append(prec)
         c = Correlator(na, 2, nc, 4, ni, precision=prec)
         c.set_delays(spec.tau, spec.phi)
         cp = Correlator(na, 2, nc, 4, ni)
@@ -323,6 +353,72 @@ def run_batched(args, rank, world, local):
     launches = (g._L.corr_kernel_launches(g._h) - l0) * args.steps // (args.steps + args.warmup)
     clk = clocks.stop()
     value = job_rate(bytes_step, world, ms)
+
+    # --- roofline: a captured graph carries no per-kernel events, so the
+    # members run once more one by one (untimed) with every stage bracketed
+    st_ms, st_n, st_bytes = [0.0] * len(STAGES), [0] * len(STAGES), [0.0] * len(STAGES)
+    for c, x, v, f, prec in zip(members, xs, vis, flags, precs):
+        bps = dict(BYTES_PER_SAMPLE)
+        if prec == 2:
+            bps.update(requant=5.0, gram=1.0)
+        c.set_option("stage_timing", 1)
+        c.stage_times()
+        c.run_dev(x, v, f)
+        m_ms, m_n = c.stage_times()
+        c.set_option("stage_timing", 0)
+        n_used = (x.shape[1] // c.M) * c.M * c.n_in
+        for i, k in enumerate(STAGES):
+            st_ms[i] += m_ms[i]
+            st_n[i] += m_n[i]
+            st_bytes[i] += bps[k] * n_used if m_n[i] else 0.0
+    tot = sum(st_ms) or 1.0
+    share = {k: st_ms[i] / tot for i, k in enumerate(STAGES)}
+    di = max((i for i, k in enumerate(STAGES) if BYTES_PER_SAMPLE[k] > 0), key=lambda i: st_ms[i])
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    avg_ms = st_ms[di] / max(1, st_n[di])
+    bpl = st_bytes[di] / max(1, st_n[di])
+    roofline = {"kernel": KERNELS[STAGES[di]], "bound": "hbm", "achieved": bpl / (avg_ms * 1e-3) / 1e9,
+                "peak": hbm, "unit": "GB/s", "frac": bpl / (avg_ms * 1e-3) / 1e9 / hbm, "traffic": None,
+                "peak_source": "measured" if peaks else "fallback", "bytes_per_launch": bpl,
+                "avg_launch_ms": avg_ms, "launches": st_n[di], "stage_share": share,
+                "source": "members run one by one outside the graph (untimed), every stage bracketed"}
+
+    # --- end to end: every step copies the eight streams from pinned host
+    # memory into the graph's input buffers, replays the graph and reads the
+    # visibilities and flags back into pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hosts = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in xs]
+        for h, x in zip(hosts, xs):
+            h.copy_(x)
+        vis_h = [torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for v in vis]
+        flags_h = [torch.empty(f.shape, dtype=f.dtype, pin_memory=True) for f in flags]
+
+        def e2e_step():
+            for h, x in zip(hosts, xs):
+                x.copy_(h, non_blocking=True)
+            g.run_dev(xs, vis, flags)
+            for a, b in zip(vis_h, vis):
+                a.copy_(b, non_blocking=True)
+            for a, b in zip(flags_h, flags):
+                a.copy_(b, non_blocking=True)
+            stream.synchronize()
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        ems = (time.perf_counter() - t0) * 1e3 / args.steps
+        ems = max_over_ranks(ems, dist if world > 1 else None, dev)
+        d2h = sum(v.numel() * v.element_size() for v in vis) + sum(f.numel() for f in flags)
+        e2e = {"value": job_rate(bytes_step, world, ems), "unit": "GB/s", "h2d_bytes_per_step": bytes_step,
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": ems,
+               "note": "copies, graph and read-back in sequence (the graph's input buffers are fixed)"}
+        del hosts, vis_h, flags_h
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -333,7 +429,8 @@ def run_batched(args, rank, world, local):
                        "tuning": [c.tuning() for c in members],
                        "path": "one captured graph; tensor-core X (int8) for members with >= %d inputs, "
                                "CUDA-core FP32 X below" % TENSOR_MIN_INPUTS},
-            "gpu_launches": int(launches), "clocks": clk,
+            "gpu_launches": int(launches), "clocks": clk, "roofline": roofline, "e2e": e2e,
+            "cpu_baseline": None if args.no_cpu else c4_cpu_baseline(),
             "plain_fp32": {"value": job_rate(bytes_step, world, ms_plain), "ms_per_step": ms_plain,
                            "ratio": ms_plain / ms},
         }
