@@ -225,6 +225,36 @@ __device__ __forceinline__ void later_passes(float2* z, const float2* tws, const
     }
 }
 
+// The same passes between two padded buffers (ping-pong): each pass loads
+// from zin and stores to zout, so one barrier per pass suffices.  Returns
+// the buffer that holds the result.
+template <int M, int NS, bool REGTW>
+__device__ __forceinline__ float2* later_passes_pp(float2* zin, float2* zout, const float2* tws,
+                                                   const float2 (&twr)[15], int tid,
+                                                   const float2* __restrict__ gtw) {
+    if constexpr (NS < M) {
+        constexpr bool last = (NS * 16 == M);
+        if (tid < M / 16) {
+            float2 v[16];
+            load_smem<M>(v, zin, tid);
+            if constexpr (last && REGTW) pass_compute_store<M, 16, NS, TW_REG>(zout, v, tws, twr, tid);
+            else if constexpr (last) pass_compute_store<M, 16, NS, TW_GLOBAL>(zout, v, tws, twr, tid, gtw);
+            else pass_compute_store<M, 16, NS, TW_SMEM>(zout, v, tws, twr, tid);
+        }
+        __syncthreads();
+        return later_passes_pp<M, NS * 16, REGTW>(zout, zin, tws, twr, tid, gtw);
+    } else {
+        return zin;
+    }
+}
+
+// Radix-16 passes after a first pass of radix R0.
+__host__ __device__ constexpr int n_later_passes(int M, int R0) {
+    int n = 0;
+    for (int ns = R0; ns < M; ns *= 16) ++n;
+    return n;
+}
+
 // Entries of the twiddle table kept in shared memory: every pass but the
 // last (whose twiddles are in registers or read from global memory).
 template <int M>
@@ -483,7 +513,14 @@ struct FftCfg {
     // prefetched; one CTA per SM then has up to 128 registers per thread.
     static constexpr bool REGTW = (M >= 32) && NACT <= 512;
     static constexpr int TWS = tw_smem_entries<M>();
-    static constexpr size_t SMEM = sizeof(float2) * (size_t)(M + M / 16 + 1 + TWS);
+    static constexpr int ZB = M + M / 16 + 1;                 // padded buffer entries
+    // Two buffers (one barrier per pass) while they fit with the table.
+    static constexpr bool PP = M <= 8192;
+    // With an odd number of radix-16 passes the result lands in the second
+    // buffer, which the next spectrum's first pass does not write: no barrier
+    // is needed between one spectrum's epilogue and the next first pass.
+    static constexpr bool RES_ALT = PP && (n_later_passes(M, first_radix(M)) % 2 == 1);
+    static constexpr size_t SMEM = sizeof(float2) * (size_t)((PP ? 2 : 1) * ZB + TWS);
 };
 
 template <int M>
@@ -498,7 +535,8 @@ __global__ void __launch_bounds__(FftCfg<M>::THREADS, FftCfg<M>::MINB) fft_kerne
     using C = FftCfg<M>;
     extern __shared__ float2 smem[];
     float2* zbuf = smem;
-    float2* tws = smem + (M + M / 16 + 1);
+    float2* zalt = smem + C::ZB;                      // second buffer (C::PP)
+    float2* tws = smem + (C::PP ? 2 : 1) * C::ZB;
     const int tid = threadIdx.x;
     constexpr int n_chan = M >> 1;
     constexpr int R0 = first_radix(M);
@@ -537,15 +575,20 @@ __global__ void __launch_bounds__(FftCfg<M>::THREADS, FftCfg<M>::MINB) fft_kerne
         // first pass (Ns = 1, no twiddles) straight from the global input
         if (tid < C::NACT) pass_compute_store<M, R0, 1, TW_NONE>(zbuf, cur, tws, twr, tid);
         __syncthreads();
-        later_passes<M, R0, C::REGTW>(zbuf, tws, twr, tid, A.tw);
+        const float2* zres = zbuf;
+        if constexpr (C::PP) {
+            zres = later_passes_pp<M, R0, C::REGTW>(zbuf, zalt, tws, twr, tid, A.tw);
+        } else {
+            later_passes<M, R0, C::REGTW>(zbuf, tws, twr, tid, A.tw);
+        }
         if constexpr (MODE == 2) {
             // |Y_a|^2 = |S|^2 / 4, |Y_b|^2 = |D|^2 / 4, summed over the row
 #pragma unroll
             for (int i = 0; i < PCH; ++i) {
                 const int k = tid + i * (int)blockDim.x;
                 if (k < n_chan) {
-                    const float2 zk = zbuf[pidx(k)];
-                    const float2 zm = zbuf[pidx((M - k) & (M - 1))];
+                    const float2 zk = zres[pidx(k)];
+                    const float2 zm = zres[pidx((M - k) & (M - 1))];
                     const float sx = zk.x + zm.x, sy = zk.y - zm.y;
                     const float dx = zk.x - zm.x, dy = zk.y + zm.y;
                     pa[i] = fmaf(sx, sx, fmaf(sy, sy, pa[i]));
@@ -578,8 +621,8 @@ __global__ void __launch_bounds__(FftCfg<M>::THREADS, FftCfg<M>::MINB) fft_kerne
             const long long slot = (s - A.v_origin) & A.v_mask;
             float4* Vout = reinterpret_cast<float4*>(A.V + (size_t)slot * n_chan * A.n_in_pad + a);
             for (int k = tid; k < n_chan; k += blockDim.x) {
-                const float2 zk = zbuf[pidx(k)];
-                const float2 zm = zbuf[pidx((M - k) & (M - 1))];
+                const float2 zk = zres[pidx(k)];
+                const float2 zm = zres[pidx((M - k) & (M - 1))];
                 const float2 S = make_float2(zk.x + zm.x, zk.y - zm.y);
                 const float2 D = make_float2(zk.x - zm.x, zk.y + zm.y);
                 float4 out;
@@ -593,7 +636,7 @@ __global__ void __launch_bounds__(FftCfg<M>::THREADS, FftCfg<M>::MINB) fft_kerne
                 Vout[(size_t)k * (A.n_in_pad >> 1)] = out;
             }
         }
-        __syncthreads();
+        if constexpr (!C::RES_ALT) __syncthreads();
         if constexpr (C::REGTW) {
 #pragma unroll
             for (int i = 0; i < 16; ++i) cur[i] = nxt[i];
