@@ -71,11 +71,11 @@ BYTES_PER_SAMPLE = {"fir": 5.0, "fft": 8.0, "xengine": 4.0, "finalize": 0.0, "fl
 
 
 # DRAM read + write per input sample of a kernel, from one ncu capture of the
-# same launch shape (profiles/fir_fft_c2_small_ncu.md: 545.4 MB per FFT
+# same launch shape (profiles/fir_fft_c2_small_ncu.md: 541.2 MB per FFT
 # launch of 1024 spectra x 4 pairs = 67.1 M samples with 256 MiB rings, cold
 # cache).  Reported as the roofline's `traffic` only for the workload and
 # kernel it was taken on.
-TRAFFIC_PER_SAMPLE = {("c2", "fft"): 545.44e6 / 67108864}
+TRAFFIC_PER_SAMPLE = {("c2", "fft"): 541.16e6 / 67108864}
 
 
 def _spec(wl, rank, samples):
