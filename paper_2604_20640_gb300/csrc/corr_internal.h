@@ -167,7 +167,9 @@ void launch_scale_from_vis(const float2* R, int n_in, int n_in_pad, int n_chan, 
                            cudaStream_t st);
 
 void launch_fir(const FirArgs& a, cudaStream_t st);
-void launch_fft(const FftArgs& a, cudaStream_t st);
+// CORR_OK, or CORR_EINVAL / CORR_ECUDA when the spectra's tensor map cannot
+// be made (V not 16-byte aligned, no driver entry point).
+int launch_fft(const FftArgs& a, cudaStream_t st);
 void launch_xengine(const XArgs& a, cudaStream_t st);
 void launch_finalize(const FinArgs& a, cudaStream_t st);
 void launch_mad_flags(const float2* R, uint8_t* F, int n_vis, int n_chan, int n_in, int window,

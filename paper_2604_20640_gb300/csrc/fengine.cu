@@ -16,13 +16,20 @@
 // rotation of Eq. 1 is constant within an integration, so the streaming
 // pipeline applies it to the integrated visibilities (finalize_kernel) and
 // fft_kernel stores U = 2Y; the stage entry point can still rotate here.
+#include "corr.h"
 #include "corr_internal.h"
+#include "tc_common.cuh"
+
+#include <cudaTypedefs.h>
 
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 
 namespace corr {
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 
 namespace {
 
@@ -228,7 +235,9 @@ __device__ __forceinline__ void later_passes(float2* z, const float2* tws, const
 // The same passes between two padded buffers (ping-pong): each pass loads
 // from zin and stores to zout, so one barrier per pass suffices.  Returns
 // the buffer that holds the result.
-template <int M, int NS, bool REGTW>
+// With STG, thread 0 waits before the last barrier until the bulk stores
+// issued from the staging buffer have read it (the epilogue rewrites it).
+template <int M, int NS, bool REGTW, bool STG>
 __device__ __forceinline__ float2* later_passes_pp(float2* zin, float2* zout, const float2* tws,
                                                    const float2 (&twr)[15], int tid,
                                                    const float2* __restrict__ gtw) {
@@ -241,8 +250,11 @@ __device__ __forceinline__ float2* later_passes_pp(float2* zin, float2* zout, co
             else if constexpr (last) pass_compute_store<M, 16, NS, TW_GLOBAL>(zout, v, tws, twr, tid, gtw);
             else pass_compute_store<M, 16, NS, TW_SMEM>(zout, v, tws, twr, tid);
         }
+        if constexpr (STG && last) {
+            if (tid == 0) tc::bulk_wait_read_all();
+        }
         __syncthreads();
-        return later_passes_pp<M, NS * 16, REGTW>(zout, zin, tws, twr, tid, gtw);
+        return later_passes_pp<M, NS * 16, REGTW, STG>(zout, zin, tws, twr, tid, gtw);
     } else {
         return zin;
     }
@@ -506,8 +518,6 @@ template <int M>
 struct FftCfg {
     static constexpr int NACT = M / 16;
     static constexpr int THREADS = NACT < 32 ? 32 : NACT;
-    // CTAs per SM the register budget is held to (128 registers a thread).
-    static constexpr int MINB = THREADS >= 512 ? 1 : 65536 / 128 / THREADS;
     // With at most 512 threads the last pass's 15 twiddles (fixed per thread)
     // stay in registers and the next spectrum's first-pass input is
     // prefetched; one CTA per SM then has up to 128 registers per thread.
@@ -520,7 +530,21 @@ struct FftCfg {
     // buffer, which the next spectrum's first pass does not write: no barrier
     // is needed between one spectrum's epilogue and the next first pass.
     static constexpr bool RES_ALT = PP && (n_later_passes(M, first_radix(M)) % 2 == 1);
-    static constexpr size_t SMEM = sizeof(float2) * (size_t)((PP ? 2 : 1) * ZB + TWS);
+    // 512 <= M <= 4096, spectra out (modes 0, 1): two input pairs per CTA,
+    // one transform per THREADS-thread group, whose spectra leave through a
+    // shared staging buffer [n_chan][2] of float4 by 2D bulk tensor stores of
+    // BOXR channels -- 32 contiguous bytes (a whole sector) per channel.
+    // Elsewhere one pair per CTA stores its 16 bytes per channel directly.
+    static constexpr bool TMA_OUT = PP && M >= 512 && M <= 4096;
+    static constexpr int BOXR = (M / 2) < 256 ? (M / 2) : 256;
+    __host__ __device__ static constexpr int pairs(int mode) { return (TMA_OUT && mode != 2) ? 2 : 1; }
+    __host__ __device__ static constexpr int threads(int mode) { return THREADS * pairs(mode); }
+    // CTAs per SM the register budget is held to (128 registers a thread)
+    __host__ __device__ static constexpr int minb(int mode) { return threads(mode) >= 512 ? 1 : 65536 / 128 / threads(mode); }
+    __host__ __device__ static constexpr size_t smem_bytes(int mode) {
+        return sizeof(float2) * (size_t)(pairs(mode) * (PP ? 2 : 1) * ZB + TWS) +
+               ((TMA_OUT && mode != 2) ? (size_t)(M / 2) * 16 * pairs(mode) + 128 : 0);
+    }
 };
 
 template <int M>
@@ -531,24 +555,36 @@ __device__ __forceinline__ const float2* fft_input(const FftArgs& A, long long s
 
 // MODE 0: store U = 2Y; 1: store the rotated V; 2: accumulate power tiles.
 template <int M, int MODE>
-__global__ void __launch_bounds__(FftCfg<M>::THREADS, FftCfg<M>::MINB) fft_kernel(const FftArgs A) {
+__global__ void __launch_bounds__(FftCfg<M>::threads(MODE), FftCfg<M>::minb(MODE))
+    fft_kernel(const FftArgs A, const __grid_constant__ CUtensorMap vmap) {
     using C = FftCfg<M>;
+    constexpr bool STG = C::TMA_OUT && MODE != 2;
+    constexpr int P = C::pairs(MODE);                 // input pairs (transforms) per CTA
     extern __shared__ float2 smem[];
-    float2* zbuf = smem;
-    float2* zalt = smem + C::ZB;                      // second buffer (C::PP)
-    float2* tws = smem + (C::PP ? 2 : 1) * C::ZB;
-    const int tid = threadIdx.x;
+    // group g of THREADS threads transforms pair blockIdx.y * P + g
+    const int g = P > 1 ? (int)threadIdx.x / C::THREADS : 0;
+    const int tid = (int)threadIdx.x - g * C::THREADS;
+    float2* zbuf = smem + (size_t)g * (C::PP ? 2 : 1) * C::ZB;
+    float2* zalt = zbuf + C::ZB;                      // second buffer (C::PP)
+    float2* tws = smem + (size_t)P * (C::PP ? 2 : 1) * C::ZB;
+    // staging buffer of one spectrum's output [n_chan][P], 128-byte aligned (STG)
+    float4* stg = nullptr;
+    if constexpr (STG) {
+        char* p = reinterpret_cast<char*>(tws + C::TWS);
+        const uint32_t b = tc::smem_u32(p);
+        stg = reinterpret_cast<float4*>(p + (((b + 127u) & ~127u) - b));
+    }
     constexpr int n_chan = M >> 1;
     constexpr int R0 = first_radix(M);
-    const int pair = blockIdx.y;
-    const int n_pairs = gridDim.y;
+    const int pair = (int)blockIdx.y * P + g;
+    const int n_pairs = (int)gridDim.y * P;
     const int a = 2 * pair;
     const long long s_lo = A.s_begin + (long long)blockIdx.x * A.spt;
     long long s_hi = s_lo + A.spt;
     if (s_hi > A.s_end) s_hi = A.s_end;
     if (s_lo >= s_hi) return;
 
-    for (int i = tid; i < C::TWS; i += blockDim.x) tws[i] = __ldg(A.tw + i);
+    for (int i = (int)threadIdx.x; i < C::TWS; i += blockDim.x) tws[i] = __ldg(A.tw + i);
     float2 twr[15];
     if constexpr (C::REGTW) {
         constexpr int NSL = M / 16;
@@ -565,6 +601,15 @@ __global__ void __launch_bounds__(FftCfg<M>::THREADS, FftCfg<M>::MINB) fft_kerne
     float pa[PCH], pb[PCH];
 #pragma unroll
     for (int i = 0; i < PCH; ++i) pa[i] = pb[i] = 0.f;
+    // Bulk stores of the staged spectrum in slot `sl` (thread 0, after a
+    // barrier that follows every thread's staging writes and proxy fence).
+    auto store_staged = [&](long long sl) {
+        for (int b = 0; b < n_chan / C::BOXR; ++b)
+            tc::tma_store_2d(&vmap, stg + b * C::BOXR * P, 4 * P * (int)blockIdx.y, (int)(sl * n_chan + b * C::BOXR));
+        tc::bulk_commit();
+    };
+    long long prev_slot = -1;
+
     float2 cur[16];
     load_first<M>(cur, fft_input<M>(A, s_lo, pair, n_pairs), tid);
     for (long long s = s_lo; s < s_hi; ++s) {
@@ -575,9 +620,13 @@ __global__ void __launch_bounds__(FftCfg<M>::THREADS, FftCfg<M>::MINB) fft_kerne
         // first pass (Ns = 1, no twiddles) straight from the global input
         if (tid < C::NACT) pass_compute_store<M, R0, 1, TW_NONE>(zbuf, cur, tws, twr, tid);
         __syncthreads();
+        if constexpr (STG) {
+            // the previous spectrum is staged and fenced by every thread
+            if (threadIdx.x == 0 && prev_slot >= 0) store_staged(prev_slot);
+        }
         const float2* zres = zbuf;
         if constexpr (C::PP) {
-            zres = later_passes_pp<M, R0, C::REGTW>(zbuf, zalt, tws, twr, tid, A.tw);
+            zres = later_passes_pp<M, R0, C::REGTW, STG>(zbuf, zalt, tws, twr, tid, A.tw);
         } else {
             later_passes<M, R0, C::REGTW>(zbuf, tws, twr, tid, A.tw);
         }
@@ -620,7 +669,7 @@ __global__ void __launch_bounds__(FftCfg<M>::THREADS, FftCfg<M>::MINB) fft_kerne
         } else {
             const long long slot = (s - A.v_origin) & A.v_mask;
             float4* Vout = reinterpret_cast<float4*>(A.V + (size_t)slot * n_chan * A.n_in_pad + a);
-            for (int k = tid; k < n_chan; k += blockDim.x) {
+            for (int k = tid; k < n_chan; k += C::THREADS) {
                 const float2 zk = zres[pidx(k)];
                 const float2 zm = zres[pidx((M - k) & (M - 1))];
                 const float2 S = make_float2(zk.x + zm.x, zk.y - zm.y);
@@ -633,7 +682,12 @@ __global__ void __launch_bounds__(FftCfg<M>::THREADS, FftCfg<M>::MINB) fft_kerne
                 } else {
                     out = make_float4(S.x, S.y, D.y, -D.x);
                 }
-                Vout[(size_t)k * (A.n_in_pad >> 1)] = out;
+                if constexpr (STG) stg[k * P + g] = out;
+                else Vout[(size_t)k * (A.n_in_pad >> 1)] = out;
+            }
+            if constexpr (STG) {
+                tc::fence_proxy_async_smem();
+                prev_slot = slot;
             }
         }
         if constexpr (!C::RES_ALT) __syncthreads();
@@ -642,6 +696,13 @@ __global__ void __launch_bounds__(FftCfg<M>::THREADS, FftCfg<M>::MINB) fft_kerne
             for (int i = 0; i < 16; ++i) cur[i] = nxt[i];
         } else {
             if (s + 1 < s_hi) load_first<M>(cur, fft_input<M>(A, s + 1, pair, n_pairs), tid);
+        }
+    }
+    if constexpr (STG) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            store_staged(prev_slot);
+            tc::bulk_wait_all();
         }
     }
 }
@@ -668,56 +729,78 @@ std::vector<float2> fft_twiddle_table(int M) {
 }
 
 template <int M, int MODE>
-static void launch_fft_m(const FftArgs& a, cudaStream_t st) {
+static int launch_fft_m(const FftArgs& a, cudaStream_t st) {
+    using C = FftCfg<M>;
+    constexpr bool STG = C::TMA_OUT && MODE != 2;
     static int resident = 0;     // CTAs per SM at this kernel's registers and shared memory
     static int sms = 0;
-    const size_t smem = FftCfg<M>::SMEM;
+    const size_t smem = C::smem_bytes(MODE);
     if (!resident) {
         cudaFuncSetAttribute(fft_kernel<M, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, fft_kernel<M, MODE>, FftCfg<M>::THREADS, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, fft_kernel<M, MODE>, C::threads(MODE), smem);
         if (resident < 1) resident = 1;
         if (sms < 1) sms = 152;
+    }
+    CUtensorMap vmap;
+    std::memset(&vmap, 0, sizeof(vmap));
+    if constexpr (STG) {
+        // V as rows of n_in_pad complex64 (2 n_in_pad floats, 8 n_in_pad
+        // bytes apart); one row per (slot, channel).  A pair writes the 16
+        // bytes at float 4 * pair of each row.
+        PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+        if (!enc) return CORR_ECUDA;
+        if ((reinterpret_cast<uintptr_t>(a.V) & 15) != 0) return CORR_EINVAL;
+        const long long slots = a.v_mask == -1LL ? a.s_end - a.v_origin : a.v_mask + 1;
+        cuuint64_t dims[2] = {(cuuint64_t)a.n_in_pad * 2, (cuuint64_t)slots * (M / 2)};
+        cuuint64_t strides[1] = {(cuuint64_t)a.n_in_pad * 8};
+        cuuint32_t box[2] = {(cuuint32_t)(4 * C::pairs(MODE)), (cuuint32_t)C::BOXR};
+        cuuint32_t estr[2] = {1, 1};
+        const CUresult r = enc(&vmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, a.V, dims, strides, box, estr,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return CORR_EINVAL;
     }
     // One wave of resident CTAs, each looping over a run of spectra of one
     // pair: runs x pairs never exceeds the resident slots (rounding up would
     // leave a few CTAs for a second, nearly empty wave as long as the first).
     const long long n = a.s_end - a.s_begin;
-    const int n_pairs = a.n_in_pad / 2;
-    long long runs = (long long)sms * resident / n_pairs;
+    const int n_groups = a.n_in_pad / 2 / C::pairs(MODE);     // n_in_pad is a multiple of 4
+    long long runs = (long long)sms * resident / n_groups;
     if (runs > n) runs = n;
     if (runs < 1) runs = 1;
     FftArgs b = a;
     b.spt = (int)((n + runs - 1) / runs);
-    dim3 grid((unsigned)((n + b.spt - 1) / b.spt), (unsigned)n_pairs);
-    fft_kernel<M, MODE><<<grid, FftCfg<M>::THREADS, smem, st>>>(b);
+    dim3 grid((unsigned)((n + b.spt - 1) / b.spt), (unsigned)n_groups);
+    fft_kernel<M, MODE><<<grid, C::threads(MODE), smem, st>>>(b, vmap);
+    return CORR_OK;
 }
 
 template <int MODE>
-static void launch_fft_mode(const FftArgs& a, cudaStream_t st) {
+static int launch_fft_mode(const FftArgs& a, cudaStream_t st) {
     switch (a.M) {
-        case 16: launch_fft_m<16, MODE>(a, st); break;
-        case 32: launch_fft_m<32, MODE>(a, st); break;
-        case 64: launch_fft_m<64, MODE>(a, st); break;
-        case 128: launch_fft_m<128, MODE>(a, st); break;
-        case 256: launch_fft_m<256, MODE>(a, st); break;
-        case 512: launch_fft_m<512, MODE>(a, st); break;
-        case 1024: launch_fft_m<1024, MODE>(a, st); break;
-        case 2048: launch_fft_m<2048, MODE>(a, st); break;
-        case 4096: launch_fft_m<4096, MODE>(a, st); break;
-        case 8192: launch_fft_m<8192, MODE>(a, st); break;
-        case 16384: launch_fft_m<16384, MODE>(a, st); break;
-        default: break;
+        case 16: return launch_fft_m<16, MODE>(a, st);
+        case 32: return launch_fft_m<32, MODE>(a, st);
+        case 64: return launch_fft_m<64, MODE>(a, st);
+        case 128: return launch_fft_m<128, MODE>(a, st);
+        case 256: return launch_fft_m<256, MODE>(a, st);
+        case 512: return launch_fft_m<512, MODE>(a, st);
+        case 1024: return launch_fft_m<1024, MODE>(a, st);
+        case 2048: return launch_fft_m<2048, MODE>(a, st);
+        case 4096: return launch_fft_m<4096, MODE>(a, st);
+        case 8192: return launch_fft_m<8192, MODE>(a, st);
+        case 16384: return launch_fft_m<16384, MODE>(a, st);
+        default: return CORR_EINVAL;
     }
 }
 
-void launch_fft(const FftArgs& a, cudaStream_t st) {
-    if (a.s_end <= a.s_begin) return;
-    if (a.tiles) launch_fft_mode<2>(a, st);
-    else if (a.phasor) launch_fft_mode<1>(a, st);
-    else launch_fft_mode<0>(a, st);
+int launch_fft(const FftArgs& a, cudaStream_t st) {
+    if (a.s_end <= a.s_begin) return CORR_OK;
+    if (a.tiles) return launch_fft_mode<2>(a, st);
+    if (a.phasor) return launch_fft_mode<1>(a, st);
+    return launch_fft_mode<0>(a, st);
 }
 
 void launch_fir(const FirArgs& a, cudaStream_t st) {

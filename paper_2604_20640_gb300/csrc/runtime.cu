@@ -387,10 +387,12 @@ int launch_f(corr_t h, const StreamView& sv, const Tables& t, float2* Z, long lo
         launch_fir(a, st);
     }
     CK(cudaGetLastError());
+    int rc;
     {
         Timed t_(h, 1, st);
-        launch_fft(f, st);
+        rc = launch_fft(f, st);
     }
+    if (rc != CORR_OK) return fail(h, rc, "FFT launch: spectra buffer not 16-byte aligned or no tensor-map encoder");
     CK(cudaGetLastError());
     return CORR_OK;
 }
