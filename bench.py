@@ -71,11 +71,9 @@ BYTES_PER_SAMPLE = {"fir": 5.0, "fft": 8.0, "xengine": 4.0, "finalize": 0.0, "fl
 
 
 # DRAM read + write per input sample of a kernel, from one ncu capture of the
-# same launch shape (profiles/fir_fft_c2_small_ncu.md: 541.2 MB per FFT
-# launch of 1024 spectra x 4 pairs = 67.1 M samples with 256 MiB rings, cold
-# cache).  Reported as the roofline's `traffic` only for the workload and
-# kernel it was taken on.
-TRAFFIC_PER_SAMPLE = {("c2", "fft"): 541.16e6 / 67108864}
+# same launch shape and the same kernel code (cold cache).  Reported as the
+# roofline's `traffic` only for the workload and kernel it was taken on.
+TRAFFIC_PER_SAMPLE = {}
 
 
 def _spec(wl, rank, samples):
@@ -848,7 +846,11 @@ def main():
     achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
     tps = TRAFFIC_PER_SAMPLE.get((args.workload, dom))
     traffic = tps * samples_timed / max(1, stage_n[di]) if tps and prec == 0 else None
-    roofline = {"kernel": KERNELS[dom], "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+    kname = KERNELS[dom]
+    if dom == "fft":
+        # mode 3: spectra ring pair-major (FP32 path with n_in_pad <= 8); 0: channel-major
+        kname = "fft_kernel<%d,%d>" % (2 * W["n_chan"], 3 if prec == 0 and (n_in + 3) // 4 * 4 <= 8 else 0)
+    roofline = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_src,
                 "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms, "launches": stage_n[di],
                 "stage_share": share}

@@ -61,6 +61,10 @@ struct FftArgs {
     // [64][256] (atomic adds; the caller zeroes them)
     float* tiles;
     int n_row, rows, n_in;
+    // spectra ring pair-major, [slot][pair][n_chan] of float4 (the pair's
+    // two complex values), instead of [slot][n_chan][n_in_pad] complex64:
+    // the small-N FP32 pipeline, whose X-engine reads that layout
+    int pair_major;
 };
 
 // X-engine launch: groups of spectra, each group summed into one partial
@@ -75,6 +79,7 @@ struct XArgs {
     long long int_start, int_end, s_limit;
     int G, j0, n_groups;
     float* part;             // [gpi][nt][32][n_chan]
+    int pair_major;          // V pair-major (n_in_pad <= 8 only), see FftArgs
 };
 
 // Finalise: R[k][a][b] = scale * Q_a[k] conj(Q_b[k]) * (sum over partial

@@ -537,13 +537,13 @@ struct FftCfg {
     // Elsewhere one pair per CTA stores its 16 bytes per channel directly.
     static constexpr bool TMA_OUT = PP && M >= 512 && M <= 4096;
     static constexpr int BOXR = (M / 2) < 256 ? (M / 2) : 256;
-    __host__ __device__ static constexpr int pairs(int mode) { return (TMA_OUT && mode != 2) ? 2 : 1; }
+    __host__ __device__ static constexpr int pairs(int mode) { return (TMA_OUT && mode <= 1) ? 2 : 1; }
     __host__ __device__ static constexpr int threads(int mode) { return THREADS * pairs(mode); }
     // CTAs per SM the register budget is held to (128 registers a thread)
     __host__ __device__ static constexpr int minb(int mode) { return threads(mode) >= 512 ? 1 : 65536 / 128 / threads(mode); }
     __host__ __device__ static constexpr size_t smem_bytes(int mode) {
         return sizeof(float2) * (size_t)(pairs(mode) * (PP ? 2 : 1) * ZB + TWS) +
-               ((TMA_OUT && mode != 2) ? (size_t)(M / 2) * 16 * pairs(mode) + 128 : 0);
+               ((TMA_OUT && mode <= 1) ? (size_t)(M / 2) * 16 * pairs(mode) + 128 : 0);
     }
 };
 
@@ -553,12 +553,13 @@ __device__ __forceinline__ const float2* fft_input(const FftArgs& A, long long s
     return A.Z + ((size_t)zs * n_pairs + pair) * M;
 }
 
-// MODE 0: store U = 2Y; 1: store the rotated V; 2: accumulate power tiles.
+// MODE 0: store U = 2Y; 1: store the rotated V; 2: accumulate power tiles;
+// 3: store U = 2Y pair-major ([slot][pair][n_chan] float4).
 template <int M, int MODE>
 __global__ void __launch_bounds__(FftCfg<M>::threads(MODE), FftCfg<M>::minb(MODE))
     fft_kernel(const FftArgs A, const __grid_constant__ CUtensorMap vmap) {
     using C = FftCfg<M>;
-    constexpr bool STG = C::TMA_OUT && MODE != 2;
+    constexpr bool STG = C::TMA_OUT && MODE <= 1;
     constexpr int P = C::pairs(MODE);                 // input pairs (transforms) per CTA
     extern __shared__ float2 smem[];
     // group g of THREADS threads transforms pair blockIdx.y * P + g
@@ -668,7 +669,16 @@ __global__ void __launch_bounds__(FftCfg<M>::threads(MODE), FftCfg<M>::minb(MODE
             }
         } else {
             const long long slot = (s - A.v_origin) & A.v_mask;
-            float4* Vout = reinterpret_cast<float4*>(A.V + (size_t)slot * n_chan * A.n_in_pad + a);
+            // channel k of the pair at Vout[k * vstride]
+            float4* Vout;
+            size_t vstride;
+            if constexpr (MODE == 3) {
+                Vout = reinterpret_cast<float4*>(A.V) + ((size_t)slot * n_pairs + pair) * n_chan;
+                vstride = 1;
+            } else {
+                Vout = reinterpret_cast<float4*>(A.V + (size_t)slot * n_chan * A.n_in_pad + a);
+                vstride = (size_t)(A.n_in_pad >> 1);
+            }
             for (int k = tid; k < n_chan; k += C::THREADS) {
                 const float2 zk = zres[pidx(k)];
                 const float2 zm = zres[pidx((M - k) & (M - 1))];
@@ -683,7 +693,7 @@ __global__ void __launch_bounds__(FftCfg<M>::threads(MODE), FftCfg<M>::minb(MODE
                     out = make_float4(S.x, S.y, D.y, -D.x);
                 }
                 if constexpr (STG) stg[k * P + g] = out;
-                else Vout[(size_t)k * (A.n_in_pad >> 1)] = out;
+                else Vout[(size_t)k * vstride] = out;
             }
             if constexpr (STG) {
                 tc::fence_proxy_async_smem();
@@ -800,6 +810,7 @@ int launch_fft(const FftArgs& a, cudaStream_t st) {
     if (a.s_end <= a.s_begin) return CORR_OK;
     if (a.tiles) return launch_fft_mode<2>(a, st);
     if (a.phasor) return launch_fft_mode<1>(a, st);
+    if (a.pair_major) return launch_fft_mode<3>(a, st);
     return launch_fft_mode<0>(a, st);
 }
 

@@ -343,6 +343,10 @@ int alloc_pipe(corr_t h, Pipe& p) {
     return CORR_OK;
 }
 
+// The FP32 pipeline with the small-N X-engine keeps its spectra ring
+// pair-major (FftArgs::pair_major); every other reader wants channel-major.
+bool pair_major_ring(corr_t h) { return h->precision == CORR_FP32 && h->n_in_pad <= 8; }
+
 // F-engine over spectra [s_begin, s_end): FIR into the Z ring, FFT into the
 // V ring.  `phasor` set -> rotated V (stage call); else U = 2Y (pipeline).
 int launch_f(corr_t h, const StreamView& sv, const Tables& t, float2* Z, long long z_origin, long long z_mask,
@@ -382,6 +386,7 @@ int launch_f(corr_t h, const StreamView& sv, const Tables& t, float2* Z, long lo
     f.n_row = n_row;
     f.rows = rows;
     f.n_in = h->n_in;
+    f.pair_major = phasor == nullptr && tiles == nullptr && pair_major_ring(h);
     {
         Timed t_(h, 0, st);
         launch_fir(a, st);
@@ -493,6 +498,7 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
                 x.j0 = j_begin;
                 x.n_groups = j_end - j_begin;
                 x.part = p.part;
+                x.pair_major = pair_major_ring(h);
                 {
                     Timed t_(h, 2, st);
                     launch_xengine(x, st);

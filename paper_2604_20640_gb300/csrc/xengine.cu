@@ -66,7 +66,8 @@ __global__ void __launch_bounds__(128) xengine_kernel(const XArgs X) {
 // one channel.  A warp covers 4 channels x 8 sub-groups; sub-group q sums
 // spectra q, q+8, q+16, ... of the group and the eight partial sums are
 // added with a fixed xor-shuffle tree, then written in the 4x4 block layout.
-template <int NB>
+// PM: spectra pair-major ([slot][pair][n_chan] float4), else channel-major.
+template <int NB, bool PM>
 __global__ void __launch_bounds__(128) xengine_small_kernel(const XArgs X) {
     constexpr int NI = 4 * NB;
     constexpr int NC = NI * (NI - 1) / 2;
@@ -87,11 +88,13 @@ __global__ void __launch_bounds__(128) xengine_small_kernel(const XArgs X) {
     for (int i = 0; i < NC; ++i) { cr[i] = 0.f; ci[i] = 0.f; }
     for (long long s = s0 + q; s < s1; s += 8) {
         const long long slot = (s - X.v_origin) & X.v_mask;
-        const float4* vp = reinterpret_cast<const float4*>(X.V) + ((size_t)slot * X.n_chan + kk) * (NI / 2);
+        const float4* vp = PM ? reinterpret_cast<const float4*>(X.V) + (size_t)slot * (NI / 2) * X.n_chan + kk
+                              : reinterpret_cast<const float4*>(X.V) + ((size_t)slot * X.n_chan + kk) * (NI / 2);
+        const size_t vs = PM ? (size_t)X.n_chan : 1;      // float4 between pairs
         float xr[NI], xi[NI];
 #pragma unroll
         for (int i = 0; i < NI / 2; ++i) {
-            const float4 t = __ldg(vp + i);
+            const float4 t = __ldg(vp + i * vs);
             xr[2 * i] = t.x; xi[2 * i] = t.y; xr[2 * i + 1] = t.z; xi[2 * i + 1] = t.w;
         }
 #pragma unroll
@@ -253,8 +256,13 @@ void launch_xengine(const XArgs& a, cudaStream_t st) {
     if (a.n_groups <= 0) return;
     if (a.n_in_pad <= 8) {
         dim3 grid((a.n_chan + 15) / 16, a.n_groups);
-        if (a.n_in_pad == 4) xengine_small_kernel<1><<<grid, 128, 0, st>>>(a);
-        else xengine_small_kernel<2><<<grid, 128, 0, st>>>(a);
+        if (a.pair_major) {
+            if (a.n_in_pad == 4) xengine_small_kernel<1, true><<<grid, 128, 0, st>>>(a);
+            else xengine_small_kernel<2, true><<<grid, 128, 0, st>>>(a);
+        } else {
+            if (a.n_in_pad == 4) xengine_small_kernel<1, false><<<grid, 128, 0, st>>>(a);
+            else xengine_small_kernel<2, false><<<grid, 128, 0, st>>>(a);
+        }
         return;
     }
     dim3 grid((a.n_chan + 127) / 128, a.nt, a.n_groups);
