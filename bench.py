@@ -71,9 +71,12 @@ BYTES_PER_SAMPLE = {"fir": 5.0, "fft": 8.0, "xengine": 4.0, "finalize": 0.0, "fl
 
 
 # DRAM read + write per input sample of a kernel, from one ncu capture of the
-# same launch shape and the same kernel code (cold cache).  Reported as the
-# roofline's `traffic` only for the workload and kernel it was taken on.
-TRAFFIC_PER_SAMPLE = {}
+# same launch shape and the same kernel code (profiles/fir_fft_c2_small_ncu.md:
+# fft_kernel<8192,3>, 268.5 MB read + 215.7 MB written per launch of 1024
+# spectra x 4 pairs = 67.1 M samples with 256 MiB rings, cold cache).
+# Reported as the roofline's `traffic` only for the workload and kernel it
+# was taken on.
+TRAFFIC_PER_SAMPLE = {("c2", "fft"): 484.27e6 / 67108864}
 
 
 def _spec(wl, rank, samples):
@@ -579,7 +582,8 @@ def run_flagger(args, rank, world, local):
     bytes_per_launch = bps_c5[dom] * n_samples_pass / max(1, stage_n[di])
     avg_ms = stage_ms[di] / max(1, stage_n[di])
     achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
-    roofline = {"kernel": KERNELS[dom], "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+    kname = "fft_kernel<%d,2> (power mode)" % (2 * W["n_chan"]) if dom == "fft" else KERNELS[dom]
+    roofline = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": None, "peak_source": "measured" if peaks else "fallback",
                 "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms, "launches": stage_n[di],
                 "stage_share": share,
