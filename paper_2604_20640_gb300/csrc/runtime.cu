@@ -318,8 +318,9 @@ int choose_fir_spt(long long n_spec, int n_pairs, int M, int taps) {
 int alloc_pipe(corr_t h, Pipe& p) {
     if (p.V) return CORR_OK;
     const unsigned long long ring_bytes = (unsigned long long)h->ring_mb << 20;
-    // Power-of-two rings of about 32 MiB each, so that the FIR output and the
-    // channelised spectra both stay in L2 between the kernels.
+    // Two power-of-two rings (FIR output and channelised spectra) of half of
+    // ring_mb each: at the 64 MiB default both stay in L2 between the
+    // kernels; larger rings mean fewer, larger launches.
     const size_t per_spec = (size_t)h->n_chan * h->n_in_pad * sizeof(float2);
     long long cap = 1;
     while (cap * 2 * per_spec <= ring_bytes && cap < 4096) cap *= 2;
