@@ -196,8 +196,9 @@ int corr_run_dev(corr_t h, const void* d_samples, size_t n_samples, size_t input
  * corr_fengine_dev -- channelise spectra s0 .. s0+n_spec-1 of the
  *   device-resident stream (same conventions as corr_run_dev) into
  *   d_V [n_spec][n_chan][n_in_pad] complex64, n_in_pad = n_in rounded up to
- *   a multiple of 4 (padding inputs are written as zeros).  Sec. 4.2 F-engine
- *   with Eq. 1's delay and phase terms.
+ *   a multiple of 4 (padding inputs are written as zeros); d_V must be
+ *   16-byte aligned (the FFT writes it with tensor stores; CORR_EINVAL
+ *   otherwise).  Sec. 4.2 F-engine with Eq. 1's delay and phase terms.
  * corr_xengine_dev -- R[k][a][b] = (1/n_spec) sum_s V V^* over all n_spec
  *   spectra of d_V (layout as above) into d_vis [n_chan][n_in][n_in]
  *   complex64.  Sec. 4.2 X-engine.
