@@ -61,3 +61,33 @@ def test_missing_library_fails_loudly(tmp_path):
             corr.load_library(str(tmp_path / "nope.so"))
     finally:
         corr._lib = saved
+
+
+def test_result_buffer_validation_on_the_host():
+    """get_vis / get_flags take caller buffers [>= n][n_chan][n_in][n_in]:
+    C-contiguous numpy arrays or CPU tensors of the right type; anything
+    else is rejected before the library is called."""
+    import types
+    import numpy as np
+    from paper_2604_20640_gb300 import Correlator, CorrError
+    me = types.SimpleNamespace(n_chan=8, n_in=3)
+    check = Correlator._result_out
+    good = np.zeros((4, 8, 3, 3), np.complex64)
+    ptr, view = check(me, good, 4, np.complex64)
+    assert ptr == good.ctypes.data and view is good
+    check(me, good, 2, np.complex64)                                   # larger than needed
+    for bad, n in [(np.zeros((4, 8, 3, 3), np.complex128), 4),          # wrong type
+                   (np.zeros((4, 8, 3, 4), np.complex64), 4),           # wrong shape
+                   (np.zeros((3, 8, 3, 3), np.complex64), 4),           # too short
+                   (np.zeros((4, 8, 3, 3, 2), np.complex64)[..., 0], 4),  # not contiguous
+                   ([[0]], 1)]:                                         # not an array
+        with pytest.raises(CorrError):
+            check(me, bad, n, np.complex64)
+    torch = pytest.importorskip("torch")
+    t = torch.zeros((4, 8, 3, 3), dtype=torch.uint8)
+    ptr, view = check(me, t, 4, np.uint8)
+    assert ptr == t.data_ptr() and view is t
+    for bad in (torch.zeros((4, 8, 3, 3), dtype=torch.int8), torch.zeros((4, 3, 8, 3), dtype=torch.uint8),
+                torch.zeros((4, 8, 3, 6), dtype=torch.uint8)[..., ::2]):
+        with pytest.raises(CorrError):
+            check(me, bad, 4, np.uint8)
