@@ -201,7 +201,9 @@ int corr_run_dev(corr_t h, const void* d_samples, size_t n_samples, size_t input
  *   otherwise).  Sec. 4.2 F-engine with Eq. 1's delay and phase terms.
  * corr_xengine_dev -- R[k][a][b] = (1/n_spec) sum_s V V^* over all n_spec
  *   spectra of d_V (layout as above) into d_vis [n_chan][n_in][n_in]
- *   complex64.  Sec. 4.2 X-engine.
+ *   complex64.  Sec. 4.2 X-engine.  d_V must be 16-byte aligned (it is read
+ *   as 16-byte vectors) and d_vis 8-byte aligned, else CORR_EINVAL before
+ *   any launch.
  * corr_flag_dev -- MAD flags (Eq. 2) of n_vis integrations d_vis into d_flags.
  */
 int corr_fengine_dev(corr_t h, const void* d_samples, size_t n_samples, size_t input_stride,
@@ -374,25 +376,31 @@ int corr_stage_times(corr_t h, double* ms, long long* counts, int n_stages);
 
 /*
  * corr_xengine_noalloc -- the X-engine of corr_xengine_dev for callers that
- * cannot allocate device memory (code recording a CUDA graph that must stay
- * replayable, real-time loops where an allocator call could stall the
- * device, hosts that manage the GPU's memory themselves).  The paper has no
- * counterpart; it is a library facility.
+ * cannot allocate device memory: real-time loops where an allocator call
+ * (which can synchronise the device) would stall the stream that has to keep
+ * up with the samples, and hosts that manage the GPU's memory budget
+ * themselves from a plan fixed at start-up.  The paper has no counterpart;
+ * it is a library facility.
  *   d_V:    device [n_spec][n_chan][n_in_pad] complex64, n_in_pad = n_in
- *           rounded up to a multiple of 4 (padding entries are ignored).
+ *           rounded up to a multiple of 4 (padding entries are ignored);
+ *           16-byte aligned.
  *   d_vis:  device [n_chan][n_in][n_in] complex64 output,
- *           R[k][a][b] = (1/n_spec) sum_s V_a V_b^*.
+ *           R[k][a][b] = (1/n_spec) sum_s V_a V_b^*; 8-byte aligned.
  *   stream: cudaStream_t as void*.
  * Needs no handle and allocates nothing: its partial sums live in one 8 MiB
  * file-scope device array that every GPU loading the library keeps until
  * exit.  Shapes whose per-group scratch ((blocks of 4 inputs, A <= B) * 32 *
  * n_chan floats) exceeds 2^21 floats are rejected with CORR_EINVAL; long
  * streams are summed in fewer, longer groups.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress); make that first
- * call before any stream capture.  All calls share the array and it keeps the
- * last call's contents (every part a call reads it first writes itself), so
- * calls that overlap on the GPU race: serialise them on one stream.  On
- * failure corr_last_error(NULL) describes the error.
+ * looks up the array's device address (cudaGetSymbolAddress) and keeps it
+ * for the life of the process; make that first call before any stream
+ * capture, and do not call it after cudaDeviceReset.  All calls share the
+ * array and it keeps the last call's contents (every part a call reads it
+ * first writes itself), so calls that overlap on the GPU race: serialise
+ * them on one stream.  Misaligned buffers are rejected with CORR_EINVAL, and
+ * a CUDA error already pending from earlier work is reported (CORR_ECUDA)
+ * without being cleared.  On failure corr_last_error(NULL) describes the
+ * error.
  */
 int corr_xengine_noalloc(const float* d_V, int n_spec, int n_in, int n_chan, float* d_vis, void* stream);
 

@@ -1,15 +1,17 @@
 // Allocation-free X-engine entry point.
 //
-// Some callers cannot allocate device memory: code running while a CUDA
-// stream is being captured into a graph that must stay replayable, real-time
-// loops that forbid allocator calls (which can synchronise the device), and
-// hosts that own the GPU's memory budget themselves.  For them,
+// Some callers cannot allocate device memory: real-time loops that forbid
+// allocator calls (cudaMalloc and cudaFree can synchronise the device and
+// stall the stream that must keep up with the samples), and hosts that own
+// the GPU's memory budget themselves (a fixed plan made at start-up, where a
+// library allocating behind their back breaks the plan).  For them,
 // corr_xengine_noalloc computes the same visibilities as corr_xengine_dev
 // without any allocation: its partial-sum scratch is the file-scope device
 // array below, which every GPU that loads the library holds until exit.
 #include "corr.h"
 #include "corr_internal.h"
 
+#include <cstdint>
 #include <mutex>
 #include <string>
 
@@ -25,7 +27,9 @@ float* g_scratch_ptr[kMaxDevices] = {};
 std::mutex g_mu;
 
 // The device address of g_scratch on the current device, looked up once per
-// device (host code may not use the array's name as a device pointer).
+// device (host code may not use the array's name as a device pointer).  The
+// address is kept for the life of the process: after cudaDeviceReset the
+// cached value would be stale, so calls after a reset are not supported.
 int scratch_address(float** out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -59,6 +63,12 @@ extern "C" int corr_xengine_noalloc(const float* d_V, int n_spec, int n_in, int 
         corr::set_global_error("corr_xengine_noalloc: bad argument");
         return CORR_EINVAL;
     }
+    // The X-engine reads V as 16-byte vectors and the finaliser writes
+    // complex64 values: misaligned buffers are refused before any launch.
+    if ((reinterpret_cast<uintptr_t>(d_V) & 15) != 0 || (reinterpret_cast<uintptr_t>(d_vis) & 7) != 0) {
+        corr::set_global_error("corr_xengine_noalloc: d_V must be 16-byte and d_vis 8-byte aligned");
+        return CORR_EINVAL;
+    }
     const int n_in_pad = (n_in + 3) & ~3;
     const int nb = n_in_pad / 4;
     const int nt = nb * (nb + 1) / 2;
@@ -68,7 +78,9 @@ extern "C" int corr_xengine_noalloc(const float* d_V, int n_spec, int n_in, int 
                                "(one group needs blocks*32*n_chan floats <= 2^21)");
         return CORR_EINVAL;
     }
-    const long long max_groups = (long long)(kScratchFloats / per_group);
+    // Groups are a grid dimension of the X-engine launch (at most 65535).
+    long long max_groups = (long long)(kScratchFloats / per_group);
+    if (max_groups > 65535) max_groups = 65535;
     long long G = 64;
     long long groups = (n_spec + G - 1) / G;
     if (groups > max_groups) {
@@ -78,6 +90,14 @@ extern "C" int corr_xengine_noalloc(const float* d_V, int n_spec, int n_in, int 
     float* scratch = nullptr;
     int rc = scratch_address(&scratch);
     if (rc != CORR_OK) return rc;
+    // An error left by earlier, unrelated work is reported as such and left
+    // in place for its owner, not taken for a failure of these launches.
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) {
+        corr::set_global_error(std::string("corr_xengine_noalloc: CUDA error pending before the call: ") +
+                               cudaGetErrorString(e));
+        return CORR_ECUDA;
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     corr::XArgs x{};
     x.V = reinterpret_cast<const float2*>(d_V);
@@ -94,6 +114,11 @@ extern "C" int corr_xengine_noalloc(const float* d_V, int n_spec, int n_in, int 
     x.n_groups = (int)groups;
     x.part = scratch;
     corr::launch_xengine(x, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        corr::set_global_error(std::string("corr_xengine_noalloc: X-engine launch: ") + cudaGetErrorString(e));
+        return CORR_ECUDA;
+    }
     corr::FinArgs f{};
     f.part = scratch;
     f.n_slots = (int)groups;
@@ -103,9 +128,9 @@ extern "C" int corr_xengine_noalloc(const float* d_V, int n_spec, int n_in, int 
     f.scale = 1.0f / (float)n_spec;
     f.R = reinterpret_cast<float2*>(d_vis);
     corr::launch_finalize(f, st);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) {
-        corr::set_global_error(std::string("corr_xengine_noalloc launch: ") + cudaGetErrorString(e));
+        corr::set_global_error(std::string("corr_xengine_noalloc: finaliser launch: ") + cudaGetErrorString(e));
         return CORR_ECUDA;
     }
     return CORR_OK;

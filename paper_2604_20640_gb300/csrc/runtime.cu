@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <deque>
@@ -1175,7 +1176,13 @@ int corr_xengine_dev(corr_t h, const float* d_V, int n_spec, float* d_vis, void*
     if (!h) return fail(h, CORR_EINVAL, "NULL handle");
     DeviceGuard g(h->dev);
     if (!d_V || !d_vis || n_spec < 1) return fail(h, CORR_EINVAL, "bad argument");
-    const int G = 64;
+    // V is read as 16-byte vectors and R written as complex64.
+    if ((reinterpret_cast<uintptr_t>(d_V) & 15) != 0 || (reinterpret_cast<uintptr_t>(d_vis) & 7) != 0)
+        return fail(h, CORR_EINVAL, "d_V must be 16-byte and d_vis 8-byte aligned");
+    // One partial slot per group of G spectra; the groups are a grid
+    // dimension of the X-engine launch, so at most 65535 of them.
+    long long G = 64;
+    if ((n_spec + G - 1) / G > 65535) G = (n_spec + 65534) / 65535;
     const long long slots = (n_spec + G - 1) / G;
     if (slots > h->part_x_slots) {
         cudaFree(h->d_part_x);
@@ -1194,7 +1201,7 @@ int corr_xengine_dev(corr_t h, const float* d_V, int n_spec, float* d_vis, void*
     x.int_start = 0;
     x.int_end = n_spec;
     x.s_limit = n_spec;
-    x.G = G;
+    x.G = (int)G;
     x.j0 = 0;
     x.n_groups = (int)slots;
     x.part = h->d_part_x;

@@ -91,3 +91,18 @@ def test_result_buffer_validation_on_the_host():
                 torch.zeros((4, 8, 3, 6), dtype=torch.uint8)[..., ::2]):
         with pytest.raises(CorrError):
             check(me, bad, 4, np.uint8)
+
+
+def test_noalloc_refuses_misaligned_buffers_before_any_cuda_call(lib_path):
+    """corr_xengine_noalloc reads V as 16-byte vectors and writes complex64
+    results: a V pointer off a 16-byte boundary, or a result pointer off an
+    8-byte one, is refused with CORR_EINVAL on the host.  The check runs
+    before the first CUDA call, so it needs no GPU (the addresses are never
+    dereferenced)."""
+    import paper_2604_20640_gb300 as pkg
+    L = pkg.load_library()
+    good_v, good_r = 0x10000, 0x20000
+    for v, r in [(good_v + 8, good_r), (good_v + 4, good_r), (good_v, good_r + 4)]:
+        rc = L.corr_xengine_noalloc(v, 16, 4, 64, r, None)
+        assert rc == pkg.CORR_EINVAL
+        assert b"aligned" in L.corr_last_error(None)

@@ -144,6 +144,36 @@ def test_xengine_matches_oracle(n_in, n_chan, n_spec):
     assert np.all(np.einsum('kaa->ka', Rg).imag == 0)
 
 
+def test_xengine_dev_rejects_misaligned_buffers():
+    """V is read as 16-byte vectors: a complex64 view one element into a
+    buffer is refused on the host (CORR_EINVAL), before any launch."""
+    from paper_2604_20640_gb300 import CorrError, CORR_EINVAL
+    c = _corr(4, 1, 64, 4, 16)
+    buf = torch.zeros((1 + 16 * 64 * 4,), dtype=torch.complex64, device=DEV)
+    R = torch.empty((64, 4, 4), dtype=torch.complex64, device=DEV)
+    with pytest.raises(CorrError) as e:
+        c.xengine_dev(buf[1:], 16, R)
+    assert e.value.code == CORR_EINVAL
+
+
+def test_xengine_dev_long_stream_beyond_the_grid_limit():
+    """More than 64 x 65535 spectra: the partial-sum groups are lengthened so
+    that their count stays a legal grid dimension; the result still matches
+    the oracle (one channel, one input, so the buffer stays small)."""
+    n_spec = 64 * 65535 + 1000
+    rng = np.random.default_rng(5)
+    V = np.zeros((n_spec, 8, 4), dtype=np.complex64)
+    V[:, :, 0] = (rng.standard_normal((n_spec, 8)) + 1j * rng.standard_normal((n_spec, 8))).astype(np.complex64)
+    c = _corr(1, 1, 8, 4, 16)
+    R = torch.empty((8, 1, 1), dtype=torch.complex64, device=DEV)
+    c.xengine_dev(torch.from_numpy(V).to(DEV), n_spec, R)
+    torch.cuda.synchronize()
+    Ro = np.mean(np.abs(V[:, :, 0].astype(np.complex128)) ** 2, axis=0)
+    # 65535 partial slots summed in order in FP32: rounding grows like
+    # u sqrt(n) ~ 1.5e-5 here, so this check of the grid split allows 1e-4
+    assert np.max(np.abs(R.cpu().numpy()[:, 0, 0].real - Ro) / Ro) < 1e-4
+
+
 @pytest.mark.parametrize("window,n_chan,n_in", [(64, 256, 3), (64, 64, 1), (32, 128, 4), (8, 8, 2), (256, 512, 2)])
 def test_mad_flags_match_oracle(window, n_chan, n_in):
     rng = np.random.default_rng(window + n_chan)
