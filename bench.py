@@ -55,19 +55,26 @@ WORKLOADS = {
                     "requantised to int8 (tensor-core X, BF16 MMA) vs the plain FP32 path"),
 }
 
-# Stages reported by corr_stage_times, their kernels, and the algorithmic bytes
-# each moves per input sample (see the design notes):
-#   FIR  reads 1 B int8, writes z = (y_a, y_b) as FP32: 4 B;
-#   FFT  reads z (4 B) and writes one complex64 per channel per input (4 B);
-#   X    reads the channelised spectra (4 B); finalise / flag: per integration.
-#   requant reads the spectra (4 B) and writes one code per component (1 B
-#   e4m3, 2 B int8-as-BF16); the tensor-core Gram reads the codes.
+# Stages reported by corr_stage_times and their kernels.
 STAGES = ["fir", "fft", "xengine", "finalize", "flag", "requant", "gram"]
 KERNELS = {"fir": "fir_kernel<4>", "fft": "fft_kernel<M,0>", "xengine": "xengine_kernel",
            "finalize": "finalize_kernel", "flag": "mad_flag_kernel", "requant": "requant_kernel",
            "gram": "gram_kernel (tcgen05)"}
-BYTES_PER_SAMPLE = {"fir": 5.0, "fft": 8.0, "xengine": 4.0, "finalize": 0.0, "flag": 0.0, "requant": 6.0,
-                    "gram": 2.0}
+# Algorithmic bytes per input sample of each hot-path kernel, in the unit the
+# scope table's measurement section fixes: the whole hot path (PFB, FFT,
+# delays, X-engine, flagging) reads each int8 input sample once (1 B); on the
+# reduced-precision path the F-engine also writes one code per real sample
+# (1 B) and the tensor-core X-engine reads it back.  Every kernel of a stage
+# is credited with the bytes of the samples it processes.
+ALG_BYTES_PER_SAMPLE = {"fir": 1.0, "fft": 1.0, "xengine": 1.0, "finalize": 0.0, "flag": 0.0,
+                        "requant": 1.0, "gram": 1.0}
+# Bytes each kernel of this build actually moves per input sample, rings
+# included (FIR: 1 B in + 4 B of z = (y_a, y_b) out; FFT: 4 B of z in + one
+# complex64 per channel per input out; X-engine: the spectra back in;
+# requantiser: spectra in, one code per component out, int8 carried as BF16;
+# Gram: the codes).  Reported beside the algorithmic figure, not used for it.
+INTERMEDIATE_BYTES_PER_SAMPLE = {"fir": 5.0, "fft": 8.0, "xengine": 4.0, "finalize": 0.0, "flag": 0.0,
+                                 "requant": 6.0, "gram": 2.0}
 
 
 # DRAM read + write per input sample of a kernel, from one ncu capture of the
@@ -142,41 +149,169 @@ def _peaks():
         return {}
 
 
-def cpu_baseline(wl, n_integrations=None):
-    """Time the FP64 oracle, as it stands, on a bounded sample of the workload:
-    the first integrations of one stream (about 10-30 s of work), one thread."""
+def _oracle_job(job):
+    """One unit of oracle work in a spawned worker (the oracle runs only
+    here, on the host cores, never on the product path).
+
+    ("integration", path, i, n_chan, taps, n_int, tau, phi, compare):
+        fx.correlate on the samples integration i of the stream reads (one
+        extra frame behind it for the coarse advance), timed; with compare =
+        (vis, flags) of the GPU for integration 0, also the visibility error
+        (max relative Frobenius per channel) and the flags that differ
+        outside the 1e-4 T band.
+    ("rho", path, f_lo, s0, s1, n_chan, taps, tau, phi, inputs, chans, vis):
+        normalised coefficients of spectra [s0, s1) on the sampled inputs and
+        channels from the oracle F-engine over the slice the spectra read
+        (frames f_lo ...); returns max |rho_gpu - rho_oracle|.
+    """
+    import numpy as np
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    from oracle import fx_oracle as fx
+    kind = job[0]
+    if kind == "integration":
+        _, path, i, n_chan, taps, n_int, tau, phi, compare = job
+        M = 2 * n_chan
+        x = np.load(path, mmap_mode="r")
+        xs = np.ascontiguousarray(x[:, i * n_int * M:(i + 1) * n_int * M + M])
+        t0 = time.perf_counter()
+        R, F, T = fx.correlate(xs, n_chan, taps, n_int, tau, phi)
+        dt = time.perf_counter() - t0
+        out = {"seconds": dt, "bytes": int(n_int * M * xs.shape[0])}
+        if compare is not None:
+            vis, flags = compare
+            err = fx.rel_frobenius_per_channel(vis[None].astype(np.complex128), R[:1])
+            A = np.abs(R[:1])
+            bad = (flags[None] != F[:1]) & ~(np.abs(A - T[:1]) < 1e-4 * T[:1])
+            out.update({"vis_rel_frobenius_max": float(err.max()), "flags_differing_outside_band": int(bad.sum()),
+                        "flags_set": int(F[:1].sum())})
+        return out
+    if kind == "rho":
+        _, path, f_lo, s0, s1, n_chan, taps, tau, phi, inputs, chans, vis = job
+        x = np.load(path, mmap_mode="r")
+        V = []
+        for a in inputs:
+            Va = fx.f_engine(np.ascontiguousarray(x[a:a + 1]), n_chan, taps, tau[a:a + 1], phi[a:a + 1])[0]
+            V.append(Va[s0 - f_lo:s1 - f_lo][:, chans])
+        V = np.stack(V)
+        R = np.einsum('ask,bsk->kab', V, V.conj()) / (s1 - s0)
+        rho_o = fx.normalised_coefficients(R)
+        rho_g = fx.normalised_coefficients(vis.astype(np.complex128))
+        return {"rho_abs_err_max": float(np.abs(rho_g - rho_o).max())}
+    raise ValueError(kind)
+
+
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_pool(n):
+    """Spawned workers with one BLAS/OpenMP thread each (spawn, so that no
+    worker inherits a CUDA context)."""
+    import multiprocessing as mp
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    return mp.get_context("spawn").Pool(n)
+
+
+def _save_host(x_dev, lo, hi):
+    """Samples [lo, hi) of every input of a device stream, saved for the
+    oracle workers; returns the file path."""
+    import numpy as np
+    f = tempfile.NamedTemporaryFile(suffix=".npy", delete=False)
+    f.close()
+    np.save(f.name, x_dev[:, lo:hi].cpu().numpy())
+    return f.name
+
+
+def oracle_leg(wl, x_dev, spec, vis0, flags0):
+    """CPU baseline and visibility / flag error of a single-stream workload.
+
+    The FP64 oracle, as it stands, on the first integrations of the timed
+    stream itself: one integration on one thread (which also gives the error
+    of the GPU's integration 0), then one integration per host core at once
+    (throughput of all cores).  The 64-input workload's integrations take
+    minutes in the oracle's O(N^2 T) correlation, so it times a 256-spectrum
+    partial integration instead and takes no error here."""
+    import numpy as np
     W = WORKLOADS[wl]
-    M = 2 * W["n_chan"]
-    if n_integrations is None:
-        n_integrations = 4
-    samples = M * W["n_int"] * n_integrations
-    partial = False
+    M, n_int = 2 * W["n_chan"], W["n_int"]
+    cores = _host_cores()
+    n_avail = x_dev.shape[1] // (n_int * M)
+    tau, phi = np.asarray(spec.tau, np.float64), np.asarray(spec.phi, np.float64)
     if wl == "c3":
-        # 64-input integrations take minutes in the oracle: time 256 spectra
-        # (one partial integration; the work per sample is the same)
-        samples, partial = M * 256, True
-    code = (
-        "import sys, time, json, numpy as np\n"
-        "sys.path.insert(0, %r)\n"
-        "from fxsynth import config_c1, config_c2, config_c3, make_stream\n"
-        "from oracle import fx_oracle as fx\n"
-        "wl = %r\n"
-        "spec = (config_c2(seed=2000, n_samples=%d, M=%d) if wl == 'c2' else\n"
-        "        config_c3(seed=3000, n_samples=%d) if wl == 'c3' else config_c1(seed=1000, n_samples=%d))\n"
-        "x = make_stream(spec)\n"
-        "t0 = time.perf_counter()\n"
-        "R, F, T = fx.correlate(x, %d, %d, %d, spec.tau, spec.phi, partial=%r)\n"
-        "dt = time.perf_counter() - t0\n"
-        "print(json.dumps({'seconds': dt, 'bytes': int(x.size), 'n_int': int(R.shape[0])}))\n"
-    ) % (ROOT, wl, samples, M, samples, samples, W["n_chan"], W["taps"], W["n_int"], partial)
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
-    if r.returncode != 0:
-        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else "failed"}
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": d["bytes"] / d["seconds"] / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": "first %d spectra of one stream (%d MiB int8), FP64 numpy oracle, 1 thread, %.1f s"
-                      % (samples // M, d["bytes"] >> 20, d["seconds"])}
+        n_int_s = 256
+        path = _save_host(x_dev, 0, n_int_s * M + M)
+        pool = _oracle_pool(cores)
+        try:
+            one = pool.apply(_oracle_job, (("integration", path, 0, W["n_chan"], W["taps"], n_int_s, tau, phi, None),))
+            t0 = time.perf_counter()
+            outs = pool.map(_oracle_job, [("integration", path, 0, W["n_chan"], W["taps"], n_int_s, tau, phi, None)]
+                            * cores, chunksize=1)
+            wall = time.perf_counter() - t0
+        finally:
+            pool.close()
+            pool.join()
+            os.unlink(path)
+        return {"value": sum(o["bytes"] for o in outs) / wall / 1e9, "unit": "GB/s", "cores": cores,
+                "kind": "oracle", "value_1_core": one["bytes"] / one["seconds"] / 1e9,
+                "sample": "first 256 spectra of the timed stream (%d MiB int8) per core, %d cores at once "
+                          "(%.1f s wall); FP64 numpy oracle, one thread per process" % (one["bytes"] >> 20, cores, wall)}, None
+    n_par = max(1, min(cores, n_avail))
+    path = _save_host(x_dev, 0, min(x_dev.shape[1], n_par * n_int * M + M))
+    pool = _oracle_pool(n_par)
+    try:
+        cmp = (vis0, flags0)
+        one = pool.apply(_oracle_job, (("integration", path, 0, W["n_chan"], W["taps"], n_int, tau, phi, cmp),))
+        t0 = time.perf_counter()
+        outs = pool.map(_oracle_job, [("integration", path, i, W["n_chan"], W["taps"], n_int, tau, phi, None)
+                                      for i in range(n_par)], chunksize=1)
+        wall = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
+        os.unlink(path)
+    cpu = {"value": sum(o["bytes"] for o in outs) / wall / 1e9, "unit": "GB/s", "cores": n_par, "kind": "oracle",
+           "value_1_core": one["bytes"] / one["seconds"] / 1e9,
+           "sample": "integrations 0-%d of the timed stream (%d MiB int8 each), one per process on %d host "
+                     "cores at once (%.1f s wall; one integration on one core: %.1f s); FP64 numpy oracle"
+                     % (n_par - 1, one["bytes"] >> 20, n_par, wall, one["seconds"])}
+    err = {"integration": 0, "vis_rel_frobenius_max": one["vis_rel_frobenius_max"], "vis_bar": 1e-5,
+           "flags_differing_outside_band": one["flags_differing_outside_band"], "flags_set": one["flags_set"],
+           "flag_band": "|A - T| < 1e-4 T"}
+    return cpu, err
+
+
+def rho_error(x_dev, spec, n_chan, taps, n_int, vis_dev, ints, n_inputs=16, chans=(0, 3, 100, 511, 512, 900, 1023)):
+    """max |rho_gpu - rho_oracle| on the first n_inputs inputs and sampled
+    channels of the given integrations, from the oracle F-engine over the
+    slice of the timed stream each integration reads (spawned workers)."""
+    import numpy as np
+    M = 2 * n_chan
+    tau, phi = np.asarray(spec.tau, np.float64), np.asarray(spec.phi, np.float64)
+    inputs = list(range(n_inputs))
+    chans = [c for c in chans if c < n_chan]
+    jobs, paths = [], []
+    for i in ints:
+        s0, s1 = i * n_int, (i + 1) * n_int
+        f_lo = max(0, s0 - taps)
+        path = _save_host(x_dev[:n_inputs], f_lo * M, min(x_dev.shape[1], (s1 + 2) * M))
+        paths.append(path)
+        vis = vis_dev[i, chans][:, :n_inputs, :n_inputs].cpu().numpy()
+        jobs.append(("rho", path, f_lo, s0, s1, n_chan, taps, tau, phi, inputs, chans, vis))
+    pool = _oracle_pool(len(jobs))
+    try:
+        outs = pool.map(_oracle_job, jobs, chunksize=1)
+    finally:
+        pool.close()
+        pool.join()
+        for p in paths:
+            os.unlink(p)
+    return {"integrations": list(ints), "inputs": n_inputs, "channels": chans,
+            "rho_abs_err_max": max(o["rho_abs_err_max"] for o in outs), "rho_bar": 5e-3}
 
 
 def c4_cpu_baseline():
@@ -234,47 +369,59 @@ def run_reference_c5(args):
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle, as it stands, on the host cores.
+    Each step correlates one integration of the workload's stream per host
+    core, all cores at once (one process each, one BLAS thread each)."""
     if rank != 0:
         return
     if args.workload == "c5":
         run_reference_c5(args)
         return
-    W = WORKLOADS[args.workload]
+    import numpy as np
+    from fxsynth import config_c1, config_c2, config_c3, make_stream
+    wl = args.workload if args.workload in ("c1", "c2", "c3") else "c2"
+    W = WORKLOADS[wl]
     M = 2 * W["n_chan"]
-    samples = M * W["n_int"]
-    code = (
-        "import sys, time, json, numpy as np\n"
-        "sys.path.insert(0, %r)\n"
-        "from fxsynth import config_c1, config_c2, make_stream\n"
-        "from oracle import fx_oracle as fx\n"
-        "spec = (config_c2(seed=2000, n_samples=%d, M=%d) if %r == 'c2' else config_c1(seed=1000, n_samples=%d))\n"
-        "x = make_stream(spec)\n"
-        "ts = []\n"
-        "for i in range(%d):\n"
-        "    t0 = time.perf_counter()\n"
-        "    fx.correlate(x, %d, %d, %d, spec.tau, spec.phi)\n"
-        "    ts.append(time.perf_counter() - t0)\n"
-        "print(json.dumps({'times': ts[%d:], 'bytes': int(x.size)}))\n"
-    ) % (ROOT, samples, M, args.workload, samples, args.warmup + args.steps, W["n_chan"], W["taps"],
-         W["n_int"], args.warmup)
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
-    if r.returncode != 0:
-        print(json.dumps({"impl": "reference", "unavailable": "oracle run failed: " +
-                          (r.stderr.strip().splitlines() or ["?"])[-1]}))
+    n_int = W["n_int"] if wl != "c3" else 256
+    samples = M * n_int + M
+    spec = (config_c2(seed=2000, n_samples=samples, M=M) if wl == "c2" else
+            config_c3(seed=3000, n_samples=samples) if wl == "c3" else config_c1(seed=1000, n_samples=samples))
+    x = make_stream(spec)
+    f = tempfile.NamedTemporaryFile(suffix=".npy", delete=False)
+    f.close()
+    np.save(f.name, x)
+    cores = _host_cores()
+    tau, phi = np.asarray(spec.tau, np.float64), np.asarray(spec.phi, np.float64)
+    job = ("integration", f.name, 0, W["n_chan"], W["taps"], n_int, tau, phi, None)
+    try:
+        pool = _oracle_pool(cores)
+        try:
+            walls, nbytes = [], 0
+            for i in range(args.warmup + args.steps):
+                t0 = time.perf_counter()
+                outs = pool.map(_oracle_job, [job] * cores, chunksize=1)
+                if i >= args.warmup:
+                    walls.append(time.perf_counter() - t0)
+                nbytes = sum(o["bytes"] for o in outs)
+        finally:
+            pool.close()
+            pool.join()
+    except Exception as e:            # the arm reports, it does not crash the driver
+        print(json.dumps({"impl": "reference", "unavailable": "oracle run failed: %s" % e}))
         return
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    ms = 1e3 * sum(d["times"]) / len(d["times"])
-    val = d["bytes"] / (ms * 1e-3) / 1e9
+    finally:
+        os.unlink(f.name)
+    ms = 1e3 * sum(walls) / len(walls)
+    val = nbytes / (ms * 1e-3) / 1e9
+    sample = ("per step: one %s (%d MiB int8) per host core, %d cores at once, FP64 numpy oracle, one thread "
+              "per process" % ("integration" if wl != "c3" else "256-spectrum partial integration",
+                               (nbytes // cores) >> 20, cores))
     out = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload + ": " + W["desc"], "sample": "one integration per step",
-                   "l2": "host CPU path"},
-        "cpu_baseline": {"value": val, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": "one integration (%d MiB int8) per step, FP64 numpy oracle, 1 thread"
-                                   % (d["bytes"] >> 20)},
+        "config": {"workload": wl + ": " + W["desc"], "sample": sample, "l2": "host CPU path"},
+        "cpu_baseline": {"value": val, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
@@ -336,7 +483,12 @@ def run_batched(args, rank, world, local):
         ms = max_over_ranks(ms, dist if world > 1 else None, dev)
         return ms
 
-    # plain: one stream after another, no graph, default tuning
+    # plain: one FP32 stream after another, no graph, each at its own
+    # autotuned ring (the same tuning step the chosen form gets)
+    cache_plain = os.path.join(tempfile.gettempdir(), "corr_tune_plain_%d.txt" % os.getpid())
+    for c, x in zip(plains, xs):
+        c.autotune(x, cache_plain)
+
     def plain():
         for c, x, v, f in zip(plains, xs, vis, flags):
             c.run_dev(x, v, f)
@@ -359,9 +511,7 @@ def run_batched(args, rank, world, local):
     # members run once more one by one (untimed) with every stage bracketed
     st_ms, st_n, st_bytes = [0.0] * len(STAGES), [0] * len(STAGES), [0.0] * len(STAGES)
     for c, x, v, f, prec in zip(members, xs, vis, flags, precs):
-        bps = dict(BYTES_PER_SAMPLE)
-        if prec == 2:
-            bps.update(requant=5.0, gram=1.0)
+        bps = dict(ALG_BYTES_PER_SAMPLE)
         c.set_option("stage_timing", 1)
         c.stage_times()
         c.run_dev(x, v, f)
@@ -374,12 +524,15 @@ def run_batched(args, rank, world, local):
             st_bytes[i] += bps[k] * n_used if m_n[i] else 0.0
     tot = sum(st_ms) or 1.0
     share = {k: st_ms[i] / tot for i, k in enumerate(STAGES)}
-    di = max((i for i, k in enumerate(STAGES) if BYTES_PER_SAMPLE[k] > 0), key=lambda i: st_ms[i])
+    di = max((i for i, k in enumerate(STAGES) if ALG_BYTES_PER_SAMPLE[k] > 0), key=lambda i: st_ms[i])
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs") or 6800.0
     avg_ms = st_ms[di] / max(1, st_n[di])
     bpl = st_bytes[di] / max(1, st_n[di])
+    inter = sum(INTERMEDIATE_BYTES_PER_SAMPLE[STAGES[di]] * (x.shape[1] // c.M) * c.M * c.n_in
+                for c, x in zip(members, xs)) / max(1, st_n[di])
     roofline = {"kernel": KERNELS[STAGES[di]], "bound": "hbm", "achieved": bpl / (avg_ms * 1e-3) / 1e9,
+                "bytes_per_sample": ALG_BYTES_PER_SAMPLE[STAGES[di]], "intermediate_bytes_per_launch": inter,
                 "peak": hbm, "unit": "GB/s", "frac": bpl / (avg_ms * 1e-3) / 1e9 / hbm, "traffic": None,
                 "peak_source": "measured" if peaks else "fallback", "bytes_per_launch": bpl,
                 "avg_launch_ms": avg_ms, "launches": st_n[di], "stage_share": share,
@@ -576,17 +729,19 @@ def run_flagger(args, rank, world, local):
     bf16 = peaks.get("bf16_tflops") or 1900.0
     flops_tile = 2.0 * 64 * 256 * 25 * (1 * 32 + 32 * 32 + 32 * 32 + 32 * 1)
     n_samples_pass = bytes_step * args.steps
-    # in the flagging pass the FFT reads z (4 B/sample) and keeps only the
-    # powers (no spectra written)
+    # algorithmic: each input sample read once (1 B); this build's kernels
+    # move more: the FIR writes z (4 B/sample), the FFT reads it back and
+    # keeps only the powers (no spectra written)
     bps_c5 = {"fir": 5.0, "fft": 4.0}
-    bytes_per_launch = bps_c5[dom] * n_samples_pass / max(1, stage_n[di])
+    bytes_per_launch = ALG_BYTES_PER_SAMPLE[dom] * n_samples_pass / max(1, stage_n[di])
     avg_ms = stage_ms[di] / max(1, stage_n[di])
     achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
     kname = "fft_kernel<%d,2> (power mode)" % (2 * W["n_chan"]) if dom == "fft" else KERNELS[dom]
     roofline = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": None, "peak_source": "measured" if peaks else "fallback",
-                "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms, "launches": stage_n[di],
-                "stage_share": share,
+                "bytes_per_launch": bytes_per_launch, "bytes_per_sample": ALG_BYTES_PER_SAMPLE[dom],
+                "intermediate_bytes_per_launch": bps_c5[dom] * n_samples_pass / max(1, stage_n[di]),
+                "avg_launch_ms": avg_ms, "launches": stage_n[di], "stage_share": share,
                 "flagger": {"bound": "tensor", "ms": flag_ms, "tiles": B,
                             "achieved_tflops": flops_tile * B / (flag_ms * 1e-3) / 1e12, "peak": bf16,
                             "unit": "TFLOP/s", "frac": flops_tile * B / (flag_ms * 1e-3) / 1e12 / bf16,
@@ -668,6 +823,8 @@ def main():
     ap.add_argument("--precision", type=int, default=None,
                     help="0 FP32 CUDA-core X, 1 int8 / 2 e4m3 tensor-core X (default: FP32, int8 for c3)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
+    ap.add_argument("--no-chosen", action="store_true",
+                    help="c2: skip the 64-input tensor-core form added to the line (chosen_form)")
     ap.add_argument("--train-steps", type=int, default=C5_TRAIN_STEPS, help="c5: Adam steps before timing")
     ap.add_argument("--ring-mb", type=int, default=0, help="c1-c3: spectrum ring size (MiB, 0 = autotuned)")
     ap.add_argument("--chunk", type=int, default=0, help="c1-c3 e2e: samples per input per push (0 = workload default)")
@@ -690,7 +847,6 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_2604_20640_gb300 import Correlator
     from paper_2604_20640_gb300.replicas import max_over_ranks, job_rate
     from fxsynth.streams_torch import make_stream_torch
 
@@ -703,50 +859,113 @@ def main():
         if world > 1:
             dist.barrier()
 
-    W = WORKLOADS[args.workload]
+    wl = args.workload
+    W = WORKLOADS[wl]
     S = args.samples or W["samples"]
     n_in = W["n_ant"] * W["n_pol"]
-    spec = _spec(args.workload, rank, S)
+    spec = _spec(wl, rank, S)
     x = make_stream_torch(spec, device=dev)
     if args.bits == 16:
         x = x.to(torch.int16) * 64          # 14-bit values in int16 containers
-    prec = args.precision if args.precision is not None else (1 if args.workload == "c3" else 0)
+    prec = args.precision if args.precision is not None else (1 if wl == "c3" else 0)
+    m = measure_stream(args, wl, prec, x, spec, dev, world, barrier, clocks=True)
+    bytes_step = n_in * S * (args.bits // 8)
+    ms = max_over_ranks(m["ms"], dist if world > 1 else None, dev)
+    value = job_rate(bytes_step, world, ms)
+
+    # ---- the plain FP32 path on the same stream, at its own autotuned ring ----
+    plain = None
+    if prec != 0 and not args.no_plain:
+        mp_ = measure_stream(args, wl, 0, x, spec, dev, world, barrier, clocks=False, stages=False)
+        pms = max_over_ranks(mp_["ms"], dist if world > 1 else None, dev)
+        plain = {"value": job_rate(bytes_step, world, pms), "ms_per_step": pms, "ratio": ms and pms / ms,
+                 "tuning": mp_["tuning"]}
+    elif prec == 0:
+        plain = {"value": value, "ms_per_step": ms, "ratio": 1.0,
+                 "note": "this workload is defined on the FP32 path (CUDA-core X-engine): the chosen form and "
+                         "the plain path are the same here; see chosen_form for the tensor-core form"}
+
+    # ---- end to end through the public host API ----
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(args, wl, prec, x, spec, m["tuning"], dev, world, dist)
+
+    # ---- oracle: CPU baseline and the error of the timed stream's results ----
+    cpu, error = None, None
+    if rank == 0 and not args.no_cpu:
+        if wl == "c3":
+            cpu, _ = oracle_leg(wl, x, spec, None, None)
+            error = rho_error(x, spec, W["n_chan"], W["taps"], W["n_int"], m["vis"], (0, m["vis"].shape[0] - 1))
+        else:
+            cpu, error = oracle_leg(wl, x, spec, m["vis"][0].cpu().numpy(), m["flags"][0].cpu().numpy())
+    del m["vis"], m["flags"]
+
+    # ---- the tensor-core form on the 64-input workload beside its plain path ----
+    chosen = None
+    if wl == "c2" and args.bits == 8 and not args.no_chosen:
+        chosen = chosen_form(args, rank, dev, world, barrier, dist)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl + ": " + W["desc"],
+                       "path": ["plain FP32 (CUDA-core X)", "int8 requantised, tcgen05 X (BF16 MMA)",
+                                "e4m3 requantised, tcgen05 X"][prec],
+                       "samples_per_input": S, "sample_bits": args.bits,
+                       "tuning": {"ring_mb": m["tuning"][0], "fir_spt": m["tuning"][1]},
+                       "l2": "inputs (%d MiB/step) larger than L2" % (bytes_step >> 20),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "gpu_launches": m["launches"], "clocks": m["clocks"], "roofline": m["roofline"], "e2e": e2e,
+            "cpu_baseline": cpu, "error": error, "plain_fp32": plain,
+        }
+        if chosen is not None:
+            out["chosen_form"] = chosen
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def measure_stream(args, wl, prec, x, spec, dev, world, barrier, clocks=True, stages=True):
+    """Time corr_run_dev over the device-resident stream x (autotuned ring
+    unless --ring-mb is given): warm-up, one untimed step with every stage
+    bracketed (stage shares, dominant kernel), then the timed steps with only
+    the dominant kernel's launches bracketed.  Returns the timing, tuning,
+    roofline entry and the last step's results."""
+    import torch
+    from paper_2604_20640_gb300 import Correlator
+    W = WORKLOADS[wl]
+    S = x.shape[1]
+    n_in = W["n_ant"] * W["n_pol"]
     ring = {"ring_mb": args.ring_mb} if args.ring_mb else {}
     c = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"], precision=prec,
                    sample_bits=args.bits, **ring)
     if not args.ring_mb:
-        # ring size and FIR run length from the library's autotuner (untimed)
-        c.autotune(x)
+        c.autotune(x)                  # ring size and FIR run length (untimed)
     tuning = c.tuning()
     c.set_delays(spec.tau, spec.phi)
     n_intg = c.n_integrations(S)
     vis = torch.empty((n_intg, W["n_chan"], n_in, n_in), dtype=torch.complex64, device=dev)
     flags = torch.empty((n_intg, W["n_chan"], n_in, n_in), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-
     for _ in range(args.warmup):
         c.run_dev(x, vis, flags)
     torch.cuda.synchronize(dev)
-    # One untimed step with every stage bracketed by events gives the stage
-    # shares and the dominant kernel; the timed steps bracket only that
-    # kernel's launches (fewer events disturb the pipeline less).
-    bps = dict(BYTES_PER_SAMPLE)
-    if args.bits == 16:
-        bps["fir"] += 1.0          # the FIR reads 2 bytes per sample
-    if prec == 2:
-        bps.update(requant=5.0, gram=1.0)
-    c.set_option("stage_timing", 1)
-    c.stage_times()
-    c.run_dev(x, vis, flags)
-    share_ms, _ = c.stage_times()
-    total_stage = sum(share_ms) or 1.0
-    share = {k: share_ms[i] / total_stage for i, k in enumerate(STAGES)}
-    dom = max((k for k in STAGES if bps[k] > 0), key=lambda k: share[k])
-    di = STAGES.index(dom)
-    c.set_option("stage_mask", 1 << di)
+    share, di = None, None
+    if stages:
+        c.set_option("stage_timing", 1)
+        c.stage_times()
+        c.run_dev(x, vis, flags)
+        share_ms, _ = c.stage_times()
+        total_stage = sum(share_ms) or 1.0
+        share = {k: share_ms[i] / total_stage for i, k in enumerate(STAGES)}
+        dom = max((k for k in STAGES if ALG_BYTES_PER_SAMPLE[k] > 0), key=lambda k: share[k])
+        di = STAGES.index(dom)
+        c.set_option("stage_mask", 1 << di)
     barrier()
     torch.cuda.synchronize(dev)
-    clocks = ClockSampler(local)
+    sampler = ClockSampler(dev.index) if clocks else None
     l0 = c.launches
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -755,130 +974,147 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize(dev)
     barrier()
-    clk = clocks.stop()
+    clk = sampler.stop() if sampler else None
     launches = c.launches - l0
     ms = e0.elapsed_time(e1) / args.steps
-    stage_ms, stage_n = c.stage_times()
-    c.set_option("stage_timing", 0)
-    c.set_option("stage_mask", 127)
-    ms = max_over_ranks(ms, dist if world > 1 else None, dev)
-    bytes_step = n_in * S * (args.bits // 8)
-    value = job_rate(bytes_step, world, ms)
+    roofline = None
+    if stages:
+        stage_ms, stage_n = c.stage_times()
+        c.set_option("stage_timing", 0)
+        c.set_option("stage_mask", 127)
+        roofline = _roofline(wl, prec, args, dom, di, share, stage_ms, stage_n, S, n_in)
+    c.close()
+    return {"ms": ms, "tuning": tuning, "launches": launches, "clocks": clk, "roofline": roofline,
+            "vis": vis, "flags": flags}
 
-    # ---- the plain FP32 path on the same stream (the metric's denominator) ----
-    plain = None
-    if prec != 0 and not args.no_plain:
-        cp = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"], sample_bits=args.bits)
-        cp.set_delays(spec.tau, spec.phi)
-        for _ in range(max(1, args.warmup)):
-            cp.run_dev(x, vis, flags)
-        torch.cuda.synchronize(dev)
-        barrier()
-        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        p0.record(stream)
-        for _ in range(args.steps):
-            cp.run_dev(x, vis, flags)
-        p1.record(stream)
-        torch.cuda.synchronize(dev)
-        pms = p0.elapsed_time(p1) / args.steps
-        pms = max_over_ranks(pms, dist if world > 1 else None, dev)
-        pval = job_rate(bytes_step, world, pms)
-        plain = {"value": pval, "ms_per_step": pms, "ratio": value / pval}
-        cp.close()
 
-    # ---- end to end through the public host API ----
-    e2e = None
-    if not args.no_e2e:
-        # The host issues every launch of the push path, once per ring pass,
-        # so it takes a ring of at least 128 MiB whatever the device-resident
-        # tuning chose (small rings make the pushes launch-bound).
-        ring_e2e = args.ring_mb or max(tuning[0], 128)
-        ce = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"], chunk=args.chunk or W["chunk"],
-                        precision=prec, sample_bits=args.bits, ring_mb=ring_e2e, fir_spt=tuning[1])
-        ce.set_delays(spec.tau, spec.phi)
-        host = torch.empty((n_in, S), dtype=x.dtype, pin_memory=True)
-        host.copy_(x)
-        chunk = args.chunk or W["chunk"]
-        # results land by DMA in pinned buffers the loop reuses
-        vis_h = torch.empty((n_intg + 1, W["n_chan"], n_in, n_in), dtype=torch.complex64, pin_memory=True)
-        flags_h = torch.empty((n_intg + 1, W["n_chan"], n_in, n_in), dtype=torch.uint8, pin_memory=True)
-
-        phase = [0.0, 0.0]          # host seconds in the pushes / in flush + pops
-
-        def e2e_step():
-            ta = time.perf_counter()
-            for p in range(0, S, chunk):
-                ce.push(host[:, p:p + chunk])
-            tb = time.perf_counter()
-            ce.flush()
-            v = ce.get_vis(out=vis_h)
-            f = ce.get_flags(out=flags_h)
-            assert v.shape[0] == f.shape[0] >= n_intg
-            ce.reset()
-            phase[0] += tb - ta
-            phase[1] += time.perf_counter() - tb
-            return v, f
-
-        for _ in range(max(1, args.warmup)):
-            e2e_step()
-        barrier()
-        phase[:] = [0.0, 0.0]
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            v, f = e2e_step()
-        t1 = time.perf_counter()
-        barrier()
-        ems = (t1 - t0) * 1e3 / args.steps
-        ems = max_over_ranks(ems, dist if world > 1 else None, dev)
-        e2e = {"value": job_rate(bytes_step, world, ems), "unit": "GB/s", "ring_mb": ring_e2e,
-               "h2d_bytes_per_step": bytes_step,
-               "d2h_bytes_per_step": int(v.numel() * v.element_size() + f.numel() * f.element_size()),
-               "ms_per_step": ems, "push_ms": phase[0] * 1e3 / args.steps,
-               "flush_pop_ms": phase[1] * 1e3 / args.steps}
-        ce.close()
-        del host
-
-    # ---- roofline of the dominant kernel, from the live per-stage events ----
+def _roofline(wl, prec, args, dom, di, share, stage_ms, stage_n, S, n_in):
+    """Roofline entry of the dominant kernel from its live CUDA-event times:
+    algorithmic bytes per launch (the samples the timed launches processed x
+    the per-sample figure) over the average launch duration."""
+    W = WORKLOADS[wl]
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs")
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
+    es = args.bits // 8
     n_spec = S // (2 * W["n_chan"])
     samples_timed = args.steps * n_spec * 2 * W["n_chan"] * n_in
-    bytes_per_launch = bps[dom] * samples_timed / max(1, stage_n[di])
-    avg_ms = stage_ms[di] / max(1, stage_n[di])
+    launches = max(1, stage_n[di])
+    alg = ALG_BYTES_PER_SAMPLE[dom] * (es if dom in ("fir", "fft", "xengine") else 1)
+    inter = dict(INTERMEDIATE_BYTES_PER_SAMPLE)
+    if es == 2:
+        inter["fir"] += 1.0
+    if prec == 2:
+        inter.update(requant=5.0, gram=1.0)
+    bytes_per_launch = alg * samples_timed / launches
+    avg_ms = stage_ms[di] / launches
     achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
-    tps = TRAFFIC_PER_SAMPLE.get((args.workload, dom))
-    traffic = tps * samples_timed / max(1, stage_n[di]) if tps and prec == 0 else None
+    tps = TRAFFIC_PER_SAMPLE.get((wl, dom))
+    traffic = tps * samples_timed / launches if tps and prec == 0 and es == 1 else None
     kname = KERNELS[dom]
     if dom == "fft":
         # mode 3: spectra ring pair-major (FP32 path with n_in_pad <= 8); 0: channel-major
         kname = "fft_kernel<%d,%d>" % (2 * W["n_chan"], 3 if prec == 0 and (n_in + 3) // 4 * 4 <= 8 else 0)
-    roofline = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_src,
-                "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms, "launches": stage_n[di],
-                "stage_share": share}
+    return {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_src,
+            "bytes_per_launch": bytes_per_launch, "bytes_per_sample": alg,
+            "intermediate_bytes_per_launch": inter[dom] * samples_timed / launches,
+            "avg_launch_ms": avg_ms, "launches": stage_n[di], "stage_share": share}
 
-    if rank == 0:
-        cpu = None if args.no_cpu else cpu_baseline(args.workload)
-        out = {
-            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload + ": " + W["desc"],
-                       "path": ["plain FP32 (CUDA-core X)", "int8 requantised, tcgen05 X (BF16 MMA)",
-                                "e4m3 requantised, tcgen05 X"][prec],
-                       "samples_per_input": S, "sample_bits": args.bits,
-                       "tuning": {"ring_mb": tuning[0], "fir_spt": tuning[1]},
-                       "l2": "inputs (%d MiB/step) larger than L2" % (bytes_step >> 20),
-                       "parallelism": "replicas" if world > 1 else "single"},
-            "gpu_launches": launches, "clocks": clk, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
-        }
-        if plain is not None:
-            out["plain_fp32"] = plain
-        print(json.dumps(out))
+
+def end_to_end(args, wl, prec, x, spec, tuning, dev, world, dist):
+    """The same stream through corr_push from pinned host memory, then
+    corr_flush and corr_get_vis / corr_get_flags into pinned buffers, per step."""
+    import torch
+    from paper_2604_20640_gb300 import Correlator
+    from paper_2604_20640_gb300.replicas import max_over_ranks, job_rate
+    W = WORKLOADS[wl]
+    S = x.shape[1]
+    n_in = W["n_ant"] * W["n_pol"]
+    bytes_step = n_in * S * (args.bits // 8)
+    # The host issues every launch of the push path, once per ring pass, so
+    # it takes a ring of at least 128 MiB whatever the device-resident tuning
+    # chose (small rings make the pushes launch-bound).
+    ring_e2e = args.ring_mb or max(tuning[0], 128)
+    chunk = args.chunk or W["chunk"]
+    ce = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"], chunk=chunk,
+                    precision=prec, sample_bits=args.bits, ring_mb=ring_e2e, fir_spt=tuning[1])
+    ce.set_delays(spec.tau, spec.phi)
+    host = torch.empty((n_in, S), dtype=x.dtype, pin_memory=True)
+    host.copy_(x)
+    n_intg = S // (2 * W["n_chan"]) // W["n_int"]
+    # results land by DMA in pinned buffers the loop reuses
+    vis_h = torch.empty((n_intg + 1, W["n_chan"], n_in, n_in), dtype=torch.complex64, pin_memory=True)
+    flags_h = torch.empty((n_intg + 1, W["n_chan"], n_in, n_in), dtype=torch.uint8, pin_memory=True)
+    phase = [0.0, 0.0]          # host seconds in the pushes / in flush + pops
+
+    def e2e_step():
+        ta = time.perf_counter()
+        for p in range(0, S, chunk):
+            ce.push(host[:, p:p + chunk])
+        tb = time.perf_counter()
+        ce.flush()
+        v = ce.get_vis(out=vis_h)
+        f = ce.get_flags(out=flags_h)
+        assert v.shape[0] == f.shape[0] >= n_intg
+        ce.reset()
+        phase[0] += tb - ta
+        phase[1] += time.perf_counter() - tb
+        return v, f
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
     if world > 1:
-        dist.destroy_process_group()
+        dist.barrier()
+    phase[:] = [0.0, 0.0]
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, f = e2e_step()
+    t1 = time.perf_counter()
+    if world > 1:
+        dist.barrier()
+    ems = (t1 - t0) * 1e3 / args.steps
+    ems = max_over_ranks(ems, dist if world > 1 else None, dev)
+    out = {"value": job_rate(bytes_step, world, ems), "unit": "GB/s", "ring_mb": ring_e2e,
+           "h2d_bytes_per_step": bytes_step,
+           "d2h_bytes_per_step": int(v.numel() * v.element_size() + f.numel() * f.element_size()),
+           "ms_per_step": ems, "push_ms": phase[0] * 1e3 / args.steps,
+           "flush_pop_ms": phase[1] * 1e3 / args.steps}
+    ce.close()
+    del host
+    return out
+
+
+def chosen_form(args, rank, dev, world, barrier, dist):
+    """The metric's chosen form where the X-engine is a dense contraction:
+    the 64-input workload (2^26 int8 samples per input, 1024 channels,
+    n_int 4096) with int8 codes on the tcgen05 X-engine, against the plain
+    FP32 path on the same stream, both at their own autotuned rings, with the
+    normalised-coefficient error of the chosen form against the oracle."""
+    from paper_2604_20640_gb300.replicas import max_over_ranks, job_rate
+    from fxsynth.streams_torch import make_stream_torch
+    W = WORKLOADS["c3"]
+    S = W["samples"]
+    n_in = W["n_ant"] * W["n_pol"]
+    spec = _spec("c3", rank, S)
+    x = make_stream_torch(spec, device=dev)
+    sub = argparse.Namespace(**vars(args))
+    sub.bits = 8
+    mc = measure_stream(sub, "c3", 1, x, spec, dev, world, barrier, clocks=False)
+    mp_ = measure_stream(sub, "c3", 0, x, spec, dev, world, barrier, clocks=False, stages=False)
+    bytes_step = n_in * S
+    ms = max_over_ranks(mc["ms"], dist if world > 1 else None, dev)
+    pms = max_over_ranks(mp_["ms"], dist if world > 1 else None, dev)
+    out = {"workload": "c3: " + W["desc"], "value": job_rate(bytes_step, world, ms), "ms_per_step": ms,
+           "plain_fp32": {"value": job_rate(bytes_step, world, pms), "ms_per_step": pms,
+                          "tuning": mp_["tuning"]},
+           "ratio": pms / ms, "tuning": mc["tuning"], "gpu_launches": mc["launches"],
+           "roofline": mc["roofline"]}
+    if rank == 0 and not args.no_cpu:
+        out["error"] = rho_error(x, spec, W["n_chan"], W["taps"], W["n_int"], mc["vis"], (0, mc["vis"].shape[0] - 1))
+    del mc["vis"], mc["flags"], mp_["vis"], mp_["flags"], x
+    return out
 
 
 if __name__ == "__main__":
