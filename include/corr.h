@@ -92,8 +92,10 @@ const char* corr_last_error(corr_t h);
  *                 channel) fixed per integration, correlated on tcgen05
  *                 tensor cores (n_in <= 64).  Scales: first integration from
  *                 the mean power of its first min(n_int, 64) spectra
- *                 (sigma = sqrt(P/2)/g, g = 32 int8, 64 e4m3), later ones
- *                 from the previous integration's autocorrelations.
+ *                 (sigma = sqrt(P_c)/g with P_c the power of one component:
+ *                 P/2, or P in the real DC channel; g = 24 int8, 64 e4m3),
+ *                 later ones from the previous integration's
+ *                 autocorrelations.
  *   "result_slots" (default 8)               pinned result FIFO depth (grows)
  *   "stage_timing" (0/1, default 0; may change at any time)  per-stage events
  *   "stage_mask"   (bit mask, default 127 = all; may change at any time)

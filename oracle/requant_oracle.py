@@ -14,10 +14,16 @@ is the build's own; each reading is also listed in the design notes):
 * int8: round half to even, saturate to [-127, 127]; e4m3: round half to
   even onto the e4m3 grid (3 mantissa bits, exponent bias 7, subnormals
   down to 2^-9), saturate to +-448.
-* Scales: sigma_a[k] = sqrt(P_a[k] / 2) / g with P the mean power |V|^2 of
-  the input/channel, g = 32 (int8) or 64 (e4m3).  The first integration
-  takes P from its first min(n_int, 64) spectra; each later integration
-  from the previous integration's autocorrelation R_aa[k].
+* Scales: sigma_a[k] = sqrt(P_c) / g with P_c the expected power of one
+  component (real or imaginary part) of V_a[k]: P_a[k] / 2 for 0 < k
+  (a circular complex value splits its power evenly), P_a[k] itself for
+  the DC channel k = 0 (the zero-frequency bin of a real transform is
+  real), where P is the mean power |V|^2 of the input/channel; g = 24
+  (int8: saturation at 127 sits 5.3 standard deviations out, so rare joint
+  extremes of two inputs in one spectrum are not clipped) or 64 (e4m3:
+  448 at 7 standard deviations).  The first integration takes P from its
+  first min(n_int, 64) spectra; each later integration from the previous
+  integration's autocorrelation R_aa[k].
 * The codes quantise the channelised voltages after the coarse delay but
   before the fine-delay / instrument-phase factor of Eq. 1; that factor is
   constant within an integration, so it multiplies the integrated sum,
@@ -33,7 +39,7 @@ import numpy as np
 
 from . import fx_oracle as fx
 
-GAIN = {"int8": 32.0, "e4m3": 64.0}
+GAIN = {"int8": 24.0, "e4m3": 64.0}
 PREPASS_SPECTRA = 64
 
 
@@ -94,8 +100,12 @@ def visibilities_from_gram(G: np.ndarray, N: int) -> np.ndarray:
 
 
 def scales_from_power(P: np.ndarray, dtype: str) -> np.ndarray:
-    P = np.asarray(P, np.float64)
-    s = np.sqrt(np.maximum(P, 0.0) / 2.0) / GAIN[dtype]
+    """sigma[..., k] = sqrt(component power) / g for mean powers P[..., k]
+    (last axis: channel k = 0 .. n_chan-1); unit scale where P = 0."""
+    P = np.maximum(np.asarray(P, np.float64), 0.0)
+    comp = P / 2.0
+    comp[..., 0] = P[..., 0]                 # DC: the real part carries all of it
+    s = np.sqrt(comp) / GAIN[dtype]
     return np.where(s > 0, s, 1.0)
 
 

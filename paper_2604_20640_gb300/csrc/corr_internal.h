@@ -130,6 +130,11 @@ struct FinQArgs {
     float2* R;
 };
 
+// Requantisation gains g (sigma = sqrt(component power) / g): int8 codes
+// saturate at 127 = 5.3 g / 24 standard deviations, e4m3 at 448 = 7 g / 64.
+constexpr float kInt8Gain = 24.f;
+constexpr float kFp8Gain = 64.f;
+
 int launch_gram(const GramArgs& a, cudaStream_t st);
 
 // General tensor-core GEMM, D[s][m][n] = sum_{k in split s} A[m][k] B[n][k]:
@@ -163,11 +168,13 @@ void launch_split_sum(const float* D, int splits, long long mn, float* out, cuda
 size_t gram_smem_bytes();
 void launch_requant(const RequantArgs& a, cudaStream_t st);
 void launch_finalize_q(const FinQArgs& a, cudaStream_t st);
-// scale[a][k] = sqrt(P / 2) / gain with P the mean |U|^2 over spectra
-// [s0, s0 + n) of the ring (first integration of a stream).
+// scale[a][k] = sqrt(c P) / gain with P the mean |U|^2 over spectra
+// [s0, s0 + n) of the ring (first integration of a stream) and c the
+// component share of the power: 1/2, or 1 in the real DC channel k = 0.
 void launch_scale_from_ring(const float2* V, long long v_origin, long long v_mask, long long s0, int n, int n_in,
                             int n_in_pad, int n_chan, float gain, float* scale, cudaStream_t st);
-// scale[a][k] = 2 sqrt(R_aa[k] / 2) / gain (U = 2V) from an integration's R.
+// scale[a][k] = 2 sqrt(c R_aa[k]) / gain (U = 2V, c as above) from an
+// integration's R.
 void launch_scale_from_vis(const float2* R, int n_in, int n_in_pad, int n_chan, float gain, float* scale,
                            cudaStream_t st);
 

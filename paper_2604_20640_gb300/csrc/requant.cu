@@ -120,7 +120,8 @@ __global__ void scale_ring_kernel(const float2* V, long long v_origin, long long
         p = fmaf(u.x, u.x, fmaf(u.y, u.y, p));
     }
     p /= (float)n;
-    float s = sqrtf(0.5f * p) / gain;
+    // power of one component: half of |U|^2, all of it in the real DC bin
+    float s = sqrtf((k == 0 ? 1.f : 0.5f) * p) / gain;
     if (!(s > 0.f) || !isfinite(s)) s = 1.f;
     scale[(size_t)a * n_chan + k] = s;
 }
@@ -130,7 +131,7 @@ __global__ void scale_vis_kernel(const float2* R, int n_in, int n_in_pad, int n_
     const int a = blockIdx.y;
     if (k >= n_chan || a >= n_in) return;
     const float raa = R[((size_t)k * n_in + a) * n_in + a].x;
-    float s = 2.f * sqrtf(0.5f * fmaxf(raa, 0.f)) / gain;
+    float s = 2.f * sqrtf((k == 0 ? 1.f : 0.5f) * fmaxf(raa, 0.f)) / gain;
     if (!(s > 0.f) || !isfinite(s)) s = 1.f;
     scale[(size_t)a * n_chan + k] = s;
 }

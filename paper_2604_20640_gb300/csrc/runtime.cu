@@ -450,7 +450,7 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
                 if (have >= want || (closing && have > 0)) {
                     const int n = (int)(have < want ? have : want);
                     launch_scale_from_ring(p.V, 0, p.v_cap - 1, istart, n, h->n_in, h->n_in_pad, h->n_chan,
-                                           h->precision == CORR_FP8 ? 64.f : 32.f, p.scale, st);
+                                           h->precision == CORR_FP8 ? kFp8Gain : kInt8Gain, p.scale, st);
                     ++h->launches;
                     CK(cudaGetLastError());
                     p.have_scale = true;
@@ -563,7 +563,7 @@ int finalize_into(corr_t h, Pipe& p, const Tables& t, float2* R, uint8_t* F, int
             launch_finalize_q(f, st);
         }
         CK(cudaGetLastError());
-        launch_scale_from_vis(R, h->n_in, h->n_in_pad, h->n_chan, g.fp8 ? 64.f : 32.f, p.scale, st);
+        launch_scale_from_vis(R, h->n_in, h->n_in_pad, h->n_chan, g.fp8 ? kFp8Gain : kInt8Gain, p.scale, st);
         ++h->launches;
         CK(cudaGetLastError());
         if (F) {

@@ -49,14 +49,24 @@ def test_normalised_coefficients_hand_case():
 
 
 @pytest.mark.parametrize("dtype,P,sigma", [
-    ("int8", 2.0 * 32 ** 2, 1.0),           # sigma = sqrt(P/2)/32
-    ("int8", 9 * 2.0 * 32 ** 2, 3.0),
+    ("int8", 2.0 * 24 ** 2, 1.0),           # sigma = sqrt(P/2)/24 off DC
+    ("int8", 9 * 2.0 * 24 ** 2, 3.0),
     ("e4m3", 2.0 * 64 ** 2, 1.0),           # sigma = sqrt(P/2)/64
     ("e4m3", 0.25 * 2.0 * 64 ** 2, 0.5),
     ("int8", 0.0, 1.0),                     # no power: unit scale
 ])
 def test_scales_from_power_hand_values(dtype, P, sigma):
-    assert rq.scales_from_power(np.array([P]), dtype)[0] == pytest.approx(sigma, rel=1e-15)
+    # channel 1 of a two-channel row (channel 0 is the DC bin, below)
+    assert rq.scales_from_power(np.array([[1.0, P]]), dtype)[0, 1] == pytest.approx(sigma, rel=1e-15)
+
+
+@pytest.mark.parametrize("dtype,g", [("int8", 24.0), ("e4m3", 64.0)])
+def test_scale_of_the_real_dc_channel(dtype, g):
+    """The DC bin of a real transform is real, so its one component carries
+    the whole power: sigma = sqrt(P)/g there, sqrt(P/2)/g elsewhere."""
+    P = np.array([[g ** 2, 2.0 * g ** 2, 4.0 * g ** 2], [9 * g ** 2, 0.0, 2.0 * g ** 2]])
+    np.testing.assert_allclose(rq.scales_from_power(P, dtype), [[1.0, 1.0, np.sqrt(2.0)], [3.0, 1.0, 1.0]],
+                               rtol=1e-15)
 
 
 def _tone_step_stream(M, n_int, a1, a2):
@@ -78,14 +88,15 @@ def test_scale_schedule_on_a_tone_step(dtype):
     H = h[0::2].sum()                                  # Y_s[k0] = A H
     R, S = rq.correlate_quantized(x, n_chan, 1, n_int, dtype=dtype)
     assert R.shape[0] == 2
-    g = {"int8": 32.0, "e4m3": 64.0}[dtype]
-    # integration 0: pre-pass over its first 64 spectra, all at a1
+    g = {"int8": 24.0, "e4m3": 64.0}[dtype]
+    # integration 0: pre-pass over its first 64 spectra, all at a1 (k0 > 0:
+    # the component power is half of |V|^2)
     s0 = np.sqrt((a1 * H) ** 2 / 2.0) / g
     assert S[0, 0, k0] == pytest.approx(s0, rel=1e-12)
     # its codes: a1 H / s0 = g sqrt(2) for 64 spectra, 2 g sqrt(2) for the rest
     c1, c2 = rq.quantize(np.array([g * np.sqrt(2.0), 2 * g * np.sqrt(2.0)]), dtype)
     if dtype == "int8":
-        assert (c1, c2) == (45.0, 91.0)                # 45.25 -> 45, 90.51 -> 91
+        assert (c1, c2) == (34.0, 68.0)                # 33.94 -> 34, 67.88 -> 68
     else:
         assert (c1, c2) == (88.0, 176.0)               # e4m3 steps of 8 and 16 there
     raa0 = s0 ** 2 * (64 * c1 ** 2 + (n_int - 64) * c2 ** 2) / n_int
