@@ -105,7 +105,13 @@ const char* corr_last_error(corr_t h);
  *   "ring_mb"      (1..4096, default 64)  MiB of each on-device spectrum ring
  *                  (more spectra per launch; see corr_autotune)
  *   "fir_spt"      (0 = automatic, 1..256; may change at any time)
- *                  spectra each FIR thread filters
+ *                  spectra each FIR thread filters (two-kernel F-engine)
+ *   "fused_f"      (1, default, or 0; may change at any time)  run the
+ *                  F-engine as one kernel (FIR output kept in shared
+ *                  memory) where it covers the shape -- int8 samples, 4
+ *                  taps, 1024 <= M <= 8192 for the pipeline's spectra
+ *                  rings and the dynamic spectra, M = 8192 for the stage
+ *                  call -- else as FIR + FFT; results are bit-identical
  *   "sample_bits"  (8, default; or 16)  input sample type of every call that
  *                  takes samples: int8 (the 8-bit truncated recorder mode of
  *                  Sec. 3) or little-endian int16 (the 16-bit padded mode,
@@ -367,7 +373,8 @@ long long corr_kernel_launches(corr_t h);
  * the per-stage timings the paper tracks in Sec. 6 (GPU compute, H2D).
  * With option "stage_timing" = 1 every kernel launch is bracketed by CUDA
  * events on its own stream.  This call waits for those events and returns,
- * for stages 0 FIR, 1 FFT (the two F-engine kernels), 2 X-engine,
+ * for stages 0 FIR, 1 FFT (the two F-engine kernels; the fused F-engine
+ * kernel counts as stage 1), 2 X-engine,
  * 3 finalise, 4 flagging, 5 requantise, 6 tensor-core Gram (first
  * n_stages entries, at most 7; the dynamic spectra of
  * corr_spectrogram_dev are accumulated by the FFT kernel), the milliseconds and

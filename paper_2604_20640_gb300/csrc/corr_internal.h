@@ -67,6 +67,27 @@ struct FftArgs {
     int pair_major;
 };
 
+// Fused F-engine (PFB + FFT in one kernel; the FIR output stays in shared
+// memory).  Spectra [f.s_begin, f.s_end) of the stream `src` are filtered
+// and transformed into the outputs `f` describes (same modes and layouts as
+// the FFT stage; f.Z is not used).  hs: [taps][M/2] FP32, the lower half of
+// every polyphase row, hs[p][m] = h[p M + m]; the prototype is symmetric,
+// h[p M + M-1-m] = h[(taps-1-p) M + m], so the half gives every branch.
+struct FusedArgs {
+    FftArgs f;
+    StreamView src;
+    const float* hs;
+    const int* coarse;       // [n_in_pad] coarse advance d_a
+    int taps;
+};
+
+// True when the fused kernel covers this shape (int8 samples, 2 <= taps <=
+// 4, transform lengths whose buffers fit one CTA); otherwise the two-kernel
+// path (launch_fir + launch_fft) runs.
+bool fused_f_supported(int M, int taps, int es, int mode);
+// CORR_OK, or CORR_EINVAL for a shape fused_f_supported rejects.
+int launch_fused_f(const FusedArgs& a, cudaStream_t st);
+
 // X-engine launch: groups of spectra, each group summed into one partial
 // slot.  Local group g (0 <= g < n_groups) covers spectra
 // [int_start + (j0+g) * G, min(that + G, int_end, s_limit)) where all groups

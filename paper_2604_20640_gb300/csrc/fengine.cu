@@ -717,6 +717,363 @@ __global__ void __launch_bounds__(FftCfg<M>::threads(MODE), FftCfg<M>::minb(MODE
     }
 }
 
+// ---- fused PFB + FFT --------------------------------------------------------
+//
+// One kernel per F-engine launch.  A CTA owns one input pair and a run of
+// consecutive spectra; for each spectrum it filters the pair's newest frame
+// in shared memory and transforms it, so the FIR output (z) never leaves the
+// SM and each input sample is read from HBM once.
+//
+// Thread t owns branches 8t .. 8t+7 and their mirrors M-8-8t .. M-1-8t.  The
+// prototype is symmetric, h[pM + M-1-m] = h[(P-1-p)M + m], so the lower half
+// of each polyphase row, hs[p][m] (m < M/2, in shared memory), gives the
+// coefficients of both.  The last P-1 frames of the thread's 16 branches of
+// both inputs stay in registers as raw int8 words (sign bits flipped, ready to
+// unpack).  The newest frame arrives in a shared staging buffer by cp.async:
+// bytes [A, A + M + 32) of each input's row, A the 16-byte aligned address at
+// or below the frame's first sample, so branch m sits at staging byte o + m
+// with o = A's offset, fixed per input.  Frames that reach outside the valid
+// samples are staged by checked byte loads instead (zero outside).
+//
+// The FIR writes z into one of the FFT's two padded buffers and the first
+// radix pass reads it from there.  Every FMA keeps the order of fir_kernel,
+// and the passes are fft_kernel's, so the spectra are bit-identical to the
+// two-kernel path's.
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    const size_t g = __cvta_generic_to_global(src);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <int M>
+struct FusedCfg {
+    static constexpr int SB = M + 32;                        // staged bytes per input
+    static constexpr int ZB = FftCfg<M>::ZB;
+    static constexpr int TWS = FftCfg<M>::TWS;
+    static constexpr size_t off_tws = sizeof(float2) * 2 * (size_t)ZB;
+    static constexpr size_t off_hs = (off_tws + sizeof(float2) * TWS + 15) / 16 * 16;
+    static constexpr size_t off_stg(int P) { return off_hs + sizeof(float) * (size_t)P * (M / 2); }
+    static constexpr size_t smem_bytes(int P) { return off_stg(P) + 2 * (size_t)SB; }
+};
+
+// Stage the samples of one frame of one input (first sample n0 = f M + d)
+// into stg: staging byte i holds sample n0 - o + i (zero outside [lo, vhi)).
+template <int M>
+__device__ __forceinline__ void stage_frame(const StreamView& sv, const int8_t* row, bool has, long long n0, int o,
+                                            uint8_t* stg, int tid, int nthr) {
+    constexpr int SB = FusedCfg<M>::SB;
+    const long long nA = n0 - o;
+    const long long lo = sv.base > 0 ? sv.base : 0;
+    if (has && nA >= lo && nA + SB <= sv.vhi) {
+        const uint32_t s0 = tc::smem_u32(stg);
+        for (int c = tid; c < SB / 16; c += nthr) cp_async16(s0 + 16 * c, row + nA + 16 * c);
+    } else {
+        for (int i = tid; i < SB; i += nthr) {
+            const long long n = nA + i;
+            stg[i] = (has && n >= lo && n < sv.vhi) ? (uint8_t)row[n] : (uint8_t)0;
+        }
+    }
+}
+
+// Eight staged bytes from byte offset off (any alignment), sign bits flipped.
+__device__ __forceinline__ uint2 staged8(const uint8_t* stg, int off) {
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(stg) + (off >> 2);
+    const int sh = 8 * (off & 3);
+    const uint32_t a = w[0], b = w[1], c = w[2];
+    return make_uint2(__funnelshift_r(a, b, sh) ^ 0x80808080u, __funnelshift_r(b, c, sh) ^ 0x80808080u);
+}
+
+// Samples n .. n+7 of a row straight from global memory, zero outside
+// [lo, vhi) and for frames before the stream; sign bits flipped.  Used for
+// the P-1 frames a CTA's run starts with.
+__device__ __noinline__ uint2 global8_checked(const int8_t* row, bool has, long long n, long long lo, long long vhi) {
+    uint32_t w0 = 0, w1 = 0;
+    for (int b = 0; b < 8; ++b) {
+        const long long i = n + b;
+        const uint32_t v = (has && i >= lo && i < vhi) ? (uint32_t)(uint8_t)row[i] : 0u;
+        if (b < 4) w0 |= v << (8 * b);
+        else w1 |= v << (8 * (b - 4));
+    }
+    return make_uint2(w0 ^ 0x80808080u, w1 ^ 0x80808080u);
+}
+
+// (x_a, x_b) of byte C of two sign-flipped words, exact (see unpack4x2).
+template <int C>
+__device__ __forceinline__ float2 unpack_pair(uint32_t fa, uint32_t fb) {
+    constexpr uint32_t sel = 0x7440u + C;
+    return sub2(make_float2(__int_as_float((int)__byte_perm(fa, 0x4B000000u, sel)),
+                            __int_as_float((int)__byte_perm(fb, 0x4B000000u, sel))),
+                make_float2(8388736.0f, 8388736.0f));
+}
+
+// The first (radix R0, Ns = 1) pass's inputs from the padded shared buffer.
+template <int M>
+__device__ __forceinline__ void load_first_smem(float2 (&v)[16], const float2* z, int tid) {
+    constexpr int R = first_radix(M);
+    constexpr int B = 16 / R;
+    constexpr int NACT = M / 16;
+    constexpr int NR = M / R;
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[b * R + r] = z[pidx(tid + b * NACT + r * NR)];
+}
+
+// later_passes_pp with the cp.async copies of the next frame completed
+// before the last pass's barrier (so the staging buffer is ready after it).
+template <int M, int NS, bool REGTW>
+__device__ __forceinline__ float2* later_passes_cp(float2* zin, float2* zout, const float2* tws,
+                                                  const float2 (&twr)[15], int tid,
+                                                  const float2* __restrict__ gtw) {
+    if constexpr (NS < M) {
+        constexpr bool last = (NS * 16 == M);
+        if (tid < M / 16) {
+            float2 v[16];
+            load_smem<M>(v, zin, tid);
+            if constexpr (last && REGTW) pass_compute_store<M, 16, NS, TW_REG>(zout, v, tws, twr, tid);
+            else if constexpr (last) pass_compute_store<M, 16, NS, TW_GLOBAL>(zout, v, tws, twr, tid, gtw);
+            else pass_compute_store<M, 16, NS, TW_SMEM>(zout, v, tws, twr, tid);
+        }
+        if constexpr (last) cp_async_wait_all();
+        __syncthreads();
+        return later_passes_cp<M, NS * 16, REGTW>(zout, zin, tws, twr, tid, gtw);
+    } else {
+        return zin;
+    }
+}
+
+__device__ __forceinline__ float2 unpack_pair(uint32_t fa, uint32_t fb, int c) {
+    const uint32_t sel = 0x7440u + (uint32_t)c;
+    return sub2(make_float2(__int_as_float((int)__byte_perm(fa, 0x4B000000u, sel)),
+                            __int_as_float((int)__byte_perm(fb, 0x4B000000u, sel))),
+                make_float2(8388736.0f, 8388736.0f));
+}
+
+// MODE as in fft_kernel (0 U = 2Y channel-major, 1 rotated V, 2 power
+// tiles, 3 U pair-major), one input pair per CTA; P taps.
+template <int M, int MODE, int P>
+__global__ void __launch_bounds__(M / 16, FftCfg<M>::minb(3)) pfb_fft_kernel(const FusedArgs A) {
+    using C = FftCfg<M>;
+    using FC = FusedCfg<M>;
+    static_assert(C::pairs(MODE) == 1, "fused kernel: one input pair per CTA");
+    static_assert(M >= 512 && C::THREADS == M / 16, "fused kernel: every thread owns 16 branches");
+    static_assert(P >= 2 && P <= 4, "fused kernel: 2 to 4 taps");
+    constexpr int NACT = M / 16;
+    constexpr int n_chan = M >> 1;
+    constexpr int R0 = first_radix(M);
+    // FIR + radix passes: with an even count the result lands in the buffer
+    // the FIR wrote, so consecutive spectra alternate between the buffers
+    constexpr bool ALT = ((1 + n_later_passes(M, R0)) % 2) == 0;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* const buf0 = reinterpret_cast<float2*>(smem_raw);
+    float2* const buf1 = buf0 + FC::ZB;
+    float2* const tws = reinterpret_cast<float2*>(smem_raw + FC::off_tws);
+    float* const hsm = reinterpret_cast<float*>(smem_raw + FC::off_hs);
+    uint8_t* const stg0 = smem_raw + FC::off_stg(P);
+    uint8_t* const stg1 = stg0 + FC::SB;
+    const FftArgs& F = A.f;
+    const int tid = (int)threadIdx.x;
+    const int pair = (int)blockIdx.y;
+    const int n_pairs = (int)gridDim.y;
+    const int a = 2 * pair;
+    const long long s_lo = F.s_begin + (long long)blockIdx.x * F.spt;
+    long long s_hi = s_lo + F.spt;
+    if (s_hi > F.s_end) s_hi = F.s_end;
+    if (s_lo >= s_hi) return;   // uniform over the CTA
+
+    for (int i = tid; i < C::TWS; i += NACT) tws[i] = __ldg(F.tw + i);
+    {
+        const float4* src = reinterpret_cast<const float4*>(A.hs);
+        float4* dst = reinterpret_cast<float4*>(hsm);
+        for (int i = tid; i < P * M / 8; i += NACT) dst[i] = __ldg(src + i);
+    }
+    float2 twr[15];
+    if constexpr (C::REGTW) {
+        constexpr int NSL = M / 16;
+        constexpr int TWL = tw_offset(M, NSL);
+#pragma unroll
+        for (int r = 1; r < 16; ++r) twr[r - 1] = __ldg(F.tw + TWL + r * NSL + tid);
+    }
+
+    // the pair's two input rows: row[n] = sample n, valid in [lo, vhi)
+    const StreamView& sv = A.src;
+    const long long lo = sv.base > 0 ? sv.base : 0;
+    const bool has0 = a < F.n_in, has1 = a + 1 < F.n_in;
+    const int d0 = has0 ? A.coarse[a] : 0, d1 = has1 ? A.coarse[a + 1] : 0;
+    const int8_t* const row0 = sv.x + (long long)a * sv.stride - sv.base;
+    const int8_t* const row1 = row0 + sv.stride;
+    const int o0 = has0 ? (int)(reinterpret_cast<uintptr_t>(row0 + d0) & 15) : 0;
+    const int o1 = has1 ? (int)(reinterpret_cast<uintptr_t>(row1 + d1) & 15) : 0;
+    const int m_lo = 8 * tid, m_mi = M - 8 - 8 * tid;   // first branch of each half
+
+    // W[q][k][w]: frame q of the window (q = P-1 the newest), input k, words
+    // lower 0-1 (branches m_lo ..) and mirror 2-3 (branches m_mi ..)
+    uint32_t W[P][2][4];
+#pragma unroll
+    for (int q = 0; q < P - 1; ++q) {
+        const long long f = s_lo - (P - 1) + q;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            uint2 x = make_uint2(0x80808080u, 0x80808080u), y = x;   // zero samples
+            if (f >= 0) {
+                const int8_t* row = k ? row1 : row0;
+                const bool has = k ? has1 : has0;
+                const long long n = f * M + (k ? d1 : d0);
+                x = global8_checked(row, has, n + m_lo, lo, sv.vhi);
+                y = global8_checked(row, has, n + m_mi, lo, sv.vhi);
+            }
+            W[q][k][0] = x.x;
+            W[q][k][1] = x.y;
+            W[q][k][2] = y.x;
+            W[q][k][3] = y.y;
+        }
+    }
+    stage_frame<M>(sv, row0, has0, s_lo * M + d0, o0, stg0, tid, NACT);
+    stage_frame<M>(sv, row1, has1, s_lo * M + d1, o1, stg1, tid, NACT);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+
+    constexpr int PCH = MODE == 2 ? ((n_chan + NACT - 1) / NACT) : 1;
+    float pa[PCH], pb[PCH];
+#pragma unroll
+    for (int i = 0; i < PCH; ++i) pa[i] = pb[i] = 0.f;
+    const float4* const hs4 = reinterpret_cast<const float4*>(hsm);
+
+    for (long long s = s_lo; s < s_hi; ++s) {
+        const int it = (int)(s - s_lo);
+        float2* const X = (ALT && (it & 1)) ? buf1 : buf0;
+        float2* const Y = (X == buf0) ? buf1 : buf0;
+        {
+            const uint2 l0 = staged8(stg0, o0 + m_lo), m0 = staged8(stg0, o0 + m_mi);
+            const uint2 l1 = staged8(stg1, o1 + m_lo), m1 = staged8(stg1, o1 + m_mi);
+            W[P - 1][0][0] = l0.x;
+            W[P - 1][0][1] = l0.y;
+            W[P - 1][0][2] = m0.x;
+            W[P - 1][0][3] = m0.y;
+            W[P - 1][1][0] = l1.x;
+            W[P - 1][1][1] = l1.y;
+            W[P - 1][1][2] = m1.x;
+            W[P - 1][1][3] = m1.y;
+        }
+        // FIR: y_s[m] = sum_p h[pM + m] x[(s-P+1+p)M + m] for both inputs at
+        // once (lanes a, b of a packed pair), taps in order p = 0 .. P-1.
+        // Branch m_lo + 4j + c is byte c of lower word j; its mirror
+        // M-1-(m_lo + 4j + c) = m_mi + 7 - 4j - c is byte 3-c of mirror word
+        // 1-j and takes h[(P-1-p)M + m_lo + 4j + c] at tap p.
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            float4 hq[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) hq[p] = hs4[(p * (M / 2) + m_lo + 4 * j) >> 2];
+            float2 ylo[4], ymi[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) ylo[c] = ymi[c] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const float hl[4] = {hq[p].x, hq[p].y, hq[p].z, hq[p].w};
+                const float hm[4] = {hq[P - 1 - p].x, hq[P - 1 - p].y, hq[P - 1 - p].z, hq[P - 1 - p].w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    ylo[c] = fma2(make_float2(hl[c], hl[c]), unpack_pair(W[p][0][j], W[p][1][j], c), ylo[c]);
+                    ymi[c] = fma2(make_float2(hm[c], hm[c]),
+                                  unpack_pair(W[p][0][3 - j], W[p][1][3 - j], 3 - c), ymi[c]);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                X[pidx(m_lo + 4 * j + c)] = ylo[c];
+                X[pidx(M - 1 - m_lo - 4 * j - c)] = ymi[c];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < P - 1; ++q)
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) W[q][k][w] = W[q + 1][k][w];
+        __syncthreads();   // z complete; the staging buffer is free
+        if (s + 1 < s_hi) {
+            stage_frame<M>(sv, row0, has0, (s + 1) * M + d0, o0, stg0, tid, NACT);
+            stage_frame<M>(sv, row1, has1, (s + 1) * M + d1, o1, stg1, tid, NACT);
+            cp_async_commit();
+        }
+        {
+            float2 v[16];
+            load_first_smem<M>(v, X, tid);
+            pass_compute_store<M, R0, 1, TW_NONE>(Y, v, tws, twr, tid);
+        }
+        __syncthreads();
+        const float2* zres = later_passes_cp<M, R0, C::REGTW>(Y, X, tws, twr, tid, F.tw);
+
+        if constexpr (MODE == 2) {
+            // |Y_a|^2 = |S|^2 / 4, |Y_b|^2 = |D|^2 / 4, summed over the row
+#pragma unroll
+            for (int i = 0; i < PCH; ++i) {
+                const int k = tid + i * NACT;
+                if (k < n_chan) {
+                    const float2 zk = zres[pidx(k)];
+                    const float2 zm = zres[pidx((M - k) & (M - 1))];
+                    const float sx = zk.x + zm.x, sy = zk.y - zm.y;
+                    const float dx = zk.x - zm.x, dy = zk.y + zm.y;
+                    pa[i] = fmaf(sx, sx, fmaf(sy, sy, pa[i]));
+                    pb[i] = fmaf(dx, dx, fmaf(dy, dy, pb[i]));
+                }
+            }
+            const long long row = s / F.n_row;
+            if (s + 1 == s_hi || (s + 1) % F.n_row == 0) {
+                const float sc = 0.25f / (float)F.n_row;
+                const int n_cb = n_chan / 256, n_rb = F.rows / 64;
+#pragma unroll
+                for (int i = 0; i < PCH; ++i) {
+                    const int k = tid + i * NACT;
+                    if (k < n_chan) {
+                        const size_t px = (size_t)(row % 64) * 256 + (k % 256);
+                        if (has0) {
+                            const size_t ta = ((size_t)a * n_rb + row / 64) * n_cb + k / 256;
+                            atomicAdd(F.tiles + ta * 16384 + px, pa[i] * sc);
+                        }
+                        if (has1) {
+                            const size_t tb = ((size_t)(a + 1) * n_rb + row / 64) * n_cb + k / 256;
+                            atomicAdd(F.tiles + tb * 16384 + px, pb[i] * sc);
+                        }
+                    }
+                    pa[i] = 0.f;
+                    pb[i] = 0.f;
+                }
+            }
+        } else {
+            const long long slot = (s - F.v_origin) & F.v_mask;
+            float4* Vout;
+            size_t vstride;
+            if constexpr (MODE == 3) {
+                Vout = reinterpret_cast<float4*>(F.V) + ((size_t)slot * n_pairs + pair) * n_chan;
+                vstride = 1;
+            } else {
+                Vout = reinterpret_cast<float4*>(F.V + (size_t)slot * n_chan * F.n_in_pad + a);
+                vstride = (size_t)(F.n_in_pad >> 1);
+            }
+            for (int k = tid; k < n_chan; k += NACT) {
+                const float2 zk = zres[pidx(k)];
+                const float2 zm = zres[pidx((M - k) & (M - 1))];
+                const float2 S = make_float2(zk.x + zm.x, zk.y - zm.y);
+                const float2 D = make_float2(zk.x - zm.x, zk.y + zm.y);
+                float4 out;
+                if constexpr (MODE == 1) {
+                    const float2 va = cmul(S, __ldg(F.phasor + (size_t)a * n_chan + k));
+                    const float2 vb = cmul(D, __ldg(F.phasor + (size_t)(a + 1) * n_chan + k));
+                    out = make_float4(va.x, va.y, vb.x, vb.y);
+                } else {
+                    out = make_float4(S.x, S.y, D.y, -D.x);
+                }
+                Vout[(size_t)k * vstride] = out;
+            }
+        }
+    }
+}
+
 }  // namespace
 
 std::vector<float2> fft_twiddle_table(int M) {
@@ -829,6 +1186,79 @@ void launch_fir(const FirArgs& a, cudaStream_t st) {
         CORR_FIR(9) CORR_FIR(10) CORR_FIR(11) CORR_FIR(12) CORR_FIR(13) CORR_FIR(14) CORR_FIR(15) CORR_FIR(16)
 #undef CORR_FIR
         default: break;
+    }
+}
+
+}  // namespace corr
+
+namespace corr {
+
+namespace {
+
+template <int M, int MODE, int P>
+int launch_fused_m(const FusedArgs& a, cudaStream_t st) {
+    using FC = FusedCfg<M>;
+    static int resident = 0;     // CTAs per SM at this kernel's registers and shared memory
+    static int sms = 0;
+    const size_t smem = FC::smem_bytes(P);
+    if (!resident) {
+        if (cudaFuncSetAttribute(pfb_fft_kernel<M, MODE, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+            return CORR_ECUDA;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int r = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, pfb_fft_kernel<M, MODE, P>, M / 16, smem) !=
+                cudaSuccess || r < 1)
+            return CORR_ECUDA;
+        if (sms < 1) sms = 152;
+        resident = r;
+    }
+    // One wave of resident CTAs, each over a run of consecutive spectra of
+    // one pair (a run's first P-1 frames are read twice: by it and by the
+    // run before).
+    const long long n = a.f.s_end - a.f.s_begin;
+    const int n_groups = a.f.n_in_pad / 2;
+    long long runs = (long long)sms * resident / n_groups;
+    if (runs > n) runs = n;
+    if (runs < 1) runs = 1;
+    FusedArgs b = a;
+    b.f.spt = (int)((n + runs - 1) / runs);
+    dim3 grid((unsigned)((n + b.f.spt - 1) / b.f.spt), (unsigned)n_groups);
+    pfb_fft_kernel<M, MODE, P><<<grid, M / 16, smem, st>>>(b);
+    return CORR_OK;
+}
+
+template <int MODE>
+int launch_fused_mode(const FusedArgs& a, cudaStream_t st) {
+    switch (a.f.M) {
+        case 1024: if constexpr (MODE >= 2) return launch_fused_m<1024, MODE, 4>(a, st); else return CORR_EINVAL;
+        case 2048: if constexpr (MODE >= 2) return launch_fused_m<2048, MODE, 4>(a, st); else return CORR_EINVAL;
+        case 4096: if constexpr (MODE >= 2) return launch_fused_m<4096, MODE, 4>(a, st); else return CORR_EINVAL;
+        case 8192: return launch_fused_m<8192, MODE, 4>(a, st);
+        default: return CORR_EINVAL;
+    }
+}
+
+}  // namespace
+
+bool fused_f_supported(int M, int taps, int es, int mode) {
+    if (es != 1 || taps != 4) return false;
+    if (mode == 2 || mode == 3) return M >= 1024 && M <= 8192;
+    return M == 8192;
+}
+
+int launch_fused_f(const FusedArgs& a, cudaStream_t st) {
+    const int mode = a.f.tiles ? 2 : a.f.phasor ? 1 : a.f.pair_major ? 3 : 0;
+    if (!fused_f_supported(a.f.M, a.taps, a.src.es, mode)) return CORR_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(a.hs) & 15) != 0) return CORR_EINVAL;
+    if (a.f.s_end <= a.f.s_begin) return CORR_OK;
+    switch (mode) {
+        case 0: return launch_fused_mode<0>(a, st);
+        case 1: return launch_fused_mode<1>(a, st);
+        case 2: return launch_fused_mode<2>(a, st);
+        default: return launch_fused_mode<3>(a, st);
     }
 }
 

@@ -126,7 +126,9 @@ struct corr_s {
     std::vector<const void*> gkey;   // pointers/sizes the graph was captured with
     // constant tables
     float* d_h = nullptr;
+    float* d_hs = nullptr;       // half rows of d_h for the fused F-engine
     float2* d_tw = nullptr;
+    int fused_f = 1;             // F-engine as one fused kernel where supported
     Tables tab_stream, tab_direct;
     std::vector<double> tau, phi;            // latest values set
     std::vector<double> tau_pend, phi_pend;  // waiting for an integration boundary
@@ -253,7 +255,18 @@ std::vector<float> make_filter(int M, int P, int window, double beta) {
         const double sn = (x == 0.0) ? 1.0 : std::sin(pi * x) / (pi * x);
         h[n] = (float)(w * sn);
     }
+    // The taper and the sinc are both symmetric about (L-1)/2; the upper half
+    // repeats the lower one exactly (the fused F-engine keeps only half).
+    for (int n = 0; n < L / 2; ++n) h[L - 1 - n] = h[n];
     return h;
+}
+
+// Lower half of every polyphase row, hs[p][m] = h[p M + m] for m < M/2.
+std::vector<float> half_rows(const std::vector<float>& h, int M, int P) {
+    std::vector<float> hs((size_t)P * (M / 2));
+    for (int p = 0; p < P; ++p)
+        for (int m = 0; m < M / 2; ++m) hs[(size_t)p * (M / 2) + m] = h[(size_t)p * M + m];
+    return hs;
 }
 
 int upload_tables(corr_t h, Tables& t, const std::vector<double>& tau, const std::vector<double>& phi,
@@ -389,6 +402,23 @@ int launch_f(corr_t h, const StreamView& sv, const Tables& t, float2* Z, long lo
     f.rows = rows;
     f.n_in = h->n_in;
     f.pair_major = phasor == nullptr && tiles == nullptr && pair_major_ring(h);
+    const int mode = tiles ? 2 : phasor ? 1 : f.pair_major ? 3 : 0;
+    if (h->fused_f && fused_f_supported(h->M, h->taps, sv.es, mode)) {
+        FusedArgs u{};
+        u.f = f;
+        u.src = sv;
+        u.hs = h->d_hs;
+        u.coarse = t.coarse;
+        u.taps = h->taps;
+        int rc;
+        {
+            Timed t_(h, 1, st);
+            rc = launch_fused_f(u, st);
+        }
+        if (rc != CORR_OK) return fail(h, rc, "fused F-engine launch failed");
+        CK(cudaGetLastError());
+        return CORR_OK;
+    }
     {
         Timed t_(h, 0, st);
         launch_fir(a, st);
@@ -882,10 +912,13 @@ int corr_create(corr_t* out, int n_ant, int n_pol, int n_chan, int taps, int n_i
         cudaEventCreateWithFlags(&h->ev_comp, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_fin, cudaEventDisableTiming) != cudaSuccess)
         return bail(CORR_ECUDA, "stream/event creation failed");
+    const std::vector<float> hsf = half_rows(hf, h->M, taps);
     if (cudaMalloc(&h->d_h, hf.size() * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&h->d_hs, hsf.size() * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&h->d_tw, tw.size() * sizeof(float2)) != cudaSuccess)
         return bail(CORR_ENOMEM, "cudaMalloc of filter tables failed");
     if (cudaMemcpy(h->d_h, hf.data(), hf.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->d_hs, hsf.data(), hsf.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(CORR_ECUDA, "upload of filter tables failed");
     if (alloc_tables(h, h->tab_stream) != CORR_OK || alloc_tables(h, h->tab_direct) != CORR_OK)
@@ -941,6 +974,7 @@ int corr_destroy(corr_t h) {
     free_pipe(h->pd);
     cudaFree(h->d_part_x);
     cudaFree(h->d_h);
+    cudaFree(h->d_hs);
     cudaFree(h->d_tw);
     cudaFree(h->tab_stream.phasor);
     cudaFree(h->tab_stream.rot);
@@ -975,7 +1009,7 @@ const char* corr_last_error(corr_t h) {
 int corr_set_option(corr_t h, const char* key, double v) {
     if (!h || !key) return fail(h, CORR_EINVAL, "NULL argument");
     const std::string k(key);
-    if (h->started && k != "stage_timing" && k != "stage_mask" && k != "fir_spt")
+    if (h->started && k != "stage_timing" && k != "stage_mask" && k != "fir_spt" && k != "fused_f")
         return fail(h, CORR_ESTATE, "options must be set before the first push");
     if (k == "flag_sigma") {
         if (!(v > 0)) return fail(h, CORR_EINVAL, "flag_sigma must be > 0");
@@ -1001,6 +1035,10 @@ int corr_set_option(corr_t h, const char* key, double v) {
         if (h->stream_alloc) return fail(h, CORR_ESTATE, "ring_mb must be set before the first push");
         h->ring_mb = (int)v;
         free_pipe(h->pd);
+    } else if (k == "fused_f") {
+        if (v != 0 && v != 1) return fail(h, CORR_EINVAL, "fused_f: 0 or 1");
+        h->fused_f = (int)v;
+        return CORR_OK;
     } else if (k == "fir_spt") {
         if (v < 0 || v > 256) return fail(h, CORR_EINVAL, "fir_spt out of range");
         h->fir_spt = (int)v;
@@ -1023,7 +1061,9 @@ int corr_set_option(corr_t h, const char* key, double v) {
         if (k == "window") h->window = (int)v;
         else h->kaiser_beta = v;
         const std::vector<float> hf = make_filter(h->M, h->taps, h->window, h->kaiser_beta);
+        const std::vector<float> hsf = half_rows(hf, h->M, h->taps);
         CK(cudaMemcpy(h->d_h, hf.data(), hf.size() * sizeof(float), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->d_hs, hsf.data(), hsf.size() * sizeof(float), cudaMemcpyHostToDevice));
     } else if (k == "result_slots") {
         if (v < 1 || v > 4096) return fail(h, CORR_EINVAL, "result_slots out of range");
         h->result_slots = (int)v;
