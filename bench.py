@@ -988,11 +988,40 @@ def measure_stream(args, wl, prec, x, spec, dev, world, barrier, clocks=True, st
             "vis": vis, "flags": flags}
 
 
+def flops_per_sample(dom, fused, M, taps, n_in):
+    """Algorithmic FP32 work per input sample of a hot-path kernel, in the
+    scope table's operation counts: PFB FIR 2P, real FFT 2.5 log2 M (the
+    conventional 5 N log2 N of an N-point complex transform carrying two real
+    inputs), X-engine 2 (n_in + 1)."""
+    import math
+    fir, fft = 2.0 * taps, 2.5 * math.log2(M)
+    if dom == "fft":
+        return fir + fft if fused else fft
+    return {"fir": fir, "xengine": 2.0 * (n_in + 1)}.get(dom, 0.0)
+
+
+_FP32_PEAK = {}
+
+
+def fp32_peak():
+    """Measured FP32 FMA rate of this device (corr_peak_fp32, scalar and
+    packed f32x2 forms), once per process."""
+    if not _FP32_PEAK:
+        from paper_2604_20640_gb300.corr import peak_fp32
+        s, _ = peak_fp32(False, 4096)
+        p, _ = peak_fp32(True, 4096)
+        _FP32_PEAK.update(scalar=s, packed=p)
+    return dict(_FP32_PEAK)
+
+
 def _roofline(wl, prec, args, dom, di, share, stage_ms, stage_n, S, n_in):
     """Roofline entry of the dominant kernel from its live CUDA-event times:
-    algorithmic bytes per launch (the samples the timed launches processed x
-    the per-sample figure) over the average launch duration."""
+    algorithmic bytes (and FP32 operations) per launch -- the samples the
+    timed launches processed x the per-sample figure -- over the average
+    launch duration.  The bound is the resource the kernel is closer to:
+    HBM (measured copy peak) or FP32 arithmetic (measured FMA peak)."""
     W = WORKLOADS[wl]
+    fused = dom == "fft" and stage_n[0] == 0
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs")
     peak_src = "measured" if hbm else "fallback"
@@ -1003,6 +1032,8 @@ def _roofline(wl, prec, args, dom, di, share, stage_ms, stage_n, S, n_in):
     launches = max(1, stage_n[di])
     alg = ALG_BYTES_PER_SAMPLE[dom] * (es if dom in ("fir", "fft", "xengine") else 1)
     inter = dict(INTERMEDIATE_BYTES_PER_SAMPLE)
+    if fused:
+        inter["fft"] = 1.0 + 4.0        # samples in, spectra out (no z ring)
     if es == 2:
         inter["fir"] += 1.0
     if prec == 2:
@@ -1010,17 +1041,36 @@ def _roofline(wl, prec, args, dom, di, share, stage_ms, stage_n, S, n_in):
     bytes_per_launch = alg * samples_timed / launches
     avg_ms = stage_ms[di] / launches
     achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
-    tps = TRAFFIC_PER_SAMPLE.get((wl, dom))
+    tps = TRAFFIC_PER_SAMPLE.get((wl, "fused" if fused else dom))
     traffic = tps * samples_timed / launches if tps and prec == 0 and es == 1 else None
     kname = KERNELS[dom]
+    M = 2 * W["n_chan"]
     if dom == "fft":
         # mode 3: spectra ring pair-major (FP32 path with n_in_pad <= 8); 0: channel-major
-        kname = "fft_kernel<%d,%d>" % (2 * W["n_chan"], 3 if prec == 0 and (n_in + 3) // 4 * 4 <= 8 else 0)
-    return {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_src,
-            "bytes_per_launch": bytes_per_launch, "bytes_per_sample": alg,
-            "intermediate_bytes_per_launch": inter[dom] * samples_timed / launches,
-            "avg_launch_ms": avg_ms, "launches": stage_n[di], "stage_share": share}
+        mode = 3 if prec == 0 and (n_in + 3) // 4 * 4 <= 8 else 0
+        kname = ("pfb_fft_kernel<%d,%d,%d> (fused PFB + FFT)" % (M, mode, W["taps"]) if fused
+                 else "fft_kernel<%d,%d>" % (M, mode))
+    fl = flops_per_sample(dom, fused, M, W["taps"], n_in)
+    hbm_part = {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_src}
+    out = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+           "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_src,
+           "bytes_per_launch": bytes_per_launch, "bytes_per_sample": alg,
+           "intermediate_bytes_per_launch": inter[dom] * samples_timed / launches,
+           "avg_launch_ms": avg_ms, "launches": stage_n[di], "stage_share": share}
+    if fl > 0:
+        fp = fp32_peak()
+        tf = fl * samples_timed / launches / (avg_ms * 1e-3) / 1e12
+        alu = {"achieved": tf, "peak": fp["scalar"], "unit": "TFLOP/s", "frac": tf / fp["scalar"],
+               "flop_per_sample": fl, "peak_source": "measured (corr_peak_fp32, scalar FMA chains)",
+               "peak_packed_f32x2": fp["packed"],
+               "peak_nominal": 152 * 128 * 2 * 2.07e9 / 1e12}
+        if alu["frac"] > out["frac"]:
+            out.update({"bound": "alu", "achieved": tf, "peak": fp["scalar"], "unit": "TFLOP/s",
+                        "frac": alu["frac"], "peak_source": alu["peak_source"], "hbm": hbm_part})
+            out["alu"] = {k: alu[k] for k in ("flop_per_sample", "peak_packed_f32x2", "peak_nominal")}
+        else:
+            out["alu"] = alu
+    return out
 
 
 def end_to_end(args, wl, prec, x, spec, tuning, dev, world, dist):

@@ -362,6 +362,21 @@ int corr_tile_mad_dev(const float* d_power, int n_tiles, float sigma, int axes, 
 int corr_calibrate_dev(const float* d_vis, const uint8_t* d_flags, int n_chan, int n_in, int ref, int k_lo, int k_hi,
                        double max_delay, double* tau, double* phi, void* stream);
 
+/*
+ * corr_peak_fp32 -- measured FP32 arithmetic peak of the current device, the
+ * ceiling of the F-engine's floating-point work (its roofline when HBM is not
+ * the bound; the paper states no such figure, this is a library facility).
+ * Independent chains of dependent fused multiply-adds in every thread of
+ * four waves of full SMs, scalar (packed = 0: 2 FLOP per lane per
+ * instruction) or packed FP32 pairs (packed = 1: fma.rn.f32x2, 4 FLOP per
+ * lane per instruction), `iters` FMAs per chain; one warm-up launch, then
+ * one launch timed with CUDA events on `stream`.  *tflops receives the rate
+ * (1e12 FLOP/s) and *ms (may be NULL) the timed launch's duration.  The SM
+ * clock during the call sets the figure.  Synchronous; CORR_EINVAL on bad
+ * arguments, CORR_ECUDA if a CUDA call fails (corr_last_error(NULL)).
+ */
+int corr_peak_fp32(int packed, int iters, double* tflops, double* ms, void* stream);
+
 /* Shapes of a handle: n_in, n_chan, taps, n_int, n_in_pad (any may be NULL). */
 int corr_shape(corr_t h, int* n_in, int* n_chan, int* taps, int* n_int, int* n_in_pad);
 

@@ -38,6 +38,7 @@ EXPORTED = [
     "corr_flagnet_num_params", "corr_flagnet_set_params", "corr_flagnet_get_params", "corr_flagnet_prepare",
     "corr_flagnet_forward", "corr_flagnet_loss_grad", "corr_flagnet_train_step", "corr_flagnet_flag",
     "corr_flagnet_status", "corr_flagnet_kernel_launches", "corr_tile_mad_dev", "corr_calibrate_dev",
+    "corr_peak_fp32",
 ]
 
 
@@ -106,6 +107,7 @@ def load_library(path: str = LIB_PATH):
         "corr_flagnet_kernel_launches": (_ll, [_vp]),
         "corr_tile_mad_dev": (_i, [_vp, _i, ctypes.c_float, _i, _vp, _vp]),
         "corr_calibrate_dev": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _d, _vp, _vp, _vp]),
+        "corr_peak_fp32": (_i, [_i, _i, ctypes.POINTER(_d), ctypes.POINTER(_d), _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -423,6 +425,16 @@ class Correlator:
     @property
     def launches(self) -> int:
         return int(self._L.corr_kernel_launches(self._h))
+
+
+def peak_fp32(packed: bool = False, iters: int = 4096, stream=None):
+    """(TFLOP/s, ms) of the FP32 FMA probe (corr_peak_fp32)."""
+    L = load_library()
+    t, ms = _d(), _d()
+    rc = L.corr_peak_fp32(1 if packed else 0, int(iters), ctypes.byref(t), ctypes.byref(ms), _stream_ptr(stream))
+    if rc != CORR_OK:
+        raise CorrError(rc, L.corr_last_error(None).decode())
+    return t.value, ms.value
 
 
 def tile_mad(power, flags_out, axes: int = 1, sigma: float = 5.0, stream=None):
