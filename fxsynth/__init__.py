@@ -10,6 +10,7 @@ it without sharing any of the method's code.
 from .streams import (  # noqa: F401
     StreamSpec,
     make_stream,
+    make_stream_iq,
     config_c1,
     config_c2,
     config_c3,

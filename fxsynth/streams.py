@@ -132,6 +132,40 @@ def make_stream(spec: StreamSpec, return_float: bool = False):
     return q
 
 
+def make_stream_iq(spec: StreamSpec) -> np.ndarray:
+    """Complex baseband counterpart of :func:`make_stream`: int8 ``[n_in][2 S]``
+    with each input's (I, Q) pairs interleaved.  Circular complex receiver
+    noise of power sigma^2 (sigma^2 / 2 per part), a common complex source at
+    src_frac of it, delayed by tau_a (per block, by a phase ramp over signed
+    frequencies) and rotated by phi_a, complex tones (freq in cycles per
+    sample, may be negative; amplitude per part), rounded half to even and
+    clipped to int8 per part."""
+    n_in, S = spec.n_in, spec.n_samples
+    rng = _rng(spec.seed, 11)
+    sc = spec.sigma * math.sqrt(spec.noise_frac / 2.0)
+    x = (rng.standard_normal((n_in, S)) + 1j * rng.standard_normal((n_in, S))) * sc
+    if spec.src_frac > 0:
+        tau = np.zeros(n_in) if spec.tau is None else np.asarray(spec.tau, np.float64)
+        phi = np.zeros(n_in) if spec.phi is None else np.asarray(spec.phi, np.float64)
+        amp = spec.sigma * math.sqrt(spec.src_frac / 2.0)
+        B = min(spec.block, S)
+        f = np.fft.fftfreq(B)
+        filt = np.exp(-2j * np.pi * f[None, :] * tau[:, None]) * np.exp(1j * phi)[:, None]
+        src = _rng(spec.seed, 12)
+        for b0 in range(0, S, B):
+            n = min(B, S - b0)
+            s_blk = (src.standard_normal(B) + 1j * src.standard_normal(B)) * amp
+            x[:, b0:b0 + n] += np.fft.ifft(np.fft.fft(s_blk)[None, :] * filt, axis=1)[:, :n]
+    t = np.arange(S, dtype=np.float64)
+    for (freq, amp, theta) in spec.tones:
+        x += amp * np.exp(1j * (2 * np.pi * freq * t + theta))[None, :]
+    lim = 1 << (spec.bits - 1)
+    out = np.empty((n_in, 2 * S), dtype=np.int8)
+    out[:, 0::2] = np.clip(np.rint(x.real), -lim, lim - 1)
+    out[:, 1::2] = np.clip(np.rint(x.imag), -lim, lim - 1)
+    return out
+
+
 def delays_for(n_in: int, seed: int, max_delay: float = 40.0, integer: bool = False):
     """Per-input geometric delays in [0, max_delay] (input 0 at 0) and phases."""
     rng = _rng(seed, 7)

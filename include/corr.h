@@ -118,6 +118,17 @@ const char* corr_last_error(corr_t h);
  *                  14-bit ADC values, Sec. 3); sample pointers are `const
  *                  void*`, counts and strides are in samples.  Before the
  *                  first push.
+ *   "sample_format" (0, default: real samples; 1: complex) -- with 1 every
+ *                  input is a stream of complex baseband samples, (I, Q)
+ *                  int8 pairs interleaved (Sec. 4.2, "converted into complex
+ *                  voltage streams"); counts and strides are in complex
+ *                  samples.  The transform is an M = n_chan point complex
+ *                  FFT that keeps all n_chan channels in FFT order, channel
+ *                  k at k/M cycles per sample below M/2 and (k - M)/M above
+ *                  (the fine delay phase exp(j 2 pi f_k r) uses these signed
+ *                  frequencies).  FP32 path only (CORR_EINVAL with reduced
+ *                  precision, 16-bit samples or n_chan < 16); the dynamic
+ *                  spectra call is for real input.  Before any buffers exist.
  *   "window"       (0 Hann, default; 1 Kaiser; 2 unit coefficients) taper
  *                  of the prototype filter h = taper x sinc (Sec. 4.2; the
  *                  8-tap Kaiser of Fig. 4); 2 with taps = 1 is the plain

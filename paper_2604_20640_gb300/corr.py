@@ -201,6 +201,7 @@ class Correlator:
         self.n_in_pad = (self.n_in + 3) // 4 * 4
         self.M = 2 * n_chan
         self.sample_bits = 8
+        self.iq = False
         for k, v in options.items():
             self.set_option(k, v)
 
@@ -232,6 +233,19 @@ class Correlator:
         self._check(self._L.corr_set_option(self._h, key.encode(), float(value)))
         if key == "sample_bits":
             self.sample_bits = int(value)
+        elif key == "sample_format":
+            self.iq = bool(value)
+            self.M = self.n_chan if self.iq else 2 * self.n_chan
+
+    def _counts(self, n_elems: int, stride_elems: int):
+        """(samples per input, input stride) in the library's sample units for
+        rows of n_elems array elements: complex input takes (I, Q) int8 pairs,
+        so two elements make one sample."""
+        if not self.iq:
+            return n_elems, stride_elems
+        if n_elems % 2 or stride_elems % 2:
+            raise CorrError(CORR_EINVAL, "complex input: rows of interleaved (I, Q) int8 pairs")
+        return n_elems // 2, stride_elems // 2
 
     def _sample_types(self):
         import torch
@@ -263,8 +277,8 @@ class Correlator:
                     raise CorrError(CORR_EINVAL, "samples must be %s [n_in][n]" % np.dtype(np_t).name)
                 if samples.stride(1) != 1:
                     raise CorrError(CORR_EINVAL, "samples rows must be contiguous")
-                self._check(self._L.corr_push(self._h, samples.data_ptr(), samples.shape[1],
-                                              samples.stride(0)))
+                self._check(self._L.corr_push(self._h, samples.data_ptr(),
+                                              *self._counts(samples.shape[1], samples.stride(0))))
                 return
         except ImportError:
             pass
@@ -273,7 +287,7 @@ class Correlator:
             raise CorrError(CORR_EINVAL, "samples must be %s [n_in][n]" % np.dtype(np_t).name)
         if a.strides[1] != a.itemsize or a.strides[0] % a.itemsize:
             a = np.ascontiguousarray(a)
-        self._check(self._L.corr_push(self._h, a.ctypes.data, a.shape[1], a.strides[0] // a.itemsize))
+        self._check(self._L.corr_push(self._h, a.ctypes.data, *self._counts(a.shape[1], a.strides[0] // a.itemsize)))
 
     def push_dev(self, samples, stream=None):
         """Append device samples (CUDA tensor ``[n_in][n]`` of the handle's
@@ -281,8 +295,8 @@ class Correlator:
         if samples.dim() != 2 or samples.shape[0] != self.n_in or samples.stride(1) != 1 or \
                 samples.dtype != self._sample_types()[1]:
             raise CorrError(CORR_EINVAL, "samples must be [n_in][n] of the sample type with contiguous rows")
-        self._check(self._L.corr_push_dev(self._h, _dev_ptr(samples, "samples"), samples.shape[1],
-                                          samples.stride(0), _stream_ptr(stream)))
+        self._check(self._L.corr_push_dev(self._h, _dev_ptr(samples, "samples"),
+                                          *self._counts(samples.shape[1], samples.stride(0)), _stream_ptr(stream)))
 
     def flush(self):
         self._check(self._L.corr_flush(self._h))
@@ -365,8 +379,9 @@ class Correlator:
         n_out = _i()
         max_int = vis_out.numel() * vis_out.element_size() // (8 * self.n_chan * self.n_in * self.n_in)
         fp = _dev_ptr(flags_out, "flags") if flags_out is not None else None
-        self._check(self._L.corr_run_dev(self._h, _dev_ptr(samples, "samples"), samples.shape[1],
-                                         samples.stride(0), _dev_ptr(vis_out, "vis"), fp, int(max_int),
+        self._check(self._L.corr_run_dev(self._h, _dev_ptr(samples, "samples"),
+                                         *self._counts(samples.shape[1], samples.stride(0)),
+                                         _dev_ptr(vis_out, "vis"), fp, int(max_int),
                                          1 if include_partial else 0, ctypes.byref(n_out),
                                          _stream_ptr(stream)))
         return n_out.value
@@ -374,8 +389,9 @@ class Correlator:
     def fengine_dev(self, samples, s0: int, n_spec: int, V_out, stream=None):
         if samples.dim() != 2 or samples.shape[0] != self.n_in or samples.stride(1) != 1:
             raise CorrError(CORR_EINVAL, "samples must be int8 [n_in][S] with contiguous rows")
-        self._check(self._L.corr_fengine_dev(self._h, _dev_ptr(samples, "samples"), samples.shape[1],
-                                             samples.stride(0), int(s0), int(n_spec), _dev_ptr(V_out, "V"),
+        self._check(self._L.corr_fengine_dev(self._h, _dev_ptr(samples, "samples"),
+                                             *self._counts(samples.shape[1], samples.stride(0)),
+                                             int(s0), int(n_spec), _dev_ptr(V_out, "V"),
                                              _stream_ptr(stream)))
 
     def xengine_dev(self, V, n_spec: int, vis_out, stream=None):
@@ -389,8 +405,9 @@ class Correlator:
     def autotune(self, samples, cache_path: Optional[str] = None, stream=None):
         """Pick ring size and FIR run length by timing (corr_autotune)."""
         cp = cache_path.encode() if cache_path else None
-        self._check(self._L.corr_autotune(self._h, _dev_ptr(samples, "samples"), samples.shape[1],
-                                          samples.stride(0), cp, _stream_ptr(stream)))
+        self._check(self._L.corr_autotune(self._h, _dev_ptr(samples, "samples"),
+                                          *self._counts(samples.shape[1], samples.stride(0)), cp,
+                                          _stream_ptr(stream)))
 
     def tuning(self):
         r, s = _i(), _i()

@@ -38,6 +38,9 @@ struct FirArgs {
     long long z_mask;
     long long s_begin, s_end;
     int n_in, n_pairs, M, lgM, taps, spt;
+    // complex input: samples are interleaved (I, Q) int8 pairs (src.es = 2);
+    // "pair" p is input p, z[m] = (y_I[m], y_Q[m]), n_pairs = n_in_pad
+    int iq;
 };
 
 // F-engine, stage 2 (M-point complex FFT of z, then the two real spectra of
@@ -65,6 +68,10 @@ struct FftArgs {
     // two complex values), instead of [slot][n_chan][n_in_pad] complex64:
     // the small-N FP32 pipeline, whose X-engine reads that layout
     int pair_major;
+    // complex input: z of input p is its complex FIR output; all M channels
+    // of its M-point spectrum Z are stored, channel-major with n_chan = M,
+    // as U = 2Z (phasor null) or V = Z P (phasor = the rotation)
+    int iq;
 };
 
 // Fused F-engine (PFB + FFT in one kernel; the FIR output stays in shared
@@ -200,6 +207,9 @@ void launch_scale_from_vis(const float2* R, int n_in, int n_in_pad, int n_chan, 
                            cudaStream_t st);
 
 void launch_fir(const FirArgs& a, cudaStream_t st);
+// The complex-input forms of the two F-engine stages (a.iq set).
+void launch_fir_iq(const FirArgs& a, cudaStream_t st);
+int launch_fft_iq(const FftArgs& a, cudaStream_t st);
 // CORR_OK, or CORR_EINVAL / CORR_ECUDA when the spectra's tensor map cannot
 // be made (V not 16-byte aligned, no driver entry point).
 int launch_fft(const FftArgs& a, cudaStream_t st);

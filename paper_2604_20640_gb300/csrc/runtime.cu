@@ -110,7 +110,8 @@ struct corr_s {
     int ring_mb = 64;            // tunable: ring capacity of Z and V (MiB each)
     int fir_spt = 0;             // tunable: spectra per FIR thread (0 = automatic)
     int window = 0;              // PFB taper: 0 Hann, 1 Kaiser, 2 unit coefficients
-    int es = 1;                  // bytes per input sample: 1 (int8) or 2 (int16, 16-bit padded mode)
+    int es = 1;                  // bytes per input sample: 1 (int8), 2 (int16, 16-bit padded mode; or int8 I/Q)
+    int iq = 0;                  // complex input: interleaved int8 I/Q, M = n_chan
     double kaiser_beta = 8.0;
     // group of handles run as one captured graph (corr_group_create)
     bool is_group = false;
@@ -282,10 +283,17 @@ int upload_tables(corr_t h, Tables& t, const std::vector<double>& tau, const std
         co[a] = (int)d;
         if (co[a] > dmax) dmax = co[a];
         // Pair packing: even inputs carry 1/2, odd inputs 1/(2j) = -j/2.
+        // Complex input: channel k at k/M cycles per sample below M/2 and
+        // (k - M)/M above, no pair factor.
         const bool odd = (a & 1) != 0;
         for (int k = 0; k < h->n_chan; ++k) {
-            const double ang = 2.0 * pi * k * r / (double)h->M - phi[a];
+            const double fk = (h->iq && k >= h->M / 2) ? (double)(k - h->M) : (double)k;
+            const double ang = 2.0 * pi * fk * r / (double)h->M - phi[a];
             rt[(size_t)a * h->n_chan + k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+            if (h->iq) {
+                ph[(size_t)a * h->n_chan + k] = rt[(size_t)a * h->n_chan + k];
+                continue;
+            }
             double re = 0.5 * std::cos(ang), im = 0.5 * std::sin(ang);
             if (odd) {
                 const double t2 = re;
@@ -360,7 +368,29 @@ int alloc_pipe(corr_t h, Pipe& p) {
 
 // The FP32 pipeline with the small-N X-engine keeps its spectra ring
 // pair-major (FftArgs::pair_major); every other reader wants channel-major.
-bool pair_major_ring(corr_t h) { return h->precision == CORR_FP32 && h->n_in_pad <= 8; }
+bool pair_major_ring(corr_t h) { return h->precision == CORR_FP32 && h->n_in_pad <= 8 && !h->iq; }
+
+// Filter, half-row and twiddle tables for the handle's current M, window
+// and taps (replaces the device copies; sizes follow M).
+int build_filter_tables(corr_t h) {
+    const std::vector<float> hf = make_filter(h->M, h->taps, h->window, h->kaiser_beta);
+    const std::vector<float> hsf = half_rows(hf, h->M, h->taps);
+    const std::vector<float2> tw = corr::fft_twiddle_table(h->M);
+    cudaFree(h->d_h);
+    cudaFree(h->d_hs);
+    cudaFree(h->d_tw);
+    h->d_h = nullptr;
+    h->d_hs = nullptr;
+    h->d_tw = nullptr;
+    if (cudaMalloc(&h->d_h, hf.size() * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&h->d_hs, hsf.size() * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&h->d_tw, tw.size() * sizeof(float2)) != cudaSuccess)
+        return fail(h, CORR_ENOMEM, "cudaMalloc of filter tables failed");
+    CK(cudaMemcpy(h->d_h, hf.data(), hf.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_hs, hsf.data(), hsf.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    return CORR_OK;
+}
 
 // F-engine over spectra [s_begin, s_end): FIR into the Z ring, FFT into the
 // V ring.  `phasor` set -> rotated V (stage call); else U = 2Y (pipeline).
@@ -377,7 +407,8 @@ int launch_f(corr_t h, const StreamView& sv, const Tables& t, float2* Z, long lo
     a.s_begin = s_begin;
     a.s_end = s_end;
     a.n_in = h->n_in;
-    a.n_pairs = h->n_in_pad / 2;
+    a.n_pairs = h->iq ? h->n_in_pad : h->n_in_pad / 2;
+    a.iq = h->iq;
     a.M = h->M;
     a.lgM = 0;
     while ((1 << a.lgM) < h->M) ++a.lgM;
@@ -402,8 +433,9 @@ int launch_f(corr_t h, const StreamView& sv, const Tables& t, float2* Z, long lo
     f.rows = rows;
     f.n_in = h->n_in;
     f.pair_major = phasor == nullptr && tiles == nullptr && pair_major_ring(h);
+    f.iq = h->iq;
     const int mode = tiles ? 2 : phasor ? 1 : f.pair_major ? 3 : 0;
-    if (h->fused_f && fused_f_supported(h->M, h->taps, sv.es, mode)) {
+    if (h->fused_f && !h->iq && fused_f_supported(h->M, h->taps, sv.es, mode)) {
         FusedArgs u{};
         u.f = f;
         u.src = sv;
@@ -1025,8 +1057,22 @@ int corr_set_option(corr_t h, const char* key, double v) {
         if (v < 1 || v > (double)(1LL << 32)) return fail(h, CORR_EINVAL, "chunk out of range");
         if (h->stream_alloc) return fail(h, CORR_ESTATE, "chunk must be set before buffers exist");
         h->chunk = (long long)v;
+    } else if (k == "sample_format") {
+        if (v != 0 && v != 1) return fail(h, CORR_EINVAL, "sample_format: 0 real, 1 complex (interleaved int8 I/Q)");
+        if (h->stream_alloc || h->pd.V) return fail(h, CORR_ESTATE, "sample_format must be set before buffers exist");
+        if (v == 1 && h->precision != CORR_FP32) return fail(h, CORR_EINVAL, "complex input runs the FP32 path");
+        if (v == 1 && h->es != 1 && !h->iq) return fail(h, CORR_EINVAL, "complex input takes int8 I/Q samples");
+        if (v == 1 && h->n_chan < 16) return fail(h, CORR_EINVAL, "complex input needs n_chan >= 16");
+        if ((int)v == h->iq) return CORR_OK;
+        h->iq = (int)v;
+        h->M = h->iq ? h->n_chan : 2 * h->n_chan;
+        h->es = h->iq ? 2 : 1;
+        CKRET(build_filter_tables(h));
+        CKRET(upload_tables(h, h->tab_direct, h->tau, h->phi, h->s_comp));
+        CKRET(upload_tables(h, h->tab_stream, h->tau, h->phi, h->s_comp));
     } else if (k == "precision") {
         if (v != CORR_FP32 && v != CORR_INT8 && v != CORR_FP8) return fail(h, CORR_EINVAL, "precision: 0, 1 or 2");
+        if (v != CORR_FP32 && h->iq) return fail(h, CORR_EINVAL, "complex input runs the FP32 path");
         if (v != CORR_FP32 && h->n_in > 64) return fail(h, CORR_EINVAL, "reduced precision needs n_in <= 64");
         if (h->stream_alloc || h->pd.V) return fail(h, CORR_ESTATE, "precision must be set before buffers exist");
         h->precision = (int)v;
@@ -1053,6 +1099,8 @@ int corr_set_option(corr_t h, const char* key, double v) {
         return CORR_OK;
     } else if (k == "sample_bits") {
         if (v != 8 && v != 16) return fail(h, CORR_EINVAL, "sample_bits: 8 or 16");
+        if (h->iq && v != 8) return fail(h, CORR_EINVAL, "complex input takes int8 I/Q samples");
+        if (h->iq) return CORR_OK;
         if (h->stream_alloc) return fail(h, CORR_ESTATE, "sample_bits must be set before the first push");
         h->es = v == 16 ? 2 : 1;
     } else if (k == "window" || k == "kaiser_beta") {
@@ -1060,10 +1108,7 @@ int corr_set_option(corr_t h, const char* key, double v) {
         if (k == "kaiser_beta" && !(v >= 0 && v <= 50)) return fail(h, CORR_EINVAL, "kaiser_beta out of range");
         if (k == "window") h->window = (int)v;
         else h->kaiser_beta = v;
-        const std::vector<float> hf = make_filter(h->M, h->taps, h->window, h->kaiser_beta);
-        const std::vector<float> hsf = half_rows(hf, h->M, h->taps);
-        CK(cudaMemcpy(h->d_h, hf.data(), hf.size() * sizeof(float), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(h->d_hs, hsf.data(), hsf.size() * sizeof(float), cudaMemcpyHostToDevice));
+        CKRET(build_filter_tables(h));
     } else if (k == "result_slots") {
         if (v < 1 || v > 4096) return fail(h, CORR_EINVAL, "result_slots out of range");
         h->result_slots = (int)v;
@@ -1576,6 +1621,7 @@ int corr_spectrogram_dev(corr_t h, const void* d_samples, size_t n_samples, size
     const long long n_spec = (long long)(n_samples / (size_t)h->M);
     const long long rows = n_spec / n_row / 64 * 64;
     if (rows < 64 || h->n_chan % 256) return fail(h, CORR_EINVAL, "need >= 64 rows and n_chan % 256 == 0");
+    if (h->iq) return fail(h, CORR_EINVAL, "dynamic spectra are built for real input");
     CKRET(alloc_pipe(h, h->pd));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     CK(cudaMemsetAsync(d_tiles, 0, sizeof(float) * (size_t)h->n_in * rows * h->n_chan, st));
