@@ -1021,7 +1021,9 @@ def _roofline(wl, prec, args, dom, di, share, stage_ms, stage_n, S, n_in):
     launch duration.  The bound is the resource the kernel is closer to:
     HBM (measured copy peak) or FP32 arithmetic (measured FMA peak)."""
     W = WORKLOADS[wl]
-    fused = dom == "fft" and stage_n[0] == 0
+    # the fused F-engine runs no FIR launches (shares come from the untimed
+    # step with every stage bracketed)
+    fused = dom == "fft" and share.get("fir", 0.0) == 0.0
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs")
     peak_src = "measured" if hbm else "fallback"

@@ -129,6 +129,16 @@ const char* corr_last_error(corr_t h);
  *                  frequencies).  FP32 path only (CORR_EINVAL with reduced
  *                  precision, 16-bit samples or n_chan < 16); the dynamic
  *                  spectra call is for real input.  Before any buffers exist.
+ *   "tc_wait_ms"   (1 .. 60000, default 2000; may change at any time)
+ *                  limit of every bounded wait of the tensor-core X-engine
+ *                  (producer / MMA / epilogue barriers); on expiry the kernel
+ *                  records CORR_ETIMEDOUT (corr_device_status), frees its
+ *                  tensor memory and returns, leaving that integration's
+ *                  Gram matrices unwritten
+ *   "inject_stall" (0, default, or 1; may change at any time) fault
+ *                  injection for testing that path: the tensor-core
+ *                  X-engine's load producer issues nothing, so the MMA
+ *                  issuer's first wait expires after tc_wait_ms
  *   "window"       (0 Hann, default; 1 Kaiser; 2 unit coefficients) taper
  *                  of the prototype filter h = taper x sinc (Sec. 4.2; the
  *                  8-tap Kaiser of Fig. 4); 2 with taps = 1 is the plain

@@ -130,6 +130,8 @@ struct GramArgs {
     bool fp8;
     void* G;
     int* status;
+    unsigned long long wait_ns;   // limit of each bounded wait (0: the 2 s default)
+    int inject_stall;             // fault injection: the producer issues no loads
 };
 
 // Requantise spectra [s_begin, s_end) of the ring V (U = 2Y, unrotated) into

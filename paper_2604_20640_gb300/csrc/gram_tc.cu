@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(128, 1) gram_kernel(const __grid_constant__ CU
     const int ch = blockIdx.x;
     const int kt_elems = FP8 ? kKTile : kKTile / 2;
     const int num_k = (A.K + kt_elems - 1) / kt_elems;
+    const unsigned long long lim = A.wait_ns ? A.wait_ns : kWaitNs;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -105,11 +106,12 @@ __global__ void __launch_bounds__(128, 1) gram_kernel(const __grid_constant__ CU
     const uint32_t tmem = sh->tmem_addr;
 
     if (warp == 0 && lane == 0) {
-        // TMA producer
-        for (int it = 0; it < num_k; ++it) {
+        // TMA producer (with inject_stall it issues nothing: the MMA issuer's
+        // first wait on a full barrier then expires -- the test of this path)
+        for (int it = 0; it < (A.inject_stall ? 0 : num_k); ++it) {
             const int s = it % kStages;
             const uint32_t ph = (uint32_t)(it / kStages) & 1u;
-            if (!mbar_wait(&sh->empty[s], ph ^ 1u)) {
+            if (!mbar_wait(&sh->empty[s], ph ^ 1u, lim)) {
                 sh->abort = 1;
                 break;
             }
@@ -124,7 +126,7 @@ __global__ void __launch_bounds__(128, 1) gram_kernel(const __grid_constant__ CU
         for (int it = 0; it < num_k && ok; ++it) {
             const int s = it % kStages;
             const uint32_t ph = (uint32_t)(it / kStages) & 1u;
-            if (!mbar_wait(&sh->full[s], ph)) {
+            if (!mbar_wait(&sh->full[s], ph, lim)) {
                 ok = false;
                 break;
             }
@@ -142,7 +144,7 @@ __global__ void __launch_bounds__(128, 1) gram_kernel(const __grid_constant__ CU
     }
     __syncwarp();
     // Epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31.
-    if (!mbar_wait(&sh->accum, 0)) sh->abort = 1;
+    if (!mbar_wait(&sh->accum, 0, lim)) sh->abort = 1;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
     if (sh->abort) {

@@ -130,6 +130,8 @@ struct corr_s {
     float* d_hs = nullptr;       // half rows of d_h for the fused F-engine
     float2* d_tw = nullptr;
     int fused_f = 1;             // F-engine as one fused kernel where supported
+    double tc_wait_ms = 2000.0;  // limit of every bounded tensor-core wait
+    int inject_stall = 0;        // fault injection: tensor-core producer issues nothing
     Tables tab_stream, tab_direct;
     std::vector<double> tau, phi;            // latest values set
     std::vector<double> tau_pend, phi_pend;  // waiting for an integration boundary
@@ -604,6 +606,8 @@ int finalize_into(corr_t h, Pipe& p, const Tables& t, float2* R, uint8_t* F, int
         g.fp8 = h->precision == CORR_FP8;
         g.G = p.G;
         g.status = h->d_status;
+        g.wait_ns = (unsigned long long)(h->tc_wait_ms * 1e6);
+        g.inject_stall = h->inject_stall;
         int rc;
         {
             Timed t_(h, 6, st);
@@ -1041,7 +1045,8 @@ const char* corr_last_error(corr_t h) {
 int corr_set_option(corr_t h, const char* key, double v) {
     if (!h || !key) return fail(h, CORR_EINVAL, "NULL argument");
     const std::string k(key);
-    if (h->started && k != "stage_timing" && k != "stage_mask" && k != "fir_spt" && k != "fused_f")
+    if (h->started && k != "stage_timing" && k != "stage_mask" && k != "fir_spt" && k != "fused_f" &&
+        k != "tc_wait_ms" && k != "inject_stall")
         return fail(h, CORR_ESTATE, "options must be set before the first push");
     if (k == "flag_sigma") {
         if (!(v > 0)) return fail(h, CORR_EINVAL, "flag_sigma must be > 0");
@@ -1081,6 +1086,14 @@ int corr_set_option(corr_t h, const char* key, double v) {
         if (h->stream_alloc) return fail(h, CORR_ESTATE, "ring_mb must be set before the first push");
         h->ring_mb = (int)v;
         free_pipe(h->pd);
+    } else if (k == "tc_wait_ms") {
+        if (!(v >= 1.0 && v <= 60000.0)) return fail(h, CORR_EINVAL, "tc_wait_ms: 1 .. 60000");
+        h->tc_wait_ms = v;
+        return CORR_OK;
+    } else if (k == "inject_stall") {
+        if (v != 0 && v != 1) return fail(h, CORR_EINVAL, "inject_stall: 0 or 1");
+        h->inject_stall = (int)v;
+        return CORR_OK;
     } else if (k == "fused_f") {
         if (v != 0 && v != 1) return fail(h, CORR_EINVAL, "fused_f: 0 or 1");
         h->fused_f = (int)v;
@@ -1350,6 +1363,8 @@ int corr_gram_dev(corr_t h, const void* d_Q, int n_chan, int k_pitch, int K, int
     a.fp8 = dtype == CORR_FP8;
     a.G = d_G;
     a.status = h->d_status;
+    a.wait_ns = (unsigned long long)(h->tc_wait_ms * 1e6);
+    a.inject_stall = h->inject_stall;
     int rc;
     {
         Timed t_(h, 2, static_cast<cudaStream_t>(stream));
