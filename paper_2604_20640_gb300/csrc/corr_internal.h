@@ -107,7 +107,7 @@ struct XArgs {
     long long int_start, int_end, s_limit;
     int G, j0, n_groups;
     float* part;             // [gpi][nt][32][n_chan]
-    int pair_major;          // V pair-major (n_in_pad <= 8 only), see FftArgs
+    int pair_major;          // V pair-major, see FftArgs
 };
 
 // Finalise: R[k][a][b] = scale * Q_a[k] conj(Q_b[k]) * (sum over partial
@@ -147,6 +147,7 @@ struct RequantArgs {
     long long s_begin, s_end, int_start;
     int n_in, n_in_pad, n_chan;
     bool fp8;
+    int pair_major;          // V pair-major ([slot][pair][n_chan] float4)
 };
 
 // R[k][a][b] = scale_a scale_b / (4 count) rot_a conj(rot_b) sum q_a conj(q_b),
@@ -202,7 +203,7 @@ void launch_finalize_q(const FinQArgs& a, cudaStream_t st);
 // [s0, s0 + n) of the ring (first integration of a stream) and c the
 // component share of the power: 1/2, or 1 in the real DC channel k = 0.
 void launch_scale_from_ring(const float2* V, long long v_origin, long long v_mask, long long s0, int n, int n_in,
-                            int n_in_pad, int n_chan, float gain, float* scale, cudaStream_t st);
+                            int n_in_pad, int n_chan, float gain, float* scale, int pair_major, cudaStream_t st);
 // scale[a][k] = 2 sqrt(c R_aa[k]) / gain (U = 2V, c as above) from an
 // integration's R.
 void launch_scale_from_vis(const float2* R, int n_in, int n_in_pad, int n_chan, float gain, float* scale,

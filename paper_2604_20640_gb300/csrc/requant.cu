@@ -108,15 +108,78 @@ __global__ void __launch_bounds__(256) requant_kernel(const RequantArgs A) {
     }
 }
 
+// Pair-major ring ([slot][pair][n_chan] float4: the pair's two complex
+// values): one thread per (input pair, channel), consecutive channels across
+// the warp (coalesced 16-byte reads), a run of RUN spectra per thread; the
+// pair's four rows (Re a, Re b, Im a, Im b) each get one whole 32-byte sector
+// of codes.
+template <bool FP8>
+__global__ void __launch_bounds__(128) requant_pm_kernel(const RequantArgs A) {
+    constexpr int RUN = FP8 ? 32 : 16;
+    constexpr int EB = FP8 ? 1 : 2;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int pr = blockIdx.y;
+    if (k >= A.n_chan) return;
+    const int N = A.n_in;
+    const int a0 = 2 * pr, a1 = 2 * pr + 1;
+    const int n_pairs = A.n_in_pad >> 1;
+    const long long sb = A.s_begin + (long long)blockIdx.z * RUN;
+    if (sb >= A.s_end) return;
+    const int ns = (int)((A.s_end - sb) < RUN ? (A.s_end - sb) : RUN);
+    const float inv0 = a0 < N ? 1.0f / A.scale[(size_t)a0 * A.n_chan + k] : 0.f;
+    const float inv1 = a1 < N ? 1.0f / A.scale[(size_t)a1 * A.n_chan + k] : 0.f;
+    uint32_t w[4][8];                 // rows Re a0, Im a0, Re a1, Im a1
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) w[r][j] = 0u;
+    const float4* V4 = reinterpret_cast<const float4*>(A.V);
+#pragma unroll
+    for (int i = 0; i < RUN; ++i) {
+        float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < ns) {
+            const long long slot = (sb + i - A.v_origin) & A.v_mask;
+            u = __ldg(V4 + ((size_t)slot * n_pairs + pr) * A.n_chan + k);
+        }
+        const float x[4] = {u.x * inv0, u.y * inv0, u.z * inv1, u.w * inv1};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            if constexpr (FP8) w[r][i / 4] |= (uint32_t)q_e4m3(x[r]) << (8 * (i % 4));
+            else w[r][i / 2] |= (uint32_t)code_bf16(q_int8(x[r])) << (16 * (i % 2));
+        }
+    }
+    const long long col = sb - A.int_start;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int a = (r < 2) ? a0 : a1;
+        if (a >= N) continue;                        // padding inputs have no rows
+        const int row = (r & 1) ? N + a : a;
+        uint8_t* dst = A.Q + ((size_t)k * 128 + row) * A.k_pitch + col * EB;
+        if (ns == RUN && ((col * EB) & 15) == 0) {
+            uint4* d = reinterpret_cast<uint4*>(dst);
+            d[0] = make_uint4(w[r][0], w[r][1], w[r][2], w[r][3]);
+            d[1] = make_uint4(w[r][4], w[r][5], w[r][6], w[r][7]);
+        } else {
+            for (int i = 0; i < ns; ++i)
+                for (int e = 0; e < EB; ++e) {
+                    const int bitpos = 8 * (i * EB + e);
+                    dst[i * EB + e] = (uint8_t)(w[r][bitpos / 32] >> (bitpos % 32));
+                }
+        }
+    }
+}
+
 __global__ void scale_ring_kernel(const float2* V, long long v_origin, long long v_mask, long long s0, int n,
-                                  int n_in, int n_in_pad, int n_chan, float gain, float* scale) {
+                                  int n_in, int n_in_pad, int n_chan, float gain, float* scale, int pm) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int a = blockIdx.y;
     if (k >= n_chan || a >= n_in) return;
     float p = 0.f;
     for (int i = 0; i < n; ++i) {
         const long long slot = (s0 + i - v_origin) & v_mask;
-        const float2 u = V[((size_t)slot * n_chan + k) * n_in_pad + a];
+        // channel-major [slot][k][a], or pair-major [slot][a/2][k][a%2]
+        const float2 u = pm ? V[(((size_t)slot * (n_in_pad >> 1) + (a >> 1)) * n_chan + k) * 2 + (a & 1)]
+                            : V[((size_t)slot * n_chan + k) * n_in_pad + a];
         p = fmaf(u.x, u.x, fmaf(u.y, u.y, p));
     }
     p /= (float)n;
@@ -173,15 +236,23 @@ __global__ void finalize_q_kernel(const FinQArgs F) {
 void launch_requant(const RequantArgs& a, cudaStream_t st) {
     const long long n = a.s_end - a.s_begin;
     if (n <= 0) return;
+    if (a.pair_major) {
+        const int run = a.fp8 ? 32 : 16;
+        dim3 grid((unsigned)((a.n_chan + 127) / 128), (unsigned)(a.n_in_pad / 2), (unsigned)((n + run - 1) / run));
+        if (a.fp8) requant_pm_kernel<true><<<grid, 128, 0, st>>>(a);
+        else requant_pm_kernel<false><<<grid, 128, 0, st>>>(a);
+        return;
+    }
     dim3 grid((unsigned)a.n_chan, (unsigned)((n + kTileS - 1) / kTileS));
     if (a.fp8) requant_kernel<true><<<grid, 256, 0, st>>>(a);
     else requant_kernel<false><<<grid, 256, 0, st>>>(a);
 }
 
 void launch_scale_from_ring(const float2* V, long long v_origin, long long v_mask, long long s0, int n, int n_in,
-                            int n_in_pad, int n_chan, float gain, float* scale, cudaStream_t st) {
+                            int n_in_pad, int n_chan, float gain, float* scale, int pair_major, cudaStream_t st) {
     dim3 grid((unsigned)((n_chan + 127) / 128), (unsigned)n_in);
-    scale_ring_kernel<<<grid, 128, 0, st>>>(V, v_origin, v_mask, s0, n, n_in, n_in_pad, n_chan, gain, scale);
+    scale_ring_kernel<<<grid, 128, 0, st>>>(V, v_origin, v_mask, s0, n, n_in, n_in_pad, n_chan, gain, scale,
+                                            pair_major);
 }
 
 void launch_scale_from_vis(const float2* R, int n_in, int n_in_pad, int n_chan, float gain, float* scale,

@@ -368,9 +368,11 @@ int alloc_pipe(corr_t h, Pipe& p) {
     return CORR_OK;
 }
 
-// The FP32 pipeline with the small-N X-engine keeps its spectra ring
-// pair-major (FftArgs::pair_major); every other reader wants channel-major.
-bool pair_major_ring(corr_t h) { return h->precision == CORR_FP32 && h->n_in_pad <= 8 && !h->iq; }
+// Every real-input pipeline keeps its spectra ring pair-major: one F-engine
+// CTA transforms one input pair and writes its channels contiguously, and the
+// X-engines and the requantiser read consecutive channels across a warp.
+// Complex input keeps the channel-major ring.
+bool pair_major_ring(corr_t h) { return !h->iq; }
 
 // Filter, half-row and twiddle tables for the handle's current M, window
 // and taps (replaces the device copies; sizes follow M).
@@ -514,7 +516,8 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
                 if (have >= want || (closing && have > 0)) {
                     const int n = (int)(have < want ? have : want);
                     launch_scale_from_ring(p.V, 0, p.v_cap - 1, istart, n, h->n_in, h->n_in_pad, h->n_chan,
-                                           h->precision == CORR_FP8 ? kFp8Gain : kInt8Gain, p.scale, st);
+                                           h->precision == CORR_FP8 ? kFp8Gain : kInt8Gain, p.scale,
+                                           pair_major_ring(h), st);
                     ++h->launches;
                     CK(cudaGetLastError());
                     p.have_scale = true;
@@ -535,6 +538,7 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
                 r.n_in_pad = h->n_in_pad;
                 r.n_chan = h->n_chan;
                 r.fp8 = h->precision == CORR_FP8;
+                r.pair_major = pair_major_ring(h);
                 {
                     Timed t_(h, 5, st);
                     launch_requant(r, st);

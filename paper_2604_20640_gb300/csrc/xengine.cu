@@ -21,6 +21,8 @@ __device__ __forceinline__ void tile_decode(int t, int nb, int& A, int& B) {
     B = r + rem;
 }
 
+// PM: spectra pair-major ([slot][pair][n_chan] float4), else channel-major.
+template <bool PM>
 __global__ void __launch_bounds__(128) xengine_kernel(const XArgs X) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int t = blockIdx.y;
@@ -36,12 +38,24 @@ __global__ void __launch_bounds__(128) xengine_kernel(const XArgs X) {
     float acc[32];
 #pragma unroll
     for (int e = 0; e < 32; ++e) acc[e] = 0.f;
-    const int q4 = X.n_in_pad >> 1;   // float4 per (slot, channel)
+    const int q4 = X.n_in_pad >> 1;   // float4 (input pairs) per (slot, channel)
     for (long long s = s0; s < s1; ++s) {
         const long long slot = (s - X.v_origin) & X.v_mask;
-        const float4* vp = reinterpret_cast<const float4*>(X.V) + ((size_t)slot * X.n_chan + k) * q4;
-        const float4 a01 = __ldg(vp + 2 * A), a23 = __ldg(vp + 2 * A + 1);
-        const float4 b01 = __ldg(vp + 2 * B), b23 = __ldg(vp + 2 * B + 1);
+        float4 a01, a23, b01, b23;
+        if constexpr (PM) {
+            // pair p of this slot at [(slot * q4 + p) * n_chan + k]
+            const float4* vp = reinterpret_cast<const float4*>(X.V) + (size_t)slot * q4 * X.n_chan + k;
+            a01 = __ldg(vp + (size_t)(2 * A) * X.n_chan);
+            a23 = __ldg(vp + (size_t)(2 * A + 1) * X.n_chan);
+            b01 = __ldg(vp + (size_t)(2 * B) * X.n_chan);
+            b23 = __ldg(vp + (size_t)(2 * B + 1) * X.n_chan);
+        } else {
+            const float4* vp = reinterpret_cast<const float4*>(X.V) + ((size_t)slot * X.n_chan + k) * q4;
+            a01 = __ldg(vp + 2 * A);
+            a23 = __ldg(vp + 2 * A + 1);
+            b01 = __ldg(vp + 2 * B);
+            b23 = __ldg(vp + 2 * B + 1);
+        }
         const float ar[4] = {a01.x, a01.z, a23.x, a23.z}, ai[4] = {a01.y, a01.w, a23.y, a23.w};
         const float br[4] = {b01.x, b01.z, b23.x, b23.z}, bi[4] = {b01.y, b01.w, b23.y, b23.w};
 #pragma unroll
@@ -266,7 +280,8 @@ void launch_xengine(const XArgs& a, cudaStream_t st) {
         return;
     }
     dim3 grid((a.n_chan + 127) / 128, a.nt, a.n_groups);
-    xengine_kernel<<<grid, 128, 0, st>>>(a);
+    if (a.pair_major) xengine_kernel<true><<<grid, 128, 0, st>>>(a);
+    else xengine_kernel<false><<<grid, 128, 0, st>>>(a);
 }
 
 void launch_finalize(const FinArgs& a, cudaStream_t st) {
