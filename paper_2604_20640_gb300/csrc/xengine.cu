@@ -204,63 +204,107 @@ __global__ void __launch_bounds__(128) finalize_kernel(const FinArgs F) {
 
 // ---- MAD flagging, Eq. 2 ------------------------------------------------
 // One warp per (integration, window, baseline a <= b).  Order statistics are
-// exact: every value's rank (ties broken by position) is counted against the
-// whole window, the value is stored at its rank, and the median is read from
-// the sorted array (even count: mean of the two middle values).
-constexpr int kMaxWindow = 256;
+// exact: the warp sorts the window's W values (E = max(W, 32) / 32 per lane,
+// element i = lane E + e, padding +inf) with a bitonic network -- exchanges
+// between registers below distance E, by shuffles above -- and reads the
+// median from the sorted order (even count: mean of the two middle values),
+// then sorts |A - med| the same way for the MAD.
 constexpr int kFlagWarps = 4;
 
-__device__ float warp_median(const float* v, float* sorted, int W, int lane) {
-    for (int c = lane; c < W; c += 32) {
-        const float x = v[c];
-        int rank = 0;
-        for (int d = 0; d < W; ++d) {
-            const float y = v[d];
-            rank += (y < x) || (y == x && d < c);
+template <int E>
+__device__ __forceinline__ void warp_bitonic_sort(float (&v)[E], int lane) {
+    constexpr int n = 32 * E;
+#pragma unroll
+    for (int k = 2; k <= n; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j < E) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int ep = e ^ j;
+                    if (ep > e) {
+                        const int i = lane * E + e;
+                        const bool asc = (i & k) == 0;
+                        const float lo = fminf(v[e], v[ep]), hi = fmaxf(v[e], v[ep]);
+                        v[e] = asc ? lo : hi;
+                        v[ep] = asc ? hi : lo;
+                    }
+                }
+            } else {
+                const int lm = j / E;                  // partner lane distance
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const float o = __shfl_xor_sync(0xffffffffu, v[e], lm);
+                    const int i = lane * E + e;
+                    const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
+                    v[e] = keep_min ? fminf(v[e], o) : fmaxf(v[e], o);
+                }
+            }
         }
-        sorted[rank] = x;
     }
-    __syncwarp();
-    const float med = (W & 1) ? sorted[W >> 1] : 0.5f * (sorted[(W >> 1) - 1] + sorted[W >> 1]);
-    __syncwarp();
-    return med;
 }
 
+// Element i of a sorted warp array (i uniform over the warp).
+template <int E>
+__device__ __forceinline__ float warp_sorted_at(const float (&v)[E], int i) {
+    const int src = i / E, e = i % E;
+    float x = v[0];
+#pragma unroll
+    for (int q = 1; q < E; ++q)
+        if (q == e) x = v[q];
+    return __shfl_sync(0xffffffffu, x, src);
+}
+
+template <int E>
+__device__ __forceinline__ float warp_sorted_median(const float (&v)[E], int W) {
+    return (W & 1) ? warp_sorted_at<E>(v, W >> 1)
+                   : 0.5f * (warp_sorted_at<E>(v, (W >> 1) - 1) + warp_sorted_at<E>(v, W >> 1));
+}
+
+template <int E>
 __global__ void __launch_bounds__(32 * kFlagWarps) mad_flag_kernel(const float2* R, uint8_t* F, int n_vis,
-                                                                   int n_chan, int n_in, int W,
-                                                                   float sigma) {
-    __shared__ float sm[kFlagWarps][3][kMaxWindow];
+                                                                   int n_chan, int n_in, int W, float sigma) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_bl = n_in * (n_in + 1) / 2;
     const int n_win = n_chan / W;
     const long long item = (long long)blockIdx.x * kFlagWarps + warp;
-    if (item >= (long long)n_vis * n_win * n_bl) return;
+    if (item >= (long long)n_vis * n_win * n_bl) return;   // uniform over the warp
     const int bl = (int)(item % n_bl);
     const int w = (int)((item / n_bl) % n_win);
     const int i = (int)(item / ((long long)n_bl * n_win));
     int a = 0, rem = bl;
     while (rem >= n_in - a) { rem -= n_in - a; ++a; }
     const int b = a + rem;
-    float* vA = sm[warp][0];
-    float* vS = sm[warp][1];
-    float* vD = sm[warp][2];
     const size_t base = (size_t)i * n_chan * n_in * n_in;
-    for (int c = lane; c < W; c += 32) {
-        const int k = w * W + c;
-        const float2 r = R[base + ((size_t)k * n_in + a) * n_in + b];
-        vA[c] = sqrtf(r.x * r.x + r.y * r.y);
+    float A[E], v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int c = lane * E + e;
+        if (c < W) {
+            const int k = w * W + c;
+            const float2 r = R[base + ((size_t)k * n_in + a) * n_in + b];
+            A[e] = sqrtf(r.x * r.x + r.y * r.y);
+        } else {
+            A[e] = __int_as_float(0x7f800000);          // +inf: sorts after every value
+        }
+        v[e] = A[e];
     }
-    __syncwarp();
-    const float med = warp_median(vA, vS, W, lane);
-    for (int c = lane; c < W; c += 32) vD[c] = fabsf(vA[c] - med);
-    __syncwarp();
-    const float mad = warp_median(vD, vS, W, lane);
+    warp_bitonic_sort<E>(v, lane);
+    const float med = warp_sorted_median<E>(v, W);
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = (lane * E + e < W) ? fabsf(A[e] - med) : __int_as_float(0x7f800000);
+    warp_bitonic_sort<E>(v, lane);
+    const float mad = warp_sorted_median<E>(v, W);
     const float T = med + sigma * mad * 1.4826f;
-    for (int c = lane; c < W; c += 32) {
-        const int k = w * W + c;
-        const uint8_t f = vA[c] > T ? 1 : 0;
-        F[base + ((size_t)k * n_in + a) * n_in + b] = f;
-        F[base + ((size_t)k * n_in + b) * n_in + a] = f;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int c = lane * E + e;
+        if (c < W) {
+            const int k = w * W + c;
+            const uint8_t f = A[e] > T ? 1 : 0;
+            F[base + ((size_t)k * n_in + a) * n_in + b] = f;
+            F[base + ((size_t)k * n_in + b) * n_in + a] = f;
+        }
     }
 }
 
@@ -294,7 +338,10 @@ void launch_mad_flags(const float2* R, uint8_t* F, int n_vis, int n_chan, int n_
     const long long items = (long long)n_vis * (n_chan / window) * (n_in * (n_in + 1) / 2);
     if (items <= 0) return;
     const unsigned blocks = (unsigned)((items + kFlagWarps - 1) / kFlagWarps);
-    mad_flag_kernel<<<blocks, 32 * kFlagWarps, 0, st>>>(R, F, n_vis, n_chan, n_in, window, sigma);
+    if (window <= 32) mad_flag_kernel<1><<<blocks, 32 * kFlagWarps, 0, st>>>(R, F, n_vis, n_chan, n_in, window, sigma);
+    else if (window <= 64) mad_flag_kernel<2><<<blocks, 32 * kFlagWarps, 0, st>>>(R, F, n_vis, n_chan, n_in, window, sigma);
+    else if (window <= 128) mad_flag_kernel<4><<<blocks, 32 * kFlagWarps, 0, st>>>(R, F, n_vis, n_chan, n_in, window, sigma);
+    else mad_flag_kernel<8><<<blocks, 32 * kFlagWarps, 0, st>>>(R, F, n_vis, n_chan, n_in, window, sigma);
 }
 
 }  // namespace corr
