@@ -163,6 +163,20 @@ class Group:
             raise CorrError(rc, self._L.corr_last_error(self._h).decode())
         return list(out)
 
+    def set_option(self, key: str, value: float):
+        """Options of the group's own tail kernel ("tc_wait_ms", "inject_stall")."""
+        rc = self._L.corr_set_option(self._h, key.encode(), float(value))
+        if rc != CORR_OK:
+            raise CorrError(rc, self._L.corr_last_error(self._h).decode())
+
+    def device_status(self) -> int:
+        """The group's device status word (CORR_ETIMEDOUT from its tail kernel), cleared on read."""
+        st = _i()
+        rc = self._L.corr_device_status(self._h, ctypes.byref(st))
+        if rc != CORR_OK:
+            raise CorrError(rc, self._L.corr_last_error(self._h).decode())
+        return st.value
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             self._L.corr_destroy(self._h)

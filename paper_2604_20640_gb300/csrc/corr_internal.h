@@ -120,6 +120,43 @@ struct FinArgs {
     float2* R;               // [n_chan][n_in][n_in]
 };
 
+// Persistent tail of a group replay (batched sub-array streams): one launch
+// finalises the integrations the members' FP32 pipelines deferred and
+// computes every member's MAD flags, pulling work items from a device queue
+// built when the group's graph is captured.  Items are claimed in queue
+// order by an atomic ticket: all finalise items come first, so a flag item
+// only ever waits (bounded by %globaltimer) for items already claimed by
+// running CTAs that never wait themselves.
+struct TailMember {
+    FinArgs fin;             // FP32 members: partial sums and R of integration 0
+    long long part_stride;   // floats between integrations' partial sums
+    long long vis_stride;    // complex values between integrations' R (and flags)
+    uint8_t* flags;          // flags of integration 0, or null (no flagging)
+    int window;              // MAD window W (a power of two <= 256)
+    float sigma;
+};
+struct TailItem {
+    int kind;                // 0: a finalise block (x, y, z); 1: MAD flags of warp items x .. x+63
+    int member, integration;
+    int x, y, z;
+    int dep;                 // dependency counter of (member, integration)
+    int need;                // finalise blocks that must be done first (flag items)
+};
+struct TailArgs {
+    const TailMember* members;
+    const TailItem* items;
+    int n_items;
+    int* ticket;             // zero before the launch
+    int* done;               // per (member, integration): finalise blocks done; zero before
+    unsigned long long wait_ns;
+    int* status;             // set to CORR_ETIMEDOUT when a wait expires
+    int inject_skip;         // fault injection: this finalise item never counts itself done (-1: none)
+};
+constexpr int kTailWarpItems = 64;   // MAD warp items per flag item (16 per warp)
+void launch_group_tail(const TailArgs& a, int grid, cudaStream_t st);
+// CTAs of the tail kernel resident at once (the persistent grid).
+int group_tail_grid();
+
 // Tensor-core Gram matrix G[c] = Q[c] Q[c]^T, Q [n_chan][128 rows][k_pitch
 // bytes] of BF16 (int8 codes) or e4m3, K valid elements per row (later ones
 // read as zero); G [n_chan][128][128] FP32.  status: device word set to

@@ -32,6 +32,10 @@ struct Pipe {
     float2* Z = nullptr;      // ring of FIR outputs (same capacity)
     int v_cap = 0;
     float* part = nullptr;    // [gpi][nt][32][n_chan]
+    // partial sums of every integration of a run whose finalisation is
+    // deferred to a group's tail kernel: [integration][gpi][nt][32][n_chan]
+    float* part_all = nullptr;
+    long long part_all_ints = 0;
     // reduced-precision path (tensor-core X-engine)
     uint8_t* Q = nullptr;     // [n_chan][128][q_pitch] codes of one integration
     int q_pitch = 0;          // bytes per row (multiple of 128)
@@ -130,6 +134,12 @@ struct corr_s {
     float* d_hs = nullptr;       // half rows of d_h for the fused F-engine
     float2* d_tw = nullptr;
     int fused_f = 1;             // F-engine as one fused kernel where supported
+    bool defer_tail = false;     // inside a group call: finalise / flag in the group's tail kernel
+    // group: the tail kernel's work queue (device) and its counters
+    TailMember* d_tail_members = nullptr;
+    TailItem* d_tail_items = nullptr;
+    int* d_tail_counters = nullptr;   // [0] ticket, [1..] per (member, integration) done counts
+    int tail_items = 0, tail_deps = 0, tail_grid = 0, tail_fin_items = 0;
     double tc_wait_ms = 2000.0;  // limit of every bounded tensor-core wait
     int inject_stall = 0;        // fault injection: tensor-core producer issues nothing
     Tables tab_stream, tab_direct;
@@ -567,7 +577,9 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
                 x.G = h->G;
                 x.j0 = j_begin;
                 x.n_groups = j_end - j_begin;
-                x.part = p.part;
+                // finalisation deferred to a group's tail: each integration
+                // keeps its own partial sums
+                x.part = h->defer_tail ? p.part_all + (size_t)i * h->gpi * h->nt * 32 * h->n_chan : p.part;
                 x.pair_major = pair_major_ring(h);
                 {
                     Timed t_(h, 2, st);
@@ -725,6 +737,15 @@ int sink_direct(corr_t h, void* vctx, const Tables& t, long long i, int count, i
     DirectCtx* c = static_cast<DirectCtx*>(vctx);
     if (i >= c->max_int) return fail(h, CORR_EINVAL, "max_int too small for the stream");
     const size_t ne = vis_elems(h);
+    if (h->defer_tail) {
+        // inside a group: the group's tail kernel finalises FP32
+        // integrations and flags every integration; the reduced-precision
+        // finalisation stays here (its autocorrelations set the next scales)
+        if (h->precision != CORR_FP32)
+            CKRET(finalize_into(h, h->pd, t, c->vis + (size_t)i * ne, nullptr, count, slots, st));
+        c->n_out = (int)i + 1;
+        return CORR_OK;
+    }
     CKRET(finalize_into(h, h->pd, t, c->vis + (size_t)i * ne, c->flags ? c->flags + (size_t)i * ne : nullptr,
                         count, slots, st));
     c->n_out = (int)i + 1;
@@ -901,6 +922,7 @@ void free_pipe(Pipe& p) {
     if (p.G) cudaFree(p.G);
     if (p.scale) cudaFree(p.scale);
     if (p.part) cudaFree(p.part);
+    if (p.part_all) cudaFree(p.part_all);
     p = Pipe{};
 }
 
@@ -990,6 +1012,10 @@ int corr_destroy(corr_t h) {
         if (h->gout) cudaEventDestroy(h->gout);
         if (h->gexec) cudaGraphExecDestroy(h->gexec);
         if (h->graph) cudaGraphDestroy(h->graph);
+        cudaFree(h->d_tail_members);
+        cudaFree(h->d_tail_items);
+        cudaFree(h->d_tail_counters);
+        cudaFree(h->d_status);
         cudaGetLastError();
         delete h;
         return CORR_OK;
@@ -1240,6 +1266,12 @@ int corr_run_dev(corr_t h, const void* d_samples, size_t n_samples, size_t strid
     long long need = n_spec / h->n_int + ((include_partial && n_spec % h->n_int) ? 1 : 0);
     if (need > max_int) return fail(h, CORR_EINVAL, "max_int too small for the stream");
     CKRET(alloc_pipe(h, h->pd));
+    if (h->defer_tail && h->precision == CORR_FP32 && h->pd.part_all_ints < need) {
+        cudaFree(h->pd.part_all);
+        h->pd.part_all = nullptr;
+        CK(cudaMalloc(&h->pd.part_all, sizeof(float) * (size_t)need * h->gpi * h->nt * 32 * h->n_chan));
+        h->pd.part_all_ints = need;
+    }
     h->pd.s_next = h->pd.s_xdone = 0;
     h->pd.have_scale = false;
     StreamView sv;
@@ -1381,6 +1413,79 @@ int corr_gram_dev(corr_t h, const void* d_Q, int n_chan, int k_pitch, int K, int
 
 // ---- batched sub-array streams: one captured graph --------------------------
 
+namespace {
+
+// The work queue of a group's tail kernel for one capture: every FP32
+// member's integrations as finalise blocks (the blocks finalize_kernel would
+// run), then every member's MAD flags in items of kTailWarpItems warp items,
+// each depending on its integration's finalise blocks; uploaded before the
+// capture so that the capture records only the counter reset and the launch.
+int build_group_tail(corr_t g, const size_t* n_samples, float* const* d_vis, uint8_t* const* d_flags) {
+    corr_t h = g;
+    const int n = (int)g->members.size();
+    std::vector<TailMember> mem(n);
+    std::vector<TailItem> fin, flg;
+    int deps = 0;
+    for (int m = 0; m < n; ++m) {
+        corr_t c = g->members[m];
+        TailMember& tm = mem[m];
+        tm = TailMember{};
+        const long long n_out = (long long)(n_samples[m] / (size_t)c->M) / c->n_int;
+        tm.fin.part = c->pd.part_all;
+        tm.fin.rot = c->tab_direct.rot;
+        tm.fin.n_slots = c->gpi;
+        tm.fin.nt = c->nt;
+        tm.fin.n_chan = c->n_chan;
+        tm.fin.n_in = c->n_in;
+        tm.fin.scale = 0.25f / (float)c->n_int;
+        tm.fin.R = reinterpret_cast<float2*>(d_vis[m]);
+        tm.part_stride = (long long)c->gpi * c->nt * 32 * c->n_chan;
+        tm.vis_stride = (long long)vis_elems(c);
+        tm.flags = d_flags ? d_flags[m] : nullptr;
+        tm.window = c->flag_window < c->n_chan ? c->flag_window : c->n_chan;
+        tm.sigma = (float)c->flag_sigma;
+        const bool fp32 = c->precision == CORR_FP32;
+        if (fp32 && !c->pd.part_all && n_out > 0) return fail(g, CORR_ESTATE, "member partial sums missing");
+        for (long long i = 0; i < n_out; ++i) {
+            const int dep = deps++;
+            int need = 0;
+            if (fp32) {
+                for (int bx = 0; bx < (c->n_chan + 127) / 128; ++bx)
+                    for (int t = 0; t < c->nt; ++t)
+                        for (int z = 0; z < 16; ++z, ++need)
+                            fin.push_back(TailItem{0, m, (int)i, bx, t, z, dep, 0});
+            }
+            if (tm.flags) {
+                const long long n_wi = (long long)(c->n_chan / tm.window) * (c->n_in * (c->n_in + 1) / 2);
+                for (long long x = 0; x < n_wi; x += kTailWarpItems)
+                    flg.push_back(TailItem{1, m, (int)i, (int)x, 0, 0, dep, need});
+            }
+        }
+    }
+    std::vector<TailItem> items(fin);
+    items.insert(items.end(), flg.begin(), flg.end());
+    cudaFree(g->d_tail_members);
+    cudaFree(g->d_tail_items);
+    cudaFree(g->d_tail_counters);
+    g->d_tail_members = nullptr;
+    g->d_tail_items = nullptr;
+    g->d_tail_counters = nullptr;
+    g->tail_items = (int)items.size();
+    g->tail_fin_items = (int)fin.size();
+    g->tail_deps = deps;
+    if (items.empty()) return CORR_OK;
+    CK(cudaMalloc(&g->d_tail_members, sizeof(TailMember) * mem.size()));
+    CK(cudaMalloc(&g->d_tail_items, sizeof(TailItem) * items.size()));
+    CK(cudaMalloc(&g->d_tail_counters, sizeof(int) * (size_t)(1 + deps)));
+    CK(cudaMemcpy(g->d_tail_members, mem.data(), sizeof(TailMember) * mem.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(g->d_tail_items, items.data(), sizeof(TailItem) * items.size(), cudaMemcpyHostToDevice));
+    if (!g->tail_grid) g->tail_grid = group_tail_grid();
+    return CORR_OK;
+}
+
+}  // namespace
+
+
 int corr_group_create(corr_t* out, const corr_t* members, int n) {
     if (!out || !members || n < 1 || n > 64) return fail(nullptr, CORR_EINVAL, "bad group arguments");
     *out = nullptr;
@@ -1404,6 +1509,8 @@ int corr_group_create(corr_t* out, const corr_t* members, int n) {
     for (int i = 0; i < n && ok; ++i)
         ok = cudaStreamCreateWithFlags(&g->mstreams[i], cudaStreamNonBlocking) == cudaSuccess &&
              cudaEventCreateWithFlags(&g->mjoin[i], cudaEventDisableTiming) == cudaSuccess;
+    if (ok) ok = cudaMalloc(&g->d_status, sizeof(int)) == cudaSuccess &&
+                 cudaMemset(g->d_status, 0, sizeof(int)) == cudaSuccess;
     if (!ok) {
         corr_destroy(g);
         return fail(nullptr, CORR_ECUDA, "group stream/event creation failed");
@@ -1435,7 +1542,21 @@ int corr_group_run_dev(corr_t g, const void* const* d_samples, const size_t* n_s
         key.push_back(d_flags ? d_flags[i] : nullptr);
         key.push_back(reinterpret_cast<const void*>((size_t)max_int[i]));
     }
+    // the tail kernel's wait limit and fault injection are captured values too
+    key.push_back(reinterpret_cast<const void*>((size_t)(g->tc_wait_ms * 1e3)));
+    key.push_back(reinterpret_cast<const void*>((size_t)g->inject_stall));
     if (!g->gexec || key != g->gkey) {
+        // Members defer finalisation (FP32) and flagging to the group's tail
+        // kernel while the group runs them.
+        struct DeferGuard {
+            corr_s* g;
+            explicit DeferGuard(corr_s* g_) : g(g_) {
+                for (corr_s* m : g->members) m->defer_tail = true;
+            }
+            ~DeferGuard() {
+                for (corr_s* m : g->members) m->defer_tail = false;
+            }
+        } defer(g);
         if (g->gexec) {
             cudaGraphExecDestroy(g->gexec);
             g->gexec = nullptr;
@@ -1457,6 +1578,7 @@ int corr_group_run_dev(corr_t g, const void* const* d_samples, const size_t* n_s
             if (rc != CORR_OK) return fail(g, rc, std::string("member ") + std::to_string(i) + ": " + m->err);
         }
         CK(cudaStreamSynchronize(origin));
+        CKRET(build_group_tail(g, n_samples, d_vis, d_flags));
         CK(cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal));
         long long k0 = 0;
         for (int i = 0; i < n; ++i) k0 += g->members[i]->launches;
@@ -1478,6 +1600,23 @@ int corr_group_run_dev(corr_t g, const void* const* d_samples, const size_t* n_s
                                   cudaStreamWaitEvent(origin, g->mjoin[i], 0) != cudaSuccess))
                 rc = CORR_ECUDA;
         }
+        // the persistent tail over every member: finalise + flags
+        if (rc == CORR_OK && g->tail_items > 0) {
+            if (cudaMemsetAsync(g->d_tail_counters, 0, sizeof(int) * (size_t)(1 + g->tail_deps), origin) !=
+                cudaSuccess)
+                rc = CORR_ECUDA;
+            TailArgs ta{};
+            ta.members = g->d_tail_members;
+            ta.items = g->d_tail_items;
+            ta.n_items = g->tail_items;
+            ta.ticket = g->d_tail_counters;
+            ta.done = g->d_tail_counters + 1;
+            ta.wait_ns = (unsigned long long)(g->tc_wait_ms * 1e6);
+            ta.status = g->d_status;
+            ta.inject_skip = (g->inject_stall && g->tail_fin_items > 0) ? 0 : -1;
+            launch_group_tail(ta, g->tail_grid, origin);
+            if (cudaGetLastError() != cudaSuccess) rc = CORR_ECUDA;
+        }
         cudaGraph_t graph = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(origin, &graph);
         if (rc != CORR_OK || ec != cudaSuccess) {
@@ -1488,7 +1627,7 @@ int corr_group_run_dev(corr_t g, const void* const* d_samples, const size_t* n_s
         g->graph = graph;
         long long k1 = 0;
         for (int i = 0; i < n; ++i) k1 += g->members[i]->launches;
-        g->graph_kernels = k1 - k0;
+        g->graph_kernels = k1 - k0 + (g->tail_items > 0 ? 1 : 0);
         CK(cudaGraphInstantiate(&g->gexec, g->graph, 0));
         g->gkey = key;
     }

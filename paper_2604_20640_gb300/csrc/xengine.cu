@@ -7,7 +7,9 @@
 // sums go to their own partial slot; the finaliser adds the slots of an
 // integration in a fixed order, so the result does not depend on how a
 // stream was split into pushes (no atomics anywhere).
+#include "corr.h"
 #include "corr_internal.h"
+#include "tc_common.cuh"
 
 namespace corr {
 
@@ -163,10 +165,10 @@ __global__ void __launch_bounds__(128) xengine_small_kernel(const XArgs X) {
 
 // One thread per (channel, 4x4 block, entry): sums the entry's partial
 // slots in slot order, scales, rotates and writes R_ab and its mirror.
-__global__ void __launch_bounds__(128) finalize_kernel(const FinArgs F) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const int t = blockIdx.y;
-    const int i = blockIdx.z >> 2, j = blockIdx.z & 3;
+// (bx, t, z): the block's channel block, 4x4 block pair and entry.
+__device__ __forceinline__ void finalize_block(const FinArgs& F, int bx, int t, int z) {
+    const int k = bx * 128 + (int)threadIdx.x;
+    const int i = z >> 2, j = z & 3;
     if (k >= F.n_chan) return;
     const int n_in_pad = (F.n_in + 3) & ~3;
     int A, B;
@@ -200,6 +202,10 @@ __global__ void __launch_bounds__(128) finalize_kernel(const FinArgs F) {
     }
     R[a * F.n_in + b] = make_float2(re, im);
     R[b * F.n_in + a] = make_float2(re, -im);
+}
+
+__global__ void __launch_bounds__(128) finalize_kernel(const FinArgs F) {
+    finalize_block(F, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z);
 }
 
 // ---- MAD flagging, Eq. 2 ------------------------------------------------
@@ -261,14 +267,12 @@ __device__ __forceinline__ float warp_sorted_median(const float (&v)[E], int W) 
                    : 0.5f * (warp_sorted_at<E>(v, (W >> 1) - 1) + warp_sorted_at<E>(v, W >> 1));
 }
 
+// The flags of warp item `item` = (integration, window, baseline) of R.
 template <int E>
-__global__ void __launch_bounds__(32 * kFlagWarps) mad_flag_kernel(const float2* R, uint8_t* F, int n_vis,
-                                                                   int n_chan, int n_in, int W, float sigma) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+__device__ __forceinline__ void mad_flag_item(const float2* R, uint8_t* F, int n_chan, int n_in, int W, float sigma,
+                                              long long item, int lane) {
     const int n_bl = n_in * (n_in + 1) / 2;
     const int n_win = n_chan / W;
-    const long long item = (long long)blockIdx.x * kFlagWarps + warp;
-    if (item >= (long long)n_vis * n_win * n_bl) return;   // uniform over the warp
     const int bl = (int)(item % n_bl);
     const int w = (int)((item / n_bl) % n_win);
     const int i = (int)(item / ((long long)n_bl * n_win));
@@ -282,7 +286,7 @@ __global__ void __launch_bounds__(32 * kFlagWarps) mad_flag_kernel(const float2*
         const int c = lane * E + e;
         if (c < W) {
             const int k = w * W + c;
-            const float2 r = R[base + ((size_t)k * n_in + a) * n_in + b];
+            const float2 r = __ldcg(R + base + ((size_t)k * n_in + a) * n_in + b);
             A[e] = sqrtf(r.x * r.x + r.y * r.y);
         } else {
             A[e] = __int_as_float(0x7f800000);          // +inf: sorts after every value
@@ -308,7 +312,95 @@ __global__ void __launch_bounds__(32 * kFlagWarps) mad_flag_kernel(const float2*
     }
 }
 
+template <int E>
+__global__ void __launch_bounds__(32 * kFlagWarps) mad_flag_kernel(const float2* R, uint8_t* F, int n_vis,
+                                                                   int n_chan, int n_in, int W, float sigma) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long item = (long long)blockIdx.x * kFlagWarps + warp;
+    const long long n_items = (long long)n_vis * (n_chan / W) * (n_in * (n_in + 1) / 2);
+    if (item >= n_items) return;   // uniform over the warp
+    mad_flag_item<E>(R, F, n_chan, n_in, W, sigma, item, lane);
+}
+
+template <int E>
+__device__ __forceinline__ void tail_flags(const TailMember& m, const TailItem& it, int warp, int lane) {
+    const int n_bl = m.fin.n_in * (m.fin.n_in + 1) / 2;
+    const long long n_wi = (long long)(m.fin.n_chan / m.window) * n_bl;
+    const float2* R = m.fin.R + (size_t)it.integration * m.vis_stride;
+    uint8_t* F = m.flags + (size_t)it.integration * m.vis_stride;
+    for (int q = warp; q < kTailWarpItems; q += kFlagWarps) {
+        const long long wi = (long long)it.x + q;
+        if (wi < n_wi) mad_flag_item<E>(R, F, m.fin.n_chan, m.fin.n_in, m.window, m.sigma, wi, lane);
+    }
+}
+
+__global__ void __launch_bounds__(128) group_tail_kernel(const TailArgs T) {
+    __shared__ int tk, ok;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        if (threadIdx.x == 0) tk = atomicAdd(T.ticket, 1);
+        __syncthreads();
+        const int t = tk;
+        __syncthreads();                 // every thread has t before tk is rewritten
+        if (t >= T.n_items) return;      // uniform over the CTA
+        const TailItem it = T.items[t];
+        const TailMember& m = T.members[it.member];
+        if (it.kind == 0) {
+            FinArgs f = m.fin;
+            f.part += (size_t)it.integration * m.part_stride;
+            f.R += (size_t)it.integration * m.vis_stride;
+            finalize_block(f, it.x, it.y, it.z);
+            __syncthreads();             // the block's R values are written
+            if (threadIdx.x == 0) {
+                __threadfence();
+                if (t != T.inject_skip) atomicAdd(T.done + it.dep, 1);
+            }
+        } else {
+            if (threadIdx.x == 0) {
+                int good = 1;
+                if (it.need > 0) {
+                    const volatile int* d = T.done + it.dep;
+                    if (*d < it.need) {
+                        const unsigned long long t0 = tc::globaltimer();
+                        while (*d < it.need) {
+                            if (tc::globaltimer() - t0 > T.wait_ns) {
+                                good = 0;
+                                break;
+                            }
+                        }
+                    }
+                    __threadfence();
+                }
+                if (!good && T.status) atomicExch(T.status, CORR_ETIMEDOUT);
+                ok = good;
+            }
+            __syncthreads();
+            if (ok) {
+                if (m.window <= 32) tail_flags<1>(m, it, warp, lane);
+                else if (m.window <= 64) tail_flags<2>(m, it, warp, lane);
+                else if (m.window <= 128) tail_flags<4>(m, it, warp, lane);
+                else tail_flags<8>(m, it, warp, lane);
+            }
+        }
+    }
+}
+
 }  // namespace
+
+void launch_group_tail(const TailArgs& a, int grid, cudaStream_t st) {
+    if (a.n_items <= 0) return;
+    group_tail_kernel<<<grid, 128, 0, st>>>(a);
+}
+
+int group_tail_grid() {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, group_tail_kernel, 128, 0);
+    if (sms < 1) sms = 152;
+    if (per < 1) per = 1;
+    return sms * per;
+}
 
 void launch_xengine(const XArgs& a, cudaStream_t st) {
     if (a.n_groups <= 0) return;

@@ -1,8 +1,12 @@
-"""Batched sub-array streams (one captured CUDA graph) and the autotuner.
+"""Batched sub-array streams (one captured CUDA graph with a persistent tail
+kernel) and the autotuner.
 
 Each member of a group must produce exactly what its own corr_run_dev
 produces (and match the FP64 oracle); replaying the graph must repeat the
-result; new buffers must be picked up by a fresh capture.  Tuning changes
+result; new buffers must be picked up by a fresh capture.  The group's tail
+kernel (finalisation and MAD flags of every member, from a device work
+queue) waits on per-integration dependency counters with a bounded wait: a
+withheld dependency must end in CORR_ETIMEDOUT, not a hang.  Tuning changes
 only speed: results stay bit-identical.
 """
 
@@ -98,3 +102,38 @@ def test_autotune_is_bit_identical_and_cached(tmp_path):
     c2.autotune(xd, cache)
     assert c2.tuning() == (ring, spt)
     assert len(open(cache).read().strip().splitlines()) == 1
+
+
+def test_group_tail_wait_expires_on_a_withheld_dependency():
+    """Fault injection: the tail kernel's first finalise item does not count
+    itself done, so the flag items of that (member, integration) wait for a
+    counter that never completes; after tc_wait_ms they record
+    CORR_ETIMEDOUT and skip.  Everything else is computed; without the
+    injection (a new capture) the group matches its members' own runs."""
+    from paper_2604_20640_gb300 import Group, CORR_ETIMEDOUT
+    ms = [_member(i, *sh) for i, sh in enumerate(SHAPES[:2])]
+    solo = []
+    for c, x, xd, vis, flags, tau, phi in ms:
+        v2, f2 = torch.zeros_like(vis), torch.zeros_like(flags)
+        c.run_dev(xd, v2, f2)
+        solo.append((v2, f2))
+    g = Group([m[0] for m in ms])
+    g.set_option("tc_wait_ms", 5)
+    g.set_option("inject_stall", 1)
+    for m in ms:
+        m[4].fill_(7)                                  # flags: 7 = never written
+    g.run_dev([m[2] for m in ms], [m[3] for m in ms], [m[4] for m in ms])
+    torch.cuda.synchronize()
+    assert g.device_status() == CORR_ETIMEDOUT
+    f0 = ms[0][4]
+    assert torch.all(f0[0] == 7)                       # member 0, integration 0: flags skipped
+    assert torch.all(f0[1:] <= 1)                      # its later integrations are flagged
+    assert torch.all(ms[1][4] <= 1)
+    assert torch.equal(ms[1][3], solo[1][0]) and torch.equal(ms[1][4], solo[1][1])
+    g.set_option("inject_stall", 0)
+    g.run_dev([m[2] for m in ms], [m[3] for m in ms], [m[4] for m in ms])
+    torch.cuda.synchronize()
+    assert g.device_status() == 0
+    for m, (v2, f2) in zip(ms, solo):
+        assert torch.equal(m[3], v2) and torch.equal(m[4], f2)
+    g.close()
