@@ -105,7 +105,9 @@ const char* corr_last_error(corr_t h);
  *   "ring_mb"      (1..4096, default 64)  MiB of each on-device spectrum ring
  *                  (more spectra per launch; see corr_autotune)
  *   "fir_spt"      (0 = automatic, 1..256; may change at any time)
- *                  spectra each FIR thread filters (two-kernel F-engine)
+ *                  spectra each F-engine thread runs over: the FIR kernel's
+ *                  run, or the fused kernel's run per CTA (automatic: one
+ *                  wave of resident CTAs); results do not depend on it
  *   "fused_f"      (1, default, or 0; may change at any time)  run the
  *                  F-engine as one kernel (FIR output kept in shared
  *                  memory) where it covers the shape -- int8 samples, 4
@@ -284,8 +286,10 @@ int corr_group_run_dev(corr_t group, const void* const* d_samples, const size_t*
                        const int* max_int, int* n_out, void* stream);
 
 /*
- * corr_autotune -- pick the ring capacity ("ring_mb" 32/64/128/256) and
- * the FIR run length ("fir_spt" auto/8/16) of a handle by timing
+ * corr_autotune -- pick the ring capacity ("ring_mb" 32/64/128/256, the
+ * spectra per launch) and the F-engine's work split ("fir_spt" auto/8/16:
+ * spectra per thread run of the FIR kernel, or per CTA of the fused
+ * kernel) of a handle by timing
  * corr_run_dev on up to eight integrations of a device sample (results do
  * not depend on either choice; larger rings mean larger launches).  cache_path (may be NULL) is a text file of
  * "gpu n_in n_chan taps n_int precision ring_mb fir_spt" lines: a matching

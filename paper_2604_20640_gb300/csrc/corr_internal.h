@@ -86,6 +86,7 @@ struct FusedArgs {
     const float* hs;
     const int* coarse;       // [n_in_pad] coarse advance d_a
     int taps;
+    int run;                 // spectra per CTA run (0: one wave of resident CTAs)
 };
 
 // True when the fused kernel covers this shape (int8 samples, 2 <= taps <=

@@ -35,7 +35,7 @@ int launch_fused_m(const FusedArgs& a, cudaStream_t st) {
     if (runs > n) runs = n;
     if (runs < 1) runs = 1;
     FusedArgs b = a;
-    b.f.spt = (int)((n + runs - 1) / runs);
+    b.f.spt = a.run > 0 ? a.run : (int)((n + runs - 1) / runs);
     dim3 grid((unsigned)((n + b.f.spt - 1) / b.f.spt), (unsigned)n_groups);
     pfb_fft_kernel<M, MODE, P><<<grid, M / 16, smem, st>>>(b);
     return CORR_OK;

@@ -456,6 +456,7 @@ int launch_f(corr_t h, const StreamView& sv, const Tables& t, float2* Z, long lo
         u.hs = h->d_hs;
         u.coarse = t.coarse;
         u.taps = h->taps;
+        u.run = h->fir_spt;
         int rc;
         {
             Timed t_(h, 1, st);
