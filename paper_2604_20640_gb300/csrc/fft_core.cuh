@@ -903,7 +903,11 @@ __global__ void __launch_bounds__(M / 16, FftCfg<M>::minb(3)) pfb_fft_kernel(con
     constexpr int R0 = first_radix(M);
     // FIR + radix passes: with an even count the result lands in the buffer
     // the FIR wrote, so consecutive spectra alternate between the buffers
-    constexpr bool ALT = ((1 + n_later_passes(M, R0)) % 2) == 0;
+    // R0 = 2: the thread's branches are closed under the first pass's
+    // butterflies (j, j + M/2), so the FIR outputs go through that pass in
+    // registers and the FIR writes its results (FP2)
+    constexpr bool FP2 = R0 == 2;
+    constexpr bool ALT = (((FP2 ? 0 : 1) + n_later_passes(M, R0)) % 2) == 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* const buf0 = reinterpret_cast<float2*>(smem_raw);
     float2* const buf1 = buf0 + FC::ZB;
@@ -945,9 +949,13 @@ __global__ void __launch_bounds__(M / 16, FftCfg<M>::minb(3)) pfb_fft_kernel(con
     const int o0 = has0 ? (int)(reinterpret_cast<uintptr_t>(row0 + d0) & 15) : 0;
     const int o1 = has1 ? (int)(reinterpret_cast<uintptr_t>(row1 + d1) & 15) : 0;
     const int m_lo = 8 * tid, m_mi = M - 8 - 8 * tid;   // first branch of each half
+    // FP2: four words of four branches, 4t, 4t + M/2, M/2 - 4 - 4t, M - 4 - 4t
+    // (each branch's mirror and first-pass partner in the same thread)
+    const int wo[4] = {FP2 ? 4 * tid : m_lo, FP2 ? 4 * tid + M / 2 : m_lo + 4,
+                       FP2 ? M / 2 - 4 - 4 * tid : m_mi, FP2 ? M - 4 - 4 * tid : m_mi + 4};
 
-    // W[q][k][w]: frame q of the window (q = P-1 the newest), input k, words
-    // lower 0-1 (branches m_lo ..) and mirror 2-3 (branches m_mi ..)
+    // W[q][k][w]: frame q of the window (q = P-1 the newest), input k, word w
+    // (the four branches from wo[w])
     uint32_t W[P][2][4];
 #pragma unroll
     for (int q = 0; q < P - 1; ++q) {
@@ -959,8 +967,15 @@ __global__ void __launch_bounds__(M / 16, FftCfg<M>::minb(3)) pfb_fft_kernel(con
                 const int8_t* row = k ? row1 : row0;
                 const bool has = k ? has1 : has0;
                 const long long n = f * M + (k ? d1 : d0);
-                x = global8_checked(row, has, n + m_lo, lo, sv.vhi);
-                y = global8_checked(row, has, n + m_mi, lo, sv.vhi);
+                if constexpr (FP2) {
+                    x = make_uint2(global8_checked(row, has, n + wo[0], lo, sv.vhi).x,
+                                   global8_checked(row, has, n + wo[1], lo, sv.vhi).x);
+                    y = make_uint2(global8_checked(row, has, n + wo[2], lo, sv.vhi).x,
+                                   global8_checked(row, has, n + wo[3], lo, sv.vhi).x);
+                } else {
+                    x = global8_checked(row, has, n + m_lo, lo, sv.vhi);
+                    y = global8_checked(row, has, n + m_mi, lo, sv.vhi);
+                }
             }
             W[q][k][0] = x.x;
             W[q][k][1] = x.y;
@@ -984,7 +999,13 @@ __global__ void __launch_bounds__(M / 16, FftCfg<M>::minb(3)) pfb_fft_kernel(con
         const int it = (int)(s - s_lo);
         float2* const X = (ALT && (it & 1)) ? buf1 : buf0;
         float2* const Y = (X == buf0) ? buf1 : buf0;
-        {
+        if constexpr (FP2) {
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                W[P - 1][0][w] = staged8(stg0, o0 + wo[w]).x;
+                W[P - 1][1][w] = staged8(stg1, o1 + wo[w]).x;
+            }
+        } else {
             const uint2 l0 = staged8(stg0, o0 + m_lo), m0 = staged8(stg0, o0 + m_mi);
             const uint2 l1 = staged8(stg1, o1 + m_lo), m1 = staged8(stg1, o1 + m_mi);
             W[P - 1][0][0] = l0.x;
@@ -996,6 +1017,50 @@ __global__ void __launch_bounds__(M / 16, FftCfg<M>::minb(3)) pfb_fft_kernel(con
             W[P - 1][1][2] = m1.x;
             W[P - 1][1][3] = m1.y;
         }
+        if constexpr (FP2) {
+            // FIR of branch groups A = 4t + i, B = 4t + i + M/2 (first-pass
+            // partner of A), C = M/2 - 1 - 4t - i (mirror of B) and
+            // D = M - 1 - 4t - i (mirror of A, partner of C); coefficients
+            // from the half rows h1 = hs[.][4t ..], h2 = hs[.][M/2 - 4 - 4t ..]
+            // (h[pM + m] = hs[P-1-p][M-1-m] above M/2), taps p = 0 .. P-1
+            float2 zA[4], zB[4], zC[4], zD[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) zA[i] = zB[i] = zC[i] = zD[i] = make_float2(0.f, 0.f);
+            // two halves, each with one coefficient set live: (A, D) then (B, C)
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                float4 hh[P];
+#pragma unroll
+                for (int p = 0; p < P; ++p) hh[p] = hs4[(p * (M / 2) + wo[half ? 2 : 0]) >> 2];
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    const float ha[4] = {hh[p].x, hh[p].y, hh[p].z, hh[p].w};
+                    const float hb[4] = {hh[P - 1 - p].x, hh[P - 1 - p].y, hh[P - 1 - p].z, hh[P - 1 - p].w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if (half == 0) {
+                            zA[i] = fma2(make_float2(ha[i], ha[i]), unpack_pair(W[p][0][0], W[p][1][0], i), zA[i]);
+                            zD[i] = fma2(make_float2(hb[i], hb[i]),
+                                         unpack_pair(W[p][0][3], W[p][1][3], 3 - i), zD[i]);
+                        } else {
+                            zB[i] = fma2(make_float2(hb[3 - i], hb[3 - i]),
+                                         unpack_pair(W[p][0][1], W[p][1][1], i), zB[i]);
+                            zC[i] = fma2(make_float2(ha[3 - i], ha[3 - i]),
+                                         unpack_pair(W[p][0][2], W[p][1][2], 3 - i), zC[i]);
+                        }
+                    }
+                }
+            }
+            // first radix-2 pass (Ns = 1): butterfly j -> positions 2j, 2j + 1
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int j = wo[0] + i, jc = M / 2 - 1 - wo[0] - i;
+                X[pidx(2 * j)] = make_float2(zA[i].x + zB[i].x, zA[i].y + zB[i].y);
+                X[pidx(2 * j + 1)] = make_float2(zA[i].x - zB[i].x, zA[i].y - zB[i].y);
+                X[pidx(2 * jc)] = make_float2(zC[i].x + zD[i].x, zC[i].y + zD[i].y);
+                X[pidx(2 * jc + 1)] = make_float2(zC[i].x - zD[i].x, zC[i].y - zD[i].y);
+            }
+        } else {
         // FIR: y_s[m] = sum_p h[pM + m] x[(s-P+1+p)M + m] for both inputs at
         // once (lanes a, b of a packed pair), taps in order p = 0 .. P-1.
         // Branch m_lo + 4j + c is byte c of lower word j; its mirror
@@ -1026,6 +1091,7 @@ __global__ void __launch_bounds__(M / 16, FftCfg<M>::minb(3)) pfb_fft_kernel(con
                 X[pidx(M - 1 - m_lo - 4 * j - c)] = ymi[c];
             }
         }
+        }
 #pragma unroll
         for (int q = 0; q < P - 1; ++q)
 #pragma unroll
@@ -1038,13 +1104,18 @@ __global__ void __launch_bounds__(M / 16, FftCfg<M>::minb(3)) pfb_fft_kernel(con
             stage_frame<M>(sv, row1, has1, (s + 1) * M + d1, o1, stg1, tid, NACT);
             cp_async_commit();
         }
-        {
-            float2 v[16];
-            load_first_smem<M>(v, X, tid);
-            pass_compute_store<M, R0, 1, TW_NONE>(Y, v, tws, twr, tid);
+        const float2* zres;
+        if constexpr (FP2) {
+            zres = later_passes_cp<M, R0, C::REGTW>(X, Y, tws, twr, tid, F.tw);
+        } else {
+            {
+                float2 v[16];
+                load_first_smem<M>(v, X, tid);
+                pass_compute_store<M, R0, 1, TW_NONE>(Y, v, tws, twr, tid);
+            }
+            __syncthreads();
+            zres = later_passes_cp<M, R0, C::REGTW>(Y, X, tws, twr, tid, F.tw);
         }
-        __syncthreads();
-        const float2* zres = later_passes_cp<M, R0, C::REGTW>(Y, X, tws, twr, tid, F.tw);
 
         if constexpr (MODE == 2) {
             // |Y_a|^2 = |S|^2 / 4, |Y_b|^2 = |D|^2 / 4, summed over the row

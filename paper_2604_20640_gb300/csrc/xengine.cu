@@ -41,9 +41,6 @@ __global__ void __launch_bounds__(128) xengine_kernel(const XArgs X) {
 #pragma unroll
     for (int e = 0; e < 32; ++e) acc[e] = 0.f;
     const int q4 = X.n_in_pad >> 1;   // float4 (input pairs) per (slot, channel)
-    // two spectra per trip: the next spectrum's loads are in flight while the
-    // current one's products accumulate (same order of additions)
-#pragma unroll 2
     for (long long s = s0; s < s1; ++s) {
         const long long slot = (s - X.v_origin) & X.v_mask;
         float4 a01, a23, b01, b23;
@@ -105,7 +102,6 @@ __global__ void __launch_bounds__(128) xengine_small_kernel(const XArgs X) {
     for (int i = 0; i < NI; ++i) au[i] = 0.f;
 #pragma unroll
     for (int i = 0; i < NC; ++i) { cr[i] = 0.f; ci[i] = 0.f; }
-#pragma unroll 2
     for (long long s = s0 + q; s < s1; s += 8) {
         const long long slot = (s - X.v_origin) & X.v_mask;
         const float4* vp = PM ? reinterpret_cast<const float4*>(X.V) + (size_t)slot * (NI / 2) * X.n_chan + kk
