@@ -736,16 +736,32 @@ def run_flagger(args, rank, world, local):
     bytes_per_launch = ALG_BYTES_PER_SAMPLE[dom] * n_samples_pass / max(1, stage_n[di])
     avg_ms = stage_ms[di] / max(1, stage_n[di])
     achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
-    kname = "fft_kernel<%d,2> (power mode)" % (2 * W["n_chan"]) if dom == "fft" else KERNELS[dom]
+    fused = dom == "fft" and share.get("fir", 0.0) == 0.0
+    M = 2 * W["n_chan"]
+    kname = (("pfb_fft_kernel<%d,2,%d> (fused PFB + FFT, power mode)" % (M, W["taps"])) if fused else
+             ("fft_kernel<%d,2> (power mode)" % M)) if dom == "fft" else KERNELS[dom]
+    if fused:
+        bps_c5["fft"] = 1.0              # samples in; powers accumulate into the tiles
+    fl = flops_per_sample(dom, fused, M, W["taps"], spec.n_in)
+    fp = fp32_peak()
+    tf = fl * n_samples_pass / max(1, stage_n[di]) / (avg_ms * 1e-3) / 1e12
     roofline = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": None, "peak_source": "measured" if peaks else "fallback",
                 "bytes_per_launch": bytes_per_launch, "bytes_per_sample": ALG_BYTES_PER_SAMPLE[dom],
                 "intermediate_bytes_per_launch": bps_c5[dom] * n_samples_pass / max(1, stage_n[di]),
                 "avg_launch_ms": avg_ms, "launches": stage_n[di], "stage_share": share,
+                "alu": {"achieved": tf, "peak": fp["scalar"], "unit": "TFLOP/s", "frac": tf / fp["scalar"],
+                        "flop_per_sample": fl, "peak_source": "measured (corr_peak_fp32, scalar FMA chains)"},
                 "flagger": {"bound": "tensor", "ms": flag_ms, "tiles": B,
                             "achieved_tflops": flops_tile * B / (flag_ms * 1e-3) / 1e12, "peak": bf16,
                             "unit": "TFLOP/s", "frac": flops_tile * B / (flag_ms * 1e-3) / 1e12 / bf16,
                             "flop_per_tile": flops_tile}}
+    if roofline["alu"]["frac"] > roofline["frac"]:
+        hbm_part = {k: roofline[k] for k in ("achieved", "peak", "unit", "frac", "peak_source")}
+        alu = roofline.pop("alu")
+        roofline.update({"bound": "alu", "achieved": alu["achieved"], "peak": alu["peak"], "unit": "TFLOP/s",
+                         "frac": alu["frac"], "peak_source": alu["peak_source"], "hbm": hbm_part,
+                         "flop_per_sample": alu["flop_per_sample"]})
     # --- end to end: pinned host input, H2D + dynamic spectra + flagger + D2H
     # flags every step; two device input buffers let the copy of step i+1
     # overlap the processing of step i
