@@ -60,6 +60,9 @@ enum {
 
 /* Precision of the X-engine (option "precision"). */
 enum { CORR_FP32 = 0, CORR_INT8 = 1, CORR_FP8 = 2 };
+/* Code layout of corr_gram_dev beside CORR_INT8 (int8 carried as BF16) and
+ * CORR_FP8: int8 codes stored as bytes. */
+enum { CORR_INT8_BYTES = 3 };
 
 /*
  * corr_create -- allocate a correlator.
@@ -88,7 +91,8 @@ const char* corr_last_error(corr_t h);
  *   "chunk"       (samples/input, default 1<<23) largest device batch
  *   "precision"   (CORR_FP32 / CORR_INT8 / CORR_FP8, default FP32): FP32
  *                 CUDA-core X-engine, or channelised voltages requantised to
- *                 int8 (carried as BF16) / e4m3 with one scale per (input,
+ *                 int8 (stored as bytes, widened to BF16 on chip) / e4m3 with
+ *                 one scale per (input,
  *                 channel) fixed per integration, correlated on tcgen05
  *                 tensor cores (n_in <= 64).  Scales: first integration from
  *                 the mean power of its first min(n_int, 64) spectra
@@ -253,6 +257,9 @@ int corr_flag_dev(corr_t h, const float* d_vis, int n_vis, uint8_t* d_flags, voi
  *                    products are exact, the sums FP32 (exact while every
  *                    partial sum stays below 2^24).
  *   dtype CORR_FP8:  e4m3 bytes; FP32 sums.
+ *   dtype CORR_INT8_BYTES: int8 codes as bytes (1 byte each), widened to
+ *                    BF16 on chip (exact), then as CORR_INT8; this is the
+ *                    form the int8 pipeline uses.
  * d_G: [n_chan][128][128] FP32.  k_pitch must be a multiple of 128 and d_Q
  * 16-byte aligned (else CORR_EINVAL).  Runs on tcgen05 tensor cores with
  * TMA-staged operands; a stalled pipeline sets the status word read by

@@ -170,12 +170,14 @@ struct GramArgs {
     int* status;
     unsigned long long wait_ns;   // limit of each bounded wait (0: the 2 s default)
     int inject_stall;             // fault injection: the producer issues no loads
+    int i8b;                      // int8 codes stored as bytes (widened to BF16 on chip)
 };
 
-// Requantise spectra [s_begin, s_end) of the ring V (U = 2Y, unrotated) into
-// Q columns s - int_start: Q[k][a][.] = q(Re U / sigma), Q[k][N+a][.] =
-// q(Im U / sigma), sigma = scale[a][k]; int8 codes (round to nearest even,
-// saturate +-127) stored as BF16, or e4m3 (satfinite) bytes.
+// Requantise spectra [s_begin, s_end) of the pair-major ring V (U = 2Y,
+// unrotated) into Q columns s - int_start: Q[k][a][.] = q(Re U / sigma),
+// Q[k][N+a][.] = q(Im U / sigma), sigma = scale[a][k]; int8 codes (round to
+// nearest even, saturate +-127) as bytes or carried as BF16, or e4m3
+// (satfinite) bytes.
 struct RequantArgs {
     const float2* V;
     long long v_origin, v_mask;
@@ -185,7 +187,8 @@ struct RequantArgs {
     long long s_begin, s_end, int_start;
     int n_in, n_in_pad, n_chan;
     bool fp8;
-    int pair_major;          // V pair-major ([slot][pair][n_chan] float4)
+    int pair_major;          // V pair-major ([slot][pair][n_chan] float4); always set
+    int i8b;                 // int8 codes as bytes (else carried as BF16)
 };
 
 // R[k][a][b] = scale_a scale_b / (4 count) rot_a conj(rot_b) sum q_a conj(q_b),

@@ -169,6 +169,189 @@ __global__ void __launch_bounds__(128, 1) gram_kernel(const __grid_constant__ CU
     }
 }
 
+// ---- int8 codes stored as bytes ---------------------------------------------
+// The same Gram matrix with the codes in HBM as int8 bytes (half the bytes of
+// the BF16-carried form).  There is no integer tcgen05 MMA on sm_103a, so the
+// codes are widened on chip: 256 threads; warp 0 lane 0 streams raw
+// 128-row x 128-byte int8 tiles by TMA (no swizzle); warps 4-7 (one row per
+// thread) widen each tile to two BF16 operand tiles of 64 K-elements in the
+// 128-byte-swizzled K-major layout the MMA descriptors describe (16-byte
+// chunk q of row r at r * 128 + ((q ^ (r & 7)) << 4)), make them visible to
+// the async proxy and signal the MMA issuer (warp 1 lane 0); warps 0-3 read
+// the accumulator.  Every wait is bounded; the converters decide each step
+// together (barrier with an AND reduction), so no converter can be left
+// alone at a named barrier.
+constexpr int kRawStages = 4;
+constexpr int kConvStages = 3;
+constexpr int kRawBytes = kRows * 128;           // 128 int8 codes per row
+constexpr int kConvBytes = 2 * kRows * 128;      // two BF16 tiles of 64 codes per row
+struct __align__(8) GramI8Shared {
+    uint64_t raw_full[kRawStages];
+    uint64_t raw_empty[kRawStages];
+    uint64_t conv_full[kConvStages];
+    uint64_t conv_empty[kConvStages];
+    uint64_t accum;
+    uint32_t tmem_addr;
+    int abort;
+};
+
+// AND of p over the 128 converter threads (named barrier 1).
+__device__ __forceinline__ bool converters_all(bool p) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred a, b;\n\tsetp.ne.u32 a, %1, 0;\n\t"
+        "bar.red.and.pred b, 1, 128, a;\n\tselp.u32 %0, 1, 0, b;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)p)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void converters_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Two BF16 values (low: byte c of w, high: byte c+1) of sign-flipped int8
+// bytes, exact: the float of each code, then its upper half (the lower half
+// of a float holding an 8-bit integer is zero).
+__device__ __forceinline__ uint32_t bf16x2_of_codes(uint32_t f, int c) {
+    const uint32_t s0 = 0x7440u + (uint32_t)c, s1 = 0x7440u + (uint32_t)(c + 1);
+    const float x0 = __int_as_float((int)__byte_perm(f, 0x4B000000u, s0)) - 8388736.0f;
+    const float x1 = __int_as_float((int)__byte_perm(f, 0x4B000000u, s1)) - 8388736.0f;
+    return __byte_perm(__float_as_uint(x0), __float_as_uint(x1), 0x7632);
+}
+
+__global__ void __launch_bounds__(256, 1) gram_i8_kernel(const __grid_constant__ CUtensorMap tmap, GramArgs A) {
+    extern __shared__ __align__(1024) uint8_t gsm_raw[];
+    uint8_t* conv = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* raw = conv + kConvStages * kConvBytes;
+    GramI8Shared* sh = reinterpret_cast<GramI8Shared*>(raw + kRawStages * kRawBytes);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ch = blockIdx.x;
+    const int num_k = (A.K + 127) / 128;
+    const unsigned long long lim = A.wait_ns ? A.wait_ns : kWaitNs;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kRawStages; ++s) {
+            mbar_init(&sh->raw_full[s], 1);
+            mbar_init(&sh->raw_empty[s], 1);
+        }
+        for (int c = 0; c < kConvStages; ++c) {
+            mbar_init(&sh->conv_full[c], 1);
+            mbar_init(&sh->conv_empty[c], 1);
+        }
+        mbar_init(&sh->accum, 1);
+        sh->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&sh->tmem_addr)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = sh->tmem_addr;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer of raw int8 tiles (with inject_stall it issues nothing)
+        for (int it = 0; it < (A.inject_stall ? 0 : num_k); ++it) {
+            const int s = it % kRawStages;
+            const uint32_t ph = (uint32_t)(it / kRawStages) & 1u;
+            if (!mbar_wait(&sh->raw_empty[s], ph ^ 1u, lim)) {
+                sh->abort = 1;
+                break;
+            }
+            mbar_expect_tx(&sh->raw_full[s], kRawBytes);
+            tma_load_2d(raw + s * kRawBytes, &tmap, &sh->raw_full[s], it * 128, ch * kRows);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: two BF16 tiles of 64 codes per converted stage
+        bool ok = true;
+        for (int it = 0; it < num_k && ok; ++it) {
+            const int c = it % kConvStages;
+            const uint32_t ph = (uint32_t)(it / kConvStages) & 1u;
+            if (!mbar_wait(&sh->conv_full[c], ph, lim)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int hf = 0; hf < 2; ++hf) {
+                const uint64_t d0 = sdesc(smem_u32(conv + c * kConvBytes + hf * kRows * 128));
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint64_t d = d0 + (uint64_t)((kk * 32) >> 4);
+                    mma<false>(tmem, d, d, (it | hf | kk) != 0 ? 1u : 0u);
+                }
+            }
+            mma_commit(&sh->conv_empty[c]);
+        }
+        if (!ok) sh->abort = 1;
+        mma_commit(&sh->accum);
+    } else if (warp >= 4) {
+        // converters: thread r widens row r of each raw tile
+        const int r = (int)threadIdx.x - 128;
+        for (int it = 0; it < num_k; ++it) {
+            const int s = it % kRawStages, c = it % kConvStages;
+            bool ok = mbar_wait(&sh->raw_full[s], (uint32_t)(it / kRawStages) & 1u, lim);
+            ok = ok && mbar_wait(&sh->conv_empty[c], ((uint32_t)(it / kConvStages) & 1u) ^ 1u, lim);
+            if (!converters_all(ok)) {
+                if (r == 0) sh->abort = 1;
+                break;
+            }
+            const uint4* src = reinterpret_cast<const uint4*>(raw + s * kRawBytes + r * 128);
+            uint8_t* drow = conv + c * kConvBytes + r * 128;
+#pragma unroll
+            for (int c16 = 0; c16 < 8; ++c16) {
+                const uint4 v = src[c16];
+                const uint32_t w[4] = {v.x ^ 0x80808080u, v.y ^ 0x80808080u, v.z ^ 0x80808080u,
+                                       v.w ^ 0x80808080u};
+                const uint4 lo = make_uint4(bf16x2_of_codes(w[0], 0), bf16x2_of_codes(w[0], 2),
+                                            bf16x2_of_codes(w[1], 0), bf16x2_of_codes(w[1], 2));
+                const uint4 hi = make_uint4(bf16x2_of_codes(w[2], 0), bf16x2_of_codes(w[2], 2),
+                                            bf16x2_of_codes(w[3], 0), bf16x2_of_codes(w[3], 2));
+                // codes 16 c16 .. +15 -> tile c16 / 4, BF16 chunks q0, q0 + 1 of that row
+                uint8_t* t = drow + (c16 >> 2) * (kRows * 128);
+                const int q0 = 2 * (c16 & 3);
+                *reinterpret_cast<uint4*>(t + ((q0 ^ (r & 7)) << 4)) = lo;
+                *reinterpret_cast<uint4*>(t + (((q0 + 1) ^ (r & 7)) << 4)) = hi;
+            }
+            fence_proxy_async_smem();
+            converters_sync();
+            if (r == 0) {
+                mbar_arrive(&sh->conv_full[c]);
+                mbar_arrive(&sh->raw_empty[s]);
+            }
+        }
+    }
+    __syncwarp();
+    if (!mbar_wait(&sh->accum, 0, lim)) sh->abort = 1;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (sh->abort) {
+        if (threadIdx.x == 0 && A.status) atomicExch(A.status, CORR_ETIMEDOUT);
+    } else if (warp < 4) {
+        const int row = warp * 32 + lane;
+        uint32_t* G = reinterpret_cast<uint32_t*>(A.G) + ((size_t)ch * kRows + row) * kRows;
+#pragma unroll
+        for (int c0 = 0; c0 < kRows; c0 += 32) {
+            uint32_t rr[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, rr);
+            uint4* o = reinterpret_cast<uint4*>(G + c0);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) o[i] = make_uint4(rr[4 * i], rr[4 * i + 1], rr[4 * i + 2], rr[4 * i + 3]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                     : "memory");
+    }
+}
+
 }  // namespace
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -186,8 +369,38 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 size_t gram_smem_bytes() { return (size_t)kStages * kStageBytes + sizeof(GramShared) + 1024; }
 
+size_t gram_i8_smem_bytes() {
+    return (size_t)kConvStages * kConvBytes + (size_t)kRawStages * kRawBytes + sizeof(GramI8Shared) + 1024;
+}
+
 int launch_gram(const GramArgs& a, cudaStream_t st) {
     if (a.n_chan <= 0 || a.K <= 0) return CORR_OK;
+    if (a.i8b) {
+        // int8 codes as bytes: raw tiles of 128 codes x 128 rows, no swizzle
+        if (a.fp8 || a.k_pitch % 128 != 0 || a.K > a.k_pitch) return CORR_EINVAL;
+        if ((reinterpret_cast<uintptr_t>(a.Q) & 15) != 0) return CORR_EINVAL;
+        PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+        if (!enc) return CORR_ECUDA;
+        CUtensorMap map;
+        cuuint64_t dims[2] = {(cuuint64_t)a.K, (cuuint64_t)a.n_chan * kRows};
+        cuuint64_t strides[1] = {(cuuint64_t)a.k_pitch};
+        cuuint32_t box[2] = {128u, (cuuint32_t)kRows};
+        cuuint32_t estr[2] = {1, 1};
+        CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(a.Q), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return CORR_EINVAL;
+        const size_t smem = gram_i8_smem_bytes();
+        static bool attr8 = false;
+        if (!attr8) {
+            if (cudaFuncSetAttribute(gram_i8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess)
+                return CORR_ECUDA;
+            attr8 = true;
+        }
+        gram_i8_kernel<<<a.n_chan, 256, smem, st>>>(map, a);
+        return CORR_OK;
+    }
     const int eb = a.fp8 ? 1 : 2;
     if (a.k_pitch % 128 != 0 || (long long)a.K * eb > a.k_pitch) return CORR_EINVAL;
     if ((reinterpret_cast<uintptr_t>(a.Q) & 15) != 0) return CORR_EINVAL;

@@ -1,14 +1,14 @@
 // Requantiser and rescaling around the tensor-core X-engine.
 //
-// requant_kernel turns a batch of channelised spectra (U = 2Y, unrotated,
-// complex64 in the ring [slot][n_chan][n_in_pad]) into the stacked operand
-// Q[k][row][t] of gram_kernel: row a holds Re U_a / sigma_a[k], row N + a
-// holds Im U_a / sigma_a[k], t the spectrum index inside the integration:
-// int8 codes (round half to even, saturate at +-127) carried as BF16, which
-// holds them exactly, or e4m3 (satfinite) bytes.  A CTA
-// covers one channel x 64 spectra; a thread owns one input and a run of
-// spectra, so reads coalesce across inputs and every row gets whole
-// 32-byte sectors of codes.
+// requant_pm_kernel turns a batch of channelised spectra (U = 2Y, unrotated,
+// in the pair-major ring [slot][pair][n_chan] float4) into the stacked
+// operand Q[k][row][t] of the tensor-core Gram: row a holds Re U_a /
+// sigma_a[k], row N + a holds Im U_a / sigma_a[k], t the spectrum index inside
+// the integration: int8 codes (round half to even, saturate at +-127) as
+// bytes (widened on chip by gram_i8_kernel) or carried as BF16, or e4m3
+// (satfinite) bytes.  A thread owns one input pair and channel over a run of
+// spectra, so reads coalesce across channels and every row gets a whole
+// 32-byte sector of codes.
 // The scales are fixed for a whole integration: the first integration of a
 // stream takes them from the mean power of its first spectra, later ones
 // from the previous integration's autocorrelations.
@@ -38,85 +38,17 @@ __device__ __forceinline__ uint16_t code_bf16(uint8_t q) {
     return __bfloat16_as_ushort(__float2bfloat16_rn((float)(int8_t)q));
 }
 
-// One thread: input a, a run of RUN consecutive spectra (one 32-byte sector
-// of codes per row: 16 BF16 or 32 e4m3).  Reads are coalesced across inputs,
-// each row's codes are written with two 16-byte stores.
-template <bool FP8>
-__global__ void __launch_bounds__(256) requant_kernel(const RequantArgs A) {
-    constexpr int RUN = FP8 ? 32 : 16;
-    const int k = blockIdx.x;
-    const int N = A.n_in;
-    const int runs = kTileS / RUN;
-    const long long s0 = A.s_begin + (long long)blockIdx.y * kTileS;
-    for (int idx = threadIdx.x; idx < N * runs; idx += blockDim.x) {
-        const int a = idx % N, r = idx / N;
-        const long long sb = s0 + (long long)r * RUN;
-        if (sb >= A.s_end) continue;
-        const int ns = (int)((A.s_end - sb) < RUN ? (A.s_end - sb) : RUN);
-        const float inv = 1.0f / A.scale[(size_t)a * A.n_chan + k];
-        // codes packed little-endian into 8 words per row (one 32-byte sector)
-        uint32_t wr[8], wi[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            wr[j] = 0u;
-            wi[j] = 0u;
-        }
-#pragma unroll
-        for (int i = 0; i < RUN; ++i) {
-            float2 u = make_float2(0.f, 0.f);
-            if (i < ns) {
-                const long long slot = (sb + i - A.v_origin) & A.v_mask;
-                u = A.V[((size_t)slot * A.n_chan + k) * A.n_in_pad + a];
-            }
-            uint32_t cr, ci;
-            if constexpr (FP8) {
-                cr = q_e4m3(u.x * inv);
-                ci = q_e4m3(u.y * inv);
-                wr[i / 4] |= cr << (8 * (i % 4));
-                wi[i / 4] |= ci << (8 * (i % 4));
-            } else {
-                cr = code_bf16(q_int8(u.x * inv));
-                ci = code_bf16(q_int8(u.y * inv));
-                wr[i / 2] |= cr << (16 * (i % 2));
-                wi[i / 2] |= ci << (16 * (i % 2));
-            }
-        }
-        constexpr int EB = FP8 ? 1 : 2;
-        const long long col = sb - A.int_start;
-        uint8_t* row_re = A.Q + ((size_t)k * 128 + a) * A.k_pitch + col * EB;
-        uint8_t* row_im = A.Q + ((size_t)k * 128 + N + a) * A.k_pitch + col * EB;
-        if (ns == RUN && ((col * EB) & 15) == 0) {
-            uint4* dr = reinterpret_cast<uint4*>(row_re);
-            uint4* di = reinterpret_cast<uint4*>(row_im);
-            dr[0] = make_uint4(wr[0], wr[1], wr[2], wr[3]);
-            dr[1] = make_uint4(wr[4], wr[5], wr[6], wr[7]);
-            di[0] = make_uint4(wi[0], wi[1], wi[2], wi[3]);
-            di[1] = make_uint4(wi[4], wi[5], wi[6], wi[7]);
-        } else {
-#pragma unroll
-            for (int i = 0; i < RUN; ++i) {
-                if (i < ns) {
-#pragma unroll
-                    for (int e = 0; e < EB; ++e) {
-                        const int bitpos = 8 * (i * EB + e);
-                        row_re[i * EB + e] = (uint8_t)(wr[bitpos / 32] >> (bitpos % 32));
-                        row_im[i * EB + e] = (uint8_t)(wi[bitpos / 32] >> (bitpos % 32));
-                    }
-                }
-            }
-        }
-    }
-}
-
 // Pair-major ring ([slot][pair][n_chan] float4: the pair's two complex
 // values): one thread per (input pair, channel), consecutive channels across
 // the warp (coalesced 16-byte reads), a run of RUN spectra per thread; the
 // pair's four rows (Re a, Re b, Im a, Im b) each get one whole 32-byte sector
 // of codes.
-template <bool FP8>
+// CODE: 0 int8 carried as BF16 (2 bytes), 1 e4m3 byte, 2 int8 byte.
+template <int CODE>
 __global__ void __launch_bounds__(128) requant_pm_kernel(const RequantArgs A) {
-    constexpr int RUN = FP8 ? 32 : 16;
-    constexpr int EB = FP8 ? 1 : 2;
+    constexpr bool FP8 = CODE == 1;
+    constexpr int EB = CODE == 0 ? 2 : 1;
+    constexpr int RUN = 32 / EB;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int pr = blockIdx.y;
     if (k >= A.n_chan) return;
@@ -145,6 +77,7 @@ __global__ void __launch_bounds__(128) requant_pm_kernel(const RequantArgs A) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             if constexpr (FP8) w[r][i / 4] |= (uint32_t)q_e4m3(x[r]) << (8 * (i % 4));
+            else if constexpr (CODE == 2) w[r][i / 4] |= (uint32_t)q_int8(x[r]) << (8 * (i % 4));
             else w[r][i / 2] |= (uint32_t)code_bf16(q_int8(x[r])) << (16 * (i % 2));
         }
     }
@@ -236,16 +169,11 @@ __global__ void finalize_q_kernel(const FinQArgs F) {
 void launch_requant(const RequantArgs& a, cudaStream_t st) {
     const long long n = a.s_end - a.s_begin;
     if (n <= 0) return;
-    if (a.pair_major) {
-        const int run = a.fp8 ? 32 : 16;
-        dim3 grid((unsigned)((a.n_chan + 127) / 128), (unsigned)(a.n_in_pad / 2), (unsigned)((n + run - 1) / run));
-        if (a.fp8) requant_pm_kernel<true><<<grid, 128, 0, st>>>(a);
-        else requant_pm_kernel<false><<<grid, 128, 0, st>>>(a);
-        return;
-    }
-    dim3 grid((unsigned)a.n_chan, (unsigned)((n + kTileS - 1) / kTileS));
-    if (a.fp8) requant_kernel<true><<<grid, 256, 0, st>>>(a);
-    else requant_kernel<false><<<grid, 256, 0, st>>>(a);
+    const int run = (a.fp8 || a.i8b) ? 32 : 16;
+    dim3 grid((unsigned)((a.n_chan + 127) / 128), (unsigned)(a.n_in_pad / 2), (unsigned)((n + run - 1) / run));
+    if (a.fp8) requant_pm_kernel<1><<<grid, 128, 0, st>>>(a);
+    else if (a.i8b) requant_pm_kernel<2><<<grid, 128, 0, st>>>(a);
+    else requant_pm_kernel<0><<<grid, 128, 0, st>>>(a);
 }
 
 void launch_scale_from_ring(const float2* V, long long v_origin, long long v_mask, long long s0, int n, int n_in,

@@ -365,7 +365,8 @@ int alloc_pipe(corr_t h, Pipe& p) {
     CK(cudaMalloc(&p.V, per_spec * (size_t)p.v_cap));
     CK(cudaMalloc(&p.Z, per_spec * (size_t)p.v_cap));
     if (h->precision != CORR_FP32) {
-        const int eb = h->precision == CORR_FP8 ? 1 : 2;
+        // one byte per code: e4m3, or int8 widened to BF16 by the Gram kernel
+        const int eb = 1;
         p.q_pitch = (int)((((long long)h->n_int * eb) + 127) / 128 * 128);
         const size_t qbytes = (size_t)h->n_chan * 128 * p.q_pitch;
         CK(cudaMalloc(&p.Q, qbytes));
@@ -550,6 +551,7 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
                 r.n_chan = h->n_chan;
                 r.fp8 = h->precision == CORR_FP8;
                 r.pair_major = pair_major_ring(h);
+                r.i8b = h->precision == CORR_INT8;
                 {
                     Timed t_(h, 5, st);
                     launch_requant(r, st);
@@ -625,6 +627,7 @@ int finalize_into(corr_t h, Pipe& p, const Tables& t, float2* R, uint8_t* F, int
         g.status = h->d_status;
         g.wait_ns = (unsigned long long)(h->tc_wait_ms * 1e6);
         g.inject_stall = h->inject_stall;
+        g.i8b = h->precision == CORR_INT8;
         int rc;
         {
             Timed t_(h, 6, st);
@@ -1390,7 +1393,7 @@ long long corr_kernel_launches(corr_t h) { return h ? h->launches : 0; }
 int corr_gram_dev(corr_t h, const void* d_Q, int n_chan, int k_pitch, int K, int dtype, float* d_G, void* stream) {
     if (!h) return fail(h, CORR_EINVAL, "NULL handle");
     DeviceGuard g(h->dev);
-    if (!d_Q || !d_G || n_chan < 1 || K < 1 || (dtype != CORR_INT8 && dtype != CORR_FP8))
+    if (!d_Q || !d_G || n_chan < 1 || K < 1 || (dtype != CORR_INT8 && dtype != CORR_FP8 && dtype != CORR_INT8_BYTES))
         return fail(h, CORR_EINVAL, "bad argument");
     GramArgs a{};
     a.Q = d_Q;
@@ -1398,6 +1401,7 @@ int corr_gram_dev(corr_t h, const void* d_Q, int n_chan, int k_pitch, int K, int
     a.K = K;
     a.k_pitch = k_pitch;
     a.fp8 = dtype == CORR_FP8;
+    a.i8b = dtype == CORR_INT8_BYTES;
     a.G = d_G;
     a.status = h->d_status;
     a.wait_ns = (unsigned long long)(h->tc_wait_ms * 1e6);

@@ -1,7 +1,8 @@
 """Tensor-core X-engine (tcgen05 Gram matrices) against the exact oracle Gram.
 
 Inputs are seeded codes drawn on the host (never produced by the CUDA path):
-int8 codes carried as BF16 and e4m3 bytes.  With int8 codes every product is
+int8 codes carried as BF16, int8 codes as bytes (widened to BF16 on chip by
+the kernel the int8 pipeline uses) and e4m3 bytes.  With int8 codes every product is
 exact and FP32 sums are exact while partial sums stay below 2^24, which
 holds for K <= 1024 (1024 * 127^2 < 2^24): there the result must be
 bit-exact.  Longer sums and e4m3 are checked against the FP32 accumulation
@@ -96,3 +97,30 @@ def test_gram_rejects_bad_layout():
     G = torch.zeros((2, 128, 128), dtype=torch.float32, device=DEV)
     with pytest.raises(CorrError):
         c.gram_dev(Q, 2, 200, 64, CORR_INT8, G)
+
+
+@pytest.mark.parametrize("rows,K,k_pitch", [(128, 1024, 1024), (16, 1000, 1024), (100, 130, 256), (128, 64, 128)])
+def test_int8_byte_gram_bit_exact(rows, K, k_pitch):
+    """int8 codes stored as bytes: the kernel widens each 128-code tile to
+    two swizzled BF16 operand tiles; exact products, exact FP32 sums up to
+    K = 1024 -> bit-exact; codes beyond K (in the row pitch) are ignored."""
+    from paper_2604_20640_gb300 import CORR_INT8_BYTES
+    rng = np.random.default_rng(rows + 7 * K)
+    n_chan = 5
+    codes = np.zeros((n_chan, 128, k_pitch), np.int64)
+    codes[:, :rows, :K] = rng.integers(-127, 128, size=(n_chan, rows, K))
+    codes[:, :rows, K:] = rng.integers(-127, 128, size=(n_chan, rows, k_pitch - K))
+    Q = codes.astype(np.int8).view(np.uint8)
+    G = _run_gram(_corr(), Q, n_chan, k_pitch, K, CORR_INT8_BYTES)
+    np.testing.assert_array_equal(G, rq.gram(codes[:, :, :K]).astype(np.float64))
+
+
+def test_int8_byte_gram_long_sums_within_fp32_bound():
+    from paper_2604_20640_gb300 import CORR_INT8_BYTES
+    rng = np.random.default_rng(3)
+    n_chan, K, k_pitch = 3, 4096, 4096
+    codes = rng.integers(-127, 128, size=(n_chan, 128, K)).astype(np.int64)
+    G = _run_gram(_corr(), codes.astype(np.int8).view(np.uint8), n_chan, k_pitch, K, CORR_INT8_BYTES)
+    ref = rq.gram(codes).astype(np.float64)
+    bound = K * 2.0 ** -24 * np.einsum('crk,csk->crs', np.abs(codes).astype(np.float64), np.abs(codes).astype(np.float64))
+    assert np.all(np.abs(G - ref) <= bound)
