@@ -135,6 +135,14 @@ const char* corr_last_error(corr_t h);
  *                  frequencies).  FP32 path only (CORR_EINVAL with reduced
  *                  precision, 16-bit samples or n_chan < 16); the dynamic
  *                  spectra call is for real input.  Before any buffers exist.
+ *   "max_pending"  (0 = no limit, default; may change at any time) a push
+ *                  is refused with CORR_EAGAIN, consuming nothing, while this
+ *                  many completed integrations wait to be popped (the
+ *                  caller's back-pressure on a full result queue)
+ *   "inject_alloc_fail" (0, default, or n; may change at any time) fault
+ *                  injection: the n-th device allocation the handle makes
+ *                  from now fails with CORR_ENOMEM (the failed step leaves
+ *                  no half-built buffers; the handle stays usable)
  *   "tc_wait_ms"   (1 .. 60000, default 2000; may change at any time)
  *                  limit of every bounded wait of the tensor-core X-engine
  *                  (producer / MMA / epilogue barriers); on expiry the kernel
@@ -408,6 +416,25 @@ int corr_calibrate_dev(const float* d_vis, const uint8_t* d_flags, int n_chan, i
  * arguments, CORR_ECUDA if a CUDA call fails (corr_last_error(NULL)).
  */
 int corr_peak_fp32(int packed, int iters, double* tflops, double* ms, void* stream);
+
+/*
+ * corr_save_state / corr_load_state -- checkpoint and resume a stream (a
+ * library facility; the paper has no counterpart).  corr_save_state waits
+ * for the handle's queued work and writes its streaming state into buf
+ * (host, caller-owned, cap bytes): the samples still needed by spectra not
+ * yet channelised, the channelised spectra not yet summed, the current
+ * integration's partial sums (FP32) or scales and codes (reduced precision),
+ * the active and pending delays, the counters and every result not yet
+ * popped.  With buf NULL it only sets *size to the bytes needed.
+ * corr_load_state restores such a state into a new (or reset) handle
+ * created with the same shape and options; pushing the rest of the stream
+ * then gives results bit-identical to an uninterrupted stream.  CORR_EINVAL
+ * for a state of another shape or options, or a truncated one; CORR_ESTATE
+ * when the handle has already started.  The format belongs to this library
+ * version.
+ */
+int corr_save_state(corr_t h, void* buf, size_t cap, size_t* size);
+int corr_load_state(corr_t h, const void* buf, size_t size);
 
 /* Shapes of a handle: n_in, n_chan, taps, n_int, n_in_pad (any may be NULL). */
 int corr_shape(corr_t h, int* n_in, int* n_chan, int* taps, int* n_int, int* n_in_pad);

@@ -39,7 +39,7 @@ EXPORTED = [
     "corr_flagnet_num_params", "corr_flagnet_set_params", "corr_flagnet_get_params", "corr_flagnet_prepare",
     "corr_flagnet_forward", "corr_flagnet_loss_grad", "corr_flagnet_train_step", "corr_flagnet_flag",
     "corr_flagnet_status", "corr_flagnet_kernel_launches", "corr_tile_mad_dev", "corr_calibrate_dev",
-    "corr_peak_fp32",
+    "corr_peak_fp32", "corr_save_state", "corr_load_state",
 ]
 
 
@@ -109,6 +109,8 @@ def load_library(path: str = LIB_PATH):
         "corr_tile_mad_dev": (_i, [_vp, _i, ctypes.c_float, _i, _vp, _vp]),
         "corr_calibrate_dev": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _d, _vp, _vp, _vp]),
         "corr_peak_fp32": (_i, [_i, _i, ctypes.POINTER(_d), ctypes.POINTER(_d), _vp]),
+        "corr_save_state": (_i, [_vp, _vp, _sz, ctypes.POINTER(_sz)]),
+        "corr_load_state": (_i, [_vp, _vp, _sz]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -315,6 +317,19 @@ class Correlator:
 
     def flush(self):
         self._check(self._L.corr_flush(self._h))
+
+    def save_state(self) -> bytes:
+        """The streaming state (corr_save_state) as bytes."""
+        n = _sz()
+        self._check(self._L.corr_save_state(self._h, None, 0, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(max(1, n.value))
+        self._check(self._L.corr_save_state(self._h, buf, n.value, ctypes.byref(n)))
+        return buf.raw[:n.value]
+
+    def load_state(self, state: bytes):
+        """Restore a saved state into this new (or reset) handle (corr_load_state)."""
+        buf = ctypes.create_string_buffer(state, len(state))
+        self._check(self._L.corr_load_state(self._h, buf, len(state)))
 
     def reset(self):
         self._check(self._L.corr_reset(self._h))

@@ -140,6 +140,9 @@ struct corr_s {
     TailItem* d_tail_items = nullptr;
     int* d_tail_counters = nullptr;   // [0] ticket, [1..] per (member, integration) done counts
     int tail_items = 0, tail_deps = 0, tail_grid = 0, tail_fin_items = 0;
+    int inject_alloc_fail = 0;   // fault injection: the n-th next device allocation fails
+    int max_pending = 0;         // pushes refused (CORR_EAGAIN) while this many results wait (0: no limit)
+    std::vector<double> stream_tau, stream_phi;  // delays in the stream tables now
     double tc_wait_ms = 2000.0;  // limit of every bounded tensor-core wait
     int inject_stall = 0;        // fault injection: tensor-core producer issues nothing
     Tables tab_stream, tab_direct;
@@ -199,6 +202,28 @@ int fail(corr_t h, int code, const std::string& msg) {
     do {                         \
         int r_ = (expr);         \
         if (r_ != CORR_OK) return r_; \
+    } while (0)
+
+// Device allocation of a handle, with the fault-injection hook
+// "inject_alloc_fail": the n-th allocation after the option is set fails.
+cudaError_t dev_malloc(corr_t h, void** ptr, size_t bytes) {
+    if (h && h->inject_alloc_fail > 0 && --h->inject_alloc_fail == 0) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(ptr, bytes);
+}
+
+template <class T>
+cudaError_t dmalloc(corr_t h, T** ptr, size_t bytes) {
+    return dev_malloc(h, reinterpret_cast<void**>(ptr), bytes);
+}
+
+#define CKA(call)                                                                           \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(h, CORR_ENOMEM, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
 // Bracket one launch of `stage` on stream st with events (when enabled).
@@ -316,6 +341,10 @@ int upload_tables(corr_t h, Tables& t, const std::vector<double>& tau, const std
         }
     }
     t.d_max = dmax;
+    if (&t == &h->tab_stream) {
+        h->stream_tau = tau;
+        h->stream_phi = phi;
+    }
     CK(cudaMemcpyAsync(t.phasor, ph.data(), ph.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(t.rot, rt.data(), rt.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(t.coarse, co.data(), co.size() * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -349,8 +378,19 @@ int choose_fir_spt(long long n_spec, int n_pairs, int M, int taps) {
     return (int)spt;
 }
 
+void free_pipe(Pipe& p);
+
+int alloc_pipe_impl(corr_t h, Pipe& p);
+
+// All of a pipe's buffers or none (a failed allocation leaves no half-built pipe).
 int alloc_pipe(corr_t h, Pipe& p) {
     if (p.V) return CORR_OK;
+    const int rc = alloc_pipe_impl(h, p);
+    if (rc != CORR_OK) free_pipe(p);
+    return rc;
+}
+
+int alloc_pipe_impl(corr_t h, Pipe& p) {
     const unsigned long long ring_bytes = (unsigned long long)h->ring_mb << 20;
     // Two power-of-two rings (FIR output and channelised spectra) of half of
     // ring_mb each: at the 64 MiB default both stay in L2 between the
@@ -362,20 +402,20 @@ int alloc_pipe(corr_t h, Pipe& p) {
     // the reduced-precision scale pre-pass reads the first 64 spectra from the ring
     while (h->precision != CORR_FP32 && cap < 64) cap *= 2;
     p.v_cap = (int)cap;
-    CK(cudaMalloc(&p.V, per_spec * (size_t)p.v_cap));
-    CK(cudaMalloc(&p.Z, per_spec * (size_t)p.v_cap));
+    CKA(dmalloc(h, &p.V, per_spec * (size_t)p.v_cap));
+    CKA(dmalloc(h, &p.Z, per_spec * (size_t)p.v_cap));
     if (h->precision != CORR_FP32) {
         // one byte per code: e4m3, or int8 widened to BF16 by the Gram kernel
         const int eb = 1;
         p.q_pitch = (int)((((long long)h->n_int * eb) + 127) / 128 * 128);
         const size_t qbytes = (size_t)h->n_chan * 128 * p.q_pitch;
-        CK(cudaMalloc(&p.Q, qbytes));
+        CKA(dmalloc(h, &p.Q, qbytes));
         CK(cudaMemset(p.Q, 0, qbytes));
-        CK(cudaMalloc(&p.G, sizeof(float) * (size_t)h->n_chan * 128 * 128));
-        CK(cudaMalloc(&p.scale, sizeof(float) * (size_t)h->n_in_pad * h->n_chan));
+        CKA(dmalloc(h, &p.G, sizeof(float) * (size_t)h->n_chan * 128 * 128));
+        CKA(dmalloc(h, &p.scale, sizeof(float) * (size_t)h->n_in_pad * h->n_chan));
         p.have_scale = false;
     }
-    CK(cudaMalloc(&p.part, sizeof(float) * (size_t)h->gpi * h->nt * 32 * h->n_chan));
+    CKA(dmalloc(h, &p.part, sizeof(float) * (size_t)h->gpi * h->nt * 32 * h->n_chan));
     return CORR_OK;
 }
 
@@ -690,11 +730,19 @@ int finalize_into(corr_t h, Pipe& p, const Tables& t, float2* R, uint8_t* F, int
 int add_slot(corr_t h) {
     Slot s;
     const size_t ne = vis_elems(h);
-    CK(cudaMalloc(&s.d_R, ne * sizeof(float2)));
-    CK(cudaMalloc(&s.d_F, ne));
-    CK(cudaHostAlloc(&s.h_R, ne * sizeof(float2), cudaHostAllocDefault));
-    CK(cudaHostAlloc(&s.h_F, ne, cudaHostAllocDefault));
-    CK(cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
+    bool ok = dmalloc(h, &s.d_R, ne * sizeof(float2)) == cudaSuccess && dmalloc(h, &s.d_F, ne) == cudaSuccess &&
+              cudaHostAlloc(&s.h_R, ne * sizeof(float2), cudaHostAllocDefault) == cudaSuccess &&
+              cudaHostAlloc(&s.h_F, ne, cudaHostAllocDefault) == cudaSuccess &&
+              cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaFree(s.d_R);
+        cudaFree(s.d_F);
+        if (s.h_R) cudaFreeHost(s.h_R);
+        if (s.h_F) cudaFreeHost(s.h_F);
+        if (s.ev) cudaEventDestroy(s.ev);
+        cudaGetLastError();
+        return fail(h, CORR_ENOMEM, "result slot allocation failed");
+    }
     h->slots.push_back(s);
     return CORR_OK;
 }
@@ -760,16 +808,37 @@ int ensure_stream_alloc(corr_t h) {
     if (h->stream_alloc) return CORR_OK;
     const long long keep = (long long)(h->taps + 1) * h->M + 2 * h->max_delay + 64;
     h->stage_cap = ((h->chunk + keep + 15) / 16) * 16;
+    // all or nothing: a failure releases the staging buffers again
+    auto undo = [&](int rc) {
+        for (int b = 0; b < 2; ++b) {
+            cudaFree(h->d_stage_buf[b]);
+            h->d_stage_buf[b] = nullptr;
+            if (h->ev_buf[b]) cudaEventDestroy(h->ev_buf[b]);
+            h->ev_buf[b] = nullptr;
+        }
+        h->d_stage = nullptr;
+        cudaGetLastError();
+        return rc;
+    };
     for (int b = 0; b < 2; ++b) {
-        CK(cudaMalloc(&h->d_stage_buf[b], (size_t)h->stage_cap * h->n_in * h->es));
-        CK(cudaMemset(h->d_stage_buf[b], 0, (size_t)h->stage_cap * h->n_in * h->es));
-        CK(cudaEventCreateWithFlags(&h->ev_buf[b], cudaEventDisableTiming));
+        if (dmalloc(h, &h->d_stage_buf[b], (size_t)h->stage_cap * h->n_in * h->es) != cudaSuccess)
+            return undo(fail(h, CORR_ENOMEM, "staging buffer allocation failed"));
+        if (cudaMemset(h->d_stage_buf[b], 0, (size_t)h->stage_cap * h->n_in * h->es) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->ev_buf[b], cudaEventDisableTiming) != cudaSuccess)
+            return undo(fail(h, CORR_ECUDA, "staging buffer set-up failed"));
         h->buf_read[b] = false;
     }
     h->cur_buf = 0;
     h->d_stage = h->d_stage_buf[0];
-    CKRET(alloc_pipe(h, h->ps));
-    while ((int)h->slots.size() < h->result_slots) CKRET(add_slot(h));
+    int rc = alloc_pipe(h, h->ps);
+    if (rc != CORR_OK) return undo(rc);
+    while ((int)h->slots.size() < h->result_slots) {
+        rc = add_slot(h);
+        if (rc != CORR_OK) {
+            free_pipe(h->ps);
+            return undo(rc);
+        }
+    }
     h->stream_alloc = true;
     return CORR_OK;
 }
@@ -816,6 +885,8 @@ int push_common(corr_t h, const int8_t* src, size_t n, size_t stride, bool on_de
     const size_t es = (size_t)h->es;   // src is a byte address; n, stride count samples
     if (h->flushed) return fail(h, CORR_ESTATE, "stream already flushed; call corr_reset");
     if (n == 0) return CORR_OK;
+    if (h->max_pending > 0 && (int)h->q_vis.size() >= h->max_pending)
+        return fail(h, CORR_EAGAIN, "result queue full (max_pending): pop results before pushing");
     if (!src) return fail(h, CORR_EINVAL, "samples is NULL");
     if (stride < n) return fail(h, CORR_EINVAL, "input_stride < n_per_input");
     CKRET(ensure_stream_alloc(h));
@@ -1080,7 +1151,7 @@ int corr_set_option(corr_t h, const char* key, double v) {
     if (!h || !key) return fail(h, CORR_EINVAL, "NULL argument");
     const std::string k(key);
     if (h->started && k != "stage_timing" && k != "stage_mask" && k != "fir_spt" && k != "fused_f" &&
-        k != "tc_wait_ms" && k != "inject_stall")
+        k != "tc_wait_ms" && k != "inject_stall" && k != "inject_alloc_fail" && k != "max_pending")
         return fail(h, CORR_ESTATE, "options must be set before the first push");
     if (k == "flag_sigma") {
         if (!(v > 0)) return fail(h, CORR_EINVAL, "flag_sigma must be > 0");
@@ -1120,6 +1191,14 @@ int corr_set_option(corr_t h, const char* key, double v) {
         if (h->stream_alloc) return fail(h, CORR_ESTATE, "ring_mb must be set before the first push");
         h->ring_mb = (int)v;
         free_pipe(h->pd);
+    } else if (k == "inject_alloc_fail") {
+        if (v < 0 || v > 1000 || v != (double)(int)v) return fail(h, CORR_EINVAL, "inject_alloc_fail: 0 .. 1000");
+        h->inject_alloc_fail = (int)v;
+        return CORR_OK;
+    } else if (k == "max_pending") {
+        if (v < 0 || v > 1e6 || v != (double)(long long)v) return fail(h, CORR_EINVAL, "max_pending: 0 .. 1e6");
+        h->max_pending = (int)v;
+        return CORR_OK;
     } else if (k == "tc_wait_ms") {
         if (!(v >= 1.0 && v <= 60000.0)) return fail(h, CORR_EINVAL, "tc_wait_ms: 1 .. 60000");
         h->tc_wait_ms = v;
@@ -1273,7 +1352,7 @@ int corr_run_dev(corr_t h, const void* d_samples, size_t n_samples, size_t strid
     if (h->defer_tail && h->precision == CORR_FP32 && h->pd.part_all_ints < need) {
         cudaFree(h->pd.part_all);
         h->pd.part_all = nullptr;
-        CK(cudaMalloc(&h->pd.part_all, sizeof(float) * (size_t)need * h->gpi * h->nt * 32 * h->n_chan));
+        CKA(dmalloc(h, &h->pd.part_all, sizeof(float) * (size_t)need * h->gpi * h->nt * 32 * h->n_chan));
         h->pd.part_all_ints = need;
     }
     h->pd.s_next = h->pd.s_xdone = 0;
@@ -1301,7 +1380,7 @@ int corr_fengine_dev(corr_t h, const void* d_samples, size_t n_samples, size_t s
     if (n_spec > h->z_f_spectra) {
         cudaFree(h->d_z_f);
         h->d_z_f = nullptr;
-        CK(cudaMalloc(&h->d_z_f, sizeof(float2) * (size_t)n_spec * h->n_in_pad * h->n_chan));
+        CKA(dmalloc(h, &h->d_z_f, sizeof(float2) * (size_t)n_spec * h->n_in_pad * h->n_chan));
         h->z_f_spectra = n_spec;
     }
     StreamView sv{static_cast<const int8_t*>(d_samples), (long long)stride, 0, (long long)n_samples, h->es};
@@ -1325,7 +1404,7 @@ int corr_xengine_dev(corr_t h, const float* d_V, int n_spec, float* d_vis, void*
     if (slots > h->part_x_slots) {
         cudaFree(h->d_part_x);
         h->d_part_x = nullptr;
-        CK(cudaMalloc(&h->d_part_x, sizeof(float) * (size_t)slots * h->nt * 32 * h->n_chan));
+        CKA(dmalloc(h, &h->d_part_x, sizeof(float) * (size_t)slots * h->nt * 32 * h->n_chan));
         h->part_x_slots = slots;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1798,6 +1877,201 @@ int corr_spectrogram_dev(corr_t h, const void* d_samples, size_t n_samples, size
                        st, d_tiles, n_row, (int)rows));
         CK(cudaGetLastError());
     }
+    return CORR_OK;
+}
+
+// ---- checkpoint / resume ----------------------------------------------------
+
+namespace {
+
+struct StateHeader {
+    char magic[8];
+    int32_t version;
+    int32_t n_in, n_chan, taps, n_int, precision, es, iq, window, flag_window, ring_mb;
+    int32_t v_cap, gpi, nt, G, q_pitch, n_in_pad;
+    int32_t started, flushed, stream_alloc, have_scale, pending, n_vis_q, n_flag_q, reserved;
+    double kaiser_beta, flag_sigma;
+    int64_t max_delay, chunk, stage_cap, n_pushed, stage_base, stage_len, s_next, s_xdone, q_cols;
+};
+constexpr char kStateMagic[8] = {'C', 'O', 'R', 'R', 'S', 'T', '0', '1'};
+
+struct StateWriter {
+    uint8_t* p;
+    size_t cap, n;
+    void put(const void* src, size_t b) {
+        if (p && n + b <= cap) std::memcpy(p + n, src, b);
+        n += b;
+    }
+};
+
+}  // namespace
+
+int corr_save_state(corr_t h, void* buf, size_t cap, size_t* size) {
+    if (!h || h->is_group || !size) return fail(h, CORR_EINVAL, "bad argument");
+    DeviceGuard dg(h->dev);
+    if (h->s_comp) CK(cudaStreamSynchronize(h->s_comp));
+    if (h->s_copy) CK(cudaStreamSynchronize(h->s_copy));
+    if (h->s_out) CK(cudaStreamSynchronize(h->s_out));
+    StateHeader H{};
+    std::memcpy(H.magic, kStateMagic, 8);
+    H.version = 1;
+    H.n_in = h->n_in; H.n_chan = h->n_chan; H.taps = h->taps; H.n_int = h->n_int; H.precision = h->precision;
+    H.es = h->es; H.iq = h->iq; H.window = h->window; H.flag_window = h->flag_window; H.ring_mb = h->ring_mb;
+    H.v_cap = h->ps.v_cap; H.gpi = h->gpi; H.nt = h->nt; H.G = h->G; H.q_pitch = h->ps.q_pitch; H.n_in_pad = h->n_in_pad;
+    H.started = h->started; H.flushed = h->flushed; H.stream_alloc = h->stream_alloc;
+    H.have_scale = h->ps.have_scale; H.pending = h->pending;
+    H.n_vis_q = (int32_t)h->q_vis.size(); H.n_flag_q = (int32_t)h->q_flag.size();
+    H.kaiser_beta = h->kaiser_beta; H.flag_sigma = h->flag_sigma;
+    H.max_delay = h->max_delay; H.chunk = h->chunk; H.stage_cap = h->stage_cap; H.n_pushed = h->n_pushed;
+    H.stage_base = h->stage_base; H.stage_len = h->stage_len; H.s_next = h->ps.s_next; H.s_xdone = h->ps.s_xdone;
+    const long long istart = (h->ps.s_xdone / h->n_int) * h->n_int;
+    H.q_cols = h->precision != CORR_FP32 ? (h->ps.s_xdone - istart) : 0;
+    StateWriter w{static_cast<uint8_t*>(buf), buf ? cap : 0, 0};
+    w.put(&H, sizeof(H));
+    auto put_vec = [&](const std::vector<double>& v) {
+        std::vector<double> z(h->n_in, 0.0);
+        for (int a = 0; a < h->n_in && a < (int)v.size(); ++a) z[a] = v[a];
+        w.put(z.data(), sizeof(double) * z.size());
+    };
+    put_vec(h->stream_tau);
+    put_vec(h->stream_phi);
+    put_vec(h->tau);
+    put_vec(h->phi);
+    put_vec(h->tau_pend);
+    put_vec(h->phi_pend);
+    const size_t ne = vis_elems(h);
+    const size_t per_spec = (size_t)h->n_chan * h->n_in_pad * sizeof(float2);
+    std::vector<uint8_t> tmp;
+    auto put_dev = [&](const void* src, size_t b) -> int {
+        if (buf) {
+            tmp.resize(b);
+            CK(cudaMemcpy(tmp.data(), src, b, cudaMemcpyDeviceToHost));
+            w.put(tmp.data(), b);
+        } else {
+            w.n += b;
+        }
+        return CORR_OK;
+    };
+    if (h->stream_alloc) {
+        for (int a = 0; a < h->n_in; ++a)
+            CKRET(put_dev(h->d_stage + (size_t)a * h->stage_cap * h->es, (size_t)h->stage_len * h->es));
+        for (long long sp = h->ps.s_xdone; sp < h->ps.s_next; ++sp)
+            CKRET(put_dev(reinterpret_cast<const uint8_t*>(h->ps.V) + (size_t)(sp & (h->ps.v_cap - 1)) * per_spec,
+                          per_spec));
+        if (h->precision == CORR_FP32) {
+            CKRET(put_dev(h->ps.part, sizeof(float) * (size_t)h->gpi * h->nt * 32 * h->n_chan));
+        } else {
+            CKRET(put_dev(h->ps.scale, sizeof(float) * (size_t)h->n_in_pad * h->n_chan));
+            for (size_t r = 0; r < (size_t)h->n_chan * 128 && H.q_cols > 0; ++r)
+                CKRET(put_dev(h->ps.Q + r * h->ps.q_pitch, (size_t)H.q_cols));
+        }
+    }
+    for (int idx : h->q_vis) w.put(h->slots[idx].h_R, ne * sizeof(float2));
+    for (int idx : h->q_flag) w.put(h->slots[idx].h_F, ne);
+    if (buf && w.n > cap) return fail(h, CORR_EINVAL, "state buffer too small (" + std::to_string(w.n) + " bytes needed)");
+    *size = w.n;
+    return CORR_OK;
+}
+
+int corr_load_state(corr_t h, const void* buf, size_t size) {
+    if (!h || h->is_group || !buf) return fail(h, CORR_EINVAL, "bad argument");
+    if (h->started) return fail(h, CORR_ESTATE, "load a state into a new or reset handle");
+    DeviceGuard dg(h->dev);
+    const uint8_t* p = static_cast<const uint8_t*>(buf);
+    size_t n = 0;
+    auto get = [&](void* dst, size_t b) {
+        if (n + b > size) return false;
+        std::memcpy(dst, p + n, b);
+        n += b;
+        return true;
+    };
+    StateHeader H{};
+    if (!get(&H, sizeof(H)) || std::memcmp(H.magic, kStateMagic, 8) != 0 || H.version != 1)
+        return fail(h, CORR_EINVAL, "not a correlator state of this version");
+    if (H.n_in != h->n_in || H.n_chan != h->n_chan || H.taps != h->taps || H.n_int != h->n_int ||
+        H.precision != h->precision || H.es != h->es || H.iq != h->iq || H.window != h->window ||
+        H.flag_window != h->flag_window || H.ring_mb != h->ring_mb || H.kaiser_beta != h->kaiser_beta ||
+        H.flag_sigma != h->flag_sigma || H.max_delay != h->max_delay || H.chunk != h->chunk)
+        return fail(h, CORR_EINVAL, "state of a correlator with another shape or other options");
+    std::vector<double> v[6];
+    for (auto& x : v) {
+        x.assign(h->n_in, 0.0);
+        if (!get(x.data(), sizeof(double) * h->n_in)) return fail(h, CORR_EINVAL, "truncated state");
+    }
+    h->tau = v[2];
+    h->phi = v[3];
+    h->tau_pend = v[4];
+    h->phi_pend = v[5];
+    h->pending = H.pending != 0;
+    CKRET(upload_tables(h, h->tab_direct, h->tau, h->phi, h->s_comp));
+    CKRET(upload_tables(h, h->tab_stream, v[0], v[1], h->s_comp));
+    const size_t ne = vis_elems(h);
+    const size_t per_spec = (size_t)h->n_chan * h->n_in_pad * sizeof(float2);
+    if (H.stream_alloc) {
+        CKRET(ensure_stream_alloc(h));
+        if (H.v_cap != h->ps.v_cap || H.gpi != h->gpi || H.q_pitch != h->ps.q_pitch || H.stage_cap != h->stage_cap ||
+            H.stage_len > h->stage_cap)
+            return fail(h, CORR_EINVAL, "state buffers do not match this handle's");
+        auto get_dev = [&](void* dst, size_t b) -> int {
+            if (n + b > size) return fail(h, CORR_EINVAL, "truncated state");
+            CK(cudaMemcpy(dst, p + n, b, cudaMemcpyHostToDevice));
+            n += b;
+            return CORR_OK;
+        };
+        h->cur_buf = 0;
+        h->d_stage = h->d_stage_buf[0];
+        h->buf_read[0] = h->buf_read[1] = false;
+        for (int a = 0; a < h->n_in; ++a)
+            CKRET(get_dev(h->d_stage + (size_t)a * h->stage_cap * h->es, (size_t)H.stage_len * h->es));
+        for (long long sp = H.s_xdone; sp < H.s_next; ++sp)
+            CKRET(get_dev(reinterpret_cast<uint8_t*>(h->ps.V) + (size_t)(sp & (h->ps.v_cap - 1)) * per_spec, per_spec));
+        if (h->precision == CORR_FP32) {
+            CKRET(get_dev(h->ps.part, sizeof(float) * (size_t)h->gpi * h->nt * 32 * h->n_chan));
+        } else {
+            CKRET(get_dev(h->ps.scale, sizeof(float) * (size_t)h->n_in_pad * h->n_chan));
+            for (size_t r = 0; r < (size_t)h->n_chan * 128 && H.q_cols > 0; ++r)
+                CKRET(get_dev(h->ps.Q + r * h->ps.q_pitch, (size_t)H.q_cols));
+        }
+        h->stage_base = H.stage_base;
+        h->stage_len = H.stage_len;
+        h->n_pushed = H.n_pushed;
+        h->ps.s_next = H.s_next;
+        h->ps.s_xdone = H.s_xdone;
+        h->ps.have_scale = H.have_scale != 0;
+    }
+    // results not yet popped: the last max(n_vis_q, n_flag_q) integrations
+    const int nq = H.n_vis_q > H.n_flag_q ? H.n_vis_q : H.n_flag_q;
+    std::vector<std::vector<uint8_t>> vis(H.n_vis_q), fl(H.n_flag_q);
+    for (auto& x : vis) {
+        x.resize(ne * sizeof(float2));
+        if (!get(x.data(), x.size())) return fail(h, CORR_EINVAL, "truncated state");
+    }
+    for (auto& x : fl) {
+        x.resize(ne);
+        if (!get(x.data(), x.size())) return fail(h, CORR_EINVAL, "truncated state");
+    }
+    if (nq > 0) CKRET(ensure_stream_alloc(h));
+    for (int j = 0; j < nq; ++j) {
+        int idx;
+        CKRET(new_slot(h, &idx));
+        Slot& sl = h->slots[idx];
+        const int jv = j - (nq - H.n_vis_q), jf = j - (nq - H.n_flag_q);
+        if (jv >= 0) {
+            std::memcpy(sl.h_R, vis[jv].data(), vis[jv].size());
+            CK(cudaMemcpy(sl.d_R, sl.h_R, vis[jv].size(), cudaMemcpyHostToDevice));
+            sl.in_vis = true;
+            h->q_vis.push_back(idx);
+        }
+        if (jf >= 0) {
+            std::memcpy(sl.h_F, fl[jf].data(), fl[jf].size());
+            CK(cudaMemcpy(sl.d_F, sl.h_F, fl[jf].size(), cudaMemcpyHostToDevice));
+            sl.in_flag = true;
+            h->q_flag.push_back(idx);
+        }
+        CK(cudaEventRecord(sl.ev, h->s_out));
+    }
+    h->started = H.started != 0;
+    h->flushed = H.flushed != 0;
     return CORR_OK;
 }
 
