@@ -57,9 +57,9 @@ WORKLOADS = {
 
 # Stages reported by corr_stage_times and their kernels.
 STAGES = ["fir", "fft", "xengine", "finalize", "flag", "requant", "gram"]
-KERNELS = {"fir": "fir_kernel<4>", "fft": "fft_kernel<M,0>", "xengine": "xengine_kernel",
-           "finalize": "finalize_kernel", "flag": "mad_flag_kernel", "requant": "requant_kernel",
-           "gram": "gram_kernel (tcgen05)"}
+KERNELS = {"fir": "fir_kernel<4>", "fft": "fft_kernel<M,3>", "xengine": "xengine_kernel",
+           "finalize": "finalize_kernel", "flag": "mad_flag_kernel", "requant": "requant_pm_kernel",
+           "gram": "gram_i8_kernel (tcgen05, int8 bytes widened on chip)"}
 # Algorithmic bytes per input sample of each hot-path kernel, in the unit the
 # scope table's measurement section fixes: the whole hot path (PFB, FFT,
 # delays, X-engine, flagging) reads each int8 input sample once (1 B); on the
@@ -71,10 +71,10 @@ ALG_BYTES_PER_SAMPLE = {"fir": 1.0, "fft": 1.0, "xengine": 1.0, "finalize": 0.0,
 # Bytes each kernel of this build actually moves per input sample, rings
 # included (FIR: 1 B in + 4 B of z = (y_a, y_b) out; FFT: 4 B of z in + one
 # complex64 per channel per input out; X-engine: the spectra back in;
-# requantiser: spectra in, one code per component out, int8 carried as BF16;
+# requantiser: spectra in, one 1-byte code (int8 or e4m3) per component out;
 # Gram: the codes).  Reported beside the algorithmic figure, not used for it.
 INTERMEDIATE_BYTES_PER_SAMPLE = {"fir": 5.0, "fft": 8.0, "xengine": 4.0, "finalize": 0.0, "flag": 0.0,
-                                 "requant": 6.0, "gram": 2.0}
+                                 "requant": 5.0, "gram": 1.0}
 
 
 # DRAM read + write per input sample of a kernel, from one ncu capture of the
@@ -510,6 +510,8 @@ def run_batched(args, rank, world, local):
     # --- roofline: a captured graph carries no per-kernel events, so the
     # members run once more one by one (untimed) with every stage bracketed
     st_ms, st_n, st_bytes = [0.0] * len(STAGES), [0] * len(STAGES), [0.0] * len(STAGES)
+    st_flops = [0.0] * len(STAGES)
+    fused_m, plain_m = [], []
     for c, x, v, f, prec in zip(members, xs, vis, flags, precs):
         bps = dict(ALG_BYTES_PER_SAMPLE)
         c.set_option("stage_timing", 1)
@@ -518,10 +520,13 @@ def run_batched(args, rank, world, local):
         m_ms, m_n = c.stage_times()
         c.set_option("stage_timing", 0)
         n_used = (x.shape[1] // c.M) * c.M * c.n_in
+        fused_c = m_n[STAGES.index("fir")] == 0       # the fused F-engine runs no FIR launches
+        (fused_m if fused_c else plain_m).append(c.M)
         for i, k in enumerate(STAGES):
             st_ms[i] += m_ms[i]
             st_n[i] += m_n[i]
             st_bytes[i] += bps[k] * n_used if m_n[i] else 0.0
+            st_flops[i] += flops_per_sample(k, fused_c, c.M, c.taps, c.n_in) * n_used if m_n[i] else 0.0
     tot = sum(st_ms) or 1.0
     share = {k: st_ms[i] / tot for i, k in enumerate(STAGES)}
     di = max((i for i, k in enumerate(STAGES) if ALG_BYTES_PER_SAMPLE[k] > 0), key=lambda i: st_ms[i])
@@ -531,12 +536,29 @@ def run_batched(args, rank, world, local):
     bpl = st_bytes[di] / max(1, st_n[di])
     inter = sum(INTERMEDIATE_BYTES_PER_SAMPLE[STAGES[di]] * (x.shape[1] // c.M) * c.M * c.n_in
                 for c, x in zip(members, xs)) / max(1, st_n[di])
-    roofline = {"kernel": KERNELS[STAGES[di]], "bound": "hbm", "achieved": bpl / (avg_ms * 1e-3) / 1e9,
+    kname = KERNELS[STAGES[di]]
+    if STAGES[di] == "fft":
+        kname = "; ".join(["pfb_fft_kernel<M,3,4> (fused PFB + FFT, M = %s)" % sorted(set(fused_m))]
+                          * bool(fused_m) +
+                          ["fft_kernel<M,3> after fir_kernel (M = %s)" % sorted(set(plain_m))] * bool(plain_m))
+    roofline = {"kernel": kname, "bound": "hbm", "achieved": bpl / (avg_ms * 1e-3) / 1e9,
                 "bytes_per_sample": ALG_BYTES_PER_SAMPLE[STAGES[di]], "intermediate_bytes_per_launch": inter,
                 "peak": hbm, "unit": "GB/s", "frac": bpl / (avg_ms * 1e-3) / 1e9 / hbm, "traffic": None,
                 "peak_source": "measured" if peaks else "fallback", "bytes_per_launch": bpl,
                 "avg_launch_ms": avg_ms, "launches": st_n[di], "stage_share": share,
                 "source": "members run one by one outside the graph (untimed), every stage bracketed"}
+    if st_flops[di] > 0:
+        fp = fp32_peak()
+        tf = st_flops[di] / (st_ms[di] * 1e-3) / 1e12
+        alu = {"achieved": tf, "peak": fp["scalar"], "unit": "TFLOP/s", "frac": tf / fp["scalar"],
+               "flop_per_sample_avg": st_flops[di] / max(1.0, st_bytes[di] / ALG_BYTES_PER_SAMPLE[STAGES[di]]),
+               "peak_source": "measured (corr_peak_fp32, scalar FMA chains)"}
+        if alu["frac"] > roofline["frac"]:
+            hbm_part = {k: roofline[k] for k in ("achieved", "peak", "unit", "frac", "peak_source")}
+            roofline.update({k: alu[k] for k in ("achieved", "peak", "unit", "frac", "peak_source")})
+            roofline.update(bound="alu", hbm=hbm_part, alu={"flop_per_sample_avg": alu["flop_per_sample_avg"]})
+        else:
+            roofline["alu"] = alu
 
     # --- end to end: every step copies the eight streams from pinned host
     # memory into the graph's input buffers, replays the graph and reads the
@@ -1054,8 +1076,6 @@ def _roofline(wl, prec, args, dom, di, share, stage_ms, stage_n, S, n_in):
         inter["fft"] = 1.0 + 4.0        # samples in, spectra out (no z ring)
     if es == 2:
         inter["fir"] += 1.0
-    if prec == 2:
-        inter.update(requant=5.0, gram=1.0)
     bytes_per_launch = alg * samples_timed / launches
     avg_ms = stage_ms[di] / launches
     achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
@@ -1064,8 +1084,7 @@ def _roofline(wl, prec, args, dom, di, share, stage_ms, stage_n, S, n_in):
     kname = KERNELS[dom]
     M = 2 * W["n_chan"]
     if dom == "fft":
-        # mode 3: spectra ring pair-major (FP32 path with n_in_pad <= 8); 0: channel-major
-        mode = 3 if prec == 0 and (n_in + 3) // 4 * 4 <= 8 else 0
+        mode = 3                         # every real-input pipeline writes the pair-major ring
         kname = ("pfb_fft_kernel<%d,%d,%d> (fused PFB + FFT)" % (M, mode, W["taps"]) if fused
                  else "fft_kernel<%d,%d>" % (M, mode))
     fl = flops_per_sample(dom, fused, M, W["taps"], n_in)

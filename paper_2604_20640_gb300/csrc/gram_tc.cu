@@ -181,10 +181,10 @@ __global__ void __launch_bounds__(128, 1) gram_kernel(const __grid_constant__ CU
 // the accumulator.  Every wait is bounded; the converters decide each step
 // together (barrier with an AND reduction), so no converter can be left
 // alone at a named barrier.
-// 3 raw + 2 converted stages: 112 KiB, so two CTAs share an SM (one CTA's
-// accumulator read-out overlaps the other's MMAs)
-constexpr int kRawStages = 3;
-constexpr int kConvStages = 2;
+// 4 raw + 3 converted stages, one CTA per SM (a 3 + 2 form with two CTAs
+// per SM measured slower)
+constexpr int kRawStages = 4;
+constexpr int kConvStages = 3;
 constexpr int kRawBytes = kRows * 128;           // 128 int8 codes per row
 constexpr int kConvBytes = 2 * kRows * 128;      // two BF16 tiles of 64 codes per row
 struct __align__(8) GramI8Shared {
@@ -221,7 +221,7 @@ __device__ __forceinline__ uint32_t bf16x2_of_codes(uint32_t f, int c) {
     return __byte_perm(__float_as_uint(x0), __float_as_uint(x1), 0x7632);
 }
 
-__global__ void __launch_bounds__(256, 2) gram_i8_kernel(const __grid_constant__ CUtensorMap tmap, GramArgs A) {
+__global__ void __launch_bounds__(256, 1) gram_i8_kernel(const __grid_constant__ CUtensorMap tmap, GramArgs A) {
     extern __shared__ __align__(1024) uint8_t gsm_raw[];
     uint8_t* conv = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* raw = conv + kConvStages * kConvBytes;
