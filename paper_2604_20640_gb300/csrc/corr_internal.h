@@ -87,10 +87,15 @@ struct FusedArgs {
     const int* coarse;       // [n_in_pad] coarse advance d_a
     int taps;
     int run;                 // spectra per CTA run (0: one wave of resident CTAs)
+    // Requantised codes instead of spectra (modes 6 int8, 7 e4m3): f.V holds
+    // a pair-major ring of 32-bit words [slot][pair][n_chan] (bytes Re U_a,
+    // Im U_a, Re U_b, Im U_b), from the inverse scales inv[a][k].
+    const float* inv;        // [n_in_pad][n_chan]; nullptr: spectra out (modes 0-3)
+    bool fp8;                // e4m3 codes (mode 7), else int8 (mode 6)
 };
 
-// True when the fused kernel covers this shape (int8 samples, 2 <= taps <=
-// 4, transform lengths whose buffers fit one CTA); otherwise the two-kernel
+// True when the fused kernel covers this shape (int8 samples, 4 taps,
+// transform lengths whose buffers fit one CTA); otherwise the two-kernel
 // path (launch_fir + launch_fft) runs.
 bool fused_f_supported(int M, int taps, int es, int mode);
 // CORR_OK, or CORR_EINVAL for a shape fused_f_supported rejects.
@@ -181,7 +186,7 @@ struct GramArgs {
 struct RequantArgs {
     const float2* V;
     long long v_origin, v_mask;
-    const float* scale;      // [n_in_pad][n_chan]
+    const float* scale;      // [2][n_in_pad][n_chan]: scales, then their inverses
     uint8_t* Q;
     int k_pitch;
     long long s_begin, s_end, int_start;
@@ -189,6 +194,7 @@ struct RequantArgs {
     bool fp8;
     int pair_major;          // V pair-major ([slot][pair][n_chan] float4); always set
     int i8b;                 // int8 codes as bytes (else carried as BF16)
+    int codes_in;            // V holds the F-engine's code words ([slot][pair][n_chan] uint32): transpose only
 };
 
 // R[k][a][b] = scale_a scale_b / (4 count) rot_a conj(rot_b) sum q_a conj(q_b),

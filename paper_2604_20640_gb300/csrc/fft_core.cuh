@@ -24,6 +24,7 @@
 
 #include "corr.h"
 #include "corr_internal.h"
+#include "quant.cuh"
 #include "tc_common.cuh"
 
 #include <cudaTypedefs.h>
@@ -41,6 +42,25 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 namespace {
 
 __device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
+
+// Packed FP32 pairs (sm_100+): one add.rn.f32x2 / sub.rn.f32x2 per complex
+// addition, the same IEEE result per lane as two scalar operations.
+__device__ __forceinline__ unsigned long long f2u(float2 v) {
+    return (unsigned long long)__float_as_uint(v.x) | ((unsigned long long)__float_as_uint(v.y) << 32);
+}
+__device__ __forceinline__ float2 u2f(unsigned long long u) {
+    return make_float2(__uint_as_float((unsigned)u), __uint_as_float((unsigned)(u >> 32)));
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(r);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(r);
+}
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -383,21 +403,10 @@ __device__ __forceinline__ typename Raw4<ES>::T fir_word(const FirArgs& A, const
     return w;
 }
 
-// Packed FP32 pairs (sm_100+): two lanes of one 64-bit register per op.
-__device__ __forceinline__ unsigned long long f2u(float2 v) {
-    return (unsigned long long)__float_as_uint(v.x) | ((unsigned long long)__float_as_uint(v.y) << 32);
-}
-__device__ __forceinline__ float2 u2f(unsigned long long u) {
-    return make_float2(__uint_as_float((unsigned)u), __uint_as_float((unsigned)(u >> 32)));
-}
+// Packed FP32 fused multiply-add: two lanes of one 64-bit register.
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
     unsigned long long r;
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)), "l"(f2u(c)));
-    return u2f(r);
-}
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-    unsigned long long r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
     return u2f(r);
 }
 
@@ -890,7 +899,10 @@ __device__ __forceinline__ float2 unpack_pair(uint32_t fa, uint32_t fb, int c) {
 }
 
 // MODE as in fft_kernel (0 U = 2Y channel-major, 1 rotated V, 2 power
-// tiles, 3 U pair-major), one input pair per CTA; P taps.
+// tiles, 3 U pair-major), or 6 / 7: U requantised to int8 / e4m3 codes, the
+// pair's four codes of a channel (Re U_a, Im U_a, Re U_b, Im U_b, low byte
+// first) as one 32-bit word of a pair-major code ring [slot][pair][n_chan];
+// one input pair per CTA; P taps.
 template <int M, int MODE, int P>
 __global__ void __launch_bounds__(M / 16, FftCfg<M>::minb(3)) pfb_fft_kernel(const FusedArgs A) {
     using C = FftCfg<M>;
@@ -1152,6 +1164,25 @@ __global__ void __launch_bounds__(M / 16, FftCfg<M>::minb(3)) pfb_fft_kernel(con
                     pa[i] = 0.f;
                     pb[i] = 0.f;
                 }
+            }
+        } else if constexpr (MODE >= 6) {
+            // the requantiser's arithmetic on the same U = 2Y values: code of
+            // U * (1 / sigma) per component; consecutive channels across the
+            // warp, so each store instruction writes whole lines
+            constexpr bool FP8 = MODE == 7;
+            const long long slot = (s - F.v_origin) & F.v_mask;
+            uint32_t* const Cout = reinterpret_cast<uint32_t*>(F.V) + ((size_t)slot * n_pairs + pair) * n_chan;
+            const float* const inv0 = A.inv + (size_t)a * n_chan;
+            const float* const inv1 = inv0 + n_chan;
+            for (int k = tid; k < n_chan; k += NACT) {
+                const float2 zk = zres[pidx(k)];
+                const float2 zm = zres[pidx((M - k) & (M - 1))];
+                const float ia = has0 ? __ldg(inv0 + k) : 0.f;
+                const float ib = has1 ? __ldg(inv1 + k) : 0.f;
+                const float sx = zk.x + zm.x, sy = zk.y - zm.y;
+                const float dx = zk.x - zm.x, dy = zk.y + zm.y;
+                Cout[k] = q_code<FP8>(sx * ia) | (q_code<FP8>(sy * ia) << 8) | (q_code<FP8>(dy * ib) << 16) |
+                          (q_code<FP8>(-dx * ib) << 24);
             }
         } else {
             const long long slot = (s - F.v_origin) & F.v_mask;

@@ -56,12 +56,12 @@ int launch_fused_mode(const FusedArgs& a, cudaStream_t st) {
 
 bool fused_f_supported(int M, int taps, int es, int mode) {
     if (es != 1 || taps != 4) return false;
-    if (mode == 2 || mode == 3) return M >= 1024 && M <= 8192;
+    if (mode == 2 || mode == 3 || mode == 6 || mode == 7) return M >= 1024 && M <= 8192;
     return M == 8192;
 }
 
 int launch_fused_f(const FusedArgs& a, cudaStream_t st) {
-    const int mode = a.f.tiles ? 2 : a.f.phasor ? 1 : a.f.pair_major ? 3 : 0;
+    const int mode = a.inv ? (a.fp8 ? 7 : 6) : a.f.tiles ? 2 : a.f.phasor ? 1 : a.f.pair_major ? 3 : 0;
     if (!fused_f_supported(a.f.M, a.taps, a.src.es, mode)) return CORR_EINVAL;
     if ((reinterpret_cast<uintptr_t>(a.hs) & 15) != 0) return CORR_EINVAL;
     if (a.f.s_end <= a.f.s_begin) return CORR_OK;
@@ -69,6 +69,8 @@ int launch_fused_f(const FusedArgs& a, cudaStream_t st) {
         case 0: return launch_fused_mode<0>(a, st);
         case 1: return launch_fused_mode<1>(a, st);
         case 2: return launch_fused_mode<2>(a, st);
+        case 6: return launch_fused_mode<6>(a, st);
+        case 7: return launch_fused_mode<7>(a, st);
         default: return launch_fused_mode<3>(a, st);
     }
 }

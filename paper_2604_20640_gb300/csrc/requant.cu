@@ -1,7 +1,8 @@
 // Requantiser and rescaling around the tensor-core X-engine.
 //
 // requant_pm_kernel turns a batch of channelised spectra (U = 2Y, unrotated,
-// in the pair-major ring [slot][pair][n_chan] float4) into the stacked
+// in the pair-major ring [slot][pair][n_chan] float4), or the code words the
+// fused F-engine already made from them, into the stacked
 // operand Q[k][row][t] of the tensor-core Gram: row a holds Re U_a /
 // sigma_a[k], row N + a holds Im U_a / sigma_a[k], t the spectrum index inside
 // the integration: int8 codes (round half to even, saturate at +-127) as
@@ -15,23 +16,13 @@
 #include "corr.h"
 #include "corr_internal.h"
 
+#include "quant.cuh"
+
 #include <cuda_bf16.h>
-#include <cuda_fp8.h>
 
 namespace corr {
 
 namespace {
-
-constexpr int kTileS = 64;
-
-__device__ __forceinline__ uint8_t q_int8(float x) {
-    x = fminf(fmaxf(x, -127.f), 127.f);
-    return (uint8_t)(int8_t)__float2int_rn(x);
-}
-
-__device__ __forceinline__ uint8_t q_e4m3(float x) {
-    return (uint8_t)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
-}
 
 // Int8 code as the bit pattern of the BF16 value with the same magnitude.
 __device__ __forceinline__ uint16_t code_bf16(uint8_t q) {
@@ -43,7 +34,9 @@ __device__ __forceinline__ uint16_t code_bf16(uint8_t q) {
 // the warp (coalesced 16-byte reads), a run of RUN spectra per thread; the
 // pair's four rows (Re a, Re b, Im a, Im b) each get one whole 32-byte sector
 // of codes.
-// CODE: 0 int8 carried as BF16 (2 bytes), 1 e4m3 byte, 2 int8 byte.
+// CODE: 0 int8 carried as BF16 (2 bytes), 1 e4m3 byte, 2 int8 byte, 3 the
+// F-engine's code words already made ([slot][pair][n_chan] 32-bit words,
+// bytes Re a, Im a, Re a+1, Im a+1): a transpose into Q only.
 template <int CODE>
 __global__ void __launch_bounds__(128) requant_pm_kernel(const RequantArgs A) {
     constexpr bool FP8 = CODE == 1;
@@ -58,16 +51,31 @@ __global__ void __launch_bounds__(128) requant_pm_kernel(const RequantArgs A) {
     const long long sb = A.s_begin + (long long)blockIdx.z * RUN;
     if (sb >= A.s_end) return;
     const int ns = (int)((A.s_end - sb) < RUN ? (A.s_end - sb) : RUN);
-    const float inv0 = a0 < N ? 1.0f / A.scale[(size_t)a0 * A.n_chan + k] : 0.f;
-    const float inv1 = a1 < N ? 1.0f / A.scale[(size_t)a1 * A.n_chan + k] : 0.f;
+    // inverse scales [n_in_pad][n_chan] follow the scales (scale + n_in_pad n_chan)
+    const float* inv = A.scale + (size_t)A.n_in_pad * A.n_chan;
+    const float inv0 = (CODE != 3 && a0 < N) ? inv[(size_t)a0 * A.n_chan + k] : 0.f;
+    const float inv1 = (CODE != 3 && a1 < N) ? inv[(size_t)a1 * A.n_chan + k] : 0.f;
     uint32_t w[4][8];                 // rows Re a0, Im a0, Re a1, Im a1
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int j = 0; j < 8; ++j) w[r][j] = 0u;
+    if constexpr (CODE == 3) {
+        const uint32_t* C = reinterpret_cast<const uint32_t*>(A.V);
+#pragma unroll
+        for (int i = 0; i < RUN; ++i) {
+            uint32_t c = 0u;
+            if (i < ns) {
+                const long long slot = (sb + i - A.v_origin) & A.v_mask;
+                c = __ldg(C + ((size_t)slot * n_pairs + pr) * A.n_chan + k);
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) w[r][i / 4] |= ((c >> (8 * r)) & 0xFFu) << (8 * (i % 4));
+        }
+    }
     const float4* V4 = reinterpret_cast<const float4*>(A.V);
 #pragma unroll
-    for (int i = 0; i < RUN; ++i) {
+    for (int i = 0; i < (CODE == 3 ? 0 : RUN); ++i) {
         float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
         if (i < ns) {
             const long long slot = (sb + i - A.v_origin) & A.v_mask;
@@ -120,6 +128,7 @@ __global__ void scale_ring_kernel(const float2* V, long long v_origin, long long
     float s = sqrtf((k == 0 ? 1.f : 0.5f) * p) / gain;
     if (!(s > 0.f) || !isfinite(s)) s = 1.f;
     scale[(size_t)a * n_chan + k] = s;
+    scale[((size_t)n_in_pad + a) * n_chan + k] = 1.0f / s;
 }
 
 __global__ void scale_vis_kernel(const float2* R, int n_in, int n_in_pad, int n_chan, float gain, float* scale) {
@@ -130,6 +139,7 @@ __global__ void scale_vis_kernel(const float2* R, int n_in, int n_in_pad, int n_
     float s = 2.f * sqrtf((k == 0 ? 1.f : 0.5f) * fmaxf(raa, 0.f)) / gain;
     if (!(s > 0.f) || !isfinite(s)) s = 1.f;
     scale[(size_t)a * n_chan + k] = s;
+    scale[((size_t)n_in_pad + a) * n_chan + k] = 1.0f / s;
 }
 
 __global__ void finalize_q_kernel(const FinQArgs F) {
@@ -169,9 +179,10 @@ __global__ void finalize_q_kernel(const FinQArgs F) {
 void launch_requant(const RequantArgs& a, cudaStream_t st) {
     const long long n = a.s_end - a.s_begin;
     if (n <= 0) return;
-    const int run = (a.fp8 || a.i8b) ? 32 : 16;
+    const int run = (a.fp8 || a.i8b || a.codes_in) ? 32 : 16;
     dim3 grid((unsigned)((a.n_chan + 127) / 128), (unsigned)(a.n_in_pad / 2), (unsigned)((n + run - 1) / run));
-    if (a.fp8) requant_pm_kernel<1><<<grid, 128, 0, st>>>(a);
+    if (a.codes_in) requant_pm_kernel<3><<<grid, 128, 0, st>>>(a);
+    else if (a.fp8) requant_pm_kernel<1><<<grid, 128, 0, st>>>(a);
     else if (a.i8b) requant_pm_kernel<2><<<grid, 128, 0, st>>>(a);
     else requant_pm_kernel<0><<<grid, 128, 0, st>>>(a);
 }

@@ -42,6 +42,7 @@ struct Pipe {
     float* G = nullptr;       // [n_chan][128][128]
     float* scale = nullptr;   // [n_in_pad][n_chan], fixed per integration
     bool have_scale = false;  // false until the first integration's pre-pass
+    bool ring_codes = false;  // the unrequantised ring slots hold the F-engine's code words
 };
 
 struct Slot {
@@ -412,7 +413,8 @@ int alloc_pipe_impl(corr_t h, Pipe& p) {
         CKA(dmalloc(h, &p.Q, qbytes));
         CK(cudaMemset(p.Q, 0, qbytes));
         CKA(dmalloc(h, &p.G, sizeof(float) * (size_t)h->n_chan * 128 * 128));
-        CKA(dmalloc(h, &p.scale, sizeof(float) * (size_t)h->n_in_pad * h->n_chan));
+        // scales, then their inverses (the requantiser's multipliers)
+        CKA(dmalloc(h, &p.scale, 2 * sizeof(float) * (size_t)h->n_in_pad * h->n_chan));
         p.have_scale = false;
     }
     CKA(dmalloc(h, &p.part, sizeof(float) * (size_t)h->gpi * h->nt * 32 * h->n_chan));
@@ -447,11 +449,27 @@ int build_filter_tables(corr_t h) {
     return CORR_OK;
 }
 
+// Requantised codes made by the F-engine itself (reduced precision, once the
+// integration's scales are fixed): the inverse scales and the code type.
+struct CodeOut {
+    const float* inv;
+    bool fp8;
+};
+
+// The fused F-engine can write the pipeline's codes for this handle.
+bool fused_codes(corr_t h, const StreamView& sv) {
+    return h->precision != CORR_FP32 && h->fused_f && !h->iq &&
+           fused_f_supported(h->M, h->taps, sv.es, h->precision == CORR_FP8 ? 7 : 6);
+}
+
 // F-engine over spectra [s_begin, s_end): FIR into the Z ring, FFT into the
-// V ring.  `phasor` set -> rotated V (stage call); else U = 2Y (pipeline).
+// V ring.  `phasor` set -> rotated V (stage call); `codes` set -> the V ring
+// holds requantised code words instead of spectra (fused kernel only); else
+// U = 2Y (pipeline).
 int launch_f(corr_t h, const StreamView& sv, const Tables& t, float2* Z, long long z_origin, long long z_mask,
              float2* V, long long v_origin, long long v_mask, const float2* phasor, long long s_begin,
-             long long s_end, cudaStream_t st, float* tiles = nullptr, int n_row = 0, int rows = 0) {
+             long long s_end, cudaStream_t st, float* tiles = nullptr, int n_row = 0, int rows = 0,
+             const CodeOut* codes = nullptr) {
     FirArgs a{};
     a.src = sv;
     a.h = h->d_h;
@@ -489,7 +507,8 @@ int launch_f(corr_t h, const StreamView& sv, const Tables& t, float2* Z, long lo
     f.n_in = h->n_in;
     f.pair_major = phasor == nullptr && tiles == nullptr && pair_major_ring(h);
     f.iq = h->iq;
-    const int mode = tiles ? 2 : phasor ? 1 : f.pair_major ? 3 : 0;
+    const int mode = codes ? (codes->fp8 ? 7 : 6) : tiles ? 2 : phasor ? 1 : f.pair_major ? 3 : 0;
+    if (codes && !fused_codes(h, sv)) return fail(h, CORR_EINVAL, "codes from the F-engine need the fused kernel");
     if (h->fused_f && !h->iq && fused_f_supported(h->M, h->taps, sv.es, mode)) {
         FusedArgs u{};
         u.f = f;
@@ -498,6 +517,10 @@ int launch_f(corr_t h, const StreamView& sv, const Tables& t, float2* Z, long lo
         u.coarse = t.coarse;
         u.taps = h->taps;
         u.run = h->fir_spt;
+        if (codes) {
+            u.inv = codes->inv;
+            u.fp8 = codes->fp8;
+        }
         int rc;
         {
             Timed t_(h, 1, st);
@@ -551,7 +574,18 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
         if (s_end > iend) s_end = iend;
         if (s_end > p.s_xdone + p.v_cap) s_end = p.s_xdone + p.v_cap;
         if (s_end > p.s_next) {
-            CKRET(launch_f(h, sv, t, p.Z, 0, p.v_cap - 1, p.V, 0, p.v_cap - 1, nullptr, p.s_next, s_end, st));
+            // scales fixed and nothing left in the ring: the F-engine
+            // requantises in its epilogue (the requantiser's arithmetic) and
+            // writes 4-byte code words instead of 16-byte spectra; the
+            // requantiser below then only transposes them into Q
+            p.ring_codes = p.have_scale && p.s_xdone == p.s_next && fused_codes(h, sv);
+            if (p.ring_codes) {
+                const CodeOut q{p.scale + (size_t)h->n_in_pad * h->n_chan, h->precision == CORR_FP8};
+                CKRET(launch_f(h, sv, t, p.Z, 0, p.v_cap - 1, p.V, 0, p.v_cap - 1, nullptr, p.s_next, s_end, st,
+                               nullptr, 0, 0, &q));
+            } else {
+                CKRET(launch_f(h, sv, t, p.Z, 0, p.v_cap - 1, p.V, 0, p.v_cap - 1, nullptr, p.s_next, s_end, st));
+            }
             p.s_next = s_end;
             progress = true;
         }
@@ -592,6 +626,7 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
                 r.fp8 = h->precision == CORR_FP8;
                 r.pair_major = pair_major_ring(h);
                 r.i8b = h->precision == CORR_INT8;
+                r.codes_in = p.ring_codes;
                 {
                     Timed t_(h, 5, st);
                     launch_requant(r, st);
@@ -1306,7 +1341,7 @@ int corr_reset(corr_t h) {
     h->buf_read[0] = h->buf_read[1] = false;
     h->n_pushed = 0;
     h->ps.s_next = h->ps.s_xdone = 0;
-    h->ps.have_scale = false;
+    h->ps.have_scale = h->ps.ring_codes = false;
     h->q_vis.clear();
     h->q_flag.clear();
     for (Slot& s : h->slots) s.in_vis = s.in_flag = false;
@@ -1356,7 +1391,7 @@ int corr_run_dev(corr_t h, const void* d_samples, size_t n_samples, size_t strid
         h->pd.part_all_ints = need;
     }
     h->pd.s_next = h->pd.s_xdone = 0;
-    h->pd.have_scale = false;
+    h->pd.have_scale = h->pd.ring_codes = false;
     StreamView sv;
     sv.x = static_cast<const int8_t*>(d_samples);
     sv.es = h->es;
@@ -1961,7 +1996,7 @@ int corr_save_state(corr_t h, void* buf, size_t cap, size_t* size) {
         if (h->precision == CORR_FP32) {
             CKRET(put_dev(h->ps.part, sizeof(float) * (size_t)h->gpi * h->nt * 32 * h->n_chan));
         } else {
-            CKRET(put_dev(h->ps.scale, sizeof(float) * (size_t)h->n_in_pad * h->n_chan));
+            CKRET(put_dev(h->ps.scale, 2 * sizeof(float) * (size_t)h->n_in_pad * h->n_chan));
             for (size_t r = 0; r < (size_t)h->n_chan * 128 && H.q_cols > 0; ++r)
                 CKRET(put_dev(h->ps.Q + r * h->ps.q_pitch, (size_t)H.q_cols));
         }
@@ -2028,7 +2063,7 @@ int corr_load_state(corr_t h, const void* buf, size_t size) {
         if (h->precision == CORR_FP32) {
             CKRET(get_dev(h->ps.part, sizeof(float) * (size_t)h->gpi * h->nt * 32 * h->n_chan));
         } else {
-            CKRET(get_dev(h->ps.scale, sizeof(float) * (size_t)h->n_in_pad * h->n_chan));
+            CKRET(get_dev(h->ps.scale, 2 * sizeof(float) * (size_t)h->n_in_pad * h->n_chan));
             for (size_t r = 0; r < (size_t)h->n_chan * 128 && H.q_cols > 0; ++r)
                 CKRET(get_dev(h->ps.Q + r * h->ps.q_pitch, (size_t)H.q_cols));
         }

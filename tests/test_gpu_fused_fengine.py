@@ -147,3 +147,37 @@ def test_fused_streaming_pushes_match_run_dev():
     c.close()
     assert v.shape[0] == g
     assert np.array_equal(v, v_run.cpu().numpy()) and np.array_equal(f, f_run.cpu().numpy())
+
+
+# (n_ant, n_pol, n_chan, n_int) of the reduced-precision pipelines whose
+# F-engine writes the codes itself: M = 1024 .. 8192, a padding input, 64
+# inputs, integration lengths that are not multiples of the requantiser's
+# 32-spectrum runs, a partial last integration
+CODE_SHAPES = [(2, 1, 512, 37), (3, 2, 1024, 45), (5, 1, 2048, 22), (32, 2, 1024, 70), (12, 2, 4096, 9)]
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("n_ant,n_pol,n_chan,n_int", CODE_SHAPES)
+@pytest.mark.parametrize("run", [0, 5])
+def test_fused_codes_are_bit_identical_to_requantiser(prec, n_ant, n_pol, n_chan, n_int, run):
+    """With fixed scales (from the first ring fill after the pre-pass on)
+    the fused F-engine requantises in its epilogue and writes 4-byte code
+    words instead of spectra, which the requantiser only transposes into the
+    tensor-core operand; with fused_f = 0 the requantiser makes the codes
+    from the U = 2Y spectra of the two-kernel F-engine.  Same codes, so the
+    visibilities and flags agree bit for bit (runs of 5 spectra per CTA and
+    1 MiB rings put launch and run boundaries at odd columns)."""
+    n_in = n_ant * n_pol
+    M = 2 * n_chan
+    S = M * (3 * n_int + 9) + 101
+    tau, phi = delays_for(n_in, 5 * n_in + n_chan)
+    tau = np.asarray(tau).copy()
+    tau[0] = -6.3
+    spec = StreamSpec(n_ant=n_ant, n_pol=n_pol, n_samples=S, seed=900 + n_chan + n_in, tau=tau, phi=phi,
+                      tones=[(0.1, 8.0, 0.2)])
+    x = torch.from_numpy(make_stream(spec)).to(DEV)
+    g1, v1, f1 = _run(n_ant, n_pol, n_chan, n_int, x, tau, phi, 1, precision=prec, fir_spt=run, ring_mb=1)
+    g0, v0, f0 = _run(n_ant, n_pol, n_chan, n_int, x, tau, phi, 0, precision=prec, ring_mb=1)
+    assert g1 == g0 == v1.shape[0] >= 4
+    assert torch.equal(v1, v0) and torch.equal(f1, f0)
+    assert torch.isfinite(torch.view_as_real(v1)).all()
