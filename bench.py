@@ -71,8 +71,9 @@ ALG_BYTES_PER_SAMPLE = {"fir": 1.0, "fft": 1.0, "xengine": 1.0, "finalize": 0.0,
 # Bytes each kernel of this build actually moves per input sample, rings
 # included (FIR: 1 B in + 4 B of z = (y_a, y_b) out; FFT: 4 B of z in + one
 # complex64 per channel per input out; X-engine: the spectra back in;
-# requantiser: spectra in, one 1-byte code (int8 or e4m3) per component out;
-# Gram: the codes).  Reported beside the algorithmic figure, not used for it.
+# requantiser: spectra in, one 1-byte code (int8 or e4m3) per component out,
+# or only a transpose of the fused F-engine's code words; Gram: the codes).
+# Reported beside the algorithmic figure, not used for it.
 INTERMEDIATE_BYTES_PER_SAMPLE = {"fir": 5.0, "fft": 8.0, "xengine": 4.0, "finalize": 0.0, "flag": 0.0,
                                  "requant": 5.0, "gram": 1.0}
 
@@ -1074,6 +1075,10 @@ def _roofline(wl, prec, args, dom, di, share, stage_ms, stage_n, S, n_in):
     inter = dict(INTERMEDIATE_BYTES_PER_SAMPLE)
     if fused:
         inter["fft"] = 1.0 + 4.0        # samples in, spectra out (no z ring)
+        if prec != 0:
+            # reduced precision: 4-byte code words per pair and channel out,
+            # which the requantiser transposes (1 B in, 1 B out)
+            inter.update(fft=1.0 + 1.0, requant=2.0)
     if es == 2:
         inter["fir"] += 1.0
     bytes_per_launch = alg * samples_timed / launches

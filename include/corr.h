@@ -117,7 +117,11 @@ const char* corr_last_error(corr_t h);
  *                  memory) where it covers the shape -- int8 samples, 4
  *                  taps, 1024 <= M <= 8192 for the pipeline's spectra
  *                  rings and the dynamic spectra, M = 8192 for the stage
- *                  call -- else as FIR + FFT; results are bit-identical
+ *                  call -- else as FIR + FFT; results are bit-identical.
+ *                  With reduced precision the fused kernel also makes the
+ *                  int8 / e4m3 codes once an integration's scales are fixed
+ *                  (the requantiser then only transposes them); the codes
+ *                  equal the requantiser's
  *   "sample_bits"  (8, default; or 16)  input sample type of every call that
  *                  takes samples: int8 (the 8-bit truncated recorder mode of
  *                  Sec. 3) or little-endian int16 (the 16-bit padded mode,

@@ -54,6 +54,7 @@ struct __align__(8) ConvShared {
     uint64_t wfull;
     uint64_t acc_full[2];
     uint64_t acc_empty[2];
+    uint64_t mma_done;       // every MMA the issuer started has completed
     uint32_t tmem_addr;
     int abort;
 };
@@ -104,6 +105,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
             mbar_init(&sh->acc_full[b], 1);
             mbar_init(&sh->acc_empty[b], 4);
         }
+        mbar_init(&sh->mma_done, 1);
         sh->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -118,6 +120,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = sh->tmem_addr;
+    int issued = 0;   // A-ring loads issued (producer thread)
 
     if (warp == 0 && lane == 0) {
         // ---- TMA producer: resident weights, then the A ring
@@ -138,6 +141,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                 mbar_expect_tx(&sh->full[s], kATile);
                 // box {8 channels, 132 pixels, 4 channel groups, 1 row, 1 image}
                 tma_load_5d(a_st + s * kATile, &tx, &sh->full[s], 0, j0 - 2, 0, i + A.sgn * (u - 2), n);
+                issued = it + 1;
             }
         }
     } else if (warp == 1 && lane == 0) {
@@ -183,6 +187,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
             }
             mma_commit(&sh->acc_full[b]);
         }
+        mma_commit(&sh->mma_done);
     } else if (warp >= 2) {
         // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31
         const int q = warp & 3;
@@ -240,7 +245,18 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     __syncwarp();
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (threadIdx.x == 0 && sh->abort && A.status) atomicExch(A.status, CORR_ETIMEDOUT);
+    if (sh->abort) {   // uniform: written before the barrier above only
+        // wait (bounded) for the copies and MMAs still in flight before the
+        // shared memory and TMEM are given back
+        if (threadIdx.x == 0 && A.status) atomicExch(A.status, CORR_ETIMEDOUT);
+        if (warp == 0 && lane == 0) {
+            drain_loads(sh->full, kAStages, issued, kWaitNs);
+            mbar_wait(&sh->wfull, 0);
+        }
+        if (warp == 1 && lane == 0) mbar_wait(&sh->mma_done, 0);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
     if (warp == 0) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
     }

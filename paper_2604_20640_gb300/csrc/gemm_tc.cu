@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ CU
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = sh->tmem_addr;
+    int issued = 0;   // TMA stage loads issued (producer thread)
 
     if (num_k > 0) {
         if (warp == 0 && lane == 0) {
@@ -100,6 +101,7 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ CU
                 mbar_expect_tx(&sh->full[s], kStage);
                 tma_load_2d(stages + s * kStage, &ta, &sh->full[s], k_begin + it * 64, m0);
                 tma_load_2d(stages + s * kStage + kATile, &tb, &sh->full[s], k_begin + it * 64, 0);
+                issued = it + 1;
             }
         } else if (warp == 1 && lane == 0) {
             bool ok = true;
@@ -131,6 +133,7 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ CU
     float* D = G.D + ((size_t)split * G.M + row) * BN;
     if (sh->abort) {
         if (threadIdx.x == 0 && G.status) atomicExch(G.status, CORR_ETIMEDOUT);
+        if (warp == 0 && lane == 0) drain_loads(sh->full, kGStages, issued, kWaitNs);
     } else if (num_k == 0) {
         if (row < G.M)
             for (int c = 0; c < BN; ++c) D[c] = 0.f;

@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(128, 1) gram_kernel(const __grid_constant__ CU
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = sh->tmem_addr;
+    int issued = 0;   // TMA loads issued (producer thread)
 
     if (warp == 0 && lane == 0) {
         // TMA producer (with inject_stall it issues nothing: the MMA issuer's
@@ -119,6 +120,7 @@ __global__ void __launch_bounds__(128, 1) gram_kernel(const __grid_constant__ CU
             // inner coordinate in elements: 128 bytes = 128 e4m3 or 64 BF16
             tma_load_2d(stages + s * kStageBytes, &tmap, &sh->full[s], it * (FP8 ? kKTile : kKTile / 2),
                         ch * kRows);
+            issued = it + 1;
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
@@ -149,6 +151,7 @@ __global__ void __launch_bounds__(128, 1) gram_kernel(const __grid_constant__ CU
     __syncthreads();
     if (sh->abort) {
         if (threadIdx.x == 0 && A.status) atomicExch(A.status, CORR_ETIMEDOUT);
+        if (warp == 0 && lane == 0) drain_loads(sh->full, kStages, issued, lim);
     } else {
         const int row = warp * 32 + lane;
         uint32_t* G = reinterpret_cast<uint32_t*>(A.G) + ((size_t)ch * kRows + row) * kRows;
@@ -173,7 +176,8 @@ __global__ void __launch_bounds__(128, 1) gram_kernel(const __grid_constant__ CU
 // The same Gram matrix with the codes in HBM as int8 bytes (half the bytes of
 // the BF16-carried form).  There is no integer tcgen05 MMA on sm_103a, so the
 // codes are widened on chip: 256 threads; warp 0 lane 0 streams raw
-// 128-row x 128-byte int8 tiles by TMA (no swizzle); warps 4-7 (one row per
+// 128-row x 128-byte int8 tiles by TMA (128-byte swizzle, so a converter
+// warp's row reads spread over all banks); warps 4-7 (one row per
 // thread) widen each tile to two BF16 operand tiles of 64 K-elements in the
 // 128-byte-swizzled K-major layout the MMA descriptors describe (16-byte
 // chunk q of row r at r * 128 + ((q ^ (r & 7)) << 4)), make them visible to
@@ -255,6 +259,7 @@ __global__ void __launch_bounds__(256, 1) gram_i8_kernel(const __grid_constant__
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = sh->tmem_addr;
+    int issued = 0;   // TMA loads issued (producer thread)
 
     if (warp == 0 && lane == 0) {
         // TMA producer of raw int8 tiles (with inject_stall it issues nothing)
@@ -267,6 +272,7 @@ __global__ void __launch_bounds__(256, 1) gram_i8_kernel(const __grid_constant__
             }
             mbar_expect_tx(&sh->raw_full[s], kRawBytes);
             tma_load_2d(raw + s * kRawBytes, &tmap, &sh->raw_full[s], it * 128, ch * kRows);
+            issued = it + 1;
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer: two BF16 tiles of 64 codes per converted stage
@@ -307,7 +313,7 @@ __global__ void __launch_bounds__(256, 1) gram_i8_kernel(const __grid_constant__
             uint8_t* drow = conv + c * kConvBytes + r * 128;
 #pragma unroll
             for (int c16 = 0; c16 < 8; ++c16) {
-                const uint4 v = src[c16];
+                const uint4 v = src[c16 ^ (r & 7)];   // the raw tile is 128-byte swizzled too
                 const uint32_t w[4] = {v.x ^ 0x80808080u, v.y ^ 0x80808080u, v.z ^ 0x80808080u,
                                        v.w ^ 0x80808080u};
                 const uint4 lo = make_uint4(bf16x2_of_codes(w[0], 0), bf16x2_of_codes(w[0], 2),
@@ -334,6 +340,7 @@ __global__ void __launch_bounds__(256, 1) gram_i8_kernel(const __grid_constant__
     __syncthreads();
     if (sh->abort) {
         if (threadIdx.x == 0 && A.status) atomicExch(A.status, CORR_ETIMEDOUT);
+        if (warp == 0 && lane == 0) drain_loads(sh->raw_full, kRawStages, issued, lim);
     } else if (warp < 4) {
         const int row = warp * 32 + lane;
         uint32_t* G = reinterpret_cast<uint32_t*>(A.G) + ((size_t)ch * kRows + row) * kRows;
@@ -378,7 +385,9 @@ size_t gram_i8_smem_bytes() {
 int launch_gram(const GramArgs& a, cudaStream_t st) {
     if (a.n_chan <= 0 || a.K <= 0) return CORR_OK;
     if (a.i8b) {
-        // int8 codes as bytes: raw tiles of 128 codes x 128 rows, no swizzle
+        // int8 codes as bytes: raw tiles of 128 codes x 128 rows, 128-byte
+        // swizzle (16-byte chunk q of row r at r * 128 + ((q ^ (r & 7)) << 4)),
+        // so the converters' row reads are free of bank conflicts
         if (a.fp8 || a.k_pitch % 128 != 0 || a.K > a.k_pitch) return CORR_EINVAL;
         if ((reinterpret_cast<uintptr_t>(a.Q) & 15) != 0) return CORR_EINVAL;
         PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
@@ -389,7 +398,7 @@ int launch_gram(const GramArgs& a, cudaStream_t st) {
         cuuint32_t box[2] = {128u, (cuuint32_t)kRows};
         cuuint32_t estr[2] = {1, 1};
         CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(a.Q), dims, strides, box, estr,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return CORR_EINVAL;
         const size_t smem = gram_i8_smem_bytes();

@@ -53,6 +53,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsign
     return true;
 }
 
+// Exit path of a kernel that gave up a wait: wait (bounded) until the last
+// `issued` TMA loads into a ring of n_stages stages, each completing on its
+// stage's full barrier, have landed, so no copy is left writing into the
+// shared memory of a finished CTA.  Loads before the last n_stages were
+// consumed already (a stage is refilled only after its consumer released it).
+__device__ __forceinline__ void drain_loads(uint64_t* full, int n_stages, int issued, unsigned long long limit_ns) {
+    for (int it = issued > n_stages ? issued - n_stages : 0; it < issued; ++it)
+        if (!mbar_wait(&full[it % n_stages], (uint32_t)(it / n_stages) & 1u, limit_ns)) return;
+}
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
