@@ -79,12 +79,16 @@ INTERMEDIATE_BYTES_PER_SAMPLE = {"fir": 5.0, "fft": 8.0, "xengine": 4.0, "finali
 
 
 # DRAM read + write per input sample of a kernel, from one ncu capture of the
-# same launch shape and the same kernel code (profiles/fir_fft_c2_small_ncu.md:
-# fft_kernel<8192,3>, 268.5 MB read + 215.7 MB written per launch of 1024
-# spectra x 4 pairs = 67.1 M samples with 256 MiB rings, cold cache).
+# same launch shape and the same kernel code (profiles/fused_fengine_c2_ncu.md:
+# pfb_fft_kernel<8192,3,4>, 74.8 MB read + 206.9 MB written per launch of
+# 1024 spectra x 4 pairs = 67.1 M samples with 256 MiB rings, cold cache).
 # Reported as the roofline's `traffic` only for the workload and kernel it
 # was taken on.
-TRAFFIC_PER_SAMPLE = {("c2", "fft"): 484.27e6 / 67108864}
+TRAFFIC_PER_SAMPLE = {("c2", "fused"): 281.71e6 / 67108864}
+
+# Inputs below this size are timed step by step with L2 flushed in between
+# (L2 is 129 MB on a GB300; twice that is written).
+L2_FLUSH_BYTES = 256 << 20
 
 
 def _spec(wl, rank, samples):
@@ -98,7 +102,9 @@ def _spec(wl, rank, samples):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms; the
+    constructor returns once the first sample is in, so the samples cover
+    the region timed after it."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -110,10 +116,22 @@ class ClockSampler:
         self.gpu = gpu_index
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.Q,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.p = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and self.p.poll() is None:
+            self.f.flush()
+            if os.path.getsize(self.f.name) > 0:
+                break
+            time.sleep(0.01)
+        self.n0 = 0
+        try:
+            self.n0 = len(open(self.f.name).read().strip().splitlines())
+        except OSError:
+            pass
 
     def stop(self):
         if self.p is None:
@@ -124,7 +142,9 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.p.kill()
         self.f.flush()
-        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        lines = open(self.f.name).read().strip().splitlines()
+        # samples taken after the first one (the timed region started then)
+        rows = [r.split(",") for r in lines[max(0, getattr(self, "n0", 0) - 1):] if r.strip()]
         os.unlink(self.f.name)
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -954,7 +974,7 @@ def main():
                                 "e4m3 requantised, tcgen05 X"][prec],
                        "samples_per_input": S, "sample_bits": args.bits,
                        "tuning": {"ring_mb": m["tuning"][0], "fir_spt": m["tuning"][1]},
-                       "l2": "inputs (%d MiB/step) larger than L2" % (bytes_step >> 20),
+                       "l2": m["l2"],
                        "parallelism": "replicas" if world > 1 else "single"},
             "gpu_launches": m["launches"], "clocks": m["clocks"], "roofline": m["roofline"], "e2e": e2e,
             "cpu_baseline": cpu, "error": error, "plain_fp32": plain,
@@ -1004,18 +1024,36 @@ def measure_stream(args, wl, prec, x, spec, dev, world, barrier, clocks=True, st
         c.set_option("stage_mask", 1 << di)
     barrier()
     torch.cuda.synchronize(dev)
+    # an input that fits in L2 (c1) is timed step by step with L2 flushed
+    # between the steps (a 256 MiB write, outside the events)
+    flush = x.numel() * x.element_size() < L2_FLUSH_BYTES
+    scratch = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev) if flush else None
     sampler = ClockSampler(dev.index) if clocks else None
     l0 = c.launches
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        c.run_dev(x, vis, flags)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
+    if flush:
+        ms_sum = 0.0
+        for i in range(args.steps):
+            scratch.fill_(i & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c.run_dev(x, vis, flags)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms_sum += e0.elapsed_time(e1)
+        ms = ms_sum / args.steps
+    else:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            c.run_dev(x, vis, flags)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / args.steps
     barrier()
     clk = sampler.stop() if sampler else None
     launches = c.launches - l0
-    ms = e0.elapsed_time(e1) / args.steps
+    l2 = ("L2 flushed between timed steps (%d MiB write outside the events)" % (L2_FLUSH_BYTES >> 20) if flush
+          else "inputs (%d MiB/step) larger than L2" % (x.numel() * x.element_size() >> 20))
     roofline = None
     if stages:
         stage_ms, stage_n = c.stage_times()
@@ -1024,7 +1062,7 @@ def measure_stream(args, wl, prec, x, spec, dev, world, barrier, clocks=True, st
         roofline = _roofline(wl, prec, args, dom, di, share, stage_ms, stage_n, S, n_in)
     c.close()
     return {"ms": ms, "tuning": tuning, "launches": launches, "clocks": clk, "roofline": roofline,
-            "vis": vis, "flags": flags}
+            "vis": vis, "flags": flags, "l2": l2}
 
 
 def flops_per_sample(dom, fused, M, taps, n_in):

@@ -79,17 +79,20 @@ __global__ void __launch_bounds__(128) xengine_kernel(const XArgs X) {
 }
 
 // n_in_pad <= 8: one thread keeps the whole Hermitian triangle (a <= b) of
-// one channel.  A warp covers 4 channels x 8 sub-groups; sub-group q sums
-// spectra q, q+8, q+16, ... of the group and the eight partial sums are
-// added with a fixed xor-shuffle tree, then written in the 4x4 block layout.
+// one channel.  A warp covers 16 consecutive channels x 2 sub-groups;
+// sub-group q sums spectra q, q+2, q+4, ... of the group (one pair's 16
+// channels are 256 contiguous bytes of the pair-major ring), the two partial
+// sums are added by one xor-shuffle, then written in the 4x4 block layout.
 // PM: spectra pair-major ([slot][pair][n_chan] float4), else channel-major.
+constexpr int kXsChan = 16;       // channels per warp
+constexpr int kXsSub = 2;         // sub-groups per channel
 template <int NB, bool PM>
 __global__ void __launch_bounds__(128) xengine_small_kernel(const XArgs X) {
     constexpr int NI = 4 * NB;
     constexpr int NC = NI * (NI - 1) / 2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int q = lane >> 2;
-    const int k = (blockIdx.x * (blockDim.x >> 5) + warp) * 4 + (lane & 3);
+    const int q = lane / kXsChan;
+    const int k = (blockIdx.x * (blockDim.x >> 5) + warp) * kXsChan + (lane % kXsChan);
     const int g = blockIdx.y;
     const bool valid = k < X.n_chan;
     const int kk = valid ? k : X.n_chan - 1;
@@ -102,7 +105,7 @@ __global__ void __launch_bounds__(128) xengine_small_kernel(const XArgs X) {
     for (int i = 0; i < NI; ++i) au[i] = 0.f;
 #pragma unroll
     for (int i = 0; i < NC; ++i) { cr[i] = 0.f; ci[i] = 0.f; }
-    for (long long s = s0 + q; s < s1; s += 8) {
+    for (long long s = s0 + q; s < s1; s += kXsSub) {
         const long long slot = (s - X.v_origin) & X.v_mask;
         const float4* vp = PM ? reinterpret_cast<const float4*>(X.V) + (size_t)slot * (NI / 2) * X.n_chan + kk
                               : reinterpret_cast<const float4*>(X.V) + ((size_t)slot * X.n_chan + kk) * (NI / 2);
@@ -126,7 +129,7 @@ __global__ void __launch_bounds__(128) xengine_small_kernel(const XArgs X) {
         }
     }
 #pragma unroll
-    for (int m = 4; m <= 16; m <<= 1) {
+    for (int m = kXsChan; m < 32; m <<= 1) {
 #pragma unroll
         for (int i = 0; i < NI; ++i) au[i] += __shfl_xor_sync(0xffffffffu, au[i], m);
 #pragma unroll
@@ -405,7 +408,8 @@ int group_tail_grid() {
 void launch_xengine(const XArgs& a, cudaStream_t st) {
     if (a.n_groups <= 0) return;
     if (a.n_in_pad <= 8) {
-        dim3 grid((a.n_chan + 15) / 16, a.n_groups);
+        constexpr int per_cta = 4 * kXsChan;          // 4 warps of 16 channels
+        dim3 grid((a.n_chan + per_cta - 1) / per_cta, a.n_groups);
         if (a.pair_major) {
             if (a.n_in_pad == 4) xengine_small_kernel<1, true><<<grid, 128, 0, st>>>(a);
             else xengine_small_kernel<2, true><<<grid, 128, 0, st>>>(a);
