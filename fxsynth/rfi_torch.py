@@ -15,7 +15,8 @@ generator seeded from it):
   - linear chirps of 16-64 rows drifting 0.25-4 channels per row;
 * broadband bursts of 1-4 rows, over the whole band or a sub-band of >= 1/16
   of it: Gaussian noise band-limited in the frequency domain, per-channel
-  INR drawn from ``bb_db``;
+  INR drawn from ``bb_db`` (0-30 dB; above about 18 dB the sum saturates the
+  int8 samples, as an 8-bit recorder does);
 * the sum rounded half-to-even and clipped to int8 (``total``);
 * the narrowband and the broadband RFI alone, each scaled by a per-input gain
   (``g_nb``, ``g_bb``) that brings its peak to about 120 and quantised the
@@ -44,7 +45,7 @@ class RfiSpec:
     seed: int = 5000
     sigma: float = 16.0
     nb_db: tuple = (0.0, 30.0)
-    bb_db: tuple = (0.0, 8.0)
+    bb_db: tuple = (0.0, 30.0)
     tones_per_tile: float = 1.5        # mean number per 64 x 256 tile
     chirps_per_tile: float = 0.6
     bursts_per_block: float = 1.2      # mean number per input and 64-row block
@@ -95,12 +96,20 @@ def make_rfi_batch(spec: RfiSpec, batch: int, device="cuda"):
                 ln = int(rng.integers(4, 65))
                 r0 = int(rng.integers(0, max(1, R - ln + 1)))
                 r1 = min(R, r0 + ln)
-            # phase in exact 32-bit fixed point: (t f 2^32) mod 2^32, t < 2^27
-            fq = int(round(f * 2.0 ** 32)) & 0xFFFFFFFF
-            t = torch.arange(r0 * spr, r1 * spr, device=device, dtype=torch.int64)
-            ph = ((t * fq) & 0xFFFFFFFF).to(torch.float32) * (2 * math.pi / 2.0 ** 32)
-            nb[r0 * spr:r1 * spr] += _amp(spec.sigma, M, rng.uniform(*spec.nb_db)) * torch.cos(
-                ph + rng.uniform(0, 2 * math.pi))
+            # phase in cycles per block of 2^16 samples t = t_b + tau: the
+            # block's start frac(f t_b) in FP64, plus frac(f tau) from one
+            # shared table, summed in FP32 (below 2 cycles: 2^-23 resolution)
+            amp = _amp(spec.sigma, M, rng.uniform(*spec.nb_db))
+            ph0 = rng.uniform(0, 2 * math.pi)
+            n = (r1 - r0) * spr
+            blk = 1 << 16
+            tb = torch.arange(r0 * spr, r1 * spr, blk, device=device, dtype=torch.float64)
+            base = torch.remainder(f * tb, 1.0).to(torch.float32)
+            loc = torch.remainder(f * torch.arange(blk, device=device, dtype=torch.float64), 1.0).to(torch.float32)
+            cyc = base[:, None] + loc[None, :]
+            cyc.mul_(2 * math.pi).add_(ph0).cos_().mul_(amp)
+            nb[r0 * spr:r1 * spr] += cyc.reshape(-1)[:n]
+            del cyc
         for _ in range(rng.poisson(spec.chirps_per_tile * n_tiles_per_input)):
             ln = int(rng.integers(16, 65))
             r0 = int(rng.integers(0, max(1, R - ln + 1)))

@@ -114,6 +114,8 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=5000)
     ap.add_argument("--init", type=int, default=0, help="seed of the He-normal initialisation")
+    ap.add_argument("--eval-inputs", type=int, default=8,
+                    help="inputs of the held-out evaluation batch (32: the flagging workload's 512 tiles)")
     ap.add_argument("--out", required=True)
     args = ap.parse_args()
     import torch
@@ -124,9 +126,12 @@ def main():
     losses = train(net, src, args.steps, args.tiles, args.lr,
                    log=lambda i: print("step %d  %.1f s" % (i, time.time() - t0), flush=True))
     np.save(args.out, net.get_params())
-    p, t, tn, tb, _ = src.batch(10 ** 6, with_parts=True)
+    t_train = time.time() - t0
+    ev = src if args.eval_inputs == 8 else TileSource(n_in=args.eval_inputs, seed=args.seed + 1)
+    p, t, tn, tb, _ = ev.batch(10 ** 6, with_parts=True)
     print({"loss_first": float(np.mean(losses[:10])), "loss_last": float(np.mean(losses[-50:])),
-           "seconds": time.time() - t0, "eval": evaluate(net, p, t, tn, tb)})
+           "steps": args.steps, "tiles_drawn": args.steps * args.tiles, "eval_tiles": int(p.shape[0]),
+           "train_seconds": round(t_train, 1), "eval": evaluate(net, p, t, tn, tb)})
 
 
 def init_params(seed: int = 0) -> np.ndarray:
