@@ -84,10 +84,25 @@ __global__ void __launch_bounds__(128) xengine_kernel(const XArgs X) {
 // channels are 256 contiguous bytes of the pair-major ring), the two partial
 // sums are added by one xor-shuffle, then written in the 4x4 block layout.
 // PM: spectra pair-major ([slot][pair][n_chan] float4), else channel-major.
+// Each thread streams its spectra through kXsDepth stages of shared memory
+// with cp.async (16-byte copies of its own chunks, so no barrier is needed):
+// four spectra in flight a thread instead of one.
 constexpr int kXsChan = 16;       // channels per warp
 constexpr int kXsSub = 2;         // sub-groups per channel
+constexpr int kXsDepth = 4;       // spectra in flight per thread
+
+__device__ __forceinline__ void xs_cp16(float4* dst, const float4* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void xs_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void xs_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int NB>
+constexpr size_t xs_smem_bytes() { return sizeof(float4) * kXsDepth * (2 * NB) * 128; }
+
 template <int NB, bool PM>
-__global__ void __launch_bounds__(128) xengine_small_kernel(const XArgs X) {
+__global__ void __launch_bounds__(128, 5) xengine_small_kernel(const XArgs X) {
     constexpr int NI = 4 * NB;
     constexpr int NC = NI * (NI - 1) / 2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -105,15 +120,29 @@ __global__ void __launch_bounds__(128) xengine_small_kernel(const XArgs X) {
     for (int i = 0; i < NI; ++i) au[i] = 0.f;
 #pragma unroll
     for (int i = 0; i < NC; ++i) { cr[i] = 0.f; ci[i] = 0.f; }
+    // stage buffer [depth][pair][thread]: thread-private chunks
+    extern __shared__ float4 xs_buf[];
+    const size_t vs = PM ? (size_t)X.n_chan : 1;          // float4 between pairs
+    auto fetch = [&](long long s, int stage) {
+        if (s < s1) {
+            const long long slot = (s - X.v_origin) & X.v_mask;
+            const float4* vp = PM ? reinterpret_cast<const float4*>(X.V) + (size_t)slot * (NI / 2) * X.n_chan + kk
+                                  : reinterpret_cast<const float4*>(X.V) + ((size_t)slot * X.n_chan + kk) * (NI / 2);
+#pragma unroll
+            for (int i = 0; i < NI / 2; ++i)
+                xs_cp16(xs_buf + ((size_t)stage * (NI / 2) + i) * 128 + threadIdx.x, vp + i * vs);
+        }
+        xs_commit();   // one group per stage, empty past the end
+    };
+#pragma unroll
+    for (int d = 0; d < kXsDepth; ++d) fetch(s0 + q + (long long)d * kXsSub, d);
+    int stage = 0;
     for (long long s = s0 + q; s < s1; s += kXsSub) {
-        const long long slot = (s - X.v_origin) & X.v_mask;
-        const float4* vp = PM ? reinterpret_cast<const float4*>(X.V) + (size_t)slot * (NI / 2) * X.n_chan + kk
-                              : reinterpret_cast<const float4*>(X.V) + ((size_t)slot * X.n_chan + kk) * (NI / 2);
-        const size_t vs = PM ? (size_t)X.n_chan : 1;      // float4 between pairs
+        xs_wait<kXsDepth - 1>();   // this thread's copies of spectrum s have landed
         float xr[NI], xi[NI];
 #pragma unroll
         for (int i = 0; i < NI / 2; ++i) {
-            const float4 t = __ldg(vp + i * vs);
+            const float4 t = xs_buf[((size_t)stage * (NI / 2) + i) * 128 + threadIdx.x];
             xr[2 * i] = t.x; xi[2 * i] = t.y; xr[2 * i + 1] = t.z; xi[2 * i + 1] = t.w;
         }
 #pragma unroll
@@ -127,6 +156,9 @@ __global__ void __launch_bounds__(128) xengine_small_kernel(const XArgs X) {
                 ci[c] = fmaf(xi[a], xr[b], fmaf(-xr[a], xi[b], ci[c]));
             }
         }
+        // this stage's values are used: refill it kXsDepth spectra ahead
+        fetch(s + (long long)kXsDepth * kXsSub, stage);
+        stage = stage + 1 == kXsDepth ? 0 : stage + 1;
     }
 #pragma unroll
     for (int m = kXsChan; m < 32; m <<= 1) {
@@ -411,11 +443,11 @@ void launch_xengine(const XArgs& a, cudaStream_t st) {
         constexpr int per_cta = 4 * kXsChan;          // 4 warps of 16 channels
         dim3 grid((a.n_chan + per_cta - 1) / per_cta, a.n_groups);
         if (a.pair_major) {
-            if (a.n_in_pad == 4) xengine_small_kernel<1, true><<<grid, 128, 0, st>>>(a);
-            else xengine_small_kernel<2, true><<<grid, 128, 0, st>>>(a);
+            if (a.n_in_pad == 4) xengine_small_kernel<1, true><<<grid, 128, xs_smem_bytes<1>(), st>>>(a);
+            else xengine_small_kernel<2, true><<<grid, 128, xs_smem_bytes<2>(), st>>>(a);
         } else {
-            if (a.n_in_pad == 4) xengine_small_kernel<1, false><<<grid, 128, 0, st>>>(a);
-            else xengine_small_kernel<2, false><<<grid, 128, 0, st>>>(a);
+            if (a.n_in_pad == 4) xengine_small_kernel<1, false><<<grid, 128, xs_smem_bytes<1>(), st>>>(a);
+            else xengine_small_kernel<2, false><<<grid, 128, xs_smem_bytes<2>(), st>>>(a);
         }
         return;
     }
