@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(128, 1) gram_kernel(const __grid_constant__ CU
 // the BF16-carried form).  There is no integer tcgen05 MMA on sm_103a, so the
 // codes are widened on chip: 256 threads; warp 0 lane 0 streams raw
 // 128-row x 128-byte int8 tiles by TMA (128-byte swizzle, so a converter
-// warp's row reads spread over all banks); warps 4-7 (one row per
+// warp's row reads spread over all banks); warps 4-11 (half a row per
 // thread) widen each tile to two BF16 operand tiles of 64 K-elements in the
 // 128-byte-swizzled K-major layout the MMA descriptors describe (16-byte
 // chunk q of row r at r * 128 + ((q ^ (r & 7)) << 4)), make them visible to
@@ -201,19 +201,23 @@ struct __align__(8) GramI8Shared {
     int abort;
 };
 
-// AND of p over the 128 converter threads (named barrier 1).
+constexpr int kConvThreads = 256;   // warps 4-11: two threads a row
+
+// AND of p over the converter threads (named barrier 1).
 __device__ __forceinline__ bool converters_all(bool p) {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred a, b;\n\tsetp.ne.u32 a, %1, 0;\n\t"
-        "bar.red.and.pred b, 1, 128, a;\n\tselp.u32 %0, 1, 0, b;\n\t}"
+        "bar.red.and.pred b, 1, %2, a;\n\tselp.u32 %0, 1, 0, b;\n\t}"
         : "=r"(r)
-        : "r"((uint32_t)p)
+        : "r"((uint32_t)p), "n"(kConvThreads)
         : "memory");
     return r != 0;
 }
 
-__device__ __forceinline__ void converters_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void converters_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kConvThreads) : "memory");
+}
 
 // Two BF16 values (low: byte c of w, high: byte c+1) of sign-flipped int8
 // bytes, exact: the float of each code, then its upper half (the lower half
@@ -225,7 +229,8 @@ __device__ __forceinline__ uint32_t bf16x2_of_codes(uint32_t f, int c) {
     return __byte_perm(__float_as_uint(x0), __float_as_uint(x1), 0x7632);
 }
 
-__global__ void __launch_bounds__(256, 1) gram_i8_kernel(const __grid_constant__ CUtensorMap tmap, GramArgs A) {
+__global__ void __launch_bounds__(128 + kConvThreads, 1) gram_i8_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                        GramArgs A) {
     extern __shared__ __align__(1024) uint8_t gsm_raw[];
     uint8_t* conv = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* raw = conv + kConvStages * kConvBytes;
@@ -299,20 +304,25 @@ __global__ void __launch_bounds__(256, 1) gram_i8_kernel(const __grid_constant__
         if (!ok) sh->abort = 1;
         mma_commit(&sh->accum);
     } else if (warp >= 4) {
-        // converters: thread r widens row r of each raw tile
-        const int r = (int)threadIdx.x - 128;
+        // converters: threads 2r and 2r + 1 widen the two halves of row r of
+        // each raw tile (16-byte chunks 0-3 and 4-7; the second half visits
+        // its chunks rotated by two, so the halves of a row never share a
+        // bank in the same step)
+        const int cv = (int)threadIdx.x - 128;
+        const int r = cv >> 1, hf = cv & 1;
         for (int it = 0; it < num_k; ++it) {
             const int s = it % kRawStages, c = it % kConvStages;
             bool ok = mbar_wait(&sh->raw_full[s], (uint32_t)(it / kRawStages) & 1u, lim);
             ok = ok && mbar_wait(&sh->conv_empty[c], ((uint32_t)(it / kConvStages) & 1u) ^ 1u, lim);
             if (!converters_all(ok)) {
-                if (r == 0) sh->abort = 1;
+                if (cv == 0) sh->abort = 1;
                 break;
             }
             const uint4* src = reinterpret_cast<const uint4*>(raw + s * kRawBytes + r * 128);
             uint8_t* drow = conv + c * kConvBytes + r * 128;
 #pragma unroll
-            for (int c16 = 0; c16 < 8; ++c16) {
+            for (int j = 0; j < 4; ++j) {
+                const int c16 = 4 * hf + ((j + 2 * hf) & 3);
                 const uint4 v = src[c16 ^ (r & 7)];   // the raw tile is 128-byte swizzled too
                 const uint32_t w[4] = {v.x ^ 0x80808080u, v.y ^ 0x80808080u, v.z ^ 0x80808080u,
                                        v.w ^ 0x80808080u};
@@ -328,7 +338,7 @@ __global__ void __launch_bounds__(256, 1) gram_i8_kernel(const __grid_constant__
             }
             fence_proxy_async_smem();
             converters_sync();
-            if (r == 0) {
+            if (cv == 0) {
                 mbar_arrive(&sh->conv_full[c]);
                 mbar_arrive(&sh->raw_empty[s]);
             }
@@ -409,7 +419,7 @@ int launch_gram(const GramArgs& a, cudaStream_t st) {
                 return CORR_ECUDA;
             attr8 = true;
         }
-        gram_i8_kernel<<<a.n_chan, 256, smem, st>>>(map, a);
+        gram_i8_kernel<<<a.n_chan, 128 + kConvThreads, smem, st>>>(map, a);
         return CORR_OK;
     }
     const int eb = a.fp8 ? 1 : 2;

@@ -37,11 +37,13 @@ __device__ __forceinline__ uint16_t code_bf16(uint8_t q) {
 // CODE: 0 int8 carried as BF16 (2 bytes), 1 e4m3 byte, 2 int8 byte, 3 the
 // F-engine's code words already made ([slot][pair][n_chan] 32-bit words,
 // bytes Re a, Im a, Re a+1, Im a+1): a transpose into Q only.
-template <int CODE>
+// RUN spectra per thread: 32 / EB, or 64 for the transpose (two whole
+// sectors a row).
+template <int CODE, int RUN = (CODE == 3 ? 64 : (CODE == 0 ? 16 : 32))>
 __global__ void __launch_bounds__(128) requant_pm_kernel(const RequantArgs A) {
     constexpr bool FP8 = CODE == 1;
     constexpr int EB = CODE == 0 ? 2 : 1;
-    constexpr int RUN = 32 / EB;
+    constexpr int NW = RUN * EB / 4;        // 32-bit words of codes per row
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int pr = blockIdx.y;
     if (k >= A.n_chan) return;
@@ -55,11 +57,11 @@ __global__ void __launch_bounds__(128) requant_pm_kernel(const RequantArgs A) {
     const float* inv = A.scale + (size_t)A.n_in_pad * A.n_chan;
     const float inv0 = (CODE != 3 && a0 < N) ? inv[(size_t)a0 * A.n_chan + k] : 0.f;
     const float inv1 = (CODE != 3 && a1 < N) ? inv[(size_t)a1 * A.n_chan + k] : 0.f;
-    uint32_t w[4][8];                 // rows Re a0, Im a0, Re a1, Im a1
+    uint32_t w[4][NW];                // rows Re a0, Im a0, Re a1, Im a1
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) w[r][j] = 0u;
+        for (int j = 0; j < NW; ++j) w[r][j] = 0u;
     if constexpr (CODE == 3) {
         const uint32_t* C = reinterpret_cast<const uint32_t*>(A.V);
 #pragma unroll
@@ -98,14 +100,16 @@ __global__ void __launch_bounds__(128) requant_pm_kernel(const RequantArgs A) {
         uint8_t* dst = A.Q + ((size_t)k * 128 + row) * A.k_pitch + col * EB;
         if (ns == RUN && ((col * EB) & 15) == 0) {
             uint4* d = reinterpret_cast<uint4*>(dst);
-            d[0] = make_uint4(w[r][0], w[r][1], w[r][2], w[r][3]);
-            d[1] = make_uint4(w[r][4], w[r][5], w[r][6], w[r][7]);
+#pragma unroll
+            for (int v = 0; v < NW / 4; ++v) d[v] = make_uint4(w[r][4 * v], w[r][4 * v + 1], w[r][4 * v + 2], w[r][4 * v + 3]);
         } else {
-            for (int i = 0; i < ns; ++i)
-                for (int e = 0; e < EB; ++e) {
-                    const int bitpos = 8 * (i * EB + e);
-                    dst[i * EB + e] = (uint8_t)(w[r][bitpos / 32] >> (bitpos % 32));
-                }
+            // ragged run: byte by byte, every index of w a compile-time
+            // constant (w stays in registers)
+#pragma unroll
+            for (int j = 0; j < NW; ++j)
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (4 * j + e < ns * EB) dst[4 * j + e] = (uint8_t)(w[r][j] >> (8 * e));
         }
     }
 }
@@ -179,7 +183,7 @@ __global__ void finalize_q_kernel(const FinQArgs F) {
 void launch_requant(const RequantArgs& a, cudaStream_t st) {
     const long long n = a.s_end - a.s_begin;
     if (n <= 0) return;
-    const int run = (a.fp8 || a.i8b || a.codes_in) ? 32 : 16;
+    const int run = a.codes_in ? 64 : (a.fp8 || a.i8b) ? 32 : 16;
     dim3 grid((unsigned)((a.n_chan + 127) / 128), (unsigned)(a.n_in_pad / 2), (unsigned)((n + run - 1) / run));
     if (a.codes_in) requant_pm_kernel<3><<<grid, 128, 0, st>>>(a);
     else if (a.fp8) requant_pm_kernel<1><<<grid, 128, 0, st>>>(a);
