@@ -253,36 +253,46 @@ __global__ void __launch_bounds__(128) finalize_kernel(const FinArgs F) {
 constexpr int kFlagWarps = 4;
 
 template <int E>
-__device__ __forceinline__ void warp_bitonic_sort(float (&v)[E], int lane) {
-    constexpr int n = 32 * E;
+__device__ __forceinline__ void warp_bitonic_stage(float (&v)[E], int lane, int k) {
+    // merge step of size k: element i pairs with i ^ j, ascending where i & k == 0
 #pragma unroll
-    for (int k = 2; k <= n; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+        if (j < E) {
 #pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j < E) {
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const int ep = e ^ j;
-                    if (ep > e) {
-                        const int i = lane * E + e;
-                        const bool asc = (i & k) == 0;
-                        const float lo = fminf(v[e], v[ep]), hi = fmaxf(v[e], v[ep]);
-                        v[e] = asc ? lo : hi;
-                        v[ep] = asc ? hi : lo;
-                    }
-                }
-            } else {
-                const int lm = j / E;                  // partner lane distance
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const float o = __shfl_xor_sync(0xffffffffu, v[e], lm);
+            for (int e = 0; e < E; ++e) {
+                const int ep = e ^ j;
+                if (ep > e) {
                     const int i = lane * E + e;
-                    const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
-                    v[e] = keep_min ? fminf(v[e], o) : fmaxf(v[e], o);
+                    const bool asc = (i & k) == 0;
+                    const float lo = fminf(v[e], v[ep]), hi = fmaxf(v[e], v[ep]);
+                    v[e] = asc ? lo : hi;
+                    v[ep] = asc ? hi : lo;
                 }
+            }
+        } else {
+            const int lm = j / E;                  // partner lane distance
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const float o = __shfl_xor_sync(0xffffffffu, v[e], lm);
+                const int i = lane * E + e;
+                const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
+                v[e] = keep_min ? fminf(v[e], o) : fmaxf(v[e], o);
             }
         }
     }
+}
+
+template <int E>
+__device__ __forceinline__ void warp_bitonic_sort(float (&v)[E], int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32 * E; k <<= 1) warp_bitonic_stage<E>(v, lane, k);
+}
+
+// Sort a bitonic sequence (non-increasing, then non-decreasing) ascending:
+// the last merge step of the sort alone.
+template <int E>
+__device__ __forceinline__ void warp_bitonic_merge(float (&v)[E], int lane) {
+    warp_bitonic_stage<E>(v, lane, 32 * E);
 }
 
 // Element i of a sorted warp array (i uniform over the warp).
@@ -330,9 +340,12 @@ __device__ __forceinline__ void mad_flag_item(const float2* R, uint8_t* F, int n
     }
     warp_bitonic_sort<E>(v, lane);
     const float med = warp_sorted_median<E>(v, W);
+    // |A - med| in the sorted order falls to the median and rises after it
+    // (the +inf padding stays last): a bitonic sequence, which one merge
+    // sorts -- the same values as sorting |A - med| from scratch
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = (lane * E + e < W) ? fabsf(A[e] - med) : __int_as_float(0x7f800000);
-    warp_bitonic_sort<E>(v, lane);
+    for (int e = 0; e < E; ++e) v[e] = fabsf(v[e] - med);
+    warp_bitonic_merge<E>(v, lane);
     const float mad = warp_sorted_median<E>(v, W);
     const float T = med + sigma * mad * 1.4826f;
 #pragma unroll
