@@ -62,7 +62,7 @@ enum {
 enum { CORR_FP32 = 0, CORR_INT8 = 1, CORR_FP8 = 2 };
 /* Code layout of corr_gram_dev beside CORR_INT8 (int8 carried as BF16) and
  * CORR_FP8: int8 codes stored as bytes. */
-enum { CORR_INT8_BYTES = 3 };
+enum { CORR_INT8_BYTES = 3, CORR_INT8_WORDS = 4 };
 
 /*
  * corr_create -- allocate a correlator.
@@ -270,8 +270,17 @@ int corr_flag_dev(corr_t h, const float* d_vis, int n_vis, uint8_t* d_flags, voi
  *                    partial sum stays below 2^24).
  *   dtype CORR_FP8:  e4m3 bytes; FP32 sums.
  *   dtype CORR_INT8_BYTES: int8 codes as bytes (1 byte each), widened to
- *                    BF16 on chip (exact), then as CORR_INT8; this is the
- *                    form the int8 pipeline uses.
+ *                    BF16 on chip (exact), then as CORR_INT8.
+ *   dtype CORR_INT8_WORDS: the form the int8 pipeline uses -- d_Q holds code
+ *                    words [K][n_pairs][n_chan] uint32, n_pairs = n_in_pad /
+ *                    2 (the handle's n_in rounded up to a multiple of 4;
+ *                    words of pairs past the last input are ignored), the
+ *                    bytes of word
+ *                    (t, p, c) being the codes of Re V_2p, Im V_2p, Re
+ *                    V_2p+1, Im V_2p+1 (low byte first); rows as above (row
+ *                    a = Re of input a, row n_in + a = Im; rows from 2 n_in
+ *                    up unspecified); k_pitch is ignored, n_chan must be a
+ *                    multiple of 4 and n_in <= 64.
  * d_G: [n_chan][128][128] FP32.  k_pitch must be a multiple of 128 and d_Q
  * 16-byte aligned (else CORR_EINVAL).  Runs on tcgen05 tensor cores with
  * TMA-staged operands; a stalled pipeline sets the status word read by

@@ -176,6 +176,9 @@ struct GramArgs {
     unsigned long long wait_ns;   // limit of each bounded wait (0: the 2 s default)
     int inject_stall;             // fault injection: the producer issues no loads
     int i8b;                      // int8 codes stored as bytes (widened to BF16 on chip)
+    // int8 code words C[t][pair][k] (Q points at them; K spectra, n_pairs
+    // pairs of n_in inputs): Gram straight from the F-engine's words
+    int words, n_pairs, n_in;
 };
 
 // Requantise spectra [s_begin, s_end) of the pair-major ring V (U = 2Y,
@@ -195,6 +198,7 @@ struct RequantArgs {
     int pair_major;          // V pair-major ([slot][pair][n_chan] float4); always set
     int i8b;                 // int8 codes as bytes (else carried as BF16)
     int codes_in;            // V holds the F-engine's code words ([slot][pair][n_chan] uint32): transpose only
+    uint32_t* C;             // set: int8 code words C[t][pair][n_chan] out instead of Q (t = s - int_start)
 };
 
 // R[k][a][b] = scale_a scale_b / (4 count) rot_a conj(rot_b) sum q_a conj(q_b),

@@ -371,6 +371,197 @@ __global__ void __launch_bounds__(128 + kConvThreads, 1) gram_i8_kernel(const __
     }
 }
 
+// ---- int8 codes as the F-engine's code words ---------------------------------
+// The Gram matrices of an integration straight from the pair-major code
+// words C[t][pair][k] (bytes Re U_a, Im U_a, Re U_a+1, Im U_a+1 of input
+// pair (a, a+1), a = 2 pair), with no transpose into row-major codes first.
+// One CTA per four channels (their four 128 x 128 FP32 accumulators fill
+// TMEM's 512 columns), 384 threads: warp 0 lane 0 loads raw boxes of 4
+// channels x 32 pairs x 64 spectra (16 contiguous bytes per pair and
+// spectrum; pairs past the last read as zero) by 3D TMA; warps 4-11 widen
+// them into each channel's BF16 operand tile (Re of input a at row a, Im at
+// row N + a; 64 K-elements per 128-byte swizzled row, chunk q of row r at
+// (q ^ (r & 7)) x 16) and signal the MMA issuer (warp 1 lane 0); warps 0-3
+// read the accumulators out.  Rows from 2N up are never written: they meet
+// only Gram entries no visibility uses.
+constexpr int kWRawStages = 3;
+constexpr int kWConvStages = 2;
+constexpr int kWChan = 4;                                   // channels per CTA
+constexpr int kWK = 64;                                     // spectra per stage
+constexpr int kWPairs = 32;                                 // pairs per box
+constexpr int kWRawBytes = kWK * kWPairs * kWChan * 4;      // 32 KiB
+constexpr int kWTileBytes = kRows * 128;                    // one channel's BF16 tile, 16 KiB
+constexpr int kWConvBytes = kWChan * kWTileBytes;           // 64 KiB
+constexpr uint32_t kWTmemCols = kWChan * 128;               // 512
+struct __align__(8) GramWShared {
+    uint64_t raw_full[kWRawStages];
+    uint64_t raw_empty[kWRawStages];
+    uint64_t conv_full[kWConvStages];
+    uint64_t conv_empty[kWConvStages];
+    uint64_t accum;
+    uint32_t tmem_addr;
+    int abort;
+};
+
+__global__ void __launch_bounds__(128 + kConvThreads, 1) gram_w_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                       GramArgs A) {
+    extern __shared__ __align__(1024) uint8_t gsm_raw[];
+    uint8_t* conv = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* raw = conv + kWConvStages * kWConvBytes;
+    GramWShared* sh = reinterpret_cast<GramWShared*>(raw + kWRawStages * kWRawBytes);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int quad = blockIdx.x;
+    const int num_k = (A.K + kWK - 1) / kWK;
+    const unsigned long long lim = A.wait_ns ? A.wait_ns : kWaitNs;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kWRawStages; ++s) {
+            mbar_init(&sh->raw_full[s], 1);
+            mbar_init(&sh->raw_empty[s], 1);
+        }
+        for (int c = 0; c < kWConvStages; ++c) {
+            mbar_init(&sh->conv_full[c], 1);
+            mbar_init(&sh->conv_empty[c], 1);
+        }
+        mbar_init(&sh->accum, 1);
+        sh->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&sh->tmem_addr)),
+                     "r"(kWTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = sh->tmem_addr;
+    int issued = 0;   // TMA loads issued (producer thread)
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer of raw code-word boxes (with inject_stall it issues nothing)
+        for (int it = 0; it < (A.inject_stall ? 0 : num_k); ++it) {
+            const int s = it % kWRawStages;
+            const uint32_t ph = (uint32_t)(it / kWRawStages) & 1u;
+            if (!mbar_wait(&sh->raw_empty[s], ph ^ 1u, lim)) {
+                sh->abort = 1;
+                break;
+            }
+            mbar_expect_tx(&sh->raw_full[s], kWRawBytes);
+            // x: channel 4 quad (16-byte aligned), y: pair 0, z: spectrum
+            tma_load_3d(raw + s * kWRawBytes, &tmap, &sh->raw_full[s], kWChan * quad, 0, it * kWK);
+            issued = it + 1;
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: per stage and channel, four K = 16 steps over its tile
+        bool ok = true;
+        for (int it = 0; it < num_k && ok; ++it) {
+            const int c = it % kWConvStages;
+            const uint32_t ph = (uint32_t)(it / kWConvStages) & 1u;
+            if (!mbar_wait(&sh->conv_full[c], ph, lim)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int ch = 0; ch < kWChan; ++ch) {
+                const uint64_t d0 = sdesc(smem_u32(conv + c * kWConvBytes + ch * kWTileBytes));
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint64_t d = d0 + (uint64_t)((kk * 32) >> 4);
+                    mma<false>(tmem + (uint32_t)(ch * 128), d, d, (it | kk) != 0 ? 1u : 0u);
+                }
+            }
+            mma_commit(&sh->conv_empty[c]);
+        }
+        if (!ok) sh->abort = 1;
+        mma_commit(&sh->accum);
+    } else if (warp >= 4) {
+        // converters: thread (ch, p, half) widens the four rows of input pair
+        // p in channel ch for the spectrum blocks of its parity (8 spectra a
+        // block), visited in an order rotated by channel so lanes of one
+        // store phase write different chunks
+        const int cv = (int)threadIdx.x - 128;
+        const int ch = cv & 3, p = (cv >> 2) & 31, tb0 = cv >> 7;
+        const int N = A.n_in;
+        int row[4];
+        bool has[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int a = 2 * p + (b >> 1);
+            has[b] = a < N;
+            row[b] = (b & 1) ? N + a : a;
+        }
+        for (int it = 0; it < num_k; ++it) {
+            const int s = it % kWRawStages, c = it % kWConvStages;
+            bool ok = mbar_wait(&sh->raw_full[s], (uint32_t)(it / kWRawStages) & 1u, lim);
+            ok = ok && mbar_wait(&sh->conv_empty[c], ((uint32_t)(it / kWConvStages) & 1u) ^ 1u, lim);
+            if (!converters_all(ok)) {
+                if (cv == 0) sh->abort = 1;
+                break;
+            }
+            const uint32_t* rw = reinterpret_cast<const uint32_t*>(raw + s * kWRawBytes);
+            uint8_t* tile = conv + c * kWConvBytes + ch * kWTileBytes;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int tb = (tb0 + 2 * k + 2 * ch) & 7;
+                uint32_t w[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) w[i] = rw[((tb * 8 + i) * kWPairs + p) * kWChan + ch];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    if (!has[b]) continue;
+                    uint32_t o[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        // byte b of spectra 2q and 2q + 1 -> low, high BF16
+                        const uint32_t x = __byte_perm(w[2 * q], w[2 * q + 1], (uint32_t)(b | ((4 + b) << 4)));
+                        o[q] = bf16x2_of_codes(x ^ 0x80808080u, 0);
+                    }
+                    *reinterpret_cast<uint4*>(tile + row[b] * 128 + ((tb ^ (row[b] & 7)) << 4)) =
+                        make_uint4(o[0], o[1], o[2], o[3]);
+                }
+            }
+            fence_proxy_async_smem();
+            converters_sync();
+            if (cv == 0) {
+                mbar_arrive(&sh->conv_full[c]);
+                mbar_arrive(&sh->raw_empty[s]);
+            }
+        }
+    }
+    __syncwarp();
+    if (!mbar_wait(&sh->accum, 0, lim)) sh->abort = 1;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (sh->abort) {
+        if (threadIdx.x == 0 && A.status) atomicExch(A.status, CORR_ETIMEDOUT);
+        if (warp == 0 && lane == 0) drain_loads(sh->raw_full, kWRawStages, issued, lim);
+    } else if (warp < 4) {
+        const int r = warp * 32 + lane;
+#pragma unroll 1
+        for (int ch = 0; ch < kWChan; ++ch) {
+            uint32_t* G = reinterpret_cast<uint32_t*>(A.G) + ((size_t)(kWChan * quad + ch) * kRows + r) * kRows;
+#pragma unroll
+            for (int c0 = 0; c0 < kRows; c0 += 32) {
+                uint32_t rr[32];
+                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 128 + c0), rr);
+                uint4* o = reinterpret_cast<uint4*>(G + c0);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) o[i] = make_uint4(rr[4 * i], rr[4 * i + 1], rr[4 * i + 2], rr[4 * i + 3]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWTmemCols)
+                     : "memory");
+    }
+}
+
 }  // namespace
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -388,12 +579,44 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 size_t gram_smem_bytes() { return (size_t)kStages * kStageBytes + sizeof(GramShared) + 1024; }
 
+size_t gram_w_smem_bytes() {
+    return (size_t)kWConvStages * kWConvBytes + (size_t)kWRawStages * kWRawBytes + sizeof(GramWShared) + 1024;
+}
+
 size_t gram_i8_smem_bytes() {
     return (size_t)kConvStages * kConvBytes + (size_t)kRawStages * kRawBytes + sizeof(GramI8Shared) + 1024;
 }
 
 int launch_gram(const GramArgs& a, cudaStream_t st) {
     if (a.n_chan <= 0 || a.K <= 0) return CORR_OK;
+    if (a.words) {
+        // code words C[t][pair][k]: 3D map (k, pair, t) of 32-bit words
+        if (a.fp8 || (a.n_chan % kWChan) != 0 || a.n_pairs < 1 || a.n_pairs > kWPairs || a.n_in < 1 ||
+            a.n_in > 2 * a.n_pairs)
+            return CORR_EINVAL;
+        if ((reinterpret_cast<uintptr_t>(a.Q) & 15) != 0) return CORR_EINVAL;
+        PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+        if (!enc) return CORR_ECUDA;
+        CUtensorMap map;
+        cuuint64_t dims[3] = {(cuuint64_t)a.n_chan, (cuuint64_t)a.n_pairs, (cuuint64_t)a.K};
+        cuuint64_t strides[2] = {(cuuint64_t)a.n_chan * 4, (cuuint64_t)a.n_pairs * a.n_chan * 4};
+        cuuint32_t box[3] = {(cuuint32_t)kWChan, (cuuint32_t)kWPairs, (cuuint32_t)kWK};
+        cuuint32_t estr[3] = {1, 1, 1};
+        CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, const_cast<void*>(a.Q), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return CORR_EINVAL;
+        const size_t smem = gram_w_smem_bytes();
+        static bool attrw = false;
+        if (!attrw) {
+            if (cudaFuncSetAttribute(gram_w_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess)
+                return CORR_ECUDA;
+            attrw = true;
+        }
+        gram_w_kernel<<<a.n_chan / kWChan, 128 + kConvThreads, smem, st>>>(map, a);
+        return CORR_OK;
+    }
     if (a.i8b) {
         // int8 codes as bytes: raw tiles of 128 codes x 128 rows, 128-byte
         // swizzle (16-byte chunk q of row r at r * 128 + ((q ^ (r & 7)) << 4)),

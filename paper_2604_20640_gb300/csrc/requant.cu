@@ -114,6 +114,29 @@ __global__ void __launch_bounds__(128) requant_pm_kernel(const RequantArgs A) {
     }
 }
 
+// Spectra of the pair-major ring into int8 code words C[t][pair][k] (bytes
+// Re U_a, Im U_a, Re U_a+1, Im U_a+1; t = s - int_start): the words the
+// fused F-engine writes once the scales are fixed, made here from the
+// spectra it wrote before (same arithmetic, same codes).  One thread per
+// (channel, pair, spectrum).
+__global__ void __launch_bounds__(128) words_from_spectra_kernel(const RequantArgs A) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int pr = blockIdx.y;
+    const long long s = A.s_begin + blockIdx.z;
+    if (k >= A.n_chan || s >= A.s_end) return;
+    const int N = A.n_in;
+    const int a0 = 2 * pr, a1 = 2 * pr + 1;
+    const int n_pairs = A.n_in_pad >> 1;
+    const float* inv = A.scale + (size_t)A.n_in_pad * A.n_chan;
+    const float inv0 = a0 < N ? inv[(size_t)a0 * A.n_chan + k] : 0.f;
+    const float inv1 = a1 < N ? inv[(size_t)a1 * A.n_chan + k] : 0.f;
+    const long long slot = (s - A.v_origin) & A.v_mask;
+    const float4 u = __ldg(reinterpret_cast<const float4*>(A.V) + ((size_t)slot * n_pairs + pr) * A.n_chan + k);
+    const uint32_t w = q_code<false>(u.x * inv0) | (q_code<false>(u.y * inv0) << 8) |
+                       (q_code<false>(u.z * inv1) << 16) | (q_code<false>(u.w * inv1) << 24);
+    A.C[((size_t)(s - A.int_start) * n_pairs + pr) * A.n_chan + k] = w;
+}
+
 __global__ void scale_ring_kernel(const float2* V, long long v_origin, long long v_mask, long long s0, int n,
                                   int n_in, int n_in_pad, int n_chan, float gain, float* scale, int pm) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -183,6 +206,11 @@ __global__ void finalize_q_kernel(const FinQArgs F) {
 void launch_requant(const RequantArgs& a, cudaStream_t st) {
     const long long n = a.s_end - a.s_begin;
     if (n <= 0) return;
+    if (a.C) {
+        dim3 grid((unsigned)((a.n_chan + 127) / 128), (unsigned)(a.n_in_pad / 2), (unsigned)n);
+        words_from_spectra_kernel<<<grid, 128, 0, st>>>(a);
+        return;
+    }
     const int run = a.codes_in ? 64 : (a.fp8 || a.i8b) ? 32 : 16;
     dim3 grid((unsigned)((a.n_chan + 127) / 128), (unsigned)(a.n_in_pad / 2), (unsigned)((n + run - 1) / run));
     if (a.codes_in) requant_pm_kernel<3><<<grid, 128, 0, st>>>(a);

@@ -43,6 +43,10 @@ struct Pipe {
     float* scale = nullptr;   // [n_in_pad][n_chan], fixed per integration
     bool have_scale = false;  // false until the first integration's pre-pass
     bool ring_codes = false;  // the unrequantised ring slots hold the F-engine's code words
+    // int8: the integration's code words C[t][pair][n_chan] (bytes Re a, Im a,
+    // Re a+1, Im a+1), read by the Gram kernel directly (no Q)
+    uint32_t* C = nullptr;
+    bool words = false;
 };
 
 struct Slot {
@@ -406,12 +410,19 @@ int alloc_pipe_impl(corr_t h, Pipe& p) {
     CKA(dmalloc(h, &p.V, per_spec * (size_t)p.v_cap));
     CKA(dmalloc(h, &p.Z, per_spec * (size_t)p.v_cap));
     if (h->precision != CORR_FP32) {
-        // one byte per code: e4m3, or int8 widened to BF16 by the Gram kernel
-        const int eb = 1;
-        p.q_pitch = (int)((((long long)h->n_int * eb) + 127) / 128 * 128);
-        const size_t qbytes = (size_t)h->n_chan * 128 * p.q_pitch;
-        CKA(dmalloc(h, &p.Q, qbytes));
-        CK(cudaMemset(p.Q, 0, qbytes));
+        p.words = h->precision == CORR_INT8 && (h->n_chan % 4) == 0;
+        if (p.words) {
+            // int8: one 32-bit word of four codes per (spectrum, pair, channel)
+            const size_t cbytes = sizeof(uint32_t) * (size_t)h->n_int * (h->n_in_pad / 2) * h->n_chan;
+            CKA(dmalloc(h, &p.C, cbytes));
+            CK(cudaMemset(p.C, 0, cbytes));
+        } else {
+            // e4m3: one byte per code, rows of K
+            p.q_pitch = (int)(((long long)h->n_int + 127) / 128 * 128);
+            const size_t qbytes = (size_t)h->n_chan * 128 * p.q_pitch;
+            CKA(dmalloc(h, &p.Q, qbytes));
+            CK(cudaMemset(p.Q, 0, qbytes));
+        }
         CKA(dmalloc(h, &p.G, sizeof(float) * (size_t)h->n_chan * 128 * 128));
         // scales, then their inverses (the requantiser's multipliers)
         CKA(dmalloc(h, &p.scale, 2 * sizeof(float) * (size_t)h->n_in_pad * h->n_chan));
@@ -578,8 +589,16 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
             // requantises in its epilogue (the requantiser's arithmetic) and
             // writes 4-byte code words instead of 16-byte spectra; the
             // requantiser below then only transposes them into Q
-            p.ring_codes = p.have_scale && p.s_xdone == p.s_next && fused_codes(h, sv);
-            if (p.ring_codes) {
+            const bool codes = p.have_scale && p.s_xdone == p.s_next && fused_codes(h, sv);
+            p.ring_codes = codes && !p.words;
+            if (codes && p.words) {
+                // int8: the words go straight into the integration's C at
+                // t = s - istart, where the Gram kernel reads them
+                const CodeOut q{p.scale + (size_t)h->n_in_pad * h->n_chan, false};
+                CKRET(launch_f(h, sv, t, p.Z, 0, p.v_cap - 1, reinterpret_cast<float2*>(p.C), istart, -1LL,
+                               nullptr, p.s_next, s_end, st, nullptr, 0, 0, &q));
+                p.s_xdone = s_end;
+            } else if (codes) {
                 const CodeOut q{p.scale + (size_t)h->n_in_pad * h->n_chan, h->precision == CORR_FP8};
                 CKRET(launch_f(h, sv, t, p.Z, 0, p.v_cap - 1, p.V, 0, p.v_cap - 1, nullptr, p.s_next, s_end, st,
                                nullptr, 0, 0, &q));
@@ -627,6 +646,7 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
                 r.pair_major = pair_major_ring(h);
                 r.i8b = h->precision == CORR_INT8;
                 r.codes_in = p.ring_codes;
+                r.C = p.words ? p.C : nullptr;
                 {
                     Timed t_(h, 5, st);
                     launch_requant(r, st);
@@ -693,7 +713,10 @@ int finalize_into(corr_t h, Pipe& p, const Tables& t, float2* R, uint8_t* F, int
         // Tensor-core Gram of the integration's codes, then rescale and
         // rotate; the autocorrelations fix the next integration's scales.
         GramArgs g{};
-        g.Q = p.Q;
+        g.Q = p.words ? static_cast<const void*>(p.C) : static_cast<const void*>(p.Q);
+        g.words = p.words;
+        g.n_pairs = h->n_in_pad / 2;
+        g.n_in = h->n_in;
         g.n_chan = h->n_chan;
         g.K = count;
         g.k_pitch = p.q_pitch;
@@ -1029,6 +1052,7 @@ void free_pipe(Pipe& p) {
     if (p.V) cudaFree(p.V);
     if (p.Z) cudaFree(p.Z);
     if (p.Q) cudaFree(p.Q);
+    if (p.C) cudaFree(p.C);
     if (p.G) cudaFree(p.G);
     if (p.scale) cudaFree(p.scale);
     if (p.part) cudaFree(p.part);
@@ -1507,7 +1531,8 @@ long long corr_kernel_launches(corr_t h) { return h ? h->launches : 0; }
 int corr_gram_dev(corr_t h, const void* d_Q, int n_chan, int k_pitch, int K, int dtype, float* d_G, void* stream) {
     if (!h) return fail(h, CORR_EINVAL, "NULL handle");
     DeviceGuard g(h->dev);
-    if (!d_Q || !d_G || n_chan < 1 || K < 1 || (dtype != CORR_INT8 && dtype != CORR_FP8 && dtype != CORR_INT8_BYTES))
+    if (!d_Q || !d_G || n_chan < 1 || K < 1 ||
+        (dtype != CORR_INT8 && dtype != CORR_FP8 && dtype != CORR_INT8_BYTES && dtype != CORR_INT8_WORDS))
         return fail(h, CORR_EINVAL, "bad argument");
     GramArgs a{};
     a.Q = d_Q;
@@ -1516,6 +1541,9 @@ int corr_gram_dev(corr_t h, const void* d_Q, int n_chan, int k_pitch, int K, int
     a.k_pitch = k_pitch;
     a.fp8 = dtype == CORR_FP8;
     a.i8b = dtype == CORR_INT8_BYTES;
+    a.words = dtype == CORR_INT8_WORDS;
+    a.n_pairs = h->n_in_pad / 2;
+    a.n_in = h->n_in;
     a.G = d_G;
     a.status = h->d_status;
     a.wait_ns = (unsigned long long)(h->tc_wait_ms * 1e6);
@@ -1525,7 +1553,9 @@ int corr_gram_dev(corr_t h, const void* d_Q, int n_chan, int k_pitch, int K, int
         Timed t_(h, 2, static_cast<cudaStream_t>(stream));
         rc = launch_gram(a, static_cast<cudaStream_t>(stream));
     }
-    if (rc != CORR_OK) return fail(h, rc, "gram: bad layout (k_pitch multiple of 128 bytes, 16-byte aligned Q)");
+    if (rc != CORR_OK)
+        return fail(h, rc, "gram: bad layout (k_pitch multiple of 128 bytes, 16-byte aligned Q; words: n_chan "
+                           "multiple of 4, n_in <= 64)");
     CK(cudaGetLastError());
     return CORR_OK;
 }
@@ -1997,8 +2027,13 @@ int corr_save_state(corr_t h, void* buf, size_t cap, size_t* size) {
             CKRET(put_dev(h->ps.part, sizeof(float) * (size_t)h->gpi * h->nt * 32 * h->n_chan));
         } else {
             CKRET(put_dev(h->ps.scale, 2 * sizeof(float) * (size_t)h->n_in_pad * h->n_chan));
-            for (size_t r = 0; r < (size_t)h->n_chan * 128 && H.q_cols > 0; ++r)
-                CKRET(put_dev(h->ps.Q + r * h->ps.q_pitch, (size_t)H.q_cols));
+            if (h->ps.words) {
+                if (H.q_cols > 0)
+                    CKRET(put_dev(h->ps.C, sizeof(uint32_t) * (size_t)H.q_cols * (h->n_in_pad / 2) * h->n_chan));
+            } else {
+                for (size_t r = 0; r < (size_t)h->n_chan * 128 && H.q_cols > 0; ++r)
+                    CKRET(put_dev(h->ps.Q + r * h->ps.q_pitch, (size_t)H.q_cols));
+            }
         }
     }
     for (int idx : h->q_vis) w.put(h->slots[idx].h_R, ne * sizeof(float2));
@@ -2064,8 +2099,13 @@ int corr_load_state(corr_t h, const void* buf, size_t size) {
             CKRET(get_dev(h->ps.part, sizeof(float) * (size_t)h->gpi * h->nt * 32 * h->n_chan));
         } else {
             CKRET(get_dev(h->ps.scale, 2 * sizeof(float) * (size_t)h->n_in_pad * h->n_chan));
-            for (size_t r = 0; r < (size_t)h->n_chan * 128 && H.q_cols > 0; ++r)
-                CKRET(get_dev(h->ps.Q + r * h->ps.q_pitch, (size_t)H.q_cols));
+            if (h->ps.words) {
+                if (H.q_cols > 0)
+                    CKRET(get_dev(h->ps.C, sizeof(uint32_t) * (size_t)H.q_cols * (h->n_in_pad / 2) * h->n_chan));
+            } else {
+                for (size_t r = 0; r < (size_t)h->n_chan * 128 && H.q_cols > 0; ++r)
+                    CKRET(get_dev(h->ps.Q + r * h->ps.q_pitch, (size_t)H.q_cols));
+            }
         }
         h->stage_base = H.stage_base;
         h->stage_len = H.stage_len;

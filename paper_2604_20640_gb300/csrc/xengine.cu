@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(128) xengine_kernel(const XArgs X) {
 // four spectra in flight a thread instead of one.
 constexpr int kXsChan = 16;       // channels per warp
 constexpr int kXsSub = 2;         // sub-groups per channel
-constexpr int kXsDepth = 4;       // spectra in flight per thread
+constexpr int kXsDepth = 6;       // spectra in flight per thread (48 KiB a CTA at n_in 8)
 
 __device__ __forceinline__ void xs_cp16(float4* dst, const float4* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");

@@ -124,3 +124,48 @@ def test_int8_byte_gram_long_sums_within_fp32_bound():
     ref = rq.gram(codes).astype(np.float64)
     bound = K * 2.0 ** -24 * np.einsum('crk,csk->crs', np.abs(codes).astype(np.float64), np.abs(codes).astype(np.float64))
     assert np.all(np.abs(G - ref) <= bound)
+
+
+def _words(q_re, q_im):
+    """Code words [K][n_pairs][n_chan] uint32 from codes q_re, q_im [N][K][n_chan]:
+    bytes Re V_2p, Im V_2p, Re V_2p+1, Im V_2p+1 (low byte first); the bytes
+    of inputs past N are zero."""
+    N, K, n_chan = q_re.shape
+    n_pairs = (N + 3) // 4 * 2          # n_in padded to a multiple of 4, in pairs
+    b = np.zeros((K, n_pairs, n_chan, 4), np.int64)
+    for a in range(N):
+        b[:, a // 2, :, 2 * (a % 2)] = q_re[a]
+        b[:, a // 2, :, 2 * (a % 2) + 1] = q_im[a]
+    u = (b & 0xFF).astype(np.uint32)
+    return u[..., 0] | (u[..., 1] << 8) | (u[..., 2] << 16) | (u[..., 3] << 24)
+
+
+@pytest.mark.parametrize("n_in,n_chan,K", [(64, 8, 1024), (20, 12, 100), (7, 4, 64), (64, 1024, 320), (33, 16, 1)])
+def test_int8_word_gram_bit_exact(n_in, n_chan, K):
+    """The int8 pipeline's form: the Gram kernel reads the F-engine's code
+    words [K][pair][channel] directly (four channels a CTA, raw boxes of 64
+    spectra by 3D TMA, widened to BF16 in rows Re a = a, Im a = N + a);
+    exact products and FP32 sums up to K = 1024 -> bit-exact on the 2N x 2N
+    block the visibilities use (ragged K, odd N, one spectrum)."""
+    from paper_2604_20640_gb300 import Correlator, CORR_INT8_WORDS
+    rng = np.random.default_rng(n_in * 1000 + n_chan + K)
+    q_re = rng.integers(-127, 128, size=(n_in, K, n_chan)).astype(np.int64)
+    q_im = rng.integers(-127, 128, size=(n_in, K, n_chan)).astype(np.int64)
+    W = _words(q_re, q_im)
+    c = Correlator(n_in, 1, 64, 4, 16)
+    G = _run_gram(c, W.view(np.uint8).reshape(-1), n_chan, 0, K, CORR_INT8_WORDS)
+    c.close()
+    ref = rq.gram(rq.stacked_rows(q_re, q_im))
+    n2 = 2 * n_in
+    np.testing.assert_array_equal(G[:, :n2, :n2], ref[:, :n2, :n2].astype(np.float64))
+
+
+def test_int8_word_gram_rejects_bad_layout():
+    from paper_2604_20640_gb300 import Correlator, CorrError, CORR_EINVAL, CORR_INT8_WORDS
+    c = Correlator(8, 1, 64, 4, 16)
+    W = torch.zeros(64 * 4 * 6, dtype=torch.uint32 if hasattr(torch, "uint32") else torch.int32, device=DEV)
+    G = torch.empty((6, 128, 128), device=DEV)
+    with pytest.raises(CorrError) as e:
+        c.gram_dev(W, 6, 0, 64, CORR_INT8_WORDS, G)             # n_chan not a multiple of 4
+    assert e.value.code == CORR_EINVAL
+    c.close()
