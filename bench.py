@@ -59,7 +59,7 @@ WORKLOADS = {
 STAGES = ["fir", "fft", "xengine", "finalize", "flag", "requant", "gram"]
 KERNELS = {"fir": "fir_kernel<4>", "fft": "fft_kernel<M,3>", "xengine": "xengine_kernel",
            "finalize": "finalize_kernel", "flag": "mad_flag_kernel", "requant": "requant_pm_kernel",
-           "gram": "gram_i8_kernel (tcgen05, int8 bytes widened on chip)"}
+           "gram": "gram_w_kernel (tcgen05, int8 code words widened on chip)"}
 # Algorithmic bytes per input sample of each hot-path kernel, in the unit the
 # scope table's measurement section fixes: the whole hot path (PFB, FFT,
 # delays, X-engine, flagging) reads each int8 input sample once (1 B); on the
@@ -1159,9 +1159,10 @@ def _roofline(wl, prec, args, dom, di, share, stage_ms, stage_n, S, n_in):
     if fused:
         inter["fft"] = 1.0 + 4.0        # samples in, spectra out (no z ring)
         if prec != 0:
-            # reduced precision: 4-byte code words per pair and channel out,
-            # which the requantiser transposes (1 B in, 1 B out)
-            inter.update(fft=1.0 + 1.0, requant=2.0)
+            # reduced precision: 4-byte code words per pair and channel out;
+            # int8 words go to the Gram as they are, e4m3 words are
+            # transposed by the requantiser (1 B in, 1 B out)
+            inter.update(fft=1.0 + 1.0, requant=2.0 if prec == 2 else 0.0)
     if es == 2:
         inter["fir"] += 1.0
     bytes_per_launch = alg * samples_timed / launches
@@ -1172,7 +1173,9 @@ def _roofline(wl, prec, args, dom, di, share, stage_ms, stage_n, S, n_in):
     kname = KERNELS[dom]
     M = 2 * W["n_chan"]
     if dom == "fft":
-        mode = 3                         # every real-input pipeline writes the pair-major ring
+        # pair-major spectra (mode 3); with reduced precision the F-engine
+        # writes int8 (6) / e4m3 (7) code words from the second ring fill on
+        mode = 3 if prec == 0 else (6 if prec == 1 else 7)
         kname = ("pfb_fft_kernel<%d,%d,%d> (fused PFB + FFT)" % (M, mode, W["taps"]) if fused
                  else "fft_kernel<%d,%d>" % (M, mode))
     fl = flops_per_sample(dom, fused, M, W["taps"], n_in)
