@@ -275,12 +275,12 @@ int corr_flag_dev(corr_t h, const float* d_vis, int n_vis, uint8_t* d_flags, voi
  *                    words [K][n_pairs][n_chan] uint32, n_pairs = n_in_pad /
  *                    2 (the handle's n_in rounded up to a multiple of 4;
  *                    words of pairs past the last input are ignored), the
- *                    bytes of word
- *                    (t, p, c) being the codes of Re V_2p, Im V_2p, Re
- *                    V_2p+1, Im V_2p+1 (low byte first); rows as above (row
- *                    a = Re of input a, row n_in + a = Im; rows from 2 n_in
- *                    up unspecified); k_pitch is ignored, n_chan must be a
- *                    multiple of 4 and n_in <= 64.
+ *                    bytes of word (t, p, c) being the codes of Re V_2p, Im
+ *                    V_2p, Re V_2p+1, Im V_2p+1 (low byte first); rows as
+ *                    above (row a = Re of input a, row n_in + a = Im); only
+ *                    the leading 2 n_in x 2 n_in block of each G[c] is
+ *                    written; k_pitch is ignored, n_chan must be a multiple
+ *                    of 4 and n_in <= 64.
  * d_G: [n_chan][128][128] FP32.  k_pitch must be a multiple of 128 and d_Q
  * 16-byte aligned (else CORR_EINVAL).  Runs on tcgen05 tensor cores with
  * TMA-staged operands; a stalled pipeline sets the status word read by

@@ -539,18 +539,24 @@ __global__ void __launch_bounds__(128 + kConvThreads, 1) gram_w_kernel(const __g
     if (sh->abort) {
         if (threadIdx.x == 0 && A.status) atomicExch(A.status, CORR_ETIMEDOUT);
         if (warp == 0 && lane == 0) drain_loads(sh->raw_full, kWRawStages, issued, lim);
-    } else if (warp < 4) {
+    } else if (warp < 4 && warp * 32 < 2 * A.n_in) {
+        // only the 2N x 2N block the visibilities use is written (in 32-column
+        // pieces); the TMEM loads are warp-wide, the stores per row
         const int r = warp * 32 + lane;
+        const int n2 = 2 * A.n_in;
 #pragma unroll 1
         for (int ch = 0; ch < kWChan; ++ch) {
             uint32_t* G = reinterpret_cast<uint32_t*>(A.G) + ((size_t)(kWChan * quad + ch) * kRows + r) * kRows;
-#pragma unroll
-            for (int c0 = 0; c0 < kRows; c0 += 32) {
+#pragma unroll 1
+            for (int c0 = 0; c0 < n2; c0 += 32) {
                 uint32_t rr[32];
                 tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 128 + c0), rr);
-                uint4* o = reinterpret_cast<uint4*>(G + c0);
+                if (r < n2) {
+                    uint4* o = reinterpret_cast<uint4*>(G + c0);
 #pragma unroll
-                for (int i = 0; i < 8; ++i) o[i] = make_uint4(rr[4 * i], rr[4 * i + 1], rr[4 * i + 2], rr[4 * i + 3]);
+                    for (int i = 0; i < 8; ++i)
+                        o[i] = make_uint4(rr[4 * i], rr[4 * i + 1], rr[4 * i + 2], rr[4 * i + 3]);
+                }
             }
         }
     }
