@@ -583,7 +583,11 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
         bool progress = false;
         long long s_end = ready_end;
         if (s_end > iend) s_end = iend;
-        if (s_end > p.s_xdone + p.v_cap) s_end = p.s_xdone + p.v_cap;
+        // the ring bounds a launch, except where the F-engine writes int8
+        // code words straight into the integration's word buffer (then one
+        // launch may cover the rest of the integration)
+        const bool to_words = p.words && p.have_scale && p.s_xdone == p.s_next && fused_codes(h, sv);
+        if (!to_words && s_end > p.s_xdone + p.v_cap) s_end = p.s_xdone + p.v_cap;
         if (s_end > p.s_next) {
             // scales fixed and nothing left in the ring: the F-engine
             // requantises in its epilogue (the requantiser's arithmetic) and
@@ -591,7 +595,7 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
             // requantiser below then only transposes them into Q
             const bool codes = p.have_scale && p.s_xdone == p.s_next && fused_codes(h, sv);
             p.ring_codes = codes && !p.words;
-            if (codes && p.words) {
+            if (to_words) {
                 // int8: the words go straight into the integration's C at
                 // t = s - istart, where the Gram kernel reads them
                 const CodeOut q{p.scale + (size_t)h->n_in_pad * h->n_chan, false};

@@ -370,6 +370,96 @@ __global__ void __launch_bounds__(32 * kFlagWarps) mad_flag_kernel(const float2*
     mad_flag_item<E>(R, F, n_chan, n_in, W, sigma, item, lane);
 }
 
+// Many items (large arrays): one thread per (integration, window,
+// baseline) item for windows of at most NW = 16 / 32 / 64 channels.  The
+// thread keeps the window's |R| values in registers and sorts them with an
+// unrolled bitonic network (no shuffles; padding +inf), reads the median,
+// turns the sorted values into |A - med| -- a bitonic sequence -- and sorts
+// those with one merge for the MAD.  Neighbouring threads take neighbouring
+// baselines, so their loads of a channel's row of R and their flag stores
+// are contiguous.  The order statistics are exact: the flags equal the warp
+// form's.  With few items (8 inputs: 36 baselines a window) the warp form
+// keeps the GPU busier.
+constexpr long long kLaneFlagItems = 16384;
+
+__device__ __forceinline__ void cmpswap(float& x, float& y) {
+    const float lo = fminf(x, y), hi = fmaxf(x, y);
+    x = lo;
+    y = hi;
+}
+
+template <int NW>
+__device__ __forceinline__ void lane_bitonic_stage(float (&v)[NW], int k) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+        for (int i = 0; i < NW; ++i) {
+            const int l = i ^ j;
+            if (l > i) {
+                if ((i & k) == 0) cmpswap(v[i], v[l]);
+                else cmpswap(v[l], v[i]);
+            }
+        }
+}
+
+// element i of v, i a runtime index (v stays in registers)
+template <int NW>
+__device__ __forceinline__ float lane_at(const float (&v)[NW], int i) {
+    float x = v[0];
+#pragma unroll
+    for (int q = 1; q < NW; ++q)
+        if (q == i) x = v[q];
+    return x;
+}
+
+template <int NW>
+__device__ __forceinline__ float lane_median(const float (&v)[NW], int W) {
+    return (W & 1) ? lane_at<NW>(v, W >> 1) : 0.5f * (lane_at<NW>(v, (W >> 1) - 1) + lane_at<NW>(v, W >> 1));
+}
+
+template <int NW>
+__global__ void __launch_bounds__(128) mad_flag_lane_kernel(const float2* R, uint8_t* F, int n_vis, int n_chan,
+                                                            int n_in, int W, float sigma) {
+    const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n_bl = n_in * (n_in + 1) / 2;
+    const int n_win = n_chan / W;
+    if (item >= (long long)n_vis * n_win * n_bl) return;
+    const int bl = (int)(item % n_bl);
+    const int w = (int)((item / n_bl) % n_win);
+    const int i = (int)(item / ((long long)n_bl * n_win));
+    int a = 0, rem = bl;
+    while (rem >= n_in - a) { rem -= n_in - a; ++a; }
+    const int b = a + rem;
+    const size_t cs = (size_t)n_in * n_in;
+    const size_t base = (size_t)i * n_chan * cs;
+    const float2* Rw = R + base + (size_t)w * W * cs + (size_t)a * n_in + b;   // channel c at Rw[c cs]
+    float v[NW];
+#pragma unroll
+    for (int c = 0; c < NW; ++c) {
+        if (c < W) {
+            const float2 r = __ldcg(Rw + c * cs);
+            v[c] = sqrtf(r.x * r.x + r.y * r.y);
+        } else {
+            v[c] = __int_as_float(0x7f800000);          // +inf: sorts after every value
+        }
+    }
+#pragma unroll
+    for (int k = 2; k <= NW; k <<= 1) lane_bitonic_stage<NW>(v, k);
+    const float med = lane_median<NW>(v, W);
+#pragma unroll
+    for (int c = 0; c < NW; ++c) v[c] = fabsf(v[c] - med);
+    lane_bitonic_stage<NW>(v, NW);
+    const float mad = lane_median<NW>(v, W);
+    const float T = med + sigma * mad * 1.4826f;
+    uint8_t* Fw = F + base + (size_t)w * W * cs;
+    for (int c = 0; c < W; ++c) {
+        const float2 r = __ldcg(Rw + c * cs);
+        const uint8_t f = sqrtf(r.x * r.x + r.y * r.y) > T ? 1 : 0;
+        Fw[c * cs + (size_t)a * n_in + b] = f;
+        Fw[c * cs + (size_t)b * n_in + a] = f;
+    }
+}
+
 template <int E>
 __device__ __forceinline__ void tail_flags(const TailMember& m, const TailItem& it, int warp, int lane) {
     const int n_bl = m.fin.n_in * (m.fin.n_in + 1) / 2;
@@ -478,6 +568,13 @@ void launch_mad_flags(const float2* R, uint8_t* F, int n_vis, int n_chan, int n_
                       float sigma, cudaStream_t st) {
     const long long items = (long long)n_vis * (n_chan / window) * (n_in * (n_in + 1) / 2);
     if (items <= 0) return;
+    if (window <= 64 && items >= kLaneFlagItems) {
+        const unsigned tb = (unsigned)((items + 127) / 128);
+        if (window <= 16) mad_flag_lane_kernel<16><<<tb, 128, 0, st>>>(R, F, n_vis, n_chan, n_in, window, sigma);
+        else if (window <= 32) mad_flag_lane_kernel<32><<<tb, 128, 0, st>>>(R, F, n_vis, n_chan, n_in, window, sigma);
+        else mad_flag_lane_kernel<64><<<tb, 128, 0, st>>>(R, F, n_vis, n_chan, n_in, window, sigma);
+        return;
+    }
     const unsigned blocks = (unsigned)((items + kFlagWarps - 1) / kFlagWarps);
     if (window <= 32) mad_flag_kernel<1><<<blocks, 32 * kFlagWarps, 0, st>>>(R, F, n_vis, n_chan, n_in, window, sigma);
     else if (window <= 64) mad_flag_kernel<2><<<blocks, 32 * kFlagWarps, 0, st>>>(R, F, n_vis, n_chan, n_in, window, sigma);

@@ -174,7 +174,10 @@ def test_xengine_dev_long_stream_beyond_the_grid_limit():
     assert np.max(np.abs(R.cpu().numpy()[:, 0, 0].real - Ro) / Ro) < 1e-4
 
 
-@pytest.mark.parametrize("window,n_chan,n_in", [(64, 256, 3), (64, 64, 1), (32, 128, 4), (8, 8, 2), (256, 512, 2)])
+# the last three have >= 16384 (window, baseline) items per call: one thread
+# per item instead of one warp
+@pytest.mark.parametrize("window,n_chan,n_in", [(64, 256, 3), (64, 64, 1), (32, 128, 4), (8, 8, 2), (256, 512, 2),
+                                                (64, 1024, 40), (32, 512, 28), (16, 256, 64)])
 def test_mad_flags_match_oracle(window, n_chan, n_in):
     rng = np.random.default_rng(window + n_chan)
     n_vis = 3
@@ -185,7 +188,7 @@ def test_mad_flags_match_oracle(window, n_chan, n_in):
     R[1, :window, 0, 0] = 2.0                                # MAD = 0 window
     R[1, 3, 0, 0] = 3.0
     R = (R + np.conj(np.swapaxes(R, -1, -2))) / 2            # Hermitian
-    R = R.astype(np.complex64)
+    R = np.ascontiguousarray(R.astype(np.complex64))
     c = _corr(n_in, 1, n_chan, 4, 16, flag_window=window)
     Rd = torch.from_numpy(R).to(DEV)
     F = torch.full(R.shape, 7, dtype=torch.uint8, device=DEV)
