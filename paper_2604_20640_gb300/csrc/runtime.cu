@@ -1938,8 +1938,12 @@ int corr_spectrogram_dev(corr_t h, const void* d_samples, size_t n_samples, size
     CK(cudaMemsetAsync(d_tiles, 0, sizeof(float) * (size_t)h->n_in * rows * h->n_chan, st));
     StreamView sv{static_cast<const int8_t*>(d_samples), (long long)stride, 0, (long long)n_samples, h->es};
     const long long s_total = rows * n_row;
-    for (long long s0 = 0; s0 < s_total; s0 += h->pd.v_cap) {
-        long long s1 = s0 + h->pd.v_cap;
+    // the fused F-engine accumulates the tiles with no ring at all: one
+    // launch; the two-kernel path passes its FIR output through the ring
+    const bool no_ring = h->fused_f && fused_f_supported(h->M, h->taps, h->es, 2);
+    const long long step = no_ring ? s_total : h->pd.v_cap;
+    for (long long s0 = 0; s0 < s_total; s0 += step) {
+        long long s1 = s0 + step;
         if (s1 > s_total) s1 = s_total;
         // the FFT accumulates the tiles directly (no spectra ring traffic)
         CKRET(launch_f(h, sv, h->tab_direct, h->pd.Z, 0, h->pd.v_cap - 1, h->pd.V, 0, h->pd.v_cap - 1, nullptr, s0, s1,
