@@ -464,7 +464,9 @@ long long corr_kernel_launches(corr_t h);
  * kernel counts as stage 1), 2 X-engine,
  * 3 finalise, 4 flagging, 5 requantise, 6 tensor-core Gram (first
  * n_stages entries, at most 7; the dynamic spectra of
- * corr_spectrogram_dev are accumulated by the FFT kernel), the milliseconds and
+ * corr_spectrogram_dev are accumulated by the FFT kernel; with at most 8
+ * inputs and flag windows of at most 64 channels the FP32 path makes the
+ * flags in the finalisation launch, stage 3), the milliseconds and
  * launch counts accumulated since the previous call, then clears them.
  * ms / counts may be NULL.
  */

@@ -269,6 +269,11 @@ int launch_fft_iq(const FftArgs& a, cudaStream_t st);
 int launch_fft(const FftArgs& a, cudaStream_t st);
 void launch_xengine(const XArgs& a, cudaStream_t st);
 void launch_finalize(const FinArgs& a, cudaStream_t st);
+// Finalisation and MAD flags of one integration in one launch (FP32 path,
+// n_in <= 8, window <= 64 channels dividing n_chan): the same results as
+// launch_finalize followed by launch_mad_flags.
+bool fin_flag_small_supported(int n_in, int window);
+void launch_fin_flag_small(const FinArgs& a, uint8_t* F, int window, float sigma, cudaStream_t st);
 void launch_mad_flags(const float2* R, uint8_t* F, int n_vis, int n_chan, int n_in, int window,
                       float sigma, cudaStream_t st);
 

@@ -773,6 +773,15 @@ int finalize_into(corr_t h, Pipe& p, const Tables& t, float2* R, uint8_t* F, int
     f.n_in = h->n_in;
     f.scale = 0.25f / (float)count;
     f.R = R;
+    const int fw = h->flag_window < h->n_chan ? h->flag_window : h->n_chan;
+    if (F && fin_flag_small_supported(h->n_in, fw) && h->n_chan % fw == 0) {
+        {
+            Timed t_(h, 3, st);
+            launch_fin_flag_small(f, F, fw, (float)h->flag_sigma, st);
+        }
+        CK(cudaGetLastError());
+        return CORR_OK;
+    }
     {
         Timed t_(h, 3, st);
         launch_finalize(f, st);

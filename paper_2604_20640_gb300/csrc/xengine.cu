@@ -201,18 +201,22 @@ __global__ void __launch_bounds__(128, 5) xengine_small_kernel(const XArgs X) {
 // One thread per (channel, 4x4 block, entry): sums the entry's partial
 // slots in slot order, scales, rotates and writes R_ab and its mirror.
 // (bx, t, z): the block's channel block, 4x4 block pair and entry.
-__device__ __forceinline__ void finalize_block(const FinArgs& F, int bx, int t, int z) {
-    const int k = bx * 128 + (int)threadIdx.x;
+// Visibility (a, b), a <= b, of channel k from element z of tile t: the
+// partial slots summed in order, scaled, rotated by Q_a conj(Q_b) off the
+// diagonal.  False where the element is padding or below the diagonal.
+__device__ __forceinline__ bool fin_value(const FinArgs& F, int k, int t, int z, int& a, int& b, float& re,
+                                          float& im) {
     const int i = z >> 2, j = z & 3;
-    if (k >= F.n_chan) return;
     const int n_in_pad = (F.n_in + 3) & ~3;
     int A, B;
     tile_decode(t, n_in_pad >> 2, A, B);
-    const int a = 4 * A + i, b = 4 * B + j;
-    if (a >= F.n_in || b >= F.n_in) return;
-    if (A == B && i > j) return;
+    a = 4 * A + i;
+    b = 4 * B + j;
+    if (a >= F.n_in || b >= F.n_in) return false;
+    if (A == B && i > j) return false;
     const int e = (i * 4 + j) * 2;
-    float re = 0.f, im = 0.f;
+    re = 0.f;
+    im = 0.f;
     for (int s = 0; s < F.n_slots; ++s) {
         const float* p = F.part + (((size_t)s * F.nt + t) * 32 + e) * F.n_chan + k;
         re += p[0];
@@ -220,10 +224,9 @@ __device__ __forceinline__ void finalize_block(const FinArgs& F, int bx, int t, 
     }
     re *= F.scale;
     im *= F.scale;
-    float2* R = F.R + (size_t)k * F.n_in * F.n_in;
     if (a == b) {
-        R[a * F.n_in + a] = make_float2(re, 0.f);
-        return;
+        im = 0.f;
+        return true;
     }
     if (F.rot) {
         // R_ab = Q_a conj(Q_b) * sum U_a U_b^*
@@ -235,8 +238,21 @@ __device__ __forceinline__ void finalize_block(const FinArgs& F, int bx, int t, 
         im = re * pi + im * pr;
         re = r2;
     }
+    return true;
+}
+
+__device__ __forceinline__ void fin_store(const FinArgs& F, int k, int a, int b, float re, float im) {
+    float2* R = F.R + (size_t)k * F.n_in * F.n_in;
     R[a * F.n_in + b] = make_float2(re, im);
-    R[b * F.n_in + a] = make_float2(re, -im);
+    if (a != b) R[b * F.n_in + a] = make_float2(re, -im);
+}
+
+__device__ __forceinline__ void finalize_block(const FinArgs& F, int bx, int t, int z) {
+    const int k = bx * 128 + (int)threadIdx.x;
+    if (k >= F.n_chan) return;
+    int a, b;
+    float re, im;
+    if (fin_value(F, k, t, z, a, b, re, im)) fin_store(F, k, a, b, re, im);
 }
 
 __global__ void __launch_bounds__(128) finalize_kernel(const FinArgs F) {
@@ -312,6 +328,27 @@ __device__ __forceinline__ float warp_sorted_median(const float (&v)[E], int W) 
                    : 0.5f * (warp_sorted_at<E>(v, (W >> 1) - 1) + warp_sorted_at<E>(v, W >> 1));
 }
 
+__device__ __forceinline__ float vis_abs(float2 r) { return sqrtf(r.x * r.x + r.y * r.y); }
+
+// Eq. 2's threshold median + sigma 1.4826 MAD over the warp's W values A
+// (element lane E + e; +inf past W).
+template <int E>
+__device__ __forceinline__ float warp_mad_threshold(const float (&A)[E], int W, float sigma, int lane) {
+    float v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = A[e];
+    warp_bitonic_sort<E>(v, lane);
+    const float med = warp_sorted_median<E>(v, W);
+    // |A - med| in the sorted order falls to the median and rises after it
+    // (the +inf padding stays last): a bitonic sequence, which one merge
+    // sorts -- the same values as sorting |A - med| from scratch
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = fabsf(v[e] - med);
+    warp_bitonic_merge<E>(v, lane);
+    const float mad = warp_sorted_median<E>(v, W);
+    return med + sigma * mad * 1.4826f;
+}
+
 // The flags of warp item `item` = (integration, window, baseline) of R.
 template <int E>
 __device__ __forceinline__ void mad_flag_item(const float2* R, uint8_t* F, int n_chan, int n_in, int W, float sigma,
@@ -325,29 +362,18 @@ __device__ __forceinline__ void mad_flag_item(const float2* R, uint8_t* F, int n
     while (rem >= n_in - a) { rem -= n_in - a; ++a; }
     const int b = a + rem;
     const size_t base = (size_t)i * n_chan * n_in * n_in;
-    float A[E], v[E];
+    float A[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int c = lane * E + e;
         if (c < W) {
             const int k = w * W + c;
-            const float2 r = __ldcg(R + base + ((size_t)k * n_in + a) * n_in + b);
-            A[e] = sqrtf(r.x * r.x + r.y * r.y);
+            A[e] = vis_abs(__ldcg(R + base + ((size_t)k * n_in + a) * n_in + b));
         } else {
             A[e] = __int_as_float(0x7f800000);          // +inf: sorts after every value
         }
-        v[e] = A[e];
     }
-    warp_bitonic_sort<E>(v, lane);
-    const float med = warp_sorted_median<E>(v, W);
-    // |A - med| in the sorted order falls to the median and rises after it
-    // (the +inf padding stays last): a bitonic sequence, which one merge
-    // sorts -- the same values as sorting |A - med| from scratch
-#pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = fabsf(v[e] - med);
-    warp_bitonic_merge<E>(v, lane);
-    const float mad = warp_sorted_median<E>(v, W);
-    const float T = med + sigma * mad * 1.4826f;
+    const float T = warp_mad_threshold<E>(A, W, sigma, lane);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int c = lane * E + e;
@@ -437,8 +463,7 @@ __global__ void __launch_bounds__(128) mad_flag_lane_kernel(const float2* R, uin
 #pragma unroll
     for (int c = 0; c < NW; ++c) {
         if (c < W) {
-            const float2 r = __ldcg(Rw + c * cs);
-            v[c] = sqrtf(r.x * r.x + r.y * r.y);
+            v[c] = vis_abs(__ldcg(Rw + c * cs));
         } else {
             v[c] = __int_as_float(0x7f800000);          // +inf: sorts after every value
         }
@@ -453,10 +478,60 @@ __global__ void __launch_bounds__(128) mad_flag_lane_kernel(const float2* R, uin
     const float T = med + sigma * mad * 1.4826f;
     uint8_t* Fw = F + base + (size_t)w * W * cs;
     for (int c = 0; c < W; ++c) {
-        const float2 r = __ldcg(Rw + c * cs);
-        const uint8_t f = sqrtf(r.x * r.x + r.y * r.y) > T ? 1 : 0;
+        const uint8_t f = vis_abs(__ldcg(Rw + c * cs)) > T ? 1 : 0;
         Fw[c * cs + (size_t)a * n_in + b] = f;
         Fw[c * cs + (size_t)b * n_in + a] = f;
+    }
+}
+
+// Finalisation and MAD flags in one kernel for small arrays (n_in <= 8,
+// windows of at most 64 channels): one CTA per (channel window, 4 x 4 tile).
+// Its threads finalise the tile's elements for the window's channels (the
+// arithmetic of finalize_kernel; consecutive threads take consecutive
+// channels, so the partial-slot reads coalesce) and keep |R| of each
+// baseline in shared memory; then one warp per baseline derives Eq. 2's
+// threshold from them exactly as mad_flag_kernel does from R, and writes
+// the flags.  One launch instead of two, and R is not read back.
+constexpr int kFinFlagW = 64;
+__global__ void __launch_bounds__(256) fin_flag_small_kernel(const FinArgs F, uint8_t* Fl, int W, float sigma) {
+    __shared__ float mag[16][kFinFlagW];
+    const int w = blockIdx.x, t = blockIdx.y;
+    for (int it = (int)threadIdx.x; it < 16 * W; it += (int)blockDim.x) {
+        const int z = it / W, c = it % W;
+        const int k = w * W + c;
+        int a, b;
+        float re, im;
+        if (fin_value(F, k, t, z, a, b, re, im)) {
+            fin_store(F, k, a, b, re, im);
+            mag[z][c] = vis_abs(make_float2(re, im));
+        }
+    }
+    __syncthreads();
+    const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    const int n_in_pad = (F.n_in + 3) & ~3;
+    int A, B;
+    tile_decode(t, n_in_pad >> 2, A, B);
+    for (int z = warp; z < 16; z += (int)(blockDim.x >> 5)) {
+        const int i = z >> 2, j = z & 3;
+        const int a = 4 * A + i, b = 4 * B + j;
+        if (a >= F.n_in || b >= F.n_in || (A == B && i > j)) continue;   // uniform over the warp
+        float v[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int c = lane * 2 + e;
+            v[e] = c < W ? mag[z][c] : __int_as_float(0x7f800000);
+        }
+        const float T = warp_mad_threshold<2>(v, W, sigma, lane);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int c = lane * 2 + e;
+            if (c < W) {
+                const int k = w * W + c;
+                const uint8_t f = v[e] > T ? 1 : 0;
+                Fl[((size_t)k * F.n_in + a) * F.n_in + b] = f;
+                Fl[((size_t)k * F.n_in + b) * F.n_in + a] = f;
+            }
+        }
     }
 }
 
@@ -562,6 +637,13 @@ void launch_xengine(const XArgs& a, cudaStream_t st) {
 void launch_finalize(const FinArgs& a, cudaStream_t st) {
     dim3 grid((a.n_chan + 127) / 128, a.nt, 16);
     finalize_kernel<<<grid, 128, 0, st>>>(a);
+}
+
+bool fin_flag_small_supported(int n_in, int window) { return n_in <= 8 && window <= kFinFlagW; }
+
+void launch_fin_flag_small(const FinArgs& a, uint8_t* F, int window, float sigma, cudaStream_t st) {
+    dim3 grid((unsigned)(a.n_chan / window), (unsigned)a.nt);
+    fin_flag_small_kernel<<<grid, 256, 0, st>>>(a, F, window, sigma);
 }
 
 void launch_mad_flags(const float2* R, uint8_t* F, int n_vis, int n_chan, int n_in, int window,

@@ -397,7 +397,8 @@ def test_stage_times_and_stage_mask():
     c.stage_times()
     c.run_dev(xd, vis, flags)
     ms, n = c.stage_times()
-    assert all(n[i] > 0 and ms[i] > 0 for i in range(5)) and n[5] == n[6] == 0
+    # with at most 8 inputs the flags are made in the finalisation launch
+    assert all(n[i] > 0 and ms[i] > 0 for i in range(4)) and n[4] == n[5] == n[6] == 0
     c.set_option("stage_mask", 1 << 1)                # the FFT alone
     c.run_dev(xd, vis, flags)
     ms2, n2 = c.stage_times()
