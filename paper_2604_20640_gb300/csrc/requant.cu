@@ -1,15 +1,17 @@
 // Requantiser and rescaling around the tensor-core X-engine.
 //
-// requant_pm_kernel turns a batch of channelised spectra (U = 2Y, unrotated,
-// in the pair-major ring [slot][pair][n_chan] float4), or the code words the
-// fused F-engine already made from them, into the stacked
-// operand Q[k][row][t] of the tensor-core Gram: row a holds Re U_a /
-// sigma_a[k], row N + a holds Im U_a / sigma_a[k], t the spectrum index inside
-// the integration: int8 codes (round half to even, saturate at +-127) as
-// bytes (widened on chip by gram_i8_kernel) or carried as BF16, or e4m3
-// (satfinite) bytes.  A thread owns one input pair and channel over a run of
-// spectra, so reads coalesce across channels and every row gets a whole
-// 32-byte sector of codes.
+// int8 pipeline: words_from_spectra_kernel turns channelised spectra (U =
+// 2Y, unrotated, in the pair-major ring [slot][pair][n_chan] float4) into
+// the integration's code words C[t][pair][k] -- the form the fused F-engine
+// writes itself once the scales are fixed, and the form gram_w_kernel reads.
+// e4m3 pipeline and stage calls: requant_pm_kernel turns the spectra, or the
+// code words the fused F-engine made from them, into the stacked operand
+// Q[k][row][t]: row a holds Re U_a / sigma_a[k], row N + a holds Im U_a /
+// sigma_a[k], t the spectrum index inside the integration; int8 codes (round
+// half to even, saturate at +-127) as bytes or carried as BF16, or e4m3
+// (satfinite) bytes.  A thread owns one input pair and channel over a run
+// of spectra, so reads coalesce across channels and every row gets whole
+// 32-byte sectors of codes.
 // The scales are fixed for a whole integration: the first integration of a
 // stream takes them from the mean power of its first spectra, later ones
 // from the previous integration's autocorrelations.
