@@ -333,6 +333,27 @@ def oracle_leg(wl, x_dev, spec, vis0, flags0):
     return cpu, err
 
 
+def e4m3_vis(args, x, spec):
+    """Visibilities of the 64-input workload's stream through the e4m3
+    pipeline (one untimed run, autotuned like the timed one)."""
+    import torch
+    from paper_2604_20640_gb300 import Correlator
+    W = WORKLOADS["c3"]
+    n_in = W["n_ant"] * W["n_pol"]
+    c = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"], precision=2,
+                   **({"ring_mb": args.ring_mb} if args.ring_mb else {}))
+    if not args.ring_mb:
+        c.autotune(x)
+    c.set_delays(spec.tau, spec.phi)
+    n = c.n_integrations(x.shape[1])
+    vis = torch.empty((n, W["n_chan"], n_in, n_in), dtype=torch.complex64, device=x.device)
+    flags = torch.empty((n, W["n_chan"], n_in, n_in), dtype=torch.uint8, device=x.device)
+    c.run_dev(x, vis, flags)
+    torch.cuda.synchronize()
+    c.close()
+    return vis
+
+
 def rho_error(x_dev, spec, n_chan, taps, n_int, vis_dev, ints, n_inputs=16, chans=(0, 3, 100, 511, 512, 900, 1023)):
     """max |rho_gpu - rho_oracle| on the first n_inputs inputs and sampled
     channels of the given integrations, from the oracle F-engine over the
@@ -1013,6 +1034,12 @@ def main():
         if wl == "c3":
             cpu, _ = oracle_leg(wl, x, spec, None, None)
             error = rho_error(x, spec, W["n_chan"], W["taps"], W["n_int"], m["vis"], (0, m["vis"].shape[0] - 1))
+            error["dtype"] = ["fp32", "int8", "e4m3"][prec]
+            if prec == 1:
+                # the other code type the workload names: the same stream
+                # through the e4m3 pipeline once (untimed), its error too
+                error["e4m3"] = rho_error(x, spec, W["n_chan"], W["taps"], W["n_int"], e4m3_vis(args, x, spec),
+                                          (0, m["vis"].shape[0] - 1))
         else:
             cpu, error = oracle_leg(wl, x, spec, m["vis"][0].cpu().numpy(), m["flags"][0].cpu().numpy())
     del m["vis"], m["flags"]

@@ -490,9 +490,9 @@ int corr_stage_times(corr_t h, double* ms, long long* counts, int n_stages);
  * exit.  Shapes whose per-group scratch ((blocks of 4 inputs, A <= B) * 32 *
  * n_chan floats) exceeds 2^21 floats are rejected with CORR_EINVAL; long
  * streams are summed in fewer, longer groups.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) and keeps it
- * for the life of the process; make that first call before any stream
- * capture, and do not call it after cudaDeviceReset.  All calls share the
+ * looks up the array's device address (cudaGetSymbolAddress, a synchronous
+ * runtime call) and keeps it for the life of the process; do not call it
+ * after cudaDeviceReset.  All calls share the
  * array and it keeps the last call's contents (every part a call reads it
  * first writes itself), so calls that overlap on the GPU race: serialise
  * them on one stream.  Misaligned buffers are rejected with CORR_EINVAL, and

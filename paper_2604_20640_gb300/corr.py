@@ -195,8 +195,10 @@ class Group:
 
 def xengine_noalloc(V, n_spec: int, n_in: int, n_chan: int, vis_out, stream=None):
     """X-engine without any device allocation (corr_xengine_noalloc): for
-    callers that may not allocate, e.g. while capturing a CUDA graph.  Same
-    layouts as :meth:`Correlator.xengine_dev`; no handle needed."""
+    callers that cannot allocate device memory (real-time loops in which an
+    allocator call could synchronise the device, hosts that plan the GPU's
+    memory themselves).  Same layouts as :meth:`Correlator.xengine_dev`; no
+    handle needed."""
     L = load_library()
     rc = L.corr_xengine_noalloc(_dev_ptr(V, "V"), int(n_spec), int(n_in), int(n_chan),
                                 _dev_ptr(vis_out, "vis"), _stream_ptr(stream))
