@@ -681,18 +681,21 @@ def run_batched(args, rank, world, local):
             torch.cuda.synchronize(dev)
 
         e2e_steps(max(2, args.warmup))
-        if world > 1:
-            dist.barrier()
-        t0 = time.perf_counter()
-        e2e_steps(args.steps)
-        ems = (time.perf_counter() - t0) * 1e3 / args.steps
+        reps = []
+        for _ in range(3):      # median of three windows (the host's copies vary)
+            if world > 1:
+                dist.barrier()
+            t0 = time.perf_counter()
+            e2e_steps(args.steps)
+            reps.append((time.perf_counter() - t0) * 1e3 / args.steps)
+        ems = sorted(reps)[1]
         ems = max_over_ranks(ems, dist if world > 1 else None, dev)
         ok = all(torch.equal(a, b) for a, b in zip(vis, vis_b)) and all(torch.equal(a, b) for a, b in zip(flags, flags_b))
         d2h_bytes = sum(v.numel() * v.element_size() for v in vis) + sum(f.numel() for f in flags)
         e2e = {"value": job_rate(bytes_step, world, ems), "unit": "GB/s", "h2d_bytes_per_step": bytes_step,
                "d2h_bytes_per_step": int(d2h_bytes), "ms_per_step": ems,
                "note": "two groups alternate: copies in, graph, read-back overlapped across steps",
-               "sets_agree": bool(ok)}
+               "sets_agree": bool(ok), "repetitions_ms_per_step": [round(r, 3) for r in reps]}
         g_b.close()
         for c in members_b:
             c.close()
@@ -912,12 +915,16 @@ def run_flagger(args, rank, world, local):
             stream.synchronize()
 
         e2e_steps(max(1, args.warmup))
-        t0 = time.perf_counter()
-        e2e_steps(args.steps)
-        ems = (time.perf_counter() - t0) * 1e3 / args.steps
+        reps = []
+        for _ in range(3):      # median of three windows (the host's copies vary)
+            t0 = time.perf_counter()
+            e2e_steps(args.steps)
+            reps.append((time.perf_counter() - t0) * 1e3 / args.steps)
+        ems = sorted(reps)[1]
         ems = max_over_ranks(ems, dist if world > 1 else None, dev)
         e2e = {"value": job_rate(bytes_step, world, ems), "unit": "GB/s",
-               "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": int(fh.numel()), "ms_per_step": ems}
+               "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": int(fh.numel()), "ms_per_step": ems,
+               "repetitions_ms_per_step": [round(r, 3) for r in reps]}
         del host, bufs
     if rank == 0:
         cpu = None
@@ -1058,7 +1065,7 @@ def main():
                        "path": ["plain FP32 (CUDA-core X)", "int8 requantised, tcgen05 X (BF16 MMA)",
                                 "e4m3 requantised, tcgen05 X"][prec],
                        "samples_per_input": S, "sample_bits": args.bits,
-                       "tuning": {"ring_mb": m["tuning"][0], "fir_spt": m["tuning"][1]},
+                       "tuning": {"ring_mb": m["tuning"][0], "fir_spt": m["tuning"][1], "x_depth": m["tuning"][2]},
                        "l2": m["l2"],
                        "parallelism": "replicas" if world > 1 else "single"},
             "gpu_launches": m["launches"], "clocks": m["clocks"], "roofline": m["roofline"], "e2e": e2e,
@@ -1260,7 +1267,7 @@ def end_to_end(args, wl, prec, x, spec, tuning, dev, world, dist):
     ring_e2e = args.ring_mb or max(tuning[0], 128)
     chunk = args.chunk or W["chunk"]
     ce = Correlator(W["n_ant"], W["n_pol"], W["n_chan"], W["taps"], W["n_int"], chunk=chunk,
-                    precision=prec, sample_bits=args.bits, ring_mb=ring_e2e, fir_spt=tuning[1])
+                    precision=prec, sample_bits=args.bits, ring_mb=ring_e2e, fir_spt=tuning[1], x_depth=tuning[2])
     ce.set_delays(spec.tau, spec.phi)
     host = torch.empty((n_in, S), dtype=x.dtype, pin_memory=True)
     host.copy_(x)
@@ -1287,30 +1294,37 @@ def end_to_end(args, wl, prec, x, spec, tuning, dev, world, dist):
 
     for _ in range(max(1, args.warmup)):
         e2e_step()
-    if world > 1:
-        dist.barrier()
-    phase[:] = [0.0, 0.0]
-    popped[0] = 0
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        v, f = e2e_step()
-    t1 = time.perf_counter()
-    if world > 1:
-        dist.barrier()
-    timed_ints = popped[0]
+    # the host->device copies of this shared host vary between windows of
+    # time: the timed steps run three times over and the median counts
+    reps = []
+    timed_ints = 0
+    for _ in range(3):
+        if world > 1:
+            dist.barrier()
+        phase[:] = [0.0, 0.0]
+        popped[0] = 0
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            v, f = e2e_step()
+        t1 = time.perf_counter()
+        if world > 1:
+            dist.barrier()
+        reps.append(((t1 - t0) * 1e3 / args.steps, phase[0] * 1e3 / args.steps, phase[1] * 1e3 / args.steps))
+        timed_ints = max(timed_ints, popped[0])
     ce.flush()
     ce.get_vis(out=vis_h)
     ce.get_flags(out=flags_h)
     # every step's integrations were read back: n_intg per step, the stream's
     # last one (held back one spectrum for the delays) popped by the next step
     assert timed_ints >= args.steps * n_intg - 1, (timed_ints, args.steps, n_intg)
-    ems = (t1 - t0) * 1e3 / args.steps
+    med = sorted(reps)[1]
+    ems = med[0]
     ems = max_over_ranks(ems, dist if world > 1 else None, dev)
     out = {"value": job_rate(bytes_step, world, ems), "unit": "GB/s", "ring_mb": ring_e2e,
            "h2d_bytes_per_step": bytes_step,
            "d2h_bytes_per_step": int(v.numel() * v.element_size() + f.numel() * f.element_size()),
-           "ms_per_step": ems, "push_ms": phase[0] * 1e3 / args.steps,
-           "pop_ms": phase[1] * 1e3 / args.steps, "integrations_read_back": timed_ints,
+           "ms_per_step": ems, "push_ms": med[1], "pop_ms": med[2], "integrations_read_back": timed_ints,
+           "repetitions_ms_per_step": [round(r[0], 3) for r in reps],
            "mode": "continuing stream: each step pushes %d MiB from pinned memory and pops the integrations "
                    "completed so far; flushed after the timed steps" % (bytes_step >> 20)}
     ce.close()

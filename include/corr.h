@@ -112,6 +112,9 @@ const char* corr_last_error(corr_t h);
  *                  spectra each F-engine thread runs over: the FIR kernel's
  *                  run, or the fused kernel's run per CTA (automatic: one
  *                  wave of resident CTAs); results do not depend on it
+ *   "x_depth"      (6, default, or 4; may change at any time)  spectra each
+ *                  thread of the small X-engine (at most 8 inputs) has in
+ *                  flight; results do not depend on it
  *   "fused_f"      (1, default, or 0; may change at any time)  run the
  *                  F-engine as one kernel (FIR output kept in shared
  *                  memory) where it covers the shape -- int8 samples, 4
@@ -315,18 +318,21 @@ int corr_group_run_dev(corr_t group, const void* const* d_samples, const size_t*
 
 /*
  * corr_autotune -- pick the ring capacity ("ring_mb" 32/64/128/256, the
- * spectra per launch) and the F-engine's work split ("fir_spt" auto/8/16:
+ * spectra per launch), the F-engine's work split ("fir_spt" auto/8/16:
  * spectra per thread run of the FIR kernel, or per CTA of the fused
- * kernel) of a handle by timing
- * corr_run_dev on up to eight integrations of a device sample (results do
- * not depend on either choice; larger rings mean larger launches).  cache_path (may be NULL) is a text file of
- * "gpu n_in n_chan taps n_int precision ring_mb fir_spt" lines: a matching
- * line is applied without timing, a new choice is appended.
- * corr_get_tuning reports the current values.
+ * kernel) and, for FP32 pipelines of at most 8 inputs, the X-engine's
+ * pipeline depth ("x_depth" 4/6: spectra each thread has in flight) of a
+ * handle by timing corr_run_dev on up to eight integrations of a device
+ * sample (results do not depend on any of the choices; larger rings mean
+ * larger launches).  cache_path (may be NULL) is a text file of
+ * "gpu n_in n_chan taps n_int precision ring_mb fir_spt x_depth" lines
+ * (x_depth may be missing: 6): a matching line is applied without timing,
+ * a new choice is appended.  corr_get_tuning reports the current values
+ * (any pointer may be NULL).
  */
 int corr_autotune(corr_t h, const void* d_samples, size_t n_samples, size_t input_stride,
                   const char* cache_path, void* stream);
-int corr_get_tuning(corr_t h, int* ring_mb, int* fir_spt);
+int corr_get_tuning(corr_t h, int* ring_mb, int* fir_spt, int* x_depth);
 
 /*
  * corr_spectrogram_dev -- autocorrelation power of every input in tiles of

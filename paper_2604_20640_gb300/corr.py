@@ -93,7 +93,7 @@ def load_library(path: str = LIB_PATH):
         "corr_group_create": (_i, [ctypes.POINTER(_vp), _vp, _i]),
         "corr_group_run_dev": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
         "corr_autotune": (_i, [_vp, _vp, _sz, _sz, ctypes.c_char_p, _vp]),
-        "corr_get_tuning": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+        "corr_get_tuning": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
         "corr_spectrogram_dev": (_i, [_vp, _vp, _sz, _sz, _i, _vp, _vp]),
         "corr_flagnet_create": (_i, [ctypes.POINTER(_vp)]),
         "corr_flagnet_destroy": (_i, [_vp]),
@@ -443,9 +443,10 @@ class Correlator:
                                           _stream_ptr(stream)))
 
     def tuning(self):
-        r, s = _i(), _i()
-        self._check(self._L.corr_get_tuning(self._h, ctypes.byref(r), ctypes.byref(s)))
-        return r.value, s.value
+        """(ring_mb, fir_spt, x_depth) as set by autotune or the options."""
+        r, s, d = _i(), _i(), _i()
+        self._check(self._L.corr_get_tuning(self._h, ctypes.byref(r), ctypes.byref(s), ctypes.byref(d)))
+        return r.value, s.value, d.value
 
     def gram_dev(self, Q, n_chan: int, k_pitch: int, K: int, dtype: int, G_out, stream=None):
         """Tensor-core Gram matrices of Q (see corr_gram_dev in include/corr.h)."""

@@ -114,6 +114,7 @@ struct XArgs {
     int G, j0, n_groups;
     float* part;             // [gpi][nt][32][n_chan]
     int pair_major;          // V pair-major, see FftArgs
+    int depth;               // n_in_pad <= 8: spectra in flight per thread, 4 or 6 (0: 6)
 };
 
 // Finalise: R[k][a][b] = scale * Q_a[k] conj(Q_b[k]) * (sum over partial

@@ -118,6 +118,7 @@ struct corr_s {
     int result_slots = 8;
     int ring_mb = 64;            // tunable: ring capacity of Z and V (MiB each)
     int fir_spt = 0;             // tunable: spectra per FIR thread (0 = automatic)
+    int x_depth = 6;             // tunable: small X-engine's spectra in flight per thread (4 or 6)
     int window = 0;              // PFB taper: 0 Hann, 1 Kaiser, 2 unit coefficients
     int es = 1;                  // bytes per input sample: 1 (int8), 2 (int16, 16-bit padded mode; or int8 I/Q)
     int iq = 0;                  // complex input: interleaved int8 I/Q, M = n_chan
@@ -683,6 +684,7 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
                 // keeps its own partial sums
                 x.part = h->defer_tail ? p.part_all + (size_t)i * h->gpi * h->nt * 32 * h->n_chan : p.part;
                 x.pair_major = pair_major_ring(h);
+                x.depth = h->x_depth;
                 {
                     Timed t_(h, 2, st);
                     launch_xengine(x, st);
@@ -1222,7 +1224,8 @@ const char* corr_last_error(corr_t h) {
 int corr_set_option(corr_t h, const char* key, double v) {
     if (!h || !key) return fail(h, CORR_EINVAL, "NULL argument");
     const std::string k(key);
-    if (h->started && k != "stage_timing" && k != "stage_mask" && k != "fir_spt" && k != "fused_f" &&
+    if (h->started && k != "stage_timing" && k != "stage_mask" && k != "fir_spt" && k != "x_depth" &&
+        k != "fused_f" &&
         k != "tc_wait_ms" && k != "inject_stall" && k != "inject_alloc_fail" && k != "max_pending")
         return fail(h, CORR_ESTATE, "options must be set before the first push");
     if (k == "flag_sigma") {
@@ -1286,6 +1289,10 @@ int corr_set_option(corr_t h, const char* key, double v) {
     } else if (k == "fir_spt") {
         if (v < 0 || v > 256) return fail(h, CORR_EINVAL, "fir_spt out of range");
         h->fir_spt = (int)v;
+        return CORR_OK;
+    } else if (k == "x_depth") {
+        if (v != 4 && v != 6) return fail(h, CORR_EINVAL, "x_depth: 4 or 6");
+        h->x_depth = (int)v;
         return CORR_OK;
     } else if (k == "stage_timing") {
         h->timer.on = v != 0;
@@ -1822,7 +1829,7 @@ std::string tune_key(corr_t h) {
     return buf;
 }
 
-bool tune_lookup(const char* path, const std::string& key, int* ring_mb, int* fir_spt) {
+bool tune_lookup(const char* path, const std::string& key, int* ring_mb, int* fir_spt, int* x_depth) {
     if (!path) return false;
     FILE* f = std::fopen(path, "r");
     if (!f) return false;
@@ -1831,10 +1838,11 @@ bool tune_lookup(const char* path, const std::string& key, int* ring_mb, int* fi
     while (std::fgets(line, sizeof(line), f)) {
         std::string l(line);
         if (l.compare(0, key.size(), key) == 0 && l.size() > key.size() && l[key.size()] == ' ') {
-            int r = 0, sp = 0;
-            if (std::sscanf(l.c_str() + key.size(), "%d %d", &r, &sp) == 2) {
+            int r = 0, sp = 0, d = 6;
+            if (std::sscanf(l.c_str() + key.size(), "%d %d %d", &r, &sp, &d) >= 2) {
                 *ring_mb = r;
                 *fir_spt = sp;
+                *x_depth = (d == 4) ? 4 : 6;
                 found = true;
             }
         }
@@ -1851,13 +1859,14 @@ int corr_autotune(corr_t h, const void* d_samples, size_t n_samples, size_t stri
     if (!d_samples || stride < n_samples) return fail(h, CORR_EINVAL, "bad sample buffer");
     DeviceGuard dg(h->dev);
     const std::string key = tune_key(h);
-    int ring = 0, spt = 0;
-    if (tune_lookup(cache_path, key, &ring, &spt)) {
+    int ring = 0, spt = 0, depth = 6;
+    if (tune_lookup(cache_path, key, &ring, &spt, &depth)) {
         if (ring != h->ring_mb) {
             h->ring_mb = ring;
             free_pipe(h->pd);
         }
         h->fir_spt = spt;
+        h->x_depth = depth;
         return CORR_OK;
     }
     // Time every candidate on (at most) eight integrations of the sample:
@@ -1876,16 +1885,22 @@ int corr_autotune(corr_t h, const void* d_samples, size_t n_samples, size_t stri
     CK(cudaEventCreate(&e1));
     const int rings[] = {32, 64, 128, 256};
     const int spts[] = {0, 8, 16};
+    // the small X-engine's pipeline depth (FP32 pipelines of at most 8 inputs)
+    const bool small_x = h->precision == CORR_FP32 && h->n_in_pad <= 8;
+    const int depths[] = {6, 4};
+    const int n_depths = small_x ? 2 : 1;
     float best = 1e30f;
-    int best_ring = h->ring_mb, best_spt = h->fir_spt;
+    int best_ring = h->ring_mb, best_spt = h->fir_spt, best_depth = h->x_depth;
     int rc = CORR_OK;
     for (int r : rings) {
         for (int sp : spts) {
+          for (int di = 0; di < n_depths; ++di) {
             if (r != h->ring_mb) {
                 h->ring_mb = r;
                 free_pipe(h->pd);
             }
             h->fir_spt = sp;
+            if (small_x) h->x_depth = depths[di];
             int got = 0;
             rc = corr_run_dev(h, d_samples, n_use, stride, reinterpret_cast<float*>(vis), flags, n_out, 0, &got,
                               stream);
@@ -1902,7 +1917,11 @@ int corr_autotune(corr_t h, const void* d_samples, size_t n_samples, size_t stri
                 best = ms;
                 best_ring = r;
                 best_spt = sp;
+                best_depth = h->x_depth;
             }
+            if (rc != CORR_OK) break;
+          }
+          if (rc != CORR_OK) break;
         }
         if (rc != CORR_OK) break;
     }
@@ -1916,20 +1935,22 @@ int corr_autotune(corr_t h, const void* d_samples, size_t n_samples, size_t stri
         free_pipe(h->pd);
     }
     h->fir_spt = best_spt;
+    h->x_depth = best_depth;
     if (cache_path) {
         FILE* f = std::fopen(cache_path, "a");
         if (f) {
-            std::fprintf(f, "%s %d %d\n", key.c_str(), best_ring, best_spt);
+            std::fprintf(f, "%s %d %d %d\n", key.c_str(), best_ring, best_spt, best_depth);
             std::fclose(f);
         }
     }
     return CORR_OK;
 }
 
-int corr_get_tuning(corr_t h, int* ring_mb, int* fir_spt) {
+int corr_get_tuning(corr_t h, int* ring_mb, int* fir_spt, int* x_depth) {
     if (!h) return fail(h, CORR_EINVAL, "NULL handle");
     if (ring_mb) *ring_mb = h->ring_mb;
     if (fir_spt) *fir_spt = h->fir_spt;
+    if (x_depth) *x_depth = h->x_depth;
     return CORR_OK;
 }
 

@@ -84,12 +84,13 @@ __global__ void __launch_bounds__(128) xengine_kernel(const XArgs X) {
 // channels are 256 contiguous bytes of the pair-major ring), the two partial
 // sums are added by one xor-shuffle, then written in the 4x4 block layout.
 // PM: spectra pair-major ([slot][pair][n_chan] float4), else channel-major.
-// Each thread streams its spectra through kXsDepth stages of shared memory
+// Each thread streams its spectra through DEPTH stages of shared memory
 // with cp.async (16-byte copies of its own chunks, so no barrier is needed):
-// four spectra in flight a thread instead of one.
+// DEPTH spectra in flight a thread instead of one.  DEPTH (4 or 6; 48 KiB a
+// CTA at n_in 8 and 6) is a tile shape the autotuner picks; it does not
+// change the result.
 constexpr int kXsChan = 16;       // channels per warp
 constexpr int kXsSub = 2;         // sub-groups per channel
-constexpr int kXsDepth = 6;       // spectra in flight per thread (48 KiB a CTA at n_in 8)
 
 __device__ __forceinline__ void xs_cp16(float4* dst, const float4* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
@@ -98,10 +99,10 @@ __device__ __forceinline__ void xs_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void xs_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-template <int NB>
-constexpr size_t xs_smem_bytes() { return sizeof(float4) * kXsDepth * (2 * NB) * 128; }
+template <int NB, int DEPTH>
+constexpr size_t xs_smem_bytes() { return sizeof(float4) * DEPTH * (2 * NB) * 128; }
 
-template <int NB, bool PM>
+template <int NB, bool PM, int DEPTH>
 __global__ void __launch_bounds__(128, 5) xengine_small_kernel(const XArgs X) {
     constexpr int NI = 4 * NB;
     constexpr int NC = NI * (NI - 1) / 2;
@@ -135,10 +136,10 @@ __global__ void __launch_bounds__(128, 5) xengine_small_kernel(const XArgs X) {
         xs_commit();   // one group per stage, empty past the end
     };
 #pragma unroll
-    for (int d = 0; d < kXsDepth; ++d) fetch(s0 + q + (long long)d * kXsSub, d);
+    for (int d = 0; d < DEPTH; ++d) fetch(s0 + q + (long long)d * kXsSub, d);
     int stage = 0;
     for (long long s = s0 + q; s < s1; s += kXsSub) {
-        xs_wait<kXsDepth - 1>();   // this thread's copies of spectrum s have landed
+        xs_wait<DEPTH - 1>();      // this thread's copies of spectrum s have landed
         float xr[NI], xi[NI];
 #pragma unroll
         for (int i = 0; i < NI / 2; ++i) {
@@ -156,9 +157,9 @@ __global__ void __launch_bounds__(128, 5) xengine_small_kernel(const XArgs X) {
                 ci[c] = fmaf(xi[a], xr[b], fmaf(-xr[a], xi[b], ci[c]));
             }
         }
-        // this stage's values are used: refill it kXsDepth spectra ahead
-        fetch(s + (long long)kXsDepth * kXsSub, stage);
-        stage = stage + 1 == kXsDepth ? 0 : stage + 1;
+        // this stage's values are used: refill it DEPTH spectra ahead
+        fetch(s + (long long)DEPTH * kXsSub, stage);
+        stage = stage + 1 == DEPTH ? 0 : stage + 1;
     }
 #pragma unroll
     for (int m = kXsChan; m < 32; m <<= 1) {
@@ -620,13 +621,16 @@ void launch_xengine(const XArgs& a, cudaStream_t st) {
     if (a.n_in_pad <= 8) {
         constexpr int per_cta = 4 * kXsChan;          // 4 warps of 16 channels
         dim3 grid((a.n_chan + per_cta - 1) / per_cta, a.n_groups);
+        const bool d4 = a.depth == 4;                 // else 6 (the default)
+#define CORR_XS(NB, PM, D) xengine_small_kernel<NB, PM, D><<<grid, 128, xs_smem_bytes<NB, D>(), st>>>(a)
         if (a.pair_major) {
-            if (a.n_in_pad == 4) xengine_small_kernel<1, true><<<grid, 128, xs_smem_bytes<1>(), st>>>(a);
-            else xengine_small_kernel<2, true><<<grid, 128, xs_smem_bytes<2>(), st>>>(a);
+            if (a.n_in_pad == 4) { if (d4) CORR_XS(1, true, 4); else CORR_XS(1, true, 6); }
+            else { if (d4) CORR_XS(2, true, 4); else CORR_XS(2, true, 6); }
         } else {
-            if (a.n_in_pad == 4) xengine_small_kernel<1, false><<<grid, 128, xs_smem_bytes<1>(), st>>>(a);
-            else xengine_small_kernel<2, false><<<grid, 128, xs_smem_bytes<2>(), st>>>(a);
+            if (a.n_in_pad == 4) { if (d4) CORR_XS(1, false, 4); else CORR_XS(1, false, 6); }
+            else { if (d4) CORR_XS(2, false, 4); else CORR_XS(2, false, 6); }
         }
+#undef CORR_XS
         return;
     }
     dim3 grid((a.n_chan + 127) / 128, a.nt, a.n_groups);

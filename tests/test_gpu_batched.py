@@ -89,8 +89,8 @@ def test_autotune_is_bit_identical_and_cached(tmp_path):
     ref_v, ref_f = vis.clone(), flags.clone()
     cache = str(tmp_path / "tune.txt")
     c.autotune(xd, cache)
-    ring, spt = c.tuning()
-    assert ring in (32, 64, 128, 256) and spt in (0, 8, 16)
+    ring, spt, depth = c.tuning()
+    assert ring in (32, 64, 128, 256) and spt in (0, 8, 16) and depth in (4, 6)
     assert os.path.exists(cache) and len(open(cache).read().strip().splitlines()) == 1
     vis.zero_()
     flags.zero_()
@@ -100,7 +100,14 @@ def test_autotune_is_bit_identical_and_cached(tmp_path):
     # a second handle of the same shape takes the cached choice without timing
     c2, *_ = _member(9, 4, 512, 32)
     c2.autotune(xd, cache)
-    assert c2.tuning() == (ring, spt)
+    assert c2.tuning() == (ring, spt, depth)
+    # the X-engine depth alone does not change the results either
+    for d in (4, 6):
+        c.set_option("x_depth", d)
+        vis.zero_()
+        c.run_dev(xd, vis, flags)
+        torch.cuda.synchronize()
+        assert torch.equal(vis, ref_v)
     assert len(open(cache).read().strip().splitlines()) == 1
 
 

@@ -82,7 +82,7 @@ def test_streaming_workload_full_size_at_its_tuning():
     x = make_stream_torch(spec, device=DEV)
     c = Correlator(4, 2, n_chan, TAPS, n_int)
     c.autotune(x)
-    ring, spt = c.tuning()
+    ring, spt, _ = c.tuning()
     c.set_delays(spec.tau, spec.phi)
     n = c.n_integrations(S)
     assert n == 32
