@@ -60,9 +60,10 @@ enum {
 
 /* Precision of the X-engine (option "precision"). */
 enum { CORR_FP32 = 0, CORR_INT8 = 1, CORR_FP8 = 2 };
-/* Code layout of corr_gram_dev beside CORR_INT8 (int8 carried as BF16) and
- * CORR_FP8: int8 codes stored as bytes. */
-enum { CORR_INT8_BYTES = 3, CORR_INT8_WORDS = 4 };
+/* Code layouts of corr_gram_dev beside CORR_INT8 (int8 carried as BF16) and
+ * CORR_FP8 (e4m3 bytes): int8 codes stored as bytes, and the pipeline's code
+ * words of int8 or e4m3 codes. */
+enum { CORR_INT8_BYTES = 3, CORR_INT8_WORDS = 4, CORR_FP8_WORDS = 5 };
 
 /*
  * corr_create -- allocate a correlator.
@@ -284,6 +285,8 @@ int corr_flag_dev(corr_t h, const float* d_vis, int n_vis, uint8_t* d_flags, voi
  *                    the leading 2 n_in x 2 n_in block of each G[c] is
  *                    written; k_pitch is ignored, n_chan must be a multiple
  *                    of 4 and n_in <= 64.
+ *   dtype CORR_FP8_WORDS: the e4m3 pipeline's form -- code words as for
+ *                    CORR_INT8_WORDS holding e4m3 codes; FP32 sums.
  * d_G: [n_chan][128][128] FP32.  k_pitch must be a multiple of 128 and d_Q
  * 16-byte aligned (else CORR_EINVAL).  Runs on tcgen05 tensor cores with
  * TMA-staged operands; a stalled pipeline sets the status word read by

@@ -10,7 +10,7 @@ and streams.  Build the library with :func:`build` (nvcc, in-tree).
 from .corr import (  # noqa: F401
     Correlator, Group, FlagNet, CorrError, load_library, LIB_PATH, EXPORTED, tile_mad, calibrate,
     CORR_OK, CORR_EINVAL, CORR_ENOMEM, CORR_ECUDA, CORR_EAGAIN, CORR_ETIMEDOUT, CORR_ESTATE,
-    CORR_FP32, CORR_INT8, CORR_FP8, CORR_INT8_BYTES, CORR_INT8_WORDS,
+    CORR_FP32, CORR_INT8, CORR_FP8, CORR_INT8_BYTES, CORR_INT8_WORDS, CORR_FP8_WORDS,
 )
 
 

@@ -28,6 +28,7 @@ CORR_ESTATE = -6
 CORR_FP32, CORR_INT8, CORR_FP8 = 0, 1, 2
 CORR_INT8_BYTES = 3          # corr_gram_dev: int8 codes stored as bytes
 CORR_INT8_WORDS = 4          # corr_gram_dev: int8 code words [K][n_pairs][n_chan] (the pipeline's form)
+CORR_FP8_WORDS = 5           # corr_gram_dev: e4m3 code words, same layout
 
 # Every symbol the header declares (checked by the CPU test-suite).
 EXPORTED = [

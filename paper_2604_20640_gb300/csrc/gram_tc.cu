@@ -371,18 +371,20 @@ __global__ void __launch_bounds__(128 + kConvThreads, 1) gram_i8_kernel(const __
     }
 }
 
-// ---- int8 codes as the F-engine's code words ---------------------------------
+// ---- codes as the F-engine's code words -------------------------------------
 // The Gram matrices of an integration straight from the pair-major code
 // words C[t][pair][k] (bytes Re U_a, Im U_a, Re U_a+1, Im U_a+1 of input
 // pair (a, a+1), a = 2 pair), with no transpose into row-major codes first.
 // One CTA per four channels (their four 128 x 128 FP32 accumulators fill
 // TMEM's 512 columns), 384 threads: warp 0 lane 0 loads raw boxes of 4
 // channels x 32 pairs x 64 spectra (16 contiguous bytes per pair and
-// spectrum; pairs past the last read as zero) by 3D TMA; warps 4-11 widen
-// them into each channel's BF16 operand tile (Re of input a at row a, Im at
-// row N + a; 64 K-elements per 128-byte swizzled row, chunk q of row r at
-// (q ^ (r & 7)) x 16) and signal the MMA issuer (warp 1 lane 0); warps 0-3
-// read the accumulators out.  Rows from 2N up are never written: they meet
+// spectrum; pairs past the last, and spectra past K, read as zero) by 3D
+// TMA; warps 4-11 turn them into each channel's operand tile (Re of input a
+// at row a, Im at row N + a; 128 bytes of K per swizzled row, chunk q of row
+// r at (q ^ (r & 7)) x 16) and signal the MMA issuer (warp 1 lane 0); warps
+// 0-3 read the accumulators out.  int8 codes are widened to BF16 (exact), 64
+// spectra a tile; e4m3 codes are regrouped bytewise, 128 spectra a tile (two
+// raw boxes, kind::f8f6f4).  Rows from 2N up are never written: they meet
 // only Gram entries no visibility uses.
 constexpr int kWRawStages = 3;
 constexpr int kWConvStages = 2;
@@ -390,7 +392,7 @@ constexpr int kWChan = 4;                                   // channels per CTA
 constexpr int kWK = 64;                                     // spectra per stage
 constexpr int kWPairs = 32;                                 // pairs per box
 constexpr int kWRawBytes = kWK * kWPairs * kWChan * 4;      // 32 KiB
-constexpr int kWTileBytes = kRows * 128;                    // one channel's BF16 tile, 16 KiB
+constexpr int kWTileBytes = kRows * 128;                    // one channel's operand tile, 16 KiB
 constexpr int kWConvBytes = kWChan * kWTileBytes;           // 64 KiB
 constexpr uint32_t kWTmemCols = kWChan * 128;               // 512
 struct __align__(8) GramWShared {
@@ -403,6 +405,18 @@ struct __align__(8) GramWShared {
     int abort;
 };
 
+// Byte b of each of w0..w3 gathered into word b (byte m of it from w_m).
+__device__ __forceinline__ void bytes_transpose4(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3, uint32_t& o0,
+                                                 uint32_t& o1, uint32_t& o2, uint32_t& o3) {
+    const uint32_t t0 = __byte_perm(w0, w1, 0x5140u), t1 = __byte_perm(w0, w1, 0x7362u);
+    const uint32_t t2 = __byte_perm(w2, w3, 0x5140u), t3 = __byte_perm(w2, w3, 0x7362u);
+    o0 = __byte_perm(t0, t2, 0x5410u);
+    o1 = __byte_perm(t0, t2, 0x7632u);
+    o2 = __byte_perm(t1, t3, 0x5410u);
+    o3 = __byte_perm(t1, t3, 0x7632u);
+}
+
+template <bool FP8>
 __global__ void __launch_bounds__(128 + kConvThreads, 1) gram_w_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                        GramArgs A) {
     extern __shared__ __align__(1024) uint8_t gsm_raw[];
@@ -411,7 +425,11 @@ __global__ void __launch_bounds__(128 + kConvThreads, 1) gram_w_kernel(const __g
     GramWShared* sh = reinterpret_cast<GramWShared*>(raw + kWRawStages * kWRawBytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int quad = blockIdx.x;
-    const int num_k = (A.K + kWK - 1) / kWK;
+    // raw boxes per operand tile: 64 spectra of BF16 or 128 of e4m3 fill a
+    // tile's 128-byte rows (a last box wholly past K reads as zeros)
+    constexpr int kRawPerConv = FP8 ? 2 : 1;
+    const int num_conv = (A.K + kRawPerConv * kWK - 1) / (kRawPerConv * kWK);
+    const int num_raw = num_conv * kRawPerConv;
     const unsigned long long lim = A.wait_ns ? A.wait_ns : kWaitNs;
 
     if (threadIdx.x == 0) {
@@ -442,22 +460,28 @@ __global__ void __launch_bounds__(128 + kConvThreads, 1) gram_w_kernel(const __g
 
     if (warp == 0 && lane == 0) {
         // TMA producer of raw code-word boxes (with inject_stall it issues nothing)
-        for (int it = 0; it < (A.inject_stall ? 0 : num_k); ++it) {
+        for (int it = 0; it < (A.inject_stall ? 0 : num_raw); ++it) {
             const int s = it % kWRawStages;
             const uint32_t ph = (uint32_t)(it / kWRawStages) & 1u;
             if (!mbar_wait(&sh->raw_empty[s], ph ^ 1u, lim)) {
                 sh->abort = 1;
                 break;
             }
-            mbar_expect_tx(&sh->raw_full[s], kWRawBytes);
-            // x: channel 4 quad (16-byte aligned), y: pair 0, z: spectrum
-            tma_load_3d(raw + s * kWRawBytes, &tmap, &sh->raw_full[s], kWChan * quad, 0, it * kWK);
+            if (it * kWK >= A.K) {
+                // the e4m3 tile's second box wholly past K: nothing to load,
+                // the converters write zeros
+                mbar_arrive(&sh->raw_full[s]);
+            } else {
+                mbar_expect_tx(&sh->raw_full[s], kWRawBytes);
+                // x: channel 4 quad (16-byte aligned), y: pair 0, z: spectrum
+                tma_load_3d(raw + s * kWRawBytes, &tmap, &sh->raw_full[s], kWChan * quad, 0, it * kWK);
+            }
             issued = it + 1;
         }
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer: per stage and channel, four K = 16 steps over its tile
+        // MMA issuer: per tile and channel, four MMAs of 32 bytes of K
         bool ok = true;
-        for (int it = 0; it < num_k && ok; ++it) {
+        for (int it = 0; it < num_conv && ok; ++it) {
             const int c = it % kWConvStages;
             const uint32_t ph = (uint32_t)(it / kWConvStages) & 1u;
             if (!mbar_wait(&sh->conv_full[c], ph, lim)) {
@@ -471,7 +495,7 @@ __global__ void __launch_bounds__(128 + kConvThreads, 1) gram_w_kernel(const __g
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
                     const uint64_t d = d0 + (uint64_t)((kk * 32) >> 4);
-                    mma<false>(tmem + (uint32_t)(ch * 128), d, d, (it | kk) != 0 ? 1u : 0u);
+                    mma<FP8>(tmem + (uint32_t)(ch * 128), d, d, (it | kk) != 0 ? 1u : 0u);
                 }
             }
             mma_commit(&sh->conv_empty[c]);
@@ -479,10 +503,10 @@ __global__ void __launch_bounds__(128 + kConvThreads, 1) gram_w_kernel(const __g
         if (!ok) sh->abort = 1;
         mma_commit(&sh->accum);
     } else if (warp >= 4) {
-        // converters: thread (ch, p, half) widens the four rows of input pair
+        // converters: thread (ch, p, half) fills the four rows of input pair
         // p in channel ch for the spectrum blocks of its parity (8 spectra a
-        // block), visited in an order rotated by channel so lanes of one
-        // store phase write different chunks
+        // block as BF16, 16 as e4m3), visited in an order rotated by channel
+        // so lanes of one store phase write different chunks
         const int cv = (int)threadIdx.x - 128;
         const int ch = cv & 3, p = (cv >> 2) & 31, tb0 = cv >> 7;
         const int N = A.n_in;
@@ -494,40 +518,67 @@ __global__ void __launch_bounds__(128 + kConvThreads, 1) gram_w_kernel(const __g
             has[b] = a < N;
             row[b] = (b & 1) ? N + a : a;
         }
-        for (int it = 0; it < num_k; ++it) {
-            const int s = it % kWRawStages, c = it % kWConvStages;
+        for (int it = 0; it < num_raw; ++it) {
+            // raw box it fills half h of tile ct (all of it for BF16)
+            const int ct = it / kRawPerConv, h = it % kRawPerConv;
+            const int s = it % kWRawStages, c = ct % kWConvStages;
             bool ok = mbar_wait(&sh->raw_full[s], (uint32_t)(it / kWRawStages) & 1u, lim);
-            ok = ok && mbar_wait(&sh->conv_empty[c], ((uint32_t)(it / kWConvStages) & 1u) ^ 1u, lim);
+            ok = ok && mbar_wait(&sh->conv_empty[c], ((uint32_t)(ct / kWConvStages) & 1u) ^ 1u, lim);
             if (!converters_all(ok)) {
                 if (cv == 0) sh->abort = 1;
                 break;
             }
             const uint32_t* rw = reinterpret_cast<const uint32_t*>(raw + s * kWRawBytes);
             uint8_t* tile = conv + c * kWConvBytes + ch * kWTileBytes;
+            if constexpr (FP8) {
+                // e4m3 bytes as they are: 16 spectra of one row per 16-byte
+                // chunk, in spectrum order; chunk 4h + j of the row
+                const bool past = it * kWK >= A.K;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int tb = (tb0 + 2 * k + 2 * ch) & 7;
-                uint32_t w[8];
+                for (int k = 0; k < 2; ++k) {
+                    const int j = (tb0 + 2 * k + ch) & 3;
+                    uint32_t w[16];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) w[i] = rw[((tb * 8 + i) * kWPairs + p) * kWChan + ch];
+                    for (int i = 0; i < 16; ++i) w[i] = past ? 0u : rw[((j * 16 + i) * kWPairs + p) * kWChan + ch];
+                    uint32_t o[4][4];
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    if (!has[b]) continue;
-                    uint32_t o[4];
+                    for (int g = 0; g < 4; ++g)
+                        bytes_transpose4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3], o[0][g], o[1][g],
+                                         o[2][g], o[3][g]);
+                    const int q = 4 * h + j;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        // byte b of spectra 2q and 2q + 1 -> low, high BF16
-                        const uint32_t x = __byte_perm(w[2 * q], w[2 * q + 1], (uint32_t)(b | ((4 + b) << 4)));
-                        o[q] = bf16x2_of_codes(x ^ 0x80808080u, 0);
+                    for (int b = 0; b < 4; ++b) {
+                        if (!has[b]) continue;
+                        *reinterpret_cast<uint4*>(tile + row[b] * 128 + ((q ^ (row[b] & 7)) << 4)) =
+                            make_uint4(o[b][0], o[b][1], o[b][2], o[b][3]);
                     }
-                    *reinterpret_cast<uint4*>(tile + row[b] * 128 + ((tb ^ (row[b] & 7)) << 4)) =
-                        make_uint4(o[0], o[1], o[2], o[3]);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int tb = (tb0 + 2 * k + 2 * ch) & 7;
+                    uint32_t w[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) w[i] = rw[((tb * 8 + i) * kWPairs + p) * kWChan + ch];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        if (!has[b]) continue;
+                        uint32_t o[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            // byte b of spectra 2q and 2q + 1 -> low, high BF16
+                            const uint32_t x = __byte_perm(w[2 * q], w[2 * q + 1], (uint32_t)(b | ((4 + b) << 4)));
+                            o[q] = bf16x2_of_codes(x ^ 0x80808080u, 0);
+                        }
+                        *reinterpret_cast<uint4*>(tile + row[b] * 128 + ((tb ^ (row[b] & 7)) << 4)) =
+                            make_uint4(o[0], o[1], o[2], o[3]);
+                    }
                 }
             }
             fence_proxy_async_smem();
             converters_sync();
             if (cv == 0) {
-                mbar_arrive(&sh->conv_full[c]);
+                if (h == kRawPerConv - 1) mbar_arrive(&sh->conv_full[c]);
                 mbar_arrive(&sh->raw_empty[s]);
             }
         }
@@ -597,7 +648,7 @@ int launch_gram(const GramArgs& a, cudaStream_t st) {
     if (a.n_chan <= 0 || a.K <= 0) return CORR_OK;
     if (a.words) {
         // code words C[t][pair][k]: 3D map (k, pair, t) of 32-bit words
-        if (a.fp8 || (a.n_chan % kWChan) != 0 || a.n_pairs < 1 || a.n_pairs > kWPairs || a.n_in < 1 ||
+        if ((a.n_chan % kWChan) != 0 || a.n_pairs < 1 || a.n_pairs > kWPairs || a.n_in < 1 ||
             a.n_in > 2 * a.n_pairs)
             return CORR_EINVAL;
         if ((reinterpret_cast<uintptr_t>(a.Q) & 15) != 0) return CORR_EINVAL;
@@ -613,14 +664,16 @@ int launch_gram(const GramArgs& a, cudaStream_t st) {
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return CORR_EINVAL;
         const size_t smem = gram_w_smem_bytes();
-        static bool attrw = false;
-        if (!attrw) {
-            if (cudaFuncSetAttribute(gram_w_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                cudaSuccess)
+        static bool attrw[2] = {false, false};
+        if (!attrw[a.fp8]) {
+            const void* fn = a.fp8 ? reinterpret_cast<const void*>(gram_w_kernel<true>)
+                                   : reinterpret_cast<const void*>(gram_w_kernel<false>);
+            if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
                 return CORR_ECUDA;
-            attrw = true;
+            attrw[a.fp8] = true;
         }
-        gram_w_kernel<<<a.n_chan / kWChan, 128 + kConvThreads, smem, st>>>(map, a);
+        if (a.fp8) gram_w_kernel<true><<<a.n_chan / kWChan, 128 + kConvThreads, smem, st>>>(map, a);
+        else gram_w_kernel<false><<<a.n_chan / kWChan, 128 + kConvThreads, smem, st>>>(map, a);
         return CORR_OK;
     }
     if (a.i8b) {

@@ -1,15 +1,16 @@
 // Requantiser and rescaling around the tensor-core X-engine.
 //
-// int8 pipeline: words_from_spectra_kernel turns channelised spectra (U =
-// 2Y, unrotated, in the pair-major ring [slot][pair][n_chan] float4) into
-// the integration's code words C[t][pair][k] -- the form the fused F-engine
-// writes itself once the scales are fixed, and the form gram_w_kernel reads.
-// e4m3 pipeline and stage calls: requant_pm_kernel turns the spectra, or the
-// code words the fused F-engine made from them, into the stacked operand
-// Q[k][row][t]: row a holds Re U_a / sigma_a[k], row N + a holds Im U_a /
-// sigma_a[k], t the spectrum index inside the integration; int8 codes (round
-// half to even, saturate at +-127) as bytes or carried as BF16, or e4m3
-// (satfinite) bytes.  A thread owns one input pair and channel over a run
+// Pipeline: words_from_spectra_kernel turns channelised spectra (U = 2Y,
+// unrotated, in the pair-major ring [slot][pair][n_chan] float4) into the
+// integration's int8 or e4m3 code words C[t][pair][k] -- the form the fused
+// F-engine writes itself once the scales are fixed, and the form
+// gram_w_kernel reads.
+// Stage calls and channel counts not a multiple of 4: requant_pm_kernel
+// turns the spectra, or code words the fused F-engine made from them, into
+// the stacked operand Q[k][row][t]: row a holds Re U_a / sigma_a[k], row
+// N + a holds Im U_a / sigma_a[k], t the spectrum index inside the
+// integration; int8 codes (round half to even, saturate at +-127) as bytes
+// or carried as BF16, or e4m3 (satfinite) bytes.  A thread owns one input pair and channel over a run
 // of spectra, so reads coalesce across channels and every row gets whole
 // 32-byte sectors of codes.
 // The scales are fixed for a whole integration: the first integration of a
@@ -116,11 +117,12 @@ __global__ void __launch_bounds__(128) requant_pm_kernel(const RequantArgs A) {
     }
 }
 
-// Spectra of the pair-major ring into int8 code words C[t][pair][k] (bytes
-// Re U_a, Im U_a, Re U_a+1, Im U_a+1; t = s - int_start): the words the
-// fused F-engine writes once the scales are fixed, made here from the
+// Spectra of the pair-major ring into int8 or e4m3 code words C[t][pair][k]
+// (bytes Re U_a, Im U_a, Re U_a+1, Im U_a+1; t = s - int_start): the words
+// the fused F-engine writes once the scales are fixed, made here from the
 // spectra it wrote before (same arithmetic, same codes).  One thread per
 // (channel, pair, spectrum).
+template <bool FP8>
 __global__ void __launch_bounds__(128) words_from_spectra_kernel(const RequantArgs A) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int pr = blockIdx.y;
@@ -134,8 +136,8 @@ __global__ void __launch_bounds__(128) words_from_spectra_kernel(const RequantAr
     const float inv1 = a1 < N ? inv[(size_t)a1 * A.n_chan + k] : 0.f;
     const long long slot = (s - A.v_origin) & A.v_mask;
     const float4 u = __ldg(reinterpret_cast<const float4*>(A.V) + ((size_t)slot * n_pairs + pr) * A.n_chan + k);
-    const uint32_t w = q_code<false>(u.x * inv0) | (q_code<false>(u.y * inv0) << 8) |
-                       (q_code<false>(u.z * inv1) << 16) | (q_code<false>(u.w * inv1) << 24);
+    const uint32_t w = q_code<FP8>(u.x * inv0) | (q_code<FP8>(u.y * inv0) << 8) |
+                       (q_code<FP8>(u.z * inv1) << 16) | (q_code<FP8>(u.w * inv1) << 24);
     A.C[((size_t)(s - A.int_start) * n_pairs + pr) * A.n_chan + k] = w;
 }
 
@@ -210,7 +212,8 @@ void launch_requant(const RequantArgs& a, cudaStream_t st) {
     if (n <= 0) return;
     if (a.C) {
         dim3 grid((unsigned)((a.n_chan + 127) / 128), (unsigned)(a.n_in_pad / 2), (unsigned)n);
-        words_from_spectra_kernel<<<grid, 128, 0, st>>>(a);
+        if (a.fp8) words_from_spectra_kernel<true><<<grid, 128, 0, st>>>(a);
+        else words_from_spectra_kernel<false><<<grid, 128, 0, st>>>(a);
         return;
     }
     const int run = a.codes_in ? 64 : (a.fp8 || a.i8b) ? 32 : 16;

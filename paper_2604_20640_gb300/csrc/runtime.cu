@@ -43,8 +43,8 @@ struct Pipe {
     float* scale = nullptr;   // [n_in_pad][n_chan], fixed per integration
     bool have_scale = false;  // false until the first integration's pre-pass
     bool ring_codes = false;  // the unrequantised ring slots hold the F-engine's code words
-    // int8: the integration's code words C[t][pair][n_chan] (bytes Re a, Im a,
-    // Re a+1, Im a+1), read by the Gram kernel directly (no Q)
+    // the integration's int8 or e4m3 code words C[t][pair][n_chan] (bytes
+    // Re a, Im a, Re a+1, Im a+1), read by the Gram kernel directly (no Q)
     uint32_t* C = nullptr;
     bool words = false;
 };
@@ -411,14 +411,14 @@ int alloc_pipe_impl(corr_t h, Pipe& p) {
     CKA(dmalloc(h, &p.V, per_spec * (size_t)p.v_cap));
     CKA(dmalloc(h, &p.Z, per_spec * (size_t)p.v_cap));
     if (h->precision != CORR_FP32) {
-        p.words = h->precision == CORR_INT8 && (h->n_chan % 4) == 0;
+        p.words = (h->n_chan % 4) == 0;
         if (p.words) {
-            // int8: one 32-bit word of four codes per (spectrum, pair, channel)
+            // one 32-bit word of four codes per (spectrum, pair, channel)
             const size_t cbytes = sizeof(uint32_t) * (size_t)h->n_int * (h->n_in_pad / 2) * h->n_chan;
             CKA(dmalloc(h, &p.C, cbytes));
             CK(cudaMemset(p.C, 0, cbytes));
         } else {
-            // e4m3: one byte per code, rows of K
+            // one byte per code, rows of K
             p.q_pitch = (int)(((long long)h->n_int + 127) / 128 * 128);
             const size_t qbytes = (size_t)h->n_chan * 128 * p.q_pitch;
             CKA(dmalloc(h, &p.Q, qbytes));
@@ -584,9 +584,9 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
         bool progress = false;
         long long s_end = ready_end;
         if (s_end > iend) s_end = iend;
-        // the ring bounds a launch, except where the F-engine writes int8
-        // code words straight into the integration's word buffer (then one
-        // launch may cover the rest of the integration)
+        // the ring bounds a launch, except where the F-engine writes code
+        // words straight into the integration's word buffer (then one launch
+        // may cover the rest of the integration)
         const bool to_words = p.words && p.have_scale && p.s_xdone == p.s_next && fused_codes(h, sv);
         if (!to_words && s_end > p.s_xdone + p.v_cap) s_end = p.s_xdone + p.v_cap;
         if (s_end > p.s_next) {
@@ -597,9 +597,9 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
             const bool codes = p.have_scale && p.s_xdone == p.s_next && fused_codes(h, sv);
             p.ring_codes = codes && !p.words;
             if (to_words) {
-                // int8: the words go straight into the integration's C at
+                // the words go straight into the integration's C at
                 // t = s - istart, where the Gram kernel reads them
-                const CodeOut q{p.scale + (size_t)h->n_in_pad * h->n_chan, false};
+                const CodeOut q{p.scale + (size_t)h->n_in_pad * h->n_chan, h->precision == CORR_FP8};
                 CKRET(launch_f(h, sv, t, p.Z, 0, p.v_cap - 1, reinterpret_cast<float2*>(p.C), istart, -1LL,
                                nullptr, p.s_next, s_end, st, nullptr, 0, 0, &q));
                 p.s_xdone = s_end;
@@ -1552,16 +1552,17 @@ int corr_gram_dev(corr_t h, const void* d_Q, int n_chan, int k_pitch, int K, int
     if (!h) return fail(h, CORR_EINVAL, "NULL handle");
     DeviceGuard g(h->dev);
     if (!d_Q || !d_G || n_chan < 1 || K < 1 ||
-        (dtype != CORR_INT8 && dtype != CORR_FP8 && dtype != CORR_INT8_BYTES && dtype != CORR_INT8_WORDS))
+        (dtype != CORR_INT8 && dtype != CORR_FP8 && dtype != CORR_INT8_BYTES && dtype != CORR_INT8_WORDS &&
+         dtype != CORR_FP8_WORDS))
         return fail(h, CORR_EINVAL, "bad argument");
     GramArgs a{};
     a.Q = d_Q;
     a.n_chan = n_chan;
     a.K = K;
     a.k_pitch = k_pitch;
-    a.fp8 = dtype == CORR_FP8;
+    a.fp8 = dtype == CORR_FP8 || dtype == CORR_FP8_WORDS;
     a.i8b = dtype == CORR_INT8_BYTES;
-    a.words = dtype == CORR_INT8_WORDS;
+    a.words = dtype == CORR_INT8_WORDS || dtype == CORR_FP8_WORDS;
     a.n_pairs = h->n_in_pad / 2;
     a.n_in = h->n_in;
     a.G = d_G;

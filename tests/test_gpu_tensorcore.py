@@ -160,6 +160,36 @@ def test_int8_word_gram_bit_exact(n_in, n_chan, K):
     np.testing.assert_array_equal(G[:, :n2, :n2], ref[:, :n2, :n2].astype(np.float64))
 
 
+@pytest.mark.parametrize("n_in,n_chan,K", [(64, 8, 1024), (20, 12, 100), (7, 4, 64), (64, 1024, 320), (33, 16, 1)])
+def test_e4m3_word_gram(n_in, n_chan, K):
+    """The e4m3 pipeline's form: the same code words holding e4m3 bytes, 128
+    spectra an operand tile (two raw boxes; a box wholly past K is zeros).
+    Against the exact Gram of the decoded codes within the FP32 summation
+    bound, and bit for bit against the row-major e4m3 Gram of the same codes
+    (same spectra in the same order through the same MMA steps) on the
+    2N x 2N block the visibilities use."""
+    from paper_2604_20640_gb300 import Correlator, CORR_FP8, CORR_FP8_WORDS
+    rng = np.random.default_rng(n_in * 1000 + n_chan + K + 5)
+    finite = np.array([b for b in range(256) if (b & 0x7F) != 0x7F], np.int64)   # no NaN codes
+    q_re = rng.choice(finite, size=(n_in, K, n_chan))
+    q_im = rng.choice(finite, size=(n_in, K, n_chan))
+    W = _words(q_re, q_im)
+    c = Correlator(n_in, 1, 64, 4, 16)
+    G = _run_gram(c, W.view(np.uint8).reshape(-1), n_chan, 0, K, CORR_FP8_WORDS)
+    k_pitch = (K + 127) // 128 * 128
+    Qb = np.zeros((n_chan, 128, k_pitch), np.uint8)
+    Qb[:, :n_in, :K] = q_re.transpose(2, 0, 1)
+    Qb[:, n_in:2 * n_in, :K] = q_im.transpose(2, 0, 1)
+    G_rm = _run_gram(c, Qb, n_chan, k_pitch, K, CORR_FP8)
+    c.close()
+    n2 = 2 * n_in
+    dec = rq.e4m3_decode(Qb[:, :n2, :K])
+    ref = rq.gram(dec)
+    bound = K * 2.0 ** -24 * rq.gram(np.abs(dec))
+    assert np.all(np.abs(G[:, :n2, :n2] - ref) <= bound + 1e-30)
+    np.testing.assert_array_equal(G[:, :n2, :n2], G_rm[:, :n2, :n2])
+
+
 def test_int8_word_gram_rejects_bad_layout():
     from paper_2604_20640_gb300 import Correlator, CorrError, CORR_EINVAL, CORR_INT8_WORDS
     c = Correlator(8, 1, 64, 4, 16)
