@@ -123,9 +123,9 @@ const char* corr_last_error(corr_t h);
  *                  rings and the dynamic spectra, M = 8192 for the stage
  *                  call -- else as FIR + FFT; results are bit-identical.
  *                  With reduced precision the fused kernel also makes the
- *                  int8 / e4m3 codes once an integration's scales are fixed
- *                  (the requantiser then only transposes them); the codes
- *                  equal the requantiser's
+ *                  int8 / e4m3 code words once an integration's scales are
+ *                  fixed, straight into the words the tensor-core X-engine
+ *                  reads; the codes equal the requantiser's
  *   "sample_bits"  (8, default; or 16)  input sample type of every call that
  *                  takes samples: int8 (the 8-bit truncated recorder mode of
  *                  Sec. 3) or little-endian int16 (the 16-bit padded mode,
@@ -275,16 +275,17 @@ int corr_flag_dev(corr_t h, const float* d_vis, int n_vis, uint8_t* d_flags, voi
  *   dtype CORR_FP8:  e4m3 bytes; FP32 sums.
  *   dtype CORR_INT8_BYTES: int8 codes as bytes (1 byte each), widened to
  *                    BF16 on chip (exact), then as CORR_INT8.
- *   dtype CORR_INT8_WORDS: the form the int8 pipeline uses -- d_Q holds code
- *                    words [K][n_pairs][n_chan] uint32, n_pairs = n_in_pad /
- *                    2 (the handle's n_in rounded up to a multiple of 4;
- *                    words of pairs past the last input are ignored), the
- *                    bytes of word (t, p, c) being the codes of Re V_2p, Im
- *                    V_2p, Re V_2p+1, Im V_2p+1 (low byte first); rows as
- *                    above (row a = Re of input a, row n_in + a = Im); only
- *                    the leading 2 n_in x 2 n_in block of each G[c] is
- *                    written; k_pitch is ignored, n_chan must be a multiple
- *                    of 4 and n_in <= 64.
+ *   dtype CORR_INT8_WORDS: the form the int8 pipeline uses (n_chan a
+ *                    multiple of 4) -- d_Q holds code words [K][n_pairs]
+ *                    [n_chan] uint32, n_pairs = n_in_pad / 2 (the handle's
+ *                    n_in rounded up to a multiple of 4; words of pairs
+ *                    past the last input are ignored), the bytes of word
+ *                    (t, p, c) being the codes of Re V_2p, Im V_2p, Re
+ *                    V_2p+1, Im V_2p+1 (low byte first); rows as above (row
+ *                    a = Re of input a, row n_in + a = Im); only the leading
+ *                    2 n_in x 2 n_in block of each G[c] is written; k_pitch
+ *                    is ignored, n_chan must be a multiple of 4 and n_in <=
+ *                    64.
  *   dtype CORR_FP8_WORDS: the e4m3 pipeline's form -- code words as for
  *                    CORR_INT8_WORDS holding e4m3 codes; FP32 sums.
  * d_G: [n_chan][128][128] FP32.  k_pitch must be a multiple of 128 and d_Q
