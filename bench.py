@@ -59,7 +59,7 @@ WORKLOADS = {
 STAGES = ["fir", "fft", "xengine", "finalize", "flag", "requant", "gram"]
 KERNELS = {"fir": "fir_kernel<4>", "fft": "fft_kernel<M,3>", "xengine": "xengine_kernel",
            "finalize": "finalize_kernel", "flag": "mad_flag_kernel", "requant": "requant_pm_kernel",
-           "gram": "gram_w_kernel (tcgen05, int8 code words widened on chip)"}
+           "gram": "gram_w_kernel (tcgen05 over the F-engine's code words, visibilities in its epilogue)"}
 # Algorithmic bytes per input sample of each hot-path kernel, in the unit the
 # scope table's measurement section fixes: the whole hot path (PFB, FFT,
 # delays, X-engine, flagging) reads each int8 input sample once (1 B); on the

@@ -476,7 +476,9 @@ long long corr_kernel_launches(corr_t h);
  * n_stages entries, at most 7; the dynamic spectra of
  * corr_spectrogram_dev are accumulated by the FFT kernel; with at most 8
  * inputs and flag windows of at most 64 channels the FP32 path makes the
- * flags in the finalisation launch, stage 3), the milliseconds and
+ * flags in the finalisation launch, stage 3; with reduced precision and a
+ * channel count that is a multiple of 4 the Gram launch, stage 6, also
+ * finalises), the milliseconds and
  * launch counts accumulated since the previous call, then clears them.
  * ms / counts may be NULL.
  */

@@ -177,9 +177,15 @@ struct GramArgs {
     unsigned long long wait_ns;   // limit of each bounded wait (0: the 2 s default)
     int inject_stall;             // fault injection: the producer issues no loads
     int i8b;                      // int8 codes stored as bytes (widened to BF16 on chip)
-    // int8 code words C[t][pair][k] (Q points at them; K spectra, n_pairs
-    // pairs of n_in inputs): Gram straight from the F-engine's words
+    // int8 or e4m3 code words C[t][pair][k] (Q points at them; K spectra,
+    // n_pairs pairs of n_in inputs): Gram straight from the F-engine's words
     int words, n_pairs, n_in;
+    // words only: with R set the kernel writes the visibilities R[k][a][b]
+    // (the finalisation: scales [n_in_pad][n_chan], count = K, optional
+    // rotation phasors) instead of G
+    float2* R;
+    const float* scale;
+    const float2* rot;
 };
 
 // Requantise spectra [s_begin, s_end) of the pair-major ring V (U = 2Y,

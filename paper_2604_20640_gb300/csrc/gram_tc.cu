@@ -22,6 +22,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include "finq.cuh"
 #include "tc_common.cuh"
 
 #include <cstdio>
@@ -385,7 +386,8 @@ __global__ void __launch_bounds__(128 + kConvThreads, 1) gram_i8_kernel(const __
 // 0-3 read the accumulators out.  int8 codes are widened to BF16 (exact), 64
 // spectra a tile; e4m3 codes are regrouped bytewise, 128 spectra a tile (two
 // raw boxes, kind::f8f6f4).  Rows from 2N up are never written: they meet
-// only Gram entries no visibility uses.
+// only Gram entries no visibility uses.  The epilogue stores the 2N x 2N
+// block of each G, or (the pipeline) finalises it into visibilities.
 constexpr int kWRawStages = 3;
 constexpr int kWConvStages = 2;
 constexpr int kWChan = 4;                                   // channels per CTA
@@ -590,6 +592,53 @@ __global__ void __launch_bounds__(128 + kConvThreads, 1) gram_w_kernel(const __g
     if (sh->abort) {
         if (threadIdx.x == 0 && A.status) atomicExch(A.status, CORR_ETIMEDOUT);
         if (warp == 0 && lane == 0) drain_loads(sh->raw_full, kWRawStages, issued, lim);
+    } else if (A.R) {
+        // the finalisation in place, a channel at a time: the 2N x 2N block
+        // goes to shared memory (row pitch 2N + 1: conflict-free by rows and
+        // by columns; the operand stages are free now) -- warps w, w + 4,
+        // w + 8 share TMEM lane quarter w and split its 32-column chunks --
+        // with the channel's scales and phasors; then every thread makes
+        // visibilities, output (a, b) from the entries of (min, max) so that
+        // both triangles are stored in order
+        float* __restrict__ Gs = reinterpret_cast<float*>(conv);
+        float* __restrict__ sS = Gs + kRows * (kRows + 1);
+        float2* __restrict__ sQ = reinterpret_cast<float2*>(sS + 64);
+        const int N = A.n_in, n2 = 2 * N, pitch = n2 + 1;
+        const float inv4c = 1.0f / (4.0f * (float)A.K);
+        const int lq = warp & 3, part = warp >> 2;
+#pragma unroll 1
+        for (int ch = 0; ch < kWChan; ++ch) {
+            const int k = kWChan * quad + ch;
+            if (lq * 32 < n2) {
+                const int r = lq * 32 + lane;
+#pragma unroll 1
+                for (int c0 = part * 32; c0 < n2; c0 += 96) {
+                    uint32_t rr[32];
+                    tmem_ld32(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(ch * 128 + c0), rr);
+                    if (r < n2) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            if (c0 + i < n2) Gs[r * pitch + c0 + i] = __uint_as_float(rr[i]);
+                    }
+                }
+            }
+            for (int a = (int)threadIdx.x; a < N; a += (int)blockDim.x) {
+                sS[a] = __ldg(A.scale + (size_t)a * A.n_chan + k);
+                if (A.rot) sQ[a] = __ldg(A.rot + (size_t)a * A.n_chan + k);
+            }
+            __syncthreads();
+            float2* __restrict__ R = A.R + (size_t)k * N * N;
+#pragma unroll 4
+            for (int idx = (int)threadIdx.x; idx < N * N; idx += (int)blockDim.x) {
+                const int a = idx / N, b = idx - a * N;
+                const int lo = a < b ? a : b, hi = a < b ? b : a;
+                const float2 v = vis_from_gram(Gs[lo * pitch + hi], Gs[(N + lo) * pitch + N + hi],
+                                               Gs[(N + lo) * pitch + hi], Gs[lo * pitch + N + hi], sS[lo], sS[hi],
+                                               inv4c, lo == hi, A.rot ? sQ + lo : nullptr, sQ + hi);
+                R[idx] = a <= b ? v : make_float2(v.x, -v.y);
+            }
+            __syncthreads();
+        }
     } else if (warp < 4 && warp * 32 < 2 * A.n_in) {
         // only the 2N x 2N block the visibilities use is written (in 32-column
         // pieces); the TMEM loads are warp-wide, the stores per row

@@ -19,6 +19,7 @@
 #include "corr.h"
 #include "corr_internal.h"
 
+#include "finq.cuh"
 #include "quant.cuh"
 
 #include <cuda_bf16.h>
@@ -177,31 +178,19 @@ __global__ void finalize_q_kernel(const FinQArgs F) {
     const int k = blockIdx.x;
     const int N = F.n_in;
     const size_t gbase = (size_t)k * 128 * 128;
+    const float inv4c = 1.0f / (4.0f * (float)F.count);
     for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
         const int a = idx / N, b = idx % N;
         if (a > b) continue;
         const float* G = reinterpret_cast<const float*>(F.G) + gbase;
-        const float cre = G[a * 128 + b] + G[(N + a) * 128 + N + b];
-        const float cim = G[(N + a) * 128 + b] - G[a * 128 + N + b];
-        const float sc = F.scale[(size_t)a * F.n_chan + k] * F.scale[(size_t)b * F.n_chan + k] /
-                         (4.0f * (float)F.count);
-        float re = cre * sc, im = cim * sc;
+        const float2* qa = F.rot ? F.rot + (size_t)a * F.n_chan + k : nullptr;
+        const float2* qb = F.rot ? F.rot + (size_t)b * F.n_chan + k : nullptr;
+        const float2 v = vis_from_gram(G[a * 128 + b], G[(N + a) * 128 + N + b], G[(N + a) * 128 + b],
+                                       G[a * 128 + N + b], F.scale[(size_t)a * F.n_chan + k],
+                                       F.scale[(size_t)b * F.n_chan + k], inv4c, a == b, qa, qb);
         float2* R = F.R + (size_t)k * N * N;
-        if (a == b) {
-            R[a * N + a] = make_float2(re, 0.f);
-            continue;
-        }
-        if (F.rot) {
-            const float2 qa = F.rot[(size_t)a * F.n_chan + k];
-            const float2 qb = F.rot[(size_t)b * F.n_chan + k];
-            const float pr = qa.x * qb.x + qa.y * qb.y;
-            const float pi = qa.y * qb.x - qa.x * qb.y;
-            const float r2 = re * pr - im * pi;
-            im = re * pi + im * pr;
-            re = r2;
-        }
-        R[a * N + b] = make_float2(re, im);
-        R[b * N + a] = make_float2(re, -im);
+        R[a * N + b] = v;
+        if (a != b) R[b * N + a] = make_float2(v.x, -v.y);
     }
 }
 

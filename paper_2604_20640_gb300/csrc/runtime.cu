@@ -424,7 +424,9 @@ int alloc_pipe_impl(corr_t h, Pipe& p) {
             CKA(dmalloc(h, &p.Q, qbytes));
             CK(cudaMemset(p.Q, 0, qbytes));
         }
-        CKA(dmalloc(h, &p.G, sizeof(float) * (size_t)h->n_chan * 128 * 128));
+        // Gram matrices (the row-major form only: the word form's Gram
+        // kernel writes the visibilities itself)
+        if (!p.words) CKA(dmalloc(h, &p.G, sizeof(float) * (size_t)h->n_chan * 128 * 128));
         // scales, then their inverses (the requantiser's multipliers)
         CKA(dmalloc(h, &p.scale, 2 * sizeof(float) * (size_t)h->n_in_pad * h->n_chan));
         p.have_scale = false;
@@ -717,7 +719,9 @@ int finalize_into(corr_t h, Pipe& p, const Tables& t, float2* R, uint8_t* F, int
                   cudaStream_t st) {
     if (h->precision != CORR_FP32) {
         // Tensor-core Gram of the integration's codes, then rescale and
-        // rotate; the autocorrelations fix the next integration's scales.
+        // rotate (in the Gram kernel's epilogue for the code words, by
+        // finalize_q_kernel for row-major codes); the autocorrelations fix
+        // the next integration's scales.
         GramArgs g{};
         g.Q = p.words ? static_cast<const void*>(p.C) : static_cast<const void*>(p.Q);
         g.words = p.words;
@@ -732,6 +736,11 @@ int finalize_into(corr_t h, Pipe& p, const Tables& t, float2* R, uint8_t* F, int
         g.wait_ns = (unsigned long long)(h->tc_wait_ms * 1e6);
         g.inject_stall = h->inject_stall;
         g.i8b = h->precision == CORR_INT8;
+        if (p.words) {
+            g.R = R;
+            g.scale = p.scale;
+            g.rot = t.rot;
+        }
         int rc;
         {
             Timed t_(h, 6, st);
@@ -739,20 +748,22 @@ int finalize_into(corr_t h, Pipe& p, const Tables& t, float2* R, uint8_t* F, int
         }
         if (rc != CORR_OK) return fail(h, rc, "tensor-core Gram launch failed");
         CK(cudaGetLastError());
-        FinQArgs f{};
-        f.G = p.G;
-        f.scale = p.scale;
-        f.rot = t.rot;
-        f.n_chan = h->n_chan;
-        f.n_in = h->n_in;
-        f.count = count;
-        f.fp8 = g.fp8;
-        f.R = R;
-        {
-            Timed t_(h, 3, st);
-            launch_finalize_q(f, st);
+        if (!p.words) {
+            FinQArgs f{};
+            f.G = p.G;
+            f.scale = p.scale;
+            f.rot = t.rot;
+            f.n_chan = h->n_chan;
+            f.n_in = h->n_in;
+            f.count = count;
+            f.fp8 = g.fp8;
+            f.R = R;
+            {
+                Timed t_(h, 3, st);
+                launch_finalize_q(f, st);
+            }
+            CK(cudaGetLastError());
         }
-        CK(cudaGetLastError());
         launch_scale_from_vis(R, h->n_in, h->n_in_pad, h->n_chan, g.fp8 ? kFp8Gain : kInt8Gain, p.scale, st);
         ++h->launches;
         CK(cudaGetLastError());
