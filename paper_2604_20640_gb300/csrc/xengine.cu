@@ -261,17 +261,21 @@ __global__ void __launch_bounds__(128) finalize_kernel(const FinArgs F) {
 }
 
 // ---- MAD flagging, Eq. 2 ------------------------------------------------
-// One warp per (integration, window, baseline a <= b).  Order statistics are
-// exact: the warp sorts the window's W values (E = max(W, 32) / 32 per lane,
-// element i = lane E + e, padding +inf) with a bitonic network -- exchanges
-// between registers below distance E, by shuffles above -- and reads the
-// median from the sorted order (even count: mean of the two middle values),
-// then sorts |A - med| the same way for the MAD.
+// An item is one (integration, window, baseline a <= b).  Its W values are
+// spread over a group of L lanes (L a power of two dividing 32; E values a
+// lane, element i = (lane mod L) E + e, padding +inf) and sorted exactly by
+// a bitonic network -- exchanges between registers below distance E, by
+// shuffles inside the group above -- the median read from the sorted order
+// (even count: mean of the two middle values), then |A - med| sorted the
+// same way for the MAD.  L = 32 (a warp an item) where a call has few items;
+// L = 8 where it has many (more items a warp, fewer shuffles).  Every form
+// gives the same order statistics and the same threshold bits.
 constexpr int kFlagWarps = 4;
 
-template <int E>
-__device__ __forceinline__ void warp_bitonic_stage(float (&v)[E], int lane, int k) {
+template <int E, int L>
+__device__ __forceinline__ void group_bitonic_stage(float (&v)[E], int lane, int k) {
     // merge step of size k: element i pairs with i ^ j, ascending where i & k == 0
+    const int gl = lane & (L - 1);
 #pragma unroll
     for (int j = k >> 1; j > 0; j >>= 1) {
         if (j < E) {
@@ -279,7 +283,7 @@ __device__ __forceinline__ void warp_bitonic_stage(float (&v)[E], int lane, int 
             for (int e = 0; e < E; ++e) {
                 const int ep = e ^ j;
                 if (ep > e) {
-                    const int i = lane * E + e;
+                    const int i = gl * E + e;
                     const bool asc = (i & k) == 0;
                     const float lo = fminf(v[e], v[ep]), hi = fmaxf(v[e], v[ep]);
                     v[e] = asc ? lo : hi;
@@ -287,11 +291,11 @@ __device__ __forceinline__ void warp_bitonic_stage(float (&v)[E], int lane, int 
                 }
             }
         } else {
-            const int lm = j / E;                  // partner lane distance
+            const int lm = j / E;                  // partner lane distance (< L: inside the group)
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const float o = __shfl_xor_sync(0xffffffffu, v[e], lm);
-                const int i = lane * E + e;
+                const int i = gl * E + e;
                 const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
                 v[e] = keep_min ? fminf(v[e], o) : fmaxf(v[e], o);
             }
@@ -299,23 +303,23 @@ __device__ __forceinline__ void warp_bitonic_stage(float (&v)[E], int lane, int 
     }
 }
 
-template <int E>
-__device__ __forceinline__ void warp_bitonic_sort(float (&v)[E], int lane) {
+template <int E, int L>
+__device__ __forceinline__ void group_bitonic_sort(float (&v)[E], int lane) {
 #pragma unroll
-    for (int k = 2; k <= 32 * E; k <<= 1) warp_bitonic_stage<E>(v, lane, k);
+    for (int k = 2; k <= L * E; k <<= 1) group_bitonic_stage<E, L>(v, lane, k);
 }
 
 // Sort a bitonic sequence (non-increasing, then non-decreasing) ascending:
 // the last merge step of the sort alone.
-template <int E>
-__device__ __forceinline__ void warp_bitonic_merge(float (&v)[E], int lane) {
-    warp_bitonic_stage<E>(v, lane, 32 * E);
+template <int E, int L>
+__device__ __forceinline__ void group_bitonic_merge(float (&v)[E], int lane) {
+    group_bitonic_stage<E, L>(v, lane, L * E);
 }
 
-// Element i of a sorted warp array (i uniform over the warp).
-template <int E>
-__device__ __forceinline__ float warp_sorted_at(const float (&v)[E], int i) {
-    const int src = i / E, e = i % E;
+// Element i of a group's sorted array (i the same in every lane).
+template <int E, int L>
+__device__ __forceinline__ float group_sorted_at(const float (&v)[E], int i, int lane) {
+    const int src = (lane & ~(L - 1)) + i / E, e = i % E;
     float x = v[0];
 #pragma unroll
     for (int q = 1; q < E; ++q)
@@ -323,66 +327,76 @@ __device__ __forceinline__ float warp_sorted_at(const float (&v)[E], int i) {
     return __shfl_sync(0xffffffffu, x, src);
 }
 
-template <int E>
-__device__ __forceinline__ float warp_sorted_median(const float (&v)[E], int W) {
-    return (W & 1) ? warp_sorted_at<E>(v, W >> 1)
-                   : 0.5f * (warp_sorted_at<E>(v, (W >> 1) - 1) + warp_sorted_at<E>(v, W >> 1));
+template <int E, int L>
+__device__ __forceinline__ float group_sorted_median(const float (&v)[E], int W, int lane) {
+    return (W & 1) ? group_sorted_at<E, L>(v, W >> 1, lane)
+                   : __fmul_rn(0.5f, __fadd_rn(group_sorted_at<E, L>(v, (W >> 1) - 1, lane),
+                                               group_sorted_at<E, L>(v, W >> 1, lane)));
 }
 
 __device__ __forceinline__ float vis_abs(float2 r) { return sqrtf(r.x * r.x + r.y * r.y); }
 
-// Eq. 2's threshold median + sigma 1.4826 MAD over the warp's W values A
-// (element lane E + e; +inf past W).
-template <int E>
-__device__ __forceinline__ float warp_mad_threshold(const float (&A)[E], int W, float sigma, int lane) {
+// Eq. 2's threshold median + sigma 1.4826 MAD over the group's W values A
+// (element (lane mod L) E + e; +inf past W); the roundings spelled out.
+template <int E, int L = 32>
+__device__ __forceinline__ float group_mad_threshold(const float (&A)[E], int W, float sigma, int lane) {
     float v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = A[e];
-    warp_bitonic_sort<E>(v, lane);
-    const float med = warp_sorted_median<E>(v, W);
+    group_bitonic_sort<E, L>(v, lane);
+    const float med = group_sorted_median<E, L>(v, W, lane);
     // |A - med| in the sorted order falls to the median and rises after it
     // (the +inf padding stays last): a bitonic sequence, which one merge
     // sorts -- the same values as sorting |A - med| from scratch
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = fabsf(v[e] - med);
-    warp_bitonic_merge<E>(v, lane);
-    const float mad = warp_sorted_median<E>(v, W);
-    return med + sigma * mad * 1.4826f;
+    group_bitonic_merge<E, L>(v, lane);
+    const float mad = group_sorted_median<E, L>(v, W, lane);
+    return __fmaf_rn(__fmul_rn(sigma, mad), 1.4826f, med);
 }
 
-// The flags of warp item `item` = (integration, window, baseline) of R.
-template <int E>
+// Baseline index bl (upper triangle, row by row) -> (a, b), a <= b.
+__device__ __forceinline__ void baseline_decode(int bl, int n_in, int& a, int& b) {
+    int aa = 0, rem = bl;
+    while (rem >= n_in - aa) {
+        rem -= n_in - aa;
+        ++aa;
+    }
+    a = aa;
+    b = aa + rem;
+}
+
+// The flags of item `item` = (integration, window, baseline) of R, by the
+// group of L lanes that holds it (store = false: compute only).
+template <int E, int L>
 __device__ __forceinline__ void mad_flag_item(const float2* R, uint8_t* F, int n_chan, int n_in, int W, float sigma,
-                                              long long item, int lane) {
+                                              long long item, int lane, bool store = true) {
     const int n_bl = n_in * (n_in + 1) / 2;
     const int n_win = n_chan / W;
     const int bl = (int)(item % n_bl);
     const int w = (int)((item / n_bl) % n_win);
     const int i = (int)(item / ((long long)n_bl * n_win));
-    int a = 0, rem = bl;
-    while (rem >= n_in - a) { rem -= n_in - a; ++a; }
-    const int b = a + rem;
-    const size_t base = (size_t)i * n_chan * n_in * n_in;
+    int a, b;
+    baseline_decode(bl, n_in, a, b);
+    const size_t cs = (size_t)n_in * n_in;
+    const size_t base = (size_t)i * n_chan * cs + (size_t)w * W * cs;
+    const int c0 = (lane & (L - 1)) * E;
+    // every load issued before the first magnitude
+    float2 u[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+        u[e] = c0 + e < W ? __ldcg(R + base + (size_t)(c0 + e) * cs + (size_t)a * n_in + b) : make_float2(0.f, 0.f);
     float A[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int c = lane * E + e;
-        if (c < W) {
-            const int k = w * W + c;
-            A[e] = vis_abs(__ldcg(R + base + ((size_t)k * n_in + a) * n_in + b));
-        } else {
-            A[e] = __int_as_float(0x7f800000);          // +inf: sorts after every value
-        }
-    }
-    const float T = warp_mad_threshold<E>(A, W, sigma, lane);
+    for (int e = 0; e < E; ++e) A[e] = c0 + e < W ? vis_abs(u[e]) : __int_as_float(0x7f800000);   // +inf last
+    const float T = group_mad_threshold<E, L>(A, W, sigma, lane);
+    if (!store) return;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        const int c = lane * E + e;
-        if (c < W) {
-            const int k = w * W + c;
+        if (c0 + e < W) {
             const uint8_t f = A[e] > T ? 1 : 0;
-            F[base + ((size_t)k * n_in + a) * n_in + b] = f;
-            F[base + ((size_t)k * n_in + b) * n_in + a] = f;
+            F[base + (size_t)(c0 + e) * cs + (size_t)a * n_in + b] = f;
+            F[base + (size_t)(c0 + e) * cs + (size_t)b * n_in + a] = f;
         }
     }
 }
@@ -394,95 +408,24 @@ __global__ void __launch_bounds__(32 * kFlagWarps) mad_flag_kernel(const float2*
     const long long item = (long long)blockIdx.x * kFlagWarps + warp;
     const long long n_items = (long long)n_vis * (n_chan / W) * (n_in * (n_in + 1) / 2);
     if (item >= n_items) return;   // uniform over the warp
-    mad_flag_item<E>(R, F, n_chan, n_in, W, sigma, item, lane);
+    mad_flag_item<E, 32>(R, F, n_chan, n_in, W, sigma, item, lane);
 }
 
-// Many items (large arrays): one thread per (integration, window,
-// baseline) item for windows of at most NW = 16 / 32 / 64 channels.  The
-// thread keeps the window's |R| values in registers and sorts them with an
-// unrolled bitonic network (no shuffles; padding +inf), reads the median,
-// turns the sorted values into |A - med| -- a bitonic sequence -- and sorts
-// those with one merge for the MAD.  Neighbouring threads take neighbouring
-// baselines, so their loads of a channel's row of R and their flag stores
-// are contiguous.  The order statistics are exact: the flags equal the warp
-// form's.  With few items (8 inputs: 36 baselines a window) the warp form
-// keeps the GPU busier.
-constexpr long long kLaneFlagItems = 16384;
+// Many items (large arrays): groups of 8 lanes, 32 / 8 items a warp.  A
+// group past the last item computes the last item again without storing, so
+// that every lane of the warp takes part in the shuffles.
+constexpr long long kGroupFlagItems = 16384;
+constexpr int kFlagGroup = 8;
 
-__device__ __forceinline__ void cmpswap(float& x, float& y) {
-    const float lo = fminf(x, y), hi = fmaxf(x, y);
-    x = lo;
-    y = hi;
-}
-
-template <int NW>
-__device__ __forceinline__ void lane_bitonic_stage(float (&v)[NW], int k) {
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1)
-#pragma unroll
-        for (int i = 0; i < NW; ++i) {
-            const int l = i ^ j;
-            if (l > i) {
-                if ((i & k) == 0) cmpswap(v[i], v[l]);
-                else cmpswap(v[l], v[i]);
-            }
-        }
-}
-
-// element i of v, i a runtime index (v stays in registers)
-template <int NW>
-__device__ __forceinline__ float lane_at(const float (&v)[NW], int i) {
-    float x = v[0];
-#pragma unroll
-    for (int q = 1; q < NW; ++q)
-        if (q == i) x = v[q];
-    return x;
-}
-
-template <int NW>
-__device__ __forceinline__ float lane_median(const float (&v)[NW], int W) {
-    return (W & 1) ? lane_at<NW>(v, W >> 1) : 0.5f * (lane_at<NW>(v, (W >> 1) - 1) + lane_at<NW>(v, W >> 1));
-}
-
-template <int NW>
-__global__ void __launch_bounds__(128) mad_flag_lane_kernel(const float2* R, uint8_t* F, int n_vis, int n_chan,
-                                                            int n_in, int W, float sigma) {
-    const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int n_bl = n_in * (n_in + 1) / 2;
-    const int n_win = n_chan / W;
-    if (item >= (long long)n_vis * n_win * n_bl) return;
-    const int bl = (int)(item % n_bl);
-    const int w = (int)((item / n_bl) % n_win);
-    const int i = (int)(item / ((long long)n_bl * n_win));
-    int a = 0, rem = bl;
-    while (rem >= n_in - a) { rem -= n_in - a; ++a; }
-    const int b = a + rem;
-    const size_t cs = (size_t)n_in * n_in;
-    const size_t base = (size_t)i * n_chan * cs;
-    const float2* Rw = R + base + (size_t)w * W * cs + (size_t)a * n_in + b;   // channel c at Rw[c cs]
-    float v[NW];
-#pragma unroll
-    for (int c = 0; c < NW; ++c) {
-        if (c < W) {
-            v[c] = vis_abs(__ldcg(Rw + c * cs));
-        } else {
-            v[c] = __int_as_float(0x7f800000);          // +inf: sorts after every value
-        }
-    }
-#pragma unroll
-    for (int k = 2; k <= NW; k <<= 1) lane_bitonic_stage<NW>(v, k);
-    const float med = lane_median<NW>(v, W);
-#pragma unroll
-    for (int c = 0; c < NW; ++c) v[c] = fabsf(v[c] - med);
-    lane_bitonic_stage<NW>(v, NW);
-    const float mad = lane_median<NW>(v, W);
-    const float T = med + sigma * mad * 1.4826f;
-    uint8_t* Fw = F + base + (size_t)w * W * cs;
-    for (int c = 0; c < W; ++c) {
-        const uint8_t f = vis_abs(__ldcg(Rw + c * cs)) > T ? 1 : 0;
-        Fw[c * cs + (size_t)a * n_in + b] = f;
-        Fw[c * cs + (size_t)b * n_in + a] = f;
-    }
+template <int E>
+__global__ void __launch_bounds__(128) mad_flag_group_kernel(const float2* R, uint8_t* F, int n_vis, int n_chan,
+                                                             int n_in, int W, float sigma) {
+    const int lane = threadIdx.x & 31;
+    const long long n_items = (long long)n_vis * (n_chan / W) * (n_in * (n_in + 1) / 2);
+    long long item = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kFlagGroup;
+    const bool valid = item < n_items;
+    if (!valid) item = n_items - 1;
+    mad_flag_item<E, kFlagGroup>(R, F, n_chan, n_in, W, sigma, item, lane, valid);
 }
 
 // Finalisation and MAD flags in one kernel for small arrays (n_in <= 8,
@@ -522,7 +465,7 @@ __global__ void __launch_bounds__(256) fin_flag_small_kernel(const FinArgs F, ui
             const int c = lane * 2 + e;
             v[e] = c < W ? mag[z][c] : __int_as_float(0x7f800000);
         }
-        const float T = warp_mad_threshold<2>(v, W, sigma, lane);
+        const float T = group_mad_threshold<2>(v, W, sigma, lane);
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const int c = lane * 2 + e;
@@ -544,7 +487,7 @@ __device__ __forceinline__ void tail_flags(const TailMember& m, const TailItem& 
     uint8_t* F = m.flags + (size_t)it.integration * m.vis_stride;
     for (int q = warp; q < kTailWarpItems; q += kFlagWarps) {
         const long long wi = (long long)it.x + q;
-        if (wi < n_wi) mad_flag_item<E>(R, F, m.fin.n_chan, m.fin.n_in, m.window, m.sigma, wi, lane);
+        if (wi < n_wi) mad_flag_item<E, 32>(R, F, m.fin.n_chan, m.fin.n_in, m.window, m.sigma, wi, lane);
     }
 }
 
@@ -654,11 +597,11 @@ void launch_mad_flags(const float2* R, uint8_t* F, int n_vis, int n_chan, int n_
                       float sigma, cudaStream_t st) {
     const long long items = (long long)n_vis * (n_chan / window) * (n_in * (n_in + 1) / 2);
     if (items <= 0) return;
-    if (window <= 64 && items >= kLaneFlagItems) {
-        const unsigned tb = (unsigned)((items + 127) / 128);
-        if (window <= 16) mad_flag_lane_kernel<16><<<tb, 128, 0, st>>>(R, F, n_vis, n_chan, n_in, window, sigma);
-        else if (window <= 32) mad_flag_lane_kernel<32><<<tb, 128, 0, st>>>(R, F, n_vis, n_chan, n_in, window, sigma);
-        else mad_flag_lane_kernel<64><<<tb, 128, 0, st>>>(R, F, n_vis, n_chan, n_in, window, sigma);
+    if (window <= 64 && items >= kGroupFlagItems) {
+        const unsigned tb = (unsigned)((items * kFlagGroup + 127) / 128);
+        if (window <= 16) mad_flag_group_kernel<2><<<tb, 128, 0, st>>>(R, F, n_vis, n_chan, n_in, window, sigma);
+        else if (window <= 32) mad_flag_group_kernel<4><<<tb, 128, 0, st>>>(R, F, n_vis, n_chan, n_in, window, sigma);
+        else mad_flag_group_kernel<8><<<tb, 128, 0, st>>>(R, F, n_vis, n_chan, n_in, window, sigma);
         return;
     }
     const unsigned blocks = (unsigned)((items + kFlagWarps - 1) / kFlagWarps);

@@ -174,10 +174,11 @@ def test_xengine_dev_long_stream_beyond_the_grid_limit():
     assert np.max(np.abs(R.cpu().numpy()[:, 0, 0].real - Ro) / Ro) < 1e-4
 
 
-# the last three have >= 16384 (window, baseline) items per call: one thread
-# per item instead of one warp
+# the last four have >= 16384 (window, baseline) items per call: a group of
+# 8 lanes per item instead of a warp (the last: 16650 items, so the last warp
+# holds groups past the end that must store nothing)
 @pytest.mark.parametrize("window,n_chan,n_in", [(64, 256, 3), (64, 64, 1), (32, 128, 4), (8, 8, 2), (256, 512, 2),
-                                                (64, 1024, 40), (32, 512, 28), (16, 256, 64)])
+                                                (64, 1024, 40), (32, 512, 28), (16, 256, 64), (64, 128, 74)])
 def test_mad_flags_match_oracle(window, n_chan, n_in):
     rng = np.random.default_rng(window + n_chan)
     n_vis = 3
