@@ -19,8 +19,8 @@
 //
 // Warp roles (192 threads): warp 0 lane 0 issues TMA into a ring of A
 // stages, warp 1 lane 0 issues tcgen05.mma into one of two TMEM accumulators
-// (M = 128, N = BN), warps 2-5 drain the other accumulator (bias, ReLU, BF16
-// NHWC store; or the FP32 logit; or raw FP32).  CTAs are persistent over M
+// (M = 128, N = BN = 32), warps 2-5 drain the other accumulator (bias, ReLU,
+// BF16 NHWC store; or raw FP32).  CTAs are persistent over M
 // tiles.  Every wait is bounded by %globaltimer; on expiry the CTA records
 // CORR_ETIMEDOUT, stops issuing, frees its TMEM and returns.
 #include "corr.h"
@@ -204,14 +204,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             uint32_t r[32];
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN);
-            if constexpr (BN == 32) {
-                tmem_ld32(taddr, r);
-            } else {
-                uint32_t r16[16];
-                tmem_ld16(taddr, r16);
-#pragma unroll
-                for (int c = 0; c < 16; ++c) r[c] = r16[c];
-            }
+            tmem_ld32(taddr, r);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&sh->acc_empty[b]);
@@ -231,8 +224,6 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                 uint4* o = reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(A.out) + p * kCh);
 #pragma unroll
                 for (int v = 0; v < 4; ++v) o[v] = make_uint4(pk[4 * v], pk[4 * v + 1], pk[4 * v + 2], pk[4 * v + 3]);
-            } else if (A.mode == 1) {
-                reinterpret_cast<float*>(A.out)[p] = __uint_as_float(r[0]) + __ldg(A.bias);
             } else {
                 float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(A.out) + p * BN);
 #pragma unroll
@@ -326,7 +317,6 @@ int launch_conv(const ConvArgs& a, cudaStream_t st) {
     if (!a.X || !a.W || !a.out || (a.sgn != 1 && a.sgn != -1) || a.kp < kTaps * kCh || a.kp % 8) return CORR_EINVAL;
     if ((reinterpret_cast<uintptr_t>(a.X) & 15) || (reinterpret_cast<uintptr_t>(a.W) & 15)) return CORR_EINVAL;
     if (a.bn == 32 && (a.mode == 0 || a.mode == 2)) return launch_bn<32>(a, st);
-    if (a.bn == 16 && (a.mode == 1 || a.mode == 2)) return launch_bn<16>(a, st);
     return CORR_EINVAL;
 }
 

@@ -240,9 +240,9 @@ struct GemmArgs {
 int launch_gemm(const GemmArgs& a, cudaStream_t st);
 // out[m][n] = sum over splits of D[s][m][n], fixed order
 // Implicit-GEMM 5x5 convolution of NHWC BF16 images [n_images][64][256][32]
-// (see conv_tc.cu).  W: [bn][kp] BF16 K-major, k = (5u+v) 32 + c.  mode 0:
-// out = BF16 ReLU(z + bias) [P][32] (bn 32); mode 1: out = FP32 z + bias[0]
-// [P] (bn 16); mode 2: out = FP32 z [P][bn].  sgn -1 negates the tap offsets.
+// (see conv_tc.cu).  W: [bn][kp] BF16 K-major, k = (5u+v) 32 + c, bn = 32.
+// mode 0: out = BF16 ReLU(z + bias) [P][32]; mode 2: out = FP32 z [P][32].
+// sgn -1 negates the tap offsets.
 struct ConvArgs {
     const void* X;
     const void* W;

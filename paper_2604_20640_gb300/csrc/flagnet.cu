@@ -227,6 +227,60 @@ __global__ void pack_weights_kernel(const float* w, int C, int Co, int Kf, int K
     if (wd) wd[(size_t)c * Kd + uv * Co + o] = b;
 }
 
+// Output layer (32 -> 1 channel) on CUDA cores: one warp per 32
+// consecutive pixels of a tile row, lane c holding input channel c.  Each
+// lane streams the five input rows once (36 pixels a row, zero outside the
+// tile) and forms all 32 outputs' partial sums over its channel with the
+// layer's BF16 weights (FP32 sums); a 31-step exchange then leaves the sum
+// over the channels of output x0 + l in lane l.  On the tensor cores the one
+// output channel filled a sixteenth of each MMA.
+__global__ void __launch_bounds__(256) conv_last_kernel(const uint16_t* __restrict__ act, int B,
+                                                        const uint16_t* __restrict__ wf,
+                                                        const float* __restrict__ bias, float* __restrict__ logit) {
+    constexpr int SEG = TW / 32;
+    const int lane = (int)threadIdx.x & 31;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (wid >= (long long)B * TH * SEG) return;   // uniform over the warp
+    const int x0 = (int)(wid % SEG) * 32;
+    const int i = (int)((wid / SEG) % TH);
+    const int n = (int)(wid / ((long long)TH * SEG));
+    float w[25];
+#pragma unroll
+    for (int t = 0; t < 25; ++t) w[t] = bf2f(wf[t * 32 + lane]);   // k = (5u + v) 32 + c, output row 0
+    float acc[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+    const uint16_t* an = act + (size_t)n * TPIX * 32 + lane;
+#pragma unroll
+    for (int u = 0; u < 5; ++u) {
+        const int ii = i + u - 2;
+        if (ii < 0 || ii >= TH) continue;         // uniform over the warp
+        float a[36];
+#pragma unroll
+        for (int q = 0; q < 36; ++q) {
+            const int xx = x0 - 2 + q;
+            a[q] = (xx >= 0 && xx < TW) ? bf2f(an[((size_t)ii * TW + xx) * 32]) : 0.f;
+        }
+#pragma unroll
+        for (int v = 0; v < 5; ++v)
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc[j] = fmaf(w[5 * u + v], a[j + v], acc[j]);
+    }
+    // sum over the lanes: at distance d each lane keeps the half of its
+    // outputs on its side of bit d and adds the partner's share of it
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+        const bool up = (lane & d) != 0;
+#pragma unroll
+        for (int j = 0; j < d; ++j) {
+            const float send = up ? acc[j] : acc[j + d];
+            const float keep = up ? acc[j + d] : acc[j];
+            acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, d);
+        }
+    }
+    logit[(size_t)n * TPIX + (size_t)i * TW + x0 + lane] = acc[0] + __ldg(bias);
+}
+
 // Layer 0 (1 -> 32 channels) on CUDA cores in FP32: one thread per pixel
 // takes its 5x5 neighbourhood of the FP32 input (zero outside the tile) and
 // forms all 32 outputs, then stores BF16 ReLU(z + b) NHWC (64 bytes).  With
@@ -576,8 +630,9 @@ int conv(corr_flagnet_t net, const uint16_t* X, const uint16_t* W, int B, int bn
 }
 
 // Forward pass over B normalised tiles x [B][64][256] -> logits.  The
-// 1-channel first layer runs on CUDA cores in FP32 (conv0_kernel); the
-// 32-channel layers are implicit-GEMM convolutions on the tensor cores.
+// 1-channel first and last layers run on CUDA cores (conv0_kernel,
+// conv_last_kernel); the 32-channel layers are implicit-GEMM convolutions
+// on the tensor cores.
 int forward(corr_flagnet_t net, const float* x, int B, cudaStream_t st, bool training) {
     const int P = B * TPIX;
     int rc = CORR_OK;
@@ -588,12 +643,13 @@ int forward(corr_flagnet_t net, const float* x, int B, cudaStream_t st, bool tra
     }
     conv0_kernel<<<blocks(P), 256, 0, st>>>(x, P, net->w[0], net->b[0], net->act[1]);
     ++net->launches;
-    for (int l = 1; l < NL; ++l) {
-        const bool last = l == NL - 1;
-        rc = conv(net, net->act[l], net->wf[l], B, last ? 16 : 32, 1, last ? 1 : 0, net->b[l],
-                  last ? static_cast<void*>(net->logit) : static_cast<void*>(net->act[l + 1]), st);
+    for (int l = 1; l < NL - 1; ++l) {
+        rc = conv(net, net->act[l], net->wf[l], B, 32, 1, 0, net->b[l], net->act[l + 1], st);
         if (rc != CORR_OK) return rc;
     }
+    conv_last_kernel<<<blocks((long long)B * TH * (TW / 32) * 32), 256, 0, st>>>(net->act[NL - 1], B, net->wf[NL - 1],
+                                                                                net->b[NL - 1], net->logit);
+    ++net->launches;
     FK(cudaGetLastError());
     return CORR_OK;
 }
