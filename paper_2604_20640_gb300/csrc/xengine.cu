@@ -218,10 +218,26 @@ __device__ __forceinline__ bool fin_value(const FinArgs& F, int k, int t, int z,
     const int e = (i * 4 + j) * 2;
     re = 0.f;
     im = 0.f;
-    for (int s = 0; s < F.n_slots; ++s) {
-        const float* p = F.part + (((size_t)s * F.nt + t) * 32 + e) * F.n_chan + k;
-        re += p[0];
-        im += p[F.n_chan];
+    // slots summed in order; their loads issued 16 at a time
+    const float* p = F.part + ((size_t)t * 32 + e) * F.n_chan + k;
+    const size_t ss = (size_t)F.nt * 32 * F.n_chan;
+    int s = 0;
+    for (; s + 16 <= F.n_slots; s += 16) {
+        float vr[16], vi[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            vr[q] = __ldcg(p + (size_t)(s + q) * ss);
+            vi[q] = __ldcg(p + (size_t)(s + q) * ss + F.n_chan);
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            re += vr[q];
+            im += vi[q];
+        }
+    }
+    for (; s < F.n_slots; ++s) {
+        re += __ldcg(p + (size_t)s * ss);
+        im += __ldcg(p + (size_t)s * ss + F.n_chan);
     }
     re *= F.scale;
     im *= F.scale;
@@ -437,7 +453,7 @@ __global__ void __launch_bounds__(128) mad_flag_group_kernel(const float2* R, ui
 // threshold from them exactly as mad_flag_kernel does from R, and writes
 // the flags.  One launch instead of two, and R is not read back.
 constexpr int kFinFlagW = 64;
-__global__ void __launch_bounds__(256) fin_flag_small_kernel(const FinArgs F, uint8_t* Fl, int W, float sigma) {
+__global__ void __launch_bounds__(512) fin_flag_small_kernel(const FinArgs F, uint8_t* Fl, int W, float sigma) {
     __shared__ float mag[16][kFinFlagW];
     const int w = blockIdx.x, t = blockIdx.y;
     for (int it = (int)threadIdx.x; it < 16 * W; it += (int)blockDim.x) {
@@ -590,7 +606,7 @@ bool fin_flag_small_supported(int n_in, int window) { return n_in <= 8 && window
 
 void launch_fin_flag_small(const FinArgs& a, uint8_t* F, int window, float sigma, cudaStream_t st) {
     dim3 grid((unsigned)(a.n_chan / window), (unsigned)a.nt);
-    fin_flag_small_kernel<<<grid, 256, 0, st>>>(a, F, window, sigma);
+    fin_flag_small_kernel<<<grid, 512, 0, st>>>(a, F, window, sigma);
 }
 
 void launch_mad_flags(const float2* R, uint8_t* F, int n_vis, int n_chan, int n_in, int window,
