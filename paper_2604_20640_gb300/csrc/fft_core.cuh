@@ -961,11 +961,14 @@ __global__ void __launch_bounds__(M / 16, FftCfg<M>::minb(3)) pfb_fft_kernel(con
     const int8_t* const row1 = row0 + sv.stride;
     const int o0 = has0 ? (int)(reinterpret_cast<uintptr_t>(row0 + d0) & 15) : 0;
     const int o1 = has1 ? (int)(reinterpret_cast<uintptr_t>(row1 + d1) & 15) : 0;
-    const int m_lo = 8 * tid, m_mi = M - 8 - 8 * tid;   // first branch of each half
-    // FP2: four words of four branches, 4t, 4t + M/2, M/2 - 4 - 4t, M - 4 - 4t
-    // (each branch's mirror and first-pass partner in the same thread)
-    const int wo[4] = {FP2 ? 4 * tid : m_lo, FP2 ? 4 * tid + M / 2 : m_lo + 4,
-                       FP2 ? M / 2 - 4 - 4 * tid : m_mi, FP2 ? M - 4 - 4 * tid : m_mi + 4};
+    // four words of four branches each: groups A = 4t and B, and their
+    // mirrors B' and A' (branch m's mirror M-1-m shares its coefficients).
+    // FP2: B = 4t + M/2, the first radix-2 pass's partner of A, so that pass
+    // stays in the thread; else B = 4t + M/4.  Consecutive threads take
+    // consecutive groups: the coefficient rows and the FIR's stores are read
+    // and written without bank conflicts.
+    const int wo[4] = {4 * tid, FP2 ? 4 * tid + M / 2 : 4 * tid + M / 4,
+                       FP2 ? M / 2 - 4 - 4 * tid : 3 * (M / 4) - 4 - 4 * tid, M - 4 - 4 * tid};
 
     // W[q][k][w]: frame q of the window (q = P-1 the newest), input k, word w
     // (the four branches from wo[w])
@@ -980,15 +983,10 @@ __global__ void __launch_bounds__(M / 16, FftCfg<M>::minb(3)) pfb_fft_kernel(con
                 const int8_t* row = k ? row1 : row0;
                 const bool has = k ? has1 : has0;
                 const long long n = f * M + (k ? d1 : d0);
-                if constexpr (FP2) {
-                    x = make_uint2(global8_checked(row, has, n + wo[0], lo, sv.vhi).x,
-                                   global8_checked(row, has, n + wo[1], lo, sv.vhi).x);
-                    y = make_uint2(global8_checked(row, has, n + wo[2], lo, sv.vhi).x,
-                                   global8_checked(row, has, n + wo[3], lo, sv.vhi).x);
-                } else {
-                    x = global8_checked(row, has, n + m_lo, lo, sv.vhi);
-                    y = global8_checked(row, has, n + m_mi, lo, sv.vhi);
-                }
+                x = make_uint2(global8_checked(row, has, n + wo[0], lo, sv.vhi).x,
+                               global8_checked(row, has, n + wo[1], lo, sv.vhi).x);
+                y = make_uint2(global8_checked(row, has, n + wo[2], lo, sv.vhi).x,
+                               global8_checked(row, has, n + wo[3], lo, sv.vhi).x);
             }
             W[q][k][0] = x.x;
             W[q][k][1] = x.y;
@@ -1012,23 +1010,10 @@ __global__ void __launch_bounds__(M / 16, FftCfg<M>::minb(3)) pfb_fft_kernel(con
         const int it = (int)(s - s_lo);
         float2* const X = (ALT && (it & 1)) ? buf1 : buf0;
         float2* const Y = (X == buf0) ? buf1 : buf0;
-        if constexpr (FP2) {
 #pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                W[P - 1][0][w] = staged8(stg0, o0 + wo[w]).x;
-                W[P - 1][1][w] = staged8(stg1, o1 + wo[w]).x;
-            }
-        } else {
-            const uint2 l0 = staged8(stg0, o0 + m_lo), m0 = staged8(stg0, o0 + m_mi);
-            const uint2 l1 = staged8(stg1, o1 + m_lo), m1 = staged8(stg1, o1 + m_mi);
-            W[P - 1][0][0] = l0.x;
-            W[P - 1][0][1] = l0.y;
-            W[P - 1][0][2] = m0.x;
-            W[P - 1][0][3] = m0.y;
-            W[P - 1][1][0] = l1.x;
-            W[P - 1][1][1] = l1.y;
-            W[P - 1][1][2] = m1.x;
-            W[P - 1][1][3] = m1.y;
+        for (int w = 0; w < 4; ++w) {
+            W[P - 1][0][w] = staged8(stg0, o0 + wo[w]).x;
+            W[P - 1][1][w] = staged8(stg1, o1 + wo[w]).x;
         }
         if constexpr (FP2) {
             // FIR of branch groups A = 4t + i, B = 4t + i + M/2 (first-pass
@@ -1076,14 +1061,14 @@ __global__ void __launch_bounds__(M / 16, FftCfg<M>::minb(3)) pfb_fft_kernel(con
         } else {
         // FIR: y_s[m] = sum_p h[pM + m] x[(s-P+1+p)M + m] for both inputs at
         // once (lanes a, b of a packed pair), taps in order p = 0 .. P-1.
-        // Branch m_lo + 4j + c is byte c of lower word j; its mirror
-        // M-1-(m_lo + 4j + c) = m_mi + 7 - 4j - c is byte 3-c of mirror word
-        // 1-j and takes h[(P-1-p)M + m_lo + 4j + c] at tap p.
+        // Branch wo[j] + c (j = 0: A, 1: B, both below M/2) is byte c of
+        // word j; its mirror M-1-(wo[j] + c) = wo[3-j] + 3 - c is byte 3-c
+        // of word 3-j and takes h[(P-1-p)M + wo[j] + c] at tap p.
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             float4 hq[P];
 #pragma unroll
-            for (int p = 0; p < P; ++p) hq[p] = hs4[(p * (M / 2) + m_lo + 4 * j) >> 2];
+            for (int p = 0; p < P; ++p) hq[p] = hs4[(p * (M / 2) + wo[j]) >> 2];
             float2 ylo[4], ymi[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) ylo[c] = ymi[c] = make_float2(0.f, 0.f);
@@ -1100,8 +1085,8 @@ __global__ void __launch_bounds__(M / 16, FftCfg<M>::minb(3)) pfb_fft_kernel(con
             }
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                X[pidx(m_lo + 4 * j + c)] = ylo[c];
-                X[pidx(M - 1 - m_lo - 4 * j - c)] = ymi[c];
+                X[pidx(wo[j] + c)] = ylo[c];
+                X[pidx(M - 1 - wo[j] - c)] = ymi[c];
             }
         }
         }
