@@ -1035,11 +1035,12 @@ def main():
     # ---- the other code type the 64-input workload names, timed the same way ----
     e4m3, e4m3_v = None, None
     if wl == "c3" and prec == 1 and not args.no_e4m3:
-        me = measure_stream(args, wl, 2, x, spec, dev, world, barrier, clocks=False, stages=False)
+        me = measure_stream(args, wl, 2, x, spec, dev, world, barrier, clocks=False, stages=True)
         ems = max_over_ranks(me["ms"], dist if world > 1 else None, dev)
         e4m3 = {"value": job_rate(bytes_step, world, ems), "ms_per_step": ems,
                 "ratio_to_plain": plain and ems and plain["ms_per_step"] / ems,
-                "tuning": me["tuning"], "path": "e4m3 requantised, tcgen05 X (kind::f8f6f4)"}
+                "tuning": me["tuning"], "path": "e4m3 requantised, tcgen05 X (kind::f8f6f4)",
+                "x_engine": (me["roofline"] or {}).get("x_engine")}
         e4m3_v = me["vis"]
         del me["flags"]
 
@@ -1126,7 +1127,7 @@ def measure_stream(args, wl, prec, x, spec, dev, world, barrier, clocks=True, st
         c.set_option("stage_timing", 1)
         c.stage_times()
         c.run_dev(x, vis, flags)
-        share_ms, _ = c.stage_times()
+        share_ms, share_n = c.stage_times()
         total_stage = sum(share_ms) or 1.0
         share = {k: share_ms[i] / total_stage for i, k in enumerate(STAGES)}
         dom = max((k for k in STAGES if ALG_BYTES_PER_SAMPLE[k] > 0), key=lambda k: share[k])
@@ -1170,9 +1171,36 @@ def measure_stream(args, wl, prec, x, spec, dev, world, barrier, clocks=True, st
         c.set_option("stage_timing", 0)
         c.set_option("stage_mask", 127)
         roofline = _roofline(wl, prec, args, dom, di, share, stage_ms, stage_n, S, n_in)
+        if prec != 0:
+            roofline["x_engine"] = _gram_roofline(wl, prec, share_ms, share_n, n_in)
     c.close()
     return {"ms": ms, "tuning": tuning, "launches": launches, "clocks": clk, "roofline": roofline,
             "vis": vis, "flags": flags, "l2": l2}
+
+
+def _gram_roofline(wl, prec, stage_ms, stage_n, n_in):
+    """The tensor-core X-engine's rate from the step with every stage
+    bracketed (live CUDA events): the algorithmic 2 (2N)^2 K flop of each
+    channel's Gram matrix (N inputs, K spectra an integration) per launch
+    against the measured BF16 tensor peak (e4m3: times the nominal ratio 2)."""
+    gi = STAGES.index("gram")
+    if not stage_n[gi]:
+        return None
+    W = WORKLOADS[wl]
+    ms = stage_ms[gi] / stage_n[gi]
+    flop = 2.0 * (2 * n_in) ** 2 * W["n_int"] * W["n_chan"]
+    peaks = _peaks()
+    burst = peaks.get("bf16_tflops") or 1900.0
+    sust = peaks.get("bf16_tflops_sustained") or 1700.0
+    scale = 2.0 if prec == 2 else 1.0
+    tf = flop / (ms * 1e-3) / 1e12
+    return {"kernel": "gram_w_kernel<%d> (%s)" % (prec == 2, "e4m3, kind::f8f6f4" if prec == 2 else
+                                                   "int8 widened to BF16, kind::f16"),
+            "bound": "tensor", "avg_launch_ms": ms, "launches": stage_n[gi], "flop_per_launch": flop,
+            "achieved": tf, "peak": burst * scale, "unit": "TFLOP/s", "frac": tf / (burst * scale),
+            "frac_of_sustained": tf / (sust * scale),
+            "peak_source": ("measured BF16 burst x nominal ratio 2" if prec == 2 else "measured BF16 burst"),
+            "input_gbs": n_in * 2 * W["n_chan"] * W["n_int"] / (ms * 1e-3) / 1e9}
 
 
 def flops_per_sample(dom, fused, M, taps, n_in):
