@@ -515,7 +515,7 @@ def run_batched(args, rank, world, local):
     members, plains, xs, vis, flags, precs = [], [], [], [], [], []
     for spec, (na, nc, ni) in zip(specs, C4_SHAPES):
         # chosen form: tensor-core X-engine (int8 codes) once N is large
-        prec = 1 if 2 * na >= TENSOR_MIN_INPUTS else 0
+        prec = 1 if 2 * na >= args.tensor_min_inputs else 0
         precs.append(prec)
         c = Correlator(na, 2, nc, 4, ni, precision=prec)
         c.set_delays(spec.tau, spec.phi)
@@ -709,7 +709,7 @@ def run_batched(args, rank, world, local):
                        "l2": "inputs (%d MiB/step) larger than L2" % (bytes_step >> 20),
                        "tuning": [c.tuning() for c in members],
                        "path": "one captured graph; tensor-core X (int8) for members with >= %d inputs, "
-                               "CUDA-core FP32 X below" % TENSOR_MIN_INPUTS},
+                               "CUDA-core FP32 X below" % args.tensor_min_inputs},
             "gpu_launches": int(launches), "clocks": clk, "roofline": roofline, "e2e": e2e,
             "cpu_baseline": None if args.no_cpu else c4_cpu_baseline(),
             "plain_fp32": {"value": job_rate(bytes_step, world, ms_plain), "ms_per_step": ms_plain,
@@ -968,6 +968,8 @@ def main():
     ap.add_argument("--precision", type=int, default=None,
                     help="0 FP32 CUDA-core X, 1 int8 / 2 e4m3 tensor-core X (default: FP32, int8 for c3)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
+    ap.add_argument("--tensor-min-inputs", type=int, default=TENSOR_MIN_INPUTS,
+                    help="c4: members with at least this many inputs use the tensor-core X-engine (int8)")
     ap.add_argument("--no-e4m3", action="store_true",
                     help="c3 at int8: skip the timed e4m3 run beside it (its error is still reported)")
     ap.add_argument("--no-chosen", action="store_true",
