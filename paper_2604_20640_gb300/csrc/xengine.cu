@@ -235,9 +235,22 @@ __device__ __forceinline__ bool fin_value(const FinArgs& F, int k, int t, int z,
             im += vi[q];
         }
     }
-    for (; s < F.n_slots; ++s) {
-        re += __ldcg(p + (size_t)s * ss);
-        im += __ldcg(p + (size_t)s * ss + F.n_chan);
+    if (s < F.n_slots) {
+        // the last n_slots mod 16 slots, loaded together as well
+        const int rem = F.n_slots - s;
+        float vr[16], vi[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            vr[q] = q < rem ? __ldcg(p + (size_t)(s + q) * ss) : 0.f;
+            vi[q] = q < rem ? __ldcg(p + (size_t)(s + q) * ss + F.n_chan) : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            if (q < rem) {
+                re += vr[q];
+                im += vi[q];
+            }
+        }
     }
     re *= F.scale;
     im *= F.scale;
