@@ -58,7 +58,7 @@ WORKLOADS = {
 # Stages reported by corr_stage_times and their kernels.
 STAGES = ["fir", "fft", "xengine", "finalize", "flag", "requant", "gram"]
 KERNELS = {"fir": "fir_kernel<4>", "fft": "fft_kernel<M,3>", "xengine": "xengine_kernel",
-           "finalize": "finalize_kernel", "flag": "mad_flag_kernel", "requant": "requant_pm_kernel",
+           "finalize": "finalize_kernel", "flag": "mad_flag_kernel", "requant": "words_from_spectra_kernel",
            "gram": "gram_w_kernel (tcgen05 over the F-engine's code words, visibilities in its epilogue)"}
 # Algorithmic bytes per input sample of each hot-path kernel, in the unit the
 # scope table's measurement section fixes: the whole hot path (PFB, FFT,
@@ -71,8 +71,8 @@ ALG_BYTES_PER_SAMPLE = {"fir": 1.0, "fft": 1.0, "xengine": 1.0, "finalize": 0.0,
 # Bytes each kernel of this build actually moves per input sample, rings
 # included (FIR: 1 B in + 4 B of z = (y_a, y_b) out; FFT: 4 B of z in + one
 # complex64 per channel per input out; X-engine: the spectra back in;
-# requantiser: spectra in, one 1-byte code (int8 or e4m3) per component out,
-# or only a transpose of the fused F-engine's code words; Gram: the codes).
+# requantiser (a stream's first ring fill): spectra in, one 1-byte code
+# (int8 or e4m3) per sample out as code words; Gram: the codes).
 # Reported beside the algorithmic figure, not used for it.
 INTERMEDIATE_BYTES_PER_SAMPLE = {"fir": 5.0, "fft": 8.0, "xengine": 4.0, "finalize": 0.0, "flag": 0.0,
                                  "requant": 5.0, "gram": 1.0}

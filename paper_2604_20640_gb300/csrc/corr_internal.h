@@ -189,34 +189,19 @@ struct GramArgs {
 };
 
 // Requantise spectra [s_begin, s_end) of the pair-major ring V (U = 2Y,
-// unrotated) into Q columns s - int_start: Q[k][a][.] = q(Re U / sigma),
-// Q[k][N+a][.] = q(Im U / sigma), sigma = scale[a][k]; int8 codes (round to
-// nearest even, saturate +-127) as bytes or carried as BF16, or e4m3
-// (satfinite) bytes.
+// unrotated; [slot][pair][n_chan] float4) into the integration's code words
+// C[t][pair][n_chan], t = s - int_start: bytes q(Re U_a / sigma_a), q(Im U_a
+// / sigma_a), q(Re U_a+1 / sigma_a+1), q(Im U_a+1 / sigma_a+1), sigma =
+// scale[a][k]; int8 codes (round to nearest even, saturate +-127) or e4m3
+// (satfinite).
 struct RequantArgs {
     const float2* V;
     long long v_origin, v_mask;
     const float* scale;      // [2][n_in_pad][n_chan]: scales, then their inverses
-    uint8_t* Q;
-    int k_pitch;
     long long s_begin, s_end, int_start;
     int n_in, n_in_pad, n_chan;
     bool fp8;
-    int pair_major;          // V pair-major ([slot][pair][n_chan] float4); always set
-    int i8b;                 // int8 codes as bytes (else carried as BF16)
-    int codes_in;            // V holds the F-engine's code words ([slot][pair][n_chan] uint32): transpose only
-    uint32_t* C;             // set: int8 code words C[t][pair][n_chan] out instead of Q (t = s - int_start)
-};
-
-// R[k][a][b] = scale_a scale_b / (4 count) rot_a conj(rot_b) sum q_a conj(q_b),
-// from the Gram matrix.
-struct FinQArgs {
-    const void* G;
-    const float* scale;      // [n_in_pad][n_chan]
-    const float2* rot;       // [n_in_pad][n_chan] or nullptr
-    int n_chan, n_in, count;
-    bool fp8;
-    float2* R;
+    uint32_t* C;
 };
 
 // Requantisation gains g (sigma = sqrt(component power) / g): int8 codes
@@ -256,7 +241,6 @@ int launch_conv(const ConvArgs& a, cudaStream_t st);
 void launch_split_sum(const float* D, int splits, long long mn, float* out, cudaStream_t st);
 size_t gram_smem_bytes();
 void launch_requant(const RequantArgs& a, cudaStream_t st);
-void launch_finalize_q(const FinQArgs& a, cudaStream_t st);
 // scale[a][k] = sqrt(c P) / gain with P the mean |U|^2 over spectra
 // [s0, s0 + n) of the ring (first integration of a stream) and c the
 // component share of the power: 1/2, or 1 in the real DC channel k = 0.

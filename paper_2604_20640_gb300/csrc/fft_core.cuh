@@ -901,9 +901,9 @@ __device__ __forceinline__ float2 unpack_pair(uint32_t fa, uint32_t fb, int c) {
 // MODE as in fft_kernel (0 U = 2Y channel-major, 1 rotated V, 2 power
 // tiles, 3 U pair-major), or 6 / 7: U requantised to int8 / e4m3 codes, the
 // pair's four codes of a channel (Re U_a, Im U_a, Re U_b, Im U_b, low byte
-// first) as one 32-bit word of pair-major words [slot][pair][n_chan] (the
-// spectra ring, or an integration's word buffer when slot = s - int_start);
-// one input pair per CTA; P taps.
+// first) as one 32-bit word of pair-major words [slot][pair][n_chan] (an
+// integration's word buffer, slot = s - int_start); one input pair per CTA;
+// P taps.
 template <int M, int MODE, int P>
 __global__ void __launch_bounds__(M / 16, FftCfg<M>::minb(3)) pfb_fft_kernel(const FusedArgs A) {
     using C = FftCfg<M>;

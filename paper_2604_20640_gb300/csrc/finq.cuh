@@ -1,6 +1,6 @@
-// Visibilities from the Gram matrix of requantised voltages (the
-// reduced-precision X-engine's finalisation), shared by finalize_q_kernel
-// and the Gram kernel's own epilogue so both give the same bits.
+// Visibilities from the Gram matrix of requantised voltages: the
+// reduced-precision X-engine's finalisation, done in the Gram kernel's own
+// epilogue.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -14,7 +14,7 @@ namespace corr {
 // qa conj(qb) (the fine-delay and phase correction of Eq. 1) unless qa is
 // null.  inv4c = 1 / (4 count), rounded once by the caller.  The
 // autocorrelation (a == b) is real and not rotated.  Roundings are spelled
-// out so that no caller's contraction differs.
+// out, so the result does not hang on how the compiler contracts them.
 __device__ __forceinline__ float2 vis_from_gram(float g_rr, float g_ii, float g_ir, float g_ri, float sa, float sb,
                                                 float inv4c, bool diag, const float2* qa, const float2* qb) {
     const float sc = __fmul_rn(__fmul_rn(sa, sb), inv4c);

@@ -37,16 +37,11 @@ struct Pipe {
     float* part_all = nullptr;
     long long part_all_ints = 0;
     // reduced-precision path (tensor-core X-engine)
-    uint8_t* Q = nullptr;     // [n_chan][128][q_pitch] codes of one integration
-    int q_pitch = 0;          // bytes per row (multiple of 128)
-    float* G = nullptr;       // [n_chan][128][128]
     float* scale = nullptr;   // [n_in_pad][n_chan], fixed per integration
     bool have_scale = false;  // false until the first integration's pre-pass
-    bool ring_codes = false;  // the unrequantised ring slots hold the F-engine's code words
     // the integration's int8 or e4m3 code words C[t][pair][n_chan] (bytes
-    // Re a, Im a, Re a+1, Im a+1), read by the Gram kernel directly (no Q)
+    // Re a, Im a, Re a+1, Im a+1), read by the Gram kernel directly
     uint32_t* C = nullptr;
-    bool words = false;
 };
 
 struct Slot {
@@ -411,22 +406,13 @@ int alloc_pipe_impl(corr_t h, Pipe& p) {
     CKA(dmalloc(h, &p.V, per_spec * (size_t)p.v_cap));
     CKA(dmalloc(h, &p.Z, per_spec * (size_t)p.v_cap));
     if (h->precision != CORR_FP32) {
-        p.words = (h->n_chan % 4) == 0;
-        if (p.words) {
-            // one 32-bit word of four codes per (spectrum, pair, channel)
-            const size_t cbytes = sizeof(uint32_t) * (size_t)h->n_int * (h->n_in_pad / 2) * h->n_chan;
-            CKA(dmalloc(h, &p.C, cbytes));
-            CK(cudaMemset(p.C, 0, cbytes));
-        } else {
-            // one byte per code, rows of K
-            p.q_pitch = (int)(((long long)h->n_int + 127) / 128 * 128);
-            const size_t qbytes = (size_t)h->n_chan * 128 * p.q_pitch;
-            CKA(dmalloc(h, &p.Q, qbytes));
-            CK(cudaMemset(p.Q, 0, qbytes));
-        }
-        // Gram matrices (the row-major form only: the word form's Gram
-        // kernel writes the visibilities itself)
-        if (!p.words) CKA(dmalloc(h, &p.G, sizeof(float) * (size_t)h->n_chan * 128 * 128));
+        // one 32-bit word of four codes per (spectrum, pair, channel) of an
+        // integration (n_chan, a power of two >= 8, is a multiple of the Gram
+        // kernel's four channels a CTA); the Gram kernel writes the
+        // visibilities itself, so no Gram matrices are kept
+        const size_t cbytes = sizeof(uint32_t) * (size_t)h->n_int * (h->n_in_pad / 2) * h->n_chan;
+        CKA(dmalloc(h, &p.C, cbytes));
+        CK(cudaMemset(p.C, 0, cbytes));
         // scales, then their inverses (the requantiser's multipliers)
         CKA(dmalloc(h, &p.scale, 2 * sizeof(float) * (size_t)h->n_in_pad * h->n_chan));
         p.have_scale = false;
@@ -589,26 +575,19 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
         // the ring bounds a launch, except where the F-engine writes code
         // words straight into the integration's word buffer (then one launch
         // may cover the rest of the integration)
-        const bool to_words = p.words && p.have_scale && p.s_xdone == p.s_next && fused_codes(h, sv);
+        const bool to_words = p.have_scale && p.s_xdone == p.s_next && fused_codes(h, sv);
         if (!to_words && s_end > p.s_xdone + p.v_cap) s_end = p.s_xdone + p.v_cap;
         if (s_end > p.s_next) {
-            // scales fixed and nothing left in the ring: the F-engine
-            // requantises in its epilogue (the requantiser's arithmetic) and
-            // writes 4-byte code words instead of 16-byte spectra; the
-            // requantiser below then only transposes them into Q
-            const bool codes = p.have_scale && p.s_xdone == p.s_next && fused_codes(h, sv);
-            p.ring_codes = codes && !p.words;
             if (to_words) {
-                // the words go straight into the integration's C at
-                // t = s - istart, where the Gram kernel reads them
+                // scales fixed and nothing left in the ring: the F-engine
+                // requantises in its epilogue (the requantiser's arithmetic)
+                // and writes 4-byte code words instead of 16-byte spectra,
+                // straight into the integration's C at t = s - istart, where
+                // the Gram kernel reads them
                 const CodeOut q{p.scale + (size_t)h->n_in_pad * h->n_chan, h->precision == CORR_FP8};
                 CKRET(launch_f(h, sv, t, p.Z, 0, p.v_cap - 1, reinterpret_cast<float2*>(p.C), istart, -1LL,
                                nullptr, p.s_next, s_end, st, nullptr, 0, 0, &q));
                 p.s_xdone = s_end;
-            } else if (codes) {
-                const CodeOut q{p.scale + (size_t)h->n_in_pad * h->n_chan, h->precision == CORR_FP8};
-                CKRET(launch_f(h, sv, t, p.Z, 0, p.v_cap - 1, p.V, 0, p.v_cap - 1, nullptr, p.s_next, s_end, st,
-                               nullptr, 0, 0, &q));
             } else {
                 CKRET(launch_f(h, sv, t, p.Z, 0, p.v_cap - 1, p.V, 0, p.v_cap - 1, nullptr, p.s_next, s_end, st));
             }
@@ -619,9 +598,11 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
         const long long s_limit = closing ? p.s_next : iend;
         int j_end = 0;
         if (h->precision != CORR_FP32) {
-            // Requantise every channelised spectrum into the integration's Q.
-            // The first integration of a stream first fixes its scales from
-            // the mean power of its first min(n_int, 64) spectra.
+            // Requantise the spectra the ring still holds (a stream's first
+            // ring fill, before the scales are known, or every fill when the
+            // F-engine is not the fused kernel) into the integration's code
+            // words.  The first integration of a stream first fixes its
+            // scales from the mean power of its first min(n_int, 64) spectra.
             if (!p.have_scale) {
                 const long long want = n_int < 64 ? n_int : 64;
                 const long long have = p.s_next - istart;
@@ -641,8 +622,6 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
                 r.v_origin = 0;
                 r.v_mask = p.v_cap - 1;
                 r.scale = p.scale;
-                r.Q = p.Q;
-                r.k_pitch = p.q_pitch;
                 r.s_begin = p.s_xdone;
                 r.s_end = p.s_next;
                 r.int_start = istart;
@@ -650,10 +629,7 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
                 r.n_in_pad = h->n_in_pad;
                 r.n_chan = h->n_chan;
                 r.fp8 = h->precision == CORR_FP8;
-                r.pair_major = pair_major_ring(h);
-                r.i8b = h->precision == CORR_INT8;
-                r.codes_in = p.ring_codes;
-                r.C = p.words ? p.C : nullptr;
+                r.C = p.C;
                 {
                     Timed t_(h, 5, st);
                     launch_requant(r, st);
@@ -718,29 +694,23 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
 int finalize_into(corr_t h, Pipe& p, const Tables& t, float2* R, uint8_t* F, int count, int slots,
                   cudaStream_t st) {
     if (h->precision != CORR_FP32) {
-        // Tensor-core Gram of the integration's codes, then rescale and
-        // rotate (in the Gram kernel's epilogue for the code words, by
-        // finalize_q_kernel for row-major codes); the autocorrelations fix
-        // the next integration's scales.
+        // Tensor-core Gram of the integration's code words, rescaled and
+        // rotated into visibilities in the same kernel's epilogue; the
+        // autocorrelations then fix the next integration's scales.
         GramArgs g{};
-        g.Q = p.words ? static_cast<const void*>(p.C) : static_cast<const void*>(p.Q);
-        g.words = p.words;
+        g.Q = p.C;
+        g.words = 1;
         g.n_pairs = h->n_in_pad / 2;
         g.n_in = h->n_in;
         g.n_chan = h->n_chan;
         g.K = count;
-        g.k_pitch = p.q_pitch;
         g.fp8 = h->precision == CORR_FP8;
-        g.G = p.G;
         g.status = h->d_status;
         g.wait_ns = (unsigned long long)(h->tc_wait_ms * 1e6);
         g.inject_stall = h->inject_stall;
-        g.i8b = h->precision == CORR_INT8;
-        if (p.words) {
-            g.R = R;
-            g.scale = p.scale;
-            g.rot = t.rot;
-        }
+        g.R = R;
+        g.scale = p.scale;
+        g.rot = t.rot;
         int rc;
         {
             Timed t_(h, 6, st);
@@ -748,22 +718,6 @@ int finalize_into(corr_t h, Pipe& p, const Tables& t, float2* R, uint8_t* F, int
         }
         if (rc != CORR_OK) return fail(h, rc, "tensor-core Gram launch failed");
         CK(cudaGetLastError());
-        if (!p.words) {
-            FinQArgs f{};
-            f.G = p.G;
-            f.scale = p.scale;
-            f.rot = t.rot;
-            f.n_chan = h->n_chan;
-            f.n_in = h->n_in;
-            f.count = count;
-            f.fp8 = g.fp8;
-            f.R = R;
-            {
-                Timed t_(h, 3, st);
-                launch_finalize_q(f, st);
-            }
-            CK(cudaGetLastError());
-        }
         launch_scale_from_vis(R, h->n_in, h->n_in_pad, h->n_chan, g.fp8 ? kFp8Gain : kInt8Gain, p.scale, st);
         ++h->launches;
         CK(cudaGetLastError());
@@ -1077,9 +1031,7 @@ int pop_results(corr_t h, std::deque<int>& q, bool vis, void* out, int max_int, 
 void free_pipe(Pipe& p) {
     if (p.V) cudaFree(p.V);
     if (p.Z) cudaFree(p.Z);
-    if (p.Q) cudaFree(p.Q);
     if (p.C) cudaFree(p.C);
-    if (p.G) cudaFree(p.G);
     if (p.scale) cudaFree(p.scale);
     if (p.part) cudaFree(p.part);
     if (p.part_all) cudaFree(p.part_all);
@@ -1396,7 +1348,7 @@ int corr_reset(corr_t h) {
     h->buf_read[0] = h->buf_read[1] = false;
     h->n_pushed = 0;
     h->ps.s_next = h->ps.s_xdone = 0;
-    h->ps.have_scale = h->ps.ring_codes = false;
+    h->ps.have_scale = false;
     h->q_vis.clear();
     h->q_flag.clear();
     for (Slot& s : h->slots) s.in_vis = s.in_flag = false;
@@ -1446,7 +1398,7 @@ int corr_run_dev(corr_t h, const void* d_samples, size_t n_samples, size_t strid
         h->pd.part_all_ints = need;
     }
     h->pd.s_next = h->pd.s_xdone = 0;
-    h->pd.have_scale = h->pd.ring_codes = false;
+    h->pd.have_scale = false;
     StreamView sv;
     sv.x = static_cast<const int8_t*>(d_samples);
     sv.es = h->es;
@@ -2003,7 +1955,7 @@ struct StateHeader {
     char magic[8];
     int32_t version;
     int32_t n_in, n_chan, taps, n_int, precision, es, iq, window, flag_window, ring_mb;
-    int32_t v_cap, gpi, nt, G, q_pitch, n_in_pad;
+    int32_t v_cap, gpi, nt, G, code_words, n_in_pad;
     int32_t started, flushed, stream_alloc, have_scale, pending, n_vis_q, n_flag_q, reserved;
     double kaiser_beta, flag_sigma;
     int64_t max_delay, chunk, stage_cap, n_pushed, stage_base, stage_len, s_next, s_xdone, q_cols;
@@ -2029,10 +1981,10 @@ int corr_save_state(corr_t h, void* buf, size_t cap, size_t* size) {
     if (h->s_out) CK(cudaStreamSynchronize(h->s_out));
     StateHeader H{};
     std::memcpy(H.magic, kStateMagic, 8);
-    H.version = 1;
+    H.version = 2;
     H.n_in = h->n_in; H.n_chan = h->n_chan; H.taps = h->taps; H.n_int = h->n_int; H.precision = h->precision;
     H.es = h->es; H.iq = h->iq; H.window = h->window; H.flag_window = h->flag_window; H.ring_mb = h->ring_mb;
-    H.v_cap = h->ps.v_cap; H.gpi = h->gpi; H.nt = h->nt; H.G = h->G; H.q_pitch = h->ps.q_pitch; H.n_in_pad = h->n_in_pad;
+    H.v_cap = h->ps.v_cap; H.gpi = h->gpi; H.nt = h->nt; H.G = h->G; H.code_words = h->precision != CORR_FP32; H.n_in_pad = h->n_in_pad;
     H.started = h->started; H.flushed = h->flushed; H.stream_alloc = h->stream_alloc;
     H.have_scale = h->ps.have_scale; H.pending = h->pending;
     H.n_vis_q = (int32_t)h->q_vis.size(); H.n_flag_q = (int32_t)h->q_flag.size();
@@ -2077,13 +2029,8 @@ int corr_save_state(corr_t h, void* buf, size_t cap, size_t* size) {
             CKRET(put_dev(h->ps.part, sizeof(float) * (size_t)h->gpi * h->nt * 32 * h->n_chan));
         } else {
             CKRET(put_dev(h->ps.scale, 2 * sizeof(float) * (size_t)h->n_in_pad * h->n_chan));
-            if (h->ps.words) {
-                if (H.q_cols > 0)
-                    CKRET(put_dev(h->ps.C, sizeof(uint32_t) * (size_t)H.q_cols * (h->n_in_pad / 2) * h->n_chan));
-            } else {
-                for (size_t r = 0; r < (size_t)h->n_chan * 128 && H.q_cols > 0; ++r)
-                    CKRET(put_dev(h->ps.Q + r * h->ps.q_pitch, (size_t)H.q_cols));
-            }
+            if (H.q_cols > 0)
+                CKRET(put_dev(h->ps.C, sizeof(uint32_t) * (size_t)H.q_cols * (h->n_in_pad / 2) * h->n_chan));
         }
     }
     for (int idx : h->q_vis) w.put(h->slots[idx].h_R, ne * sizeof(float2));
@@ -2106,7 +2053,7 @@ int corr_load_state(corr_t h, const void* buf, size_t size) {
         return true;
     };
     StateHeader H{};
-    if (!get(&H, sizeof(H)) || std::memcmp(H.magic, kStateMagic, 8) != 0 || H.version != 1)
+    if (!get(&H, sizeof(H)) || std::memcmp(H.magic, kStateMagic, 8) != 0 || H.version != 2)
         return fail(h, CORR_EINVAL, "not a correlator state of this version");
     if (H.n_in != h->n_in || H.n_chan != h->n_chan || H.taps != h->taps || H.n_int != h->n_int ||
         H.precision != h->precision || H.es != h->es || H.iq != h->iq || H.window != h->window ||
@@ -2129,7 +2076,8 @@ int corr_load_state(corr_t h, const void* buf, size_t size) {
     const size_t per_spec = (size_t)h->n_chan * h->n_in_pad * sizeof(float2);
     if (H.stream_alloc) {
         CKRET(ensure_stream_alloc(h));
-        if (H.v_cap != h->ps.v_cap || H.gpi != h->gpi || H.q_pitch != h->ps.q_pitch || H.stage_cap != h->stage_cap ||
+        if (H.v_cap != h->ps.v_cap || H.gpi != h->gpi || H.code_words != (h->precision != CORR_FP32) ||
+            H.stage_cap != h->stage_cap ||
             H.stage_len > h->stage_cap)
             return fail(h, CORR_EINVAL, "state buffers do not match this handle's");
         auto get_dev = [&](void* dst, size_t b) -> int {
@@ -2149,13 +2097,8 @@ int corr_load_state(corr_t h, const void* buf, size_t size) {
             CKRET(get_dev(h->ps.part, sizeof(float) * (size_t)h->gpi * h->nt * 32 * h->n_chan));
         } else {
             CKRET(get_dev(h->ps.scale, 2 * sizeof(float) * (size_t)h->n_in_pad * h->n_chan));
-            if (h->ps.words) {
-                if (H.q_cols > 0)
-                    CKRET(get_dev(h->ps.C, sizeof(uint32_t) * (size_t)H.q_cols * (h->n_in_pad / 2) * h->n_chan));
-            } else {
-                for (size_t r = 0; r < (size_t)h->n_chan * 128 && H.q_cols > 0; ++r)
-                    CKRET(get_dev(h->ps.Q + r * h->ps.q_pitch, (size_t)H.q_cols));
-            }
+            if (H.q_cols > 0)
+                CKRET(get_dev(h->ps.C, sizeof(uint32_t) * (size_t)H.q_cols * (h->n_in_pad / 2) * h->n_chan));
         }
         h->stage_base = H.stage_base;
         h->stage_len = H.stage_len;

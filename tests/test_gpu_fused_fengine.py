@@ -151,8 +151,8 @@ def test_fused_streaming_pushes_match_run_dev():
 
 # (n_ant, n_pol, n_chan, n_int) of the reduced-precision pipelines whose
 # F-engine writes the codes itself: M = 1024 .. 8192, a padding input, 64
-# inputs, integration lengths that are not multiples of the requantiser's
-# 32-spectrum runs, a partial last integration
+# inputs, integration lengths that are not multiples of the Gram kernel's
+# 64- or 128-spectrum tiles, a partial last integration
 CODE_SHAPES = [(2, 1, 512, 37), (3, 2, 1024, 45), (5, 1, 2048, 22), (32, 2, 1024, 70), (12, 2, 4096, 9)]
 
 
@@ -162,11 +162,11 @@ CODE_SHAPES = [(2, 1, 512, 37), (3, 2, 1024, 45), (5, 1, 2048, 22), (32, 2, 1024
 def test_fused_codes_are_bit_identical_to_requantiser(prec, n_ant, n_pol, n_chan, n_int, run):
     """With fixed scales (from the first ring fill after the pre-pass on)
     the fused F-engine requantises in its epilogue and writes 4-byte code
-    words instead of spectra, which the requantiser only transposes into the
-    tensor-core operand; with fused_f = 0 the requantiser makes the codes
-    from the U = 2Y spectra of the two-kernel F-engine.  Same codes, so the
-    visibilities and flags agree bit for bit (runs of 5 spectra per CTA and
-    1 MiB rings put launch and run boundaries at odd columns)."""
+    words straight into the integration's word buffer instead of spectra;
+    with fused_f = 0 the requantiser makes the same words from the U = 2Y
+    spectra of the two-kernel F-engine.  Same codes, so the visibilities
+    and flags agree bit for bit (runs of 5 spectra per CTA and 1 MiB rings
+    put launch and run boundaries at odd columns)."""
     n_in = n_ant * n_pol
     M = 2 * n_chan
     S = M * (3 * n_int + 9) + 101
