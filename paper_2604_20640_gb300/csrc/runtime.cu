@@ -51,6 +51,7 @@ struct Slot {
     uint8_t* h_F = nullptr;
     cudaEvent_t ev = nullptr;
     bool in_vis = false, in_flag = false;
+    bool has_image = false;   // h_R / h_F hold the results (or will once ev completes)
 };
 
 struct Tables {
@@ -178,6 +179,8 @@ struct corr_s {
     long long z_f_spectra = 0;
     std::vector<Slot> slots;
     std::deque<int> q_vis, q_flag;
+    // the last pop went to pinned memory: new results get no host image
+    bool pop_pinned = false;
     std::string err;
     long long launches = 0;
     StageTimer timer;
@@ -797,19 +800,31 @@ int new_slot(corr_t h, int* idx) {
     return CORR_OK;
 }
 
+// Copies a slot's results into its pinned host image behind its kernels (on
+// s_out; s.ev then marks the image complete).
+int slot_image(corr_t h, Slot& s) {
+    const size_t ne = vis_elems(h);
+    CK(cudaStreamWaitEvent(h->s_out, s.ev, 0));
+    CK(cudaMemcpyAsync(s.h_R, s.d_R, ne * sizeof(float2), cudaMemcpyDeviceToHost, h->s_out));
+    CK(cudaMemcpyAsync(s.h_F, s.d_F, ne, cudaMemcpyDeviceToHost, h->s_out));
+    CK(cudaEventRecord(s.ev, h->s_out));
+    s.has_image = true;
+    return CORR_OK;
+}
+
 int sink_stream(corr_t h, void*, const Tables& t, long long, int count, int slots, cudaStream_t st) {
     int idx;
     CKRET(new_slot(h, &idx));
     Slot& s = h->slots[idx];
     CKRET(finalize_into(h, h->ps, t, s.d_R, s.d_F, count, slots, st));
-    const size_t ne = vis_elems(h);
     // The slot is rewritten only after the host has taken its results
-    // (pop_results waits on s.ev), so the copies may trail the kernels.
-    CK(cudaEventRecord(h->ev_fin, st));
-    CK(cudaStreamWaitEvent(h->s_out, h->ev_fin, 0));
-    CK(cudaMemcpyAsync(s.h_R, s.d_R, ne * sizeof(float2), cudaMemcpyDeviceToHost, h->s_out));
-    CK(cudaMemcpyAsync(s.h_F, s.d_F, ne, cudaMemcpyDeviceToHost, h->s_out));
-    CK(cudaEventRecord(s.ev, h->s_out));
+    // (pop_results waits on s.ev), so the copies may trail the kernels.  A
+    // caller that pops into pinned memory takes the results by DMA straight
+    // from the slot: while the last pop was such a one, no host image is
+    // made (a later pop into other memory, or a checkpoint, makes it).
+    CK(cudaEventRecord(s.ev, st));
+    s.has_image = false;
+    if (!h->pop_pinned) CKRET(slot_image(h, s));
     s.in_vis = s.in_flag = true;
     h->q_vis.push_back(idx);
     h->q_flag.push_back(idx);
@@ -1006,6 +1021,7 @@ int pop_results(corr_t h, std::deque<int>& q, bool vis, void* out, int max_int, 
                 e = cudaMemcpyAsync(dst, vis ? static_cast<const void*>(s.d_R) : static_cast<const void*>(s.d_F),
                                     bytes, cudaMemcpyDeviceToHost, h->s_get);
         } else {
+            if (!s.has_image && (rc = slot_image(h, s)) != CORR_OK) break;
             e = cudaEventSynchronize(s.ev);
             if (e == cudaSuccess)
                 std::memcpy(dst, vis ? static_cast<const void*>(s.h_R) : static_cast<const void*>(s.h_F), bytes);
@@ -1018,6 +1034,7 @@ int pop_results(corr_t h, std::deque<int>& q, bool vis, void* out, int max_int, 
         q.pop_front();
         ++got;
     }
+    if (!taken.empty()) h->pop_pinned = pinned;
     if (pinned && !taken.empty()) {
         const cudaError_t e = cudaStreamSynchronize(h->s_get);
         if (e != cudaSuccess && rc == CORR_OK) rc = fail(h, CORR_ECUDA, std::string("result copy: ") + cudaGetErrorString(e));
@@ -2033,6 +2050,15 @@ int corr_save_state(corr_t h, void* buf, size_t cap, size_t* size) {
                 CKRET(put_dev(h->ps.C, sizeof(uint32_t) * (size_t)H.q_cols * (h->n_in_pad / 2) * h->n_chan));
         }
     }
+    // queued results without a host image get one first
+    bool imaged = false;
+    for (const std::deque<int>* q : {&h->q_vis, &h->q_flag})
+        for (int idx : *q)
+            if (!h->slots[idx].has_image) {
+                CKRET(slot_image(h, h->slots[idx]));
+                imaged = true;
+            }
+    if (imaged) CK(cudaStreamSynchronize(h->s_out));
     for (int idx : h->q_vis) w.put(h->slots[idx].h_R, ne * sizeof(float2));
     for (int idx : h->q_flag) w.put(h->slots[idx].h_F, ne);
     if (buf && w.n > cap) return fail(h, CORR_EINVAL, "state buffer too small (" + std::to_string(w.n) + " bytes needed)");
@@ -2137,6 +2163,7 @@ int corr_load_state(corr_t h, const void* buf, size_t size) {
             h->q_flag.push_back(idx);
         }
         CK(cudaEventRecord(sl.ev, h->s_out));
+        sl.has_image = true;
     }
     h->started = H.started != 0;
     h->flushed = H.flushed != 0;

@@ -386,6 +386,41 @@ def test_results_popped_into_pinned_and_pageable_buffers_agree():
             c.get_vis(max_int=1, out=bad)
 
 
+def test_results_without_host_images_after_pinned_pops():
+    """After a pop into pinned memory, new results get no host image (the next
+    pinned pop takes them by DMA from the device slots); a pop into pageable
+    memory, or a checkpoint, makes the image on demand.  Every route gives
+    the results of a stream popped the usual way."""
+    n_chan, n_int, n_in = 256, 8, 4
+    M = 2 * n_chan
+    third = M * n_int * 2
+    S = 3 * third + 300
+    x = _stream(n_in, S, seed=29)
+    ref = _corr(n_in, 1, n_chan, 4, n_int)
+    ref.push(x)
+    ref.flush()
+    Rv, Rf = ref.get_vis(), ref.get_flags()
+    assert Rv.shape[0] == 6
+    c = _corr(n_in, 1, n_chan, 4, n_int)
+    shape = (8, n_chan, n_in, n_in)
+    pv = torch.zeros(shape, dtype=torch.complex64).pin_memory()
+    pf = torch.zeros(shape, dtype=torch.uint8).pin_memory()
+    c.push(x[:, :third])
+    vs = [c.get_vis(out=pv).numpy().copy()]
+    fs = [c.get_flags(out=pf).numpy().copy()]            # pinned: later results skip the image
+    c.push(x[:, third:2 * third])
+    vs.append(c.get_vis())                               # pageable: image made on demand
+    fs.append(c.get_flags(out=pf).numpy().copy())        # pinned again
+    c.push(x[:, 2 * third:])
+    c.flush()
+    state = c.save_state()                               # queued results without images
+    c2 = _corr(n_in, 1, n_chan, 4, n_int)
+    c2.load_state(state)
+    vs.append(c2.get_vis())
+    fs.append(c2.get_flags())
+    assert np.array_equal(np.concatenate(vs), Rv) and np.array_equal(np.concatenate(fs), Rf)
+
+
 def test_stage_times_and_stage_mask():
     n_chan, n_int, n_in = 256, 8, 4
     M = 2 * n_chan
