@@ -214,8 +214,11 @@ int corr_reset(corr_t h);
  * [max_int][n_chan][n_in][n_in] (vis: complex64 as float pairs; flags: uint8).
  * Visibilities and flags are popped independently, in the same order.
  * Page-locked (pinned) out is filled by DMA straight from device memory;
- * other host memory receives a copy of the library's pinned image.  Blocks
- * only until the popped integrations' results have landed.
+ * other host memory receives a copy of the library's pinned image.  While
+ * the last pop went to pinned memory, integrations finished afterwards get
+ * no pinned image (no second device-to-host copy); a pop into other memory
+ * makes it then.  Blocks only until the popped integrations' results have
+ * landed.
  * *n_got receives the count (0 and CORR_EAGAIN when none is queued).
  */
 int corr_get_vis(corr_t h, float* out, int max_int, int* n_got);
