@@ -72,6 +72,11 @@ struct FftArgs {
     // of its M-point spectrum Z are stored, channel-major with n_chan = M,
     // as U = 2Z (phasor null) or V = Z P (phasor = the rotation)
     int iq;
+    // codes instead of spectra (M = 16384, the size the fused F-engine does
+    // not cover): V holds the pair-major code words [slot][pair][n_chan]
+    // made with the inverse scales inv [n_in_pad][n_chan], e4m3 when fp8
+    const float* inv;
+    bool fp8;
 };
 
 // Fused F-engine (PFB + FFT in one kernel; the FIR output stays in shared

@@ -44,6 +44,11 @@ static int launch_fft_mode(const FftArgs& a, cudaStream_t st) {
 
 int launch_fft(const FftArgs& a, cudaStream_t st) {
     if (a.s_end <= a.s_begin) return CORR_OK;
+    if (a.inv) {
+        // code words out: the size the fused F-engine leaves to this path
+        if (a.M != 16384 || a.iq || a.tiles || a.phasor) return CORR_EINVAL;
+        return a.fp8 ? launch_fft_m<16384, 7>(a, st) : launch_fft_m<16384, 6>(a, st);
+    }
     if (a.iq) return launch_fft_iq(a, st);
     if (a.tiles) return launch_fft_mode<2>(a, st);
     if (a.phasor) return launch_fft_mode<1>(a, st);

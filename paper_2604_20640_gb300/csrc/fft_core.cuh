@@ -702,6 +702,26 @@ __global__ void __launch_bounds__(FftCfg<M>::threads(MODE), FftCfg<M>::minb(MODE
                     pb[i] = 0.f;
                 }
             }
+        } else if constexpr (MODE >= 6) {
+            // codes (6 int8, 7 e4m3): the fused F-engine's epilogue -- the
+            // requantiser's arithmetic on U = 2Y, one word of the pair's four
+            // codes per channel, consecutive channels across the threads
+            constexpr bool FP8 = MODE == 7;
+            const long long slot = (s - A.v_origin) & A.v_mask;
+            uint32_t* const Cout = reinterpret_cast<uint32_t*>(A.V) + ((size_t)slot * n_pairs + pair) * n_chan;
+            const float* const inv0 = A.inv + (size_t)a * n_chan;
+            const float* const inv1 = inv0 + n_chan;
+            const bool has0 = a < A.n_in, has1 = a + 1 < A.n_in;
+            for (int k = tid; k < n_chan; k += C::THREADS) {
+                const float2 zk = zres[pidx(k)];
+                const float2 zm = zres[pidx((M - k) & (M - 1))];
+                const float ia = has0 ? __ldg(inv0 + k) : 0.f;
+                const float ib = has1 ? __ldg(inv1 + k) : 0.f;
+                const float sx = zk.x + zm.x, sy = zk.y - zm.y;
+                const float dx = zk.x - zm.x, dy = zk.y + zm.y;
+                Cout[k] = q_code<FP8>(sx * ia) | (q_code<FP8>(sy * ia) << 8) | (q_code<FP8>(dy * ib) << 16) |
+                          (q_code<FP8>(-dx * ib) << 24);
+            }
         } else if constexpr (MODE >= 4) {
             // complex input: all M channels of input `pair`, channel-major
             // (n_chan = M), U = 2Z (4) or the rotated V = Z P (5)
@@ -1242,7 +1262,7 @@ int launch_fft_m(const FftArgs& a, cudaStream_t st) {
     const long long n = a.s_end - a.s_begin;
     // transforms per spectrum: one per input pair, or one per input (complex
     // input); n_in_pad is a multiple of 4
-    const int n_groups = (MODE >= 4 ? a.n_in_pad : a.n_in_pad / 2) / C::pairs(MODE);
+    const int n_groups = (MODE == 4 || MODE == 5 ? a.n_in_pad : a.n_in_pad / 2) / C::pairs(MODE);
     long long runs = (long long)sms * resident / n_groups;
     if (runs > n) runs = n;
     if (runs < 1) runs = 1;

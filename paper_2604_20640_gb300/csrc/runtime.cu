@@ -459,15 +459,21 @@ struct CodeOut {
     bool fp8;
 };
 
-// The fused F-engine can write the pipeline's codes for this handle.
+// The fused F-engine writes the pipeline's codes for this handle.
 bool fused_codes(corr_t h, const StreamView& sv) {
     return h->precision != CORR_FP32 && h->fused_f && !h->iq &&
            fused_f_supported(h->M, h->taps, sv.es, h->precision == CORR_FP8 ? 7 : 6);
 }
 
+// The F-engine writes them: the fused kernel, or the two-kernel FFT at
+// M = 16384 (beyond the fused kernel's shared memory).
+bool f_codes(corr_t h, const StreamView& sv) {
+    return fused_codes(h, sv) || (h->precision != CORR_FP32 && !h->iq && h->M == 16384);
+}
+
 // F-engine over spectra [s_begin, s_end): FIR into the Z ring, FFT into the
-// V ring.  `phasor` set -> rotated V (stage call); `codes` set -> the V ring
-// holds requantised code words instead of spectra (fused kernel only); else
+// V ring.  `phasor` set -> rotated V (stage call); `codes` set -> V holds
+// requantised code words instead of spectra (where f_codes holds); else
 // U = 2Y (pipeline).
 int launch_f(corr_t h, const StreamView& sv, const Tables& t, float2* Z, long long z_origin, long long z_mask,
              float2* V, long long v_origin, long long v_mask, const float2* phasor, long long s_begin,
@@ -511,7 +517,11 @@ int launch_f(corr_t h, const StreamView& sv, const Tables& t, float2* Z, long lo
     f.pair_major = phasor == nullptr && tiles == nullptr && pair_major_ring(h);
     f.iq = h->iq;
     const int mode = codes ? (codes->fp8 ? 7 : 6) : tiles ? 2 : phasor ? 1 : f.pair_major ? 3 : 0;
-    if (codes && !fused_codes(h, sv)) return fail(h, CORR_EINVAL, "codes from the F-engine need the fused kernel");
+    if (codes && !f_codes(h, sv)) return fail(h, CORR_EINVAL, "codes from the F-engine: not for this shape");
+    if (codes) {
+        f.inv = codes->inv;
+        f.fp8 = codes->fp8;
+    }
     if (h->fused_f && !h->iq && fused_f_supported(h->M, h->taps, sv.es, mode)) {
         FusedArgs u{};
         u.f = f;
@@ -578,8 +588,9 @@ int drive(corr_t h, Pipe& p, const StreamView& sv, Tables& t, long long ready_en
         // the ring bounds a launch, except where the F-engine writes code
         // words straight into the integration's word buffer (then one launch
         // may cover the rest of the integration)
-        const bool to_words = p.have_scale && p.s_xdone == p.s_next && fused_codes(h, sv);
-        if (!to_words && s_end > p.s_xdone + p.v_cap) s_end = p.s_xdone + p.v_cap;
+        const bool to_words = p.have_scale && p.s_xdone == p.s_next && f_codes(h, sv);
+        // (the two-kernel path keeps the bound: its FIR fills the z ring)
+        if (!(to_words && fused_codes(h, sv)) && s_end > p.s_xdone + p.v_cap) s_end = p.s_xdone + p.v_cap;
         if (s_end > p.s_next) {
             if (to_words) {
                 // scales fixed and nothing left in the ring: the F-engine

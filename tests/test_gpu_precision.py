@@ -66,6 +66,38 @@ def test_precision_run_matches_oracle(prec, name, n_ant, n_chan, n_int):
     assert np.abs(da - 1).max() < 2e-3
 
 
+@pytest.mark.parametrize("prec,name,bar", [(1, "int8", 5e-3), (2, "e4m3", 1e-2)])
+def test_precision_codes_from_the_two_kernel_fft(prec, name, bar):
+    """8192 channels (M = 16384, beyond the fused F-engine): from the second
+    integration on the two-kernel F-engine's FFT writes the code words
+    itself.  The code path is checked against the oracle that emulates the
+    same requantisation (within 1e-3, as above).  Against full precision the
+    bar is the requantisation noise of K = 512 spectra: rho's noise falls as
+    1/sqrt(K), and e4m3's (3 mantissa bits, about 1.8e-3 at K = 4096 over 16
+    inputs) reaches 5e-3 at K = 512, so its bar is 1e-2 over 8192 channels;
+    int8's stays under 5e-3."""
+    from paper_2604_20640_gb300 import Correlator
+    n_ant, n_chan, n_int = 2, 8192, 512
+    n_in = 2 * n_ant
+    M = 2 * n_chan
+    S = M * n_int * 2 + 100
+    x, tau, phi = _stream(n_ant, 2, S, seed=n_ant * 10 + prec)
+    c = Correlator(n_ant, 2, n_chan, 4, n_int, precision=prec)
+    c.set_delays(tau, phi)
+    xd = torch.from_numpy(x).to(DEV)
+    n = c.n_integrations(S)
+    vis = torch.empty((n, n_chan, n_in, n_in), dtype=torch.complex64, device=DEV)
+    flags = torch.empty((n, n_chan, n_in, n_in), dtype=torch.uint8, device=DEV)
+    assert c.run_dev(xd, vis, flags) == n == 2
+    torch.cuda.synchronize()
+    assert c.device_status() == 0
+    rho_g = fx.normalised_coefficients(vis.cpu().numpy().astype(np.complex128))
+    Rq, _ = rq.correlate_quantized(x, n_chan, 4, n_int, tau, phi, dtype=name)
+    assert np.abs(rho_g - fx.normalised_coefficients(Rq)).max() < 1e-3
+    Ro = fx.correlate(x, n_chan, 4, n_int, tau, phi)[0]
+    assert np.abs(rho_g - fx.normalised_coefficients(Ro)).max() < bar
+
+
 def test_precision_streaming_chunking_is_bit_identical():
     from paper_2604_20640_gb300 import Correlator
     n_ant, n_chan, n_int = 8, 128, 300
