@@ -589,7 +589,9 @@ __device__ __forceinline__ const float2* fft_input(const FftArgs& A, long long s
 }
 
 // MODE 0: store U = 2Y; 1: store the rotated V; 2: accumulate power tiles;
-// 3: store U = 2Y pair-major ([slot][pair][n_chan] float4).
+// 3: store U = 2Y pair-major ([slot][pair][n_chan] float4); 4 / 5: complex
+// input; 6 / 7: int8 / e4m3 code words of U (pair-major, as the fused
+// kernel writes them).
 template <int M, int MODE>
 __global__ void __launch_bounds__(FftCfg<M>::threads(MODE), FftCfg<M>::minb(MODE))
     fft_kernel(const FftArgs A, const __grid_constant__ CUtensorMap vmap) {
