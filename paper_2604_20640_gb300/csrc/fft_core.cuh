@@ -793,10 +793,10 @@ __global__ void __launch_bounds__(FftCfg<M>::threads(MODE), FftCfg<M>::minb(MODE
 // in shared memory and transforms it, so the FIR output (z) never leaves the
 // SM and each input sample is read from HBM once.
 //
-// Thread t owns branches 8t .. 8t+7 and their mirrors M-8-8t .. M-1-8t.  The
-// prototype is symmetric, h[pM + M-1-m] = h[(P-1-p)M + m], so the lower half
-// of each polyphase row, hs[p][m] (m < M/2, in shared memory), gives the
-// coefficients of both.  The last P-1 frames of the thread's 16 branches of
+// Thread t owns the branch groups 4t .. 4t+3 and B .. B+3 (B = 4t + M/2 at
+// M = 8192, 4t + M/4 below) and their mirrors.  The prototype is symmetric,
+// h[pM + M-1-m] = h[(P-1-p)M + m], so the lower half of each polyphase row,
+// hs[p][m] (m < M/2, in shared memory), gives the coefficients of both.  The last P-1 frames of the thread's 16 branches of
 // both inputs stay in registers as raw int8 words (sign bits flipped, ready to
 // unpack).  The newest frame arrives in a shared staging buffer by cp.async:
 // bytes [A, A + M + 32) of each input's row, A the 16-byte aligned address at
