@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(128) finalize_kernel(const FinArgs F) {
 // shuffles inside the group above -- the median read from the sorted order
 // (even count: mean of the two middle values), then |A - med| sorted the
 // same way for the MAD.  L = 32 (a warp an item) where a call has few items;
-// L = 8 where it has many (more items a warp, fewer shuffles).  Every form
+// L = 4 where it has many (more items a warp, fewer shuffles).  Every form
 // gives the same order statistics and the same threshold bits.
 constexpr int kFlagWarps = 4;
 
@@ -440,11 +440,11 @@ __global__ void __launch_bounds__(32 * kFlagWarps) mad_flag_kernel(const float2*
     mad_flag_item<E, 32>(R, F, n_chan, n_in, W, sigma, item, lane);
 }
 
-// Many items (large arrays): groups of 8 lanes, 32 / 8 items a warp.  A
+// Many items (large arrays): groups of 4 lanes, 32 / 4 items a warp.  A
 // group past the last item computes the last item again without storing, so
 // that every lane of the warp takes part in the shuffles.
 constexpr long long kGroupFlagItems = 16384;
-constexpr int kFlagGroup = 8;
+constexpr int kFlagGroup = 4;
 
 template <int E>
 __global__ void __launch_bounds__(128) mad_flag_group_kernel(const float2* R, uint8_t* F, int n_vis, int n_chan,
@@ -628,9 +628,10 @@ void launch_mad_flags(const float2* R, uint8_t* F, int n_vis, int n_chan, int n_
     if (items <= 0) return;
     if (window <= 64 && items >= kGroupFlagItems) {
         const unsigned tb = (unsigned)((items * kFlagGroup + 127) / 128);
-        if (window <= 16) mad_flag_group_kernel<2><<<tb, 128, 0, st>>>(R, F, n_vis, n_chan, n_in, window, sigma);
-        else if (window <= 32) mad_flag_group_kernel<4><<<tb, 128, 0, st>>>(R, F, n_vis, n_chan, n_in, window, sigma);
-        else mad_flag_group_kernel<8><<<tb, 128, 0, st>>>(R, F, n_vis, n_chan, n_in, window, sigma);
+        constexpr int G = kFlagGroup;
+        if (window <= 16) mad_flag_group_kernel<16 / G><<<tb, 128, 0, st>>>(R, F, n_vis, n_chan, n_in, window, sigma);
+        else if (window <= 32) mad_flag_group_kernel<32 / G><<<tb, 128, 0, st>>>(R, F, n_vis, n_chan, n_in, window, sigma);
+        else mad_flag_group_kernel<64 / G><<<tb, 128, 0, st>>>(R, F, n_vis, n_chan, n_in, window, sigma);
         return;
     }
     const unsigned blocks = (unsigned)((items + kFlagWarps - 1) / kFlagWarps);

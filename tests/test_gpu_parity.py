@@ -175,7 +175,7 @@ def test_xengine_dev_long_stream_beyond_the_grid_limit():
 
 
 # the last four have >= 16384 (window, baseline) items per call: a group of
-# 8 lanes per item instead of a warp (the last: 16650 items, so the last warp
+# 4 lanes per item instead of a warp (the last: 16650 items, so the last warp
 # holds groups past the end that must store nothing)
 @pytest.mark.parametrize("window,n_chan,n_in", [(64, 256, 3), (64, 64, 1), (32, 128, 4), (8, 8, 2), (256, 512, 2),
                                                 (64, 1024, 40), (32, 512, 28), (16, 256, 64), (64, 128, 74)])
