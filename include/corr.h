@@ -125,7 +125,8 @@ const char* corr_last_error(corr_t h);
  *                  With reduced precision the fused kernel also makes the
  *                  int8 / e4m3 code words once an integration's scales are
  *                  fixed, straight into the words the tensor-core X-engine
- *                  reads; the codes equal the requantiser's
+ *                  reads (at M = 16384 the two-kernel FFT does, whatever
+ *                  this option); the codes equal the requantiser's
  *   "sample_bits"  (8, default; or 16)  input sample type of every call that
  *                  takes samples: int8 (the 8-bit truncated recorder mode of
  *                  Sec. 3) or little-endian int16 (the 16-bit padded mode,
